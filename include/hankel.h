@@ -1,0 +1,226 @@
+/*
+ * hankel.h -- C ABI of the GB300 (sm_103a) fast Hankel-type transform library.
+ *
+ * The library evaluates the sums of Townsend, "A fast analysis-based
+ * discrete Hankel transform using asymptotic expansions" (arXiv:1501.01652),
+ * Eq. (2):
+ *
+ *     f_k = sum_{n=1}^{N} c_n J_nu(r_k omega_n),   k = 1..N,
+ *
+ * for the three tasks of Section 1:
+ *   HANKEL_SCHLOMILCH      omega_n = (n+gamma) pi (Section 4, Eq. 11; the
+ *                          integer shift gamma is Remark 4.1's), any nu >= 0;
+ *   HANKEL_FOURIER_BESSEL  omega_n = j_{0,n}, the n-th root of J_0
+ *                          (Section 5, Eq. 20), any nu >= 0;
+ *   HANKEL_DHT             the discrete Hankel transform of order 0
+ *                          (Section 6, Eq. 25): nu = 0, omega_n = j_{0,n},
+ *                          r_k = j_{0,k}/j_{0,N+1}.
+ * For the first two tasks the sample points are r_k = (k-1)/(N-1)
+ * (HANKEL_GRID_UNIT, the default) or the paper's r_k = k/N
+ * (HANKEL_GRID_PAPER).
+ *
+ * Method (Sections 3-6): the N x N matrix J_nu(r omega^T) is split into a
+ * near field, summed directly with J evaluated per entry, and the far-field
+ * blocks of the recursive partition of Section 4.2 (Eq. 19), where J is
+ * replaced by 2M terms of its Hankel expansion (Eq. 4) wrapped, for Bessel-
+ * root nodes, in the truncated Neumann-addition/Taylor sums of Sections 5.1
+ * and 6 (Eqs. 21, 22, 26). The parameters M, s_{nu,M}(eps), alpha, beta, P,
+ * K and T come from the paper's Table 4 and Eqs. (23)-(24). Each far block
+ * becomes one multi-column chirp-z transform on the GPU.
+ *
+ * Conventions shared by every call:
+ *  - Index k and n are 1-based in the formulas; arrays are 0-based, so
+ *    c[n-1] holds c_n and f[k-1] holds f_k.
+ *  - Device pointers are CUDA global-memory pointers of the device the plan
+ *    was created on; host pointers are ordinary pageable or pinned memory.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream). Device-pointer calls are asynchronous and stream-ordered.
+ *  - Return values are hankel_status codes; nothing is thrown across the ABI.
+ *    On any code other than HANKEL_OK, output buffers hold unspecified data.
+ *  - A plan serialises its own executions: it owns one workspace, so two
+ *    executions of the same plan must not overlap on the GPU. Distinct
+ *    plans are independent.
+ */
+#ifndef HANKEL_H
+#define HANKEL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Opaque plan handle. Owned by the caller from hankel_plan*() until hankel_destroy(). */
+typedef struct hankel_plan_s* hankel_plan_t;
+
+enum hankel_task {
+  HANKEL_SCHLOMILCH = 0,
+  HANKEL_FOURIER_BESSEL = 1,
+  HANKEL_DHT = 2
+};
+
+enum hankel_grid {
+  HANKEL_GRID_UNIT = 0,  /* r_k = (k-1)/(N-1) */
+  HANKEL_GRID_PAPER = 1  /* r_k = k/N (Sections 4, 5) */
+};
+
+enum hankel_precision {
+  HANKEL_PREC_AUTO = 0,  /* FP64 below eps = 1e-5, FP32 transform stages at eps >= 1e-5 */
+  HANKEL_PREC_FP64 = 1,  /* every stage in FP64 */
+  HANKEL_PREC_FP32 = 2   /* FP32 stages; refused (HANKEL_EUNSUPPORTED) when eps < 1e-5 */
+};
+
+enum hankel_status {
+  HANKEL_OK = 0,
+  HANKEL_EINVAL = 1,        /* an argument is out of range or inconsistent */
+  HANKEL_ENOMEM = 2,        /* a host or device allocation failed */
+  HANKEL_ECUDA = 3,         /* a CUDA runtime call or kernel launch failed */
+  HANKEL_EUNSUPPORTED = 4,  /* a valid request this build does not serve */
+  HANKEL_ETIMEOUT = 5       /* a bounded device wait expired */
+};
+
+/* Plan flags (hankel_options.flags). */
+#define HANKEL_FLAG_HOST_ONLY 1u  /* build host tables only; no CUDA call is made */
+
+/* Options for hankel_plan_ex(). Fill with hankel_options_default() first. */
+typedef struct {
+  int task;               /* enum hankel_task */
+  int nu;                 /* order of J; >= 0; must be 0 for HANKEL_DHT */
+  int64_t N;              /* number of coefficients and of outputs; 2 <= N <= 2^24 */
+  double eps;             /* working accuracy, 1e-16 <= eps < 1 */
+  int grid;               /* enum hankel_grid (tasks 0 and 1 only) */
+  int64_t gamma;          /* Schlomilch shift: omega_n = (n+gamma) pi; default nu */
+  int precision;          /* enum hankel_precision */
+  int max_nrhs;           /* largest nrhs a batched call will pass; >= 1 */
+  unsigned flags;         /* HANKEL_FLAG_* */
+  size_t workspace_limit; /* device bytes the plan may use for FFT columns; 0 = default (4 GiB) */
+} hankel_options;
+
+/* Parameters a plan chose (Table 4, Eqs. 23-24) and its sizes. */
+typedef struct {
+  int task, nu, grid, precision;
+  int64_t N, gamma;
+  double eps;
+  int M;                  /* terms of the Hankel expansion, Eq. (4): 2M terms */
+  int mu_max;             /* largest |order| met by the expansion in this task */
+  double s;               /* s_{mu_max,M}(eps), Section 3.1 */
+  double alpha, beta;     /* partition parameters, Table 4 */
+  int P;                  /* number of partition levels, Table 4 */
+  int K, T;               /* Neumann / Taylor truncation for the row perturbation (DHT) or column perturbation (FB) */
+  int K2, T2;             /* column-perturbation truncation of the DHT (equal to K, T otherwise) */
+  int64_t direct_rows;    /* leading rows summed directly (DHT, Section 6) */
+  int64_t direct_cols;    /* leading columns summed directly (FB and DHT, Section 5) */
+  int nblocks;            /* far-field blocks actually used (1 + 2P at most) */
+  int ncols;              /* stacked transform columns per block per right-hand side */
+  int npairs;             /* Schlomilch-type evaluations in the paper's count: 1, 2T+K-2 or (2T+K-2)^2 */
+  int64_t near_count;     /* matrix entries summed directly */
+  int64_t far_count;      /* matrix entries covered by far-field blocks */
+  double near_zmax;       /* largest argument r_k omega_n in the near field */
+  size_t device_bytes;    /* device memory held by the plan (tables + workspace) */
+  size_t workspace_bytes; /* part of device_bytes used as transform workspace */
+} hankel_info;
+
+/* One far-field block of the partition, 1-based inclusive index ranges. */
+typedef struct {
+  int64_t k0, k1;  /* rows */
+  int64_t n0, n1;  /* columns */
+  int64_t fft_len; /* chirp-z transform length F (a power of two >= rows + cols - 1) */
+} hankel_block;
+
+/* Fill *o with defaults for (task, nu, N, eps). Host only. Returns HANKEL_OK or HANKEL_EINVAL (o == NULL). */
+int hankel_options_default(hankel_options* o, int task, int nu, int64_t N, double eps);
+
+/* Create a plan with default options on the current CUDA device.
+ * Computes parameters, nodes (j_{0,n} as (n, b_n)), the partition, weight
+ * tables and chirp spectra, and allocates the workspace. Blocking. */
+int hankel_plan(hankel_plan_t* out, int task, int nu, int64_t N, double eps);
+
+/* Create a plan from options. With HANKEL_FLAG_HOST_ONLY no CUDA call is made and
+ * only hankel_plan_info / hankel_plan_blocks / hankel_plan_entry / hankel_destroy
+ * accept the plan. Errors: EINVAL (bad option), EUNSUPPORTED (eps < 1e-16, FP32 asked
+ * at eps < 1e-5), ENOMEM, ECUDA. *out is NULL on error. */
+int hankel_plan_ex(hankel_plan_t* out, const hankel_options* opts);
+
+/* f = J_nu(r omega^T) c for one vector. c and f are device arrays of N doubles
+ * (c read, f overwritten); they may not overlap. Asynchronous on `stream`. */
+int hankel_exec(hankel_plan_t p, const double* c, double* f, void* stream);
+
+/* Batched form: for r < nrhs, f[r*ldf + k-1] = sum_n c[r*ldc + n-1] J_nu(r_k omega_n).
+ * Device arrays; ldc, ldf >= N; 1 <= nrhs <= max_nrhs of the plan. Asynchronous. */
+int hankel_exec_batched(hankel_plan_t p, const double* c, int64_t ldc, double* f, int64_t ldf,
+                        int nrhs, void* stream);
+
+/* End-to-end form with HOST arrays (same layout as hankel_exec_batched): copies c to the
+ * device, runs the transform and copies f back. Blocks until f is written. */
+int hankel_exec_host(hankel_plan_t p, const double* c, int64_t ldc, double* f, int64_t ldf, int nrhs);
+
+/* Parameters and sizes of a plan. Host only. */
+int hankel_plan_info(hankel_plan_t p, hankel_info* out);
+
+/* Copy up to `cap` far-field blocks into out; *count receives the number of blocks. Host only. */
+int hankel_plan_blocks(hankel_plan_t p, hankel_block* out, int cap, int* count);
+
+/* Host evaluation of the plan's representation of matrix entry (k, n), 1-based:
+ * *value receives the number the plan uses for J_nu(r_k omega_n) (the near-field
+ * evaluator or the far-field expansion) and *is_far is 1 when (k, n) lies in a
+ * far-field block. Slow; for tests. Host only. */
+int hankel_plan_entry(hankel_plan_t p, int64_t k, int64_t n, double* value, int* is_far);
+
+/* Near-field prefix of row k (1-based): columns 1..*nend are summed directly. Host only. */
+int hankel_plan_near_prefix(hankel_plan_t p, int64_t k, int64_t* nend);
+
+/* Execution stages of a plan, for hankel_plan_stage_stats(). */
+enum hankel_stage {
+  HANKEL_STAGE_NEAR = 0,      /* near-field direct sum (and its partial-sum combine) */
+  HANKEL_STAGE_GEN = 1,       /* far-field column generation */
+  HANKEL_STAGE_FFT = 2,       /* forward and inverse multi-column FFT passes */
+  HANKEL_STAGE_POINTWISE = 3, /* product with the chirp spectrum */
+  HANKEL_STAGE_OUT = 4,       /* row weights and accumulation into f */
+  HANKEL_STAGE_COUNT = 5
+};
+
+/* Accumulated statistics of one stage since timing was (re)enabled. */
+typedef struct {
+  double ms;         /* summed kernel time from CUDA events on the execution stream (0 when timing is off) */
+  double flops;      /* algorithmic floating-point operations (FFT: 5 F log2 F per column transform) */
+  double entries;    /* near field: matrix entries evaluated (times right-hand sides) */
+  int64_t launches;  /* kernel launches */
+} hankel_stage_stat;
+
+/* Enable (1) or disable (0) per-stage event timing for later executions of p and reset the
+ * accumulated statistics. Launch counts are accumulated in both modes. Host call. */
+int hankel_plan_set_timing(hankel_plan_t p, int enable);
+
+/* Copy the accumulated statistics of every stage into out[HANKEL_STAGE_COUNT]. Waits for the
+ * recorded events of earlier executions to complete. Host call. */
+int hankel_plan_stage_stats(hankel_plan_t p, hankel_stage_stat* out);
+
+/* Release a plan and all memory it holds. NULL is accepted. Synchronises the plan's device work. */
+int hankel_destroy(hankel_plan_t p);
+
+/* Static, NUL-terminated description of a status code. Never NULL. */
+const char* hankel_status_string(int status);
+
+/* ---- Host-only parameter formulas (no plan, no GPU) ---- */
+
+/* s_{nu,M}(eps): four fixed-point iterations from s = 1 (Section 3.1, Table 1). */
+double hankel_s_nu_M(int nu, int M, double eps);
+/* t_{nu,T}(eps) ~ (2^{2T+nu} (T+nu)! T! eps)^{1/(2T+nu)} (Section 3.2, Table 2). */
+double hankel_t_nu_T(int nu, int T, double eps);
+/* Largest |dz| with 5.2 (e|dz|/2)^K <= eps: (2/e)(eps/5.2)^{1/K} (Eq. 10, Table 3). */
+double hankel_neumann_radius(int K, double eps);
+/* p_K(eps) of Eq. (23) and q_T(eps) of Eq. (24). */
+double hankel_p_K(int K, double eps);
+double hankel_q_T(int T, double eps);
+/* Parameters a plan with these options would choose, without building it. */
+int hankel_params(const hankel_options* opts, hankel_info* out);
+/* b[n-1] = j_{0,n} - (n-1/4) pi for n = 1..count (Lemma 3.2), computed to full FP64
+ * relative accuracy (host only; b must hold count doubles). Returns HANKEL_EINVAL if
+ * count < 1 or b == NULL. */
+int hankel_j0_zero_offsets(int64_t count, double* b);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HANKEL_H */

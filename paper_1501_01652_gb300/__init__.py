@@ -1,0 +1,172 @@
+"""GB300-native fast Hankel-type transforms (Townsend, arXiv:1501.01652).
+
+Thin Python binding over the C ABI of ``include/hankel.h``: every step of the
+transform runs in the CUDA library ``_build/libhankel.so``; this module only
+marshals arguments (torch CUDA tensors or numpy arrays) and raises on error.
+There is no CPU fallback: if the library cannot be built or a CUDA call fails,
+the call raises.
+"""
+import ctypes
+
+import numpy as np
+
+from . import _lib
+
+TASKS = {"schlomilch": 0, "fourier_bessel": 1, "dht": 2}
+GRIDS = {"unit": 0, "paper": 1}
+PRECISIONS = {"auto": 0, "fp64": 1, "fp32": 2}
+
+
+def _options(task, nu, N, eps, grid="unit", gamma=None, precision="auto", max_nrhs=1, workspace_limit=0,
+             host_only=False):
+    lib = _lib.load()
+    o = _lib.Options()
+    _lib.check(lib.hankel_options_default(ctypes.byref(o), TASKS[task], int(nu), int(N), float(eps)),
+               "hankel_options_default")
+    o.grid = GRIDS[grid]
+    if gamma is not None:
+        o.gamma = int(gamma)
+    o.precision = PRECISIONS[precision]
+    o.max_nrhs = int(max_nrhs)
+    o.workspace_limit = int(workspace_limit)
+    o.flags = _lib.FLAG_HOST_ONLY if host_only else 0
+    return o
+
+
+def params(task, nu, N, eps, **kw):
+    """Parameters (Table 4, Eqs. 23-24) a plan would choose, as a dict; no GPU needed."""
+    lib = _lib.load()
+    o = _options(task, nu, N, eps, **kw)
+    info = _lib.Info()
+    _lib.check(lib.hankel_params(ctypes.byref(o), ctypes.byref(info)), "hankel_params")
+    return info.as_dict()
+
+
+def s_nu_M(nu, M, eps):
+    return _lib.load().hankel_s_nu_M(int(nu), int(M), float(eps))
+
+
+def t_nu_T(nu, T, eps):
+    return _lib.load().hankel_t_nu_T(int(nu), int(T), float(eps))
+
+
+def neumann_radius(K, eps):
+    return _lib.load().hankel_neumann_radius(int(K), float(eps))
+
+
+def p_K(K, eps):
+    return _lib.load().hankel_p_K(int(K), float(eps))
+
+
+def q_T(T, eps):
+    return _lib.load().hankel_q_T(int(T), float(eps))
+
+
+def j0_zero_offsets(count):
+    """b_n = j_{0,n} - (n-1/4)pi, n = 1..count, from the library's node builder."""
+    b = np.empty(int(count), dtype=np.float64)
+    _lib.check(_lib.load().hankel_j0_zero_offsets(int(count), b.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+               "hankel_j0_zero_offsets")
+    return b
+
+
+class Plan:
+    """A transform plan: f = J_nu(r omega^T) c for one task, order, size and accuracy."""
+
+    def __init__(self, task, nu, N, eps, grid="unit", gamma=None, precision="auto", max_nrhs=1,
+                 workspace_limit=0, host_only=False):
+        self._lib = _lib.load()
+        self._h = ctypes.c_void_p()
+        self.task, self.nu, self.N, self.eps = task, int(nu), int(N), float(eps)
+        self.max_nrhs = int(max_nrhs)
+        o = _options(task, nu, N, eps, grid, gamma, precision, max_nrhs, workspace_limit, host_only)
+        _lib.check(self._lib.hankel_plan_ex(ctypes.byref(self._h), ctypes.byref(o)), "hankel_plan_ex")
+
+    def __del__(self):
+        self.destroy()
+
+    def destroy(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self._lib.hankel_destroy(h)
+            self._h = ctypes.c_void_p()
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def info(self):
+        info = _lib.Info()
+        _lib.check(self._lib.hankel_plan_info(self._h, ctypes.byref(info)), "hankel_plan_info")
+        return info.as_dict()
+
+    def blocks(self):
+        cnt = ctypes.c_int(0)
+        _lib.check(self._lib.hankel_plan_blocks(self._h, None, 0, ctypes.byref(cnt)), "hankel_plan_blocks")
+        arr = (_lib.Block * max(cnt.value, 1))()
+        _lib.check(self._lib.hankel_plan_blocks(self._h, arr, cnt.value, ctypes.byref(cnt)), "hankel_plan_blocks")
+        return [(b.k0, b.k1, b.n0, b.n1, b.fft_len) for b in arr[:cnt.value]]
+
+    def entry(self, k, n):
+        """(value, is_far) of the plan's representation of matrix entry (k, n), 1-based."""
+        v = ctypes.c_double()
+        far = ctypes.c_int()
+        _lib.check(self._lib.hankel_plan_entry(self._h, int(k), int(n), ctypes.byref(v), ctypes.byref(far)),
+                   "hankel_plan_entry")
+        return v.value, bool(far.value)
+
+    def near_prefix(self, k):
+        ne = ctypes.c_int64()
+        _lib.check(self._lib.hankel_plan_near_prefix(self._h, int(k), ctypes.byref(ne)), "hankel_plan_near_prefix")
+        return ne.value
+
+    def set_timing(self, enable=True):
+        """Turn per-stage CUDA-event timing on or off and reset the stage statistics."""
+        _lib.check(self._lib.hankel_plan_set_timing(self._h, 1 if enable else 0), "hankel_plan_set_timing")
+
+    def stage_stats(self):
+        """Accumulated per-stage statistics: {stage: {ms, flops, entries, launches}}."""
+        arr = (_lib.StageStat * len(_lib.STAGES))()
+        _lib.check(self._lib.hankel_plan_stage_stats(self._h, arr), "hankel_plan_stage_stats")
+        return {name: {"ms": a.ms, "flops": a.flops, "entries": a.entries, "launches": a.launches}
+                for name, a in zip(_lib.STAGES, arr)}
+
+    def exec(self, c, f=None, stream=None):
+        """Run on torch CUDA float64 tensors of shape (N,) or (nrhs, N); returns f."""
+        import torch
+
+        if not (c.is_cuda and c.dtype == torch.float64):
+            raise TypeError("c must be a CUDA float64 tensor")
+        single = c.dim() == 1
+        c2 = c.reshape(1, -1) if single else c
+        if c2.shape[-1] != self.N or c2.stride(-1) != 1:
+            raise ValueError("c must have N contiguous entries per row")
+        nrhs = c2.shape[0]
+        if f is None:
+            f2 = torch.empty((nrhs, self.N), dtype=torch.float64, device=c.device)
+        else:
+            f2 = f.reshape(1, -1) if f.dim() == 1 else f
+            if not (f2.is_cuda and f2.dtype == torch.float64) or f2.shape != (nrhs, self.N) or f2.stride(-1) != 1:
+                raise ValueError("f must be a CUDA float64 tensor shaped like c")
+        if stream is None:
+            stream = torch.cuda.current_stream(c.device)
+        st = self._lib.hankel_exec_batched(self._h, ctypes.c_void_p(c2.data_ptr()), c2.stride(0) if nrhs > 1 else self.N,
+                                           ctypes.c_void_p(f2.data_ptr()), f2.stride(0) if nrhs > 1 else self.N,
+                                           nrhs, ctypes.c_void_p(stream.cuda_stream))
+        _lib.check(st, "hankel_exec_batched")
+        if f is not None:
+            return f
+        return f2[0] if single else f2
+
+    def exec_host(self, c, out=None):
+        """End-to-end call on host arrays (numpy float64, (N,) or (nrhs, N)); returns f."""
+        c = np.ascontiguousarray(c, dtype=np.float64)
+        single = c.ndim == 1
+        c2 = c.reshape(1, -1) if single else c
+        nrhs = c2.shape[0]
+        f = out if out is not None else np.empty((nrhs, self.N), dtype=np.float64)
+        dp = ctypes.POINTER(ctypes.c_double)
+        st = self._lib.hankel_exec_host(self._h, c2.ctypes.data_as(dp), self.N, f.ctypes.data_as(dp), self.N, nrhs)
+        _lib.check(st, "hankel_exec_host")
+        return f[0] if (single and out is None) else f

@@ -1,0 +1,109 @@
+"""ctypes declarations of the C ABI in include/hankel.h (argument marshalling only)."""
+import ctypes
+import os
+
+from . import build as _build
+
+_lib = None
+
+HANKEL_OK = 0
+STATUS_NAMES = {0: "HANKEL_OK", 1: "HANKEL_EINVAL", 2: "HANKEL_ENOMEM", 3: "HANKEL_ECUDA",
+                4: "HANKEL_EUNSUPPORTED", 5: "HANKEL_ETIMEOUT"}
+FLAG_HOST_ONLY = 1
+
+# Every function include/hankel.h declares.
+EXPORTED = [
+    "hankel_options_default", "hankel_plan", "hankel_plan_ex", "hankel_exec", "hankel_exec_batched",
+    "hankel_exec_host", "hankel_plan_info", "hankel_plan_blocks", "hankel_plan_entry",
+    "hankel_plan_near_prefix", "hankel_destroy", "hankel_status_string", "hankel_s_nu_M",
+    "hankel_t_nu_T", "hankel_neumann_radius", "hankel_p_K", "hankel_q_T", "hankel_params",
+    "hankel_j0_zero_offsets", "hankel_plan_set_timing", "hankel_plan_stage_stats",
+]
+STAGES = ["near", "gen", "fft", "pointwise", "out"]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("task", ctypes.c_int), ("nu", ctypes.c_int), ("N", ctypes.c_int64), ("eps", ctypes.c_double),
+                ("grid", ctypes.c_int), ("gamma", ctypes.c_int64), ("precision", ctypes.c_int),
+                ("max_nrhs", ctypes.c_int), ("flags", ctypes.c_uint), ("workspace_limit", ctypes.c_size_t)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("task", ctypes.c_int), ("nu", ctypes.c_int), ("grid", ctypes.c_int), ("precision", ctypes.c_int),
+                ("N", ctypes.c_int64), ("gamma", ctypes.c_int64), ("eps", ctypes.c_double), ("M", ctypes.c_int),
+                ("mu_max", ctypes.c_int), ("s", ctypes.c_double), ("alpha", ctypes.c_double),
+                ("beta", ctypes.c_double), ("P", ctypes.c_int), ("K", ctypes.c_int), ("T", ctypes.c_int),
+                ("K2", ctypes.c_int), ("T2", ctypes.c_int), ("direct_rows", ctypes.c_int64),
+                ("direct_cols", ctypes.c_int64), ("nblocks", ctypes.c_int), ("ncols", ctypes.c_int),
+                ("npairs", ctypes.c_int), ("near_count", ctypes.c_int64), ("far_count", ctypes.c_int64),
+                ("near_zmax", ctypes.c_double), ("device_bytes", ctypes.c_size_t),
+                ("workspace_bytes", ctypes.c_size_t)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class StageStat(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double), ("flops", ctypes.c_double), ("entries", ctypes.c_double),
+                ("launches", ctypes.c_int64)]
+
+
+class Block(ctypes.Structure):
+    _fields_ = [("k0", ctypes.c_int64), ("k1", ctypes.c_int64), ("n0", ctypes.c_int64), ("n1", ctypes.c_int64),
+                ("fft_len", ctypes.c_int64)]
+
+
+def load():
+    """Load (building first if needed) libhankel.so. Raises if it cannot be built or loaded."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build()
+    lib = ctypes.CDLL(path)
+    i32, i64, dbl, vp = ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
+    pplan = ctypes.POINTER(ctypes.c_void_p)
+    dp = ctypes.POINTER(ctypes.c_double)
+    sig = {
+        "hankel_options_default": (i32, [ctypes.POINTER(Options), i32, i32, i64, dbl]),
+        "hankel_plan": (i32, [pplan, i32, i32, i64, dbl]),
+        "hankel_plan_ex": (i32, [pplan, ctypes.POINTER(Options)]),
+        "hankel_exec": (i32, [vp, vp, vp, vp]),
+        "hankel_exec_batched": (i32, [vp, vp, i64, vp, i64, i32, vp]),
+        "hankel_exec_host": (i32, [vp, dp, i64, dp, i64, i32]),
+        "hankel_plan_info": (i32, [vp, ctypes.POINTER(Info)]),
+        "hankel_plan_blocks": (i32, [vp, ctypes.POINTER(Block), i32, ctypes.POINTER(i32)]),
+        "hankel_plan_entry": (i32, [vp, i64, i64, dp, ctypes.POINTER(i32)]),
+        "hankel_plan_near_prefix": (i32, [vp, i64, ctypes.POINTER(i64)]),
+        "hankel_destroy": (i32, [vp]),
+        "hankel_status_string": (ctypes.c_char_p, [i32]),
+        "hankel_s_nu_M": (dbl, [i32, i32, dbl]),
+        "hankel_t_nu_T": (dbl, [i32, i32, dbl]),
+        "hankel_neumann_radius": (dbl, [i32, dbl]),
+        "hankel_p_K": (dbl, [i32, dbl]),
+        "hankel_q_T": (dbl, [i32, dbl]),
+        "hankel_params": (i32, [ctypes.POINTER(Options), ctypes.POINTER(Info)]),
+        "hankel_j0_zero_offsets": (i32, [i64, dp]),
+        "hankel_plan_set_timing": (i32, [vp, i32]),
+        "hankel_plan_stage_stats": (i32, [vp, ctypes.POINTER(StageStat)]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def library_path():
+    return _build.LIB_PATH
+
+
+def check(status, what):
+    if status != HANKEL_OK:
+        msg = load().hankel_status_string(status).decode()
+        raise RuntimeError("%s failed: %s (%s)" % (what, STATUS_NAMES.get(status, status), msg))
+
+
+def loaded_path():
+    """Path of the shared object this process loaded (None before load())."""
+    return os.path.realpath(_build.LIB_PATH) if _lib is not None else None

@@ -1,0 +1,28 @@
+// Interface between the host ABI layer and the CUDA translation units.
+#pragma once
+#include <stddef.h>
+
+#include "plan.h"
+
+namespace hk {
+struct DevicePlan;  // defined in exec.cu
+}
+
+struct hankel_plan_s {
+  hk::HostPlan hp;
+  bool host_only = false;
+  hk::DevicePlan* dev = nullptr;
+};
+
+namespace hk {
+// Allocate device tables and workspace and build the chirp spectra.
+int dev_plan_create(hankel_plan_s* p);
+// Free everything dev_plan_create made (also after a partial failure).
+int dev_plan_destroy(hankel_plan_s* p);
+int dev_exec(hankel_plan_s* p, const double* c, int64_t ldc, double* f, int64_t ldf, int nrhs, void* stream);
+int dev_exec_host(hankel_plan_s* p, const double* c, int64_t ldc, double* f, int64_t ldf, int nrhs);
+int dev_set_timing(hankel_plan_s* p, int enable);
+int dev_stage_stats(hankel_plan_s* p, hankel_stage_stat* out);
+size_t dev_plan_bytes(const hankel_plan_s* p);
+size_t dev_workspace_bytes(const hankel_plan_s* p);
+}  // namespace hk

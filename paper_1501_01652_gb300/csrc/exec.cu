@@ -1,0 +1,384 @@
+// Device side of a plan: table upload, chirp spectra, and the execution of
+// one transform (near field + far-field blocks) on a CUDA stream.
+//
+// Far field (Section 4.2, Eq. 19, with Sections 5-6 for Bessel-root nodes):
+// every block with rows k0..k1 and columns n0..n1 needs, for each stacked
+// column l, Z_l(k) = sum_n exp(i theta~_kn) X_l(n) c_n with the exact phase
+// theta~_kn = pi U_k V_n / E. Writing U V = (U^2 + V^2 - (U-V)^2)/2 turns
+// that sum into a linear convolution in k - n (a chirp-z transform), done
+// with power-of-two FFTs of length F >= R + C - 1.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "device.h"
+#include "kernels.cuh"
+
+namespace hk {
+
+namespace {
+
+constexpr size_t kDefaultWorkspace = size_t(4) << 30;
+constexpr int64_t kNearPiece = 4096;  // near-field columns handled by one warp
+
+struct DevBlock {
+  Block b;
+  double2* wU = nullptr;  // exp(i pi U_k^2 / (2E)), k = k0..k1
+  double2* wV = nullptr;  // exp(i pi V_n^2 / (2E)), n = n0..n1
+  double2* H = nullptr;   // FFT_F of the chirp exp(-i pi (U-V)^2 / (2E)), times 1/F
+  int64_t cap = 0;        // columns per chunk
+};
+
+}  // namespace
+
+struct DevicePlan {
+  int device = 0;
+  NodeTables nodes{};
+  DevColSpec* cols = nullptr;
+  int ncols = 0;
+  double* jtab = nullptr;
+  NearItem* items = nullptr;
+  int64_t nitems = 0;
+  NearRow* mrows = nullptr;
+  int64_t nmrows = 0;
+  double* partial = nullptr;
+  int64_t nslots = 0;
+  std::vector<DevBlock> blocks;
+  double2* tw = nullptr;
+  int logFmax = 6;
+  double2* bufA = nullptr;
+  double2* bufB = nullptr;
+  size_t ws_bytes = 0;
+  double* c_stage = nullptr;
+  double* f_stage = nullptr;
+  size_t bytes = 0;
+  std::vector<void*> allocs;
+  // stage statistics (hankel_plan_set_timing / hankel_plan_stage_stats)
+  bool timing = false;
+  hankel_stage_stat acc[HANKEL_STAGE_COUNT] = {};
+  struct Rec {
+    int stage;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> pending;
+  std::vector<cudaEvent_t> pool;
+  size_t pool_used = 0;
+};
+
+namespace {
+
+template <class T>
+int dalloc(DevicePlan* d, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  void* q = nullptr;
+  if (cudaMalloc(&q, count * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    return HANKEL_ENOMEM;
+  }
+  d->allocs.push_back(q);
+  d->bytes += count * sizeof(T);
+  *p = (T*)q;
+  return HANKEL_OK;
+}
+
+template <class T>
+int upload(DevicePlan* d, T** p, const T* src, size_t count) {
+  int st = dalloc(d, p, count);
+  if (st != HANKEL_OK) return st;
+  if (cudaMemcpy(*p, src, count * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess) return HANKEL_ECUDA;
+  return HANKEL_OK;
+}
+
+cudaEvent_t pool_event(DevicePlan* d) {
+  if (d->pool_used == d->pool.size()) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    d->pool.push_back(e);
+  }
+  return d->pool[d->pool_used++];
+}
+
+// Brackets the launches of one stage with events when timing is on and tallies its work.
+struct StageScope {
+  DevicePlan* d;
+  int stage;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr;
+  StageScope(DevicePlan* d_, int stage_, cudaStream_t st_) : d(d_), stage(stage_), st(st_) {
+    if (d->timing) {
+      a = pool_event(d);
+      if (a) cudaEventRecord(a, st);
+    }
+  }
+  void done(int64_t launches, double flops, double entries) {
+    d->acc[stage].launches += launches;
+    d->acc[stage].flops += flops;
+    d->acc[stage].entries += entries;
+    if (d->timing && a) {
+      cudaEvent_t b = pool_event(d);
+      if (b) {
+        cudaEventRecord(b, st);
+        d->pending.push_back(DevicePlan::Rec{stage, a, b});
+      }
+    }
+  }
+};
+
+#define HK_TRY(x)                        \
+  do {                                   \
+    int st_ = (x);                       \
+    if (st_ != HANKEL_OK) return st_;    \
+  } while (0)
+#define HK_LAUNCHED()                                              \
+  do {                                                             \
+    if (cudaGetLastError() != cudaSuccess) return HANKEL_ECUDA;    \
+  } while (0)
+
+}  // namespace
+
+int dev_plan_create(hankel_plan_s* p) {
+  const HostPlan& hp = p->hp;
+  DevicePlan* d = new DevicePlan();
+  p->dev = d;
+  if (cudaGetDevice(&d->device) != cudaSuccess) return HANKEL_ECUDA;
+  const int64_t N = hp.opt.N;
+
+  // Node tables and their derived powers.
+  std::vector<double> tmp(N);
+  HK_TRY(upload(d, &d->nodes.r_true, hp.r_true.data(), N));
+  HK_TRY(upload(d, &d->nodes.om_true, hp.om_true.data(), N));
+  HK_TRY(upload(d, &d->nodes.rowvar, hp.rowvar.data(), N));
+  HK_TRY(upload(d, &d->nodes.rowpert, hp.rowpert.data(), N));
+  HK_TRY(upload(d, &d->nodes.omt, hp.omt.data(), N));
+  HK_TRY(upload(d, &d->nodes.betan, hp.betan.data(), N));
+  HK_TRY(upload(d, &d->nodes.colpow, hp.colpow.data(), N));
+  for (int64_t i = 0; i < N; ++i) tmp[i] = hp.rowvar[i] > 0 ? 1.0 / std::sqrt(hp.rowvar[i]) : 0.0;
+  HK_TRY(upload(d, &d->nodes.rs_rowvar, tmp.data(), N));
+  for (int64_t i = 0; i < N; ++i) tmp[i] = hp.rowvar[i] > 0 ? 1.0 / hp.rowvar[i] : 0.0;
+  HK_TRY(upload(d, &d->nodes.inv_rowvar, tmp.data(), N));
+  for (int64_t i = 0; i < N; ++i) tmp[i] = 1.0 / std::sqrt(hp.omt[i]);
+  HK_TRY(upload(d, &d->nodes.rs_omt, tmp.data(), N));
+  for (int64_t i = 0; i < N; ++i) tmp[i] = 1.0 / hp.omt[i];
+  HK_TRY(upload(d, &d->nodes.inv_omt, tmp.data(), N));
+
+  // Stacked-column specifications.
+  std::vector<DevColSpec> cs(hp.cols.size());
+  for (size_t i = 0; i < hp.cols.size(); ++i) {
+    memset(&cs[i], 0, sizeof(DevColSpec));
+    cs[i].u1 = hp.cols[i].u1;
+    cs[i].delta = hp.cols[i].delta;
+    cs[i].nterm = hp.cols[i].nterm;
+    for (int u = 0; u < kMaxU; ++u) cs[i].G[u] = make_double2(hp.cols[i].G[u].real(), hp.cols[i].G[u].imag());
+  }
+  d->ncols = (int)cs.size();
+  HK_TRY(upload(d, &d->cols, cs.data(), cs.size()));
+  HK_TRY(upload(d, &d->jtab, hp.jtab.data(), hp.jtab.size()));
+
+  // Near-field work list: each row's prefix 1..nend(k) cut into pieces of <= kNearPiece columns.
+  std::vector<NearItem> items;
+  std::vector<NearRow> mrows;
+  items.reserve(N + hp.near_count / kNearPiece + 16);
+  int64_t slot = 0;
+  for (int64_t k = 1; k <= N; ++k) {
+    int64_t ne = hp.nend[k - 1];
+    if (ne <= kNearPiece) {
+      items.push_back(NearItem{k, 1, ne, -1});
+    } else {
+      int64_t np = (ne + kNearPiece - 1) / kNearPiece;
+      mrows.push_back(NearRow{k, slot, (int32_t)np, 0});
+      for (int64_t j = 0; j < np; ++j)
+        items.push_back(NearItem{k, 1 + j * kNearPiece, std::min(ne, (j + 1) * kNearPiece), slot++});
+    }
+  }
+  d->nitems = (int64_t)items.size();
+  d->nmrows = (int64_t)mrows.size();
+  d->nslots = slot;
+  HK_TRY(upload(d, &d->items, items.data(), items.size()));
+  if (!mrows.empty()) HK_TRY(upload(d, &d->mrows, mrows.data(), mrows.size()));
+  HK_TRY(dalloc(d, &d->partial, (size_t)std::max<int64_t>(slot, 1) * hp.opt.max_nrhs));
+
+  // Twiddle table W_{Fmax}^t = exp(-2 pi i t / Fmax).
+  int logFmax = 6;
+  for (const Block& b : hp.blocks) logFmax = std::max(logFmax, b.logF);
+  d->logFmax = logFmax;
+  HK_TRY(dalloc(d, &d->tw, (size_t)1 << logFmax));
+  launch_twiddles(d->tw, logFmax, 0);
+  HK_LAUNCHED();
+
+  // Workspace: two ping-pong column buffers.
+  size_t limit = hp.opt.workspace_limit ? hp.opt.workspace_limit : kDefaultWorkspace;
+  size_t need = 0;
+  for (const Block& b : hp.blocks) {
+    int64_t total = (int64_t)d->ncols * hp.opt.max_nrhs;
+    int64_t cap = (int64_t)(limit / (2 * sizeof(double2) * (size_t)b.F));
+    cap = std::max<int64_t>(1, std::min<int64_t>(cap, total));
+    cap = std::min<int64_t>(cap, 65535);
+    need = std::max(need, (size_t)cap * (size_t)b.F);
+  }
+  need = std::max<size_t>(need, (size_t)1 << logFmax);  // room for the chirp spectra FFTs
+  HK_TRY(dalloc(d, &d->bufA, need));
+  HK_TRY(dalloc(d, &d->bufB, need));
+  d->ws_bytes = 2 * need * sizeof(double2);
+
+  // Per-block chirp vectors and kernel spectrum.
+  for (const Block& b : hp.blocks) {
+    DevBlock db;
+    db.b = b;
+    db.cap = std::max<int64_t>(1, std::min<int64_t>((int64_t)(need / (size_t)b.F), (int64_t)d->ncols * hp.opt.max_nrhs));
+    db.cap = std::min<int64_t>(db.cap, 65535);
+    HK_TRY(dalloc(d, &db.wU, b.R));
+    HK_TRY(dalloc(d, &db.wV, b.C));
+    HK_TRY(dalloc(d, &db.H, b.F));
+    d->blocks.push_back(db);
+    ChirpGeom g{hp.Ua, hp.Ub, hp.Va, hp.Vb, hp.E, b.k0, b.n0, b.R, b.C, b.F};
+    launch_chirps(g, db.wU, db.wV, d->bufA, 0);
+    HK_LAUNCHED();
+    double2* res = nullptr;
+    HK_TRY(run_fft(d->bufA, d->bufB, b.logF, 1, /*inverse=*/false, d->tw, d->logFmax, 0, &res));
+    launch_scale_copy(res, db.H, b.F, 1.0 / (double)b.F, 0);
+    HK_LAUNCHED();
+  }
+
+  if (cudaDeviceSynchronize() != cudaSuccess) return HANKEL_ECUDA;
+  return HANKEL_OK;
+}
+
+int dev_plan_destroy(hankel_plan_s* p) {
+  DevicePlan* d = p->dev;
+  if (!d) return HANKEL_OK;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(d->device);
+  cudaDeviceSynchronize();
+  for (cudaEvent_t e : d->pool) cudaEventDestroy(e);
+  for (void* q : d->allocs) cudaFree(q);
+  cudaSetDevice(cur);
+  delete d;
+  p->dev = nullptr;
+  return HANKEL_OK;
+}
+
+size_t dev_plan_bytes(const hankel_plan_s* p) { return p->dev ? p->dev->bytes : 0; }
+size_t dev_workspace_bytes(const hankel_plan_s* p) { return p->dev ? p->dev->ws_bytes : 0; }
+
+int dev_exec(hankel_plan_s* p, const double* c, int64_t ldc, double* f, int64_t ldf, int nrhs, void* stream) {
+  const HostPlan& hp = p->hp;
+  DevicePlan* d = p->dev;
+  cudaStream_t st = (cudaStream_t)stream;
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (cur != d->device) cudaSetDevice(d->device);
+
+  // Near field: overwrite f with the directly summed part.
+  {
+    StageScope sc(d, HANKEL_STAGE_NEAR, st);
+    launch_near(d->items, d->nitems, d->mrows, d->nmrows, d->partial, nrhs, c, ldc, f, ldf, d->nodes, d->jtab,
+                hp.jt_n, hp.jt_deg, st);
+    HK_LAUNCHED();
+    sc.done(d->nmrows > 0 ? 2 : 1, 0.0, (double)hp.near_count * nrhs);
+  }
+
+  // Far field, block by block, columns in chunks.
+  const int64_t total = (int64_t)d->ncols * nrhs;
+  for (const DevBlock& db : d->blocks) {
+    const Block& b = db.b;
+    for (int64_t c0 = 0; c0 < total; c0 += db.cap) {
+      int nc = (int)std::min<int64_t>(db.cap, total - c0);
+      {
+        StageScope sc(d, HANKEL_STAGE_GEN, st);
+        GenArgs ga{d->bufA, b.F, b.C, b.n0, nc, c0, d->ncols, c, ldc, d->nodes, d->cols, db.wV};
+        launch_gen(ga, st);
+        HK_LAUNCHED();
+        sc.done(1, 0.0, 0.0);
+      }
+      const double fft_flops = 5.0 * (double)b.F * (double)b.logF * nc;
+      double2* res = nullptr;
+      {
+        StageScope sc(d, HANKEL_STAGE_FFT, st);
+        int np = 0;
+        HK_TRY(run_fft(d->bufA, d->bufB, b.logF, nc, false, d->tw, d->logFmax, st, &res, &np));
+        HK_LAUNCHED();
+        sc.done(np, fft_flops, 0.0);
+      }
+      {
+        StageScope sc(d, HANKEL_STAGE_POINTWISE, st);
+        launch_pointwise(res, db.H, b.F, nc, st);
+        HK_LAUNCHED();
+        sc.done(1, 0.0, 0.0);
+      }
+      double2* other = (res == d->bufA) ? d->bufB : d->bufA;
+      double2* res2 = nullptr;
+      {
+        StageScope sc(d, HANKEL_STAGE_FFT, st);
+        int np = 0;
+        HK_TRY(run_fft(res, other, b.logF, nc, true, d->tw, d->logFmax, st, &res2, &np));
+        HK_LAUNCHED();
+        sc.done(np, fft_flops, 0.0);
+      }
+      {
+        StageScope sc(d, HANKEL_STAGE_OUT, st);
+        OutArgs oa{res2, b.F, b.R, b.C, b.k0, nc, c0, d->ncols, f, ldf, d->nodes, d->cols, db.wU};
+        launch_out(oa, st);
+        HK_LAUNCHED();
+        sc.done(1, 0.0, 0.0);
+      }
+    }
+  }
+  if (cur >= 0 && cur != d->device) cudaSetDevice(cur);
+  return HANKEL_OK;
+}
+
+int dev_set_timing(hankel_plan_s* p, int enable) {
+  DevicePlan* d = p->dev;
+  for (const auto& r : d->pending) cudaEventSynchronize(r.b);
+  d->pending.clear();
+  d->pool_used = 0;
+  memset(d->acc, 0, sizeof(d->acc));
+  d->timing = enable != 0;
+  return HANKEL_OK;
+}
+
+int dev_stage_stats(hankel_plan_s* p, hankel_stage_stat* out) {
+  DevicePlan* d = p->dev;
+  for (const auto& r : d->pending) {
+    if (cudaEventSynchronize(r.b) != cudaSuccess) return HANKEL_ECUDA;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) return HANKEL_ECUDA;
+    d->acc[r.stage].ms += ms;
+  }
+  d->pending.clear();
+  d->pool_used = 0;
+  memcpy(out, d->acc, sizeof(d->acc));
+  return HANKEL_OK;
+}
+
+int dev_exec_host(hankel_plan_s* p, const double* c, int64_t ldc, double* f, int64_t ldf, int nrhs) {
+  const int64_t N = p->hp.opt.N;
+  DevicePlan* d = p->dev;
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (cur != d->device) cudaSetDevice(d->device);
+  cudaStream_t st = 0;
+  if (!d->c_stage) {  // staging buffers for host arrays, made on first use
+    HK_TRY(dalloc(d, &d->c_stage, (size_t)N * p->hp.opt.max_nrhs));
+    HK_TRY(dalloc(d, &d->f_stage, (size_t)N * p->hp.opt.max_nrhs));
+  }
+  if (cudaMemcpy2DAsync(d->c_stage, N * sizeof(double), c, ldc * sizeof(double), N * sizeof(double), nrhs,
+                        cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return HANKEL_ECUDA;
+  int s = dev_exec(p, d->c_stage, N, d->f_stage, N, nrhs, st);
+  if (s != HANKEL_OK) return s;
+  if (cudaMemcpy2DAsync(f, ldf * sizeof(double), d->f_stage, N * sizeof(double), N * sizeof(double), nrhs,
+                        cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return HANKEL_ECUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return HANKEL_ECUDA;
+  if (cur >= 0 && cur != d->device) cudaSetDevice(cur);
+  return HANKEL_OK;
+}
+
+}  // namespace hk

@@ -1,0 +1,87 @@
+// Kernel-side structures and launch wrappers of the transform.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "plan.h"
+
+namespace hk {
+
+// Per-index node tables on the device (0-based index i = k-1 or n-1).
+struct NodeTables {
+  double* r_true;     // r_k
+  double* om_true;    // omega_n
+  double* rowvar;     // r_k (Schlomilch, Fourier-Bessel) or r~_k (DHT)
+  double* rs_rowvar;  // rowvar^{-1/2}
+  double* inv_rowvar; // rowvar^{-1}
+  double* rowpert;    // e_k (DHT)
+  double* omt;        // omega~_n
+  double* rs_omt;     // omega~_n^{-1/2}
+  double* inv_omt;    // omega~_n^{-1}
+  double* betan;      // b_n / omega~_n
+  double* colpow;     // j_{0,n} (DHT)
+};
+
+// One stacked column: row factor rowpert^u1 rowvar^(delta-1/2), column factor
+// colpow^u1 omt^(delta-1/2) sum_u2 G[u2] betan^u2.
+struct DevColSpec {
+  int u1, delta, nterm, pad;
+  double2 G[kMaxU];
+};
+
+// Near-field work item: row k, columns n0..n1 (1-based, inclusive; empty when n0 > n1).
+// slot < 0: the item is the whole prefix of its row and writes f directly.
+struct NearItem {
+  int64_t k, n0, n1, slot;
+};
+// A row whose near prefix is split into npieces items with partial slots slot0.. .
+struct NearRow {
+  int64_t k, slot0;
+  int32_t npieces, pad;
+};
+
+struct ChirpGeom {
+  int64_t Ua, Ub, Va, Vb, E, k0, n0, R, C, F;
+};
+
+struct GenArgs {
+  double2* A;         // [nc][F] output columns
+  int64_t F, C, n0;   // transform length, block columns, first column (1-based)
+  int nc;             // columns in this chunk
+  int64_t c0;         // global index of the first column (rhs * ncols + l)
+  int ncols;          // stacked columns per right-hand side
+  const double* c;    // coefficients, c[rhs * ldc + n-1]
+  int64_t ldc;
+  NodeTables nodes;
+  const DevColSpec* cols;
+  const double2* wV;  // column chirp of the block
+};
+
+struct OutArgs {
+  const double2* Y;   // [nc][F] inverse-transformed columns
+  int64_t F, R, C, k0;
+  int nc;
+  int64_t c0;
+  int ncols;
+  double* f;          // f[rhs * ldf + k-1] += ...
+  int64_t ldf;
+  NodeTables nodes;
+  const DevColSpec* cols;
+  const double2* wU;  // row chirp of the block
+};
+
+void launch_twiddles(double2* tw, int logF, cudaStream_t st);
+void launch_chirps(const ChirpGeom& g, double2* wU, double2* wV, double2* hh, cudaStream_t st);
+// Out-of-place multi-column FFT of length 2^logF over ncols contiguous columns,
+// ping-ponging between a (input) and b; *result receives the buffer holding the output.
+int run_fft(double2* a, double2* b, int logF, int ncols, bool inverse, const double2* tw, int logFmax,
+            cudaStream_t st, double2** result, int* npasses = nullptr);
+void launch_scale_copy(const double2* src, double2* dst, int64_t n, double scale, cudaStream_t st);
+void launch_pointwise(double2* y, const double2* H, int64_t F, int ncols, cudaStream_t st);
+void launch_gen(const GenArgs& a, cudaStream_t st);
+void launch_out(const OutArgs& a, cudaStream_t st);
+void launch_near(const NearItem* items, int64_t nitems, const NearRow* mrows, int64_t nmrows, double* partial,
+                 int nrhs, const double* c, int64_t ldc, double* f, int64_t ldf, const NodeTables& nodes,
+                 const double* jtab, int64_t jt_n, int deg, cudaStream_t st);
+
+}  // namespace hk

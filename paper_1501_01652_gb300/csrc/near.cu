@@ -1,0 +1,93 @@
+// Near field (the direct part J^EVAL of Eqs. 18-19 and the directly summed
+// leading rows/columns of Sections 5-6): f_k = sum_{n <= nend(k)} c_n J_nu(r_k omega_n)
+// with J evaluated per entry and summed by one warp per work item.
+//
+// J_nu on [0, zmax] comes from a table of degree-15 Taylor polynomials about
+// the centres i + 1/2 of unit intervals (built at plan time from the Neumann
+// addition formula, Eq. 8), so one evaluation costs a table row load and 15 FMAs.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "kernels.cuh"
+
+namespace hk {
+
+namespace {
+
+constexpr int kRhsGroup = 4;
+
+__device__ __forceinline__ double table_j(const double* __restrict__ jtab, int64_t jt_n, int deg, double z) {
+  int64_t i = (int64_t)z;
+  i = i < 0 ? 0 : (i >= jt_n ? jt_n - 1 : i);
+  const double d = z - ((double)i + 0.5);
+  const double* t = jtab + i * (deg + 1);
+  double v = __ldg(&t[deg]);
+  for (int j = deg - 1; j >= 0; --j) v = fma(v, d, __ldg(&t[j]));
+  return v;
+}
+
+__global__ void __launch_bounds__(256) k_near(const NearItem* __restrict__ items, int64_t nitems, double* partial,
+                                              int nrhs, const double* __restrict__ c, int64_t ldc, double* f,
+                                              int64_t ldf, const double* __restrict__ r_true,
+                                              const double* __restrict__ om_true, const double* __restrict__ jtab,
+                                              int64_t jt_n, int deg) {
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= nitems) return;
+  const NearItem it = items[warp];
+  const double r = r_true[it.k - 1];
+  for (int r0 = 0; r0 < nrhs; r0 += kRhsGroup) {
+    double acc[kRhsGroup];
+#pragma unroll
+    for (int g = 0; g < kRhsGroup; ++g) acc[g] = 0.0;
+    for (int64_t n = it.n0 + lane; n <= it.n1; n += 32) {
+      const double J = table_j(jtab, jt_n, deg, r * __ldg(&om_true[n - 1]));
+#pragma unroll
+      for (int g = 0; g < kRhsGroup; ++g)
+        if (r0 + g < nrhs) acc[g] = fma(__ldg(&c[(int64_t)(r0 + g) * ldc + n - 1]), J, acc[g]);
+    }
+#pragma unroll
+    for (int g = 0; g < kRhsGroup; ++g) {
+      double v = acc[g];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      acc[g] = v;
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int g = 0; g < kRhsGroup; ++g) {
+        if (r0 + g >= nrhs) break;
+        if (it.slot < 0) f[(int64_t)(r0 + g) * ldf + it.k - 1] = acc[g];
+        else partial[it.slot * nrhs + r0 + g] = acc[g];
+      }
+    }
+  }
+}
+
+__global__ void k_near_combine(const NearRow* __restrict__ rows, int64_t nrows, const double* __restrict__ partial,
+                               int nrhs, double* f, int64_t ldf) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nrows * nrhs) return;
+  const int64_t i = t / nrhs;
+  const int rr = (int)(t - i * nrhs);
+  const NearRow row = rows[i];
+  double s = 0.0;
+  for (int j = 0; j < row.npieces; ++j) s += partial[(row.slot0 + j) * nrhs + rr];
+  f[(int64_t)rr * ldf + row.k - 1] = s;
+}
+
+}  // namespace
+
+void launch_near(const NearItem* items, int64_t nitems, const NearRow* mrows, int64_t nmrows, double* partial,
+                 int nrhs, const double* c, int64_t ldc, double* f, int64_t ldf, const NodeTables& nodes,
+                 const double* jtab, int64_t jt_n, int deg, cudaStream_t st) {
+  const int64_t threads = nitems * 32;
+  k_near<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(items, nitems, partial, nrhs, c, ldc, f, ldf,
+                                                             nodes.r_true, nodes.om_true, jtab, jt_n, deg);
+  if (nmrows > 0) {
+    const int64_t n = nmrows * nrhs;
+    k_near_combine<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(mrows, nmrows, partial, nrhs, f, ldf);
+  }
+}
+
+}  // namespace hk

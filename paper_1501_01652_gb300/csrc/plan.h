@@ -1,0 +1,82 @@
+// Internal plan structures shared by the host planner and the CUDA side.
+#pragma once
+#include <stdint.h>
+
+#include <complex>
+#include <vector>
+
+#include "hankel.h"
+
+namespace hk {
+
+typedef std::complex<double> cplx;
+
+// Largest number of Taylor powers u2 of the column perturbation b_n carried
+// by one stacked column (2T+K-2 of Section 5.1 at eps = 1e-16 is 10).
+constexpr int kMaxU = 16;
+// Near-field Bessel table: intervals of width 1 with Taylor polynomials of this degree.
+constexpr int kJTabDeg = 15;
+constexpr int kJTabDegF32 = 8;
+
+// A far-field block: rows k0..k1, columns n0..n1 (1-based, inclusive), one
+// chirp-z transform of length F = 2^logF >= R + C - 1.
+struct Block {
+  int64_t k0, k1, n0, n1;
+  int64_t R, C, F;
+  int logF;
+};
+
+// One stacked column of a block: the row function rowpert(k)^u1 rowvar(k)^(delta-1/2)
+// times the column function colpow(n)^u1 omt(n)^(delta-1/2) sum_u2 G[u2] beta(n)^u2.
+struct ColSpec {
+  int u1;
+  int delta;
+  int nterm;            // number of u2 terms (U2)
+  cplx G[kMaxU];
+};
+
+struct HostPlan {
+  hankel_options opt;
+  // Table 4 and Eqs. (23)-(24)
+  int M = 0, K = 1, T = 1, K2 = 1, T2 = 1, U1 = 1, U2 = 1, P = 0, mu_max = 0;
+  double s = 0, alpha = 0, beta = 1;
+  int64_t nrd = 0, ncd = 0;  // direct rows / columns
+  bool fp32 = false;
+  // exact phase theta~_kn = pi U_k V_n / E with U_k = Ua k + Ub, V_n = Va n + Vb
+  int64_t Ua = 1, Ub = 0, Va = 1, Vb = 0, E = 1;
+  // partition coordinates X_k = k - x0, Y_n = n + y0, z~ = pi X Y / D
+  double x0 = 0, y0 = 0, D = 1;
+  // nodes, index i = k-1 or n-1
+  std::vector<double> b;        // b_n = j_{0,n} - (n-1/4)pi, n = 1..N+1 (FB, DHT)
+  std::vector<double> r_true;   // r_k
+  std::vector<double> om_true;  // omega_n
+  std::vector<double> rowvar;   // r_k (S, FB) or r~_k (DHT)
+  std::vector<double> rowpert;  // e_k (DHT), else 0
+  std::vector<double> omt;      // omega~_n = omega_n (S) or (n-1/4)pi
+  std::vector<double> betan;    // b_n / omega~_n (FB, DHT), else 0
+  std::vector<double> colpow;   // j_{0,n} (DHT), else 1
+  // partition
+  std::vector<Block> blocks;
+  std::vector<int64_t> nend;  // near prefix length per row
+  int64_t near_count = 0, far_count = 0;
+  double zmax = 0;
+  // stacked columns per block
+  std::vector<ColSpec> cols;
+  // near-field J table: ntab intervals [i, i+1), centre i + 1/2, deg+1 Taylor coefficients each
+  int jt_deg = kJTabDeg;
+  int64_t jt_n = 0;
+  std::vector<double> jtab;
+};
+
+// Builds every host table of a plan. Returns a hankel_status code.
+int build_host_plan(const hankel_options& opt, HostPlan& hp);
+// Parameter selection only (no nodes or tables). Returns a hankel_status code.
+int choose_params(const hankel_options& opt, HostPlan& hp);
+// Host value of the plan's representation of entry (k, n), 1-based.
+double host_entry(const HostPlan& hp, int64_t k, int64_t n, int* is_far);
+// Near-field J from the Taylor table (host copy of the device evaluator).
+double table_j(const HostPlan& hp, double z);
+// j_{0,n} - (n-1/4)pi for n = 1..count.
+void j0_zero_offsets(int64_t count, double* b);
+
+}  // namespace hk

@@ -1,0 +1,569 @@
+// Host planner: algorithmic parameters, Bessel-root nodes, the recursive
+// partition, the stacked-column weight tables and the near-field Bessel
+// table of a plan. Pure host C++; no CUDA call is made here.
+//
+// References are to Townsend, arXiv:1501.01652 (sections, equations, tables).
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <utility>
+#include <vector>
+
+#include "plan.h"
+
+namespace hk {
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+// ---------------------------------------------------------------------------
+// Double-double arithmetic (head + tail), used for plan-time Bessel values.
+// ---------------------------------------------------------------------------
+struct DD {
+  double h, l;
+};
+inline DD ddv(double a) { return DD{a, 0.0}; }
+inline DD dd_fast(double a, double b) {
+  double s = a + b;
+  return DD{s, b - (s - a)};
+}
+inline DD dd_add(DD a, DD b) {
+  double s = a.h + b.h, v = s - a.h;
+  double e = (a.h - (s - v)) + (b.h - v);
+  e += a.l + b.l;
+  return dd_fast(s, e);
+}
+inline DD dd_neg(DD a) { return DD{-a.h, -a.l}; }
+inline DD dd_mul(DD a, DD b) {
+  double p = a.h * b.h;
+  double e = std::fma(a.h, b.h, -p) + (a.h * b.l + a.l * b.h);
+  return dd_fast(p, e);
+}
+inline DD dd_div(DD a, DD b) {
+  double q1 = a.h / b.h;
+  DD r = dd_add(a, dd_neg(dd_mul(ddv(q1), b)));
+  double q2 = r.h / b.h;
+  r = dd_add(r, dd_neg(dd_mul(ddv(q2), b)));
+  double q3 = r.h / b.h;
+  return dd_add(dd_fast(q1, q2), ddv(q3));
+}
+inline DD dd_scale(DD a, double p2) { return DD{a.h * p2, a.l * p2}; }
+const DD kPiDD = {3.141592653589793116, 1.2246467991473532072e-16};
+
+// J_lambda(z) for lambda = 0..L (z > 0) by Miller's backward recurrence
+// J_{k-1} = (2k/z) J_k - J_{k+1} (DLMF 3.6(vi)), normalised with
+// J_0 + 2 sum_{k>=1} J_{2k} = 1 (DLMF 10.12.4). Double-double throughout.
+void miller_all(DD z, int L, std::vector<DD>& out) {
+  int start = (int)z.h + 90 + L;
+  if (start & 1) ++start;
+  std::vector<DD> v(L + 1, ddv(0.0));
+  DD twoz = dd_div(ddv(2.0), z);
+  DD jp1 = ddv(0.0), j = ddv(1e-40), norm = ddv(0.0);
+  for (int k = start; k >= 1; --k) {
+    if (k <= L) v[k] = j;
+    if ((k & 1) == 0) norm = dd_add(norm, dd_scale(j, 2.0));
+    DD jm1 = dd_add(dd_mul(dd_mul(ddv((double)k), twoz), j), dd_neg(jp1));
+    jp1 = j;
+    j = jm1;
+    if (std::fabs(j.h) > 1e200) {
+      const double sc = 0x1p-700;
+      j = dd_scale(j, sc);
+      jp1 = dd_scale(jp1, sc);
+      norm = dd_scale(norm, sc);
+      for (int i = k; i <= L; ++i) v[i] = dd_scale(v[i], sc);
+    }
+  }
+  v[0] = j;
+  norm = dd_add(norm, j);
+  out.resize(L + 1);
+  for (int i = 0; i <= L; ++i) out[i] = dd_div(v[i], norm);
+}
+
+// ---------------------------------------------------------------------------
+// Hankel expansion coefficients (Eq. 4)
+// ---------------------------------------------------------------------------
+// a_m(nu) = prod_{i=1}^m (4nu^2 - (2i-1)^2) / (m! 8^m), m = 0..mmax.
+void hankel_a(int nu, int mmax, double* a) {
+  double mu4 = 4.0 * (double)nu * (double)nu;
+  a[0] = 1.0;
+  for (int m = 1; m <= mmax; ++m) a[m] = a[m - 1] * (mu4 - (2.0 * m - 1.0) * (2.0 * m - 1.0)) / (8.0 * m);
+}
+
+// exp(i pi q / 4) for integer q, with exact values.
+cplx expi_quarter_pi(int q) {
+  const double h = 0.70710678118654752440;
+  static const double cr[8] = {1, h, 0, -h, -1, -h, 0, h};
+  static const double ci[8] = {0, h, 1, h, 0, -h, -1, -h};
+  int r = ((q % 8) + 8) % 8;
+  return cplx(cr[r], ci[r]);
+}
+
+// J_lam(z) ~ Re[ e^{iz} sum_{j<2M} c_j(lam) z^{-(j+1/2)} ] with
+// c_j(lam) = sqrt(2/pi) e^{-i(2lam+1)pi/4} i^j a_j(lam): Eq. (4) written with
+// cos(mu) = Re e^{i mu}, sin(mu) = Im e^{i mu}, mu = z - (2lam+1)pi/4.
+void hankel_c(int lam, int M, cplx* c) {
+  double a[64];
+  hankel_a(lam, 2 * M - 1, a);
+  const double s2p = 0.79788456080286535588;  // sqrt(2/pi)
+  for (int j = 0; j < 2 * M; ++j) c[j] = s2p * a[j] * expi_quarter_pi(2 * j - 2 * lam - 1);
+}
+
+// Rearranged truncated Neumann/Taylor sum of Section 5.1: for perturbed
+// arguments, J_nu(x(v+w)) ~ sum_{u=0}^{2T+K-3} (x w)^u sum_lam g_{u,lam} J_lam(x v), with
+// g collecting (-1)^t 2^{-u} / (t!(u-t)!) [J_{nu-s} + (-1)^s J_{nu+s}], s = u - 2t,
+// t from max(ceil((u-K+1)/2), 0) to min(floor(u/2), T-1), and the s = 0 term halved
+// (the primed sums). Returns (lam, g) pairs for one u.
+std::vector<std::pair<int, double>> neumann_terms(int nu, int K, int T, int u) {
+  std::vector<std::pair<int, double>> out;
+  int a = u - K + 1;
+  int tlo = a <= 0 ? 0 : (a + 1) / 2;
+  int thi = std::min(u / 2, T - 1);
+  for (int t = tlo; t <= thi; ++t) {
+    int s = u - 2 * t;
+    double c = (t & 1) ? -1.0 : 1.0;
+    c = std::ldexp(c, -u);
+    for (int i = 2; i <= t; ++i) c /= i;
+    for (int i = 2; i <= u - t; ++i) c /= i;
+    if (s == 0) {
+      out.push_back({nu, c});
+    } else {
+      out.push_back({nu - s, c});
+      out.push_back({nu + s, (s & 1) ? -c : c});
+    }
+  }
+  return out;
+}
+
+double factorial(int n) {
+  double f = 1.0;
+  for (int i = 2; i <= n; ++i) f *= i;
+  return f;
+}
+
+// ---------------------------------------------------------------------------
+// Bessel roots j_{0,n} as b_n = j_{0,n} - (n-1/4)pi (Lemma 3.2)
+// ---------------------------------------------------------------------------
+// Large roots: from Eq. (4) with lam = 0, J_0 ~ sqrt(2/(pi z)) (P cos mu - Q sin mu) and
+// mu = (n-1/2)pi + b, so J_0 = 0 <=> tan b = -Q(z)/P(z), z = (n-1/4)pi + b. The map
+// b -> atan(-Q/P) contracts by ~1/(8 z^2); its fixed point keeps b's full relative accuracy.
+double root_offset_large(int64_t n) {
+  double beta = (n - 0.25) * kPi;
+  double b = 0.125 / beta;
+  double a[80];
+  hankel_a(0, 79, a);
+  for (int it = 0; it < 12; ++it) {
+    double z = beta + b;
+    double iz = 1.0 / z, p = 0.0, q = 0.0, zm = 1.0;
+    for (int m = 0; m < 79; ++m) {
+      double term = a[m] * zm;
+      if (m > 2 && std::fabs(term) < 1e-21) break;
+      int r = m & 3;
+      if (r == 0) p += term; else if (r == 1) q += term; else if (r == 2) p -= term; else q -= term;
+      zm *= iz;
+    }
+    double nb = std::atan(-q / p);
+    if (std::fabs(nb - b) <= 1e-19 * b) { b = nb; break; }
+    b = nb;
+  }
+  return b;
+}
+
+// Small roots: Newton on J_0 in double-double from the large-root formula's guess.
+double root_offset_small(int64_t n) {
+  DD base = dd_mul(kPiDD, ddv(n - 0.25));
+  DD b = ddv(root_offset_large(n));
+  std::vector<DD> J;
+  for (int it = 0; it < 10; ++it) {
+    miller_all(dd_add(base, b), 1, J);
+    DD step = dd_div(J[0], J[1]);  // J_0' = -J_1
+    b = dd_add(b, step);
+    if (std::fabs(step.h) < 1e-32 * std::fabs(b.h)) break;
+  }
+  return b.h + b.l;
+}
+
+// sin and cos of pi*A/B (integers, B > 0), reduced in integers to a quarter turn.
+void sincospi_ratio(int64_t A, int64_t B, double* s, double* c) {
+  int64_t a = A % (2 * B);
+  if (a < 0) a += 2 * B;
+  int64_t q = (4 * a + B) / (2 * B);  // round(2a/B)
+  int64_t y = 2 * a - q * B;          // angle = pi*(q/2 + y/(2B)), |y/(2B)| <= 1/4
+  double t = kPi * ((double)y / (double)(2 * B));
+  double ct = std::cos(t), st = std::sin(t);
+  switch (q & 3) {
+    case 0: *c = ct; *s = st; break;
+    case 1: *c = -st; *s = ct; break;
+    case 2: *c = -ct; *s = -st; break;
+    default: *c = st; *s = -ct; break;
+  }
+}
+
+int64_t ceil_index(double tau, double shift) {
+  // smallest integer i >= 1 with i + shift >= tau
+  double v = std::ceil(tau - shift);
+  int64_t i = (int64_t)v;
+  while (i > 1 && (double)(i - 1) + shift >= tau) --i;
+  while ((double)i + shift < tau) ++i;
+  return std::max<int64_t>(i, 1);
+}
+
+}  // namespace
+
+void j0_zero_offsets(int64_t count, double* b) {
+  for (int64_t n = 1; n <= count; ++n) b[n - 1] = ((n - 0.25) * kPi < 30.0) ? root_offset_small(n) : root_offset_large(n);
+}
+
+}  // namespace hk
+
+// ---------------------------------------------------------------------------
+// Host-only parameter formulas exported through the C ABI
+// ---------------------------------------------------------------------------
+extern "C" double hankel_s_nu_M(int nu, int M, double eps) {
+  // Section 3.1: s^{(j+1)} = (sqrt(2)(|a_2M| + |a_2M+1|/s^{(j)}) / (sqrt(pi) eps))^{1/(2M+1/2)}, s^{(0)} = 1, four steps.
+  double a[128];
+  if (M < 1 || M > 60 || !(eps > 0)) return NAN;
+  hk::hankel_a(nu, 2 * M + 1, a);
+  double s = 1.0;
+  for (int j = 0; j < 4; ++j)
+    s = std::pow(std::sqrt(2.0) * (std::fabs(a[2 * M]) + std::fabs(a[2 * M + 1]) / s) / (std::sqrt(hk::kPi) * eps),
+                 1.0 / (2.0 * M + 0.5));
+  return s;
+}
+
+extern "C" double hankel_t_nu_T(int nu, int T, double eps) {
+  // Section 3.2: t_{nu,T}(eps) ~ (2^{2T+nu} (T+nu)! T! eps)^{1/(2T+nu)}
+  if (T < 1 || nu < 0 || !(eps > 0)) return NAN;
+  double e = 2.0 * T + nu;
+  double lg = e * std::log(2.0) + std::lgamma(T + nu + 1.0) + std::lgamma(T + 1.0) + std::log(eps);
+  return std::exp(lg / e);
+}
+
+extern "C" double hankel_neumann_radius(int K, double eps) {
+  // Eq. (10): |dz| <= (2/e) (eps/5.2)^{1/K}
+  if (K < 1 || !(eps > 0)) return NAN;
+  return 2.0 / std::exp(1.0) * std::pow(eps / 5.2, 1.0 / K);
+}
+
+extern "C" double hankel_p_K(int K, double eps) {
+  // Eq. (23): p_K(eps) = e/(16 pi) (5.2/eps)^{1/K} + 1/4
+  if (K < 1 || !(eps > 0)) return NAN;
+  return std::exp(1.0) / (16.0 * hk::kPi) * std::pow(5.2 / eps, 1.0 / K) + 0.25;
+}
+
+extern "C" double hankel_q_T(int T, double eps) {
+  // Eq. (24): q_T(eps) = eps^{-1/(2T)} / (16 pi (T!)^{1/T}) + 1/4
+  if (T < 1 || !(eps > 0)) return NAN;
+  return std::pow(eps, -1.0 / (2.0 * T)) / (16.0 * hk::kPi * std::pow(hk::factorial(T), 1.0 / T)) + 0.25;
+}
+
+namespace hk {
+
+int choose_params(const hankel_options& o, HostPlan& hp) {
+  hp.opt = o;
+  if (o.N < 2 || o.N > (int64_t(1) << 24)) return HANKEL_EINVAL;
+  if (!(o.eps > 0.0) || !(o.eps < 1.0)) return HANKEL_EINVAL;
+  if (o.nu < 0 || o.nu > 64) return HANKEL_EINVAL;
+  if (o.task < HANKEL_SCHLOMILCH || o.task > HANKEL_DHT) return HANKEL_EINVAL;
+  if (o.task == HANKEL_DHT && o.nu != 0) return HANKEL_EINVAL;
+  if (o.grid != HANKEL_GRID_UNIT && o.grid != HANKEL_GRID_PAPER) return HANKEL_EINVAL;
+  if (o.max_nrhs < 1) return HANKEL_EINVAL;
+  if (o.precision < HANKEL_PREC_AUTO || o.precision > HANKEL_PREC_FP32) return HANKEL_EINVAL;
+  if (o.task == HANKEL_SCHLOMILCH && (o.gamma < -1 || o.gamma > 1024)) return HANKEL_EINVAL;
+  if (o.eps < 1e-16) return HANKEL_EUNSUPPORTED;
+  if (o.precision == HANKEL_PREC_FP32 && o.eps < 1e-5) return HANKEL_EUNSUPPORTED;
+  hp.fp32 = (o.precision == HANKEL_PREC_FP32);
+
+  const int64_t N = o.N;
+  // Table 4: M = max(floor(0.3 log(1/eps)), 3), natural logarithm.
+  hp.M = std::max((int)std::floor(0.3 * std::log(1.0 / o.eps)), 3);
+
+  if (o.task == HANKEL_SCHLOMILCH) {
+    hp.K = hp.T = hp.K2 = hp.T2 = 1;
+    hp.U1 = hp.U2 = 1;
+    hp.mu_max = o.nu;
+  } else {
+    // Section 5: K, T the smallest integers with p_K <= 30 and q_T <= 30 (Eqs. 23-24);
+    // Section 6 (DHT rows): the smallest with 1.01 max(p_K, q_T) <= 30.
+    auto smallest_K = [&](double fac) { int K = 1; while (fac * hankel_p_K(K, o.eps) > 30.0) ++K; return K; };
+    auto smallest_T = [&](double fac) { int T = 1; while (fac * hankel_q_T(T, o.eps) > 30.0) ++T; return T; };
+    if (o.task == HANKEL_FOURIER_BESSEL) {
+      hp.K = hp.K2 = smallest_K(1.0);
+      hp.T = hp.T2 = smallest_T(1.0);
+      hp.U1 = 1;
+      hp.U2 = 2 * hp.T + hp.K - 2;
+      hp.mu_max = o.nu + hp.K - 1;
+      hp.ncd = (int64_t)std::floor(std::max(hankel_p_K(hp.K, o.eps), hankel_q_T(hp.T, o.eps)));
+    } else {
+      hp.K = smallest_K(1.01);
+      hp.T = smallest_T(1.01);
+      hp.K2 = smallest_K(1.0);
+      hp.T2 = smallest_T(1.0);
+      hp.U1 = 2 * hp.T + hp.K - 2;
+      hp.U2 = 2 * hp.T2 + hp.K2 - 2;
+      hp.mu_max = (hp.K - 1) + (hp.K2 - 1);
+      hp.nrd = (int64_t)std::floor(1.01 * std::max(hankel_p_K(hp.K, o.eps), hankel_q_T(hp.T, o.eps)));
+      hp.ncd = (int64_t)std::floor(std::max(hankel_p_K(hp.K2, o.eps), hankel_q_T(hp.T2, o.eps)));
+    }
+    if (hp.U1 > kMaxU || hp.U2 > kMaxU) return HANKEL_EUNSUPPORTED;
+  }
+  hp.nrd = std::min(hp.nrd, N);
+  hp.ncd = std::min(hp.ncd, N);
+  // alpha from the largest order met in the expansion (all orders share one partition).
+  hp.s = hankel_s_nu_M(hp.mu_max, hp.M, o.eps);
+  hp.alpha = std::sqrt(hp.s / kPi);
+  // Table 4: beta = min(3/log N, 1), P = ceil(log(30 alpha^{-1} N^{-1/2}) / log beta), at least 0.
+  hp.beta = std::min(3.0 / std::log((double)N), 1.0);
+  hp.P = 0;
+  if (hp.beta < 1.0) {
+    double v = std::log(30.0 / (hp.alpha * std::sqrt((double)N))) / std::log(hp.beta);
+    hp.P = std::max(0, (int)std::ceil(v));
+  }
+
+  // Phase and partition coordinates of each task.
+  if (o.task == HANKEL_SCHLOMILCH) {
+    hp.Ua = 1; hp.Va = 1; hp.Vb = o.gamma;
+    hp.y0 = (double)o.gamma;
+    if (o.grid == HANKEL_GRID_UNIT) { hp.Ub = -1; hp.E = N - 1; hp.x0 = 1.0; hp.D = (double)(N - 1); }
+    else { hp.Ub = 0; hp.E = N; hp.x0 = 0.0; hp.D = (double)N; }
+  } else if (o.task == HANKEL_FOURIER_BESSEL) {
+    hp.Ua = 4; hp.Va = 4; hp.Vb = -1;
+    hp.y0 = -0.25;
+    if (o.grid == HANKEL_GRID_UNIT) { hp.Ub = -4; hp.E = 16 * (N - 1); hp.x0 = 1.0; hp.D = (double)(N - 1); }
+    else { hp.Ub = 0; hp.E = 16 * N; hp.x0 = 0.0; hp.D = (double)N; }
+  } else {
+    hp.Ua = 4; hp.Ub = -1; hp.Va = 4; hp.Vb = -1; hp.E = 16 * N + 12;
+    hp.x0 = 0.25; hp.y0 = -0.25; hp.D = (double)N + 0.75;
+  }
+  return HANKEL_OK;
+}
+
+namespace {
+
+void build_nodes(HostPlan& hp) {
+  const hankel_options& o = hp.opt;
+  const int64_t N = o.N;
+  hp.r_true.assign(N, 0.0);
+  hp.om_true.assign(N, 0.0);
+  hp.rowvar.assign(N, 0.0);
+  hp.rowpert.assign(N, 0.0);
+  hp.omt.assign(N, 0.0);
+  hp.betan.assign(N, 0.0);
+  hp.colpow.assign(N, 1.0);
+  if (o.task != HANKEL_SCHLOMILCH) {
+    hp.b.assign(N + 1, 0.0);
+    j0_zero_offsets(N + 1, hp.b.data());
+  }
+  for (int64_t k = 1; k <= N; ++k) {
+    double r;
+    if (o.task == HANKEL_DHT) {
+      // r_k = j_{0,k}/j_{0,N+1} = r~_k + e_k, r~_k = (4k-1)/(4N+3),
+      // e_k = (b_k (N+3/4) - b_{N+1} (k-1/4)) / (j_{0,N+1} (N+3/4)) (proof of Lemma 3.2).
+      double jN1 = (N + 0.75) * kPi + hp.b[N];
+      double rt = (double)(4 * k - 1) / (double)(4 * N + 3);
+      double e = (hp.b[k - 1] * (N + 0.75) - hp.b[N] * (k - 0.25)) / (jN1 * (N + 0.75));
+      hp.rowvar[k - 1] = rt;
+      hp.rowpert[k - 1] = e;
+      r = rt + e;
+    } else {
+      r = (o.grid == HANKEL_GRID_UNIT) ? (double)(k - 1) / (double)(N - 1) : (double)k / (double)N;
+      hp.rowvar[k - 1] = r;
+    }
+    hp.r_true[k - 1] = r;
+  }
+  for (int64_t n = 1; n <= N; ++n) {
+    if (o.task == HANKEL_SCHLOMILCH) {
+      double w = (double)(n + o.gamma) * kPi;
+      hp.om_true[n - 1] = w;
+      hp.omt[n - 1] = w;
+    } else {
+      double wt = (n - 0.25) * kPi;
+      double bn = hp.b[n - 1];
+      hp.omt[n - 1] = wt;
+      hp.om_true[n - 1] = wt + bn;
+      hp.betan[n - 1] = bn / wt;
+      if (o.task == HANKEL_DHT) hp.colpow[n - 1] = wt + bn;
+    }
+  }
+}
+
+void build_partition(HostPlan& hp) {
+  const int64_t N = hp.opt.N;
+  const double sq = std::sqrt(hp.D);
+  auto tau = [&](int p) { return hp.alpha * std::pow(hp.beta, (double)p) * sq; };
+  auto kidx = [&](double t) { return ceil_index(t, -hp.x0); };  // k - x0 >= t
+  auto nidx = [&](double t) { return ceil_index(t, hp.y0); };   // n + y0 >= t
+  std::vector<Block> raw;
+  auto add = [&](int64_t k0, int64_t k1, int64_t n0, int64_t n1) {
+    k0 = std::max(k0, hp.nrd + 1);
+    n0 = std::max(n0, hp.ncd + 1);
+    k1 = std::min(k1, N);
+    n1 = std::min(n1, N);
+    if (k0 > k1 || n0 > n1) return;
+    Block b;
+    b.k0 = k0; b.k1 = k1; b.n0 = n0; b.n1 = n1;
+    b.R = k1 - k0 + 1;
+    b.C = n1 - n0 + 1;
+    int lf = 6;  // at least 64 points
+    while ((int64_t(1) << lf) < b.R + b.C - 1) ++lf;
+    b.logF = lf;
+    b.F = int64_t(1) << lf;
+    raw.push_back(b);
+  };
+  // Eq. (19): Q1 J Q1 and, for p = 1..P, Q_{2p+1} J Q_{2p} and Q_{2p} J Q_{2p+1}, with the
+  // row band of Q_{2p+1} read as [alpha beta^p sqrt(N), alpha beta^{p-1} sqrt(N)).
+  add(kidx(tau(0)), N, nidx(tau(0)), N);
+  for (int p = 1; p <= hp.P; ++p) {
+    add(kidx(tau(p)), kidx(tau(p - 1)) - 1, nidx(tau(-p)), N);
+    add(kidx(tau(-p)), N, nidx(tau(p)), nidx(tau(p - 1)) - 1);
+  }
+  hp.blocks = raw;
+  // Near set: per row, the columns not covered by a block; always a prefix 1..nend(k).
+  std::vector<int64_t> fstart(N + 2, N + 1), covered(N + 2, 0);
+  hp.far_count = 0;
+  for (const Block& b : hp.blocks) {
+    for (int64_t k = b.k0; k <= b.k1; ++k) {
+      fstart[k] = std::min(fstart[k], b.n0);
+      covered[k] += b.C;
+    }
+    hp.far_count += b.R * b.C;
+  }
+  hp.nend.assign(N, 0);
+  hp.near_count = 0;
+  hp.zmax = 0.0;
+  for (int64_t k = 1; k <= N; ++k) {
+    int64_t ne = fstart[k] - 1;
+    // the far columns of row k must be exactly fstart..N
+    if (covered[k] != N - ne) { hp.nend.clear(); return; }
+    hp.nend[k - 1] = ne;
+    hp.near_count += ne;
+    if (ne > 0) hp.zmax = std::max(hp.zmax, hp.r_true[k - 1] * hp.om_true[ne - 1]);
+  }
+}
+
+void build_columns(HostPlan& hp) {
+  const hankel_options& o = hp.opt;
+  const int M = hp.M;
+  const int U1 = hp.U1, U2 = hp.U2;
+  const int nd = 2 * M + U2 - 1;  // delta = u2 - j in [-(2M-1), U2-1]
+  std::vector<cplx> G((size_t)U1 * nd * U2, cplx(0.0, 0.0));
+  auto at = [&](int u1, int delta, int u2) -> cplx& { return G[((size_t)u1 * nd + (delta + 2 * M - 1)) * U2 + u2]; };
+  cplx c[128];
+  if (o.task == HANKEL_SCHLOMILCH) {
+    hankel_c(o.nu, M, c);
+    for (int j = 0; j < 2 * M; ++j) at(0, -j, 0) += c[j];
+  } else if (o.task == HANKEL_FOURIER_BESSEL) {
+    // Section 5.1: J_nu(r j_{0,n}) ~ sum_u (r b_n)^u sum_lam g_{u,lam} J_lam(r omega~_n) (Eq. 22 rearranged)
+    for (int u = 0; u < U2; ++u)
+      for (auto& t : neumann_terms(o.nu, hp.K, hp.T, u)) {
+        hankel_c(t.first, M, c);
+        for (int j = 0; j < 2 * M; ++j) at(0, u - j, u) += t.second * c[j];
+      }
+  } else {
+    // Section 6, Eq. (26): rows perturbed by e_k (outer sum over u1, truncation K, T), then each
+    // J_lam(r~_k j_{0,n}) expanded in b_n as in Section 5 (inner sum over u2, truncation K2, T2).
+    for (int u1 = 0; u1 < U1; ++u1)
+      for (auto& t1 : neumann_terms(0, hp.K, hp.T, u1))
+        for (int u2 = 0; u2 < U2; ++u2)
+          for (auto& t2 : neumann_terms(t1.first, hp.K2, hp.T2, u2)) {
+            hankel_c(t2.first, M, c);
+            for (int j = 0; j < 2 * M; ++j) at(u1, u2 - j, u2) += (t1.second * t2.second) * c[j];
+          }
+  }
+  hp.cols.clear();
+  for (int u1 = 0; u1 < U1; ++u1)
+    for (int d = -(2 * M - 1); d <= U2 - 1; ++d) {
+      ColSpec cs;
+      cs.u1 = u1;
+      cs.delta = d;
+      cs.nterm = U2;
+      for (int u2 = 0; u2 < kMaxU; ++u2) cs.G[u2] = u2 < U2 ? at(u1, d, u2) : cplx(0.0, 0.0);
+      hp.cols.push_back(cs);
+    }
+}
+
+// Taylor polynomials of J_nu about z_c = i + 1/2 on [i, i+1). The coefficients follow from
+// the Neumann addition formula (Eq. 8) with each J_s(delta) expanded in its Taylor series
+// (Eq. 6) -- the same rearrangement as Section 5.1 with K and T unbounded:
+// t_d = 2^{-d} sum_t (-1)^t / (t!(d-t)!) [J_{nu-s}(z_c) + (-1)^s J_{nu+s}(z_c)], s = d-2t,
+// the s = 0 term counted once.
+void build_jtable(HostPlan& hp) {
+  const int nu = hp.opt.nu;
+  const int deg = hp.fp32 ? kJTabDegF32 : kJTabDeg;
+  hp.jt_deg = deg;
+  hp.jt_n = (int64_t)std::ceil(hp.zmax) + 2;
+  hp.jtab.assign((size_t)hp.jt_n * (deg + 1), 0.0);
+  std::vector<DD> J;
+  const int L = nu + deg + 1;
+  for (int64_t i = 0; i < hp.jt_n; ++i) {
+    DD zc = ddv(i + 0.5);
+    miller_all(zc, L, J);
+    auto jl = [&](int lam) -> DD {  // J_lam for any integer lam (DLMF 10.4.1)
+      if (lam >= 0) return J[lam];
+      return ((-lam) & 1) ? dd_neg(J[-lam]) : J[-lam];
+    };
+    for (int d = 0; d <= deg; ++d) {
+      DD acc = ddv(0.0);
+      for (int t = 0; 2 * t <= d; ++t) {
+        int s = d - 2 * t;
+        double coef = std::ldexp((t & 1) ? -1.0 : 1.0, -d) / (factorial(t) * factorial(d - t));
+        DD term = (s == 0) ? jl(nu) : dd_add(jl(nu - s), (s & 1) ? dd_neg(jl(nu + s)) : jl(nu + s));
+        acc = dd_add(acc, dd_mul(ddv(coef), term));
+      }
+      hp.jtab[(size_t)i * (deg + 1) + d] = acc.h + acc.l;
+    }
+  }
+}
+
+}  // namespace
+
+int build_host_plan(const hankel_options& opt, HostPlan& hp) {
+  int st = choose_params(opt, hp);
+  if (st != HANKEL_OK) return st;
+  build_nodes(hp);
+  build_partition(hp);
+  if (hp.nend.empty()) return HANKEL_EINVAL;  // partition invariant violated
+  build_columns(hp);
+  build_jtable(hp);
+  return HANKEL_OK;
+}
+
+double table_j(const HostPlan& hp, double z) {
+  int64_t i = (int64_t)z;
+  if (i < 0) i = 0;
+  if (i >= hp.jt_n) i = hp.jt_n - 1;
+  double d = z - ((double)i + 0.5);
+  const double* t = &hp.jtab[(size_t)i * (hp.jt_deg + 1)];
+  double v = t[hp.jt_deg];
+  for (int j = hp.jt_deg - 1; j >= 0; --j) v = v * d + t[j];
+  return v;
+}
+
+double host_entry(const HostPlan& hp, int64_t k, int64_t n, int* is_far) {
+  const int64_t N = hp.opt.N;
+  *is_far = 0;
+  if (n > hp.nend[k - 1]) {
+    *is_far = 1;
+    // exp(i theta~_kn), theta~ = pi U_k V_n / E reduced exactly
+    __int128 U = (__int128)hp.Ua * k + hp.Ub, V = (__int128)hp.Va * n + hp.Vb;
+    __int128 num = (U * V) % ((__int128)2 * hp.E);
+    double s, c;
+    sincospi_ratio((int64_t)num, hp.E, &s, &c);
+    cplx ph(c, s), acc(0.0, 0.0);
+    double rv = hp.rowvar[k - 1], rp = hp.rowpert[k - 1];
+    double w = hp.omt[n - 1], bt = hp.betan[n - 1], cp = hp.colpow[n - 1];
+    for (const ColSpec& cs : hp.cols) {
+      cplx poly(0.0, 0.0);
+      for (int u2 = cs.nterm - 1; u2 >= 0; --u2) poly = poly * bt + cs.G[u2];
+      double row = std::pow(rv, cs.delta - 0.5) * (cs.u1 ? std::pow(rp, cs.u1) : 1.0);
+      double col = std::pow(w, cs.delta - 0.5) * (cs.u1 ? std::pow(cp, cs.u1) : 1.0);
+      acc += row * col * poly;
+    }
+    return (ph * acc).real();
+  }
+  (void)N;
+  return table_j(hp, hp.r_true[k - 1] * hp.om_true[n - 1]);
+}
+
+}  // namespace hk

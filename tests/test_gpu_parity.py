@@ -1,0 +1,148 @@
+"""GPU parity: the CUDA path against the CPU oracle, element by element.
+
+Bar: max_k |f_k - f_k^oracle| <= 10 eps sum_n |c_n| (the paper's O(eps ||c||_1) accuracy,
+Sections 5.2 and 6.1, with the constant fixed at 10). Small sizes compare every output; the
+full-size workloads compare seeded sampled rows that the oracle computes one by one.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from hankel_inputs import coefficients, sample_rows
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1501_01652_gb300 as hk  # noqa: E402
+
+GRID = {"unit": 0, "paper": 1}
+
+
+def _run(task, nu, N, eps, c, grid="unit", **kw):
+    plan = hk.Plan(task, nu, N, eps, grid=grid, max_nrhs=c.shape[0], **kw)
+    cd = torch.from_numpy(c).cuda()
+    f = plan.exec(cd)
+    torch.cuda.synchronize()
+    return f.cpu().numpy(), plan
+
+
+def _check(task, nu, N, eps, c, rows=None, grid="unit", **kw):
+    f, plan = _run(task, nu, N, eps, c, grid=grid, **kw)
+    ref = oracle.transform(task, nu, N, c, rows=rows, grid=GRID[grid])
+    got = f if rows is None else f[:, rows]
+    bound = 10.0 * eps * np.abs(c).sum(axis=1)
+    err = np.abs(got - ref).max(axis=1)
+    assert np.all(err <= bound), (err / (eps * np.abs(c).sum(axis=1)), plan.info)
+    return err / (eps * np.abs(c).sum(axis=1))
+
+
+@pytest.mark.parametrize("N", [2, 3, 17, 64, 100, 257, 1000, 1023])
+@pytest.mark.parametrize("task", ["schlomilch", "fourier_bessel", "dht"])
+def test_small_and_ragged_sizes(task, N):
+    c = coefficients("normal", N, 2, 50 + N)
+    _check(task, 0, N, 1e-15, c)
+
+
+def test_schlomilch_nu0_N4096_full():
+    # Schlomilch, omega_n = n pi, r_k = (k-1)/(N-1), N = 4096, eps = 1e-15, every output
+    c = coefficients("uniform", 4096, 1, 1000)
+    _check("schlomilch", 0, 4096, 1e-15, c)
+
+
+@pytest.mark.parametrize("nu", [0, 1, 4])
+@pytest.mark.parametrize("eps", [1e-15, 1e-8])
+def test_schlomilch_shifted_orders(nu, eps):
+    N = 6000
+    c = coefficients("uniform", N, 3, 2000 + nu)
+    _check("schlomilch", nu, N, eps, c)
+
+
+def test_schlomilch_decaying_coefficients():
+    N = 5000
+    c = coefficients("decaying", N, 2, 2100)
+    _check("schlomilch", 1, N, 1e-15, c)
+
+
+@pytest.mark.parametrize("eps", [1e-15, 1e-8])
+def test_fourier_bessel_full(eps):
+    N = 5000
+    c = coefficients("uniform", N, 2, 3000)
+    _check("fourier_bessel", 0, N, eps, c)
+
+
+@pytest.mark.parametrize("eps", [1e-15, 1e-8, 1e-4])
+def test_dht_full(eps):
+    N = 5000
+    c = coefficients("normal", N, 2, 4000)
+    _check("dht", 0, N, eps, c)
+
+
+def test_paper_grid():
+    N = 3000
+    c = coefficients("uniform", N, 1, 4100)
+    _check("schlomilch", 0, N, 1e-15, c, grid="paper")
+    _check("fourier_bessel", 0, N, 1e-15, c, grid="paper")
+
+
+@pytest.mark.parametrize("task,nu,N,eps,kind", [
+    ("schlomilch", 0, 2 ** 16, 1e-15, "uniform"), ("schlomilch", 4, 2 ** 16, 1e-8, "decaying"),
+    ("fourier_bessel", 0, 2 ** 18, 1e-15, "uniform"), ("dht", 0, 2 ** 16, 1e-15, "normal"),
+    ("dht", 0, 2 ** 16, 1e-8, "normal"),
+])
+def test_workload_sizes_sampled_rows(task, nu, N, eps, kind):
+    c = coefficients(kind, N, 1, 5000 + N % 997)
+    rows = sample_rows(N, 96, 7)
+    _check(task, nu, N, eps, c, rows=rows)
+
+
+@pytest.mark.parametrize("eps", [1e-15, 1e-8])
+def test_dht_2p20_sampled_rows(eps):
+    # the benchmarked workload: DHT-0, N = 2^20, standard normal coefficients
+    N = 2 ** 20
+    c = coefficients("normal", N, 1, 4 * 1000)
+    rows = sample_rows(N, 64, 11)
+    _check("dht", 0, N, eps, c, rows=rows)
+
+
+def test_batched_matches_single():
+    N = 3000
+    c = coefficients("normal", N, 5, 6000)
+    fb, plan = _run("dht", 0, N, 1e-8, c)
+    for r in range(c.shape[0]):
+        fs, _ = _run("dht", 0, N, 1e-8, c[r:r + 1])
+        assert np.array_equal(fb[r], fs[0])
+
+
+def test_deterministic_and_host_entry_point():
+    N = 4097
+    c = coefficients("uniform", N, 2, 6100)
+    plan = hk.Plan("fourier_bessel", 0, N, 1e-15, max_nrhs=2)
+    cd = torch.from_numpy(c).cuda()
+    f1 = plan.exec(cd).cpu().numpy()
+    f2 = plan.exec(cd).cpu().numpy()
+    assert np.array_equal(f1, f2)
+    fh = plan.exec_host(c)
+    assert np.array_equal(f1, fh)
+
+
+def test_dht_self_inverse_gpu():
+    # Eq. (28): (1/j_{0,N+1}^2) J D_v J D_v c ~ c, v_n = 2/J_1(j_{0,n})^2, with both DHTs on the GPU.
+    N = 400
+    c = coefficients("normal", N, 1, 7)[0]
+    b = oracle.j0_zero_offsets(N + 1)
+    j = (np.arange(1, N + 2) - 0.25) * math.pi + b
+    v = np.array([2.0 / oracle.besselj_pi(1, 4 * n - 1, 4, b[n - 1]) ** 2 for n in range(1, N + 1)])
+    plan = hk.Plan("dht", 0, N, 1e-15)
+    y = plan.exec(torch.from_numpy(v * c).cuda())
+    ct = plan.exec(torch.from_numpy(v).cuda() * y).cpu().numpy() / j[N] ** 2
+    assert np.max(np.abs(ct - c)) <= 2e-11
+
+
+def test_rejects_bad_arguments():
+    plan = hk.Plan("schlomilch", 0, 100, 1e-8)
+    with pytest.raises(TypeError):
+        plan.exec(torch.zeros(100, dtype=torch.float32, device="cuda"))
+    with pytest.raises(RuntimeError, match="EINVAL"):
+        plan.exec(torch.zeros((2, 100), dtype=torch.float64, device="cuda"))  # nrhs > max_nrhs

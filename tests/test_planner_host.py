@@ -1,0 +1,108 @@
+"""Host-side plan tables (no GPU): nodes, partition geometry and the entry-wise
+representation of J_nu(r_k omega_n) against the oracle."""
+import ctypes
+import math
+import re
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1501_01652_gb300 as hk
+from paper_1501_01652_gb300 import _lib
+
+GRID = {"unit": 0, "paper": 1}
+CASES = [
+    ("schlomilch", 0, 1500, 1e-15, "unit"), ("schlomilch", 1, 1200, 1e-8, "unit"),
+    ("schlomilch", 4, 1500, 1e-15, "unit"), ("schlomilch", 0, 1400, 1e-4, "unit"),
+    ("schlomilch", 0, 900, 1e-15, "paper"), ("fourier_bessel", 0, 1500, 1e-15, "unit"),
+    ("fourier_bessel", 0, 1500, 1e-8, "unit"), ("fourier_bessel", 1, 1000, 1e-15, "paper"),
+    ("dht", 0, 1500, 1e-15, "unit"), ("dht", 0, 1500, 1e-8, "unit"), ("dht", 0, 1500, 1e-4, "unit"),
+]
+
+
+def test_library_exports_every_declared_symbol():
+    header = open(os.path.join(os.path.dirname(__file__), "..", "include", "hankel.h")).read()
+    declared = set(re.findall(r"^\s*(?:int|double|const char\*)\s+(hankel_\w+)\s*\(", header, re.M))
+    assert declared == set(_lib.EXPORTED)
+    lib = _lib.load()
+    for name in declared:
+        assert hasattr(lib, name), name
+
+
+def test_status_strings():
+    lib = _lib.load()
+    for code in range(0, 7):
+        assert lib.hankel_status_string(code)
+
+
+def test_node_offsets_against_oracle_and_lemma():
+    n = 20000
+    b = hk.j0_zero_offsets(n)
+    ref = oracle.j0_zero_offsets(n)
+    assert np.max(np.abs(b - ref) / ref) <= 4e-15
+    k = np.arange(1, n + 1)
+    assert np.all((b >= 0) & (b <= 1 / (8 * (k - 0.25) * math.pi)))
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: "%s-nu%d-N%d-%g-%s" % c)
+def test_partition_invariants(case):
+    task, nu, N, eps, grid = case
+    p = hk.Plan(task, nu, N, eps, grid=grid, host_only=True)
+    info = p.info
+    blocks = p.blocks()
+    assert len(blocks) <= 1 + 2 * info["P"]
+    covered = np.zeros(N + 1, dtype=np.int64)
+    for (k0, k1, n0, n1, F) in blocks:
+        assert 1 <= k0 <= k1 <= N and 1 <= n0 <= n1 <= N
+        assert F >= (k1 - k0 + 1) + (n1 - n0 + 1) - 1 and F & (F - 1) == 0
+        assert k0 > info["direct_rows"] and n0 > info["direct_cols"]
+        # every entry of the block has z~ = r~_k omega~_n >= s (corner is the minimum)
+        v, far = p.entry(k0, n0)
+        assert far
+        covered[k0:k1 + 1] += n1 - n0 + 1
+    total_near = 0
+    for k in range(1, N + 1):
+        ne = p.near_prefix(k)
+        assert covered[k] == N - ne  # far columns of row k are exactly ne+1..N
+        total_near += ne
+    assert total_near == info["near_count"]
+    assert info["near_count"] + info["far_count"] == N * N
+
+
+def _z_tilde(task, nu, N, grid, k, n):
+    # exact-grid argument r~_k omega~_n of a block corner, from the definitions of Sections 4-6
+    if task == "schlomilch":
+        r = (k - 1) / (N - 1) if grid == "unit" else k / N
+        return r * (n + nu) * math.pi
+    if task == "fourier_bessel":
+        r = (k - 1) / (N - 1) if grid == "unit" else k / N
+        return r * (n - 0.25) * math.pi
+    return (k - 0.25) / (N + 0.75) * (n - 0.25) * math.pi
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: "%s-nu%d-N%d-%g-%s" % c)
+def test_far_blocks_satisfy_criterion(case):
+    task, nu, N, eps, grid = case
+    p = hk.Plan(task, nu, N, eps, grid=grid, host_only=True)
+    s = p.info["s"]
+    for (k0, k1, n0, n1, F) in p.blocks():
+        assert _z_tilde(task, nu, N, grid, k0, n0) >= s * (1 - 1e-12)
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: "%s-nu%d-N%d-%g-%s" % c)
+def test_entries_against_oracle(case):
+    # The plan's value for each entry (near-field evaluator or far-field expansion) is within
+    # eps of J_nu(r_k omega_n) (Sections 3-6: each expansion is used only where it is eps-accurate).
+    task, nu, N, eps, grid = case
+    p = hk.Plan(task, nu, N, eps, grid=grid, host_only=True)
+    info = p.info
+    rows = sorted({1, 2, info["direct_rows"] + 1, N // 7, N // 2, N - 1, N})
+    eye = np.eye(N)
+    for k in rows:
+        ref = oracle.transform(task, nu, N, eye, rows=np.array([k - 1]), grid=GRID[grid])[:, 0]
+        for n in range(1, N + 1, 3):
+            v, far = p.entry(k, n)
+            tol = eps if far else 4e-15
+            assert abs(v - ref[n - 1]) <= tol, (k, n, far, v, ref[n - 1])
