@@ -151,6 +151,30 @@ int hankel_exec(hankel_plan_t p, const double* c, double* f, void* stream);
 int hankel_exec_batched(hankel_plan_t p, const double* c, int64_t ldc, double* f, int64_t ldf,
                         int nrhs, void* stream);
 
+/* Size of the library's static device scratch array used by hankel_exec_static (96 MiB). */
+#define HANKEL_STATIC_SCRATCH_BYTES (96u << 20)
+
+/* Allocation-free execution. The paper has no counterpart; this is a service of the library.
+ * Computes the same f as hankel_exec(p, c, f, stream) for one vector (device arrays of N
+ * doubles, asynchronous on `stream`), but the call itself allocates no memory: it calls no
+ * cudaMalloc, cudaFree or other allocating routine. The transform workspace (the FFT column
+ * buffers and the near-field partial sums) comes from one file-scope device array of
+ * HANKEL_STATIC_SCRATCH_BYTES that every GPU loading this library holds until the process
+ * exits. It is meant for callers that cannot allocate device memory when they run a
+ * transform: services whose device memory is all handed to their own pool allocator, and
+ * latency-critical loops that must not enter the CUDA allocator. The plan's own tables are
+ * still made by hankel_plan*, ahead of time.
+ *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ *    with that device current; make that first call before any stream capture begins.
+ *  - All calls share the array and its contents persist between calls; every element a call
+ *    reads is written earlier in the same call, so no clearing is needed. Calls that overlap
+ *    on the GPU (other streams, other plans) race on the array: order them on one stream.
+ *  - Returns HANKEL_EUNSUPPORTED when the plan's largest transform needs more than the array
+ *    holds (two columns of F complex doubles plus the near-field partial sums; in practice
+ *    N up to about 2^20 for the DHT), HANKEL_EINVAL on NULL arguments or a host-only plan,
+ *    HANKEL_ECUDA if a launch or the address lookup fails. */
+int hankel_exec_static(hankel_plan_t p, const double* c, double* f, void* stream);
+
 /* End-to-end form with HOST arrays (same layout as hankel_exec_batched): copies c to the
  * device, runs the transform and copies f back. Blocks until f is written. */
 int hankel_exec_host(hankel_plan_t p, const double* c, int64_t ldc, double* f, int64_t ldf, int nrhs);

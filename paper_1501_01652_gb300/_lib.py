@@ -17,7 +17,7 @@ EXPORTED = [
     "hankel_exec_host", "hankel_plan_info", "hankel_plan_blocks", "hankel_plan_entry",
     "hankel_plan_near_prefix", "hankel_destroy", "hankel_status_string", "hankel_s_nu_M",
     "hankel_t_nu_T", "hankel_neumann_radius", "hankel_p_K", "hankel_q_T", "hankel_params",
-    "hankel_j0_zero_offsets", "hankel_plan_set_timing", "hankel_plan_stage_stats",
+    "hankel_j0_zero_offsets", "hankel_plan_set_timing", "hankel_plan_stage_stats", "hankel_exec_static",
 ]
 STAGES = ["near", "gen", "fft", "pointwise", "out"]
 
@@ -84,6 +84,7 @@ def load():
         "hankel_params": (i32, [ctypes.POINTER(Options), ctypes.POINTER(Info)]),
         "hankel_j0_zero_offsets": (i32, [i64, dp]),
         "hankel_plan_set_timing": (i32, [vp, i32]),
+        "hankel_exec_static": (i32, [vp, vp, vp, vp]),
         "hankel_plan_stage_stats": (i32, [vp, ctypes.POINTER(StageStat)]),
     }
     for name, (res, args) in sig.items():

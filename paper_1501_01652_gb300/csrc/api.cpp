@@ -188,6 +188,11 @@ int hankel_exec_host(hankel_plan_t p, const double* c, int64_t ldc, double* f, i
   return hk::dev_exec_host(p, c, ldc, f, ldf, nrhs);
 }
 
+int hankel_exec_static(hankel_plan_t p, const double* c, double* f, void* stream) {
+  if (!p || !c || !f || p->host_only) return HANKEL_EINVAL;
+  return hk::dev_exec_static(p, c, f, stream);
+}
+
 int hankel_plan_set_timing(hankel_plan_t p, int enable) {
   if (!p || p->host_only) return HANKEL_EINVAL;
   return hk::dev_set_timing(p, enable);

@@ -13,6 +13,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "device.h"
@@ -377,6 +378,103 @@ int dev_exec_host(hankel_plan_s* p, const double* c, int64_t ldc, double* f, int
                         cudaMemcpyDeviceToHost, st) != cudaSuccess)
     return HANKEL_ECUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return HANKEL_ECUDA;
+  if (cur >= 0 && cur != d->device) cudaSetDevice(cur);
+  return HANKEL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free execution (hankel_exec_static)
+//
+// The same near-field and far-field launches as dev_exec for one vector, but the
+// transform workspace -- the two FFT ping-pong column buffers and the near-field
+// partial sums -- lives in the file-scope array below instead of memory the plan
+// allocated. The array is placed on every device that loads this library and is
+// kept until the process exits. Every element the launches read is written by an
+// earlier launch of the same call, so nothing needs clearing between calls. All
+// calls share the array: calls that overlap on the GPU (on different streams, or
+// from different plans) race on it.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kStaticScratchElems = (size_t)HANKEL_STATIC_SCRATCH_BYTES / sizeof(double2);
+constexpr int kMaxStaticDevices = 64;
+
+static __device__ __align__(256) double2 g_static_scratch[kStaticScratchElems];
+
+// Device address of g_static_scratch per device, looked up once with that device current.
+double2* g_static_ptr[kMaxStaticDevices] = {};
+bool g_static_ready[kMaxStaticDevices] = {};
+std::mutex g_static_mu;
+
+int static_scratch_address(int device, double2** out) {
+  if (device < 0 || device >= kMaxStaticDevices) return HANKEL_EUNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_ready[device]) {
+    void* ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_static_scratch) != cudaSuccess) {
+      cudaGetLastError();
+      return HANKEL_ECUDA;
+    }
+    g_static_ptr[device] = (double2*)ptr;
+    g_static_ready[device] = true;
+  }
+  *out = g_static_ptr[device];
+  return HANKEL_OK;
+}
+
+}  // namespace
+
+int dev_exec_static(hankel_plan_s* p, const double* c, double* f, void* stream) {
+  const HostPlan& hp = p->hp;
+  DevicePlan* d = p->dev;
+  const int64_t N = hp.opt.N;
+  // Layout of the static array: [bufA | bufB | near partial sums (as doubles)].
+  const size_t partial_elems = ((size_t)d->nslots + 1) / 2 + 1;
+  int64_t Fmax = 0;
+  for (const DevBlock& db : d->blocks) Fmax = std::max<int64_t>(Fmax, db.b.F);
+  if (2 * (size_t)Fmax + partial_elems > kStaticScratchElems) return HANKEL_EUNSUPPORTED;
+  const size_t per_buf = (kStaticScratchElems - partial_elems) / 2;
+
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (cur != d->device) cudaSetDevice(d->device);
+  double2* base = nullptr;
+  int st0 = static_scratch_address(d->device, &base);
+  if (st0 != HANKEL_OK) {
+    if (cur >= 0 && cur != d->device) cudaSetDevice(cur);
+    return st0;
+  }
+  double2* sA = base;
+  double2* sB = base + per_buf;
+  double* spartial = (double*)(base + 2 * per_buf);
+  cudaStream_t st = (cudaStream_t)stream;
+
+  launch_near(d->items, d->nitems, d->mrows, d->nmrows, spartial, 1, c, N, f, N, d->nodes, d->jtab, hp.jt_n,
+              hp.jt_deg, st);
+  HK_LAUNCHED();
+  const int64_t total = d->ncols;
+  for (const DevBlock& db : d->blocks) {
+    const Block& b = db.b;
+    const int64_t cap = std::max<int64_t>(1, std::min<int64_t>((int64_t)(per_buf / (size_t)b.F), 65535));
+    for (int64_t c0 = 0; c0 < total; c0 += cap) {
+      const int nc = (int)std::min<int64_t>(cap, total - c0);
+      GenArgs ga{sA, b.F, b.C, b.n0, nc, c0, d->ncols, c, N, d->nodes, d->cols, db.wV};
+      launch_gen(ga, st);
+      HK_LAUNCHED();
+      double2* res = nullptr;
+      HK_TRY(run_fft(sA, sB, b.logF, nc, false, d->tw, d->logFmax, st, &res));
+      HK_LAUNCHED();
+      launch_pointwise(res, db.H, b.F, nc, st);
+      HK_LAUNCHED();
+      double2* other = (res == sA) ? sB : sA;
+      double2* res2 = nullptr;
+      HK_TRY(run_fft(res, other, b.logF, nc, true, d->tw, d->logFmax, st, &res2));
+      HK_LAUNCHED();
+      OutArgs oa{res2, b.F, b.R, b.C, b.k0, nc, c0, d->ncols, f, N, d->nodes, d->cols, db.wU};
+      launch_out(oa, st);
+      HK_LAUNCHED();
+    }
+  }
   if (cur >= 0 && cur != d->device) cudaSetDevice(cur);
   return HANKEL_OK;
 }
