@@ -81,7 +81,8 @@ enum hankel_status {
 };
 
 /* Plan flags (hankel_options.flags). */
-#define HANKEL_FLAG_HOST_ONLY 1u  /* build host tables only; no CUDA call is made */
+#define HANKEL_FLAG_HOST_ONLY 1u   /* build host tables only; no CUDA call is made */
+#define HANKEL_FLAG_NO_SEGMENT 2u  /* one full-length chirp-z transform per block (no segmenting of thin blocks) */
 
 /* Options for hankel_plan_ex(). Fill with hankel_options_default() first. */
 typedef struct {
@@ -125,7 +126,11 @@ typedef struct {
 typedef struct {
   int64_t k0, k1;  /* rows */
   int64_t n0, n1;  /* columns */
-  int64_t fft_len; /* chirp-z transform length F (a power of two >= rows + cols - 1) */
+  int64_t fft_len; /* length F of its FFTs, a power of two */
+  int64_t seg_len; /* segment length S of the long side (= columns for an unsegmented block) */
+  int64_t nseg;    /* number of segments (1 = one transform with F >= rows + cols - 1) */
+  int mode;        /* 0 unsegmented; 1 columns segmented (overlap-add), F >= rows + S - 1;
+                      2 rows segmented (overlap-save), F >= S + cols - 1 */
 } hankel_block;
 
 /* Fill *o with defaults for (task, nu, N, eps). Host only. Returns HANKEL_OK or HANKEL_EINVAL (o == NULL). */

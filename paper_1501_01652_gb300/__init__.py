@@ -18,7 +18,7 @@ PRECISIONS = {"auto": 0, "fp64": 1, "fp32": 2}
 
 
 def _options(task, nu, N, eps, grid="unit", gamma=None, precision="auto", max_nrhs=1, workspace_limit=0,
-             host_only=False):
+             host_only=False, segment=True):
     lib = _lib.load()
     o = _lib.Options()
     _lib.check(lib.hankel_options_default(ctypes.byref(o), TASKS[task], int(nu), int(N), float(eps)),
@@ -29,7 +29,7 @@ def _options(task, nu, N, eps, grid="unit", gamma=None, precision="auto", max_nr
     o.precision = PRECISIONS[precision]
     o.max_nrhs = int(max_nrhs)
     o.workspace_limit = int(workspace_limit)
-    o.flags = _lib.FLAG_HOST_ONLY if host_only else 0
+    o.flags = (_lib.FLAG_HOST_ONLY if host_only else 0) | (0 if segment else _lib.FLAG_NO_SEGMENT)
     return o
 
 
@@ -74,12 +74,12 @@ class Plan:
     """A transform plan: f = J_nu(r omega^T) c for one task, order, size and accuracy."""
 
     def __init__(self, task, nu, N, eps, grid="unit", gamma=None, precision="auto", max_nrhs=1,
-                 workspace_limit=0, host_only=False):
+                 workspace_limit=0, host_only=False, segment=True):
         self._lib = _lib.load()
         self._h = ctypes.c_void_p()
         self.task, self.nu, self.N, self.eps = task, int(nu), int(N), float(eps)
         self.max_nrhs = int(max_nrhs)
-        o = _options(task, nu, N, eps, grid, gamma, precision, max_nrhs, workspace_limit, host_only)
+        o = _options(task, nu, N, eps, grid, gamma, precision, max_nrhs, workspace_limit, host_only, segment)
         _lib.check(self._lib.hankel_plan_ex(ctypes.byref(self._h), ctypes.byref(o)), "hankel_plan_ex")
 
     def __del__(self):
@@ -106,7 +106,8 @@ class Plan:
         _lib.check(self._lib.hankel_plan_blocks(self._h, None, 0, ctypes.byref(cnt)), "hankel_plan_blocks")
         arr = (_lib.Block * max(cnt.value, 1))()
         _lib.check(self._lib.hankel_plan_blocks(self._h, arr, cnt.value, ctypes.byref(cnt)), "hankel_plan_blocks")
-        return [(b.k0, b.k1, b.n0, b.n1, b.fft_len) for b in arr[:cnt.value]]
+        return [dict(k0=b.k0, k1=b.k1, n0=b.n0, n1=b.n1, F=b.fft_len, S=b.seg_len, nseg=b.nseg, mode=b.mode)
+                for b in arr[:cnt.value]]
 
     def entry(self, k, n):
         """(value, is_far) of the plan's representation of matrix entry (k, n), 1-based."""

@@ -10,6 +10,7 @@ HANKEL_OK = 0
 STATUS_NAMES = {0: "HANKEL_OK", 1: "HANKEL_EINVAL", 2: "HANKEL_ENOMEM", 3: "HANKEL_ECUDA",
                 4: "HANKEL_EUNSUPPORTED", 5: "HANKEL_ETIMEOUT"}
 FLAG_HOST_ONLY = 1
+FLAG_NO_SEGMENT = 2
 
 # Every function include/hankel.h declares.
 EXPORTED = [
@@ -50,7 +51,8 @@ class StageStat(ctypes.Structure):
 
 class Block(ctypes.Structure):
     _fields_ = [("k0", ctypes.c_int64), ("k1", ctypes.c_int64), ("n0", ctypes.c_int64), ("n1", ctypes.c_int64),
-                ("fft_len", ctypes.c_int64)]
+                ("fft_len", ctypes.c_int64), ("seg_len", ctypes.c_int64), ("nseg", ctypes.c_int64),
+                ("mode", ctypes.c_int)]
 
 
 def load():

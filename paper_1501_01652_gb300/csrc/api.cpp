@@ -151,6 +151,9 @@ int hankel_plan_blocks(hankel_plan_t p, hankel_block* out, int cap, int* count) 
     out[i].n0 = bl[i].n0;
     out[i].n1 = bl[i].n1;
     out[i].fft_len = bl[i].F;
+    out[i].seg_len = bl[i].S;
+    out[i].nseg = bl[i].nseg;
+    out[i].mode = bl[i].mode;
   }
   return HANKEL_OK;
 }

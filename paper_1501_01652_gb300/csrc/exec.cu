@@ -26,11 +26,14 @@ namespace {
 constexpr size_t kDefaultWorkspace = size_t(4) << 30;
 constexpr int64_t kNearPiece = 4096;  // near-field columns handled by one warp
 
+// Complex elements one stacked column occupies in a workspace buffer.
+size_t column_footprint(const Block& b) { return (size_t)b.F * (size_t)b.nseg; }
+
 struct DevBlock {
   Block b;
   double2* wU = nullptr;  // exp(i pi U_k^2 / (2E)), k = k0..k1
   double2* wV = nullptr;  // exp(i pi V_n^2 / (2E)), n = n0..n1
-  double2* H = nullptr;   // FFT_F of the chirp exp(-i pi (U-V)^2 / (2E)), times 1/F
+  double2* H = nullptr;   // per segment: FFT_F of the chirp exp(-i pi (U-V)^2 / (2E)), times 1/F
   int64_t cap = 0;        // columns per chunk
 };
 
@@ -54,6 +57,7 @@ struct DevicePlan {
   double2* bufA = nullptr;
   double2* bufB = nullptr;
   size_t ws_bytes = 0;
+  size_t ws_elems = 0;
   double* c_stage = nullptr;
   double* f_stage = nullptr;
   size_t bytes = 0;
@@ -110,13 +114,16 @@ struct StageScope {
   int stage;
   cudaStream_t st;
   cudaEvent_t a = nullptr;
-  StageScope(DevicePlan* d_, int stage_, cudaStream_t st_) : d(d_), stage(stage_), st(st_) {
-    if (d->timing) {
+  bool on;
+  StageScope(DevicePlan* d_, int stage_, cudaStream_t st_, bool record = true)
+      : d(d_), stage(stage_), st(st_), on(record) {
+    if (on && d->timing) {
       a = pool_event(d);
       if (a) cudaEventRecord(a, st);
     }
   }
   void done(int64_t launches, double flops, double entries) {
+    if (!on) return;
     d->acc[stage].launches += launches;
     d->acc[stage].flops += flops;
     d->acc[stage].entries += entries;
@@ -211,37 +218,44 @@ int dev_plan_create(hankel_plan_s* p) {
   launch_twiddles(d->tw, logFmax, 0);
   HK_LAUNCHED();
 
-  // Workspace: two ping-pong column buffers.
+  // Workspace: two ping-pong buffers, each holding a chunk of stacked columns of a block
+  // (nseg transforms of length F per stacked column for segmented blocks).
   size_t limit = hp.opt.workspace_limit ? hp.opt.workspace_limit : kDefaultWorkspace;
-  size_t need = 0;
+  size_t need = (size_t)1 << logFmax;
   for (const Block& b : hp.blocks) {
-    int64_t total = (int64_t)d->ncols * hp.opt.max_nrhs;
-    int64_t cap = (int64_t)(limit / (2 * sizeof(double2) * (size_t)b.F));
+    const size_t foot = column_footprint(b);
+    const int64_t total = (int64_t)d->ncols * hp.opt.max_nrhs;
+    int64_t cap = (int64_t)(limit / (2 * sizeof(double2) * foot));
     cap = std::max<int64_t>(1, std::min<int64_t>(cap, total));
-    cap = std::min<int64_t>(cap, 65535);
-    need = std::max(need, (size_t)cap * (size_t)b.F);
+    need = std::max(need, (size_t)cap * foot);
+    need = std::max(need, (size_t)b.nseg * (size_t)b.F);  // room for the segment spectra
   }
-  need = std::max<size_t>(need, (size_t)1 << logFmax);  // room for the chirp spectra FFTs
   HK_TRY(dalloc(d, &d->bufA, need));
   HK_TRY(dalloc(d, &d->bufB, need));
   d->ws_bytes = 2 * need * sizeof(double2);
+  d->ws_elems = need;
 
-  // Per-block chirp vectors and kernel spectrum.
+  // Per-block chirp vectors and the spectra of its convolution kernels (one per segment).
   for (const Block& b : hp.blocks) {
     DevBlock db;
     db.b = b;
-    db.cap = std::max<int64_t>(1, std::min<int64_t>((int64_t)(need / (size_t)b.F), (int64_t)d->ncols * hp.opt.max_nrhs));
-    db.cap = std::min<int64_t>(db.cap, 65535);
+    db.cap = std::max<int64_t>(1, std::min<int64_t>((int64_t)(need / column_footprint(b)),
+                                                    (int64_t)d->ncols * hp.opt.max_nrhs));
     HK_TRY(dalloc(d, &db.wU, b.R));
     HK_TRY(dalloc(d, &db.wV, b.C));
-    HK_TRY(dalloc(d, &db.H, b.F));
+    HK_TRY(dalloc(d, &db.H, (size_t)b.nseg * b.F));
     d->blocks.push_back(db);
     ChirpGeom g{hp.Ua, hp.Ub, hp.Va, hp.Vb, hp.E, b.k0, b.n0, b.R, b.C, b.F};
-    launch_chirps(g, db.wU, db.wV, d->bufA, 0);
+    launch_chirps(g, db.wU, db.wV, 0);
+    HK_LAUNCHED();
+    SegGeom sg{hp.Ua, hp.Ub, hp.Vb, hp.E, b.k0, b.n0, b.R, b.C, 0, 0, 1, b.F};
+    if (b.mode == kBlockRowSeg) { sg.Cc = b.S; sg.dn = b.S; sg.nseg = b.nseg; }
+    if (b.mode == kBlockColSeg) { sg.Rr = b.S; sg.dk = b.S; sg.nseg = b.nseg; }
+    launch_seg_hh(sg, d->bufA, 0);
     HK_LAUNCHED();
     double2* res = nullptr;
-    HK_TRY(run_fft(d->bufA, d->bufB, b.logF, 1, /*inverse=*/false, d->tw, d->logFmax, 0, &res));
-    launch_scale_copy(res, db.H, b.F, 1.0 / (double)b.F, 0);
+    HK_TRY(run_fft(d->bufA, d->bufB, b.logF, (int)b.nseg, /*inverse=*/false, d->tw, d->logFmax, 0, &res));
+    launch_scale_copy(res, db.H, b.nseg * b.F, 1.0 / (double)b.F, 0);
     HK_LAUNCHED();
   }
 
@@ -267,6 +281,68 @@ int dev_plan_destroy(hankel_plan_s* p) {
 size_t dev_plan_bytes(const hankel_plan_s* p) { return p->dev ? p->dev->bytes : 0; }
 size_t dev_workspace_bytes(const hankel_plan_s* p) { return p->dev ? p->dev->ws_bytes : 0; }
 
+namespace {
+
+// Far-field work of one block for nrhs vectors: chunks of `cap` stacked columns through
+// generation, forward FFTs, the product with the kernel spectra (summed over column segments
+// or replicated over row segments), inverse FFTs and the row accumulation into f.
+int run_block(DevicePlan* d, const DevBlock& db, const double* c, int64_t ldc, double* f, int64_t ldf, int nrhs,
+              double2* A, double2* B, int64_t cap, cudaStream_t st, bool record) {
+  const Block& b = db.b;
+  const int64_t total = (int64_t)d->ncols * nrhs;
+  const bool rowseg = b.mode == kBlockRowSeg, colseg = b.mode == kBlockColSeg;
+  for (int64_t c0 = 0; c0 < total; c0 += cap) {
+    const int nc = (int)std::min<int64_t>(cap, total - c0);
+    const int64_t nfwd = rowseg ? (int64_t)nc * b.nseg : nc;  // forward transforms
+    const int64_t ninv = colseg ? (int64_t)nc * b.nseg : nc;  // inverse transforms
+    {
+      StageScope sc(d, HANKEL_STAGE_GEN, st, record);
+      GenArgs ga{A, b.F, b.C, b.n0, rowseg ? b.S : b.C, rowseg ? b.nseg : 1, nc, c0, d->ncols, c, ldc,
+                 d->nodes, d->cols, db.wV};
+      launch_gen(ga, st);
+      HK_LAUNCHED();
+      sc.done(1, 0.0, 0.0);
+    }
+    double2* res = nullptr;
+    {
+      StageScope sc(d, HANKEL_STAGE_FFT, st, record);
+      int np = 0;
+      HK_TRY(run_fft(A, B, b.logF, (int)nfwd, false, d->tw, d->logFmax, st, &res, &np));
+      HK_LAUNCHED();
+      sc.done(np, 5.0 * (double)b.F * (double)b.logF * (double)nfwd, 0.0);
+    }
+    double2* other = (res == A) ? B : A;
+    double2* spec = res;
+    {
+      StageScope sc(d, HANKEL_STAGE_POINTWISE, st, record);
+      if (rowseg) { launch_seg_mac(res, db.H, other, b.F, b.nseg, nc, st); spec = other; }
+      else if (colseg) { launch_seg_expand(res, db.H, other, b.F, b.nseg, nc, st); spec = other; }
+      else launch_pointwise(res, db.H, b.F, nc, st);
+      HK_LAUNCHED();
+      sc.done(1, 0.0, 0.0);
+    }
+    double2* res2 = nullptr;
+    {
+      StageScope sc(d, HANKEL_STAGE_FFT, st, record);
+      int np = 0;
+      HK_TRY(run_fft(spec, spec == A ? B : A, b.logF, (int)ninv, true, d->tw, d->logFmax, st, &res2, &np));
+      HK_LAUNCHED();
+      sc.done(np, 5.0 * (double)b.F * (double)b.logF * (double)ninv, 0.0);
+    }
+    {
+      StageScope sc(d, HANKEL_STAGE_OUT, st, record);
+      OutArgs oa{res2, b.F, b.R, b.k0, (rowseg ? b.S : b.C) - 1, colseg ? b.S : b.R, colseg ? b.nseg : 1,
+                 nc, c0, d->ncols, f, ldf, d->nodes, d->cols, db.wU};
+      launch_out(oa, st);
+      HK_LAUNCHED();
+      sc.done(1, 0.0, 0.0);
+    }
+  }
+  return HANKEL_OK;
+}
+
+}  // namespace
+
 int dev_exec(hankel_plan_s* p, const double* c, int64_t ldc, double* f, int64_t ldf, int nrhs, void* stream) {
   const HostPlan& hp = p->hp;
   DevicePlan* d = p->dev;
@@ -283,53 +359,8 @@ int dev_exec(hankel_plan_s* p, const double* c, int64_t ldc, double* f, int64_t 
     HK_LAUNCHED();
     sc.done(d->nmrows > 0 ? 2 : 1, 0.0, (double)hp.near_count * nrhs);
   }
-
-  // Far field, block by block, columns in chunks.
-  const int64_t total = (int64_t)d->ncols * nrhs;
-  for (const DevBlock& db : d->blocks) {
-    const Block& b = db.b;
-    for (int64_t c0 = 0; c0 < total; c0 += db.cap) {
-      int nc = (int)std::min<int64_t>(db.cap, total - c0);
-      {
-        StageScope sc(d, HANKEL_STAGE_GEN, st);
-        GenArgs ga{d->bufA, b.F, b.C, b.n0, nc, c0, d->ncols, c, ldc, d->nodes, d->cols, db.wV};
-        launch_gen(ga, st);
-        HK_LAUNCHED();
-        sc.done(1, 0.0, 0.0);
-      }
-      const double fft_flops = 5.0 * (double)b.F * (double)b.logF * nc;
-      double2* res = nullptr;
-      {
-        StageScope sc(d, HANKEL_STAGE_FFT, st);
-        int np = 0;
-        HK_TRY(run_fft(d->bufA, d->bufB, b.logF, nc, false, d->tw, d->logFmax, st, &res, &np));
-        HK_LAUNCHED();
-        sc.done(np, fft_flops, 0.0);
-      }
-      {
-        StageScope sc(d, HANKEL_STAGE_POINTWISE, st);
-        launch_pointwise(res, db.H, b.F, nc, st);
-        HK_LAUNCHED();
-        sc.done(1, 0.0, 0.0);
-      }
-      double2* other = (res == d->bufA) ? d->bufB : d->bufA;
-      double2* res2 = nullptr;
-      {
-        StageScope sc(d, HANKEL_STAGE_FFT, st);
-        int np = 0;
-        HK_TRY(run_fft(res, other, b.logF, nc, true, d->tw, d->logFmax, st, &res2, &np));
-        HK_LAUNCHED();
-        sc.done(np, fft_flops, 0.0);
-      }
-      {
-        StageScope sc(d, HANKEL_STAGE_OUT, st);
-        OutArgs oa{res2, b.F, b.R, b.C, b.k0, nc, c0, d->ncols, f, ldf, d->nodes, d->cols, db.wU};
-        launch_out(oa, st);
-        HK_LAUNCHED();
-        sc.done(1, 0.0, 0.0);
-      }
-    }
-  }
+  // Far field, block by block.
+  for (const DevBlock& db : d->blocks) HK_TRY(run_block(d, db, c, ldc, f, ldf, nrhs, d->bufA, d->bufB, db.cap, st, true));
   if (cur >= 0 && cur != d->device) cudaSetDevice(cur);
   return HANKEL_OK;
 }
@@ -430,9 +461,9 @@ int dev_exec_static(hankel_plan_s* p, const double* c, double* f, void* stream) 
   const int64_t N = hp.opt.N;
   // Layout of the static array: [bufA | bufB | near partial sums (as doubles)].
   const size_t partial_elems = ((size_t)d->nslots + 1) / 2 + 1;
-  int64_t Fmax = 0;
-  for (const DevBlock& db : d->blocks) Fmax = std::max<int64_t>(Fmax, db.b.F);
-  if (2 * (size_t)Fmax + partial_elems > kStaticScratchElems) return HANKEL_EUNSUPPORTED;
+  size_t foot_max = 0;
+  for (const DevBlock& db : d->blocks) foot_max = std::max(foot_max, column_footprint(db.b));
+  if (2 * foot_max + partial_elems > kStaticScratchElems) return HANKEL_EUNSUPPORTED;
   const size_t per_buf = (kStaticScratchElems - partial_elems) / 2;
 
   int cur = -1;
@@ -452,28 +483,9 @@ int dev_exec_static(hankel_plan_s* p, const double* c, double* f, void* stream) 
   launch_near(d->items, d->nitems, d->mrows, d->nmrows, spartial, 1, c, N, f, N, d->nodes, d->jtab, hp.jt_n,
               hp.jt_deg, st);
   HK_LAUNCHED();
-  const int64_t total = d->ncols;
   for (const DevBlock& db : d->blocks) {
-    const Block& b = db.b;
-    const int64_t cap = std::max<int64_t>(1, std::min<int64_t>((int64_t)(per_buf / (size_t)b.F), 65535));
-    for (int64_t c0 = 0; c0 < total; c0 += cap) {
-      const int nc = (int)std::min<int64_t>(cap, total - c0);
-      GenArgs ga{sA, b.F, b.C, b.n0, nc, c0, d->ncols, c, N, d->nodes, d->cols, db.wV};
-      launch_gen(ga, st);
-      HK_LAUNCHED();
-      double2* res = nullptr;
-      HK_TRY(run_fft(sA, sB, b.logF, nc, false, d->tw, d->logFmax, st, &res));
-      HK_LAUNCHED();
-      launch_pointwise(res, db.H, b.F, nc, st);
-      HK_LAUNCHED();
-      double2* other = (res == sA) ? sB : sA;
-      double2* res2 = nullptr;
-      HK_TRY(run_fft(res, other, b.logF, nc, true, d->tw, d->logFmax, st, &res2));
-      HK_LAUNCHED();
-      OutArgs oa{res2, b.F, b.R, b.C, b.k0, nc, c0, d->ncols, f, N, d->nodes, d->cols, db.wU};
-      launch_out(oa, st);
-      HK_LAUNCHED();
-    }
+    const int64_t cap = std::max<int64_t>(1, (int64_t)(per_buf / column_footprint(db.b)));
+    HK_TRY(run_block(d, db, c, N, f, N, 1, sA, sB, cap, st, false));
   }
   if (cur >= 0 && cur != d->device) cudaSetDevice(cur);
   return HANKEL_OK;

@@ -27,32 +27,36 @@ __device__ __forceinline__ double ipow(double x, int e) {
 }
 
 __global__ void __launch_bounds__(256) k_gen(GenArgs a) {
-  const int cc = blockIdx.y;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= a.F) return;
-  double2* A = a.A + (int64_t)cc * a.F;
-  if (t >= a.C) {
-    A[t] = make_double2(0.0, 0.0);
-    return;
+  const int64_t ncolumns = (int64_t)a.nc * a.nsegc;
+  for (int64_t y = blockIdx.y; y < ncolumns; y += gridDim.y) {
+    double2* A = a.A + y * a.F;
+    const int64_t cc = y / a.nsegc, sg = y - cc * a.nsegc;
+    const int64_t np = sg * a.S + t;  // column offset within the block
+    if (t >= a.S || np >= a.C) {
+      A[t] = make_double2(0.0, 0.0);
+      continue;
+    }
+    const int64_t g = a.c0 + cc;
+    const int rhs = (int)(g / a.ncols);
+    const int l = (int)(g - (int64_t)rhs * a.ncols);
+    const DevColSpec& cs = a.cols[l];
+    const int64_t i = a.n0 - 1 + np;
+    const double bt = a.nodes.betan[i];
+    double pr = cs.G[cs.nterm - 1].x, pim = cs.G[cs.nterm - 1].y;
+    for (int u = cs.nterm - 2; u >= 0; --u) {
+      pr = fma(pr, bt, cs.G[u].x);
+      pim = fma(pim, bt, cs.G[u].y);
+    }
+    const int d = cs.delta;
+    double pw = a.nodes.rs_omt[i] * ipow(d >= 0 ? a.nodes.omt[i] : a.nodes.inv_omt[i], d >= 0 ? d : -d);
+    if (cs.u1) pw *= ipow(a.nodes.colpow[i], cs.u1);
+    const double cv = a.c[(int64_t)rhs * a.ldc + i] * pw;
+    const double xr = pr * cv, xi = pim * cv;
+    const double2 w = a.wV[np];
+    A[t] = make_double2(fma(xr, w.x, -xi * w.y), fma(xr, w.y, xi * w.x));
   }
-  const int64_t g = a.c0 + cc;
-  const int rhs = (int)(g / a.ncols);
-  const int l = (int)(g - (int64_t)rhs * a.ncols);
-  const DevColSpec& cs = a.cols[l];
-  const int64_t i = a.n0 - 1 + t;
-  const double bt = a.nodes.betan[i];
-  double pr = cs.G[cs.nterm - 1].x, pim = cs.G[cs.nterm - 1].y;
-  for (int u = cs.nterm - 2; u >= 0; --u) {
-    pr = fma(pr, bt, cs.G[u].x);
-    pim = fma(pim, bt, cs.G[u].y);
-  }
-  const int d = cs.delta;
-  double pw = a.nodes.rs_omt[i] * ipow(d >= 0 ? a.nodes.omt[i] : a.nodes.inv_omt[i], d >= 0 ? d : -d);
-  if (cs.u1) pw *= ipow(a.nodes.colpow[i], cs.u1);
-  const double cv = a.c[(int64_t)rhs * a.ldc + i] * pw;
-  const double xr = pr * cv, xi = pim * cv;
-  const double2 w = a.wV[t];
-  A[t] = make_double2(fma(xr, w.x, -xi * w.y), fma(xr, w.y, xi * w.x));
 }
 
 __global__ void __launch_bounds__(256) k_out(OutArgs a) {
@@ -62,7 +66,8 @@ __global__ void __launch_bounds__(256) k_out(OutArgs a) {
   const double rv = a.nodes.rowvar[i], irv = a.nodes.inv_rowvar[i], rs = a.nodes.rs_rowvar[i];
   const double rp = a.nodes.rowpert[i];
   const double2 wu = a.wU[kp];
-  const double2* Y = a.Y + kp + a.C - 1;
+  const int64_t sg = kp / a.Sr;
+  const double2* Y = a.Y + sg * a.F + (kp - sg * a.Sr) + a.off;
   double ar = 0.0, ai = 0.0;
   int cur = (int)(a.c0 / a.ncols);
   for (int cc = 0; cc < a.nc; ++cc) {
@@ -77,18 +82,63 @@ __global__ void __launch_bounds__(256) k_out(OutArgs a) {
     const int d = cs.delta;
     double wgt = rs * ipow(d >= 0 ? rv : irv, d >= 0 ? d : -d);
     if (cs.u1) wgt *= ipow(rp, cs.u1);
-    const double2 y = Y[(int64_t)cc * a.F];
+    const double2 y = Y[(int64_t)cc * a.nsegr * a.F];
     ar = fma(wgt, y.x, ar);
     ai = fma(wgt, y.y, ai);
   }
   a.f[(int64_t)cur * a.ldf + i] += fma(wu.x, ar, -wu.y * ai);
 }
 
+__global__ void k_seg_mac(const double2* __restrict__ in, const double2* __restrict__ H, double2* __restrict__ out,
+                          int64_t F, int64_t nseg, int64_t total) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t cc = e / F, t = e - cc * F;
+    const double2* x = in + cc * nseg * F + t;
+    double ar = 0.0, ai = 0.0;
+    for (int64_t s = 0; s < nseg; ++s) {
+      const double2 v = x[s * F];
+      const double2 h = __ldg(&H[s * F + t]);
+      ar = fma(v.x, h.x, fma(-v.y, h.y, ar));
+      ai = fma(v.x, h.y, fma(v.y, h.x, ai));
+    }
+    out[e] = make_double2(ar, ai);
+  }
+}
+
+__global__ void k_seg_expand(const double2* __restrict__ in, const double2* __restrict__ H, double2* __restrict__ out,
+                             int64_t F, int64_t nseg, int64_t total) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t t = e % F, q = e / F;
+    const int64_t cc = q / nseg, s = q - cc * nseg;
+    const double2 v = in[cc * F + t];
+    const double2 h = __ldg(&H[s * F + t]);
+    out[e] = make_double2(fma(v.x, h.x, -v.y * h.y), fma(v.x, h.y, v.y * h.x));
+  }
+}
+
+unsigned grid1d(int64_t n) {
+  int64_t g = (n + 255) / 256;
+  return (unsigned)std::min<int64_t>(std::max<int64_t>(g, 1), int64_t(152) * 32);
+}
+
 }  // namespace
 
 void launch_gen(const GenArgs& a, cudaStream_t st) {
-  dim3 grid((unsigned)((a.F + 255) / 256), (unsigned)a.nc);
+  const int64_t ny = std::min<int64_t>((int64_t)a.nc * a.nsegc, 65535);
+  dim3 grid((unsigned)((a.F + 255) / 256), (unsigned)ny);
   k_gen<<<grid, 256, 0, st>>>(a);
+}
+
+void launch_seg_mac(const double2* in, const double2* H, double2* out, int64_t F, int64_t nseg, int nc,
+                    cudaStream_t st) {
+  const int64_t total = F * nc;
+  k_seg_mac<<<grid1d(total), 256, 0, st>>>(in, H, out, F, nseg, total);
+}
+
+void launch_seg_expand(const double2* in, const double2* H, double2* out, int64_t F, int64_t nseg, int nc,
+                       cudaStream_t st) {
+  const int64_t total = F * nseg * nc;
+  k_seg_expand<<<grid1d(total), 256, 0, st>>>(in, H, out, F, nseg, total);
 }
 
 void launch_out(const OutArgs& a, cudaStream_t st) {

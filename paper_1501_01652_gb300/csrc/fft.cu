@@ -190,17 +190,25 @@ __device__ __forceinline__ double2 chirp_phase(int64_t v, int64_t E, double sign
   return make_double2(c, sign * s);
 }
 
-__global__ void k_chirps(ChirpGeom g, double2* wU, double2* wV, double2* hh) {
-  const int64_t L = g.R + g.C - 1;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < g.F; t += (int64_t)gridDim.x * blockDim.x) {
+__global__ void k_chirps(ChirpGeom g, double2* wU, double2* wV) {
+  const int64_t n = g.R > g.C ? g.R : g.C;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
     if (t < g.R) wU[t] = chirp_phase(g.Ua * (g.k0 + t) + g.Ub, g.E, 1.0);
     if (t < g.C) wV[t] = chirp_phase(g.Va * (g.n0 + t) + g.Vb, g.E, 1.0);
+  }
+}
+
+__global__ void k_seg_hh(SegGeom g, double2* hh) {
+  const int64_t total = g.nseg * g.F;
+  const int64_t L = g.Rr + g.Cc - 1;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t y = e / g.F, t = e - y * g.F;
     if (t < L) {
-      // U_k - V_n with k - n = t - (C-1) + (k0 - n0)
-      const int64_t duv = g.Ua * (t - (g.C - 1) + g.k0 - g.n0) + (g.Ub - g.Vb);
-      hh[t] = chirp_phase(duv, g.E, -1.0);
+      // U_k - V_n with k - n = t - (Cc-1) + (k0 + y dk) - (n0 + y dn)
+      const int64_t duv = g.Ua * (t - (g.Cc - 1) + (g.k0 + y * g.dk) - (g.n0 + y * g.dn)) + (g.Ub - g.Vb);
+      hh[e] = chirp_phase(duv, g.E, -1.0);
     } else {
-      hh[t] = make_double2(0.0, 0.0);
+      hh[e] = make_double2(0.0, 0.0);
     }
   }
 }
@@ -226,8 +234,12 @@ void launch_twiddles(double2* tw, int logF, cudaStream_t st) {
   k_twiddles<<<grid_for(int64_t(1) << logF, 256), 256, 0, st>>>(tw, logF);
 }
 
-void launch_chirps(const ChirpGeom& g, double2* wU, double2* wV, double2* hh, cudaStream_t st) {
-  k_chirps<<<grid_for(g.F, 256), 256, 0, st>>>(g, wU, wV, hh);
+void launch_chirps(const ChirpGeom& g, double2* wU, double2* wV, cudaStream_t st) {
+  k_chirps<<<grid_for(g.R > g.C ? g.R : g.C, 256), 256, 0, st>>>(g, wU, wV);
+}
+
+void launch_seg_hh(const SegGeom& g, double2* hh, cudaStream_t st) {
+  k_seg_hh<<<grid_for(g.nseg * g.F, 256), 256, 0, st>>>(g, hh);
 }
 
 void launch_scale_copy(const double2* src, double2* dst, int64_t n, double scale, cudaStream_t st) {

@@ -45,8 +45,10 @@ struct ChirpGeom {
 };
 
 struct GenArgs {
-  double2* A;         // [nc][F] output columns
+  double2* A;         // [nc * nsegc][F] output columns
   int64_t F, C, n0;   // transform length, block columns, first column (1-based)
+  int64_t S;          // columns per segment (C when the columns are not segmented)
+  int64_t nsegc;      // column segments per stacked column (1 when not segmented)
   int nc;             // columns in this chunk
   int64_t c0;         // global index of the first column (rhs * ncols + l)
   int ncols;          // stacked columns per right-hand side
@@ -58,8 +60,11 @@ struct GenArgs {
 };
 
 struct OutArgs {
-  const double2* Y;   // [nc][F] inverse-transformed columns
-  int64_t F, R, C, k0;
+  const double2* Y;   // [nc * nsegr][F] inverse-transformed columns
+  int64_t F, R, k0;
+  int64_t off;        // index of output row k0 in a transformed column (convolution offset)
+  int64_t Sr;         // rows per row segment (R when the rows are not segmented)
+  int64_t nsegr;      // row segments per stacked column
   int nc;
   int64_t c0;
   int ncols;
@@ -70,8 +75,22 @@ struct OutArgs {
   const double2* wU;  // row chirp of the block
 };
 
+// Convolution kernels of the segments of a block: for y < nseg and t < F,
+// hh[y*F + t] = exp(-i pi D^2 / (2E)), D = Ua (t - (Cc-1) + (k0 + y dk) - (n0 + y dn)) + Ub - Vb
+// for t < Rr + Cc - 1, and 0 beyond.
+struct SegGeom {
+  int64_t Ua, Ub, Vb, E, k0, n0, Rr, Cc, dk, dn, nseg, F;
+};
+
 void launch_twiddles(double2* tw, int logF, cudaStream_t st);
-void launch_chirps(const ChirpGeom& g, double2* wU, double2* wV, double2* hh, cudaStream_t st);
+void launch_chirps(const ChirpGeom& g, double2* wU, double2* wV, cudaStream_t st);
+void launch_seg_hh(const SegGeom& g, double2* hh, cudaStream_t st);
+// out[cc][t] = sum_s in[cc*nseg + s][t] * H[s][t]   (overlap-add of column segments)
+void launch_seg_mac(const double2* in, const double2* H, double2* out, int64_t F, int64_t nseg, int nc,
+                    cudaStream_t st);
+// out[cc*nseg + s][t] = in[cc][t] * H[s][t]         (overlap-save of row segments)
+void launch_seg_expand(const double2* in, const double2* H, double2* out, int64_t F, int64_t nseg, int nc,
+                       cudaStream_t st);
 // Out-of-place multi-column FFT of length 2^logF over ncols contiguous columns,
 // ping-ponging between a (input) and b; *result receives the buffer holding the output.
 int run_fft(double2* a, double2* b, int logF, int ncols, bool inverse, const double2* tw, int logFmax,

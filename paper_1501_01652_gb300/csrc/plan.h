@@ -18,12 +18,22 @@ constexpr int kMaxU = 16;
 constexpr int kJTabDeg = 15;
 constexpr int kJTabDegF32 = 8;
 
-// A far-field block: rows k0..k1, columns n0..n1 (1-based, inclusive), one
-// chirp-z transform of length F = 2^logF >= R + C - 1.
+// How a block's chirp-z convolution is carried out.
+enum BlockMode {
+  kBlockFull = 0,    // one transform of length F >= R + C - 1
+  kBlockRowSeg = 1,  // few rows: columns cut into nseg segments of S, overlap-add, F >= R + S - 1
+  kBlockColSeg = 2   // few columns: rows cut into nseg segments of S, overlap-save, F >= S + C - 1
+};
+
+// A far-field block: rows k0..k1, columns n0..n1 (1-based, inclusive), and its
+// chirp-z convolution in transforms of length F = 2^logF.
 struct Block {
   int64_t k0, k1, n0, n1;
   int64_t R, C, F;
   int logF;
+  int mode;       // BlockMode
+  int64_t S;      // segment length (C for full blocks)
+  int64_t nseg;   // number of segments (1 for full blocks)
 };
 
 // One stacked column of a block: the row function rowpert(k)^u1 rowvar(k)^(delta-1/2)

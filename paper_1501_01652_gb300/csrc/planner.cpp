@@ -388,6 +388,34 @@ void build_nodes(HostPlan& hp) {
   }
 }
 
+// A thin block (few rows or few columns) does not need one transform as long as
+// R + C: cutting the long side into segments of S gives short convolutions of
+// length F >= thin + S - 1 whose results add up exactly (overlap-add over column
+// segments when rows are few, overlap-save over row segments when columns are
+// few). Pick the length with the fewest estimated FP64 operations per column:
+// about 3.6 per point and radix-2 stage of each FFT plus 4 per point and segment
+// for the spectrum products.
+void choose_segments(Block& b) {
+  const int64_t thin = std::min(b.R, b.C), wide = std::max(b.R, b.C);
+  const double kStage = 3.6, kMac = 4.0;
+  double best = 2.0 * b.F * b.logF * kStage + kMac * b.F;
+  for (int lf = 6; lf < b.logF; ++lf) {
+    const int64_t Fs = int64_t(1) << lf;
+    if (Fs < 2 * thin) continue;
+    const int64_t S = Fs - thin + 1;
+    const int64_t nseg = (wide + S - 1) / S;
+    const double cost = (double)(nseg + 1) * Fs * lf * kStage + kMac * (double)nseg * Fs;
+    if (cost < best) {
+      best = cost;
+      b.mode = (b.R <= b.C) ? kBlockRowSeg : kBlockColSeg;
+      b.F = Fs;
+      b.logF = lf;
+      b.S = S;
+      b.nseg = nseg;
+    }
+  }
+}
+
 void build_partition(HostPlan& hp) {
   const int64_t N = hp.opt.N;
   const double sq = std::sqrt(hp.D);
@@ -409,6 +437,10 @@ void build_partition(HostPlan& hp) {
     while ((int64_t(1) << lf) < b.R + b.C - 1) ++lf;
     b.logF = lf;
     b.F = int64_t(1) << lf;
+    b.mode = kBlockFull;
+    b.S = b.C;
+    b.nseg = 1;
+    if (!(hp.opt.flags & HANKEL_FLAG_NO_SEGMENT)) choose_segments(b);
     raw.push_back(b);
   };
   // Eq. (19): Q1 J Q1 and, for p = 1..P, Q_{2p+1} J Q_{2p} and Q_{2p} J Q_{2p+1}, with the

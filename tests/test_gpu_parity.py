@@ -97,6 +97,19 @@ def test_workload_sizes_sampled_rows(task, nu, N, eps, kind):
     _check(task, nu, N, eps, c, rows=rows)
 
 
+@pytest.mark.parametrize("segment", [True, False])
+@pytest.mark.parametrize("task,nu,N,eps", [
+    ("dht", 0, 2 ** 17, 1e-15), ("fourier_bessel", 0, 2 ** 17, 1e-8), ("schlomilch", 1, 2 ** 17, 1e-15),
+])
+def test_segmented_and_full_blocks(task, nu, N, eps, segment):
+    # thin far blocks run as segmented convolutions by default; both forms must meet the bar
+    c = coefficients("normal", N, 2, 5500)
+    rows = sample_rows(N, 48, 13)
+    _check(task, nu, N, eps, c, rows=rows, segment=segment)
+    plan = hk.Plan(task, nu, N, eps, segment=segment, host_only=True)
+    assert any(b["mode"] != 0 for b in plan.blocks()) == segment
+
+
 @pytest.mark.parametrize("eps", [1e-15, 1e-8])
 def test_dht_2p20_sampled_rows(eps):
     # the benchmarked workload: DHT-0, N = 2^20, standard normal coefficients

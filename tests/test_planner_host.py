@@ -37,6 +37,14 @@ def test_status_strings():
         assert lib.hankel_status_string(code)
 
 
+def test_thin_blocks_are_segmented_at_workload_size():
+    p = hk.Plan("dht", 0, 2 ** 20, 1e-15, host_only=True)
+    modes = sorted(b["mode"] for b in p.blocks())
+    assert modes == [0, 1, 1, 1, 2, 2, 2]
+    q = hk.Plan("dht", 0, 2 ** 20, 1e-15, host_only=True, segment=False)
+    assert all(b["mode"] == 0 and b["nseg"] == 1 for b in q.blocks())
+
+
 def test_node_offsets_against_oracle_and_lemma():
     n = 20000
     b = hk.j0_zero_offsets(n)
@@ -54,9 +62,17 @@ def test_partition_invariants(case):
     blocks = p.blocks()
     assert len(blocks) <= 1 + 2 * info["P"]
     covered = np.zeros(N + 1, dtype=np.int64)
-    for (k0, k1, n0, n1, F) in blocks:
+    for b in blocks:
+        k0, k1, n0, n1, F = b["k0"], b["k1"], b["n0"], b["n1"], b["F"]
+        R, C = k1 - k0 + 1, n1 - n0 + 1
         assert 1 <= k0 <= k1 <= N and 1 <= n0 <= n1 <= N
-        assert F >= (k1 - k0 + 1) + (n1 - n0 + 1) - 1 and F & (F - 1) == 0
+        assert F & (F - 1) == 0
+        if b["mode"] == 0:
+            assert b["nseg"] == 1 and F >= R + C - 1
+        elif b["mode"] == 1:  # column segments: every segment's convolution fits
+            assert F >= R + b["S"] - 1 and b["nseg"] * b["S"] >= C > (b["nseg"] - 1) * b["S"]
+        else:
+            assert F >= b["S"] + C - 1 and b["nseg"] * b["S"] >= R > (b["nseg"] - 1) * b["S"]
         assert k0 > info["direct_rows"] and n0 > info["direct_cols"]
         # every entry of the block has z~ = r~_k omega~_n >= s (corner is the minimum)
         v, far = p.entry(k0, n0)
@@ -87,8 +103,8 @@ def test_far_blocks_satisfy_criterion(case):
     task, nu, N, eps, grid = case
     p = hk.Plan(task, nu, N, eps, grid=grid, host_only=True)
     s = p.info["s"]
-    for (k0, k1, n0, n1, F) in p.blocks():
-        assert _z_tilde(task, nu, N, grid, k0, n0) >= s * (1 - 1e-12)
+    for b in p.blocks():
+        assert _z_tilde(task, nu, N, grid, b["k0"], b["n0"]) >= s * (1 - 1e-12)
 
 
 @pytest.mark.parametrize("case", CASES, ids=lambda c: "%s-nu%d-N%d-%g-%s" % c)
