@@ -83,6 +83,8 @@ enum hankel_status {
 /* Plan flags (hankel_options.flags). */
 #define HANKEL_FLAG_HOST_ONLY 1u   /* build host tables only; no CUDA call is made */
 #define HANKEL_FLAG_NO_SEGMENT 2u  /* one full-length chirp-z transform per block (no segmenting of thin blocks) */
+#define HANKEL_FLAG_NO_TABLES 4u   /* compute column/row factors per use instead of keeping tables of
+                                      ncols * N * 24 bytes on the device (tables are skipped anyway above 16 GiB) */
 
 /* Options for hankel_plan_ex(). Fill with hankel_options_default() first. */
 typedef struct {

@@ -11,6 +11,7 @@ STATUS_NAMES = {0: "HANKEL_OK", 1: "HANKEL_EINVAL", 2: "HANKEL_ENOMEM", 3: "HANK
                 4: "HANKEL_EUNSUPPORTED", 5: "HANKEL_ETIMEOUT"}
 FLAG_HOST_ONLY = 1
 FLAG_NO_SEGMENT = 2
+FLAG_NO_TABLES = 4
 
 # Every function include/hankel.h declares.
 EXPORTED = [

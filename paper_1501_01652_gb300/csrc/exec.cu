@@ -24,6 +24,8 @@ namespace hk {
 namespace {
 
 constexpr size_t kDefaultWorkspace = size_t(4) << 30;
+// Largest size of the column/row factor tables a plan builds (beyond it, factors are computed per use).
+constexpr size_t kTableLimit = size_t(16) << 30;
 constexpr int64_t kNearPiece = 4096;  // near-field columns handled by one warp
 
 // Complex elements one stacked column occupies in a workspace buffer.
@@ -41,6 +43,7 @@ struct DevBlock {
 
 struct DevicePlan {
   int device = 0;
+  int64_t hpN = 0;
   NodeTables nodes{};
   DevColSpec* cols = nullptr;
   int ncols = 0;
@@ -60,6 +63,8 @@ struct DevicePlan {
   size_t ws_elems = 0;
   double* c_stage = nullptr;
   double* f_stage = nullptr;
+  double2* T = nullptr;  // column factor table (or nullptr)
+  double* W = nullptr;   // row factor table (or nullptr)
   size_t bytes = 0;
   std::vector<void*> allocs;
   // stage statistics (hankel_plan_set_timing / hankel_plan_stage_stats)
@@ -155,6 +160,7 @@ int dev_plan_create(hankel_plan_s* p) {
   p->dev = d;
   if (cudaGetDevice(&d->device) != cudaSuccess) return HANKEL_ECUDA;
   const int64_t N = hp.opt.N;
+  d->hpN = N;
 
   // Node tables and their derived powers.
   std::vector<double> tmp(N);
@@ -186,6 +192,16 @@ int dev_plan_create(hankel_plan_s* p) {
   d->ncols = (int)cs.size();
   HK_TRY(upload(d, &d->cols, cs.data(), cs.size()));
   HK_TRY(upload(d, &d->jtab, hp.jtab.data(), hp.jtab.size()));
+
+  // Factor tables: the column and row functions of every stacked column at every index.
+  const size_t tab_bytes = (size_t)d->ncols * (size_t)N * (sizeof(double2) + sizeof(double));
+  if (!(hp.opt.flags & HANKEL_FLAG_NO_TABLES) && !hp.blocks.empty() && tab_bytes <= kTableLimit) {
+    HK_TRY(dalloc(d, &d->T, (size_t)d->ncols * N));
+    HK_TRY(dalloc(d, &d->W, (size_t)d->ncols * N));
+    TabArgs ta{d->T, d->W, N, d->ncols, d->nodes, d->cols, hp.Va, hp.Vb, hp.E};
+    launch_build_tables(ta, 0);
+    HK_LAUNCHED();
+  }
 
   // Near-field work list: each row's prefix 1..nend(k) cut into pieces of <= kNearPiece columns.
   std::vector<NearItem> items;
@@ -298,7 +314,7 @@ int run_block(DevicePlan* d, const DevBlock& db, const double* c, int64_t ldc, d
     {
       StageScope sc(d, HANKEL_STAGE_GEN, st, record);
       GenArgs ga{A, b.F, b.C, b.n0, rowseg ? b.S : b.C, rowseg ? b.nseg : 1, nc, c0, d->ncols, c, ldc,
-                 d->nodes, d->cols, db.wV};
+                 d->nodes, d->cols, db.wV, d->T, d->hpN};
       launch_gen(ga, st);
       HK_LAUNCHED();
       sc.done(1, 0.0, 0.0);
@@ -332,7 +348,7 @@ int run_block(DevicePlan* d, const DevBlock& db, const double* c, int64_t ldc, d
     {
       StageScope sc(d, HANKEL_STAGE_OUT, st, record);
       OutArgs oa{res2, b.F, b.R, b.k0, (rowseg ? b.S : b.C) - 1, colseg ? b.S : b.R, colseg ? b.nseg : 1,
-                 nc, c0, d->ncols, f, ldf, d->nodes, d->cols, db.wU};
+                 nc, c0, d->ncols, f, ldf, d->nodes, d->cols, db.wU, d->W, d->hpN};
       launch_out(oa, st);
       HK_LAUNCHED();
       sc.done(1, 0.0, 0.0);

@@ -41,8 +41,14 @@ __global__ void __launch_bounds__(256) k_gen(GenArgs a) {
     const int64_t g = a.c0 + cc;
     const int rhs = (int)(g / a.ncols);
     const int l = (int)(g - (int64_t)rhs * a.ncols);
-    const DevColSpec& cs = a.cols[l];
     const int64_t i = a.n0 - 1 + np;
+    if (a.T) {
+      const double cv = a.c[(int64_t)rhs * a.ldc + i];
+      const double2 x = a.T[(int64_t)l * a.N + i];
+      A[t] = make_double2(cv * x.x, cv * x.y);
+      continue;
+    }
+    const DevColSpec& cs = a.cols[l];
     const double bt = a.nodes.betan[i];
     double pr = cs.G[cs.nterm - 1].x, pim = cs.G[cs.nterm - 1].y;
     for (int u = cs.nterm - 2; u >= 0; --u) {
@@ -63,8 +69,13 @@ __global__ void __launch_bounds__(256) k_out(OutArgs a) {
   const int64_t kp = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (kp >= a.R) return;
   const int64_t i = a.k0 - 1 + kp;
-  const double rv = a.nodes.rowvar[i], irv = a.nodes.inv_rowvar[i], rs = a.nodes.rs_rowvar[i];
-  const double rp = a.nodes.rowpert[i];
+  double rv = 0.0, irv = 0.0, rs = 0.0, rp = 0.0;
+  if (!a.W) {
+    rv = a.nodes.rowvar[i];
+    irv = a.nodes.inv_rowvar[i];
+    rs = a.nodes.rs_rowvar[i];
+    rp = a.nodes.rowpert[i];
+  }
   const double2 wu = a.wU[kp];
   const int64_t sg = kp / a.Sr;
   const double2* Y = a.Y + sg * a.F + (kp - sg * a.Sr) + a.off;
@@ -78,10 +89,16 @@ __global__ void __launch_bounds__(256) k_out(OutArgs a) {
       ar = ai = 0.0;
       cur = rhs;
     }
-    const DevColSpec& cs = a.cols[(int)(g - (int64_t)rhs * a.ncols)];
-    const int d = cs.delta;
-    double wgt = rs * ipow(d >= 0 ? rv : irv, d >= 0 ? d : -d);
-    if (cs.u1) wgt *= ipow(rp, cs.u1);
+    const int l = (int)(g - (int64_t)rhs * a.ncols);
+    double wgt;
+    if (a.W) {
+      wgt = a.W[(int64_t)l * a.N + i];
+    } else {
+      const DevColSpec& cs = a.cols[l];
+      const int d = cs.delta;
+      wgt = rs * ipow(d >= 0 ? rv : irv, d >= 0 ? d : -d);
+      if (cs.u1) wgt *= ipow(rp, cs.u1);
+    }
     const double2 y = Y[(int64_t)cc * a.nsegr * a.F];
     ar = fma(wgt, y.x, ar);
     ai = fma(wgt, y.y, ai);
@@ -116,6 +133,32 @@ __global__ void k_seg_expand(const double2* __restrict__ in, const double2* __re
   }
 }
 
+__global__ void __launch_bounds__(256) k_build_tables(TabArgs a) {
+  const int64_t total = (int64_t)a.ncols * a.N;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int l = (int)(e / a.N);
+    const int64_t i = e - (int64_t)l * a.N;
+    const DevColSpec& cs = a.cols[l];
+    const int d = cs.delta, ad = d >= 0 ? d : -d;
+    const double bt = a.nodes.betan[i];
+    double pr = cs.G[cs.nterm - 1].x, pim = cs.G[cs.nterm - 1].y;
+    for (int u = cs.nterm - 2; u >= 0; --u) {
+      pr = fma(pr, bt, cs.G[u].x);
+      pim = fma(pim, bt, cs.G[u].y);
+    }
+    double pw = a.nodes.rs_omt[i] * ipow(d >= 0 ? a.nodes.omt[i] : a.nodes.inv_omt[i], ad);
+    double rw = a.nodes.rs_rowvar[i] * ipow(d >= 0 ? a.nodes.rowvar[i] : a.nodes.inv_rowvar[i], ad);
+    if (cs.u1) {
+      pw *= ipow(a.nodes.colpow[i], cs.u1);
+      rw *= ipow(a.nodes.rowpert[i], cs.u1);
+    }
+    const double2 w = chirp_phase(a.Va * (i + 1) + a.Vb, a.E, 1.0);
+    const double xr = pr * pw, xi = pim * pw;
+    a.T[e] = make_double2(fma(xr, w.x, -xi * w.y), fma(xr, w.y, xi * w.x));
+    a.W[e] = rw;
+  }
+}
+
 unsigned grid1d(int64_t n) {
   int64_t g = (n + 255) / 256;
   return (unsigned)std::min<int64_t>(std::max<int64_t>(g, 1), int64_t(152) * 32);
@@ -139,6 +182,10 @@ void launch_seg_expand(const double2* in, const double2* H, double2* out, int64_
                        cudaStream_t st) {
   const int64_t total = F * nseg * nc;
   k_seg_expand<<<grid1d(total), 256, 0, st>>>(in, H, out, F, nseg, total);
+}
+
+void launch_build_tables(const TabArgs& a, cudaStream_t st) {
+  k_build_tables<<<grid1d((int64_t)a.ncols * a.N), 256, 0, st>>>(a);
 }
 
 void launch_out(const OutArgs& a, cudaStream_t st) {

@@ -34,70 +34,134 @@ __device__ __forceinline__ double2 twiddle(const double2* __restrict__ tw, int64
   return t;
 }
 
-// R-point DFTs of kTile sequences held as a[e * kTile + i] (element e, sequence i).
-// Returns the buffer (a or b) that holds the result in natural order.
-template <int LOGR, bool INV>
-__device__ double2* smem_dft(double2* a, double2* b, const double2* __restrict__ tw, int logFmax) {
-  constexpr int R = 1 << LOGR;
-  int logn = LOGR, logs = 0;
-  while (logn >= 2) {
-    const int n4 = 1 << (logn - 2);
-    const int s = 1 << logs;
-    const int tshift = logFmax - logn;
-    for (int idx = threadIdx.x; idx < kTile * (R / 4); idx += blockDim.x) {
-      const int i = idx & (kTile - 1);
-      const int bf = idx / kTile;
-      const int pp = bf >> logs, qq = bf & (s - 1);
-      const double2 a0 = a[(qq + s * pp) * kTile + i];
-      const double2 a1 = a[(qq + s * (pp + n4)) * kTile + i];
-      const double2 a2 = a[(qq + s * (pp + 2 * n4)) * kTile + i];
-      const double2 a3 = a[(qq + s * (pp + 3 * n4)) * kTile + i];
-      const double2 t0 = cadd(a0, a2), t1 = csub(a0, a2), t2 = cadd(a1, a3), t3 = csub(a1, a3);
-      // -i t3 (forward) or +i t3 (inverse)
-      const double2 jt3 = INV ? make_double2(-t3.y, t3.x) : make_double2(t3.y, -t3.x);
-      double2 b0 = cadd(t0, t2), b1 = cadd(t1, jt3), b2 = csub(t0, t2), b3 = csub(t1, jt3);
-      if (pp != 0) {
-        b1 = cmul(b1, twiddle<INV>(tw, (int64_t)(pp) << tshift));
-        b2 = cmul(b2, twiddle<INV>(tw, (int64_t)(2 * pp) << tshift));
-        b3 = cmul(b3, twiddle<INV>(tw, (int64_t)(3 * pp) << tshift));
-      }
-      const int o = qq + s * 4 * pp;
-      b[(o)*kTile + i] = b0;
-      b[(o + s) * kTile + i] = b1;
-      b[(o + 2 * s) * kTile + i] = b2;
-      b[(o + 3 * s) * kTile + i] = b3;
-    }
-    __syncthreads();
-    double2* t = a;
-    a = b;
-    b = t;
-    logn -= 2;
-    logs += 2;
+// Radix-4 decimation-in-time butterfly on x_j = a_j w_j (w_0 = 1), written so that every
+// twiddle product is folded into an FMA: u0 = a0 + w2 a2, u1 = 2 a0 - u0, t = w1 a1,
+// v0 = t + w3 a3, v1 = 2t - v0; then y0 = u0 + v0, y2 = u0 - v0, y1 = u1 -/+ i v1,
+// y3 = u1 +/- i v1 (forward/inverse). 24 FP64 instructions for 4 points and 2 stages.
+template <bool INV>
+__device__ __forceinline__ void bfly4(double2& a0, double2& a1, double2& a2, double2& a3, double2 w1, double2 w2,
+                                      double2 w3) {
+  double2 u0, u1, t, v0, v1;
+  u0.x = fma(w2.x, a2.x, fma(-w2.y, a2.y, a0.x));
+  u0.y = fma(w2.x, a2.y, fma(w2.y, a2.x, a0.y));
+  u1.x = fma(2.0, a0.x, -u0.x);
+  u1.y = fma(2.0, a0.y, -u0.y);
+  t.x = fma(w1.x, a1.x, -w1.y * a1.y);
+  t.y = fma(w1.x, a1.y, w1.y * a1.x);
+  v0.x = fma(w3.x, a3.x, fma(-w3.y, a3.y, t.x));
+  v0.y = fma(w3.x, a3.y, fma(w3.y, a3.x, t.y));
+  v1.x = fma(2.0, t.x, -v0.x);
+  v1.y = fma(2.0, t.y, -v0.y);
+  a0 = make_double2(u0.x + v0.x, u0.y + v0.y);
+  a2 = make_double2(u0.x - v0.x, u0.y - v0.y);
+  if (INV) {
+    a1 = make_double2(u1.x - v1.y, u1.y + v1.x);
+    a3 = make_double2(u1.x + v1.y, u1.y - v1.x);
+  } else {
+    a1 = make_double2(u1.x + v1.y, u1.y - v1.x);
+    a3 = make_double2(u1.x - v1.y, u1.y + v1.x);
   }
-  if (logn == 1) {
-    const int s = 1 << logs;  // = R/2
+}
+
+// Radix-2 decimation-in-time butterfly on (a0, a1 w): y0 = a0 + w a1, y1 = 2 a0 - y0.
+__device__ __forceinline__ void bfly2(double2& a0, double2& a1, double2 w) {
+  double2 y0;
+  y0.x = fma(w.x, a1.x, fma(-w.y, a1.y, a0.x));
+  y0.y = fma(w.x, a1.y, fma(w.y, a1.x, a0.y));
+  a1 = make_double2(fma(2.0, a0.x, -y0.x), fma(2.0, a0.y, -y0.y));
+  a0 = y0;
+}
+
+// R-point DFTs of kTile sequences held as a[e * kTile + i] (element e, sequence i), each
+// input e first multiplied by W_F^{pt[i] * e} (the pass twiddle; pt[i] = p*s of sequence i).
+// Decimation-in-time Stockham sub-steps of radix 2 (first, when log2 R is odd) and 4. The
+// pass twiddle of input e = q' + s1*j splits into W^{pt q'} W^{pt s1 j}: the second factor is
+// applied in the first sub-step and the first is deferred into the twiddle index of the
+// second sub-step, so it costs no extra multiplication. Returns the buffer with the result.
+template <int LOGR, bool INV>
+__device__ double2* smem_dft(double2* a, double2* b, const double2* __restrict__ tw, int logFmax, int logF,
+                             const int64_t* pt) {
+  constexpr int R = 1 << LOGR;
+  const int fsh = logFmax - logF;
+  const int64_t fmask = (int64_t(1) << logFmax) - 1;
+  int logn = 0;     // sub-length already transformed (log2)
+  int step = 0;     // sub-step counter
+  int logs1 = 0;    // log2 of the first sub-step's stride
+  if (LOGR & 1) {
+    // radix-2 sub-step: n = 2, s = R/2, m = 1
+    const int logs = LOGR - 1, s = 1 << logs;
+    logs1 = logs;
     for (int idx = threadIdx.x; idx < kTile * (R / 2); idx += blockDim.x) {
-      const int i = idx & (kTile - 1);
-      const int qq = idx / kTile;
-      const double2 a0 = a[qq * kTile + i];
-      const double2 a1 = a[(qq + s) * kTile + i];
-      b[qq * kTile + i] = cadd(a0, a1);
-      b[(qq + s) * kTile + i] = csub(a0, a1);
+      const int i = idx & (kTile - 1), q = idx / kTile;
+      double2 a0 = a[q * kTile + i], a1 = a[(q + s) * kTile + i];
+      const double2 w = twiddle<INV>(tw, ((pt[i] << logs) << fsh) & fmask);
+      bfly2(a0, a1, w);
+      b[q * kTile + i] = a0;
+      b[(q + s) * kTile + i] = a1;
     }
     __syncthreads();
-    double2* t = a;
-    a = b;
-    b = t;
+    double2* t = a; a = b; b = t;
+    logn = 1;
+    ++step;
+  }
+  while (logn < LOGR) {
+    // radix-4 sub-step: sub-length n' = 4 * 2^logn, stride s = R / n', m = 2^logn
+    const int lognn = logn + 2, logs = LOGR - lognn, s = 1 << logs, m = 1 << logn;
+    for (int idx = threadIdx.x; idx < kTile * (R / 4); idx += blockDim.x) {
+      const int i = idx & (kTile - 1), bf = idx / kTile;
+      const int pp = bf >> logs, qq = bf & (s - 1);
+      const int e0 = qq + s * 4 * pp;  // inputs e0 + s*j, outputs qq + s*(pp + r m)
+      double2 a0 = a[(e0)*kTile + i], a1 = a[(e0 + s) * kTile + i];
+      double2 a2 = a[(e0 + 2 * s) * kTile + i], a3 = a[(e0 + 3 * s) * kTile + i];
+      double2 w1, w2, w3;
+      if (step == 0) {
+        // pass twiddle W_F^{pt * s * j}; the factor W_F^{pt * qq} is deferred
+        const int64_t base = (pt[i] << logs) << fsh;
+        w1 = twiddle<INV>(tw, base & fmask);
+        w2 = twiddle<INV>(tw, (2 * base) & fmask);
+        w3 = twiddle<INV>(tw, (3 * base) & fmask);
+      } else {
+        // W_{n'}^{pp j} times, in the second sub-step, the deferred W_F^{pt (e mod s1)}
+        const int64_t inner = (int64_t)pp << (logFmax - lognn);
+        int64_t d0 = 0, d1 = 0, d2 = 0, d3 = 0;
+        if (step == 1) {
+          const int64_t s1m = (int64_t(1) << logs1) - 1;
+          d0 = ((pt[i] * (e0 & s1m)) << fsh);
+          d1 = ((pt[i] * ((e0 + s) & s1m)) << fsh);
+          d2 = ((pt[i] * ((e0 + 2 * s) & s1m)) << fsh);
+          d3 = ((pt[i] * ((e0 + 3 * s) & s1m)) << fsh);
+          if (d0) a0 = cmul(a0, twiddle<INV>(tw, d0 & fmask));
+        }
+        w1 = twiddle<INV>(tw, (inner + d1) & fmask);
+        w2 = twiddle<INV>(tw, (2 * inner + d2) & fmask);
+        w3 = twiddle<INV>(tw, (3 * inner + d3) & fmask);
+      }
+      bfly4<INV>(a0, a1, a2, a3, w1, w2, w3);
+      b[(qq + s * pp) * kTile + i] = a0;
+      b[(qq + s * (pp + m)) * kTile + i] = a1;
+      b[(qq + s * (pp + 2 * m)) * kTile + i] = a2;
+      b[(qq + s * (pp + 3 * m)) * kTile + i] = a3;
+    }
+    __syncthreads();
+    double2* t = a; a = b; b = t;
+    if (step == 0) logs1 = logs;
+    logn = lognn;
+    ++step;
   }
   return a;
 }
 
+// One decimation-in-time Stockham pass of sub-length n = F/s with radix R = 2^LOGR: for
+// pairs (p < n/R, q < s), z_j = y[q + s(R p + j)] W_n^{p j}, Z = DFT_R(z), x[q + s(p + r n/R)] = Z_r.
+// The store index is pi + r F/R with pi = p s + q, so a tile of kTile consecutive pairs writes
+// kTile consecutive elements per r; the loads are contiguous runs of kTile or s*R elements.
 template <int LOGR, bool INV>
 __global__ void __launch_bounds__(kFftThreads) k_fft_pass(const double2* __restrict__ src, double2* __restrict__ dst,
                                                           int logF, int logS, const double2* __restrict__ tw,
                                                           int logFmax) {
   constexpr int R = 1 << LOGR;
   extern __shared__ double2 sm[];
+  __shared__ int64_t pt[kTile];
   double2* v = sm;
   double2* w = sm + R * kTile;
   const int64_t F = int64_t(1) << logF;
@@ -107,35 +171,29 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_pass(const double2* __restr
   const int64_t pi0 = G0 - col * FR;
   const double2* x = src + col * F;
   double2* y = dst + col * F;
-  for (int idx = threadIdx.x; idx < R * kTile; idx += blockDim.x) {
-    const int i = idx & (kTile - 1), j = idx / kTile;
-    v[j * kTile + i] = x[pi0 + i + (int64_t)j * FR];
-  }
-  __syncthreads();
-  const double2* res = smem_dft<LOGR, INV>(v, w, tw, logFmax);
   const int64_t s = int64_t(1) << logS;
-  const int tshift = logFmax - logF;
+  if (threadIdx.x < kTile) pt[threadIdx.x] = ((pi0 + threadIdx.x) >> logS) << logS;  // p * s
   if (s >= kTile) {
     const int64_t p = pi0 >> logS, q0 = pi0 & (s - 1);
+    const int64_t base = q0 + s * R * p;
     for (int idx = threadIdx.x; idx < R * kTile; idx += blockDim.x) {
-      const int i = idx & (kTile - 1), r = idx / kTile;
-      double2 val = res[r * kTile + i];
-      const int64_t e = ((p * r) << logS) & (F - 1);
-      if (e) val = cmul(val, twiddle<INV>(tw, e << tshift));
-      y[q0 + i + s * (p * R + r)] = val;
+      const int i = idx & (kTile - 1), j = idx / kTile;
+      v[j * kTile + i] = x[base + i + s * j];
     }
   } else {
-    const int64_t p0 = pi0 >> logS;
-    const int64_t base = (p0 << logS) << LOGR;  // s R p0
+    const int64_t base = pi0 << LOGR;  // s R p0 with pi0 = s p0
     for (int idx = threadIdx.x; idx < R * kTile; idx += blockDim.x) {
       const int pl = idx >> (logS + LOGR);
       const int rem = idx & ((int)(s << LOGR) - 1);
-      const int r = rem >> logS, q = rem & ((int)s - 1);
-      double2 val = res[r * kTile + ((pl << logS) + q)];
-      const int64_t e = (((p0 + pl) * r) << logS) & (F - 1);
-      if (e) val = cmul(val, twiddle<INV>(tw, e << tshift));
-      y[base + idx] = val;
+      const int j = rem >> logS, q = rem & ((int)s - 1);
+      v[j * kTile + ((pl << logS) + q)] = x[base + idx];
     }
+  }
+  __syncthreads();
+  const double2* res = smem_dft<LOGR, INV>(v, w, tw, logFmax, logF, pt);
+  for (int idx = threadIdx.x; idx < R * kTile; idx += blockDim.x) {
+    const int i = idx & (kTile - 1), r = idx / kTile;
+    y[pi0 + i + (int64_t)r * FR] = res[r * kTile + i];
   }
 }
 
@@ -176,18 +234,6 @@ __global__ void k_twiddles(double2* tw, int logF) {
     sincospi(-2.0 * (double)t / (double)F, &s, &c);
     tw[t] = make_double2(c, s);
   }
-}
-
-// exp(i pi q / (2E)) for q = v^2 mod 4E (the period of the phase in v^2).
-__device__ __forceinline__ double2 chirp_phase(int64_t v, int64_t E, double sign) {
-  const int64_t m = 4 * E;
-  int64_t a = v % m;
-  if (a < 0) a += m;
-  // a^2 < 16 E^2 fits in 64 bits for E < 2^30
-  const int64_t q = (int64_t)(((unsigned long long)a * (unsigned long long)a) % (unsigned long long)m);
-  double s, c;
-  sincospi((double)q / (double)(2 * E), &s, &c);
-  return make_double2(c, sign * s);
 }
 
 __global__ void k_chirps(ChirpGeom g, double2* wU, double2* wV) {
@@ -259,12 +305,13 @@ int run_fft(double2* a, double2* b, int logF, int ncols, bool inverse, const dou
   const int base = logF / np, extra = logF % np;
   double2* src = a;
   double2* dst = b;
-  int logS = 0;
+  int done = 0;  // log2 of the sub-length transformed so far
   for (int i = 0; i < np; ++i) {
     const int lr = base + (i < extra ? 1 : 0);
+    done += lr;
+    const int logS = logF - done;
     if (inverse) launch_pass_r<true>(lr, src, dst, logF, logS, ncols, tw, logFmax, st);
     else launch_pass_r<false>(lr, src, dst, logF, logS, ncols, tw, logFmax, st);
-    logS += lr;
     std::swap(src, dst);
   }
   *result = src;

@@ -7,6 +7,19 @@
 
 namespace hk {
 
+// exp(i pi q / (2E)) for q = v^2 mod 4E (the period of the phase in v^2): the chirp
+// factors of the exact phase pi U V / E, reduced in integers before sincospi.
+__device__ __forceinline__ double2 chirp_phase(int64_t v, int64_t E, double sign) {
+  const int64_t m = 4 * E;
+  int64_t a = v % m;
+  if (a < 0) a += m;
+  // a^2 < 16 E^2 fits in 64 bits for E < 2^30
+  const int64_t q = (int64_t)(((unsigned long long)a * (unsigned long long)a) % (unsigned long long)m);
+  double s, c;
+  sincospi((double)q / (double)(2 * E), &s, &c);
+  return make_double2(c, sign * s);
+}
+
 // Per-index node tables on the device (0-based index i = k-1 or n-1).
 struct NodeTables {
   double* r_true;     // r_k
@@ -57,6 +70,8 @@ struct GenArgs {
   NodeTables nodes;
   const DevColSpec* cols;
   const double2* wV;  // column chirp of the block
+  const double2* T;   // optional [ncols][N] column factors times the column chirp (nullptr: computed here)
+  int64_t N;
 };
 
 struct OutArgs {
@@ -73,7 +88,23 @@ struct OutArgs {
   NodeTables nodes;
   const DevColSpec* cols;
   const double2* wU;  // row chirp of the block
+  const double* W;    // optional [ncols][N] row factors (nullptr: computed here)
+  int64_t N;
 };
+
+// Plan-time tables of the factors that do not depend on c:
+// T[l][n-1] = colpow^u1 omt^(delta-1/2) poly_l(beta) exp(i pi V_n^2/(2E)),
+// W[l][k-1] = rowpert^u1 rowvar^(delta-1/2).
+struct TabArgs {
+  double2* T;
+  double* W;
+  int64_t N;
+  int ncols;
+  NodeTables nodes;
+  const DevColSpec* cols;
+  int64_t Va, Vb, E;
+};
+void launch_build_tables(const TabArgs& a, cudaStream_t st);
 
 // Convolution kernels of the segments of a block: for y < nseg and t < F,
 // hh[y*F + t] = exp(-i pi D^2 / (2E)), D = Ua (t - (Cc-1) + (k0 + y dk) - (n0 + y dn)) + Ub - Vb

@@ -110,6 +110,15 @@ def test_segmented_and_full_blocks(task, nu, N, eps, segment):
     assert any(b["mode"] != 0 for b in plan.blocks()) == segment
 
 
+@pytest.mark.parametrize("tables", [True, False])
+def test_factor_tables_on_and_off(tables):
+    # column/row factors from plan-time device tables or computed per use give the same bar
+    N = 6000
+    c = coefficients("normal", N, 2, 5600)
+    _check("dht", 0, N, 1e-15, c, tables=tables)
+    _check("fourier_bessel", 0, N, 1e-8, c, tables=tables)
+
+
 @pytest.mark.parametrize("eps", [1e-15, 1e-8])
 def test_dht_2p20_sampled_rows(eps):
     # the benchmarked workload: DHT-0, N = 2^20, standard normal coefficients
