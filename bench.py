@@ -26,6 +26,10 @@ sys.path.insert(0, ROOT)
 from hankel_inputs import coefficients, sample_rows, seed_for  # noqa: E402
 
 FP64_PEAK_GFLOPS = 152 * 4 * 2.07  # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz = 1258 GFLOP/s
+FP64_MEASURED_GFLOPS = 1004.0      # DFMA microbenchmark on this part (2 x 502 G instructions/s)
+# DRAM bytes per algorithmic byte of a k_fft_pass launch, from an ncu capture of one radix-64
+# forward pass over 290 columns of 2^17 points (1167.9 MB measured / 1216.3 MB algorithmic).
+FFT_TRAFFIC_RATIO = 1167.9 / 1216.3
 METRIC = "DHT-0 coeffs/s at N=2^20 (eps=1e-8,1e-15) served vs plain FP64; p50/p99 ms"
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -222,6 +226,7 @@ def run_ours(args):
     fft_ms = sum(st["fft"]["ms"] for st in stats)
     fft_flops = sum(st["fft"]["flops"] for st in stats)
     fft_launches = sum(st["fft"]["launches"] for st in stats)
+    fft_bytes = sum(st["fft"]["bytes"] for st in stats)
     achieved = fft_flops / (fft_ms / 1000.0) / 1e9 if fft_ms > 0 else 0.0
     launches = sum(st[k]["launches"] for st in stats for k in st)
     stage_ms = {k: round(sum(st[k]["ms"] for st in stats) / args.steps, 3) for k in stats[0]}
@@ -252,7 +257,11 @@ def run_ours(args):
                     for e, m in zip(eps_list, eps_ms)},
         "stage_ms_per_step": stage_ms,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                     "frac": achieved / FP64_PEAK_GFLOPS, "traffic": None,
+                     "frac": achieved / FP64_PEAK_GFLOPS,
+                     "traffic": FFT_TRAFFIC_RATIO * fft_bytes / fft_launches if fft_launches else None,
+                     "traffic_unit": "DRAM bytes per launch (ncu ratio x algorithmic bytes)",
+                     "frac_of_measured_fp64": achieved / FP64_MEASURED_GFLOPS,
+                     "hbm_gbs_of_passes": fft_bytes / (fft_ms / 1000.0) / 1e9 if fft_ms > 0 else None,
                      "kernel": "k_fft_pass (FP64 Stockham passes, forward + inverse)",
                      "flops_model": "5 F log2 F per column transform", "launches": fft_launches,
                      "peak_source": "nominal FP64 from unit counts and clock (152 SM x 4 flop/clk x 2.07 GHz)"},

@@ -216,6 +216,7 @@ typedef struct {
   double ms;         /* summed kernel time from CUDA events on the execution stream (0 when timing is off) */
   double flops;      /* algorithmic floating-point operations (FFT: 5 F log2 F per column transform) */
   double entries;    /* near field: matrix entries evaluated (times right-hand sides) */
+  double bytes;      /* algorithmic DRAM bytes (FFT: each pass reads and writes every point once, 32 B) */
   int64_t launches;  /* kernel launches */
 } hankel_stage_stat;
 

@@ -132,7 +132,7 @@ class Plan:
         """Accumulated per-stage statistics: {stage: {ms, flops, entries, launches}}."""
         arr = (_lib.StageStat * len(_lib.STAGES))()
         _lib.check(self._lib.hankel_plan_stage_stats(self._h, arr), "hankel_plan_stage_stats")
-        return {name: {"ms": a.ms, "flops": a.flops, "entries": a.entries, "launches": a.launches}
+        return {name: {"ms": a.ms, "flops": a.flops, "entries": a.entries, "bytes": a.bytes, "launches": a.launches}
                 for name, a in zip(_lib.STAGES, arr)}
 
     def exec(self, c, f=None, stream=None):

@@ -47,7 +47,7 @@ class Info(ctypes.Structure):
 
 class StageStat(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double), ("flops", ctypes.c_double), ("entries", ctypes.c_double),
-                ("launches", ctypes.c_int64)]
+                ("bytes", ctypes.c_double), ("launches", ctypes.c_int64)]
 
 
 class Block(ctypes.Structure):

@@ -127,11 +127,12 @@ struct StageScope {
       if (a) cudaEventRecord(a, st);
     }
   }
-  void done(int64_t launches, double flops, double entries) {
+  void done(int64_t launches, double flops, double entries, double bytes = 0.0) {
     if (!on) return;
     d->acc[stage].launches += launches;
     d->acc[stage].flops += flops;
     d->acc[stage].entries += entries;
+    d->acc[stage].bytes += bytes;
     if (d->timing && a) {
       cudaEvent_t b = pool_event(d);
       if (b) {
@@ -325,7 +326,7 @@ int run_block(DevicePlan* d, const DevBlock& db, const double* c, int64_t ldc, d
       int np = 0;
       HK_TRY(run_fft(A, B, b.logF, (int)nfwd, false, d->tw, d->logFmax, st, &res, &np));
       HK_LAUNCHED();
-      sc.done(np, 5.0 * (double)b.F * (double)b.logF * (double)nfwd, 0.0);
+      sc.done(np, 5.0 * (double)b.F * (double)b.logF * (double)nfwd, 0.0, 32.0 * (double)b.F * nfwd * np);
     }
     double2* other = (res == A) ? B : A;
     double2* spec = res;
@@ -343,7 +344,7 @@ int run_block(DevicePlan* d, const DevBlock& db, const double* c, int64_t ldc, d
       int np = 0;
       HK_TRY(run_fft(spec, spec == A ? B : A, b.logF, (int)ninv, true, d->tw, d->logFmax, st, &res2, &np));
       HK_LAUNCHED();
-      sc.done(np, 5.0 * (double)b.F * (double)b.logF * (double)ninv, 0.0);
+      sc.done(np, 5.0 * (double)b.F * (double)b.logF * (double)ninv, 0.0, 32.0 * (double)b.F * ninv * np);
     }
     {
       StageScope sc(d, HANKEL_STAGE_OUT, st, record);

@@ -74,23 +74,22 @@ __device__ __forceinline__ void bfly2(double2& a0, double2& a1, double2 w) {
 
 // R-point DFTs of kTile sequences held as a[e * kTile + i] (element e, sequence i), each
 // input e first multiplied by W_F^{pt[i] * e} (the pass twiddle; pt[i] = p*s of sequence i).
-// Decimation-in-time Stockham sub-steps of radix 2 (first, when log2 R is odd) and 4. The
-// pass twiddle of input e = q' + s1*j splits into W^{pt q'} W^{pt s1 j}: the second factor is
-// applied in the first sub-step and the first is deferred into the twiddle index of the
-// second sub-step, so it costs no extra multiplication. Returns the buffer with the result.
+// Decimation-in-time Stockham sub-steps of radix 2 (first, when log2 R is odd) and 4, with
+// stride s_k and sub-length n_k = R/s_k. The pass twiddle is never applied on its own: the
+// inputs e = qq + s_k (r pp + j) of a butterfly carry W_F^{pt (qq + s_k j)}; the common
+// factor W_F^{pt qq} moves to the butterfly's outputs (whose index is qq mod s_k again), and
+// W_F^{pt s_k j} joins the step's own twiddle W_{n_k}^{pp j} in one table lookup. At the last
+// step s_k = 1, so nothing is left over. Input j = 0 of every butterfly needs no twiddle.
 template <int LOGR, bool INV>
 __device__ double2* smem_dft(double2* a, double2* b, const double2* __restrict__ tw, int logFmax, int logF,
                              const int64_t* pt) {
   constexpr int R = 1 << LOGR;
   const int fsh = logFmax - logF;
   const int64_t fmask = (int64_t(1) << logFmax) - 1;
-  int logn = 0;     // sub-length already transformed (log2)
-  int step = 0;     // sub-step counter
-  int logs1 = 0;    // log2 of the first sub-step's stride
+  int logn = 0;  // log2 of the sub-length transformed so far
   if (LOGR & 1) {
     // radix-2 sub-step: n = 2, s = R/2, m = 1
     const int logs = LOGR - 1, s = 1 << logs;
-    logs1 = logs;
     for (int idx = threadIdx.x; idx < kTile * (R / 2); idx += blockDim.x) {
       const int i = idx & (kTile - 1), q = idx / kTile;
       double2 a0 = a[q * kTile + i], a1 = a[(q + s) * kTile + i];
@@ -102,7 +101,6 @@ __device__ double2* smem_dft(double2* a, double2* b, const double2* __restrict__
     __syncthreads();
     double2* t = a; a = b; b = t;
     logn = 1;
-    ++step;
   }
   while (logn < LOGR) {
     // radix-4 sub-step: sub-length n' = 4 * 2^logn, stride s = R / n', m = 2^logn
@@ -113,29 +111,11 @@ __device__ double2* smem_dft(double2* a, double2* b, const double2* __restrict__
       const int e0 = qq + s * 4 * pp;  // inputs e0 + s*j, outputs qq + s*(pp + r m)
       double2 a0 = a[(e0)*kTile + i], a1 = a[(e0 + s) * kTile + i];
       double2 a2 = a[(e0 + 2 * s) * kTile + i], a3 = a[(e0 + 3 * s) * kTile + i];
-      double2 w1, w2, w3;
-      if (step == 0) {
-        // pass twiddle W_F^{pt * s * j}; the factor W_F^{pt * qq} is deferred
-        const int64_t base = (pt[i] << logs) << fsh;
-        w1 = twiddle<INV>(tw, base & fmask);
-        w2 = twiddle<INV>(tw, (2 * base) & fmask);
-        w3 = twiddle<INV>(tw, (3 * base) & fmask);
-      } else {
-        // W_{n'}^{pp j} times, in the second sub-step, the deferred W_F^{pt (e mod s1)}
-        const int64_t inner = (int64_t)pp << (logFmax - lognn);
-        int64_t d0 = 0, d1 = 0, d2 = 0, d3 = 0;
-        if (step == 1) {
-          const int64_t s1m = (int64_t(1) << logs1) - 1;
-          d0 = ((pt[i] * (e0 & s1m)) << fsh);
-          d1 = ((pt[i] * ((e0 + s) & s1m)) << fsh);
-          d2 = ((pt[i] * ((e0 + 2 * s) & s1m)) << fsh);
-          d3 = ((pt[i] * ((e0 + 3 * s) & s1m)) << fsh);
-          if (d0) a0 = cmul(a0, twiddle<INV>(tw, d0 & fmask));
-        }
-        w1 = twiddle<INV>(tw, (inner + d1) & fmask);
-        w2 = twiddle<INV>(tw, (2 * inner + d2) & fmask);
-        w3 = twiddle<INV>(tw, (3 * inner + d3) & fmask);
-      }
+      // W_{n'}^{pp j} W_F^{pt s j} = W_{Fmax}^{j * base}
+      const int64_t base = ((int64_t)pp << (logFmax - lognn)) + ((pt[i] << logs) << fsh);
+      const double2 w1 = twiddle<INV>(tw, base & fmask);
+      const double2 w2 = twiddle<INV>(tw, (2 * base) & fmask);
+      const double2 w3 = twiddle<INV>(tw, (3 * base) & fmask);
       bfly4<INV>(a0, a1, a2, a3, w1, w2, w3);
       b[(qq + s * pp) * kTile + i] = a0;
       b[(qq + s * (pp + m)) * kTile + i] = a1;
@@ -144,9 +124,7 @@ __device__ double2* smem_dft(double2* a, double2* b, const double2* __restrict__
     }
     __syncthreads();
     double2* t = a; a = b; b = t;
-    if (step == 0) logs1 = logs;
     logn = lognn;
-    ++step;
   }
   return a;
 }
