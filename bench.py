@@ -26,6 +26,7 @@ sys.path.insert(0, ROOT)
 from hankel_inputs import coefficients, sample_rows, seed_for  # noqa: E402
 
 FP64_PEAK_GFLOPS = 152 * 4 * 2.07  # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz = 1258 GFLOP/s
+HBM_FALLBACK_GBS = 6800.0          # used only when MEASURED_PEAKS.json is absent
 FP64_MEASURED_GFLOPS = 1004.0      # DFMA microbenchmark on this part (2 x 502 G instructions/s)
 # DRAM bytes per algorithmic byte of a k_fft_pass launch, from an ncu capture of one radix-64
 # forward pass over 290 columns of 2^17 points (1167.9 MB measured / 1216.3 MB algorithmic).
@@ -105,6 +106,14 @@ class ClockSampler:
                     reasons.add(name)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, KeyError, ValueError):
+        return HBM_FALLBACK_GBS, "fallback"
 
 
 def cpu_baseline(N, rows_count, seed):
@@ -243,28 +252,40 @@ def run_ours(args):
     e2e_s = time.perf_counter() - t0
     e2e_value = world * coeffs_per_step * e2e_steps / e2e_s
 
+    fp32 = all(p.info["precision"] == 2 for p in plans)
+    pass_gbs = fft_bytes / (fft_ms / 1000.0) / 1e9 if fft_ms > 0 else None
+    if fp32:
+        # FP32 stages are memory-bound: report the FFT passes against HBM bandwidth
+        peak, src = hbm_peak()
+        roofline = {"bound": "hbm", "achieved": pass_gbs, "peak": peak, "unit": "GB/s",
+                    "frac": (pass_gbs or 0.0) / peak, "traffic": None, "peak_source": src,
+                    "kernel": "k_fft_pass (FP32 Stockham passes, forward + inverse)",
+                    "bytes_model": "each pass reads and writes every point once (16 B per complex float)",
+                    "launches": fft_launches}
+    else:
+        roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                    "frac": achieved / FP64_PEAK_GFLOPS,
+                    "traffic": FFT_TRAFFIC_RATIO * fft_bytes / fft_launches if fft_launches else None,
+                    "traffic_unit": "DRAM bytes per launch (ncu ratio x algorithmic bytes)",
+                    "frac_of_measured_fp64": achieved / FP64_MEASURED_GFLOPS, "hbm_gbs_of_passes": pass_gbs,
+                    "kernel": "k_fft_pass (FP64 Stockham passes, forward + inverse)",
+                    "flops_model": "5 F log2 F per column transform", "launches": fft_launches,
+                    "peak_source": "nominal FP64 from unit counts and clock (152 SM x 4 flop/clk x 2.07 GHz)"}
     if rank != 0:
         return
     line = {
         "metric": METRIC, "value": value, "unit": "coeffs/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if fp32 else "f64", "data": "synthetic",
         "config": {"workload": "dht0_N%d_eps%s_nrhs%d_plain" % (N, "+".join(args.eps.split(",")), nrhs),
-                   "N": N, "eps": eps_list, "nrhs": nrhs, "form": "plain per-request FP64",
+                   "N": N, "eps": eps_list, "nrhs": nrhs,
+                   "form": "plain per-request " + ("FP32 stages (eps >= 1e-5)" if fp32 else "FP64"),
                    "l2": "flushed between timed steps (256 MB write)", "coefficients": "N(0,1) seeded"},
         "per_eps": {str(e): {"ms": statistics.mean(m), "coeffs_per_s": N * nrhs / (statistics.mean(m) / 1000.0),
                              "p50_ms": statistics.median(m), "p99_ms": max(m)}
                     for e, m in zip(eps_list, eps_ms)},
         "stage_ms_per_step": stage_ms,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                     "frac": achieved / FP64_PEAK_GFLOPS,
-                     "traffic": FFT_TRAFFIC_RATIO * fft_bytes / fft_launches if fft_launches else None,
-                     "traffic_unit": "DRAM bytes per launch (ncu ratio x algorithmic bytes)",
-                     "frac_of_measured_fp64": achieved / FP64_MEASURED_GFLOPS,
-                     "hbm_gbs_of_passes": fft_bytes / (fft_ms / 1000.0) / 1e9 if fft_ms > 0 else None,
-                     "kernel": "k_fft_pass (FP64 Stockham passes, forward + inverse)",
-                     "flops_model": "5 F log2 F per column transform", "launches": fft_launches,
-                     "peak_source": "nominal FP64 from unit counts and clock (152 SM x 4 flop/clk x 2.07 GHz)"},
+        "roofline": roofline,
         "e2e": {"value": e2e_value, "unit": "coeffs/s", "h2d_bytes_per_step": len(plans) * N * nrhs * 8,
                 "d2h_bytes_per_step": len(plans) * N * nrhs * 8, "steps": e2e_steps},
         "gpu_launches": launches,

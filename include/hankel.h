@@ -177,9 +177,10 @@ int hankel_exec_batched(hankel_plan_t p, const double* c, int64_t ldc, double* f
  *    reads is written earlier in the same call, so no clearing is needed. Calls that overlap
  *    on the GPU (other streams, other plans) race on the array: order them on one stream.
  *  - Returns HANKEL_EUNSUPPORTED when the plan's largest transform needs more than the array
- *    holds (two columns of F complex doubles plus the near-field partial sums; in practice
- *    N up to about 2^20 for the DHT), HANKEL_EINVAL on NULL arguments or a host-only plan,
- *    HANKEL_ECUDA if a launch or the address lookup fails. */
+ *    holds (two columns of F complex values of the plan's precision plus the near-field
+ *    partial sums; in practice N up to about 2^20 for an FP64 DHT, twice that for FP32 plans),
+ *    HANKEL_EINVAL on NULL arguments or a host-only plan, HANKEL_ECUDA if a launch or the
+ *    address lookup fails. */
 int hankel_exec_static(hankel_plan_t p, const double* c, double* f, void* stream);
 
 /* End-to-end form with HOST arrays (same layout as hankel_exec_batched): copies c to the

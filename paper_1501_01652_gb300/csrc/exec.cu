@@ -35,8 +35,10 @@ struct DevBlock {
   Block b;
   double2* wU = nullptr;  // exp(i pi U_k^2 / (2E)), k = k0..k1
   double2* wV = nullptr;  // exp(i pi V_n^2 / (2E)), n = n0..n1
-  double2* H = nullptr;   // per segment: FFT_F of the chirp exp(-i pi (U-V)^2 / (2E)), times 1/F
-  int64_t cap = 0;        // columns per chunk
+  void* H = nullptr;      // per segment: FFT_F of the chirp exp(-i pi (U-V)^2 / (2E)), times 1/F (plan precision)
+  double* scale = nullptr;   // FP32 plans: per stacked column, power of two keeping generated values near 1
+  double* iscale = nullptr;  // its inverse, applied to the row factors
+  int64_t cap = 0;           // columns per chunk
 };
 
 }  // namespace
@@ -48,17 +50,22 @@ struct DevicePlan {
   DevColSpec* cols = nullptr;
   int ncols = 0;
   double* jtab = nullptr;
+  bool fp32 = false;
+  float* rf = nullptr;     // FP32 plans: r_k, omega_n and the J table in single precision
+  float* omf = nullptr;
+  float* jtabf = nullptr;
   NearItem* items = nullptr;
   int64_t nitems = 0;
   NearRow* mrows = nullptr;
   int64_t nmrows = 0;
-  double* partial = nullptr;
+  void* partial = nullptr;  // near-field partial sums (plan precision)
   int64_t nslots = 0;
   std::vector<DevBlock> blocks;
-  double2* tw = nullptr;
+  double2* tw = nullptr;   // W_{Fmax}^t in FP64 (plan-time spectra of every plan)
+  float2* twf = nullptr;   // the same table rounded to FP32 (FP32 plans)
   int logFmax = 6;
-  double2* bufA = nullptr;
-  double2* bufB = nullptr;
+  void* bufA = nullptr;    // workspace, elements of the plan precision
+  void* bufB = nullptr;
   size_t ws_bytes = 0;
   size_t ws_elems = 0;
   double* c_stage = nullptr;
@@ -193,6 +200,17 @@ int dev_plan_create(hankel_plan_s* p) {
   d->ncols = (int)cs.size();
   HK_TRY(upload(d, &d->cols, cs.data(), cs.size()));
   HK_TRY(upload(d, &d->jtab, hp.jtab.data(), hp.jtab.size()));
+  d->fp32 = hp.fp32;
+  const size_t esz = d->fp32 ? sizeof(float2) : sizeof(double2);  // workspace element size
+  if (d->fp32) {
+    std::vector<float> tf(std::max<size_t>((size_t)N, hp.jtab.size()));
+    for (int64_t i = 0; i < N; ++i) tf[i] = (float)hp.r_true[i];
+    HK_TRY(upload(d, &d->rf, tf.data(), N));
+    for (int64_t i = 0; i < N; ++i) tf[i] = (float)hp.om_true[i];
+    HK_TRY(upload(d, &d->omf, tf.data(), N));
+    for (size_t i = 0; i < hp.jtab.size(); ++i) tf[i] = (float)hp.jtab[i];
+    HK_TRY(upload(d, &d->jtabf, tf.data(), hp.jtab.size()));
+  }
 
   // Factor tables: the column and row functions of every stacked column at every index.
   const size_t tab_bytes = (size_t)d->ncols * (size_t)N * (sizeof(double2) + sizeof(double));
@@ -225,7 +243,13 @@ int dev_plan_create(hankel_plan_s* p) {
   d->nslots = slot;
   HK_TRY(upload(d, &d->items, items.data(), items.size()));
   if (!mrows.empty()) HK_TRY(upload(d, &d->mrows, mrows.data(), mrows.size()));
-  HK_TRY(dalloc(d, &d->partial, (size_t)std::max<int64_t>(slot, 1) * hp.opt.max_nrhs));
+  {
+    void* q = nullptr;
+    const size_t cnt = (size_t)std::max<int64_t>(slot, 1) * hp.opt.max_nrhs;
+    if (d->fp32) { float* pf; HK_TRY(dalloc(d, &pf, cnt)); q = pf; }
+    else { double* pd; HK_TRY(dalloc(d, &pd, cnt)); q = pd; }
+    d->partial = q;
+  }
 
   // Twiddle table W_{Fmax}^t = exp(-2 pi i t / Fmax).
   int logFmax = 6;
@@ -234,22 +258,35 @@ int dev_plan_create(hankel_plan_s* p) {
   HK_TRY(dalloc(d, &d->tw, (size_t)1 << logFmax));
   launch_twiddles(d->tw, logFmax, 0);
   HK_LAUNCHED();
+  if (d->fp32) {
+    HK_TRY(dalloc(d, &d->twf, (size_t)1 << logFmax));
+    launch_scale_copy<float2>(d->tw, d->twf, int64_t(1) << logFmax, 1.0, 0);
+    HK_LAUNCHED();
+  }
 
   // Workspace: two ping-pong buffers, each holding a chunk of stacked columns of a block
   // (nseg transforms of length F per stacked column for segmented blocks).
+  // The plan-time spectra are computed in FP64 in the same buffers, so they hold at least
+  // nseg*F double2 values whatever the plan precision.
   size_t limit = hp.opt.workspace_limit ? hp.opt.workspace_limit : kDefaultWorkspace;
-  size_t need = (size_t)1 << logFmax;
+  const size_t dfac = sizeof(double2) / esz;  // workspace elements per double2
+  size_t need = dfac << logFmax;
   for (const Block& b : hp.blocks) {
     const size_t foot = column_footprint(b);
     const int64_t total = (int64_t)d->ncols * hp.opt.max_nrhs;
-    int64_t cap = (int64_t)(limit / (2 * sizeof(double2) * foot));
+    int64_t cap = (int64_t)(limit / (2 * esz * foot));
     cap = std::max<int64_t>(1, std::min<int64_t>(cap, total));
     need = std::max(need, (size_t)cap * foot);
-    need = std::max(need, (size_t)b.nseg * (size_t)b.F);  // room for the segment spectra
+    need = std::max(need, dfac * (size_t)b.nseg * (size_t)b.F);
   }
-  HK_TRY(dalloc(d, &d->bufA, need));
-  HK_TRY(dalloc(d, &d->bufB, need));
-  d->ws_bytes = 2 * need * sizeof(double2);
+  {
+    char* qa; char* qb;
+    HK_TRY(dalloc(d, &qa, need * esz));
+    HK_TRY(dalloc(d, &qb, need * esz));
+    d->bufA = qa;
+    d->bufB = qb;
+  }
+  d->ws_bytes = 2 * need * esz;
   d->ws_elems = need;
 
   // Per-block chirp vectors and the spectra of its convolution kernels (one per segment).
@@ -260,7 +297,30 @@ int dev_plan_create(hankel_plan_s* p) {
                                                     (int64_t)d->ncols * hp.opt.max_nrhs));
     HK_TRY(dalloc(d, &db.wU, b.R));
     HK_TRY(dalloc(d, &db.wV, b.C));
-    HK_TRY(dalloc(d, &db.H, (size_t)b.nseg * b.F));
+    if (d->fp32) {
+      float2* h; HK_TRY(dalloc(d, &h, (size_t)b.nseg * b.F)); db.H = h;
+      // per stacked column: the power of two that brings max |colfun(n)| over the block to ~1
+      std::vector<double> sc(d->ncols), isc(d->ncols);
+      for (int l = 0; l < d->ncols; ++l) {
+        const ColSpec& csp = hp.cols[l];
+        double mag = 0.0;
+        for (int64_t n : {b.n0, b.n1}) {
+          const int64_t i = n - 1;
+          cplx poly(0.0, 0.0);
+          for (int u = csp.nterm - 1; u >= 0; --u) poly = poly * hp.betan[i] + csp.G[u];
+          double m = std::abs(poly) * std::pow(hp.omt[i], csp.delta - 0.5);
+          if (csp.u1) m *= std::pow(hp.colpow[i], csp.u1);
+          mag = std::max(mag, m);
+        }
+        const int e = (mag > 0.0 && std::isfinite(mag)) ? -(int)std::lround(std::log2(mag)) : 0;
+        sc[l] = std::ldexp(1.0, e);
+        isc[l] = std::ldexp(1.0, -e);
+      }
+      HK_TRY(upload(d, &db.scale, sc.data(), sc.size()));
+      HK_TRY(upload(d, &db.iscale, isc.data(), isc.size()));
+    } else {
+      double2* h; HK_TRY(dalloc(d, &h, (size_t)b.nseg * b.F)); db.H = h;
+    }
     d->blocks.push_back(db);
     ChirpGeom g{hp.Ua, hp.Ub, hp.Va, hp.Vb, hp.E, b.k0, b.n0, b.R, b.C, b.F};
     launch_chirps(g, db.wU, db.wV, 0);
@@ -268,11 +328,14 @@ int dev_plan_create(hankel_plan_s* p) {
     SegGeom sg{hp.Ua, hp.Ub, hp.Vb, hp.E, b.k0, b.n0, b.R, b.C, 0, 0, 1, b.F};
     if (b.mode == kBlockRowSeg) { sg.Cc = b.S; sg.dn = b.S; sg.nseg = b.nseg; }
     if (b.mode == kBlockColSeg) { sg.Rr = b.S; sg.dk = b.S; sg.nseg = b.nseg; }
-    launch_seg_hh(sg, d->bufA, 0);
+    double2* hA = (double2*)d->bufA;
+    double2* hB = (double2*)d->bufB;
+    launch_seg_hh(sg, hA, 0);
     HK_LAUNCHED();
     double2* res = nullptr;
-    HK_TRY(run_fft(d->bufA, d->bufB, b.logF, (int)b.nseg, /*inverse=*/false, d->tw, d->logFmax, 0, &res));
-    launch_scale_copy(res, db.H, b.nseg * b.F, 1.0 / (double)b.F, 0);
+    HK_TRY(run_fft<double2>(hA, hB, b.logF, (int)b.nseg, /*inverse=*/false, d->tw, d->logFmax, 0, &res));
+    if (d->fp32) launch_scale_copy<float2>(res, (float2*)d->blocks.back().H, b.nseg * b.F, 1.0 / (double)b.F, 0);
+    else launch_scale_copy<double2>(res, (double2*)d->blocks.back().H, b.nseg * b.F, 1.0 / (double)b.F, 0);
     HK_LAUNCHED();
   }
 
@@ -303,9 +366,13 @@ namespace {
 // Far-field work of one block for nrhs vectors: chunks of `cap` stacked columns through
 // generation, forward FFTs, the product with the kernel spectra (summed over column segments
 // or replicated over row segments), inverse FFTs and the row accumulation into f.
+// C = double2 (FP64 plans) or float2 (FP32 plans).
+template <class C>
 int run_block(DevicePlan* d, const DevBlock& db, const double* c, int64_t ldc, double* f, int64_t ldf, int nrhs,
-              double2* A, double2* B, int64_t cap, cudaStream_t st, bool record) {
+              C* A, C* B, int64_t cap, cudaStream_t st, bool record) {
   const Block& b = db.b;
+  const C* tw = d->fp32 ? (const C*)d->twf : (const C*)d->tw;
+  const C* H = (const C*)db.H;
   const int64_t total = (int64_t)d->ncols * nrhs;
   const bool rowseg = b.mode == kBlockRowSeg, colseg = b.mode == kBlockColSeg;
   for (int64_t c0 = 0; c0 < total; c0 += cap) {
@@ -315,42 +382,42 @@ int run_block(DevicePlan* d, const DevBlock& db, const double* c, int64_t ldc, d
     {
       StageScope sc(d, HANKEL_STAGE_GEN, st, record);
       GenArgs ga{A, b.F, b.C, b.n0, rowseg ? b.S : b.C, rowseg ? b.nseg : 1, nc, c0, d->ncols, c, ldc,
-                 d->nodes, d->cols, db.wV, d->T, d->hpN};
-      launch_gen(ga, st);
+                 d->nodes, d->cols, db.wV, d->T, d->hpN, db.scale};
+      launch_gen<C>(ga, st);
       HK_LAUNCHED();
       sc.done(1, 0.0, 0.0);
     }
-    double2* res = nullptr;
+    C* res = nullptr;
     {
       StageScope sc(d, HANKEL_STAGE_FFT, st, record);
       int np = 0;
-      HK_TRY(run_fft(A, B, b.logF, (int)nfwd, false, d->tw, d->logFmax, st, &res, &np));
+      HK_TRY(run_fft<C>(A, B, b.logF, (int)nfwd, false, tw, d->logFmax, st, &res, &np));
       HK_LAUNCHED();
-      sc.done(np, 5.0 * (double)b.F * (double)b.logF * (double)nfwd, 0.0, 32.0 * (double)b.F * nfwd * np);
+      sc.done(np, 5.0 * (double)b.F * (double)b.logF * (double)nfwd, 0.0, 2.0 * sizeof(C) * (double)b.F * nfwd * np);
     }
-    double2* other = (res == A) ? B : A;
-    double2* spec = res;
+    C* other = (res == A) ? B : A;
+    C* spec = res;
     {
       StageScope sc(d, HANKEL_STAGE_POINTWISE, st, record);
-      if (rowseg) { launch_seg_mac(res, db.H, other, b.F, b.nseg, nc, st); spec = other; }
-      else if (colseg) { launch_seg_expand(res, db.H, other, b.F, b.nseg, nc, st); spec = other; }
-      else launch_pointwise(res, db.H, b.F, nc, st);
+      if (rowseg) { launch_seg_mac<C>(res, H, other, b.F, b.nseg, nc, st); spec = other; }
+      else if (colseg) { launch_seg_expand<C>(res, H, other, b.F, b.nseg, nc, st); spec = other; }
+      else launch_pointwise<C>(res, H, b.F, nc, st);
       HK_LAUNCHED();
       sc.done(1, 0.0, 0.0);
     }
-    double2* res2 = nullptr;
+    C* res2 = nullptr;
     {
       StageScope sc(d, HANKEL_STAGE_FFT, st, record);
       int np = 0;
-      HK_TRY(run_fft(spec, spec == A ? B : A, b.logF, (int)ninv, true, d->tw, d->logFmax, st, &res2, &np));
+      HK_TRY(run_fft<C>(spec, spec == A ? B : A, b.logF, (int)ninv, true, tw, d->logFmax, st, &res2, &np));
       HK_LAUNCHED();
-      sc.done(np, 5.0 * (double)b.F * (double)b.logF * (double)ninv, 0.0, 32.0 * (double)b.F * ninv * np);
+      sc.done(np, 5.0 * (double)b.F * (double)b.logF * (double)ninv, 0.0, 2.0 * sizeof(C) * (double)b.F * ninv * np);
     }
     {
       StageScope sc(d, HANKEL_STAGE_OUT, st, record);
       OutArgs oa{res2, b.F, b.R, b.k0, (rowseg ? b.S : b.C) - 1, colseg ? b.S : b.R, colseg ? b.nseg : 1,
-                 nc, c0, d->ncols, f, ldf, d->nodes, d->cols, db.wU, d->W, d->hpN};
-      launch_out(oa, st);
+                 nc, c0, d->ncols, f, ldf, d->nodes, d->cols, db.wU, d->W, d->hpN, db.iscale};
+      launch_out<C>(oa, st);
       HK_LAUNCHED();
       sc.done(1, 0.0, 0.0);
     }
@@ -358,28 +425,43 @@ int run_block(DevicePlan* d, const DevBlock& db, const double* c, int64_t ldc, d
   return HANKEL_OK;
 }
 
+// Near field of a plan in its precision, then every far block.
+int run_all(DevicePlan* d, const HostPlan& hp, const double* c, int64_t ldc, double* f, int64_t ldf, int nrhs,
+            void* A, void* B, void* partial, size_t capacity_elems, bool chunk_from_capacity, cudaStream_t st,
+            bool record) {
+  {
+    StageScope sc(d, HANKEL_STAGE_NEAR, st, record);
+    if (d->fp32)
+      launch_near<float>(d->items, d->nitems, d->mrows, d->nmrows, (float*)partial, nrhs, c, ldc, f, ldf, d->rf,
+                         d->omf, d->jtabf, hp.jt_n, hp.jt_deg, st);
+    else
+      launch_near<double>(d->items, d->nitems, d->mrows, d->nmrows, (double*)partial, nrhs, c, ldc, f, ldf,
+                          d->nodes.r_true, d->nodes.om_true, d->jtab, hp.jt_n, hp.jt_deg, st);
+    HK_LAUNCHED();
+    sc.done(d->nmrows > 0 ? 2 : 1, 0.0, (double)hp.near_count * nrhs);
+  }
+  for (const DevBlock& db : d->blocks) {
+    const int64_t cap = chunk_from_capacity
+                            ? std::max<int64_t>(1, (int64_t)(capacity_elems / column_footprint(db.b)))
+                            : db.cap;
+    if (d->fp32) HK_TRY(run_block<float2>(d, db, c, ldc, f, ldf, nrhs, (float2*)A, (float2*)B, cap, st, record));
+    else HK_TRY(run_block<double2>(d, db, c, ldc, f, ldf, nrhs, (double2*)A, (double2*)B, cap, st, record));
+  }
+  return HANKEL_OK;
+}
+
 }  // namespace
 
 int dev_exec(hankel_plan_s* p, const double* c, int64_t ldc, double* f, int64_t ldf, int nrhs, void* stream) {
-  const HostPlan& hp = p->hp;
   DevicePlan* d = p->dev;
   cudaStream_t st = (cudaStream_t)stream;
   int cur = -1;
   cudaGetDevice(&cur);
   if (cur != d->device) cudaSetDevice(d->device);
-
-  // Near field: overwrite f with the directly summed part.
-  {
-    StageScope sc(d, HANKEL_STAGE_NEAR, st);
-    launch_near(d->items, d->nitems, d->mrows, d->nmrows, d->partial, nrhs, c, ldc, f, ldf, d->nodes, d->jtab,
-                hp.jt_n, hp.jt_deg, st);
-    HK_LAUNCHED();
-    sc.done(d->nmrows > 0 ? 2 : 1, 0.0, (double)hp.near_count * nrhs);
-  }
-  // Far field, block by block.
-  for (const DevBlock& db : d->blocks) HK_TRY(run_block(d, db, c, ldc, f, ldf, nrhs, d->bufA, d->bufB, db.cap, st, true));
+  // near field overwrites f; far blocks add to it
+  const int s = run_all(d, p->hp, c, ldc, f, ldf, nrhs, d->bufA, d->bufB, d->partial, 0, false, st, true);
   if (cur >= 0 && cur != d->device) cudaSetDevice(cur);
-  return HANKEL_OK;
+  return s;
 }
 
 int dev_set_timing(hankel_plan_s* p, int enable) {
@@ -476,12 +558,15 @@ int dev_exec_static(hankel_plan_s* p, const double* c, double* f, void* stream) 
   const HostPlan& hp = p->hp;
   DevicePlan* d = p->dev;
   const int64_t N = hp.opt.N;
-  // Layout of the static array: [bufA | bufB | near partial sums (as doubles)].
+  // Layout of the static array (bytes): [bufA | bufB | near partial sums], elements of the
+  // plan's precision.
+  const size_t esz = d->fp32 ? sizeof(float2) : sizeof(double2);
+  const size_t total_elems = (size_t)HANKEL_STATIC_SCRATCH_BYTES / esz;
   const size_t partial_elems = ((size_t)d->nslots + 1) / 2 + 1;
   size_t foot_max = 0;
   for (const DevBlock& db : d->blocks) foot_max = std::max(foot_max, column_footprint(db.b));
-  if (2 * foot_max + partial_elems > kStaticScratchElems) return HANKEL_EUNSUPPORTED;
-  const size_t per_buf = (kStaticScratchElems - partial_elems) / 2;
+  if (2 * foot_max + partial_elems > total_elems) return HANKEL_EUNSUPPORTED;
+  const size_t per_buf = (total_elems - partial_elems) / 2;
 
   int cur = -1;
   cudaGetDevice(&cur);
@@ -492,17 +577,15 @@ int dev_exec_static(hankel_plan_s* p, const double* c, double* f, void* stream) 
     if (cur >= 0 && cur != d->device) cudaSetDevice(cur);
     return st0;
   }
-  double2* sA = base;
-  double2* sB = base + per_buf;
-  double* spartial = (double*)(base + 2 * per_buf);
+  char* bytes = (char*)base;
+  void* sA = bytes;
+  void* sB = bytes + per_buf * esz;
+  void* spartial = bytes + 2 * per_buf * esz;
   cudaStream_t st = (cudaStream_t)stream;
-
-  launch_near(d->items, d->nitems, d->mrows, d->nmrows, spartial, 1, c, N, f, N, d->nodes, d->jtab, hp.jt_n,
-              hp.jt_deg, st);
-  HK_LAUNCHED();
-  for (const DevBlock& db : d->blocks) {
-    const int64_t cap = std::max<int64_t>(1, (int64_t)(per_buf / column_footprint(db.b)));
-    HK_TRY(run_block(d, db, c, N, f, N, 1, sA, sB, cap, st, false));
+  const int s = run_all(d, hp, c, N, f, N, 1, sA, sB, spartial, per_buf, true, st, false);
+  if (s != HANKEL_OK) {
+    if (cur >= 0 && cur != d->device) cudaSetDevice(cur);
+    return s;
   }
   if (cur >= 0 && cur != d->device) cudaSetDevice(cur);
   return HANKEL_OK;

@@ -10,6 +10,7 @@
 
 #include <algorithm>
 
+#include "cplx.cuh"
 #include "kernels.cuh"
 
 namespace hk {
@@ -26,16 +27,17 @@ __device__ __forceinline__ double ipow(double x, int e) {
   return r;
 }
 
+template <class C>
 __global__ void __launch_bounds__(256) k_gen(GenArgs a) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= a.F) return;
   const int64_t ncolumns = (int64_t)a.nc * a.nsegc;
   for (int64_t y = blockIdx.y; y < ncolumns; y += gridDim.y) {
-    double2* A = a.A + y * a.F;
+    C* A = reinterpret_cast<C*>(a.A) + y * a.F;
     const int64_t cc = y / a.nsegc, sg = y - cc * a.nsegc;
     const int64_t np = sg * a.S + t;  // column offset within the block
     if (t >= a.S || np >= a.C) {
-      A[t] = make_double2(0.0, 0.0);
+      A[t] = from_d2<C>(make_double2(0.0, 0.0));
       continue;
     }
     const int64_t g = a.c0 + cc;
@@ -43,9 +45,10 @@ __global__ void __launch_bounds__(256) k_gen(GenArgs a) {
     const int l = (int)(g - (int64_t)rhs * a.ncols);
     const int64_t i = a.n0 - 1 + np;
     if (a.T) {
-      const double cv = a.c[(int64_t)rhs * a.ldc + i];
+      double cv = a.c[(int64_t)rhs * a.ldc + i];
+      if (a.scale) cv *= a.scale[l];
       const double2 x = a.T[(int64_t)l * a.N + i];
-      A[t] = make_double2(cv * x.x, cv * x.y);
+      A[t] = from_d2<C>(make_double2(cv * x.x, cv * x.y));
       continue;
     }
     const DevColSpec& cs = a.cols[l];
@@ -58,13 +61,15 @@ __global__ void __launch_bounds__(256) k_gen(GenArgs a) {
     const int d = cs.delta;
     double pw = a.nodes.rs_omt[i] * ipow(d >= 0 ? a.nodes.omt[i] : a.nodes.inv_omt[i], d >= 0 ? d : -d);
     if (cs.u1) pw *= ipow(a.nodes.colpow[i], cs.u1);
-    const double cv = a.c[(int64_t)rhs * a.ldc + i] * pw;
+    double cv = a.c[(int64_t)rhs * a.ldc + i] * pw;
+    if (a.scale) cv *= a.scale[l];
     const double xr = pr * cv, xi = pim * cv;
     const double2 w = a.wV[np];
-    A[t] = make_double2(fma(xr, w.x, -xi * w.y), fma(xr, w.y, xi * w.x));
+    A[t] = from_d2<C>(make_double2(fma(xr, w.x, -xi * w.y), fma(xr, w.y, xi * w.x)));
   }
 }
 
+template <class C>
 __global__ void __launch_bounds__(256) k_out(OutArgs a) {
   const int64_t kp = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (kp >= a.R) return;
@@ -78,7 +83,7 @@ __global__ void __launch_bounds__(256) k_out(OutArgs a) {
   }
   const double2 wu = a.wU[kp];
   const int64_t sg = kp / a.Sr;
-  const double2* Y = a.Y + sg * a.F + (kp - sg * a.Sr) + a.off;
+  const C* Y = reinterpret_cast<const C*>(a.Y) + sg * a.F + (kp - sg * a.Sr) + a.off;
   double ar = 0.0, ai = 0.0;
   int cur = (int)(a.c0 / a.ncols);
   for (int cc = 0; cc < a.nc; ++cc) {
@@ -99,37 +104,39 @@ __global__ void __launch_bounds__(256) k_out(OutArgs a) {
       wgt = rs * ipow(d >= 0 ? rv : irv, d >= 0 ? d : -d);
       if (cs.u1) wgt *= ipow(rp, cs.u1);
     }
-    const double2 y = Y[(int64_t)cc * a.nsegr * a.F];
-    ar = fma(wgt, y.x, ar);
-    ai = fma(wgt, y.y, ai);
+    if (a.iscale) wgt *= a.iscale[l];
+    const C y = Y[(int64_t)cc * a.nsegr * a.F];
+    ar = fma(wgt, (double)y.x, ar);
+    ai = fma(wgt, (double)y.y, ai);
   }
   a.f[(int64_t)cur * a.ldf + i] += fma(wu.x, ar, -wu.y * ai);
 }
 
-__global__ void k_seg_mac(const double2* __restrict__ in, const double2* __restrict__ H, double2* __restrict__ out,
-                          int64_t F, int64_t nseg, int64_t total) {
+template <class C>
+__global__ void k_seg_mac(const C* __restrict__ in, const C* __restrict__ H, C* __restrict__ out, int64_t F,
+                          int64_t nseg, int64_t total) {
+  typedef typename RealOf<C>::type R;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t cc = e / F, t = e - cc * F;
-    const double2* x = in + cc * nseg * F + t;
-    double ar = 0.0, ai = 0.0;
+    const C* x = in + cc * nseg * F + t;
+    R ar = 0, ai = 0;
     for (int64_t s = 0; s < nseg; ++s) {
-      const double2 v = x[s * F];
-      const double2 h = __ldg(&H[s * F + t]);
-      ar = fma(v.x, h.x, fma(-v.y, h.y, ar));
-      ai = fma(v.x, h.y, fma(v.y, h.x, ai));
+      const C v = x[s * F];
+      const C h = __ldg(&H[s * F + t]);
+      ar = fmar(v.x, h.x, fmar(-v.y, h.y, ar));
+      ai = fmar(v.x, h.y, fmar(v.y, h.x, ai));
     }
-    out[e] = make_double2(ar, ai);
+    out[e] = mkc(ar, ai);
   }
 }
 
-__global__ void k_seg_expand(const double2* __restrict__ in, const double2* __restrict__ H, double2* __restrict__ out,
-                             int64_t F, int64_t nseg, int64_t total) {
+template <class C>
+__global__ void k_seg_expand(const C* __restrict__ in, const C* __restrict__ H, C* __restrict__ out, int64_t F,
+                             int64_t nseg, int64_t total) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t t = e % F, q = e / F;
     const int64_t cc = q / nseg, s = q - cc * nseg;
-    const double2 v = in[cc * F + t];
-    const double2 h = __ldg(&H[s * F + t]);
-    out[e] = make_double2(fma(v.x, h.x, -v.y * h.y), fma(v.x, h.y, v.y * h.x));
+    out[e] = cmul(in[cc * F + t], __ldg(&H[s * F + t]));
   }
 }
 
@@ -166,30 +173,42 @@ unsigned grid1d(int64_t n) {
 
 }  // namespace
 
+template <class C>
 void launch_gen(const GenArgs& a, cudaStream_t st) {
   const int64_t ny = std::min<int64_t>((int64_t)a.nc * a.nsegc, 65535);
   dim3 grid((unsigned)((a.F + 255) / 256), (unsigned)ny);
-  k_gen<<<grid, 256, 0, st>>>(a);
+  k_gen<C><<<grid, 256, 0, st>>>(a);
 }
 
-void launch_seg_mac(const double2* in, const double2* H, double2* out, int64_t F, int64_t nseg, int nc,
-                    cudaStream_t st) {
+template <class C>
+void launch_seg_mac(const C* in, const C* H, C* out, int64_t F, int64_t nseg, int nc, cudaStream_t st) {
   const int64_t total = F * nc;
-  k_seg_mac<<<grid1d(total), 256, 0, st>>>(in, H, out, F, nseg, total);
+  k_seg_mac<C><<<grid1d(total), 256, 0, st>>>(in, H, out, F, nseg, total);
 }
 
-void launch_seg_expand(const double2* in, const double2* H, double2* out, int64_t F, int64_t nseg, int nc,
-                       cudaStream_t st) {
+template <class C>
+void launch_seg_expand(const C* in, const C* H, C* out, int64_t F, int64_t nseg, int nc, cudaStream_t st) {
   const int64_t total = F * nseg * nc;
-  k_seg_expand<<<grid1d(total), 256, 0, st>>>(in, H, out, F, nseg, total);
+  k_seg_expand<C><<<grid1d(total), 256, 0, st>>>(in, H, out, F, nseg, total);
 }
 
 void launch_build_tables(const TabArgs& a, cudaStream_t st) {
   k_build_tables<<<grid1d((int64_t)a.ncols * a.N), 256, 0, st>>>(a);
 }
 
+template <class C>
 void launch_out(const OutArgs& a, cudaStream_t st) {
-  k_out<<<(unsigned)((a.R + 255) / 256), 256, 0, st>>>(a);
+  k_out<C><<<(unsigned)((a.R + 255) / 256), 256, 0, st>>>(a);
 }
+
+template void launch_gen<double2>(const GenArgs&, cudaStream_t);
+template void launch_gen<float2>(const GenArgs&, cudaStream_t);
+template void launch_out<double2>(const OutArgs&, cudaStream_t);
+template void launch_out<float2>(const OutArgs&, cudaStream_t);
+template void launch_seg_mac<double2>(const double2*, const double2*, double2*, int64_t, int64_t, int, cudaStream_t);
+template void launch_seg_mac<float2>(const float2*, const float2*, float2*, int64_t, int64_t, int, cudaStream_t);
+template void launch_seg_expand<double2>(const double2*, const double2*, double2*, int64_t, int64_t, int,
+                                         cudaStream_t);
+template void launch_seg_expand<float2>(const float2*, const float2*, float2*, int64_t, int64_t, int, cudaStream_t);
 
 }  // namespace hk

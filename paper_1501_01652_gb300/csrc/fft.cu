@@ -1,17 +1,15 @@
-// Multi-column power-of-two FFT (Stockham autosort, FP64) and the chirp-z
-// helpers of the far field.
+// Multi-column power-of-two FFT (Stockham autosort, decimation in time) in FP64
+// (double2) or FP32 (float2), and the chirp-z helpers of the far field.
 //
-// A pass with current sub-length n and stride s (n*s = F) computes, for
-// every pair (p, q) with p < n/R, q < s, the R-point DFT of
-// x[q + s(p + j n/R)], j < R, multiplies output r by W_n^{p r}, and stores it
-// at y[q + s(R p + r)]; after passes with radices R_1 R_2 ... = F the output
-// is in natural order. One CTA handles kTile consecutive pairs (so every
-// global load and store touches kTile or more consecutive elements) and does
-// the R-point DFT in shared memory with radix-4/radix-2 Stockham steps.
+// After passes with radices R_1 R_2 ... = F the output is in natural order. One
+// CTA handles kTile consecutive (p, q) pairs of a pass, so every global load and
+// store touches kTile or more consecutive elements, and does the R-point DFT in
+// shared memory with radix-4/radix-2 Stockham sub-steps.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 
+#include "cplx.cuh"
 #include "kernels.cuh"
 
 namespace hk {
@@ -21,15 +19,9 @@ namespace {
 constexpr int kTile = 16;
 constexpr int kFftThreads = 256;
 
-__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
-  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
-}
-__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
-
-template <bool INV>
-__device__ __forceinline__ double2 twiddle(const double2* __restrict__ tw, int64_t idx) {
-  double2 t = __ldg(&tw[idx]);
+template <bool INV, class C>
+__device__ __forceinline__ C twiddle(const C* __restrict__ tw, int64_t idx) {
+  C t = __ldg(&tw[idx]);
   if (INV) t.y = -t.y;
   return t;
 }
@@ -38,37 +30,40 @@ __device__ __forceinline__ double2 twiddle(const double2* __restrict__ tw, int64
 // twiddle product is folded into an FMA: u0 = a0 + w2 a2, u1 = 2 a0 - u0, t = w1 a1,
 // v0 = t + w3 a3, v1 = 2t - v0; then y0 = u0 + v0, y2 = u0 - v0, y1 = u1 -/+ i v1,
 // y3 = u1 +/- i v1 (forward/inverse). 24 FP64 instructions for 4 points and 2 stages.
-template <bool INV>
-__device__ __forceinline__ void bfly4(double2& a0, double2& a1, double2& a2, double2& a3, double2 w1, double2 w2,
-                                      double2 w3) {
-  double2 u0, u1, t, v0, v1;
-  u0.x = fma(w2.x, a2.x, fma(-w2.y, a2.y, a0.x));
-  u0.y = fma(w2.x, a2.y, fma(w2.y, a2.x, a0.y));
-  u1.x = fma(2.0, a0.x, -u0.x);
-  u1.y = fma(2.0, a0.y, -u0.y);
-  t.x = fma(w1.x, a1.x, -w1.y * a1.y);
-  t.y = fma(w1.x, a1.y, w1.y * a1.x);
-  v0.x = fma(w3.x, a3.x, fma(-w3.y, a3.y, t.x));
-  v0.y = fma(w3.x, a3.y, fma(w3.y, a3.x, t.y));
-  v1.x = fma(2.0, t.x, -v0.x);
-  v1.y = fma(2.0, t.y, -v0.y);
-  a0 = make_double2(u0.x + v0.x, u0.y + v0.y);
-  a2 = make_double2(u0.x - v0.x, u0.y - v0.y);
+template <bool INV, class C>
+__device__ __forceinline__ void bfly4(C& a0, C& a1, C& a2, C& a3, C w1, C w2, C w3) {
+  typedef typename RealOf<C>::type R;
+  const R two = (R)2;
+  C u0, u1, t, v0, v1;
+  u0.x = fmar(w2.x, a2.x, fmar(-w2.y, a2.y, a0.x));
+  u0.y = fmar(w2.x, a2.y, fmar(w2.y, a2.x, a0.y));
+  u1.x = fmar(two, a0.x, -u0.x);
+  u1.y = fmar(two, a0.y, -u0.y);
+  t.x = fmar(w1.x, a1.x, -w1.y * a1.y);
+  t.y = fmar(w1.x, a1.y, w1.y * a1.x);
+  v0.x = fmar(w3.x, a3.x, fmar(-w3.y, a3.y, t.x));
+  v0.y = fmar(w3.x, a3.y, fmar(w3.y, a3.x, t.y));
+  v1.x = fmar(two, t.x, -v0.x);
+  v1.y = fmar(two, t.y, -v0.y);
+  a0 = mkc(u0.x + v0.x, u0.y + v0.y);
+  a2 = mkc(u0.x - v0.x, u0.y - v0.y);
   if (INV) {
-    a1 = make_double2(u1.x - v1.y, u1.y + v1.x);
-    a3 = make_double2(u1.x + v1.y, u1.y - v1.x);
+    a1 = mkc(u1.x - v1.y, u1.y + v1.x);
+    a3 = mkc(u1.x + v1.y, u1.y - v1.x);
   } else {
-    a1 = make_double2(u1.x + v1.y, u1.y - v1.x);
-    a3 = make_double2(u1.x - v1.y, u1.y + v1.x);
+    a1 = mkc(u1.x + v1.y, u1.y - v1.x);
+    a3 = mkc(u1.x - v1.y, u1.y + v1.x);
   }
 }
 
 // Radix-2 decimation-in-time butterfly on (a0, a1 w): y0 = a0 + w a1, y1 = 2 a0 - y0.
-__device__ __forceinline__ void bfly2(double2& a0, double2& a1, double2 w) {
-  double2 y0;
-  y0.x = fma(w.x, a1.x, fma(-w.y, a1.y, a0.x));
-  y0.y = fma(w.x, a1.y, fma(w.y, a1.x, a0.y));
-  a1 = make_double2(fma(2.0, a0.x, -y0.x), fma(2.0, a0.y, -y0.y));
+template <class C>
+__device__ __forceinline__ void bfly2(C& a0, C& a1, C w) {
+  typedef typename RealOf<C>::type R;
+  C y0;
+  y0.x = fmar(w.x, a1.x, fmar(-w.y, a1.y, a0.x));
+  y0.y = fmar(w.x, a1.y, fmar(w.y, a1.x, a0.y));
+  a1 = mkc(fmar((R)2, a0.x, -y0.x), fmar((R)2, a0.y, -y0.y));
   a0 = y0;
 }
 
@@ -80,9 +75,8 @@ __device__ __forceinline__ void bfly2(double2& a0, double2& a1, double2 w) {
 // factor W_F^{pt qq} moves to the butterfly's outputs (whose index is qq mod s_k again), and
 // W_F^{pt s_k j} joins the step's own twiddle W_{n_k}^{pp j} in one table lookup. At the last
 // step s_k = 1, so nothing is left over. Input j = 0 of every butterfly needs no twiddle.
-template <int LOGR, bool INV>
-__device__ double2* smem_dft(double2* a, double2* b, const double2* __restrict__ tw, int logFmax, int logF,
-                             const int64_t* pt) {
+template <int LOGR, bool INV, class C>
+__device__ C* smem_dft(C* a, C* b, const C* __restrict__ tw, int logFmax, int logF, const int64_t* pt) {
   constexpr int R = 1 << LOGR;
   const int fsh = logFmax - logF;
   const int64_t fmask = (int64_t(1) << logFmax) - 1;
@@ -92,14 +86,14 @@ __device__ double2* smem_dft(double2* a, double2* b, const double2* __restrict__
     const int logs = LOGR - 1, s = 1 << logs;
     for (int idx = threadIdx.x; idx < kTile * (R / 2); idx += blockDim.x) {
       const int i = idx & (kTile - 1), q = idx / kTile;
-      double2 a0 = a[q * kTile + i], a1 = a[(q + s) * kTile + i];
-      const double2 w = twiddle<INV>(tw, ((pt[i] << logs) << fsh) & fmask);
+      C a0 = a[q * kTile + i], a1 = a[(q + s) * kTile + i];
+      const C w = twiddle<INV>(tw, ((pt[i] << logs) << fsh) & fmask);
       bfly2(a0, a1, w);
       b[q * kTile + i] = a0;
       b[(q + s) * kTile + i] = a1;
     }
     __syncthreads();
-    double2* t = a; a = b; b = t;
+    C* t = a; a = b; b = t;
     logn = 1;
   }
   while (logn < LOGR) {
@@ -109,13 +103,13 @@ __device__ double2* smem_dft(double2* a, double2* b, const double2* __restrict__
       const int i = idx & (kTile - 1), bf = idx / kTile;
       const int pp = bf >> logs, qq = bf & (s - 1);
       const int e0 = qq + s * 4 * pp;  // inputs e0 + s*j, outputs qq + s*(pp + r m)
-      double2 a0 = a[(e0)*kTile + i], a1 = a[(e0 + s) * kTile + i];
-      double2 a2 = a[(e0 + 2 * s) * kTile + i], a3 = a[(e0 + 3 * s) * kTile + i];
+      C a0 = a[(e0)*kTile + i], a1 = a[(e0 + s) * kTile + i];
+      C a2 = a[(e0 + 2 * s) * kTile + i], a3 = a[(e0 + 3 * s) * kTile + i];
       // W_{n'}^{pp j} W_F^{pt s j} = W_{Fmax}^{j * base}
       const int64_t base = ((int64_t)pp << (logFmax - lognn)) + ((pt[i] << logs) << fsh);
-      const double2 w1 = twiddle<INV>(tw, base & fmask);
-      const double2 w2 = twiddle<INV>(tw, (2 * base) & fmask);
-      const double2 w3 = twiddle<INV>(tw, (3 * base) & fmask);
+      const C w1 = twiddle<INV>(tw, base & fmask);
+      const C w2 = twiddle<INV>(tw, (2 * base) & fmask);
+      const C w3 = twiddle<INV>(tw, (3 * base) & fmask);
       bfly4<INV>(a0, a1, a2, a3, w1, w2, w3);
       b[(qq + s * pp) * kTile + i] = a0;
       b[(qq + s * (pp + m)) * kTile + i] = a1;
@@ -123,7 +117,7 @@ __device__ double2* smem_dft(double2* a, double2* b, const double2* __restrict__
       b[(qq + s * (pp + 3 * m)) * kTile + i] = a3;
     }
     __syncthreads();
-    double2* t = a; a = b; b = t;
+    C* t = a; a = b; b = t;
     logn = lognn;
   }
   return a;
@@ -133,22 +127,21 @@ __device__ double2* smem_dft(double2* a, double2* b, const double2* __restrict__
 // pairs (p < n/R, q < s), z_j = y[q + s(R p + j)] W_n^{p j}, Z = DFT_R(z), x[q + s(p + r n/R)] = Z_r.
 // The store index is pi + r F/R with pi = p s + q, so a tile of kTile consecutive pairs writes
 // kTile consecutive elements per r; the loads are contiguous runs of kTile or s*R elements.
-template <int LOGR, bool INV>
-__global__ void __launch_bounds__(kFftThreads) k_fft_pass(const double2* __restrict__ src, double2* __restrict__ dst,
-                                                          int logF, int logS, const double2* __restrict__ tw,
-                                                          int logFmax) {
+template <int LOGR, bool INV, class C>
+__global__ void __launch_bounds__(kFftThreads) k_fft_pass(const C* __restrict__ src, C* __restrict__ dst, int logF,
+                                                          int logS, const C* __restrict__ tw, int logFmax) {
   constexpr int R = 1 << LOGR;
-  extern __shared__ double2 sm[];
+  extern __shared__ __align__(16) unsigned char sm_raw[];
   __shared__ int64_t pt[kTile];
-  double2* v = sm;
-  double2* w = sm + R * kTile;
+  C* v = reinterpret_cast<C*>(sm_raw);
+  C* w = v + R * kTile;
   const int64_t F = int64_t(1) << logF;
   const int64_t FR = F >> LOGR;  // pairs per column, a multiple of kTile
   const int64_t G0 = (int64_t)blockIdx.x * kTile;
   const int64_t col = G0 / FR;
   const int64_t pi0 = G0 - col * FR;
-  const double2* x = src + col * F;
-  double2* y = dst + col * F;
+  const C* x = src + col * F;
+  C* y = dst + col * F;
   const int64_t s = int64_t(1) << logS;
   if (threadIdx.x < kTile) pt[threadIdx.x] = ((pi0 + threadIdx.x) >> logS) << logS;  // p * s
   if (s >= kTile) {
@@ -168,31 +161,30 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_pass(const double2* __restr
     }
   }
   __syncthreads();
-  const double2* res = smem_dft<LOGR, INV>(v, w, tw, logFmax, logF, pt);
+  const C* res = smem_dft<LOGR, INV>(v, w, tw, logFmax, logF, pt);
   for (int idx = threadIdx.x; idx < R * kTile; idx += blockDim.x) {
     const int i = idx & (kTile - 1), r = idx / kTile;
     y[pi0 + i + (int64_t)r * FR] = res[r * kTile + i];
   }
 }
 
-template <int LOGR, bool INV>
-void launch_pass(const double2* src, double2* dst, int logF, int logS, int ncols, const double2* tw, int logFmax,
-                 cudaStream_t st) {
+template <int LOGR, bool INV, class C>
+void launch_pass(const C* src, C* dst, int logF, int logS, int ncols, const C* tw, int logFmax, cudaStream_t st) {
   constexpr int R = 1 << LOGR;
-  const size_t smem = 2 * (size_t)R * kTile * sizeof(double2);
+  const size_t smem = 2 * (size_t)R * kTile * sizeof(C);
   static bool configured = false;
   if (!configured) {
-    cudaFuncSetAttribute(k_fft_pass<LOGR, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_fft_pass<LOGR, INV, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     configured = true;
   }
   const int64_t pairs = ((int64_t)ncols << logF) >> LOGR;
   const int64_t grid = pairs / kTile;
-  k_fft_pass<LOGR, INV><<<(unsigned)grid, kFftThreads, smem, st>>>(src, dst, logF, logS, tw, logFmax);
+  k_fft_pass<LOGR, INV, C><<<(unsigned)grid, kFftThreads, smem, st>>>(src, dst, logF, logS, tw, logFmax);
 }
 
-template <bool INV>
-void launch_pass_r(int logR, const double2* src, double2* dst, int logF, int logS, int ncols, const double2* tw,
-                   int logFmax, cudaStream_t st) {
+template <bool INV, class C>
+void launch_pass_r(int logR, const C* src, C* dst, int logF, int logS, int ncols, const C* tw, int logFmax,
+                   cudaStream_t st) {
   switch (logR) {
     case 1: launch_pass<1, INV>(src, dst, logF, logS, ncols, tw, logFmax, st); break;
     case 2: launch_pass<2, INV>(src, dst, logF, logS, ncols, tw, logFmax, st); break;
@@ -237,12 +229,14 @@ __global__ void k_seg_hh(SegGeom g, double2* hh) {
   }
 }
 
-__global__ void k_scale_copy(const double2* src, double2* dst, int64_t n, double scale) {
+template <class C>
+__global__ void k_scale_copy(const double2* src, C* dst, int64_t n, double scale) {
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
-    dst[t] = make_double2(src[t].x * scale, src[t].y * scale);
+    dst[t] = from_d2<C>(make_double2(src[t].x * scale, src[t].y * scale));
 }
 
-__global__ void k_pointwise(double2* y, const double2* __restrict__ H, int64_t F, int64_t total) {
+template <class C>
+__global__ void k_pointwise(C* y, const C* __restrict__ H, int64_t F, int64_t total) {
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x)
     y[t] = cmul(y[t], __ldg(&H[t & (F - 1)]));
 }
@@ -266,35 +260,46 @@ void launch_seg_hh(const SegGeom& g, double2* hh, cudaStream_t st) {
   k_seg_hh<<<grid_for(g.nseg * g.F, 256), 256, 0, st>>>(g, hh);
 }
 
-void launch_scale_copy(const double2* src, double2* dst, int64_t n, double scale, cudaStream_t st) {
-  k_scale_copy<<<grid_for(n, 256), 256, 0, st>>>(src, dst, n, scale);
+template <class C>
+void launch_scale_copy(const double2* src, C* dst, int64_t n, double scale, cudaStream_t st) {
+  k_scale_copy<C><<<grid_for(n, 256), 256, 0, st>>>(src, dst, n, scale);
 }
 
-void launch_pointwise(double2* y, const double2* H, int64_t F, int ncols, cudaStream_t st) {
+template <class C>
+void launch_pointwise(C* y, const C* H, int64_t F, int ncols, cudaStream_t st) {
   const int64_t total = F * ncols;
-  k_pointwise<<<grid_for(total, 256), 256, 0, st>>>(y, H, F, total);
+  k_pointwise<C><<<grid_for(total, 256), 256, 0, st>>>(y, H, F, total);
 }
 
-int run_fft(double2* a, double2* b, int logF, int ncols, bool inverse, const double2* tw, int logFmax,
-            cudaStream_t st, double2** result, int* npasses) {
+template <class C>
+int run_fft(C* a, C* b, int logF, int ncols, bool inverse, const C* tw, int logFmax, cudaStream_t st, C** result,
+            int* npasses) {
   if (logF < 6 || logF > logFmax) return HANKEL_EINVAL;
   const int maxlog = std::min(7, logF - 4);  // keeps F/R >= kTile pairs per column
   const int np = (logF + maxlog - 1) / maxlog;
   const int base = logF / np, extra = logF % np;
-  double2* src = a;
-  double2* dst = b;
+  C* src = a;
+  C* dst = b;
   int done = 0;  // log2 of the sub-length transformed so far
   for (int i = 0; i < np; ++i) {
     const int lr = base + (i < extra ? 1 : 0);
     done += lr;
     const int logS = logF - done;
-    if (inverse) launch_pass_r<true>(lr, src, dst, logF, logS, ncols, tw, logFmax, st);
-    else launch_pass_r<false>(lr, src, dst, logF, logS, ncols, tw, logFmax, st);
+    if (inverse) launch_pass_r<true, C>(lr, src, dst, logF, logS, ncols, tw, logFmax, st);
+    else launch_pass_r<false, C>(lr, src, dst, logF, logS, ncols, tw, logFmax, st);
     std::swap(src, dst);
   }
   *result = src;
   if (npasses) *npasses = np;
   return HANKEL_OK;
 }
+
+template int run_fft<double2>(double2*, double2*, int, int, bool, const double2*, int, cudaStream_t, double2**,
+                              int*);
+template int run_fft<float2>(float2*, float2*, int, int, bool, const float2*, int, cudaStream_t, float2**, int*);
+template void launch_scale_copy<double2>(const double2*, double2*, int64_t, double, cudaStream_t);
+template void launch_scale_copy<float2>(const double2*, float2*, int64_t, double, cudaStream_t);
+template void launch_pointwise<double2>(double2*, const double2*, int64_t, int, cudaStream_t);
+template void launch_pointwise<float2>(float2*, const float2*, int64_t, int, cudaStream_t);
 
 }  // namespace hk

@@ -58,7 +58,7 @@ struct ChirpGeom {
 };
 
 struct GenArgs {
-  double2* A;         // [nc * nsegc][F] output columns
+  void* A;            // [nc * nsegc][F] output columns (double2 or float2)
   int64_t F, C, n0;   // transform length, block columns, first column (1-based)
   int64_t S;          // columns per segment (C when the columns are not segmented)
   int64_t nsegc;      // column segments per stacked column (1 when not segmented)
@@ -72,10 +72,11 @@ struct GenArgs {
   const double2* wV;  // column chirp of the block
   const double2* T;   // optional [ncols][N] column factors times the column chirp (nullptr: computed here)
   int64_t N;
+  const double* scale;  // optional per stacked column: factor applied before rounding to FP32 (nullptr: 1)
 };
 
 struct OutArgs {
-  const double2* Y;   // [nc * nsegr][F] inverse-transformed columns
+  const void* Y;      // [nc * nsegr][F] inverse-transformed columns (double2 or float2)
   int64_t F, R, k0;
   int64_t off;        // index of output row k0 in a transformed column (convolution offset)
   int64_t Sr;         // rows per row segment (R when the rows are not segmented)
@@ -90,6 +91,7 @@ struct OutArgs {
   const double2* wU;  // row chirp of the block
   const double* W;    // optional [ncols][N] row factors (nullptr: computed here)
   int64_t N;
+  const double* iscale;  // optional per stacked column: inverse of GenArgs::scale (nullptr: 1)
 };
 
 // Plan-time tables of the factors that do not depend on c:
@@ -117,21 +119,30 @@ void launch_twiddles(double2* tw, int logF, cudaStream_t st);
 void launch_chirps(const ChirpGeom& g, double2* wU, double2* wV, cudaStream_t st);
 void launch_seg_hh(const SegGeom& g, double2* hh, cudaStream_t st);
 // out[cc][t] = sum_s in[cc*nseg + s][t] * H[s][t]   (overlap-add of column segments)
-void launch_seg_mac(const double2* in, const double2* H, double2* out, int64_t F, int64_t nseg, int nc,
-                    cudaStream_t st);
+template <class C>
+void launch_seg_mac(const C* in, const C* H, C* out, int64_t F, int64_t nseg, int nc, cudaStream_t st);
 // out[cc*nseg + s][t] = in[cc][t] * H[s][t]         (overlap-save of row segments)
-void launch_seg_expand(const double2* in, const double2* H, double2* out, int64_t F, int64_t nseg, int nc,
-                       cudaStream_t st);
+template <class C>
+void launch_seg_expand(const C* in, const C* H, C* out, int64_t F, int64_t nseg, int nc, cudaStream_t st);
 // Out-of-place multi-column FFT of length 2^logF over ncols contiguous columns,
 // ping-ponging between a (input) and b; *result receives the buffer holding the output.
-int run_fft(double2* a, double2* b, int logF, int ncols, bool inverse, const double2* tw, int logFmax,
-            cudaStream_t st, double2** result, int* npasses = nullptr);
-void launch_scale_copy(const double2* src, double2* dst, int64_t n, double scale, cudaStream_t st);
-void launch_pointwise(double2* y, const double2* H, int64_t F, int ncols, cudaStream_t st);
+// C is double2 (FP64) or float2 (FP32); tw is the matching twiddle table of 2^logFmax entries.
+template <class C>
+int run_fft(C* a, C* b, int logF, int ncols, bool inverse, const C* tw, int logFmax, cudaStream_t st, C** result,
+            int* npasses = nullptr);
+template <class C>
+void launch_scale_copy(const double2* src, C* dst, int64_t n, double scale, cudaStream_t st);
+template <class C>
+void launch_pointwise(C* y, const C* H, int64_t F, int ncols, cudaStream_t st);
+template <class C>
 void launch_gen(const GenArgs& a, cudaStream_t st);
+template <class C>
 void launch_out(const OutArgs& a, cudaStream_t st);
-void launch_near(const NearItem* items, int64_t nitems, const NearRow* mrows, int64_t nmrows, double* partial,
-                 int nrhs, const double* c, int64_t ldc, double* f, int64_t ldf, const NodeTables& nodes,
-                 const double* jtab, int64_t jt_n, int deg, cudaStream_t st);
+// Near field in FP64 (R = double: r, omega, jtab from the FP64 tables) or FP32 (R = float:
+// rf, omf, jtabf single-precision copies); sums are accumulated in R, outputs written as double.
+template <class R>
+void launch_near(const NearItem* items, int64_t nitems, const NearRow* mrows, int64_t nmrows, R* partial, int nrhs,
+                 const double* c, int64_t ldc, double* f, int64_t ldf, const R* r, const R* om, const R* jtab,
+                 int64_t jt_n, int deg, cudaStream_t st);
 
 }  // namespace hk

@@ -9,6 +9,7 @@
 
 #include <algorithm>
 
+#include "cplx.cuh"
 #include "kernels.cuh"
 
 namespace hk {
@@ -17,39 +18,41 @@ namespace {
 
 constexpr int kRhsGroup = 4;
 
-__device__ __forceinline__ double table_j(const double* __restrict__ jtab, int64_t jt_n, int deg, double z) {
+template <class R>
+__device__ __forceinline__ R table_j(const R* __restrict__ jtab, int64_t jt_n, int deg, R z) {
   int64_t i = (int64_t)z;
   i = i < 0 ? 0 : (i >= jt_n ? jt_n - 1 : i);
-  const double d = z - ((double)i + 0.5);
-  const double* t = jtab + i * (deg + 1);
-  double v = __ldg(&t[deg]);
-  for (int j = deg - 1; j >= 0; --j) v = fma(v, d, __ldg(&t[j]));
+  const R d = z - ((R)i + (R)0.5);
+  const R* t = jtab + i * (deg + 1);
+  R v = __ldg(&t[deg]);
+  for (int j = deg - 1; j >= 0; --j) v = fmar(v, d, __ldg(&t[j]));
   return v;
 }
 
-__global__ void __launch_bounds__(256) k_near(const NearItem* __restrict__ items, int64_t nitems, double* partial,
+template <class R>
+__global__ void __launch_bounds__(256) k_near(const NearItem* __restrict__ items, int64_t nitems, R* partial,
                                               int nrhs, const double* __restrict__ c, int64_t ldc, double* f,
-                                              int64_t ldf, const double* __restrict__ r_true,
-                                              const double* __restrict__ om_true, const double* __restrict__ jtab,
+                                              int64_t ldf, const R* __restrict__ r_true,
+                                              const R* __restrict__ om_true, const R* __restrict__ jtab,
                                               int64_t jt_n, int deg) {
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= nitems) return;
   const NearItem it = items[warp];
-  const double r = r_true[it.k - 1];
+  const R r = r_true[it.k - 1];
   for (int r0 = 0; r0 < nrhs; r0 += kRhsGroup) {
-    double acc[kRhsGroup];
+    R acc[kRhsGroup];
 #pragma unroll
-    for (int g = 0; g < kRhsGroup; ++g) acc[g] = 0.0;
+    for (int g = 0; g < kRhsGroup; ++g) acc[g] = 0;
     for (int64_t n = it.n0 + lane; n <= it.n1; n += 32) {
-      const double J = table_j(jtab, jt_n, deg, r * __ldg(&om_true[n - 1]));
+      const R J = table_j(jtab, jt_n, deg, r * __ldg(&om_true[n - 1]));
 #pragma unroll
       for (int g = 0; g < kRhsGroup; ++g)
-        if (r0 + g < nrhs) acc[g] = fma(__ldg(&c[(int64_t)(r0 + g) * ldc + n - 1]), J, acc[g]);
+        if (r0 + g < nrhs) acc[g] = fmar((R)__ldg(&c[(int64_t)(r0 + g) * ldc + n - 1]), J, acc[g]);
     }
 #pragma unroll
     for (int g = 0; g < kRhsGroup; ++g) {
-      double v = acc[g];
+      R v = acc[g];
       for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
       acc[g] = v;
     }
@@ -64,30 +67,39 @@ __global__ void __launch_bounds__(256) k_near(const NearItem* __restrict__ items
   }
 }
 
-__global__ void k_near_combine(const NearRow* __restrict__ rows, int64_t nrows, const double* __restrict__ partial,
+template <class R>
+__global__ void k_near_combine(const NearRow* __restrict__ rows, int64_t nrows, const R* __restrict__ partial,
                                int nrhs, double* f, int64_t ldf) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nrows * nrhs) return;
   const int64_t i = t / nrhs;
   const int rr = (int)(t - i * nrhs);
   const NearRow row = rows[i];
-  double s = 0.0;
+  R s = 0;
   for (int j = 0; j < row.npieces; ++j) s += partial[(row.slot0 + j) * nrhs + rr];
-  f[(int64_t)rr * ldf + row.k - 1] = s;
+  f[(int64_t)rr * ldf + row.k - 1] = (double)s;
 }
 
 }  // namespace
 
-void launch_near(const NearItem* items, int64_t nitems, const NearRow* mrows, int64_t nmrows, double* partial,
-                 int nrhs, const double* c, int64_t ldc, double* f, int64_t ldf, const NodeTables& nodes,
-                 const double* jtab, int64_t jt_n, int deg, cudaStream_t st) {
+template <class R>
+void launch_near(const NearItem* items, int64_t nitems, const NearRow* mrows, int64_t nmrows, R* partial, int nrhs,
+                 const double* c, int64_t ldc, double* f, int64_t ldf, const R* r, const R* om, const R* jtab,
+                 int64_t jt_n, int deg, cudaStream_t st) {
   const int64_t threads = nitems * 32;
-  k_near<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(items, nitems, partial, nrhs, c, ldc, f, ldf,
-                                                             nodes.r_true, nodes.om_true, jtab, jt_n, deg);
+  k_near<R><<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(items, nitems, partial, nrhs, c, ldc, f, ldf, r, om,
+                                                                jtab, jt_n, deg);
   if (nmrows > 0) {
     const int64_t n = nmrows * nrhs;
-    k_near_combine<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(mrows, nmrows, partial, nrhs, f, ldf);
+    k_near_combine<R><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(mrows, nmrows, partial, nrhs, f, ldf);
   }
 }
+
+template void launch_near<double>(const NearItem*, int64_t, const NearRow*, int64_t, double*, int, const double*,
+                                  int64_t, double*, int64_t, const double*, const double*, const double*, int64_t,
+                                  int, cudaStream_t);
+template void launch_near<float>(const NearItem*, int64_t, const NearRow*, int64_t, float*, int, const double*,
+                                 int64_t, double*, int64_t, const float*, const float*, const float*, int64_t, int,
+                                 cudaStream_t);
 
 }  // namespace hk

@@ -273,7 +273,9 @@ int choose_params(const hankel_options& o, HostPlan& hp) {
   if (o.task == HANKEL_SCHLOMILCH && (o.gamma < -1 || o.gamma > 1024)) return HANKEL_EINVAL;
   if (o.eps < 1e-16) return HANKEL_EUNSUPPORTED;
   if (o.precision == HANKEL_PREC_FP32 && o.eps < 1e-5) return HANKEL_EUNSUPPORTED;
-  hp.fp32 = (o.precision == HANKEL_PREC_FP32);
+  // FP32 transform and near-field stages only where the accuracy goal allows them (eps >= 1e-5);
+  // nodes, phases and all plan tables stay FP64.
+  hp.fp32 = (o.precision == HANKEL_PREC_FP32) || (o.precision == HANKEL_PREC_AUTO && o.eps >= 1e-5);
 
   const int64_t N = o.N;
   // Table 4: M = max(floor(0.3 log(1/eps)), 3), natural logarithm.

@@ -110,6 +110,25 @@ def test_segmented_and_full_blocks(task, nu, N, eps, segment):
     assert any(b["mode"] != 0 for b in plan.blocks()) == segment
 
 
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("task,nu,kind", [("dht", 0, "normal"), ("schlomilch", 1, "uniform"),
+                                          ("schlomilch", 4, "decaying"), ("fourier_bessel", 0, "uniform")])
+@pytest.mark.parametrize("eps", [1e-4, 1e-5])
+def test_fp32_stages_at_relaxed_accuracy(task, nu, kind, eps, precision):
+    # FP32 transform and near-field stages are admitted at eps >= 1e-5 and meet the same bar
+    N = 7000
+    c = coefficients(kind, N, 2, 7000 + nu)
+    _check(task, nu, N, eps, c, precision=precision)
+
+
+@pytest.mark.parametrize("eps", [1e-4, 1e-5])
+def test_fp32_workload_size_sampled_rows(eps):
+    N = 2 ** 20
+    c = coefficients("normal", N, 2, 4 * 1000 + 3)
+    rows = sample_rows(N, 48, 17)
+    _check("dht", 0, N, eps, c, rows=rows)
+
+
 @pytest.mark.parametrize("tables", [True, False])
 def test_factor_tables_on_and_off(tables):
     # column/row factors from plan-time device tables or computed per use give the same bar

@@ -37,6 +37,15 @@ def test_status_strings():
         assert lib.hankel_status_string(code)
 
 
+def test_precision_policy():
+    assert hk.params("dht", 0, 4096, 1e-4)["precision"] == 2       # AUTO: FP32 stages at eps >= 1e-5
+    assert hk.params("dht", 0, 4096, 1e-5)["precision"] == 2
+    assert hk.params("dht", 0, 4096, 9e-6)["precision"] == 1       # FP64 below
+    assert hk.params("dht", 0, 4096, 1e-4, precision="fp64")["precision"] == 1
+    with pytest.raises(RuntimeError, match="EUNSUPPORTED"):
+        hk.params("dht", 0, 4096, 9e-6, precision="fp32")
+
+
 def test_thin_blocks_are_segmented_at_workload_size():
     p = hk.Plan("dht", 0, 2 ** 20, 1e-15, host_only=True)
     modes = sorted(b["mode"] for b in p.blocks())
@@ -118,7 +127,8 @@ def test_entries_against_oracle(case):
     eye = np.eye(N)
     for k in rows:
         ref = oracle.transform(task, nu, N, eye, rows=np.array([k - 1]), grid=GRID[grid])[:, 0]
+        near_tol = 4e-15 if info["precision"] == 1 else 2e-8  # FP32 plans keep a degree-8 J table
         for n in range(1, N + 1, 3):
             v, far = p.entry(k, n)
-            tol = eps if far else 4e-15
+            tol = eps if far else near_tol
             assert abs(v - ref[n - 1]) <= tol, (k, n, far, v, ref[n - 1])

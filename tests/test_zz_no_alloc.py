@@ -23,7 +23,7 @@ from paper_1501_01652_gb300 import _lib  # noqa: E402
 
 @pytest.mark.parametrize("task,nu,N,eps", [
     ("dht", 0, 3000, 1e-15), ("fourier_bessel", 0, 2 ** 16, 1e-8), ("schlomilch", 4, 4096, 1e-15),
-    ("dht", 0, 2 ** 20, 1e-8),
+    ("dht", 0, 2 ** 20, 1e-8), ("dht", 0, 2 ** 18, 1e-4),
 ])
 def test_static_scratch_matches_exec(task, nu, N, eps):
     lib = _lib.load()
@@ -47,7 +47,7 @@ def test_static_scratch_matches_exec(task, nu, N, eps):
 
 def test_static_scratch_rejects_oversized_plans():
     lib = _lib.load()
-    plan = hk.Plan("schlomilch", 0, 2 ** 21, 1e-4)  # its largest chirp-z transform has 2^22 points
+    plan = hk.Plan("schlomilch", 0, 2 ** 21, 1e-4, precision="fp64")  # largest transform: 2^22 FP64 points
     c = torch.zeros(2 ** 21, dtype=torch.float64, device="cuda")
     f = torch.zeros_like(c)
     st = lib.hankel_exec_static(plan.handle, ctypes.c_void_p(c.data_ptr()), ctypes.c_void_p(f.data_ptr()), None)
