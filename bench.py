@@ -2,8 +2,12 @@
 """Benchmark: DHT-0 coefficients/s at N = 2^20, eps in {1e-15, 1e-8}, FP64, one GB300.
 
 One step = one discrete Hankel transform of order 0 (Section 6, Eq. 25) at eps = 1e-15 plus
-one at eps = 1e-8, each over a batch of ``--nrhs`` seeded standard-normal coefficient
-vectors (the paper's Gaussian experiments). value = coefficients transformed / device time.
+one at eps = 1e-8, each over a batch of ``--nrhs`` seeded standard-normal coefficient vectors
+(the paper's Gaussian experiments): the served/batched form. value = coefficients transformed /
+device time with the inputs resident. The line also carries the plain form (one vector per
+execution, FP64) measured the same way, and both forms driven through the library's request
+loop with host arrays: throughput when all requests arrive at once (e2e) and p50/p99 latency
+under Poisson arrivals.
 
 Prints one JSON line (rank 0). ``--impl reference`` times the CPU oracle instead (direct
 O(N^2) FP64 summation on this host's cores) on a bounded sample of rows of the same workload.
@@ -44,9 +48,10 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--N", type=int, default=2 ** 20)
-    ap.add_argument("--nrhs", type=int, default=1)
+    ap.add_argument("--nrhs", type=int, default=16, help="vectors per batched execution (served form)")
+    ap.add_argument("--requests", type=int, default=16, help="requests per serving run")
+    ap.add_argument("--rate", type=float, default=0.0, help="Poisson request rate (0: 70%% of plain capacity)")
     ap.add_argument("--eps", default="1e-15,1e-8")
-    ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--cpu-rows", type=int, default=1024, help="oracle rows per sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -167,6 +172,74 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def timed_steps(plans, c, fs, stream, steps, warmup, flush, timing):
+    """Warm up, then time `steps` steps (each: every plan once) with CUDA events on `stream`.
+
+    L2 is flushed between steps, outside the step events. Returns per-step ms, per-plan ms
+    lists and (when timing) the plans' stage statistics."""
+    import torch
+
+    for _ in range(warmup):
+        for p, f in zip(plans, fs):
+            p.exec(c, f, stream=stream)
+    torch.cuda.synchronize()
+    if timing:
+        for p in plans:
+            p.set_timing(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    pev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in plans]
+           for _ in range(steps)]
+    torch.cuda.synchronize()
+    for s in range(steps):
+        flush.zero_()
+        ev[s][0].record(stream)
+        for i, (p, f) in enumerate(zip(plans, fs)):
+            pev[s][i][0].record(stream)
+            p.exec(c, f, stream=stream)
+            pev[s][i][1].record(stream)
+        ev[s][1].record(stream)
+    torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    plan_ms = [[pev[s][i][0].elapsed_time(pev[s][i][1]) for s in range(steps)] for i in range(len(plans))]
+    stats = [p.stage_stats() for p in plans] if timing else None
+    if timing:
+        for p in plans:
+            p.set_timing(False)
+    return step_ms, plan_ms, stats
+
+
+def serve_stream(hk, server_kw, requests, rate, seed):
+    """Feed `requests` [(eps, c)] to a server with Poisson arrivals at `rate` per second
+    (rate <= 0: all at once). Returns (coefficients/s over the makespan, latencies in ms)."""
+    srv = hk.Server(**server_kw)
+    # warm the plan cache and, with graphs, the captured launch sequences
+    for eps, c in requests[:2]:
+        t, _ = srv.submit("dht", 0, c.shape[-1], eps, c)
+        srv.wait(t)
+    for eps, c in requests[:2]:
+        t, _ = srv.submit("dht", 0, c.shape[-1], eps, c)
+        srv.wait(t)
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / rate, size=len(requests)) if rate > 0 else np.zeros(len(requests))
+    t0 = time.perf_counter()
+    due = t0
+    tickets = []
+    for (eps, c), gap in zip(requests, gaps):
+        due += gap
+        while time.perf_counter() < due:
+            time.sleep(min(0.001, max(0.0, due - time.perf_counter())))
+        tickets.append(srv.submit("dht", 0, c.shape[-1], eps, c)[0])
+    lat = [srv.wait(t) for t in tickets]
+    makespan = time.perf_counter() - t0
+    coeffs = sum(c.size for _, c in requests)
+    srv.close()
+    return coeffs / makespan, lat
+
+
+def pct(values, q):
+    return float(np.percentile(np.asarray(values), q)) if values else None
+
+
 def run_ours(args):
     import torch
 
@@ -179,59 +252,43 @@ def run_ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    N, nrhs = args.N, args.nrhs
+    N, B = args.N, args.nrhs
     eps_list = [float(e) for e in args.eps.split(",")]
-    plans = [hk.Plan("dht", 0, N, e, max_nrhs=nrhs) for e in eps_list]
-    c_host = coefficients("normal", N, nrhs, seed_for(4, rank))
-    c = torch.from_numpy(c_host).to(dev)
-    fs = [torch.empty((nrhs, N), dtype=torch.float64, device=dev) for _ in plans]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
     stream = torch.cuda.current_stream(dev)
 
-    def step():
-        for p, f in zip(plans, fs):
-            p.exec(c, f, stream=stream)
+    # plain form: one vector per execution, every stage FP64
+    c1_host = coefficients("normal", N, 1, seed_for(4, rank))
+    c1 = torch.from_numpy(c1_host).to(dev)
+    plain = [hk.Plan("dht", 0, N, e, precision="fp64") for e in eps_list]
+    f1 = [torch.empty((1, N), dtype=torch.float64, device=dev) for _ in plain]
+    p_step, p_plan, _ = timed_steps(plain, c1, f1, stream, max(1, args.steps), 1, flush, False)
+    plain_cps = len(plain) * N * len(p_step) / (sum(p_step) / 1000.0)
+    for p in plain:
+        p.destroy()
 
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    for p in plans:
-        p.set_timing(True)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    per_eps_ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-                   for _ in plans] for _ in range(args.steps)]
+    # served form: batches of B vectors per plan, precision chosen by eps (FP64 below 1e-5)
+    cB_host = coefficients("normal", N, B, seed_for(4, 100 + rank))
+    cB = torch.from_numpy(cB_host).to(dev)
+    plans = [hk.Plan("dht", 0, N, e, max_nrhs=B) for e in eps_list]
+    fs = [torch.empty((B, N), dtype=torch.float64, device=dev) for _ in plans]
     if world > 1:
         torch.distributed.barrier()
-    torch.cuda.synchronize()
     with ClockSampler(local) as clocks:
         wall0 = time.perf_counter()
-        for s in range(args.steps):
-            flush.zero_()  # evict L2 between timed steps (outside the step events)
-            ev[s][0].record(stream)
-            for i, (p, f) in enumerate(zip(plans, fs)):
-                per_eps_ev[s][i][0].record(stream)
-                p.exec(c, f, stream=stream)
-                per_eps_ev[s][i][1].record(stream)
-            ev[s][1].record(stream)
-        torch.cuda.synchronize()
+        step_ms, plan_ms, stats = timed_steps(plans, cB, fs, stream, args.steps, args.warmup, flush, True)
         wall = time.perf_counter() - wall0
     if world > 1:
         torch.distributed.barrier()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    eps_ms = [[per_eps_ev[s][i][0].elapsed_time(per_eps_ev[s][i][1]) for s in range(args.steps)]
-              for i in range(len(plans))]
-    stats = [p.stage_stats() for p in plans]
-    for p in plans:
-        p.set_timing(False)
     total_ms = sum(step_ms)
     if world > 1:
         t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         total_ms = float(t.item())
-    coeffs_per_step = len(plans) * N * nrhs
+    coeffs_per_step = len(plans) * N * B
     value = world * coeffs_per_step * args.steps / (total_ms / 1000.0)
 
-    # dominant kernel: the FFT passes (FP64, bound by the FP64 pipe, not HBM)
+    # dominant kernel: the FFT passes
     fft_ms = sum(st["fft"]["ms"] for st in stats)
     fft_flops = sum(st["fft"]["flops"] for st in stats)
     fft_launches = sum(st["fft"]["launches"] for st in stats)
@@ -239,23 +296,26 @@ def run_ours(args):
     achieved = fft_flops / (fft_ms / 1000.0) / 1e9 if fft_ms > 0 else 0.0
     launches = sum(st[k]["launches"] for st in stats for k in st)
     stage_ms = {k: round(sum(st[k]["ms"] for st in stats) / args.steps, 3) for k in stats[0]}
-
-    # end to end: host arrays in and out through the C ABI, copies inside the timed region
-    e2e_steps = args.e2e_steps if args.e2e_steps is not None else max(1, min(args.steps, 2))
-    c_pin = torch.from_numpy(c_host).pin_memory()
-    f_pin = torch.empty((nrhs, N), dtype=torch.float64).pin_memory()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        for p in plans:
-            p.exec_host(c_pin.numpy(), out=f_pin.numpy())
-    e2e_s = time.perf_counter() - t0
-    e2e_value = world * coeffs_per_step * e2e_steps / e2e_s
-
     fp32 = all(p.info["precision"] == 2 for p in plans)
+    for p in plans:
+        p.destroy()
+    del fs
+
+    # request streams through the library's server: end to end with host arrays
+    reqs = []
+    for i in range(args.requests):
+        e = eps_list[i % len(eps_list)]
+        reqs.append((e, coefficients("normal", N, 1, seed_for(4, 200 + i))[0]))
+    served_kw = dict(streams=4, max_batch=B, use_graphs=True, precision="auto")
+    plain_kw = dict(streams=1, max_batch=1, use_graphs=False, precision="fp64")
+    served_e2e, served_sat_lat = serve_stream(hk, served_kw, reqs, 0.0, 1)
+    plain_e2e, plain_sat_lat = serve_stream(hk, plain_kw, reqs, 0.0, 1)
+    rate = args.rate if args.rate > 0 else 0.7 * plain_e2e / N  # 70 % of the plain form's capacity
+    served_cps_p, served_lat = serve_stream(hk, served_kw, reqs, rate, 2)
+    plain_cps_p, plain_lat = serve_stream(hk, plain_kw, reqs, rate, 2)
+
     pass_gbs = fft_bytes / (fft_ms / 1000.0) / 1e9 if fft_ms > 0 else None
     if fp32:
-        # FP32 stages are memory-bound: report the FFT passes against HBM bandwidth
         peak, src = hbm_peak()
         roofline = {"bound": "hbm", "achieved": pass_gbs, "peak": peak, "unit": "GB/s",
                     "frac": (pass_gbs or 0.0) / peak, "traffic": None, "peak_source": src,
@@ -277,17 +337,31 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": "coeffs/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if fp32 else "f64", "data": "synthetic",
-        "config": {"workload": "dht0_N%d_eps%s_nrhs%d_plain" % (N, "+".join(args.eps.split(",")), nrhs),
-                   "N": N, "eps": eps_list, "nrhs": nrhs,
-                   "form": "plain per-request " + ("FP32 stages (eps >= 1e-5)" if fp32 else "FP64"),
+        "config": {"workload": "dht0_N%d_eps%s_batch%d" % (N, "+".join(args.eps.split(",")), B),
+                   "N": N, "eps": eps_list, "batch": B,
+                   "form": "served/batched: %d vectors per execution per plan, precision by eps (FP64 below 1e-5)"
+                           % B,
                    "l2": "flushed between timed steps (256 MB write)", "coefficients": "N(0,1) seeded"},
-        "per_eps": {str(e): {"ms": statistics.mean(m), "coeffs_per_s": N * nrhs / (statistics.mean(m) / 1000.0),
-                             "p50_ms": statistics.median(m), "p99_ms": max(m)}
-                    for e, m in zip(eps_list, eps_ms)},
+        "per_eps": {str(e): {"batch_ms": statistics.mean(m),
+                             "coeffs_per_s": N * B / (statistics.mean(m) / 1000.0),
+                             "plain_ms": statistics.mean(pm)}
+                    for e, m, pm in zip(eps_list, plan_ms, p_plan)},
+        "plain_fp64": {"coeffs_per_s": plain_cps, "ms_per_step": sum(p_step) / len(p_step),
+                       "form": "one vector per execution, every stage FP64"},
+        "served_over_plain": value / plain_cps,
         "stage_ms_per_step": stage_ms,
         "roofline": roofline,
-        "e2e": {"value": e2e_value, "unit": "coeffs/s", "h2d_bytes_per_step": len(plans) * N * nrhs * 8,
-                "d2h_bytes_per_step": len(plans) * N * nrhs * 8, "steps": e2e_steps},
+        "e2e": {"value": served_e2e, "unit": "coeffs/s", "h2d_bytes_per_step": coeffs_per_step * 8,
+                "d2h_bytes_per_step": coeffs_per_step * 8,
+                "form": "hankel_server, %d single-vector requests submitted at once, host arrays" % len(reqs),
+                "plain_value": plain_e2e},
+        "latency_ms": {"rate_per_s": rate, "requests": len(reqs),
+                       "served": {"p50": pct(served_lat, 50), "p99": pct(served_lat, 99),
+                                  "coeffs_per_s": served_cps_p},
+                       "plain": {"p50": pct(plain_lat, 50), "p99": pct(plain_lat, 99),
+                                 "coeffs_per_s": plain_cps_p},
+                       "saturated": {"served_p50": pct(served_sat_lat, 50), "served_p99": pct(served_sat_lat, 99),
+                                     "plain_p50": pct(plain_sat_lat, 50), "plain_p99": pct(plain_sat_lat, 99)}},
         "gpu_launches": launches,
         "clocks": clocks.summary(),
         "wall_s_timed": wall,

@@ -235,6 +235,62 @@ int hankel_destroy(hankel_plan_t p);
 /* Static, NUL-terminated description of a status code. Never NULL. */
 const char* hankel_status_string(int status);
 
+/* ---- Serving: a request loop over cached plans ----
+ *
+ * A server owns a dispatcher thread, a set of CUDA streams and a cache of plans keyed by
+ * (task, nu, N, eps). Requests carry host arrays of coefficients; the dispatcher admits them
+ * by device memory, packs the waiting requests of one plan (up to max_batch vectors) into
+ * one batched execution, and runs batches of different plans concurrently on its streams.
+ * A plan executes one batch at a time (it owns one workspace). Completed results are copied
+ * to the request's host output array and the request's latency (submit to completion) is
+ * recorded. This layer is a service around the paper's transform, not part of the paper. */
+typedef struct hankel_server_s* hankel_server_t;
+
+typedef struct {
+  size_t memory_cap;  /* device bytes the server's plans and buffers may hold (0 = 120 GiB) */
+  int streams;        /* CUDA streams, i.e. batches in flight at once (default 4, at most 16) */
+  int max_batch;      /* most coefficient vectors packed into one execution (default 64) */
+  int use_graphs;     /* 1: replay each (plan, batch size, stream) launch sequence from a captured CUDA graph */
+  int precision;      /* precision every plan is built with: HANKEL_PREC_AUTO (FP32 stages at eps >= 1e-5)
+                         or HANKEL_PREC_FP64 */
+} hankel_server_options;
+
+/* Statistics since the server was created. */
+typedef struct {
+  int64_t submitted, completed, failed;  /* requests */
+  int64_t batches;                       /* batched executions launched */
+  int64_t vectors;                       /* coefficient vectors transformed */
+  double coefficients;                   /* sum over completed requests of N * nrhs */
+  int64_t plans_built, plans_evicted;    /* plan cache activity */
+  int64_t graphs_captured;               /* CUDA graphs captured */
+  size_t device_bytes;                   /* device memory held now */
+} hankel_server_stats;
+
+/* Defaults: 120 GiB cap, 4 streams, batches of up to 64 vectors, no graphs, AUTO precision. */
+int hankel_server_options_default(hankel_server_options* o);
+
+/* Create a server on the current CUDA device and start its dispatcher. */
+int hankel_server_create(hankel_server_t* out, const hankel_server_options* o);
+
+/* Queue one request: nrhs vectors of N coefficients in host array c (row r at c + r*N) and the
+ * host output array f (same layout). Both must stay valid until the request completes. *ticket
+ * receives the request's id. Never blocks on the GPU. Errors: EINVAL (arguments), EUNSUPPORTED
+ * (a plan could not be built for these parameters, reported at completion as a failed request). */
+int hankel_server_submit(hankel_server_t s, int task, int nu, int64_t N, double eps, const double* c, double* f,
+                         int nrhs, int64_t* ticket);
+
+/* Block until request `ticket` completes. *status receives its hankel_status, *latency_ms the
+ * time from submission to completion (either pointer may be NULL). */
+int hankel_server_wait(hankel_server_t s, int64_t ticket, int* status, double* latency_ms);
+
+/* Block until every submitted request has completed. */
+int hankel_server_drain(hankel_server_t s);
+
+int hankel_server_get_stats(hankel_server_t s, hankel_server_stats* out);
+
+/* Stop the dispatcher after draining, and free every plan, stream and buffer. NULL is accepted. */
+int hankel_server_destroy(hankel_server_t s);
+
 /* ---- Host-only parameter formulas (no plan, no GPU) ---- */
 
 /* s_{nu,M}(eps): four fixed-point iterations from s = 1 (Section 3.1, Table 1). */

@@ -173,3 +173,67 @@ class Plan:
         st = self._lib.hankel_exec_host(self._h, c2.ctypes.data_as(dp), self.N, f.ctypes.data_as(dp), self.N, nrhs)
         _lib.check(st, "hankel_exec_host")
         return f[0] if (single and out is None) else f
+
+
+class Server:
+    """Request loop over cached plans (hankel_server_* of the C ABI).
+
+    ``submit`` queues nrhs coefficient vectors (numpy float64, host memory) and returns a
+    ticket; the library's dispatcher batches waiting requests of the same plan, runs batches
+    of different plans concurrently on its CUDA streams and writes each result into the array
+    ``submit`` returned. ``precision="fp64"`` builds every plan in FP64 (the plain form);
+    ``"auto"`` admits FP32 stages at eps >= 1e-5.
+    """
+
+    def __init__(self, streams=4, max_batch=64, use_graphs=False, precision="auto", memory_cap=0):
+        self._lib = _lib.load()
+        o = _lib.ServerOptions()
+        _lib.check(self._lib.hankel_server_options_default(ctypes.byref(o)), "hankel_server_options_default")
+        o.streams, o.max_batch, o.use_graphs = int(streams), int(max_batch), int(bool(use_graphs))
+        o.precision = PRECISIONS[precision]
+        if memory_cap:
+            o.memory_cap = int(memory_cap)
+        self._h = ctypes.c_void_p()
+        _lib.check(self._lib.hankel_server_create(ctypes.byref(self._h), ctypes.byref(o)), "hankel_server_create")
+        self._live = {}  # ticket -> (c, f) kept alive until completion
+
+    def submit(self, task, nu, N, eps, c):
+        """Queue c ((N,) or (nrhs, N) float64); returns (ticket, f) with f filled on completion."""
+        c = np.ascontiguousarray(c, dtype=np.float64)
+        c2 = c.reshape(1, -1) if c.ndim == 1 else c
+        f = np.empty_like(c2)
+        t = ctypes.c_int64()
+        dp = ctypes.POINTER(ctypes.c_double)
+        _lib.check(self._lib.hankel_server_submit(self._h, TASKS[task], int(nu), int(N), float(eps),
+                                                  c2.ctypes.data_as(dp), f.ctypes.data_as(dp), c2.shape[0],
+                                                  ctypes.byref(t)), "hankel_server_submit")
+        self._live[t.value] = (c2, f)
+        return t.value, (f[0] if c.ndim == 1 else f)
+
+    def wait(self, ticket):
+        """Block until `ticket` completes; returns its latency in ms. Raises if the request failed."""
+        st = ctypes.c_int()
+        lat = ctypes.c_double()
+        _lib.check(self._lib.hankel_server_wait(self._h, int(ticket), ctypes.byref(st), ctypes.byref(lat)),
+                   "hankel_server_wait")
+        self._live.pop(int(ticket), None)
+        _lib.check(st.value, "request %d" % ticket)
+        return lat.value
+
+    def drain(self):
+        _lib.check(self._lib.hankel_server_drain(self._h), "hankel_server_drain")
+
+    def stats(self):
+        out = _lib.ServerStats()
+        _lib.check(self._lib.hankel_server_get_stats(self._h, ctypes.byref(out)), "hankel_server_get_stats")
+        return out.as_dict()
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self._lib.hankel_server_destroy(h)
+            self._h = ctypes.c_void_p()
+            self._live.clear()
+
+    def __del__(self):
+        self.close()

@@ -20,6 +20,8 @@ EXPORTED = [
     "hankel_plan_near_prefix", "hankel_destroy", "hankel_status_string", "hankel_s_nu_M",
     "hankel_t_nu_T", "hankel_neumann_radius", "hankel_p_K", "hankel_q_T", "hankel_params",
     "hankel_j0_zero_offsets", "hankel_plan_set_timing", "hankel_plan_stage_stats", "hankel_exec_static",
+    "hankel_server_options_default", "hankel_server_create", "hankel_server_submit", "hankel_server_wait",
+    "hankel_server_drain", "hankel_server_get_stats", "hankel_server_destroy",
 ]
 STAGES = ["near", "gen", "fft", "pointwise", "out"]
 
@@ -48,6 +50,21 @@ class Info(ctypes.Structure):
 class StageStat(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double), ("flops", ctypes.c_double), ("entries", ctypes.c_double),
                 ("bytes", ctypes.c_double), ("launches", ctypes.c_int64)]
+
+
+class ServerOptions(ctypes.Structure):
+    _fields_ = [("memory_cap", ctypes.c_size_t), ("streams", ctypes.c_int), ("max_batch", ctypes.c_int),
+                ("use_graphs", ctypes.c_int), ("precision", ctypes.c_int)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("batches", ctypes.c_int64), ("vectors", ctypes.c_int64), ("coefficients", ctypes.c_double),
+                ("plans_built", ctypes.c_int64), ("plans_evicted", ctypes.c_int64),
+                ("graphs_captured", ctypes.c_int64), ("device_bytes", ctypes.c_size_t)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
 
 
 class Block(ctypes.Structure):
@@ -88,6 +105,13 @@ def load():
         "hankel_j0_zero_offsets": (i32, [i64, dp]),
         "hankel_plan_set_timing": (i32, [vp, i32]),
         "hankel_exec_static": (i32, [vp, vp, vp, vp]),
+        "hankel_server_options_default": (i32, [ctypes.POINTER(ServerOptions)]),
+        "hankel_server_create": (i32, [pplan, ctypes.POINTER(ServerOptions)]),
+        "hankel_server_submit": (i32, [vp, i32, i32, i64, dbl, dp, dp, i32, ctypes.POINTER(i64)]),
+        "hankel_server_wait": (i32, [vp, i64, ctypes.POINTER(i32), ctypes.POINTER(dbl)]),
+        "hankel_server_drain": (i32, [vp]),
+        "hankel_server_get_stats": (i32, [vp, ctypes.POINTER(ServerStats)]),
+        "hankel_server_destroy": (i32, [vp]),
         "hankel_plan_stage_stats": (i32, [vp, ctypes.POINTER(StageStat)]),
     }
     for name, (res, args) in sig.items():

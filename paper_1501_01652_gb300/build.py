@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(OUT_DIR, "libhankel.so")
-HOST_SOURCES = ["api.cpp", "planner.cpp"]
+HOST_SOURCES = ["api.cpp", "planner.cpp", "server.cpp"]
 CUDA_SOURCES = ["exec.cu", "fft.cu", "far.cu", "near.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
@@ -60,7 +60,7 @@ def build(force=False, verbose=False):
     with concurrent.futures.ThreadPoolExecutor(max_workers=len(srcs)) as ex:
         objs = list(ex.map(_compile, srcs))
     tmp = LIB_PATH + ".tmp.%d" % os.getpid()
-    cmd = [_nvcc(), ARCH, "-shared", "-o", tmp] + objs
+    cmd = [_nvcc(), ARCH, "-shared", "-o", tmp] + objs + ["-lpthread"]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError("link failed: %s\n%s" % (res.stdout, res.stderr))

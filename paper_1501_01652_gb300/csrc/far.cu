@@ -112,21 +112,37 @@ __global__ void __launch_bounds__(256) k_out(OutArgs a) {
   a.f[(int64_t)cur * a.ldf + i] += fma(wu.x, ar, -wu.y * ai);
 }
 
+// Overlap-add of column segments: out[cc][t] = sum_s in[cc*nseg + s][t] H[s][t]. A CTA covers
+// kMacPts consecutive points of one column; its kMacLanes thread rows split the segments
+// (s = lane, lane + kMacLanes, ...) and the partial sums are added in a fixed order.
+constexpr int kMacPts = 32, kMacLanes = 8;
+
 template <class C>
-__global__ void k_seg_mac(const C* __restrict__ in, const C* __restrict__ H, C* __restrict__ out, int64_t F,
-                          int64_t nseg, int64_t total) {
+__global__ void __launch_bounds__(kMacPts* kMacLanes) k_seg_mac(const C* __restrict__ in, const C* __restrict__ H,
+                                                                 C* __restrict__ out, int64_t F, int64_t nseg) {
   typedef typename RealOf<C>::type R;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t cc = e / F, t = e - cc * F;
-    const C* x = in + cc * nseg * F + t;
-    R ar = 0, ai = 0;
-    for (int64_t s = 0; s < nseg; ++s) {
-      const C v = x[s * F];
-      const C h = __ldg(&H[s * F + t]);
-      ar = fmar(v.x, h.x, fmar(-v.y, h.y, ar));
-      ai = fmar(v.x, h.y, fmar(v.y, h.x, ai));
+  __shared__ R sr[kMacLanes][kMacPts], si[kMacLanes][kMacPts];
+  const int pt = threadIdx.x % kMacPts, lane = threadIdx.x / kMacPts;
+  const int64_t tiles = F / kMacPts;
+  const int64_t cc = blockIdx.x / tiles;
+  const int64_t t = (blockIdx.x - cc * tiles) * kMacPts + pt;
+  const C* x = in + cc * nseg * F + t;
+  R ar = 0, ai = 0;
+  for (int64_t s = lane; s < nseg; s += kMacLanes) {
+    const C v = x[s * F];
+    const C h = __ldg(&H[s * F + t]);
+    ar = fmar(v.x, h.x, fmar(-v.y, h.y, ar));
+    ai = fmar(v.x, h.y, fmar(v.y, h.x, ai));
+  }
+  sr[lane][pt] = ar;
+  si[lane][pt] = ai;
+  __syncthreads();
+  if (lane == 0) {
+    for (int j = 1; j < kMacLanes; ++j) {
+      ar += sr[j][pt];
+      ai += si[j][pt];
     }
-    out[e] = mkc(ar, ai);
+    out[cc * F + t] = mkc(ar, ai);
   }
 }
 
@@ -182,8 +198,9 @@ void launch_gen(const GenArgs& a, cudaStream_t st) {
 
 template <class C>
 void launch_seg_mac(const C* in, const C* H, C* out, int64_t F, int64_t nseg, int nc, cudaStream_t st) {
-  const int64_t total = F * nc;
-  k_seg_mac<C><<<grid1d(total), 256, 0, st>>>(in, H, out, F, nseg, total);
+  // F >= 64 is a multiple of kMacPts
+  const int64_t blocks = (F / kMacPts) * nc;
+  k_seg_mac<C><<<(unsigned)blocks, kMacPts * kMacLanes, 0, st>>>(in, H, out, F, nseg);
 }
 
 template <class C>

@@ -1,0 +1,470 @@
+// Request loop over cached plans (hankel_server_* in include/hankel.h).
+//
+// One dispatcher thread owns every plan, stream and staging buffer. submit() only appends to
+// the request table and the queue under the lock; the dispatcher
+//  1. retires finished batches (event query), copies results to the callers' host arrays and
+//     records each request's latency;
+//  2. fills idle streams: it takes the oldest queued request whose plan is idle, gathers the
+//     queued requests of the same plan (FIFO, up to max_batch vectors), builds the plan if it
+//     is not cached (evicting idle plans, least recently used first, while the device memory
+//     held exceeds the cap), packs the coefficients into the stream's pinned buffer and issues
+//     copy-in, batched execution and copy-out on the stream (or replays them from a captured
+//     CUDA graph).
+#include <cuda_runtime_api.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <tuple>
+#include <vector>
+
+#include "hankel.h"
+
+namespace {
+
+typedef std::chrono::steady_clock Clock;
+typedef std::tuple<int, int, int64_t, double> Key;  // task, nu, N, eps
+
+constexpr size_t kDefaultCap = size_t(120) << 30;
+constexpr size_t kPlanWorkspace = size_t(1) << 30;
+
+struct Request {
+  Key key;
+  const double* c;
+  double* f;
+  int nrhs;
+  Clock::time_point t_submit, t_done;
+  int status = HANKEL_OK;
+  bool done = false;
+};
+
+struct PlanEntry {
+  hankel_plan_t plan = nullptr;
+  size_t bytes = 0;
+  bool busy = false;
+  int64_t runs = 0;
+  uint64_t last_used = 0;
+  std::map<std::pair<int, int>, cudaGraphExec_t> graphs;  // (stream slot, nrhs) -> graph
+};
+
+// A request as the dispatcher carries it through a batch (copied under the lock).
+struct Item {
+  int64_t ticket;
+  const double* c;
+  double* f;
+  int nrhs;
+};
+
+struct Slot {
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+  double* c_pin = nullptr;
+  double* f_pin = nullptr;
+  double* c_dev = nullptr;
+  double* f_dev = nullptr;
+  size_t cap = 0;  // doubles in each buffer
+  bool busy = false;
+  std::vector<Item> items;
+  Key key;
+  int64_t N = 0;
+};
+
+}  // namespace
+
+struct hankel_server_s {
+  hankel_server_options opt;
+  int device = 0;
+  std::thread worker;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<Request> reqs;   // indexed by ticket
+  std::deque<int64_t> queue;  // tickets waiting for dispatch
+  int64_t outstanding = 0;    // submitted but not completed
+  bool stop = false;
+  hankel_server_stats stats{};
+  // dispatcher-owned
+  std::map<Key, PlanEntry> plans;
+  std::vector<Slot> slots;
+  uint64_t tick = 0;
+  size_t plan_bytes = 0, slot_bytes = 0;
+};
+
+namespace {
+
+void drop_slot_graphs(hankel_server_s* s, int slot) {
+  for (auto& kv : s->plans) {
+    for (auto it = kv.second.graphs.begin(); it != kv.second.graphs.end();) {
+      if (it->first.first == slot) {
+        cudaGraphExecDestroy(it->second);
+        it = kv.second.graphs.erase(it);
+      } else {
+        ++it;
+      }
+    }
+  }
+}
+
+void free_slot_buffers(Slot& sl) {
+  if (sl.c_pin) cudaFreeHost(sl.c_pin);
+  if (sl.f_pin) cudaFreeHost(sl.f_pin);
+  if (sl.c_dev) cudaFree(sl.c_dev);
+  if (sl.f_dev) cudaFree(sl.f_dev);
+  sl.c_pin = sl.f_pin = sl.c_dev = sl.f_dev = nullptr;
+  sl.cap = 0;
+}
+
+int ensure_slot_capacity(hankel_server_s* s, int i, size_t need) {
+  Slot& sl = s->slots[i];
+  if (sl.cap >= need) return HANKEL_OK;
+  drop_slot_graphs(s, i);
+  s->slot_bytes -= 2 * sl.cap * sizeof(double);
+  free_slot_buffers(sl);
+  size_t cap = std::max(need, size_t(1) << 16);
+  if (cudaMallocHost((void**)&sl.c_pin, cap * sizeof(double)) != cudaSuccess ||
+      cudaMallocHost((void**)&sl.f_pin, cap * sizeof(double)) != cudaSuccess ||
+      cudaMalloc((void**)&sl.c_dev, cap * sizeof(double)) != cudaSuccess ||
+      cudaMalloc((void**)&sl.f_dev, cap * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    free_slot_buffers(sl);
+    return HANKEL_ENOMEM;
+  }
+  sl.cap = cap;
+  s->slot_bytes += 2 * cap * sizeof(double);
+  return HANKEL_OK;
+}
+
+void destroy_plan(hankel_server_s* s, PlanEntry& pe) {
+  for (auto& g : pe.graphs) cudaGraphExecDestroy(g.second);
+  pe.graphs.clear();
+  hankel_destroy(pe.plan);
+  s->plan_bytes -= pe.bytes;
+  pe.plan = nullptr;
+}
+
+// Cached plan for key, built on a miss; idle plans are evicted (LRU) while over the cap.
+int get_plan(hankel_server_s* s, const Key& key, PlanEntry** out) {
+  auto it = s->plans.find(key);
+  if (it == s->plans.end()) {
+    hankel_options o;
+    hankel_options_default(&o, std::get<0>(key), std::get<1>(key), std::get<2>(key), std::get<3>(key));
+    o.max_nrhs = s->opt.max_batch;
+    o.precision = s->opt.precision;
+    o.workspace_limit = kPlanWorkspace;
+    hankel_plan_t p = nullptr;
+    int st = hankel_plan_ex(&p, &o);
+    if (st != HANKEL_OK) return st;
+    hankel_info info;
+    hankel_plan_info(p, &info);
+    PlanEntry pe;
+    pe.plan = p;
+    pe.bytes = info.device_bytes;
+    s->plan_bytes += pe.bytes;
+    it = s->plans.emplace(key, pe).first;
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stats.plans_built++;
+  }
+  it->second.last_used = ++s->tick;
+  const size_t cap = s->opt.memory_cap;
+  while (s->plan_bytes + s->slot_bytes > cap) {
+    auto victim = s->plans.end();
+    for (auto jt = s->plans.begin(); jt != s->plans.end(); ++jt)
+      if (jt != it && !jt->second.busy && (victim == s->plans.end() || jt->second.last_used < victim->second.last_used))
+        victim = jt;
+    if (victim == s->plans.end()) break;  // only busy plans left: admit and let them retire
+    destroy_plan(s, victim->second);
+    s->plans.erase(victim);
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stats.plans_evicted++;
+  }
+  *out = &it->second;
+  return HANKEL_OK;
+}
+
+// Issue copy-in, execution and copy-out of a packed batch on slot i.
+int launch_batch(hankel_server_s* s, int i, PlanEntry& pe, int64_t N, int nrhs) {
+  Slot& sl = s->slots[i];
+  const size_t bytes = (size_t)N * nrhs * sizeof(double);
+  auto direct = [&]() -> int {
+    if (cudaMemcpyAsync(sl.c_dev, sl.c_pin, bytes, cudaMemcpyHostToDevice, sl.stream) != cudaSuccess)
+      return HANKEL_ECUDA;
+    int st = hankel_exec_batched(pe.plan, sl.c_dev, N, sl.f_dev, N, nrhs, sl.stream);
+    if (st != HANKEL_OK) return st;
+    if (cudaMemcpyAsync(sl.f_pin, sl.f_dev, bytes, cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess)
+      return HANKEL_ECUDA;
+    return HANKEL_OK;
+  };
+  if (!s->opt.use_graphs || pe.runs == 0) return direct();  // first run configures kernels uncaptured
+  auto key = std::make_pair(i, nrhs);
+  auto it = pe.graphs.find(key);
+  if (it == pe.graphs.end()) {
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(sl.stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return HANKEL_ECUDA;
+    int st = direct();
+    cudaError_t e = cudaStreamEndCapture(sl.stream, &g);
+    if (st != HANKEL_OK || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return st != HANKEL_OK ? st : HANKEL_ECUDA;
+    }
+    cudaGraphExec_t ge = nullptr;
+    e = cudaGraphInstantiate(&ge, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return HANKEL_ECUDA;
+    it = pe.graphs.emplace(key, ge).first;
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stats.graphs_captured++;
+  }
+  return cudaGraphLaunch(it->second, sl.stream) == cudaSuccess ? HANKEL_OK : HANKEL_ECUDA;
+}
+
+void finish(hankel_server_s* s, const std::vector<Item>& items, int status) {
+  std::lock_guard<std::mutex> lk(s->mu);
+  const auto now = Clock::now();
+  for (const Item& it : items) {
+    Request& r = s->reqs[it.ticket];
+    r.done = true;
+    r.status = status;
+    r.t_done = now;
+    s->outstanding--;
+    if (status == HANKEL_OK) {
+      s->stats.completed++;
+      s->stats.coefficients += (double)std::get<2>(r.key) * r.nrhs;
+    } else {
+      s->stats.failed++;
+    }
+  }
+  s->cv_done.notify_all();
+}
+
+// Retire finished batches. Returns true if any finished.
+bool retire(hankel_server_s* s) {
+  bool any = false;
+  for (size_t i = 0; i < s->slots.size(); ++i) {
+    Slot& sl = s->slots[i];
+    if (!sl.busy) continue;
+    cudaError_t q = cudaEventQuery(sl.done);
+    if (q == cudaErrorNotReady) continue;
+    int status = q == cudaSuccess ? HANKEL_OK : HANKEL_ECUDA;
+    if (status == HANKEL_OK) {
+      size_t off = 0;
+      for (const Item& it : sl.items) {
+        memcpy(it.f, sl.f_pin + off, (size_t)sl.N * it.nrhs * sizeof(double));
+        off += (size_t)sl.N * it.nrhs;
+      }
+    }
+    auto pit = s->plans.find(sl.key);
+    if (pit != s->plans.end()) pit->second.busy = false;
+    finish(s, sl.items, status);
+    sl.items.clear();
+    sl.busy = false;
+    any = true;
+  }
+  return any;
+}
+
+// Fill one idle slot. Returns true if a batch was dispatched.
+bool dispatch(hankel_server_s* s, int i) {
+  std::vector<Item> batch;
+  Key key;
+  int nrhs = 0;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto busy = [&](const Key& k) {
+      auto it = s->plans.find(k);
+      return it != s->plans.end() && it->second.busy;
+    };
+    auto q = s->queue.begin();
+    while (q != s->queue.end() && busy(s->reqs[*q].key)) ++q;
+    if (q == s->queue.end()) return false;
+    key = s->reqs[*q].key;
+    for (auto it = s->queue.begin(); it != s->queue.end();) {
+      const Request& r = s->reqs[*it];
+      if (r.key == key && nrhs + r.nrhs <= s->opt.max_batch) {
+        nrhs += r.nrhs;
+        batch.push_back(Item{*it, r.c, r.f, r.nrhs});
+        it = s->queue.erase(it);
+      } else {
+        ++it;
+      }
+    }
+  }
+  PlanEntry* pe = nullptr;
+  int st = get_plan(s, key, &pe);
+  const int64_t N = std::get<2>(key);
+  if (st == HANKEL_OK) st = ensure_slot_capacity(s, i, (size_t)N * nrhs);
+  if (st != HANKEL_OK) {
+    finish(s, batch, st);
+    return true;
+  }
+  Slot& sl = s->slots[i];
+  size_t off = 0;
+  for (const Item& it : batch) {
+    memcpy(sl.c_pin + off, it.c, (size_t)N * it.nrhs * sizeof(double));
+    off += (size_t)N * it.nrhs;
+  }
+  st = launch_batch(s, i, *pe, N, nrhs);
+  if (st == HANKEL_OK && cudaEventRecord(sl.done, sl.stream) != cudaSuccess) st = HANKEL_ECUDA;
+  if (st != HANKEL_OK) {
+    cudaStreamSynchronize(sl.stream);
+    cudaGetLastError();
+    finish(s, batch, st);
+    return true;
+  }
+  pe->busy = true;
+  pe->runs++;
+  sl.busy = true;
+  sl.items = batch;
+  sl.key = key;
+  sl.N = N;
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->stats.batches++;
+  s->stats.vectors += nrhs;
+  return true;
+}
+
+void run(hankel_server_s* s) {
+  cudaSetDevice(s->device);
+  for (;;) {
+    bool progressed = retire(s);
+    for (size_t i = 0; i < s->slots.size(); ++i)
+      if (!s->slots[i].busy && dispatch(s, (int)i)) progressed = true;
+    bool inflight = false;
+    for (const Slot& sl : s->slots) inflight |= sl.busy;
+    std::unique_lock<std::mutex> lk(s->mu);
+    if (s->stop && s->queue.empty() && !inflight) break;
+    if (progressed) continue;
+    if (inflight) {
+      // batches are running: poll their events again shortly, or sooner if work arrives
+      s->cv_work.wait_for(lk, std::chrono::microseconds(20));
+    } else {
+      s->cv_work.wait(lk, [&] { return s->stop || !s->queue.empty(); });
+    }
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+int hankel_server_options_default(hankel_server_options* o) {
+  if (!o) return HANKEL_EINVAL;
+  memset(o, 0, sizeof(*o));
+  o->memory_cap = kDefaultCap;
+  o->streams = 4;
+  o->max_batch = 64;
+  o->use_graphs = 0;
+  o->precision = HANKEL_PREC_AUTO;
+  return HANKEL_OK;
+}
+
+int hankel_server_create(hankel_server_t* out, const hankel_server_options* o) {
+  if (!out) return HANKEL_EINVAL;
+  *out = nullptr;
+  hankel_server_options opt;
+  hankel_server_options_default(&opt);
+  if (o) opt = *o;
+  if (opt.memory_cap == 0) opt.memory_cap = kDefaultCap;
+  if (opt.streams < 1 || opt.streams > 16 || opt.max_batch < 1) return HANKEL_EINVAL;
+  if (opt.precision != HANKEL_PREC_AUTO && opt.precision != HANKEL_PREC_FP64) return HANKEL_EINVAL;
+  hankel_server_s* s = new hankel_server_s();
+  s->opt = opt;
+  if (cudaGetDevice(&s->device) != cudaSuccess) {
+    delete s;
+    return HANKEL_ECUDA;
+  }
+  s->slots.resize(opt.streams);
+  for (Slot& sl : s->slots) {
+    if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      for (Slot& t : s->slots) {
+        if (t.stream) cudaStreamDestroy(t.stream);
+        if (t.done) cudaEventDestroy(t.done);
+      }
+      delete s;
+      return HANKEL_ECUDA;
+    }
+  }
+  s->worker = std::thread(run, s);
+  *out = s;
+  return HANKEL_OK;
+}
+
+int hankel_server_submit(hankel_server_t s, int task, int nu, int64_t N, double eps, const double* c, double* f,
+                         int nrhs, int64_t* ticket) {
+  if (!s || !c || !f || !ticket || nrhs < 1 || nrhs > s->opt.max_batch || N < 2) return HANKEL_EINVAL;
+  hankel_options o;
+  hankel_options_default(&o, task, nu, N, eps);
+  o.precision = s->opt.precision;
+  hankel_info info;
+  int st = hankel_params(&o, &info);  // reject bad parameters now, without a GPU round trip
+  if (st != HANKEL_OK) return st;
+  std::lock_guard<std::mutex> lk(s->mu);
+  Request r;
+  r.key = Key(task, nu, N, eps);
+  r.c = c;
+  r.f = f;
+  r.nrhs = nrhs;
+  r.t_submit = Clock::now();
+  s->reqs.push_back(r);
+  *ticket = (int64_t)s->reqs.size() - 1;
+  s->queue.push_back(*ticket);
+  s->outstanding++;
+  s->stats.submitted++;
+  s->cv_work.notify_one();
+  return HANKEL_OK;
+}
+
+int hankel_server_wait(hankel_server_t s, int64_t ticket, int* status, double* latency_ms) {
+  if (!s) return HANKEL_EINVAL;
+  std::unique_lock<std::mutex> lk(s->mu);
+  if (ticket < 0 || ticket >= (int64_t)s->reqs.size()) return HANKEL_EINVAL;
+  s->cv_done.wait(lk, [&] { return s->reqs[ticket].done; });
+  const Request& r = s->reqs[ticket];
+  if (status) *status = r.status;
+  if (latency_ms) *latency_ms = std::chrono::duration<double, std::milli>(r.t_done - r.t_submit).count();
+  return HANKEL_OK;
+}
+
+int hankel_server_drain(hankel_server_t s) {
+  if (!s) return HANKEL_EINVAL;
+  std::unique_lock<std::mutex> lk(s->mu);
+  s->cv_done.wait(lk, [&] { return s->outstanding == 0; });
+  return HANKEL_OK;
+}
+
+int hankel_server_get_stats(hankel_server_t s, hankel_server_stats* out) {
+  if (!s || !out) return HANKEL_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  *out = s->stats;
+  out->device_bytes = s->plan_bytes + s->slot_bytes;
+  return HANKEL_OK;
+}
+
+int hankel_server_destroy(hankel_server_t s) {
+  if (!s) return HANKEL_OK;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+    s->cv_work.notify_all();
+  }
+  s->worker.join();
+  cudaSetDevice(s->device);
+  for (auto& kv : s->plans) destroy_plan(s, kv.second);
+  s->plans.clear();
+  for (Slot& sl : s->slots) {
+    cudaStreamSynchronize(sl.stream);
+    free_slot_buffers(sl);
+    cudaStreamDestroy(sl.stream);
+    cudaEventDestroy(sl.done);
+  }
+  delete s;
+  return HANKEL_OK;
+}
+
+}  // extern "C"
