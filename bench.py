@@ -54,6 +54,12 @@ def parse_args():
     ap.add_argument("--eps", default="1e-15,1e-8")
     ap.add_argument("--cpu-rows", type=int, default=1024, help="oracle rows per sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", default="dht", choices=["dht", "mix"], help="mix: the serving-mix workload")
+    ap.add_argument("--mix-requests", type=int, default=150)
+    ap.add_argument("--mix-rate", type=float, default=100.0, help="Poisson arrivals per second")
+    ap.add_argument("--mix-nmin", type=int, default=10)
+    ap.add_argument("--mix-nmax", type=int, default=16)
+    ap.add_argument("--mix-vmax", type=int, default=64)
     return ap.parse_args()
 
 
@@ -172,6 +178,19 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def aggregate(world, coeffs_per_step, steps, total_ms, device):
+    """Whole-job throughput of `world` replicas: the slowest rank's summed step time over
+    every rank's coefficients. Returns (value, max_total_ms)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return world * coeffs_per_step * steps / (total_ms / 1000.0), total_ms
+
+
 def timed_steps(plans, c, fs, stream, steps, warmup, flush, timing):
     """Warm up, then time `steps` steps (each: every plan once) with CUDA events on `stream`.
 
@@ -280,13 +299,8 @@ def run_ours(args):
         wall = time.perf_counter() - wall0
     if world > 1:
         torch.distributed.barrier()
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
     coeffs_per_step = len(plans) * N * B
-    value = world * coeffs_per_step * args.steps / (total_ms / 1000.0)
+    value, total_ms = aggregate(world, coeffs_per_step, args.steps, sum(step_ms), dev)
 
     # dominant kernel: the FFT passes
     fft_ms = sum(st["fft"]["ms"] for st in stats)
@@ -307,7 +321,7 @@ def run_ours(args):
         e = eps_list[i % len(eps_list)]
         reqs.append((e, coefficients("normal", N, 1, seed_for(4, 200 + i))[0]))
     served_kw = dict(streams=4, max_batch=B, use_graphs=True, precision="auto")
-    plain_kw = dict(streams=1, max_batch=1, use_graphs=False, precision="fp64")
+    plain_kw = dict(streams=1, max_batch=1, use_graphs=False, precision="fp64", pack=False)
     served_e2e, served_sat_lat = serve_stream(hk, served_kw, reqs, 0.0, 1)
     plain_e2e, plain_sat_lat = serve_stream(hk, plain_kw, reqs, 0.0, 1)
     rate = args.rate if args.rate > 0 else 0.7 * plain_e2e / N  # 70 % of the plain form's capacity
@@ -373,10 +387,83 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+MIX_TASKS = [("schlomilch", 0), ("schlomilch", 1), ("fourier_bessel", 0), ("dht", 0)]
+MIX_EPS = [1e-15, 1e-8, 1e-4]
+
+
+def mix_requests(args):
+    """Seeded serving mix: task uniform over MIX_TASKS, N = 2^k with k uniform in
+    [mix_nmin, mix_nmax] (log-uniform N), eps uniform over MIX_EPS, 1..mix_vmax vectors."""
+    rng = np.random.default_rng(seed_for(5, 0))
+    reqs = []
+    for i in range(args.mix_requests):
+        task, nu = MIX_TASKS[rng.integers(len(MIX_TASKS))]
+        N = 1 << int(rng.integers(args.mix_nmin, args.mix_nmax + 1))
+        eps = MIX_EPS[rng.integers(len(MIX_EPS))]
+        nv = int(rng.integers(1, args.mix_vmax + 1))
+        reqs.append((task, nu, N, eps, coefficients("uniform", N, nv, seed_for(5, 1 + i))))
+    return reqs
+
+
+def run_mix_stream(hk, server_kw, reqs, rate, seed):
+    srv = hk.Server(**server_kw)
+    seen = set()
+    for task, nu, N, eps, c in reqs:  # warm the plan cache: one small request per plan key
+        if (task, nu, N, eps) not in seen:
+            seen.add((task, nu, N, eps))
+            t, _ = srv.submit(task, nu, N, eps, c[:1])
+            srv.wait(t)
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / rate, size=len(reqs))
+    t0 = time.perf_counter()
+    due = t0
+    tickets = []
+    for (task, nu, N, eps, c), gap in zip(reqs, gaps):
+        due += gap
+        while time.perf_counter() < due:
+            time.sleep(min(0.0005, max(0.0, due - time.perf_counter())))
+        tickets.append(srv.submit(task, nu, N, eps, c)[0])
+    lat = [srv.wait(t) for t in tickets]
+    makespan = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    coeffs = sum(c.size for *_, c in reqs)
+    return {"coeffs_per_s": coeffs / makespan, "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99),
+            "makespan_s": makespan, "batches": st["batches"], "plans": st["plans_built"],
+            "graphs": st["graphs_captured"]}
+
+
+def run_mix(args):
+    """Serving mix through the request loop: served (batched, 4 streams, graphs, FP32 stages
+    where eps >= 1e-5) against plain (one request at a time, FP64), same arrival stream."""
+    import torch
+
+    import paper_1501_01652_gb300 as hk
+
+    torch.cuda.set_device(0)
+    reqs = mix_requests(args)
+    served = run_mix_stream(hk, dict(streams=4, max_batch=64, use_graphs=True, precision="auto"), reqs,
+                            args.mix_rate, 3)
+    plain = run_mix_stream(hk, dict(streams=1, max_batch=64, use_graphs=False, precision="fp64", pack=False), reqs,
+                           args.mix_rate, 3)
+    line = {"metric": "serving mix coeffs/s and p50/p99 ms, served vs plain FP64", "value": served["coeffs_per_s"],
+            "unit": "coeffs/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
+            "config": {"workload": "serving_mix", "requests": len(reqs), "rate_per_s": args.mix_rate,
+                       "N": "2^%d..2^%d log-uniform" % (args.mix_nmin, args.mix_nmax),
+                       "vectors_per_request": "1..%d" % args.mix_vmax, "eps": MIX_EPS,
+                       "tasks": ["%s-%d" % t for t in MIX_TASKS]},
+            "served": served, "plain_fp64": plain,
+            "served_over_plain": served["coeffs_per_s"] / plain["coeffs_per_s"],
+            "p99_ratio_plain_over_served": plain["p99_ms"] / served["p99_ms"]}
+    print(json.dumps(line))
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.mode == "mix":
+        run_mix(args)
     else:
         run_ours(args)
 

@@ -253,6 +253,7 @@ typedef struct {
   int use_graphs;     /* 1: replay each (plan, batch size, stream) launch sequence from a captured CUDA graph */
   int precision;      /* precision every plan is built with: HANKEL_PREC_AUTO (FP32 stages at eps >= 1e-5)
                          or HANKEL_PREC_FP64 */
+  int pack_requests;  /* 1: pack waiting requests of one plan into one execution; 0: one request each */
 } hankel_server_options;
 
 /* Statistics since the server was created. */
@@ -266,7 +267,7 @@ typedef struct {
   size_t device_bytes;                   /* device memory held now */
 } hankel_server_stats;
 
-/* Defaults: 120 GiB cap, 4 streams, batches of up to 64 vectors, no graphs, AUTO precision. */
+/* Defaults: 120 GiB cap, 4 streams, batches of up to 64 vectors, no graphs, AUTO precision, packing on. */
 int hankel_server_options_default(hankel_server_options* o);
 
 /* Create a server on the current CUDA device and start its dispatcher. */

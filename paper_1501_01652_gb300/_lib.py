@@ -54,7 +54,7 @@ class StageStat(ctypes.Structure):
 
 class ServerOptions(ctypes.Structure):
     _fields_ = [("memory_cap", ctypes.c_size_t), ("streams", ctypes.c_int), ("max_batch", ctypes.c_int),
-                ("use_graphs", ctypes.c_int), ("precision", ctypes.c_int)]
+                ("use_graphs", ctypes.c_int), ("precision", ctypes.c_int), ("pack_requests", ctypes.c_int)]
 
 
 class ServerStats(ctypes.Structure):

@@ -284,7 +284,7 @@ bool dispatch(hankel_server_s* s, int i) {
     key = s->reqs[*q].key;
     for (auto it = s->queue.begin(); it != s->queue.end();) {
       const Request& r = s->reqs[*it];
-      if (r.key == key && nrhs + r.nrhs <= s->opt.max_batch) {
+      if (r.key == key && nrhs + r.nrhs <= s->opt.max_batch && (s->opt.pack_requests || batch.empty())) {
         nrhs += r.nrhs;
         batch.push_back(Item{*it, r.c, r.f, r.nrhs});
         it = s->queue.erase(it);
@@ -359,6 +359,7 @@ int hankel_server_options_default(hankel_server_options* o) {
   o->max_batch = 64;
   o->use_graphs = 0;
   o->precision = HANKEL_PREC_AUTO;
+  o->pack_requests = 1;
   return HANKEL_OK;
 }
 

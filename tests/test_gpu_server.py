@@ -89,6 +89,16 @@ def test_plain_fp64_server_at_relaxed_eps():
     srv.close()
 
 
+def test_unpacked_server_runs_one_request_per_execution():
+    srv = hk.Server(streams=1, max_batch=8, pack=False)
+    c = coefficients("uniform", 2048, 1, 5)
+    tickets = [srv.submit("schlomilch", 0, 2048, 1e-8, c) for _ in range(6)]
+    for t, f in tickets:
+        srv.wait(t)
+    assert srv.stats()["batches"] == 6
+    srv.close()
+
+
 def test_rejects_invalid_requests():
     srv = hk.Server(streams=1)
     with pytest.raises(RuntimeError, match="EINVAL"):
