@@ -55,6 +55,7 @@ def parse_args():
     ap.add_argument("--cpu-rows", type=int, default=1024, help="oracle rows per sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="dht", choices=["dht", "mix"], help="mix: the serving-mix workload")
+    ap.add_argument("--quick", action="store_true", help="batched form only (no plain form, serving runs or CPU leg)")
     ap.add_argument("--mix-requests", type=int, default=150)
     ap.add_argument("--mix-rate", type=float, default=100.0, help="Poisson arrivals per second")
     ap.add_argument("--mix-nmin", type=int, default=10)
@@ -277,14 +278,16 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
 
     # plain form: one vector per execution, every stage FP64
-    c1_host = coefficients("normal", N, 1, seed_for(4, rank))
-    c1 = torch.from_numpy(c1_host).to(dev)
-    plain = [hk.Plan("dht", 0, N, e, precision="fp64") for e in eps_list]
-    f1 = [torch.empty((1, N), dtype=torch.float64, device=dev) for _ in plain]
-    p_step, p_plan, _ = timed_steps(plain, c1, f1, stream, max(1, args.steps), 1, flush, False)
-    plain_cps = len(plain) * N * len(p_step) / (sum(p_step) / 1000.0)
-    for p in plain:
-        p.destroy()
+    plain_cps, p_step, p_plan = None, [float("nan")], [[float("nan")] for _ in eps_list]
+    if not args.quick:
+        c1_host = coefficients("normal", N, 1, seed_for(4, rank))
+        c1 = torch.from_numpy(c1_host).to(dev)
+        plain = [hk.Plan("dht", 0, N, e, precision="fp64") for e in eps_list]
+        f1 = [torch.empty((1, N), dtype=torch.float64, device=dev) for _ in plain]
+        p_step, p_plan, _ = timed_steps(plain, c1, f1, stream, max(1, args.steps), 1, flush, False)
+        plain_cps = len(plain) * N * len(p_step) / (sum(p_step) / 1000.0)
+        for p in plain:
+            p.destroy()
 
     # served form: batches of B vectors per plan, precision chosen by eps (FP64 below 1e-5)
     cB_host = coefficients("normal", N, B, seed_for(4, 100 + rank))
@@ -322,11 +325,15 @@ def run_ours(args):
         reqs.append((e, coefficients("normal", N, 1, seed_for(4, 200 + i))[0]))
     served_kw = dict(streams=4, max_batch=B, use_graphs=True, precision="auto")
     plain_kw = dict(streams=1, max_batch=1, use_graphs=False, precision="fp64", pack=False)
-    served_e2e, served_sat_lat = serve_stream(hk, served_kw, reqs, 0.0, 1)
-    plain_e2e, plain_sat_lat = serve_stream(hk, plain_kw, reqs, 0.0, 1)
-    rate = args.rate if args.rate > 0 else 0.7 * plain_e2e / N  # 70 % of the plain form's capacity
-    served_cps_p, served_lat = serve_stream(hk, served_kw, reqs, rate, 2)
-    plain_cps_p, plain_lat = serve_stream(hk, plain_kw, reqs, rate, 2)
+    if args.quick:
+        served_e2e = plain_e2e = served_cps_p = plain_cps_p = rate = None
+        served_sat_lat = plain_sat_lat = served_lat = plain_lat = []
+    else:
+        served_e2e, served_sat_lat = serve_stream(hk, served_kw, reqs, 0.0, 1)
+        plain_e2e, plain_sat_lat = serve_stream(hk, plain_kw, reqs, 0.0, 1)
+        rate = args.rate if args.rate > 0 else 0.7 * plain_e2e / N  # 70 % of the plain form's capacity
+        served_cps_p, served_lat = serve_stream(hk, served_kw, reqs, rate, 2)
+        plain_cps_p, plain_lat = serve_stream(hk, plain_kw, reqs, rate, 2)
 
     pass_gbs = fft_bytes / (fft_ms / 1000.0) / 1e9 if fft_ms > 0 else None
     if fp32:
@@ -358,11 +365,11 @@ def run_ours(args):
                    "l2": "flushed between timed steps (256 MB write)", "coefficients": "N(0,1) seeded"},
         "per_eps": {str(e): {"batch_ms": statistics.mean(m),
                              "coeffs_per_s": N * B / (statistics.mean(m) / 1000.0),
-                             "plain_ms": statistics.mean(pm)}
+                             "plain_ms": statistics.mean(pm) if plain_cps else None}
                     for e, m, pm in zip(eps_list, plan_ms, p_plan)},
-        "plain_fp64": {"coeffs_per_s": plain_cps, "ms_per_step": sum(p_step) / len(p_step),
+        "plain_fp64": {"coeffs_per_s": plain_cps, "ms_per_step": (sum(p_step) / len(p_step)) if plain_cps else None,
                        "form": "one vector per execution, every stage FP64"},
-        "served_over_plain": value / plain_cps,
+        "served_over_plain": value / plain_cps if plain_cps else None,
         "stage_ms_per_step": stage_ms,
         "roofline": roofline,
         "e2e": {"value": served_e2e, "unit": "coeffs/s", "h2d_bytes_per_step": coeffs_per_step * 8,
@@ -380,7 +387,7 @@ def run_ours(args):
         "clocks": clocks.summary(),
         "wall_s_timed": wall,
     }
-    if world == 1 and not args.no_cpu_baseline:
+    if world == 1 and not args.no_cpu_baseline and not args.quick:
         line["cpu_baseline"] = cpu_baseline(N, args.cpu_rows, seed_for(4, 99))
     print(json.dumps(line))
     if world > 1:

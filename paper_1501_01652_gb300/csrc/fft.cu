@@ -17,10 +17,11 @@ namespace hk {
 namespace {
 
 constexpr int kTile = 16;
+constexpr int kRow = kTile + 1;  // padded shared-memory row (elements)
 constexpr int kFftThreads = 256;
 
 template <bool INV, class C>
-__device__ __forceinline__ C twiddle(const C* __restrict__ tw, int64_t idx) {
+__device__ __forceinline__ C twiddle(const C* __restrict__ tw, uint32_t idx) {
   C t = __ldg(&tw[idx]);
   if (INV) t.y = -t.y;
   return t;
@@ -67,30 +68,32 @@ __device__ __forceinline__ void bfly2(C& a0, C& a1, C w) {
   a0 = y0;
 }
 
-// R-point DFTs of kTile sequences held as a[e * kTile + i] (element e, sequence i), each
-// input e first multiplied by W_F^{pt[i] * e} (the pass twiddle; pt[i] = p*s of sequence i).
+// R-point DFTs of kTile sequences held as a[e * kRow + i] (element e, sequence i; rows padded
+// to kRow = kTile + 1 elements so that column-wise accesses do not hit one shared-memory bank),
+// each input e first multiplied by W_F^{pt[i] * e} (the pass twiddle; pt[i] = p*s of sequence i).
 // Decimation-in-time Stockham sub-steps of radix 2 (first, when log2 R is odd) and 4, with
 // stride s_k and sub-length n_k = R/s_k. The pass twiddle is never applied on its own: the
 // inputs e = qq + s_k (r pp + j) of a butterfly carry W_F^{pt (qq + s_k j)}; the common
 // factor W_F^{pt qq} moves to the butterfly's outputs (whose index is qq mod s_k again), and
 // W_F^{pt s_k j} joins the step's own twiddle W_{n_k}^{pp j} in one table lookup. At the last
 // step s_k = 1, so nothing is left over. Input j = 0 of every butterfly needs no twiddle.
+// Every index fits in 32 bits (F, Fmax <= 2^24).
 template <int LOGR, bool INV, class C>
-__device__ C* smem_dft(C* a, C* b, const C* __restrict__ tw, int logFmax, int logF, const int64_t* pt) {
+__device__ C* smem_dft(C* a, C* b, const C* __restrict__ tw, int logFmax, int logF, const uint32_t* pt) {
   constexpr int R = 1 << LOGR;
   const int fsh = logFmax - logF;
-  const int64_t fmask = (int64_t(1) << logFmax) - 1;
+  const uint32_t fmask = (1u << logFmax) - 1u;
   int logn = 0;  // log2 of the sub-length transformed so far
   if (LOGR & 1) {
     // radix-2 sub-step: n = 2, s = R/2, m = 1
     const int logs = LOGR - 1, s = 1 << logs;
-    for (int idx = threadIdx.x; idx < kTile * (R / 2); idx += blockDim.x) {
-      const int i = idx & (kTile - 1), q = idx / kTile;
-      C a0 = a[q * kTile + i], a1 = a[(q + s) * kTile + i];
+    for (uint32_t idx = threadIdx.x; idx < kTile * (R / 2); idx += blockDim.x) {
+      const uint32_t i = idx & (kTile - 1), q = idx / kTile;
+      C a0 = a[q * kRow + i], a1 = a[(q + s) * kRow + i];
       const C w = twiddle<INV>(tw, ((pt[i] << logs) << fsh) & fmask);
       bfly2(a0, a1, w);
-      b[q * kTile + i] = a0;
-      b[(q + s) * kTile + i] = a1;
+      b[q * kRow + i] = a0;
+      b[(q + s) * kRow + i] = a1;
     }
     __syncthreads();
     C* t = a; a = b; b = t;
@@ -98,23 +101,24 @@ __device__ C* smem_dft(C* a, C* b, const C* __restrict__ tw, int logFmax, int lo
   }
   while (logn < LOGR) {
     // radix-4 sub-step: sub-length n' = 4 * 2^logn, stride s = R / n', m = 2^logn
-    const int lognn = logn + 2, logs = LOGR - lognn, s = 1 << logs, m = 1 << logn;
-    for (int idx = threadIdx.x; idx < kTile * (R / 4); idx += blockDim.x) {
-      const int i = idx & (kTile - 1), bf = idx / kTile;
-      const int pp = bf >> logs, qq = bf & (s - 1);
-      const int e0 = qq + s * 4 * pp;  // inputs e0 + s*j, outputs qq + s*(pp + r m)
-      C a0 = a[(e0)*kTile + i], a1 = a[(e0 + s) * kTile + i];
-      C a2 = a[(e0 + 2 * s) * kTile + i], a3 = a[(e0 + 3 * s) * kTile + i];
+    const int lognn = logn + 2, logs = LOGR - lognn;
+    const uint32_t s = 1u << logs, m = 1u << logn;
+    for (uint32_t idx = threadIdx.x; idx < kTile * (R / 4); idx += blockDim.x) {
+      const uint32_t i = idx & (kTile - 1), bf = idx / kTile;
+      const uint32_t pp = bf >> logs, qq = bf & (s - 1);
+      const uint32_t e0 = qq + s * 4 * pp;  // inputs e0 + s*j, outputs qq + s*(pp + r m)
+      C a0 = a[e0 * kRow + i], a1 = a[(e0 + s) * kRow + i];
+      C a2 = a[(e0 + 2 * s) * kRow + i], a3 = a[(e0 + 3 * s) * kRow + i];
       // W_{n'}^{pp j} W_F^{pt s j} = W_{Fmax}^{j * base}
-      const int64_t base = ((int64_t)pp << (logFmax - lognn)) + ((pt[i] << logs) << fsh);
+      const uint32_t base = (pp << (logFmax - lognn)) + ((pt[i] << logs) << fsh);
       const C w1 = twiddle<INV>(tw, base & fmask);
       const C w2 = twiddle<INV>(tw, (2 * base) & fmask);
       const C w3 = twiddle<INV>(tw, (3 * base) & fmask);
       bfly4<INV>(a0, a1, a2, a3, w1, w2, w3);
-      b[(qq + s * pp) * kTile + i] = a0;
-      b[(qq + s * (pp + m)) * kTile + i] = a1;
-      b[(qq + s * (pp + 2 * m)) * kTile + i] = a2;
-      b[(qq + s * (pp + 3 * m)) * kTile + i] = a3;
+      b[(qq + s * pp) * kRow + i] = a0;
+      b[(qq + s * (pp + m)) * kRow + i] = a1;
+      b[(qq + s * (pp + 2 * m)) * kRow + i] = a2;
+      b[(qq + s * (pp + 3 * m)) * kRow + i] = a3;
     }
     __syncthreads();
     C* t = a; a = b; b = t;
@@ -132,46 +136,46 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_pass(const C* __restrict__ 
                                                           int logS, const C* __restrict__ tw, int logFmax) {
   constexpr int R = 1 << LOGR;
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  __shared__ int64_t pt[kTile];
+  __shared__ uint32_t pt[kTile];
   C* v = reinterpret_cast<C*>(sm_raw);
-  C* w = v + R * kTile;
-  const int64_t F = int64_t(1) << logF;
-  const int64_t FR = F >> LOGR;  // pairs per column, a multiple of kTile
-  const int64_t G0 = (int64_t)blockIdx.x * kTile;
-  const int64_t col = G0 / FR;
-  const int64_t pi0 = G0 - col * FR;
-  const C* x = src + col * F;
-  C* y = dst + col * F;
-  const int64_t s = int64_t(1) << logS;
+  C* w = v + R * kRow;
+  const int logFR = logF - LOGR;  // pairs per column (a multiple of kTile) = 2^logFR
+  const uint64_t G0 = (uint64_t)blockIdx.x * kTile;
+  const uint64_t col = G0 >> logFR;
+  const uint32_t pi0 = (uint32_t)(G0 & ((1ull << logFR) - 1));
+  const C* x = src + (col << logF);
+  C* y = dst + (col << logF);
+  const uint32_t s = 1u << logS;
   if (threadIdx.x < kTile) pt[threadIdx.x] = ((pi0 + threadIdx.x) >> logS) << logS;  // p * s
   if (s >= kTile) {
-    const int64_t p = pi0 >> logS, q0 = pi0 & (s - 1);
-    const int64_t base = q0 + s * R * p;
-    for (int idx = threadIdx.x; idx < R * kTile; idx += blockDim.x) {
-      const int i = idx & (kTile - 1), j = idx / kTile;
-      v[j * kTile + i] = x[base + i + s * j];
+    const uint32_t p = pi0 >> logS, q0 = pi0 & (s - 1);
+    const C* xb = x + q0 + ((p << LOGR) << logS);  // + s R p
+    for (uint32_t idx = threadIdx.x; idx < R * kTile; idx += blockDim.x) {
+      const uint32_t i = idx & (kTile - 1), j = idx / kTile;
+      v[j * kRow + i] = xb[i + (j << logS)];
     }
   } else {
-    const int64_t base = pi0 << LOGR;  // s R p0 with pi0 = s p0
-    for (int idx = threadIdx.x; idx < R * kTile; idx += blockDim.x) {
-      const int pl = idx >> (logS + LOGR);
-      const int rem = idx & ((int)(s << LOGR) - 1);
-      const int j = rem >> logS, q = rem & ((int)s - 1);
-      v[j * kTile + ((pl << logS) + q)] = x[base + idx];
+    const C* xb = x + (pi0 << LOGR);  // s R p0 with pi0 = s p0
+    const uint32_t srm = (s << LOGR) - 1;
+    for (uint32_t idx = threadIdx.x; idx < R * kTile; idx += blockDim.x) {
+      const uint32_t pl = idx >> (logS + LOGR), rem = idx & srm;
+      const uint32_t j = rem >> logS, q = rem & (s - 1);
+      v[j * kRow + ((pl << logS) + q)] = xb[idx];
     }
   }
   __syncthreads();
   const C* res = smem_dft<LOGR, INV>(v, w, tw, logFmax, logF, pt);
-  for (int idx = threadIdx.x; idx < R * kTile; idx += blockDim.x) {
-    const int i = idx & (kTile - 1), r = idx / kTile;
-    y[pi0 + i + (int64_t)r * FR] = res[r * kTile + i];
+  C* yb = y + pi0;
+  for (uint32_t idx = threadIdx.x; idx < R * kTile; idx += blockDim.x) {
+    const uint32_t i = idx & (kTile - 1), r = idx / kTile;
+    yb[i + (r << logFR)] = res[r * kRow + i];
   }
 }
 
 template <int LOGR, bool INV, class C>
 void launch_pass(const C* src, C* dst, int logF, int logS, int ncols, const C* tw, int logFmax, cudaStream_t st) {
   constexpr int R = 1 << LOGR;
-  const size_t smem = 2 * (size_t)R * kTile * sizeof(C);
+  const size_t smem = 2 * (size_t)R * kRow * sizeof(C);
   static bool configured = false;
   if (!configured) {
     cudaFuncSetAttribute(k_fft_pass<LOGR, INV, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
