@@ -38,6 +38,8 @@ struct DevBlock {
   void* H = nullptr;      // per segment: FFT_F of the chirp exp(-i pi (U-V)^2 / (2E)), times 1/F (plan precision)
   double* scale = nullptr;   // FP32 plans: per stacked column, power of two keeping generated values near 1
   double* iscale = nullptr;  // its inverse, applied to the row factors
+  float2* Tf = nullptr;      // FP32 plans with tables: [ncols][C] column factors x chirp x scale
+  float* Wf = nullptr;       // FP32 plans with tables: [ncols][R] row factors x iscale
   int64_t cap = 0;           // columns per chunk
 };
 
@@ -70,8 +72,9 @@ struct DevicePlan {
   size_t ws_elems = 0;
   double* c_stage = nullptr;
   double* f_stage = nullptr;
-  double2* T = nullptr;  // column factor table (or nullptr)
+  double2* T = nullptr;  // column factor table (or nullptr; FP32 plans keep per-block tables instead)
   double* W = nullptr;   // row factor table (or nullptr)
+  float* cf = nullptr;   // FP32 plans with per-block tables: the coefficients rounded to FP32 [max_nrhs][N]
   size_t bytes = 0;
   std::vector<void*> allocs;
   // stage statistics (hankel_plan_set_timing / hankel_plan_stage_stats)
@@ -101,6 +104,20 @@ int dalloc(DevicePlan* d, T** p, size_t count) {
   d->bytes += count * sizeof(T);
   *p = (T*)q;
   return HANKEL_OK;
+}
+
+// Releases one allocation made by dalloc.
+template <class T>
+void dfree(DevicePlan* d, T** p, size_t count) {
+  if (!*p) return;
+  for (size_t j = 0; j < d->allocs.size(); ++j)
+    if (d->allocs[j] == (void*)*p) {
+      cudaFree(*p);
+      d->allocs.erase(d->allocs.begin() + (long)j);
+      d->bytes -= std::max<size_t>(count, 1) * sizeof(T);
+      break;
+    }
+  *p = nullptr;
 }
 
 template <class T>
@@ -318,6 +335,12 @@ int dev_plan_create(hankel_plan_s* p) {
       }
       HK_TRY(upload(d, &db.scale, sc.data(), sc.size()));
       HK_TRY(upload(d, &db.iscale, isc.data(), isc.size()));
+      if (d->T) {
+        HK_TRY(dalloc(d, &db.Tf, (size_t)d->ncols * b.C));
+        HK_TRY(dalloc(d, &db.Wf, (size_t)d->ncols * b.R));
+        launch_block_tables_f32(d->T, d->W, N, d->ncols, b.n0, b.C, b.k0, b.R, db.scale, db.iscale, db.Tf, db.Wf, 0);
+        HK_LAUNCHED();
+      }
     } else {
       double2* h; HK_TRY(dalloc(d, &h, (size_t)b.nseg * b.F)); db.H = h;
     }
@@ -337,6 +360,14 @@ int dev_plan_create(hankel_plan_s* p) {
     if (d->fp32) launch_scale_copy<float2>(res, (float2*)d->blocks.back().H, b.nseg * b.F, 1.0 / (double)b.F, 0);
     else launch_scale_copy<double2>(res, (double2*)d->blocks.back().H, b.nseg * b.F, 1.0 / (double)b.F, 0);
     HK_LAUNCHED();
+  }
+
+  if (d->fp32 && d->T) {
+    // FP32 plans run from the per-block FP32 tables alone
+    if (cudaDeviceSynchronize() != cudaSuccess) return HANKEL_ECUDA;
+    dfree(d, &d->T, (size_t)d->ncols * N);
+    dfree(d, &d->W, (size_t)d->ncols * N);
+    HK_TRY(dalloc(d, &d->cf, (size_t)hp.opt.max_nrhs * N));
   }
 
   if (cudaDeviceSynchronize() != cudaSuccess) return HANKEL_ECUDA;
@@ -382,7 +413,7 @@ int run_block(DevicePlan* d, const DevBlock& db, const double* c, int64_t ldc, d
     {
       StageScope sc(d, HANKEL_STAGE_GEN, st, record);
       GenArgs ga{A, b.F, b.C, b.n0, rowseg ? b.S : b.C, rowseg ? b.nseg : 1, nc, c0, d->ncols, c, ldc,
-                 d->nodes, d->cols, db.wV, d->T, d->hpN, db.scale};
+                 d->nodes, d->cols, db.wV, d->T, d->hpN, db.scale, d->cf, d->hpN, db.Tf};
       launch_gen<C>(ga, st);
       HK_LAUNCHED();
       sc.done(1, 0.0, 0.0);
@@ -416,7 +447,7 @@ int run_block(DevicePlan* d, const DevBlock& db, const double* c, int64_t ldc, d
     {
       StageScope sc(d, HANKEL_STAGE_OUT, st, record);
       OutArgs oa{res2, b.F, b.R, b.k0, (rowseg ? b.S : b.C) - 1, colseg ? b.S : b.R, colseg ? b.nseg : 1,
-                 nc, c0, d->ncols, f, ldf, d->nodes, d->cols, db.wU, d->W, d->hpN, db.iscale};
+                 nc, c0, d->ncols, f, ldf, d->nodes, d->cols, db.wU, d->W, d->hpN, db.iscale, db.Wf};
       launch_out<C>(oa, st);
       HK_LAUNCHED();
       sc.done(1, 0.0, 0.0);
@@ -439,6 +470,12 @@ int run_all(DevicePlan* d, const HostPlan& hp, const double* c, int64_t ldc, dou
                           d->nodes.r_true, d->nodes.om_true, d->jtab, hp.jt_n, hp.jt_deg, st);
     HK_LAUNCHED();
     sc.done(d->nmrows > 0 ? 2 : 1, 0.0, (double)hp.near_count * nrhs);
+  }
+  if (d->cf && !d->blocks.empty()) {
+    StageScope sc(d, HANKEL_STAGE_GEN, st, record);
+    launch_coeffs_f32(c, ldc, d->cf, d->hpN, nrhs, st);
+    HK_LAUNCHED();
+    sc.done(1, 0.0, 0.0);
   }
   for (const DevBlock& db : d->blocks) {
     const int64_t cap = chunk_from_capacity

@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "cplx.cuh"
 #include "kernels.cuh"
@@ -27,48 +28,88 @@ __device__ __forceinline__ double ipow(double x, int e) {
   return r;
 }
 
+// One CTA row (blockIdx.y) per stacked column at a time, so the column's indices are derived
+// once per column; the threads of the row stride over the F points of the column.
 template <class C>
 __global__ void __launch_bounds__(256) k_gen(GenArgs a) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= a.F) return;
   const int64_t ncolumns = (int64_t)a.nc * a.nsegc;
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, dt = (int64_t)gridDim.x * blockDim.x;
   for (int64_t y = blockIdx.y; y < ncolumns; y += gridDim.y) {
     C* A = reinterpret_cast<C*>(a.A) + y * a.F;
     const int64_t cc = y / a.nsegc, sg = y - cc * a.nsegc;
-    const int64_t np = sg * a.S + t;  // column offset within the block
-    if (t >= a.S || np >= a.C) {
-      A[t] = from_d2<C>(make_double2(0.0, 0.0));
-      continue;
-    }
     const int64_t g = a.c0 + cc;
-    const int rhs = (int)(g / a.ncols);
-    const int l = (int)(g - (int64_t)rhs * a.ncols);
-    const int64_t i = a.n0 - 1 + np;
+    const int64_t rhs = g / a.ncols;
+    const int l = (int)(g - rhs * a.ncols);
+    const int64_t nlo = sg * a.S;                          // first column offset of this segment
+    const int64_t lim = min(a.S, a.C - nlo);               // points t < lim carry data, the rest is padding
+    const double* cr = a.c + rhs * a.ldc + (a.n0 - 1 + nlo);
+    const double sc = a.scale ? a.scale[l] : 1.0;
     if (a.T) {
-      double cv = a.c[(int64_t)rhs * a.ldc + i];
-      if (a.scale) cv *= a.scale[l];
-      const double2 x = a.T[(int64_t)l * a.N + i];
-      A[t] = from_d2<C>(make_double2(cv * x.x, cv * x.y));
+      const double2* tr = a.T + (int64_t)l * a.N + (a.n0 - 1 + nlo);
+      for (int64_t t = t0; t < a.F; t += dt) {
+        double2 v = make_double2(0.0, 0.0);
+        if (t < lim) {
+          const double cv = cr[t] * sc;
+          const double2 x = tr[t];
+          v = make_double2(cv * x.x, cv * x.y);
+        }
+        A[t] = from_d2<C>(v);
+      }
       continue;
     }
     const DevColSpec& cs = a.cols[l];
-    const double bt = a.nodes.betan[i];
-    double pr = cs.G[cs.nterm - 1].x, pim = cs.G[cs.nterm - 1].y;
-    for (int u = cs.nterm - 2; u >= 0; --u) {
-      pr = fma(pr, bt, cs.G[u].x);
-      pim = fma(pim, bt, cs.G[u].y);
-    }
     const int d = cs.delta;
-    double pw = a.nodes.rs_omt[i] * ipow(d >= 0 ? a.nodes.omt[i] : a.nodes.inv_omt[i], d >= 0 ? d : -d);
-    if (cs.u1) pw *= ipow(a.nodes.colpow[i], cs.u1);
-    double cv = a.c[(int64_t)rhs * a.ldc + i] * pw;
-    if (a.scale) cv *= a.scale[l];
-    const double xr = pr * cv, xi = pim * cv;
-    const double2 w = a.wV[np];
-    A[t] = from_d2<C>(make_double2(fma(xr, w.x, -xi * w.y), fma(xr, w.y, xi * w.x)));
+    for (int64_t t = t0; t < a.F; t += dt) {
+      if (t >= lim) {
+        A[t] = from_d2<C>(make_double2(0.0, 0.0));
+        continue;
+      }
+      const int64_t np = nlo + t;
+      const int64_t i = a.n0 - 1 + np;
+      const double bt = a.nodes.betan[i];
+      double pr = cs.G[cs.nterm - 1].x, pim = cs.G[cs.nterm - 1].y;
+      for (int u = cs.nterm - 2; u >= 0; --u) {
+        pr = fma(pr, bt, cs.G[u].x);
+        pim = fma(pim, bt, cs.G[u].y);
+      }
+      double pw = a.nodes.rs_omt[i] * ipow(d >= 0 ? a.nodes.omt[i] : a.nodes.inv_omt[i], d >= 0 ? d : -d);
+      if (cs.u1) pw *= ipow(a.nodes.colpow[i], cs.u1);
+      const double cv = cr[t] * pw * sc;
+      const double xr = pr * cv, xi = pim * cv;
+      const double2 w = a.wV[np];
+      A[t] = from_d2<C>(make_double2(fma(xr, w.x, -xi * w.y), fma(xr, w.y, xi * w.x)));
+    }
   }
 }
 
+// FP32 plans with per-block tables: every operation of the generation in FP32.
+__global__ void __launch_bounds__(256) k_gen_f32(GenArgs a) {
+  const int64_t ncolumns = (int64_t)a.nc * a.nsegc;
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, dt = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t y = blockIdx.y; y < ncolumns; y += gridDim.y) {
+    float2* A = reinterpret_cast<float2*>(a.A) + y * a.F;
+    const int64_t cc = y / a.nsegc, sg = y - cc * a.nsegc;
+    const int64_t g = a.c0 + cc;
+    const int64_t rhs = g / a.ncols, l = g - rhs * a.ncols;
+    const int64_t nlo = sg * a.S;
+    const int64_t lim = min(a.S, a.C - nlo);
+    const float* cr = a.cf + rhs * a.ldcf + (a.n0 - 1 + nlo);
+    const float2* tr = a.Tf + l * a.C + nlo;
+    for (int64_t t = t0; t < a.F; t += dt) {
+      float2 v = make_float2(0.f, 0.f);
+      if (t < lim) {
+        const float cv = __ldg(&cr[t]);
+        const float2 x = __ldg(&tr[t]);
+        v = make_float2(cv * x.x, cv * x.y);
+      }
+      A[t] = v;
+    }
+  }
+}
+
+// Thread per output row and CTA row (blockIdx.y) per right-hand side of the chunk: the thread
+// adds up that right-hand side's stacked columns of the chunk in order l = lo..hi-1, so every
+// f entry has one writer per chunk and the sum order is fixed.
 template <class C>
 __global__ void __launch_bounds__(256) k_out(OutArgs a) {
   const int64_t kp = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -84,32 +125,52 @@ __global__ void __launch_bounds__(256) k_out(OutArgs a) {
   const double2 wu = a.wU[kp];
   const int64_t sg = kp / a.Sr;
   const C* Y = reinterpret_cast<const C*>(a.Y) + sg * a.F + (kp - sg * a.Sr) + a.off;
-  double ar = 0.0, ai = 0.0;
-  int cur = (int)(a.c0 / a.ncols);
-  for (int cc = 0; cc < a.nc; ++cc) {
-    const int64_t g = a.c0 + cc;
-    const int rhs = (int)(g / a.ncols);
-    if (rhs != cur) {
-      a.f[(int64_t)cur * a.ldf + i] += fma(wu.x, ar, -wu.y * ai);
-      ar = ai = 0.0;
-      cur = rhs;
+  const int64_t r_first = a.c0 / a.ncols, r_last = (a.c0 + a.nc - 1) / a.ncols;
+  for (int64_t rhs = r_first + blockIdx.y; rhs <= r_last; rhs += gridDim.y) {
+    const int64_t lo = max(a.c0, rhs * a.ncols), hi = min(a.c0 + a.nc, (rhs + 1) * a.ncols);
+    double ar = 0.0, ai = 0.0;
+    for (int64_t g = lo; g < hi; ++g) {
+      const int l = (int)(g - rhs * a.ncols);
+      double wgt;
+      if (a.W) {
+        wgt = a.W[(int64_t)l * a.N + i];
+      } else {
+        const DevColSpec& cs = a.cols[l];
+        const int d = cs.delta;
+        wgt = rs * ipow(d >= 0 ? rv : irv, d >= 0 ? d : -d);
+        if (cs.u1) wgt *= ipow(rp, cs.u1);
+      }
+      if (a.iscale) wgt *= a.iscale[l];
+      const C y = Y[(g - a.c0) * a.nsegr * a.F];
+      ar = fma(wgt, (double)y.x, ar);
+      ai = fma(wgt, (double)y.y, ai);
     }
-    const int l = (int)(g - (int64_t)rhs * a.ncols);
-    double wgt;
-    if (a.W) {
-      wgt = a.W[(int64_t)l * a.N + i];
-    } else {
-      const DevColSpec& cs = a.cols[l];
-      const int d = cs.delta;
-      wgt = rs * ipow(d >= 0 ? rv : irv, d >= 0 ? d : -d);
-      if (cs.u1) wgt *= ipow(rp, cs.u1);
-    }
-    if (a.iscale) wgt *= a.iscale[l];
-    const C y = Y[(int64_t)cc * a.nsegr * a.F];
-    ar = fma(wgt, (double)y.x, ar);
-    ai = fma(wgt, (double)y.y, ai);
+    a.f[rhs * a.ldf + i] += fma(wu.x, ar, -wu.y * ai);
   }
-  a.f[(int64_t)cur * a.ldf + i] += fma(wu.x, ar, -wu.y * ai);
+}
+
+// FP32 plans with per-block tables: the sum over stacked columns in FP32, the row chirp and
+// the addition into f in FP64.
+__global__ void __launch_bounds__(256) k_out_f32(OutArgs a) {
+  const int64_t kp = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (kp >= a.R) return;
+  const int64_t i = a.k0 - 1 + kp;
+  const double2 wu = a.wU[kp];
+  const int64_t sg = kp / a.Sr;
+  const float2* Y = reinterpret_cast<const float2*>(a.Y) + sg * a.F + (kp - sg * a.Sr) + a.off;
+  const int64_t r_first = a.c0 / a.ncols, r_last = (a.c0 + a.nc - 1) / a.ncols;
+  for (int64_t rhs = r_first + blockIdx.y; rhs <= r_last; rhs += gridDim.y) {
+    const int64_t lo = max(a.c0, rhs * a.ncols), hi = min(a.c0 + a.nc, (rhs + 1) * a.ncols);
+    float ar = 0.f, ai = 0.f;
+    for (int64_t g = lo; g < hi; ++g) {
+      const int64_t l = g - rhs * a.ncols;
+      const float wgt = __ldg(&a.Wf[l * a.R + kp]);
+      const float2 y = Y[(g - a.c0) * a.nsegr * a.F];
+      ar = fmaf(wgt, y.x, ar);
+      ai = fmaf(wgt, y.y, ai);
+    }
+    a.f[rhs * a.ldf + i] += fma(wu.x, (double)ar, -wu.y * (double)ai);
+  }
 }
 
 // Overlap-add of column segments: out[cc][t] = sum_s in[cc*nseg + s][t] H[s][t]. A CTA covers
@@ -182,6 +243,30 @@ __global__ void __launch_bounds__(256) k_build_tables(TabArgs a) {
   }
 }
 
+__global__ void __launch_bounds__(256) k_block_tables_f32(const double2* __restrict__ T, const double* __restrict__ W,
+                                                         int64_t N, int ncols, int64_t n0, int64_t C, int64_t k0,
+                                                         int64_t R, const double* __restrict__ scale,
+                                                         const double* __restrict__ iscale, float2* Tf, float* Wf) {
+  const int64_t m = C > R ? C : R;
+  const int64_t total = (int64_t)ncols * m;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t l = e / m, j = e - l * m;
+    if (j < C) {
+      const double2 x = T[l * N + n0 - 1 + j];
+      Tf[l * C + j] = make_float2((float)(x.x * scale[l]), (float)(x.y * scale[l]));
+    }
+    if (j < R) Wf[l * R + j] = (float)(W[l * N + k0 - 1 + j] * iscale[l]);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_coeffs_f32(const double* __restrict__ c, int64_t ldc, float* cf, int64_t N,
+                                                   int64_t total) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / N, i = e - r * N;
+    cf[e] = (float)c[r * ldc + i];
+  }
+}
+
 unsigned grid1d(int64_t n) {
   int64_t g = (n + 255) / 256;
   return (unsigned)std::min<int64_t>(std::max<int64_t>(g, 1), int64_t(152) * 32);
@@ -189,11 +274,15 @@ unsigned grid1d(int64_t n) {
 
 }  // namespace
 
+// Each thread writes up to kGenPts points of a column.
+constexpr int64_t kGenPts = 4;
+
 template <class C>
 void launch_gen(const GenArgs& a, cudaStream_t st) {
   const int64_t ny = std::min<int64_t>((int64_t)a.nc * a.nsegc, 65535);
-  dim3 grid((unsigned)((a.F + 255) / 256), (unsigned)ny);
-  k_gen<C><<<grid, 256, 0, st>>>(a);
+  dim3 grid((unsigned)((a.F + 256 * kGenPts - 1) / (256 * kGenPts)), (unsigned)ny);
+  if (std::is_same<C, float2>::value && a.Tf) k_gen_f32<<<grid, 256, 0, st>>>(a);
+  else k_gen<C><<<grid, 256, 0, st>>>(a);
 }
 
 template <class C>
@@ -215,7 +304,22 @@ void launch_build_tables(const TabArgs& a, cudaStream_t st) {
 
 template <class C>
 void launch_out(const OutArgs& a, cudaStream_t st) {
-  k_out<C><<<(unsigned)((a.R + 255) / 256), 256, 0, st>>>(a);
+  const int64_t nr = (a.c0 + a.nc - 1) / a.ncols - a.c0 / a.ncols + 1;  // right-hand sides in the chunk
+  dim3 grid((unsigned)((a.R + 255) / 256), (unsigned)std::min<int64_t>(nr, 65535));
+  if (std::is_same<C, float2>::value && a.Wf) k_out_f32<<<grid, 256, 0, st>>>(a);
+  else k_out<C><<<grid, 256, 0, st>>>(a);
+}
+
+void launch_block_tables_f32(const double2* T, const double* W, int64_t N, int ncols, int64_t n0, int64_t C,
+                             int64_t k0, int64_t R, const double* scale, const double* iscale, float2* Tf, float* Wf,
+                             cudaStream_t st) {
+  k_block_tables_f32<<<grid1d((int64_t)ncols * std::max(C, R)), 256, 0, st>>>(T, W, N, ncols, n0, C, k0, R, scale,
+                                                                               iscale, Tf, Wf);
+}
+
+void launch_coeffs_f32(const double* c, int64_t ldc, float* cf, int64_t N, int nrhs, cudaStream_t st) {
+  const int64_t total = N * nrhs;
+  k_coeffs_f32<<<grid1d(total), 256, 0, st>>>(c, ldc, cf, N, total);
 }
 
 template void launch_gen<double2>(const GenArgs&, cudaStream_t);

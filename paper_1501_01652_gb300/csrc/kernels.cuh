@@ -73,6 +73,11 @@ struct GenArgs {
   const double2* T;   // optional [ncols][N] column factors times the column chirp (nullptr: computed here)
   int64_t N;
   const double* scale;  // optional per stacked column: factor applied before rounding to FP32 (nullptr: 1)
+  // FP32 plans with factor tables: coefficients rounded to FP32, cf[rhs * ldcf + n-1], and the
+  // block's [ncols][C] column factors times the column chirp and scale, in FP32 (nullptr: unused)
+  const float* cf;
+  int64_t ldcf;
+  const float2* Tf;
 };
 
 struct OutArgs {
@@ -92,6 +97,7 @@ struct OutArgs {
   const double* W;    // optional [ncols][N] row factors (nullptr: computed here)
   int64_t N;
   const double* iscale;  // optional per stacked column: inverse of GenArgs::scale (nullptr: 1)
+  const float* Wf;       // FP32 plans with factor tables: the block's [ncols][R] row factors times iscale
 };
 
 // Plan-time tables of the factors that do not depend on c:
@@ -107,6 +113,13 @@ struct TabArgs {
   int64_t Va, Vb, E;
 };
 void launch_build_tables(const TabArgs& a, cudaStream_t st);
+// Per-block FP32 factor tables (FP32 plans): Tf[l][np] = T[l][n0-1+np] scale[l] (np < C),
+// Wf[l][kp] = W[l][k0-1+kp] iscale[l] (kp < R), each rounded to FP32 once.
+void launch_block_tables_f32(const double2* T, const double* W, int64_t N, int ncols, int64_t n0, int64_t C,
+                             int64_t k0, int64_t R, const double* scale, const double* iscale, float2* Tf, float* Wf,
+                             cudaStream_t st);
+// cf[r * N + i] = (float) c[r * ldc + i] for r < nrhs, i < N.
+void launch_coeffs_f32(const double* c, int64_t ldc, float* cf, int64_t N, int nrhs, cudaStream_t st);
 
 // Convolution kernels of the segments of a block: for y < nseg and t < F,
 // hh[y*F + t] = exp(-i pi D^2 / (2E)), D = Ua (t - (Cc-1) + (k0 + y dk) - (n0 + y dn)) + Ub - Vb

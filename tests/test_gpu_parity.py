@@ -136,6 +136,8 @@ def test_factor_tables_on_and_off(tables):
     c = coefficients("normal", N, 2, 5600)
     _check("dht", 0, N, 1e-15, c, tables=tables)
     _check("fourier_bessel", 0, N, 1e-8, c, tables=tables)
+    _check("dht", 0, N, 1e-4, c, tables=tables, precision="fp32")
+    _check("schlomilch", 2, N, 1e-5, c, tables=tables, precision="fp32")
 
 
 @pytest.mark.parametrize("eps", [1e-15, 1e-8])
@@ -154,6 +156,21 @@ def test_batched_matches_single():
     for r in range(c.shape[0]):
         fs, _ = _run("dht", 0, N, 1e-8, c[r:r + 1])
         assert np.array_equal(fb[r], fs[0])
+
+
+@pytest.mark.parametrize("eps,precision", [(1e-8, "fp64"), (1e-4, "fp32")])
+def test_chunks_that_split_right_hand_sides(eps, precision):
+    # a small workspace cuts the stacked columns of one right-hand side across chunks; every
+    # chunk adds its share of each vector's columns, so the result equals one chunk per block
+    N = 5000
+    c = coefficients("normal", N, 5, 6050)
+    big, _ = _run("dht", 0, N, eps, c, precision=precision)
+    small, plan = _run("dht", 0, N, eps, c, precision=precision, workspace_limit=3 << 20)
+    assert any(b["mode"] == 0 for b in plan.blocks())
+    bound = 10.0 * eps * np.abs(c).sum(axis=1, keepdims=True)
+    assert np.all(np.abs(small - big) <= bound)
+    ref = oracle.transform("dht", 0, N, c)
+    assert np.all(np.abs(small - ref) <= bound)
 
 
 def test_deterministic_and_host_entry_point():
