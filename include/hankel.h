@@ -85,6 +85,9 @@ enum hankel_status {
 #define HANKEL_FLAG_NO_SEGMENT 2u  /* one full-length chirp-z transform per block (no segmenting of thin blocks) */
 #define HANKEL_FLAG_NO_TABLES 4u   /* compute column/row factors per use instead of keeping tables of
                                       ncols * N * 24 bytes on the device (tables are skipped anyway above 16 GiB) */
+#define HANKEL_FLAG_ALL_COLUMNS 8u /* every block keeps all ncols stacked columns; by default a block leaves
+                                      out the columns whose summed bound on its entries stays within
+                                      eps/10 per entry (hankel_block.ncols, hankel_info.block_cols) */
 
 /* Options for hankel_plan_ex(). Fill with hankel_options_default() first. */
 typedef struct {
@@ -122,6 +125,7 @@ typedef struct {
   double near_zmax;       /* largest argument r_k omega_n in the near field */
   size_t device_bytes;    /* device memory held by the plan (tables + workspace) */
   size_t workspace_bytes; /* part of device_bytes used as transform workspace */
+  int64_t block_cols;     /* stacked columns kept, summed over blocks (nblocks * ncols when none is left out) */
 } hankel_info;
 
 /* One far-field block of the partition, 1-based inclusive index ranges. */
@@ -133,6 +137,8 @@ typedef struct {
   int64_t nseg;    /* number of segments (1 = one transform with F >= rows + cols - 1) */
   int mode;        /* 0 unsegmented; 1 columns segmented (overlap-add), F >= rows + S - 1;
                       2 rows segmented (overlap-save), F >= S + cols - 1 */
+  int ncols;       /* stacked columns this block transforms per right-hand side (<= hankel_info.ncols) */
+  double dropped;  /* bound on the change of any entry of the block from the columns it leaves out */
 } hankel_block;
 
 /* Fill *o with defaults for (task, nu, N, eps). Host only. Returns HANKEL_OK or HANKEL_EINVAL (o == NULL). */

@@ -12,6 +12,7 @@ STATUS_NAMES = {0: "HANKEL_OK", 1: "HANKEL_EINVAL", 2: "HANKEL_ENOMEM", 3: "HANK
 FLAG_HOST_ONLY = 1
 FLAG_NO_SEGMENT = 2
 FLAG_NO_TABLES = 4
+FLAG_ALL_COLUMNS = 8
 
 # Every function include/hankel.h declares.
 EXPORTED = [
@@ -41,7 +42,7 @@ class Info(ctypes.Structure):
                 ("direct_cols", ctypes.c_int64), ("nblocks", ctypes.c_int), ("ncols", ctypes.c_int),
                 ("npairs", ctypes.c_int), ("near_count", ctypes.c_int64), ("far_count", ctypes.c_int64),
                 ("near_zmax", ctypes.c_double), ("device_bytes", ctypes.c_size_t),
-                ("workspace_bytes", ctypes.c_size_t)]
+                ("workspace_bytes", ctypes.c_size_t), ("block_cols", ctypes.c_int64)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -70,7 +71,7 @@ class ServerStats(ctypes.Structure):
 class Block(ctypes.Structure):
     _fields_ = [("k0", ctypes.c_int64), ("k1", ctypes.c_int64), ("n0", ctypes.c_int64), ("n1", ctypes.c_int64),
                 ("fft_len", ctypes.c_int64), ("seg_len", ctypes.c_int64), ("nseg", ctypes.c_int64),
-                ("mode", ctypes.c_int)]
+                ("mode", ctypes.c_int), ("ncols", ctypes.c_int), ("dropped", ctypes.c_double)]
 
 
 def load():

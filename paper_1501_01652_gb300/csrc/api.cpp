@@ -68,6 +68,8 @@ static void fill_info(const hankel_plan_s* p, const hk::HostPlan& hp, hankel_inf
     // parameters only: the count the planner would build
     out->ncols = hp.U1 * (2 * hp.M + hp.U2 - 1);
   }
+  out->block_cols = 0;
+  for (const hk::Block& b : hp.blocks) out->block_cols += (int64_t)b.lcols.size();
   out->near_count = hp.near_count;
   out->far_count = hp.far_count;
   out->near_zmax = hp.zmax;
@@ -154,6 +156,8 @@ int hankel_plan_blocks(hankel_plan_t p, hankel_block* out, int cap, int* count) 
     out[i].seg_len = bl[i].S;
     out[i].nseg = bl[i].nseg;
     out[i].mode = bl[i].mode;
+    out[i].ncols = (int)bl[i].lcols.size();
+    out[i].dropped = bl[i].dropped;
   }
   return HANKEL_OK;
 }

@@ -38,8 +38,10 @@ struct DevBlock {
   void* H = nullptr;      // per segment: FFT_F of the chirp exp(-i pi (U-V)^2 / (2E)), times 1/F (plan precision)
   double* scale = nullptr;   // FP32 plans: per stacked column, power of two keeping generated values near 1
   double* iscale = nullptr;  // its inverse, applied to the row factors
-  float2* Tf = nullptr;      // FP32 plans with tables: [ncols][C] column factors x chirp x scale
-  float* Wf = nullptr;       // FP32 plans with tables: [ncols][R] row factors x iscale
+  int* lmap = nullptr;       // the block's kept stacked columns (indices into the plan's columns)
+  int nl = 0;                // their number
+  float2* Tf = nullptr;      // FP32 plans with tables: [nl][C] column factors x chirp x scale
+  float* Wf = nullptr;       // FP32 plans with tables: [nl][R] row factors x iscale
   int64_t cap = 0;           // columns per chunk
 };
 
@@ -314,6 +316,8 @@ int dev_plan_create(hankel_plan_s* p) {
                                                     (int64_t)d->ncols * hp.opt.max_nrhs));
     HK_TRY(dalloc(d, &db.wU, b.R));
     HK_TRY(dalloc(d, &db.wV, b.C));
+    db.nl = (int)b.lcols.size();
+    HK_TRY(upload(d, &db.lmap, b.lcols.data(), b.lcols.size()));
     if (d->fp32) {
       float2* h; HK_TRY(dalloc(d, &h, (size_t)b.nseg * b.F)); db.H = h;
       // per stacked column: the power of two that brings max |colfun(n)| over the block to ~1
@@ -336,9 +340,10 @@ int dev_plan_create(hankel_plan_s* p) {
       HK_TRY(upload(d, &db.scale, sc.data(), sc.size()));
       HK_TRY(upload(d, &db.iscale, isc.data(), isc.size()));
       if (d->T) {
-        HK_TRY(dalloc(d, &db.Tf, (size_t)d->ncols * b.C));
-        HK_TRY(dalloc(d, &db.Wf, (size_t)d->ncols * b.R));
-        launch_block_tables_f32(d->T, d->W, N, d->ncols, b.n0, b.C, b.k0, b.R, db.scale, db.iscale, db.Tf, db.Wf, 0);
+        HK_TRY(dalloc(d, &db.Tf, (size_t)db.nl * b.C));
+        HK_TRY(dalloc(d, &db.Wf, (size_t)db.nl * b.R));
+        launch_block_tables_f32(d->T, d->W, N, db.nl, db.lmap, b.n0, b.C, b.k0, b.R, db.scale, db.iscale, db.Tf,
+                                db.Wf, 0);
         HK_LAUNCHED();
       }
     } else {
@@ -404,7 +409,7 @@ int run_block(DevicePlan* d, const DevBlock& db, const double* c, int64_t ldc, d
   const Block& b = db.b;
   const C* tw = d->fp32 ? (const C*)d->twf : (const C*)d->tw;
   const C* H = (const C*)db.H;
-  const int64_t total = (int64_t)d->ncols * nrhs;
+  const int64_t total = (int64_t)db.nl * nrhs;
   const bool rowseg = b.mode == kBlockRowSeg, colseg = b.mode == kBlockColSeg;
   for (int64_t c0 = 0; c0 < total; c0 += cap) {
     const int nc = (int)std::min<int64_t>(cap, total - c0);
@@ -412,7 +417,7 @@ int run_block(DevicePlan* d, const DevBlock& db, const double* c, int64_t ldc, d
     const int64_t ninv = colseg ? (int64_t)nc * b.nseg : nc;  // inverse transforms
     {
       StageScope sc(d, HANKEL_STAGE_GEN, st, record);
-      GenArgs ga{A, b.F, b.C, b.n0, rowseg ? b.S : b.C, rowseg ? b.nseg : 1, nc, c0, d->ncols, c, ldc,
+      GenArgs ga{A, b.F, b.C, b.n0, rowseg ? b.S : b.C, rowseg ? b.nseg : 1, nc, c0, db.nl, db.lmap, c, ldc,
                  d->nodes, d->cols, db.wV, d->T, d->hpN, db.scale, d->cf, d->hpN, db.Tf};
       launch_gen<C>(ga, st);
       HK_LAUNCHED();
@@ -447,7 +452,7 @@ int run_block(DevicePlan* d, const DevBlock& db, const double* c, int64_t ldc, d
     {
       StageScope sc(d, HANKEL_STAGE_OUT, st, record);
       OutArgs oa{res2, b.F, b.R, b.k0, (rowseg ? b.S : b.C) - 1, colseg ? b.S : b.R, colseg ? b.nseg : 1,
-                 nc, c0, d->ncols, f, ldf, d->nodes, d->cols, db.wU, d->W, d->hpN, db.iscale, db.Wf};
+                 nc, c0, db.nl, db.lmap, f, ldf, d->nodes, d->cols, db.wU, d->W, d->hpN, db.iscale, db.Wf};
       launch_out<C>(oa, st);
       HK_LAUNCHED();
       sc.done(1, 0.0, 0.0);

@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(256) k_gen(GenArgs a) {
     const int64_t cc = y / a.nsegc, sg = y - cc * a.nsegc;
     const int64_t g = a.c0 + cc;
     const int64_t rhs = g / a.ncols;
-    const int l = (int)(g - rhs * a.ncols);
+    const int l = a.lmap[g - rhs * a.ncols];
     const int64_t nlo = sg * a.S;                          // first column offset of this segment
     const int64_t lim = min(a.S, a.C - nlo);               // points t < lim carry data, the rest is padding
     const double* cr = a.c + rhs * a.ldc + (a.n0 - 1 + nlo);
@@ -90,11 +90,11 @@ __global__ void __launch_bounds__(256) k_gen_f32(GenArgs a) {
     float2* A = reinterpret_cast<float2*>(a.A) + y * a.F;
     const int64_t cc = y / a.nsegc, sg = y - cc * a.nsegc;
     const int64_t g = a.c0 + cc;
-    const int64_t rhs = g / a.ncols, l = g - rhs * a.ncols;
+    const int64_t rhs = g / a.ncols, li = g - rhs * a.ncols;  // kept-column position: per-block table row
     const int64_t nlo = sg * a.S;
     const int64_t lim = min(a.S, a.C - nlo);
     const float* cr = a.cf + rhs * a.ldcf + (a.n0 - 1 + nlo);
-    const float2* tr = a.Tf + l * a.C + nlo;
+    const float2* tr = a.Tf + li * a.C + nlo;
     for (int64_t t = t0; t < a.F; t += dt) {
       float2 v = make_float2(0.f, 0.f);
       if (t < lim) {
@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(256) k_out(OutArgs a) {
     const int64_t lo = max(a.c0, rhs * a.ncols), hi = min(a.c0 + a.nc, (rhs + 1) * a.ncols);
     double ar = 0.0, ai = 0.0;
     for (int64_t g = lo; g < hi; ++g) {
-      const int l = (int)(g - rhs * a.ncols);
+      const int l = a.lmap[g - rhs * a.ncols];
       double wgt;
       if (a.W) {
         wgt = a.W[(int64_t)l * a.N + i];
@@ -163,8 +163,8 @@ __global__ void __launch_bounds__(256) k_out_f32(OutArgs a) {
     const int64_t lo = max(a.c0, rhs * a.ncols), hi = min(a.c0 + a.nc, (rhs + 1) * a.ncols);
     float ar = 0.f, ai = 0.f;
     for (int64_t g = lo; g < hi; ++g) {
-      const int64_t l = g - rhs * a.ncols;
-      const float wgt = __ldg(&a.Wf[l * a.R + kp]);
+      const int64_t li = g - rhs * a.ncols;  // kept-column position: per-block table row
+      const float wgt = __ldg(&a.Wf[li * a.R + kp]);
       const float2 y = Y[(g - a.c0) * a.nsegr * a.F];
       ar = fmaf(wgt, y.x, ar);
       ai = fmaf(wgt, y.y, ai);
@@ -244,18 +244,20 @@ __global__ void __launch_bounds__(256) k_build_tables(TabArgs a) {
 }
 
 __global__ void __launch_bounds__(256) k_block_tables_f32(const double2* __restrict__ T, const double* __restrict__ W,
-                                                         int64_t N, int ncols, int64_t n0, int64_t C, int64_t k0,
-                                                         int64_t R, const double* __restrict__ scale,
+                                                         int64_t N, int nl, const int* __restrict__ lmap, int64_t n0,
+                                                         int64_t C, int64_t k0, int64_t R,
+                                                         const double* __restrict__ scale,
                                                          const double* __restrict__ iscale, float2* Tf, float* Wf) {
   const int64_t m = C > R ? C : R;
-  const int64_t total = (int64_t)ncols * m;
+  const int64_t total = (int64_t)nl * m;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t l = e / m, j = e - l * m;
+    const int64_t li = e / m, j = e - li * m;
+    const int64_t l = lmap[li];
     if (j < C) {
       const double2 x = T[l * N + n0 - 1 + j];
-      Tf[l * C + j] = make_float2((float)(x.x * scale[l]), (float)(x.y * scale[l]));
+      Tf[li * C + j] = make_float2((float)(x.x * scale[l]), (float)(x.y * scale[l]));
     }
-    if (j < R) Wf[l * R + j] = (float)(W[l * N + k0 - 1 + j] * iscale[l]);
+    if (j < R) Wf[li * R + j] = (float)(W[l * N + k0 - 1 + j] * iscale[l]);
   }
 }
 
@@ -310,11 +312,11 @@ void launch_out(const OutArgs& a, cudaStream_t st) {
   else k_out<C><<<grid, 256, 0, st>>>(a);
 }
 
-void launch_block_tables_f32(const double2* T, const double* W, int64_t N, int ncols, int64_t n0, int64_t C,
-                             int64_t k0, int64_t R, const double* scale, const double* iscale, float2* Tf, float* Wf,
-                             cudaStream_t st) {
-  k_block_tables_f32<<<grid1d((int64_t)ncols * std::max(C, R)), 256, 0, st>>>(T, W, N, ncols, n0, C, k0, R, scale,
-                                                                               iscale, Tf, Wf);
+void launch_block_tables_f32(const double2* T, const double* W, int64_t N, int nl, const int* lmap, int64_t n0,
+                             int64_t C, int64_t k0, int64_t R, const double* scale, const double* iscale, float2* Tf,
+                             float* Wf, cudaStream_t st) {
+  k_block_tables_f32<<<grid1d((int64_t)nl * std::max(C, R)), 256, 0, st>>>(T, W, N, nl, lmap, n0, C, k0, R, scale,
+                                                                            iscale, Tf, Wf);
 }
 
 void launch_coeffs_f32(const double* c, int64_t ldc, float* cf, int64_t N, int nrhs, cudaStream_t st) {

@@ -3,8 +3,9 @@
 //
 // After passes with radices R_1 R_2 ... = F the output is in natural order. One
 // CTA handles kTile consecutive (p, q) pairs of a pass, so every global load and
-// store touches kTile or more consecutive elements, and does the R-point DFT in
-// shared memory with radix-4/radix-2 Stockham sub-steps.
+// store touches kTile or more consecutive elements. Radices R <= 16 do the R-point
+// DFT in shared memory with radix-4/radix-2 Stockham sub-steps; radices 32..256 in
+// two register sub-stages with one exchange through shared memory.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -172,18 +173,142 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_pass(const C* __restrict__ 
   }
 }
 
+// Twiddled radix-2^LQ DFT in registers: on return a[r] = sum_j W_Q^{r j} w^j a_j (Q = 2^LQ),
+// where w^t is the table entry (t * base) mod Fmax. Iterative radix-2 decimation in time on the
+// bit-reversed inputs (a compile-time renaming of registers): the size-m sub-DFTs of stage
+// s = log2 m combine as E_k + W_m^k w^{Q/m} O_k, so stage s looks up m/2 twiddles at
+// k Fmax/m + base Q/m, and every butterfly is the FMA-folded bfly2.
+// bit reversal of j in L <= 4 bits
+__host__ __device__ constexpr int bitrev(int j, int L) {
+  return (((j & 1) << 3) | ((j & 2) << 1) | ((j & 4) >> 1) | ((j & 8) >> 3)) >> (4 - L);
+}
+
+template <int LQ, bool INV, class C>
+__device__ __forceinline__ void reg_dft(C (&a)[1 << LQ], uint32_t base, const C* __restrict__ tw, int logFmax,
+                                        uint32_t fmask) {
+  constexpr int Q = 1 << LQ;
+  C b[Q];
+#pragma unroll
+  for (int j = 0; j < Q; ++j) b[bitrev(j, LQ)] = a[j];
+#pragma unroll
+  for (int s = 1; s <= LQ; ++s) {
+    const int half = 1 << (s - 1);
+#pragma unroll
+    for (int k = 0; k < half; ++k) {
+      const C v = twiddle<INV>(tw, (((uint32_t)k << (logFmax - s)) + (base << (LQ - s))) & fmask);
+#pragma unroll
+      for (int g = 0; g < Q; g += 2 * half) bfly2(b[g + k], b[g + k + half], v);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < Q; ++j) a[j] = b[j];
+}
+
+// The same pass as k_fft_pass for 5 <= log2 R <= 8, with the R-point DFTs done as two
+// Stockham sub-stages of radix Q1 = 2^L1 and Q2 = 2^L2 (L1 + L2 = log2 R) held in registers.
+// Sub-stage 1 (stride R/Q1 = Q2): butterfly qq of sequence i takes elements qq + Q2 j, which for
+// pass strides s >= kTile sit kTile-contiguous in global memory and are loaded straight into
+// registers (Q1 independent loads per thread); for s < kTile the tile is first transposed
+// through shared memory. Its outputs go to shared memory; sub-stage 2 (stride 1) reads
+// elements Q2 pp + j there and writes its outputs pp + Q1 r straight to global memory, again
+// kTile-contiguous per element. The block has kTile Q1 threads, one butterfly per thread and
+// sub-stage. Twiddle deferral as in smem_dft; the pass twiddle exponent p s of a thread's
+// sequence is recomputed per thread.
+template <int LOGR, bool INV, class C>
+__global__ void __launch_bounds__(kFftThreads) k_fft_pass_reg(const C* __restrict__ src, C* __restrict__ dst,
+                                                              int logF, int logS, const C* __restrict__ tw,
+                                                              int logFmax) {
+  constexpr int R = 1 << LOGR;
+  constexpr int L1 = (LOGR + 1) / 2, L2 = LOGR - L1;
+  constexpr int Q1 = 1 << L1, Q2 = 1 << L2;
+  constexpr int NT = kTile * Q1;                     // threads = butterflies of sub-stage 2
+  constexpr int NB1 = kTile * Q2;                    // butterflies of sub-stage 1 (<= NT)
+  constexpr int PER = R * kTile / NT;                // points per thread in the transposing fill
+  static_assert(NT <= kFftThreads && NB1 <= NT, "one butterfly per thread and sub-stage");
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  C* v = reinterpret_cast<C*>(sm_raw);
+  const int logFR = logF - LOGR;
+  const uint64_t G0 = (uint64_t)blockIdx.x * kTile;
+  const uint64_t col = G0 >> logFR;
+  const uint32_t pi0 = (uint32_t)(G0 & ((1ull << logFR) - 1));
+  const C* x = src + (col << logF);
+  C* y = dst + (col << logF);
+  const uint32_t s = 1u << logS;
+  const int fsh = logFmax - logF;
+  const uint32_t fmask = (1u << logFmax) - 1u;
+  const uint32_t i = threadIdx.x & (kTile - 1), bf = threadIdx.x / kTile;
+  const uint32_t pti = ((pi0 + i) >> logS) << logS;  // p * s of this thread's sequence
+  const bool act1 = threadIdx.x < NB1;
+  C a[Q1];
+  if (s >= kTile) {
+    if (act1) {
+      const uint32_t p = pi0 >> logS, q0 = pi0 & (s - 1);
+      const C* xb = x + q0 + ((p << LOGR) << logS) + i;
+#pragma unroll
+      for (int j = 0; j < Q1; ++j) a[j] = xb[(bf + Q2 * j) << logS];
+    }
+  } else {
+    const C* xb = x + (pi0 << LOGR);
+    const uint32_t srm = (s << LOGR) - 1;
+    C t[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) t[u] = xb[threadIdx.x + u * NT];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const uint32_t idx = threadIdx.x + u * NT;
+      const uint32_t pl = idx >> (logS + LOGR), rem = idx & srm;
+      const uint32_t j = rem >> logS, q = rem & (s - 1);
+      v[j * kRow + ((pl << logS) + q)] = t[u];
+    }
+    __syncthreads();
+    if (act1) {
+#pragma unroll
+      for (int j = 0; j < Q1; ++j) a[j] = v[(bf + Q2 * j) * kRow + i];
+    }
+    __syncthreads();  // sub-stage 1 overwrites the tile in place
+  }
+  if (act1) {
+    reg_dft<L1, INV>(a, (pti << L2) << fsh, tw, logFmax, fmask);
+#pragma unroll
+    for (int r = 0; r < Q1; ++r) v[(bf + Q2 * r) * kRow + i] = a[r];
+  }
+  __syncthreads();
+  {
+    C b[Q2];
+#pragma unroll
+    for (int j = 0; j < Q2; ++j) b[j] = v[(Q2 * bf + j) * kRow + i];
+    reg_dft<L2, INV>(b, (bf << (logFmax - LOGR)) + (pti << fsh), tw, logFmax, fmask);
+    C* yb = y + pi0 + i;
+#pragma unroll
+    for (int r = 0; r < Q2; ++r) yb[(bf + Q1 * r) << logFR] = b[r];
+  }
+}
+
 template <int LOGR, bool INV, class C>
 void launch_pass(const C* src, C* dst, int logF, int logS, int ncols, const C* tw, int logFmax, cudaStream_t st) {
   constexpr int R = 1 << LOGR;
-  const size_t smem = 2 * (size_t)R * kRow * sizeof(C);
-  static bool configured = false;
-  if (!configured) {
-    cudaFuncSetAttribute(k_fft_pass<LOGR, INV, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    configured = true;
-  }
   const int64_t pairs = ((int64_t)ncols << logF) >> LOGR;
   const int64_t grid = pairs / kTile;
-  k_fft_pass<LOGR, INV, C><<<(unsigned)grid, kFftThreads, smem, st>>>(src, dst, logF, logS, tw, logFmax);
+  if constexpr (LOGR >= 5) {
+    // one buffer (the sub-stages work in place); threads = butterflies of the wider sub-stage
+    constexpr int L2 = LOGR - (LOGR + 1) / 2;
+    constexpr int threads = kTile * (R >> L2);
+    const size_t smem = (size_t)R * kRow * sizeof(C);
+    static bool configured = false;
+    if (!configured) {
+      cudaFuncSetAttribute(k_fft_pass_reg<LOGR, INV, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      configured = true;
+    }
+    k_fft_pass_reg<LOGR, INV, C><<<(unsigned)grid, threads, smem, st>>>(src, dst, logF, logS, tw, logFmax);
+  } else {
+    const size_t smem = 2 * (size_t)R * kRow * sizeof(C);
+    static bool configured = false;
+    if (!configured) {
+      cudaFuncSetAttribute(k_fft_pass<LOGR, INV, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      configured = true;
+    }
+    k_fft_pass<LOGR, INV, C><<<(unsigned)grid, kFftThreads, smem, st>>>(src, dst, logF, logS, tw, logFmax);
+  }
 }
 
 template <bool INV, class C>
@@ -196,7 +321,8 @@ void launch_pass_r(int logR, const C* src, C* dst, int logF, int logS, int ncols
     case 4: launch_pass<4, INV>(src, dst, logF, logS, ncols, tw, logFmax, st); break;
     case 5: launch_pass<5, INV>(src, dst, logF, logS, ncols, tw, logFmax, st); break;
     case 6: launch_pass<6, INV>(src, dst, logF, logS, ncols, tw, logFmax, st); break;
-    default: launch_pass<7, INV>(src, dst, logF, logS, ncols, tw, logFmax, st); break;
+    case 7: launch_pass<7, INV>(src, dst, logF, logS, ncols, tw, logFmax, st); break;
+    default: launch_pass<8, INV>(src, dst, logF, logS, ncols, tw, logFmax, st); break;
   }
 }
 
@@ -279,7 +405,7 @@ template <class C>
 int run_fft(C* a, C* b, int logF, int ncols, bool inverse, const C* tw, int logFmax, cudaStream_t st, C** result,
             int* npasses) {
   if (logF < 6 || logF > logFmax) return HANKEL_EINVAL;
-  const int maxlog = std::min(7, logF - 4);  // keeps F/R >= kTile pairs per column
+  const int maxlog = std::min(8, logF - 4);  // keeps F/R >= kTile pairs per column
   const int np = (logF + maxlog - 1) / maxlog;
   const int base = logF / np, extra = logF % np;
   C* src = a;

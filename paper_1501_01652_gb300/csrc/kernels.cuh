@@ -63,8 +63,9 @@ struct GenArgs {
   int64_t S;          // columns per segment (C when the columns are not segmented)
   int64_t nsegc;      // column segments per stacked column (1 when not segmented)
   int nc;             // columns in this chunk
-  int64_t c0;         // global index of the first column (rhs * ncols + l)
-  int ncols;          // stacked columns per right-hand side
+  int64_t c0;         // global index of the first column (rhs * ncols + li)
+  int ncols;          // stacked columns the block keeps per right-hand side
+  const int* lmap;    // li -> index of the stacked column in the plan's column list
   const double* c;    // coefficients, c[rhs * ldc + n-1]
   int64_t ldc;
   NodeTables nodes;
@@ -88,7 +89,8 @@ struct OutArgs {
   int64_t nsegr;      // row segments per stacked column
   int nc;
   int64_t c0;
-  int ncols;
+  int ncols;          // stacked columns the block keeps per right-hand side
+  const int* lmap;    // li -> index of the stacked column in the plan's column list
   double* f;          // f[rhs * ldf + k-1] += ...
   int64_t ldf;
   NodeTables nodes;
@@ -113,11 +115,12 @@ struct TabArgs {
   int64_t Va, Vb, E;
 };
 void launch_build_tables(const TabArgs& a, cudaStream_t st);
-// Per-block FP32 factor tables (FP32 plans): Tf[l][np] = T[l][n0-1+np] scale[l] (np < C),
-// Wf[l][kp] = W[l][k0-1+kp] iscale[l] (kp < R), each rounded to FP32 once.
-void launch_block_tables_f32(const double2* T, const double* W, int64_t N, int ncols, int64_t n0, int64_t C,
-                             int64_t k0, int64_t R, const double* scale, const double* iscale, float2* Tf, float* Wf,
-                             cudaStream_t st);
+// Per-block FP32 factor tables (FP32 plans), for the block's kept columns l = lmap[li]:
+// Tf[li][np] = T[l][n0-1+np] scale[l] (np < C), Wf[li][kp] = W[l][k0-1+kp] iscale[l] (kp < R),
+// each rounded to FP32 once.
+void launch_block_tables_f32(const double2* T, const double* W, int64_t N, int nl, const int* lmap, int64_t n0,
+                             int64_t C, int64_t k0, int64_t R, const double* scale, const double* iscale, float2* Tf,
+                             float* Wf, cudaStream_t st);
 // cf[r * N + i] = (float) c[r * ldc + i] for r < nrhs, i < N.
 void launch_coeffs_f32(const double* c, int64_t ldc, float* cf, int64_t N, int nrhs, cudaStream_t st);
 

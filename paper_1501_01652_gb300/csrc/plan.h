@@ -34,6 +34,8 @@ struct Block {
   int mode;       // BlockMode
   int64_t S;      // segment length (C for full blocks)
   int64_t nseg;   // number of segments (1 for full blocks)
+  std::vector<int> lcols;  // stacked columns this block keeps (indices into HostPlan::cols, ascending)
+  double dropped = 0.0;    // bound on |entry change| from the stacked columns it leaves out
 };
 
 // One stacked column of a block: the row function rowpert(k)^u1 rowvar(k)^(delta-1/2)

@@ -517,6 +517,77 @@ void build_columns(HostPlan& hp) {
     }
 }
 
+// Per-block choice of stacked columns. Column l contributes W_l(k) T_l(n) to entry (k, n) of
+// a block (times a unimodular chirp), with |W_l(k)| = |rowpert|^u1 rowvar^(delta-1/2) and
+// |T_l(n)| <= |colpow|^u1 omt^(delta-1/2) sum_u2 |G_l[u2]| |beta|^u2. Each factor is a power of
+// a positive quantity, so its largest value over the block is taken at the block's extreme
+// node values, and A_l = max|W_l| max|T_l| bounds the column's share of any entry. The
+// truncations K, T, K2, T2 and M are fixed for the worst block (Sections 5.2, 6.1); in blocks
+// far from the near field the perturbations e_k omega_n and r b_n are orders of magnitude
+// smaller, and many columns contribute less than eps. A block drops its columns in increasing
+// order of A_l while their sum stays within its share of a budget of kDropFrac * eps per entry
+// (split evenly between the blocks that meet in one row); the change of every entry is at
+// most that sum, so |f_k - f'_k| <= kDropFrac * eps * sum_n |c_n|.
+constexpr double kDropFrac = 0.1;
+
+void select_columns(HostPlan& hp) {
+  const int64_t N = hp.opt.N;
+  const int ncols = (int)hp.cols.size();
+  // blocks meeting in one row
+  std::vector<int> per_row(N + 2, 0);
+  for (const Block& b : hp.blocks) {
+    per_row[b.k0] += 1;
+    per_row[b.k1 + 1] -= 1;
+  }
+  int maxrow = 1, run = 0;
+  for (int64_t k = 1; k <= N; ++k) maxrow = std::max(maxrow, run += per_row[k]);
+  const double budget = kDropFrac * hp.opt.eps / maxrow;
+  const bool keep_all = (hp.opt.flags & HANKEL_FLAG_ALL_COLUMNS) != 0;
+  auto pw = [](double x, double e) { return std::pow(x, e); };
+  for (Block& b : hp.blocks) {
+    b.lcols.clear();
+    b.dropped = 0.0;
+    if (keep_all) {
+      for (int l = 0; l < ncols; ++l) b.lcols.push_back(l);
+      continue;
+    }
+    double rp = 0.0, rv0 = INFINITY, rv1 = 0.0, cp = 0.0, om0 = INFINITY, om1 = 0.0, bt = 0.0;
+    for (int64_t k = b.k0; k <= b.k1; ++k) {
+      rp = std::max(rp, std::fabs(hp.rowpert[k - 1]));
+      rv0 = std::min(rv0, hp.rowvar[k - 1]);
+      rv1 = std::max(rv1, hp.rowvar[k - 1]);
+    }
+    for (int64_t n = b.n0; n <= b.n1; ++n) {
+      cp = std::max(cp, std::fabs(hp.colpow[n - 1]));
+      om0 = std::min(om0, hp.omt[n - 1]);
+      om1 = std::max(om1, hp.omt[n - 1]);
+      bt = std::max(bt, std::fabs(hp.betan[n - 1]));
+    }
+    std::vector<std::pair<double, int>> bound(ncols);
+    for (int l = 0; l < ncols; ++l) {
+      const ColSpec& cs = hp.cols[l];
+      const double e = cs.delta - 0.5;
+      double poly = 0.0, bp = 1.0;
+      for (int u = 0; u < cs.nterm; ++u, bp *= bt) poly += std::abs(cs.G[u]) * bp;
+      double a = std::max(pw(rv0, e), pw(rv1, e)) * std::max(pw(om0, e), pw(om1, e)) * poly;
+      if (cs.u1) a *= pw(rp, cs.u1) * pw(cp, cs.u1);
+      bound[l] = {std::isfinite(a) ? a : INFINITY, l};
+    }
+    std::sort(bound.begin(), bound.end());
+    std::vector<char> keep(ncols, 1);
+    double sum = 0.0;
+    for (const auto& x : bound) {
+      if (sum + x.first > budget) break;
+      sum += x.first;
+      keep[x.second] = 0;
+    }
+    b.dropped = sum;
+    for (int l = 0; l < ncols; ++l)
+      if (keep[l]) b.lcols.push_back(l);
+    if (b.lcols.empty()) b.lcols.push_back(bound.back().second);  // every block keeps one column
+  }
+}
+
 // Taylor polynomials of J_nu about z_c = i + 1/2 on [i, i+1). The coefficients follow from
 // the Neumann addition formula (Eq. 8) with each J_s(delta) expanded in its Taylor series
 // (Eq. 6) -- the same rearrangement as Section 5.1 with K and T unbounded:
@@ -559,6 +630,7 @@ int build_host_plan(const hankel_options& opt, HostPlan& hp) {
   build_partition(hp);
   if (hp.nend.empty()) return HANKEL_EINVAL;  // partition invariant violated
   build_columns(hp);
+  select_columns(hp);
   build_jtable(hp);
   return HANKEL_OK;
 }
@@ -587,7 +659,11 @@ double host_entry(const HostPlan& hp, int64_t k, int64_t n, int* is_far) {
     cplx ph(c, s), acc(0.0, 0.0);
     double rv = hp.rowvar[k - 1], rp = hp.rowpert[k - 1];
     double w = hp.omt[n - 1], bt = hp.betan[n - 1], cp = hp.colpow[n - 1];
-    for (const ColSpec& cs : hp.cols) {
+    const Block* blk = nullptr;
+    for (const Block& b : hp.blocks)
+      if (k >= b.k0 && k <= b.k1 && n >= b.n0 && n <= b.n1) blk = &b;
+    for (int l : blk->lcols) {
+      const ColSpec& cs = hp.cols[l];
       cplx poly(0.0, 0.0);
       for (int u2 = cs.nterm - 1; u2 >= 0; --u2) poly = poly * bt + cs.G[u2];
       double row = std::pow(rv, cs.delta - 0.5) * (cs.u1 ? std::pow(rp, cs.u1) : 1.0);

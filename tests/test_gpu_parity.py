@@ -158,6 +158,20 @@ def test_batched_matches_single():
         assert np.array_equal(fb[r], fs[0])
 
 
+@pytest.mark.parametrize("task,eps", [("dht", 1e-15), ("dht", 1e-8), ("fourier_bessel", 1e-15), ("dht", 1e-4)])
+def test_kept_columns_against_every_column(task, eps):
+    # blocks that leave out columns (bound eps/10 per entry) against blocks that keep all
+    N = 6000
+    c = coefficients("normal", N, 2, 5700)
+    fp, plan = _run(task, 0, N, eps, c)
+    fa, plan_all = _run(task, 0, N, eps, c, prune=False)
+    assert plan.info["block_cols"] < plan_all.info["block_cols"]
+    l1 = np.abs(c).sum(axis=1, keepdims=True)
+    assert np.all(np.abs(fp - fa) <= 2 * eps * l1)
+    ref = oracle.transform(task, 0, N, c)
+    assert np.all(np.abs(fp - ref) <= 10 * eps * l1)
+
+
 @pytest.mark.parametrize("eps,precision", [(1e-8, "fp64"), (1e-4, "fp32")])
 def test_chunks_that_split_right_hand_sides(eps, precision):
     # a small workspace cuts the stacked columns of one right-hand side across chunks; every

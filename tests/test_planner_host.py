@@ -132,3 +132,43 @@ def test_entries_against_oracle(case):
             v, far = p.entry(k, n)
             tol = eps if far else near_tol
             assert abs(v - ref[n - 1]) <= tol, (k, n, far, v, ref[n - 1])
+
+
+@pytest.mark.parametrize("case", [c for c in CASES if c[0] != "schlomilch"] + [("dht", 0, 20000, 1e-15, "unit")],
+                         ids=lambda c: "%s-nu%d-N%d-%g-%s" % c)
+def test_kept_columns_change_entries_within_their_bound(case):
+    # Each block leaves out stacked columns whose bound max|W_l| max|T_l| sums to at most
+    # eps/10 split over the blocks of one row; the plan's far entries move by no more than that
+    # (plus rounding) against the plan that keeps every column.
+    task, nu, N, eps, grid = case
+    p = hk.Plan(task, nu, N, eps, grid=grid, host_only=True)
+    q = hk.Plan(task, nu, N, eps, grid=grid, host_only=True, prune=False)
+    info, blocks = p.info, p.blocks()
+    assert all(b["ncols"] == info["ncols"] for b in q.blocks())
+    assert q.info["block_cols"] == info["ncols"] * len(blocks)
+    per_row = np.zeros(N + 2, dtype=int)
+    for b in blocks:
+        per_row[b["k0"]:b["k1"] + 1] += 1
+        assert 1 <= b["ncols"] <= info["ncols"]
+    for b in blocks:
+        assert b["dropped"] <= 0.1 * eps / per_row.max() * (1 + 1e-12)
+    rng = np.random.default_rng(5)
+    for b in blocks:
+        ks = rng.integers(b["k0"], b["k1"] + 1, 6)
+        ns = rng.integers(b["n0"], b["n1"] + 1, 6)
+        for k, n in zip(ks, ns):
+            vp, fp = p.entry(k, n)
+            vq, fq = q.entry(k, n)
+            assert fp and fq
+            assert abs(vp - vq) <= b["dropped"] + 4e-16, (k, n, vp, vq, b)
+
+
+def test_column_selection_shrinks_the_workload_transforms():
+    # DHT-0 at N = 2^20: rows and columns far from the near field barely feel the perturbations
+    # e_k omega_n and r b_n, so most of the 290 (eps = 1e-15) or 90 (1e-8) stacked columns go
+    for eps, full in [(1e-15, 290), (1e-8, 90)]:
+        p = hk.Plan("dht", 0, 2 ** 20, eps, host_only=True)
+        assert p.info["ncols"] == full
+        work = sum((b["nseg"] + 1 if b["mode"] else 2) * b["F"] * math.log2(b["F"]) * b["ncols"] for b in p.blocks())
+        work_all = sum((b["nseg"] + 1 if b["mode"] else 2) * b["F"] * math.log2(b["F"]) * full for b in p.blocks())
+        assert work < 0.25 * work_all
