@@ -88,6 +88,9 @@ enum hankel_status {
 #define HANKEL_FLAG_ALL_COLUMNS 8u /* every block keeps all ncols stacked columns; by default a block leaves
                                       out the columns whose summed bound on its entries stays within
                                       eps/10 per entry (hankel_block.ncols, hankel_info.block_cols) */
+#define HANKEL_FLAG_NO_REFINE 16u  /* keep the blocks of Eq. (19) as they are; by default a block is cut into
+                                      smaller ones where that lowers the estimated work (fewer kept columns
+                                      away from the near field) */
 
 /* Options for hankel_plan_ex(). Fill with hankel_options_default() first. */
 typedef struct {

@@ -13,6 +13,7 @@ FLAG_HOST_ONLY = 1
 FLAG_NO_SEGMENT = 2
 FLAG_NO_TABLES = 4
 FLAG_ALL_COLUMNS = 8
+FLAG_NO_REFINE = 16
 
 # Every function include/hankel.h declares.
 EXPORTED = [

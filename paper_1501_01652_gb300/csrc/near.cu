@@ -16,7 +16,9 @@ namespace hk {
 
 namespace {
 
-constexpr int kRhsGroup = 4;
+// Right-hand sides handled per table evaluation: every entry's J is evaluated once per group
+// of G vectors (G = 1, 2, 4, 8 or 16, the smallest that covers nrhs, groups of 16 beyond).
+constexpr int kMaxRhsGroup = 16;
 
 template <class R>
 __device__ __forceinline__ R table_j(const R* __restrict__ jtab, int64_t jt_n, int deg, R z) {
@@ -29,7 +31,7 @@ __device__ __forceinline__ R table_j(const R* __restrict__ jtab, int64_t jt_n, i
   return v;
 }
 
-template <class R>
+template <class R, int G>
 __global__ void __launch_bounds__(256) k_near(const NearItem* __restrict__ items, int64_t nitems, R* partial,
                                               int nrhs, const double* __restrict__ c, int64_t ldc, double* f,
                                               int64_t ldf, const R* __restrict__ r_true,
@@ -40,25 +42,25 @@ __global__ void __launch_bounds__(256) k_near(const NearItem* __restrict__ items
   if (warp >= nitems) return;
   const NearItem it = items[warp];
   const R r = r_true[it.k - 1];
-  for (int r0 = 0; r0 < nrhs; r0 += kRhsGroup) {
-    R acc[kRhsGroup];
+  for (int r0 = 0; r0 < nrhs; r0 += G) {
+    R acc[G];
 #pragma unroll
-    for (int g = 0; g < kRhsGroup; ++g) acc[g] = 0;
+    for (int g = 0; g < G; ++g) acc[g] = 0;
     for (int64_t n = it.n0 + lane; n <= it.n1; n += 32) {
       const R J = table_j(jtab, jt_n, deg, r * __ldg(&om_true[n - 1]));
 #pragma unroll
-      for (int g = 0; g < kRhsGroup; ++g)
+      for (int g = 0; g < G; ++g)
         if (r0 + g < nrhs) acc[g] = fmar((R)__ldg(&c[(int64_t)(r0 + g) * ldc + n - 1]), J, acc[g]);
     }
 #pragma unroll
-    for (int g = 0; g < kRhsGroup; ++g) {
+    for (int g = 0; g < G; ++g) {
       R v = acc[g];
       for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
       acc[g] = v;
     }
     if (lane == 0) {
 #pragma unroll
-      for (int g = 0; g < kRhsGroup; ++g) {
+      for (int g = 0; g < G; ++g) {
         if (r0 + g >= nrhs) break;
         if (it.slot < 0) f[(int64_t)(r0 + g) * ldf + it.k - 1] = acc[g];
         else partial[it.slot * nrhs + r0 + g] = acc[g];
@@ -87,8 +89,18 @@ void launch_near(const NearItem* items, int64_t nitems, const NearRow* mrows, in
                  const double* c, int64_t ldc, double* f, int64_t ldf, const R* r, const R* om, const R* jtab,
                  int64_t jt_n, int deg, cudaStream_t st) {
   const int64_t threads = nitems * 32;
-  k_near<R><<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(items, nitems, partial, nrhs, c, ldc, f, ldf, r, om,
-                                                                jtab, jt_n, deg);
+  const unsigned grid = (unsigned)((threads + 255) / 256);
+  if (nrhs <= 1)
+    k_near<R, 1><<<grid, 256, 0, st>>>(items, nitems, partial, nrhs, c, ldc, f, ldf, r, om, jtab, jt_n, deg);
+  else if (nrhs <= 2)
+    k_near<R, 2><<<grid, 256, 0, st>>>(items, nitems, partial, nrhs, c, ldc, f, ldf, r, om, jtab, jt_n, deg);
+  else if (nrhs <= 4)
+    k_near<R, 4><<<grid, 256, 0, st>>>(items, nitems, partial, nrhs, c, ldc, f, ldf, r, om, jtab, jt_n, deg);
+  else if (nrhs <= 8)
+    k_near<R, 8><<<grid, 256, 0, st>>>(items, nitems, partial, nrhs, c, ldc, f, ldf, r, om, jtab, jt_n, deg);
+  else
+    k_near<R, kMaxRhsGroup><<<grid, 256, 0, st>>>(items, nitems, partial, nrhs, c, ldc, f, ldf, r, om, jtab, jt_n,
+                                                  deg);
   if (nmrows > 0) {
     const int64_t n = nmrows * nrhs;
     k_near_combine<R><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(mrows, nmrows, partial, nrhs, f, ldf);

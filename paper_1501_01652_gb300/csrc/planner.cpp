@@ -397,10 +397,14 @@ void build_nodes(HostPlan& hp) {
 // few). Pick the length with the fewest estimated FP64 operations per column:
 // about 3.6 per point and radix-2 stage of each FFT plus 4 per point and segment
 // for the spectrum products.
+constexpr double kStageOps = 3.6, kMacOps = 4.0;
+
+double full_column_cost(const Block& b) { return 2.0 * b.F * b.logF * kStageOps + kMacOps * b.F; }
+
 void choose_segments(Block& b) {
   const int64_t thin = std::min(b.R, b.C), wide = std::max(b.R, b.C);
-  const double kStage = 3.6, kMac = 4.0;
-  double best = 2.0 * b.F * b.logF * kStage + kMac * b.F;
+  const double kStage = kStageOps, kMac = kMacOps;
+  double best = full_column_cost(b);
   for (int lf = 6; lf < b.logF; ++lf) {
     const int64_t Fs = int64_t(1) << lf;
     if (Fs < 2 * thin) continue;
@@ -418,6 +422,29 @@ void choose_segments(Block& b) {
   }
 }
 
+// Estimated FP64 operations per stacked column of a block (the model of choose_segments).
+double column_cost(const Block& b) {
+  if (b.mode == kBlockFull) return full_column_cost(b);
+  return (double)(b.nseg + 1) * b.F * b.logF * kStageOps + kMacOps * (double)b.nseg * b.F;
+}
+
+// A far block on rows k0..k1 and columns n0..n1 with its transform length and segmenting.
+Block make_block(const HostPlan& hp, int64_t k0, int64_t k1, int64_t n0, int64_t n1) {
+  Block b;
+  b.k0 = k0; b.k1 = k1; b.n0 = n0; b.n1 = n1;
+  b.R = k1 - k0 + 1;
+  b.C = n1 - n0 + 1;
+  int lf = 6;  // at least 64 points
+  while ((int64_t(1) << lf) < b.R + b.C - 1) ++lf;
+  b.logF = lf;
+  b.F = int64_t(1) << lf;
+  b.mode = kBlockFull;
+  b.S = b.C;
+  b.nseg = 1;
+  if (!(hp.opt.flags & HANKEL_FLAG_NO_SEGMENT)) choose_segments(b);
+  return b;
+}
+
 void build_partition(HostPlan& hp) {
   const int64_t N = hp.opt.N;
   const double sq = std::sqrt(hp.D);
@@ -431,19 +458,7 @@ void build_partition(HostPlan& hp) {
     k1 = std::min(k1, N);
     n1 = std::min(n1, N);
     if (k0 > k1 || n0 > n1) return;
-    Block b;
-    b.k0 = k0; b.k1 = k1; b.n0 = n0; b.n1 = n1;
-    b.R = k1 - k0 + 1;
-    b.C = n1 - n0 + 1;
-    int lf = 6;  // at least 64 points
-    while ((int64_t(1) << lf) < b.R + b.C - 1) ++lf;
-    b.logF = lf;
-    b.F = int64_t(1) << lf;
-    b.mode = kBlockFull;
-    b.S = b.C;
-    b.nseg = 1;
-    if (!(hp.opt.flags & HANKEL_FLAG_NO_SEGMENT)) choose_segments(b);
-    raw.push_back(b);
+    raw.push_back(make_block(hp, k0, k1, n0, n1));
   };
   // Eq. (19): Q1 J Q1 and, for p = 1..P, Q_{2p+1} J Q_{2p} and Q_{2p} J Q_{2p+1}, with the
   // row band of Q_{2p+1} read as [alpha beta^p sqrt(N), alpha beta^{p-1} sqrt(N)).
@@ -518,22 +533,161 @@ void build_columns(HostPlan& hp) {
 }
 
 // Per-block choice of stacked columns. Column l contributes W_l(k) T_l(n) to entry (k, n) of
-// a block (times a unimodular chirp), with |W_l(k)| = |rowpert|^u1 rowvar^(delta-1/2) and
-// |T_l(n)| <= |colpow|^u1 omt^(delta-1/2) sum_u2 |G_l[u2]| |beta|^u2. Each factor is a power of
-// a positive quantity, so its largest value over the block is taken at the block's extreme
-// node values, and A_l = max|W_l| max|T_l| bounds the column's share of any entry. The
-// truncations K, T, K2, T2 and M are fixed for the worst block (Sections 5.2, 6.1); in blocks
-// far from the near field the perturbations e_k omega_n and r b_n are orders of magnitude
-// smaller, and many columns contribute less than eps. A block drops its columns in increasing
-// order of A_l while their sum stays within its share of a budget of kDropFrac * eps per entry
-// (split evenly between the blocks that meet in one row); the change of every entry is at
-// most that sum, so |f_k - f'_k| <= kDropFrac * eps * sum_n |c_n|.
+// a block (times a unimodular chirp), with W_l(k) = rowpert^u1 rowvar^(delta-1/2) and
+// |T_l(n)| <= |colpow^u1| omt^(delta-1/2) sum_u2 |G_l[u2]| |beta|^u2. Written as
+//   |W_l(k)| = (|rowpert| rowvar)^u1 rowvar^(delta-1/2-u1),
+//   |colpow^u1 omt^(delta-1/2)| = (|colpow|/omt)^u1 omt^(delta-1/2+u1),
+// each is a slowly varying factor (e_k r~_k and omega_n/omega~_n change little over a
+// block) times a power of a monotone node value, so the block maxima of the slowly varying
+// factors (found by a scan) and of the powers (at the block's end nodes) bound max|W_l| and
+// max|T_l| closely, and A_l = max|W_l| max|T_l| bounds the column's share of every entry.
+// The truncations K, T, K2, T2 and M are fixed for the worst block (Sections 5.2, 6.1); far
+// from the near field the perturbations e_k omega_n and r b_n are tiny and many columns
+// contribute less than eps. A block drops its columns in increasing order of A_l while their
+// sum stays within its share of a budget of kDropFrac * eps per entry (split evenly between
+// the blocks that meet in one row); every entry then moves by at most that sum, so
+// |f_k - f'_k| <= kDropFrac * eps * sum_n |c_n|.
 constexpr double kDropFrac = 0.1;
+// Blocks that may meet in one row while a block's budget is kDropFrac * eps / kRowBlocks.
+constexpr int kRowBlocks = 16;
+
+// Range maxima of a node sequence over index ranges, from maxima of chunks of 1024.
+struct RangeMax {
+  std::vector<double> v, chunk;
+  static constexpr int64_t kChunk = 1024;
+  explicit RangeMax(std::vector<double> x) : v(std::move(x)) {
+    chunk.assign((v.size() + kChunk - 1) / kChunk, -INFINITY);
+    for (size_t i = 0; i < v.size(); ++i) chunk[i / kChunk] = std::max(chunk[i / kChunk], v[i]);
+  }
+  double max(int64_t a, int64_t b) const {  // 0-based inclusive
+    double m = -INFINITY;
+    while (a <= b && a % kChunk) m = std::max(m, v[a++]);
+    while (a + kChunk - 1 <= b) m = std::max(m, chunk[a / kChunk]), a += kChunk;
+    while (a <= b) m = std::max(m, v[a++]);
+    return m;
+  }
+};
+
+struct NodeRanges {
+  RangeMax rp, rv, nrv, cp, om, nom, bt;  // maxima of |e_k| r~_k, rowvar, -rowvar, colpow/omt, omt, -omt, |beta|
+  explicit NodeRanges(const HostPlan& hp)
+      : rp(map(hp.rowpert, hp.rowvar, [](double e, double r) { return std::fabs(e) * r; })),
+        rv(hp.rowvar),
+        nrv(map(hp.rowvar, hp.rowvar, [](double r, double) { return -r; })),
+        cp(map(hp.colpow, hp.omt, [](double c, double w) { return std::fabs(c) / w; })),
+        om(hp.omt),
+        nom(map(hp.omt, hp.omt, [](double w, double) { return -w; })),
+        bt(map(hp.betan, hp.betan, [](double b, double) { return std::fabs(b); })) {}
+  template <class Fn>
+  static std::vector<double> map(const std::vector<double>& a, const std::vector<double>& b, Fn fn) {
+    std::vector<double> o(a.size());
+    for (size_t i = 0; i < a.size(); ++i) o[i] = fn(a[i], b[i]);
+    return o;
+  }
+};
+
+void block_columns(const HostPlan& hp, const NodeRanges& nr, Block& b, double budget) {
+  const int ncols = (int)hp.cols.size();
+  b.lcols.clear();
+  b.dropped = 0.0;
+  if (hp.opt.flags & HANKEL_FLAG_ALL_COLUMNS) {
+    for (int l = 0; l < ncols; ++l) b.lcols.push_back(l);
+    return;
+  }
+  const double rp = nr.rp.max(b.k0 - 1, b.k1 - 1), rv0 = -nr.nrv.max(b.k0 - 1, b.k1 - 1),
+               rv1 = nr.rv.max(b.k0 - 1, b.k1 - 1);
+  const double cp = nr.cp.max(b.n0 - 1, b.n1 - 1), om0 = -nr.nom.max(b.n0 - 1, b.n1 - 1),
+               om1 = nr.om.max(b.n0 - 1, b.n1 - 1), bt = nr.bt.max(b.n0 - 1, b.n1 - 1);
+  auto pw = [](double x, double e) { return std::pow(x, e); };
+  std::vector<std::pair<double, int>> bound(ncols);
+  for (int l = 0; l < ncols; ++l) {
+    const ColSpec& cs = hp.cols[l];
+    const double er = cs.delta - 0.5 - cs.u1, ec = cs.delta - 0.5 + cs.u1;
+    double poly = 0.0, bp = 1.0;
+    for (int u = 0; u < cs.nterm; ++u, bp *= bt) poly += std::abs(cs.G[u]) * bp;
+    double a = std::max(pw(rv0, er), pw(rv1, er)) * std::max(pw(om0, ec), pw(om1, ec)) * poly;
+    if (cs.u1) a *= pw(rp, cs.u1) * pw(cp, cs.u1);
+    bound[l] = {std::isfinite(a) ? a : INFINITY, l};
+  }
+  std::sort(bound.begin(), bound.end());
+  std::vector<char> keep(ncols, 1);
+  double sum = 0.0;
+  for (const auto& x : bound) {
+    if (sum + x.first > budget) break;
+    sum += x.first;
+    keep[x.second] = 0;
+  }
+  b.dropped = sum;
+  for (int l = 0; l < ncols; ++l)
+    if (keep[l]) b.lcols.push_back(l);
+  if (b.lcols.empty()) b.lcols.push_back(bound.back().second);  // every block keeps one column
+}
+
+// Subdivision of the far blocks (an addition to the partition of Eq. 19). The blocks of
+// Eq. (19) touch the near field at one corner, where z~ ~ s and every stacked column is
+// needed, but stretch to z~ ~ N: away from that corner the Hankel tail and the perturbation
+// terms shrink and far fewer columns pass the drop bound. A block is cut in two, across its
+// rows or its columns at one of a few geometric points, when the cut lowers the estimated
+// work (kept columns x column_cost, plus a fixed cost per block execution spread over
+// max_nrhs vectors); the halves are refined again. The union of the blocks, hence the near
+// set, does not change.
+constexpr double kBlockLaunchOps = 1e7;  // FP64-operation equivalent of the launches of one block
+constexpr int64_t kMinSide = 64;
+
+double block_work(const HostPlan& hp, const Block& b) {
+  return (double)b.lcols.size() * column_cost(b) + kBlockLaunchOps / hp.opt.max_nrhs;
+}
+
+void refine(const HostPlan& hp, const NodeRanges& nr, Block b, double budget, int depth, std::vector<Block>& out) {
+  block_columns(hp, nr, b, budget);
+  const double w0 = block_work(hp, b);
+  double best = 0.97 * w0;
+  Block bl1, bl2;
+  bool found = false;
+  auto consider = [&](Block c1, Block c2) {
+    block_columns(hp, nr, c1, budget);
+    block_columns(hp, nr, c2, budget);
+    const double w = block_work(hp, c1) + block_work(hp, c2);
+    if (w < best) {
+      best = w;
+      bl1 = c1;
+      bl2 = c2;
+      found = true;
+    }
+  };
+  if (depth < 24) {
+    for (double t : {0.25, 0.5, 0.75}) {
+      if (b.R >= 2 * kMinSide) {
+        int64_t km = (int64_t)std::llround(std::exp((1 - t) * std::log((double)b.k0) + t * std::log((double)b.k1)));
+        km = std::min(std::max(km, b.k0 + kMinSide), b.k1 - kMinSide + 1);
+        consider(make_block(hp, b.k0, km - 1, b.n0, b.n1), make_block(hp, km, b.k1, b.n0, b.n1));
+      }
+      if (b.C >= 2 * kMinSide) {
+        int64_t nm = (int64_t)std::llround(std::exp((1 - t) * std::log((double)b.n0) + t * std::log((double)b.n1)));
+        nm = std::min(std::max(nm, b.n0 + kMinSide), b.n1 - kMinSide + 1);
+        consider(make_block(hp, b.k0, b.k1, b.n0, nm - 1), make_block(hp, b.k0, b.k1, nm, b.n1));
+      }
+    }
+  }
+  if (!found) {
+    out.push_back(b);
+    return;
+  }
+  refine(hp, nr, bl1, budget, depth + 1, out);
+  refine(hp, nr, bl2, budget, depth + 1, out);
+}
 
 void select_columns(HostPlan& hp) {
   const int64_t N = hp.opt.N;
-  const int ncols = (int)hp.cols.size();
-  // blocks meeting in one row
+  NodeRanges nr(hp);
+  double budget = kDropFrac * hp.opt.eps / kRowBlocks;
+  const bool subdivide = !(hp.opt.flags & (HANKEL_FLAG_NO_REFINE | HANKEL_FLAG_ALL_COLUMNS));
+  if (subdivide) {
+    std::vector<Block> out;
+    for (const Block& b : hp.blocks) refine(hp, nr, b, budget, 0, out);
+    hp.blocks = out;
+  }
+  // blocks meeting in one row; the budget must cover all of them
   std::vector<int> per_row(N + 2, 0);
   for (const Block& b : hp.blocks) {
     per_row[b.k0] += 1;
@@ -541,51 +695,8 @@ void select_columns(HostPlan& hp) {
   }
   int maxrow = 1, run = 0;
   for (int64_t k = 1; k <= N; ++k) maxrow = std::max(maxrow, run += per_row[k]);
-  const double budget = kDropFrac * hp.opt.eps / maxrow;
-  const bool keep_all = (hp.opt.flags & HANKEL_FLAG_ALL_COLUMNS) != 0;
-  auto pw = [](double x, double e) { return std::pow(x, e); };
-  for (Block& b : hp.blocks) {
-    b.lcols.clear();
-    b.dropped = 0.0;
-    if (keep_all) {
-      for (int l = 0; l < ncols; ++l) b.lcols.push_back(l);
-      continue;
-    }
-    double rp = 0.0, rv0 = INFINITY, rv1 = 0.0, cp = 0.0, om0 = INFINITY, om1 = 0.0, bt = 0.0;
-    for (int64_t k = b.k0; k <= b.k1; ++k) {
-      rp = std::max(rp, std::fabs(hp.rowpert[k - 1]));
-      rv0 = std::min(rv0, hp.rowvar[k - 1]);
-      rv1 = std::max(rv1, hp.rowvar[k - 1]);
-    }
-    for (int64_t n = b.n0; n <= b.n1; ++n) {
-      cp = std::max(cp, std::fabs(hp.colpow[n - 1]));
-      om0 = std::min(om0, hp.omt[n - 1]);
-      om1 = std::max(om1, hp.omt[n - 1]);
-      bt = std::max(bt, std::fabs(hp.betan[n - 1]));
-    }
-    std::vector<std::pair<double, int>> bound(ncols);
-    for (int l = 0; l < ncols; ++l) {
-      const ColSpec& cs = hp.cols[l];
-      const double e = cs.delta - 0.5;
-      double poly = 0.0, bp = 1.0;
-      for (int u = 0; u < cs.nterm; ++u, bp *= bt) poly += std::abs(cs.G[u]) * bp;
-      double a = std::max(pw(rv0, e), pw(rv1, e)) * std::max(pw(om0, e), pw(om1, e)) * poly;
-      if (cs.u1) a *= pw(rp, cs.u1) * pw(cp, cs.u1);
-      bound[l] = {std::isfinite(a) ? a : INFINITY, l};
-    }
-    std::sort(bound.begin(), bound.end());
-    std::vector<char> keep(ncols, 1);
-    double sum = 0.0;
-    for (const auto& x : bound) {
-      if (sum + x.first > budget) break;
-      sum += x.first;
-      keep[x.second] = 0;
-    }
-    b.dropped = sum;
-    for (int l = 0; l < ncols; ++l)
-      if (keep[l]) b.lcols.push_back(l);
-    if (b.lcols.empty()) b.lcols.push_back(bound.back().second);  // every block keeps one column
-  }
+  budget = kDropFrac * hp.opt.eps / std::max(maxrow, subdivide ? kRowBlocks : 1);
+  for (Block& b : hp.blocks) block_columns(hp, nr, b, budget);
 }
 
 // Taylor polynomials of J_nu about z_c = i + 1/2 on [i, i+1). The coefficients follow from

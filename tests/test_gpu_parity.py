@@ -150,11 +150,13 @@ def test_dht_2p20_sampled_rows(eps):
 
 
 def test_batched_matches_single():
+    # one plan (its blocks depend on max_nrhs): five vectors at once equal five single calls
     N = 3000
     c = coefficients("normal", N, 5, 6000)
-    fb, plan = _run("dht", 0, N, 1e-8, c)
+    plan = hk.Plan("dht", 0, N, 1e-8, max_nrhs=5)
+    fb = plan.exec(torch.from_numpy(c).cuda()).cpu().numpy()
     for r in range(c.shape[0]):
-        fs, _ = _run("dht", 0, N, 1e-8, c[r:r + 1])
+        fs = plan.exec(torch.from_numpy(c[r:r + 1]).cuda()).cpu().numpy()
         assert np.array_equal(fb[r], fs[0])
 
 

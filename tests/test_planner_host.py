@@ -47,11 +47,31 @@ def test_precision_policy():
 
 
 def test_thin_blocks_are_segmented_at_workload_size():
-    p = hk.Plan("dht", 0, 2 ** 20, 1e-15, host_only=True)
+    # Eq. (19) at N = 2^20 (P = 3): one square block and three thin ones on each side
+    p = hk.Plan("dht", 0, 2 ** 20, 1e-15, host_only=True, refine=False)
     modes = sorted(b["mode"] for b in p.blocks())
     assert modes == [0, 1, 1, 1, 2, 2, 2]
     q = hk.Plan("dht", 0, 2 ** 20, 1e-15, host_only=True, segment=False)
     assert all(b["mode"] == 0 and b["nseg"] == 1 for b in q.blocks())
+    r = hk.Plan("dht", 0, 2 ** 20, 1e-15, host_only=True)
+    assert {b["mode"] for b in r.blocks()} == {0, 1, 2}
+
+
+@pytest.mark.parametrize("case", CASES + [("dht", 0, 2 ** 18, 1e-15, "unit"), ("schlomilch", 0, 2 ** 18, 1e-8, "unit")],
+                         ids=lambda c: "%s-nu%d-N%d-%g-%s" % c)
+def test_subdivided_blocks_tile_the_same_far_set(case):
+    # cutting blocks changes neither the near prefixes nor the far entries covered, and the
+    # pieces do not overlap (their areas add up to the far count)
+    task, nu, N, eps, grid = case
+    p = hk.Plan(task, nu, N, eps, grid=grid, host_only=True)
+    q = hk.Plan(task, nu, N, eps, grid=grid, host_only=True, refine=False)
+    assert p.info["far_count"] == q.info["far_count"]
+    assert sum((b["k1"] - b["k0"] + 1) * (b["n1"] - b["n0"] + 1) for b in p.blocks()) == p.info["far_count"]
+    for k in sorted({1, 2, N // 3, N // 2, N}):
+        assert p.near_prefix(k) == q.near_prefix(k)
+    for b in p.blocks():
+        assert any(c["k0"] <= b["k0"] and b["k1"] <= c["k1"] and c["n0"] <= b["n0"] and b["n1"] <= c["n1"]
+                   for c in q.blocks())
 
 
 def test_node_offsets_against_oracle_and_lemma():
@@ -145,7 +165,7 @@ def test_kept_columns_change_entries_within_their_bound(case):
     q = hk.Plan(task, nu, N, eps, grid=grid, host_only=True, prune=False)
     info, blocks = p.info, p.blocks()
     assert all(b["ncols"] == info["ncols"] for b in q.blocks())
-    assert q.info["block_cols"] == info["ncols"] * len(blocks)
+    assert q.info["block_cols"] == info["ncols"] * len(q.blocks())
     per_row = np.zeros(N + 2, dtype=int)
     for b in blocks:
         per_row[b["k0"]:b["k1"] + 1] += 1
@@ -163,12 +183,18 @@ def test_kept_columns_change_entries_within_their_bound(case):
             assert abs(vp - vq) <= b["dropped"] + 4e-16, (k, n, vp, vq, b)
 
 
+def _fft_work(plan):
+    return sum((b["nseg"] + 1 if b["mode"] else 2) * b["F"] * math.log2(b["F"]) * b["ncols"] for b in plan.blocks())
+
+
 def test_column_selection_shrinks_the_workload_transforms():
     # DHT-0 at N = 2^20: rows and columns far from the near field barely feel the perturbations
-    # e_k omega_n and r b_n, so most of the 290 (eps = 1e-15) or 90 (1e-8) stacked columns go
+    # e_k omega_n and r b_n, so most of the 290 (eps = 1e-15) or 90 (1e-8) stacked columns go;
+    # cutting the blocks further from the near field drops more
     for eps, full in [(1e-15, 290), (1e-8, 90)]:
-        p = hk.Plan("dht", 0, 2 ** 20, eps, host_only=True)
-        assert p.info["ncols"] == full
-        work = sum((b["nseg"] + 1 if b["mode"] else 2) * b["F"] * math.log2(b["F"]) * b["ncols"] for b in p.blocks())
-        work_all = sum((b["nseg"] + 1 if b["mode"] else 2) * b["F"] * math.log2(b["F"]) * full for b in p.blocks())
-        assert work < 0.25 * work_all
+        p = hk.Plan("dht", 0, 2 ** 20, eps, host_only=True, refine=False)
+        r = hk.Plan("dht", 0, 2 ** 20, eps, host_only=True, max_nrhs=16)
+        q = hk.Plan("dht", 0, 2 ** 20, eps, host_only=True, prune=False)
+        assert p.info["ncols"] == full and all(b["ncols"] == full for b in q.blocks())
+        assert _fft_work(p) < 0.2 * _fft_work(q)
+        assert _fft_work(r) < 0.7 * _fft_work(p)
