@@ -32,9 +32,10 @@ from hankel_inputs import coefficients, sample_rows, seed_for  # noqa: E402
 FP64_PEAK_GFLOPS = 152 * 4 * 2.07  # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz = 1258 GFLOP/s
 HBM_FALLBACK_GBS = 6800.0          # used only when MEASURED_PEAKS.json is absent
 FP64_MEASURED_GFLOPS = 1004.0      # DFMA microbenchmark on this part (2 x 502 G instructions/s)
-# DRAM bytes per algorithmic byte of a k_fft_pass launch, from an ncu capture of one radix-64
-# forward pass over 290 columns of 2^17 points (1167.9 MB measured / 1216.3 MB algorithmic).
-FFT_TRAFFIC_RATIO = 1167.9 / 1216.3
+# DRAM bytes per algorithmic byte of an FP64 FFT pass launch, from an ncu capture of one
+# radix-128 inverse pass (k_fft_pass_reg, 4608 CTAs of 16 x 128 points: 151.0 MB read +
+# 104.7 MB written, 302.0 MB algorithmic; part of the output is still in L2 at kernel end).
+FFT_TRAFFIC_RATIO = (151.05 + 104.67) / 301.99
 METRIC = "DHT-0 coeffs/s at N=2^20 (eps=1e-8,1e-15) served vs plain FP64; p50/p99 ms"
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -145,6 +146,15 @@ def cpu_baseline(N, rows_count, seed):
             "seconds": dt}
 
 
+def workload_config(args):
+    """The workload both arms report: DHT-0 at N, every eps of --eps, batches of --nrhs vectors."""
+    B = args.nrhs
+    return {"workload": "dht0_N%d_eps%s_batch%d" % (args.N, "+".join(args.eps.split(",")), B),
+            "N": args.N, "eps": [float(e) for e in args.eps.split(",")], "batch": B,
+            "form": "served/batched: %d vectors per execution per plan, precision by eps (FP64 below 1e-5)" % B,
+            "l2": "flushed between timed steps (256 MB write)", "coefficients": "N(0,1) seeded"}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -164,14 +174,13 @@ def run_reference(args):
             rows_total += args.cpu_rows
     # the oracle's cost does not depend on eps; one step covers both eps values of the workload
     value = rows_total / sum(times)
-    ms_per_step = 1000.0 * len(eps) * N / value
+    ms_per_step = 1000.0 * len(eps) * N * args.nrhs / value  # the same step as the GPU arm: every eps, a batch
     cores = len(os.sched_getaffinity(0))
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "coeffs/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "dht0_N%d_eps%s" % (N, "+".join(args.eps.split(","))), "N": N, "eps": eps,
-                   "nrhs": 1, "sample_rows_per_step": args.cpu_rows},
+        "config": dict(workload_config(args), sample_rows_per_step=args.cpu_rows),
         "cpu_baseline": {"value": value, "unit": "coeffs/s", "cores": cores, "kind": "oracle",
                          "sample": "%d seeded rows per step of a DHT-0 at N=%d" % (args.cpu_rows, N)},
         "e2e": {"value": value, "unit": "coeffs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -358,11 +367,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": "coeffs/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if fp32 else "f64", "data": "synthetic",
-        "config": {"workload": "dht0_N%d_eps%s_batch%d" % (N, "+".join(args.eps.split(",")), B),
-                   "N": N, "eps": eps_list, "batch": B,
-                   "form": "served/batched: %d vectors per execution per plan, precision by eps (FP64 below 1e-5)"
-                           % B,
-                   "l2": "flushed between timed steps (256 MB write)", "coefficients": "N(0,1) seeded"},
+        "config": workload_config(args),
         "per_eps": {str(e): {"batch_ms": statistics.mean(m),
                              "coeffs_per_s": N * B / (statistics.mean(m) / 1000.0),
                              "plain_ms": statistics.mean(pm) if plain_cps else None}
