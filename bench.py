@@ -134,16 +134,21 @@ def cpu_baseline(N, rows_count, seed):
     import oracle
 
     c = coefficients("normal", N, 1, seed)[0]
-    rows = sample_rows(N, rows_count, seed + 1)
+    rows = base_rows(N, rows_count, seed)
     t0 = time.perf_counter()
-    oracle.transform("dht", 0, N, c, rows=rows)
+    f = oracle.transform("dht", 0, N, c, rows=rows)
     dt = time.perf_counter() - t0
     cores = len(os.sched_getaffinity(0))
     # one output row costs N J-evaluations; a full transform is N rows, so coefficients/s = rows/s
     return {"value": len(rows) / dt, "unit": "coeffs/s", "cores": cores, "kind": "oracle",
             "sample": "%d of %d rows of one DHT-0 at N=%d (direct O(N^2) FP64 Kahan sum; rows/s = "
                       "coefficients/s of a full transform)" % (len(rows), N, N),
-            "seconds": dt}
+            "seconds": dt, "f": np.asarray(f).reshape(-1)}
+
+
+def base_rows(N, rows_count, seed):
+    """Rows (0-based) the CPU baseline evaluates."""
+    return sample_rows(N, rows_count, seed + 1)
 
 
 def workload_config(args):
@@ -169,6 +174,7 @@ def run_reference(args):
     rows_total = 0
     for step in range(args.warmup + args.steps):
         r = cpu_baseline(N, args.cpu_rows, seed_for(4, step))
+        r.pop("f")
         if step >= args.warmup:
             times.append(r["seconds"])
             rows_total += args.cpu_rows
@@ -323,6 +329,14 @@ def run_ours(args):
     launches = sum(st[k]["launches"] for st in stats for k in st)
     stage_ms = {k: round(sum(st[k]["ms"] for st in stats) / args.steps, 3) for k in stats[0]}
     fp32 = all(p.info["precision"] == 2 for p in plans)
+    # accuracy of the timed plans on the CPU baseline's vector and rows (checked by the oracle
+    # there, outside every timed region)
+    err_c = coefficients("normal", N, 1, seed_for(4, 99))
+    f_err = []
+    if world == 1 and not args.no_cpu_baseline and not args.quick:
+        ce = torch.from_numpy(err_c).to(dev)
+        for p in plans:
+            f_err.append(p.exec(ce).cpu().numpy()[0])
     for p in plans:
         p.destroy()
     del fs
@@ -393,7 +407,13 @@ def run_ours(args):
         "wall_s_timed": wall,
     }
     if world == 1 and not args.no_cpu_baseline and not args.quick:
-        line["cpu_baseline"] = cpu_baseline(N, args.cpu_rows, seed_for(4, 99))
+        base = cpu_baseline(N, args.cpu_rows, seed_for(4, 99))
+        ref = base.pop("f")
+        line["cpu_baseline"] = base
+        # max over the sampled rows of |f - f_oracle| / (eps sum|c|); the parity bar is 10
+        l1 = float(np.abs(err_c).sum())
+        line["error_vs_oracle"] = {str(e): float(np.max(np.abs(f[base_rows(N, args.cpu_rows, seed_for(4, 99))] - ref))
+                                                / (e * l1)) for e, f in zip(eps_list, f_err)}
     print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -208,6 +208,13 @@ int hankel_plan_blocks(hankel_plan_t p, hankel_block* out, int cap, int* count);
  * far-field block. Slow; for tests. Host only. */
 int hankel_plan_entry(hankel_plan_t p, int64_t k, int64_t n, double* value, int* is_far);
 
+/* Host evaluation of the far-field expansion (Eq. 4 with the Neumann/Taylor sums of Eqs. 21-22
+ * and 26, every stacked column) at entry (k, n), 1-based, wherever the entry lies: the value
+ * the transform would use if the partition of Eq. (19) were dropped and the expansion applied
+ * to every entry. Where z = r_k omega_n is below s_{nu,M} it is not eps-accurate (Section 3.1;
+ * at r_k = 0 it is not finite). For tests of the partition. Host only. Errors: EINVAL. */
+int hankel_plan_expansion_entry(hankel_plan_t p, int64_t k, int64_t n, double* value);
+
 /* Near-field prefix of row k (1-based): columns 1..*nend are summed directly. Host only. */
 int hankel_plan_near_prefix(hankel_plan_t p, int64_t k, int64_t* nend);
 

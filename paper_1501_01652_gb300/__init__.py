@@ -121,6 +121,13 @@ class Plan:
                    "hankel_plan_entry")
         return v.value, bool(far.value)
 
+    def expansion_entry(self, k, n):
+        """The far-field expansion at entry (k, n), 1-based, ignoring the partition."""
+        v = ctypes.c_double()
+        _lib.check(self._lib.hankel_plan_expansion_entry(self._h, int(k), int(n), ctypes.byref(v)),
+                   "hankel_plan_expansion_entry")
+        return v.value
+
     def near_prefix(self, k):
         ne = ctypes.c_int64()
         _lib.check(self._lib.hankel_plan_near_prefix(self._h, int(k), ctypes.byref(ne)), "hankel_plan_near_prefix")

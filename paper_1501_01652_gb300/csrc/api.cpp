@@ -169,6 +169,13 @@ int hankel_plan_entry(hankel_plan_t p, int64_t k, int64_t n, double* value, int*
   return HANKEL_OK;
 }
 
+int hankel_plan_expansion_entry(hankel_plan_t p, int64_t k, int64_t n, double* value) {
+  if (!p || !value) return HANKEL_EINVAL;
+  if (k < 1 || k > p->hp.opt.N || n < 1 || n > p->hp.opt.N) return HANKEL_EINVAL;
+  *value = hk::expansion_entry(p->hp, k, n, nullptr);
+  return HANKEL_OK;
+}
+
 int hankel_plan_near_prefix(hankel_plan_t p, int64_t k, int64_t* nend) {
   if (!p || !nend || k < 1 || k > p->hp.opt.N) return HANKEL_EINVAL;
   *nend = p->hp.nend[k - 1];

@@ -86,6 +86,9 @@ int build_host_plan(const hankel_options& opt, HostPlan& hp);
 int choose_params(const hankel_options& opt, HostPlan& hp);
 // Host value of the plan's representation of entry (k, n), 1-based.
 double host_entry(const HostPlan& hp, int64_t k, int64_t n, int* is_far);
+// The far-field expansion of entry (k, n) over the listed stacked columns (all when null),
+// wherever (k, n) lies.
+double expansion_entry(const HostPlan& hp, int64_t k, int64_t n, const std::vector<int>* lcols);
 // Near-field J from the Taylor table (host copy of the device evaluator).
 double table_j(const HostPlan& hp, double z);
 // j_{0,n} - (n-1/4)pi for n = 1..count.

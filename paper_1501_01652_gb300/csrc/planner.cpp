@@ -757,33 +757,38 @@ double table_j(const HostPlan& hp, double z) {
   return v;
 }
 
+// The far-field representation of entry (k, n) summed over the given stacked columns:
+// Re[ exp(i theta~_kn) sum_l rowfun_l(k) colfun_l(n) ].
+double expansion_entry(const HostPlan& hp, int64_t k, int64_t n, const std::vector<int>* lcols) {
+  // exp(i theta~_kn), theta~ = pi U_k V_n / E reduced exactly
+  __int128 U = (__int128)hp.Ua * k + hp.Ub, V = (__int128)hp.Va * n + hp.Vb;
+  __int128 num = (U * V) % ((__int128)2 * hp.E);
+  double s, c;
+  sincospi_ratio((int64_t)num, hp.E, &s, &c);
+  cplx ph(c, s), acc(0.0, 0.0);
+  double rv = hp.rowvar[k - 1], rp = hp.rowpert[k - 1];
+  double w = hp.omt[n - 1], bt = hp.betan[n - 1], cp = hp.colpow[n - 1];
+  const size_t count = lcols ? lcols->size() : hp.cols.size();
+  for (size_t j = 0; j < count; ++j) {
+    const ColSpec& cs = hp.cols[lcols ? (*lcols)[j] : (int)j];
+    cplx poly(0.0, 0.0);
+    for (int u2 = cs.nterm - 1; u2 >= 0; --u2) poly = poly * bt + cs.G[u2];
+    double row = std::pow(rv, cs.delta - 0.5) * (cs.u1 ? std::pow(rp, cs.u1) : 1.0);
+    double col = std::pow(w, cs.delta - 0.5) * (cs.u1 ? std::pow(cp, cs.u1) : 1.0);
+    acc += row * col * poly;
+  }
+  return (ph * acc).real();
+}
+
 double host_entry(const HostPlan& hp, int64_t k, int64_t n, int* is_far) {
-  const int64_t N = hp.opt.N;
   *is_far = 0;
   if (n > hp.nend[k - 1]) {
     *is_far = 1;
-    // exp(i theta~_kn), theta~ = pi U_k V_n / E reduced exactly
-    __int128 U = (__int128)hp.Ua * k + hp.Ub, V = (__int128)hp.Va * n + hp.Vb;
-    __int128 num = (U * V) % ((__int128)2 * hp.E);
-    double s, c;
-    sincospi_ratio((int64_t)num, hp.E, &s, &c);
-    cplx ph(c, s), acc(0.0, 0.0);
-    double rv = hp.rowvar[k - 1], rp = hp.rowpert[k - 1];
-    double w = hp.omt[n - 1], bt = hp.betan[n - 1], cp = hp.colpow[n - 1];
     const Block* blk = nullptr;
     for (const Block& b : hp.blocks)
       if (k >= b.k0 && k <= b.k1 && n >= b.n0 && n <= b.n1) blk = &b;
-    for (int l : blk->lcols) {
-      const ColSpec& cs = hp.cols[l];
-      cplx poly(0.0, 0.0);
-      for (int u2 = cs.nterm - 1; u2 >= 0; --u2) poly = poly * bt + cs.G[u2];
-      double row = std::pow(rv, cs.delta - 0.5) * (cs.u1 ? std::pow(rp, cs.u1) : 1.0);
-      double col = std::pow(w, cs.delta - 0.5) * (cs.u1 ? std::pow(cp, cs.u1) : 1.0);
-      acc += row * col * poly;
-    }
-    return (ph * acc).real();
+    return expansion_entry(hp, k, n, &blk->lcols);
   }
-  (void)N;
   return table_j(hp, hp.r_true[k - 1] * hp.om_true[n - 1]);
 }
 

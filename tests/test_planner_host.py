@@ -198,3 +198,24 @@ def test_column_selection_shrinks_the_workload_transforms():
         assert p.info["ncols"] == full and all(b["ncols"] == full for b in q.blocks())
         assert _fft_work(p) < 0.2 * _fft_work(q)
         assert _fft_work(r) < 0.7 * _fft_work(p)
+
+
+@pytest.mark.parametrize("task,nu,N,eps,grid", [("dht", 0, 300, 1e-15, "unit"), ("schlomilch", 0, 300, 1e-8, "paper"),
+                                                ("fourier_bessel", 0, 300, 1e-15, "paper")])
+def test_expansion_without_the_partition_fails_the_bar(task, nu, N, eps, grid):
+    # Negative test: the far-field expansion used for every entry (the partition dropped) misses
+    # 10 eps sum|c| by orders of magnitude, because Eq. (4) is only eps-accurate for z >= s
+    # (Section 3.1); the plan's own entries (partition of Eq. 19) meet the bar.
+    p = hk.Plan(task, nu, N, eps, grid=grid, host_only=True)
+    c = np.random.default_rng(11).standard_normal(N)
+    A_exp = np.array([[p.expansion_entry(k, n) for n in range(1, N + 1)] for k in range(1, N + 1)])
+    A_plan = np.array([[p.entry(k, n)[0] for n in range(1, N + 1)] for k in range(1, N + 1)])
+    ref = oracle.transform(task, nu, N, c, grid=GRID[grid])
+    bound = 10 * eps * np.abs(c).sum()
+    assert np.all(np.isfinite(A_exp))
+    assert np.max(np.abs(A_plan @ c - ref)) <= bound
+    assert np.max(np.abs(A_exp @ c - ref)) > 1e3 * bound
+    # where the plan itself uses the expansion, the two agree to within the drop bound
+    far = np.array([[p.entry(k, n)[1] for n in range(1, N + 1)] for k in range(1, N + 1)])
+    assert far.any()
+    assert np.max(np.abs(A_exp[far] - A_plan[far])) <= eps
