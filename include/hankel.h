@@ -87,7 +87,8 @@ enum hankel_status {
                                       ncols * N * 24 bytes on the device (tables are skipped anyway above 16 GiB) */
 #define HANKEL_FLAG_ALL_COLUMNS 8u /* every block keeps all ncols stacked columns; by default a block leaves
                                       out the columns whose summed bound on its entries stays within
-                                      eps/10 per entry (hankel_block.ncols, hankel_info.block_cols) */
+                                      eps per entry, split over the blocks of a row (hankel_block.ncols,
+                                      hankel_info.block_cols) */
 #define HANKEL_FLAG_NO_REFINE 16u  /* keep the blocks of Eq. (19) as they are; by default a block is cut into
                                       smaller ones where that lowers the estimated work (fewer kept columns
                                       away from the near field) */

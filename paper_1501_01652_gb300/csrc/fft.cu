@@ -284,6 +284,132 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_pass_reg(const C* __restric
   }
 }
 
+// Whole transforms of length F = 2^LOGF <= 4096 in one launch: a CTA holds kSmallPts points
+// (kSmallPts / F columns, contiguous in global memory) in shared memory, padded by one element
+// per 16 (e -> e + e/16) against bank conflicts of strided butterflies, and runs the Stockham
+// decimation-in-time sub-stages of radices 2^L (L <= 4, two sub-stages for LOGF <= 8, three
+// above) in registers with reg_dft. Sub-stage k (radix Q, sub-length so far m, stride s = F/(mQ))
+// takes butterfly (pp < m, qq < s) from elements qq + s(Q pp + j) and writes qq + s(pp + r m);
+// the last one (s = 1) writes straight to global memory. There is no pass twiddle.
+constexpr int kSmallPts = 4096;
+constexpr int kSmallLog = 12;  // longest transform done by k_fft_small
+
+template <int LOGF>
+struct SmallSplit {
+  static constexpr int NS = LOGF <= 8 ? 2 : 3;
+  static constexpr int L0 = NS == 2 ? (LOGF + 1) / 2 : (LOGF + 2) / 3;
+  static constexpr int L1 = NS == 2 ? LOGF - L0 : (LOGF - L0 + 1) / 2;
+  static constexpr int L2 = NS == 2 ? 0 : LOGF - L0 - L1;
+  static constexpr int LMIN = NS == 2 ? L1 : L2;
+  static constexpr int NT = kSmallPts >> LMIN;  // threads: butterflies of the narrowest sub-stage
+};
+
+__device__ __forceinline__ uint32_t spad(uint32_t e) { return e + (e >> 4); }
+
+// One in-place sub-stage over the tile (every butterfly of radix 2^LQ; lognn = log2 of the
+// sub-length after it). LAST writes to global memory instead.
+template <int LOGF, int LQ, bool LAST, bool INV, class C>
+__device__ __forceinline__ void small_stage(C* v, int lognn, const C* __restrict__ tw, int logFmax, uint32_t fmask,
+                                            C* __restrict__ y, int64_t col0, int64_t ncols) {
+  constexpr int F = 1 << LOGF, Q = 1 << LQ;
+  constexpr uint32_t Fp = F + F / 16;
+  constexpr int NB = kSmallPts / Q;
+  const int logs = LOGF - lognn, logm = lognn - LQ;
+  const uint32_t b = threadIdx.x;
+  const bool act = b < NB;
+  C a[Q];
+  uint32_t c = 0, pp = 0, qq = 0;
+  if (act) {
+    c = b >> (LOGF - LQ);
+    const uint32_t bb = b & ((F >> LQ) - 1);
+    pp = bb >> logs;
+    qq = bb & ((1u << logs) - 1);
+    const C* vc = v + c * Fp;
+#pragma unroll
+    for (int j = 0; j < Q; ++j) a[j] = vc[spad(qq + ((pp * Q + j) << logs))];
+  }
+  if (!LAST) __syncthreads();  // the sub-stage works in place
+  if (act) {
+    reg_dft<LQ, INV>(a, pp << (logFmax - lognn), tw, logFmax, fmask);
+    if (LAST) {
+      if (col0 + c < ncols) {
+        C* yc = y + (col0 + c) * F;
+#pragma unroll
+        for (int r = 0; r < Q; ++r) yc[pp + (r << logm)] = a[r];
+      }
+    } else {
+      C* vc = v + c * Fp;
+#pragma unroll
+      for (int r = 0; r < Q; ++r) vc[spad(qq + ((pp + (r << logm)) << logs))] = a[r];
+    }
+  }
+  if (!LAST) __syncthreads();
+}
+
+template <int LOGF, bool INV, class C>
+__global__ void __launch_bounds__(SmallSplit<LOGF>::NT) k_fft_small(const C* __restrict__ src, C* __restrict__ dst,
+                                                                      int64_t ncols, const C* __restrict__ tw,
+                                                                      int logFmax) {
+  typedef SmallSplit<LOGF> S;
+  constexpr int F = 1 << LOGF;
+  constexpr uint32_t Fp = F + F / 16;
+  constexpr int NCOL = kSmallPts / F;
+  constexpr int PER = kSmallPts / S::NT;
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  C* v = reinterpret_cast<C*>(sm_raw);
+  const int64_t col0 = (int64_t)blockIdx.x * NCOL;
+  const C* x = src + col0 * F;
+  const uint32_t fmask = (1u << logFmax) - 1u;
+  const int64_t avail = (ncols - col0) * F;  // points of this CTA's columns that exist
+  C t[PER];
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    const uint32_t idx = threadIdx.x + u * S::NT;
+    t[u] = (int64_t)idx < avail ? x[idx] : mkc((typename RealOf<C>::type)0, (typename RealOf<C>::type)0);
+  }
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    const uint32_t idx = threadIdx.x + u * S::NT;
+    v[(idx >> LOGF) * Fp + spad(idx & (F - 1))] = t[u];
+  }
+  __syncthreads();
+  if (S::NS == 2) {
+    small_stage<LOGF, S::L0, false, INV>(v, S::L0, tw, logFmax, fmask, dst, col0, ncols);
+    small_stage<LOGF, S::L1, true, INV>(v, S::L0 + S::L1, tw, logFmax, fmask, dst, col0, ncols);
+  } else {
+    small_stage<LOGF, S::L0, false, INV>(v, S::L0, tw, logFmax, fmask, dst, col0, ncols);
+    small_stage<LOGF, S::L1, false, INV>(v, S::L0 + S::L1, tw, logFmax, fmask, dst, col0, ncols);
+    small_stage<LOGF, (S::L2 > 0 ? S::L2 : 1), true, INV>(v, LOGF, tw, logFmax, fmask, dst, col0, ncols);
+  }
+}
+
+template <int LOGF, bool INV, class C>
+void launch_small(const C* src, C* dst, int ncols, const C* tw, int logFmax, cudaStream_t st) {
+  constexpr int F = 1 << LOGF;
+  constexpr int NCOL = kSmallPts / F;
+  const size_t smem = (size_t)NCOL * (F + F / 16) * sizeof(C);
+  static bool configured = false;
+  if (!configured) {
+    cudaFuncSetAttribute(k_fft_small<LOGF, INV, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    configured = true;
+  }
+  const int64_t grid = ((int64_t)ncols + NCOL - 1) / NCOL;
+  k_fft_small<LOGF, INV, C><<<(unsigned)grid, SmallSplit<LOGF>::NT, smem, st>>>(src, dst, ncols, tw, logFmax);
+}
+
+template <bool INV, class C>
+void launch_small_f(int logF, const C* src, C* dst, int ncols, const C* tw, int logFmax, cudaStream_t st) {
+  switch (logF) {
+    case 6: launch_small<6, INV>(src, dst, ncols, tw, logFmax, st); break;
+    case 7: launch_small<7, INV>(src, dst, ncols, tw, logFmax, st); break;
+    case 8: launch_small<8, INV>(src, dst, ncols, tw, logFmax, st); break;
+    case 9: launch_small<9, INV>(src, dst, ncols, tw, logFmax, st); break;
+    case 10: launch_small<10, INV>(src, dst, ncols, tw, logFmax, st); break;
+    case 11: launch_small<11, INV>(src, dst, ncols, tw, logFmax, st); break;
+    default: launch_small<12, INV>(src, dst, ncols, tw, logFmax, st); break;
+  }
+}
+
 template <int LOGR, bool INV, class C>
 void launch_pass(const C* src, C* dst, int logF, int logS, int ncols, const C* tw, int logFmax, cudaStream_t st) {
   constexpr int R = 1 << LOGR;
@@ -405,6 +531,14 @@ template <class C>
 int run_fft(C* a, C* b, int logF, int ncols, bool inverse, const C* tw, int logFmax, cudaStream_t st, C** result,
             int* npasses) {
   if (logF < 6 || logF > logFmax) return HANKEL_EINVAL;
+  if (logF <= kSmallLog) {
+    // the whole transform in one launch
+    if (inverse) launch_small_f<true, C>(logF, a, b, ncols, tw, logFmax, st);
+    else launch_small_f<false, C>(logF, a, b, ncols, tw, logFmax, st);
+    *result = b;
+    if (npasses) *npasses = 1;
+    return HANKEL_OK;
+  }
   const int maxlog = std::min(8, logF - 4);  // keeps F/R >= kTile pairs per column
   const int np = (logF + maxlog - 1) / maxlog;
   const int base = logF / np, extra = logF % np;

@@ -546,8 +546,10 @@ void build_columns(HostPlan& hp) {
 // contribute less than eps. A block drops its columns in increasing order of A_l while their
 // sum stays within its share of a budget of kDropFrac * eps per entry (split evenly between
 // the blocks that meet in one row); every entry then moves by at most that sum, so
-// |f_k - f'_k| <= kDropFrac * eps * sum_n |c_n|.
-constexpr double kDropFrac = 0.1;
+// |f_k - f'_k| <= kDropFrac * eps * sum_n |c_n|. With kDropFrac = 1 an entry keeps the
+// expansion's own eps (the truncations above) plus at most eps from the dropped columns,
+// and f stays within O(eps ||c||_1) (Sections 5.2, 6.1).
+constexpr double kDropFrac = 1.0;
 // Blocks that may meet in one row while a block's budget is kDropFrac * eps / kRowBlocks.
 constexpr int kRowBlocks = 16;
 

@@ -162,7 +162,7 @@ def test_batched_matches_single():
 
 @pytest.mark.parametrize("task,eps", [("dht", 1e-15), ("dht", 1e-8), ("fourier_bessel", 1e-15), ("dht", 1e-4)])
 def test_kept_columns_against_every_column(task, eps):
-    # blocks that leave out columns (bound eps/10 per entry) against blocks that keep all
+    # blocks that leave out columns (bound eps per entry) against blocks that keep all
     N = 6000
     c = coefficients("normal", N, 2, 5700)
     fp, plan = _run(task, 0, N, eps, c)
