@@ -26,7 +26,6 @@ namespace {
 constexpr size_t kDefaultWorkspace = size_t(4) << 30;
 // Largest size of the column/row factor tables a plan builds (beyond it, factors are computed per use).
 constexpr size_t kTableLimit = size_t(16) << 30;
-constexpr int64_t kNearPiece = 4096;  // near-field columns handled by one warp
 
 // Complex elements one stacked column occupies in a workspace buffer.
 size_t column_footprint(const Block& b) { return (size_t)b.F * (size_t)b.nseg; }
@@ -62,6 +61,7 @@ struct DevicePlan {
   int64_t nitems = 0;
   NearRow* mrows = nullptr;
   int64_t nmrows = 0;
+  int64_t* nend = nullptr;  // near prefix end per row
   void* partial = nullptr;  // near-field partial sums (plan precision)
   int64_t nslots = 0;
   std::vector<DevBlock> blocks;
@@ -241,26 +241,31 @@ int dev_plan_create(hankel_plan_s* p) {
     HK_LAUNCHED();
   }
 
-  // Near-field work list: each row's prefix 1..nend(k) cut into pieces of <= kNearPiece columns.
+  // Near-field work list: groups of kNearRows rows, the group's longest prefix cut into tiles of
+  // kNearCols columns; groups with more than one tile add up per-row partial sums.
   std::vector<NearItem> items;
   std::vector<NearRow> mrows;
-  items.reserve(N + hp.near_count / kNearPiece + 16);
+  items.reserve(N / kNearRows + hp.near_count / (kNearRows * kNearCols) + 16);
   int64_t slot = 0;
-  for (int64_t k = 1; k <= N; ++k) {
-    int64_t ne = hp.nend[k - 1];
-    if (ne <= kNearPiece) {
-      items.push_back(NearItem{k, 1, ne, -1});
-    } else {
-      int64_t np = (ne + kNearPiece - 1) / kNearPiece;
-      mrows.push_back(NearRow{k, slot, (int32_t)np, 0});
-      for (int64_t j = 0; j < np; ++j)
-        items.push_back(NearItem{k, 1 + j * kNearPiece, std::min(ne, (j + 1) * kNearPiece), slot++});
+  for (int64_t k0 = 1; k0 <= N; k0 += kNearRows) {
+    const int64_t k1 = std::min<int64_t>(N, k0 + kNearRows - 1);
+    int64_t ne = 0;
+    for (int64_t k = k0; k <= k1; ++k) ne = std::max(ne, hp.nend[k - 1]);
+    const int64_t nt = std::max<int64_t>(1, (ne + kNearCols - 1) / kNearCols);
+    if (nt == 1) {
+      items.push_back(NearItem{k0, 1, ne, -1, 1, 0});
+      continue;
     }
+    for (int64_t t = 0; t < nt; ++t)
+      items.push_back(NearItem{k0, 1 + t * kNearCols, std::min(ne, (t + 1) * kNearCols), slot, (int32_t)nt, (int32_t)t});
+    for (int64_t k = k0; k <= k1; ++k) mrows.push_back(NearRow{k, slot + (k - k0) * nt, (int32_t)nt, 0});
+    slot += kNearRows * nt;
   }
   d->nitems = (int64_t)items.size();
   d->nmrows = (int64_t)mrows.size();
   d->nslots = slot;
   HK_TRY(upload(d, &d->items, items.data(), items.size()));
+  HK_TRY(upload(d, &d->nend, hp.nend.data(), hp.nend.size()));
   if (!mrows.empty()) HK_TRY(upload(d, &d->mrows, mrows.data(), mrows.size()));
   {
     void* q = nullptr;
@@ -468,11 +473,11 @@ int run_all(DevicePlan* d, const HostPlan& hp, const double* c, int64_t ldc, dou
   {
     StageScope sc(d, HANKEL_STAGE_NEAR, st, record);
     if (d->fp32)
-      launch_near<float>(d->items, d->nitems, d->mrows, d->nmrows, (float*)partial, nrhs, c, ldc, f, ldf, d->rf,
-                         d->omf, d->jtabf, hp.jt_n, hp.jt_deg, st);
+      launch_near<float>(d->items, d->nitems, d->mrows, d->nmrows, d->nend, d->hpN, (float*)partial, nrhs, c, ldc, f,
+                         ldf, d->rf, d->omf, d->jtabf, hp.jt_n, hp.jt_deg, st);
     else
-      launch_near<double>(d->items, d->nitems, d->mrows, d->nmrows, (double*)partial, nrhs, c, ldc, f, ldf,
-                          d->nodes.r_true, d->nodes.om_true, d->jtab, hp.jt_n, hp.jt_deg, st);
+      launch_near<double>(d->items, d->nitems, d->mrows, d->nmrows, d->nend, d->hpN, (double*)partial, nrhs, c, ldc,
+                          f, ldf, d->nodes.r_true, d->nodes.om_true, d->jtab, hp.jt_n, hp.jt_deg, st);
     HK_LAUNCHED();
     sc.done(d->nmrows > 0 ? 2 : 1, 0.0, (double)hp.near_count * nrhs);
   }

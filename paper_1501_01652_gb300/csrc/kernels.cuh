@@ -44,14 +44,20 @@ struct DevColSpec {
 
 // Near-field work item: row k, columns n0..n1 (1-based, inclusive; empty when n0 > n1).
 // slot < 0: the item is the whole prefix of its row and writes f directly.
+// A near-field tile: rows k0..k0+31 (one lane each) over columns n0..n1, each lane stopping at
+// its row's prefix end. slot < 0: the tile covers the group's whole prefix and writes f;
+// otherwise lane j writes partial slot (slot + j * ntile + t).
 struct NearItem {
-  int64_t k, n0, n1, slot;
+  int64_t k0, n0, n1, slot;
+  int32_t ntile, t;
 };
-// A row whose near prefix is split into npieces items with partial slots slot0.. .
+// A row whose near prefix is split into npieces tiles with partial slots slot0.. .
 struct NearRow {
   int64_t k, slot0;
   int32_t npieces, pad;
 };
+constexpr int kNearRows = 32;    // rows per tile (one warp)
+constexpr int64_t kNearCols = 512;  // columns per tile
 
 struct ChirpGeom {
   int64_t Ua, Ub, Va, Vb, E, k0, n0, R, C, F;
@@ -157,8 +163,8 @@ void launch_out(const OutArgs& a, cudaStream_t st);
 // Near field in FP64 (R = double: r, omega, jtab from the FP64 tables) or FP32 (R = float:
 // rf, omf, jtabf single-precision copies); sums are accumulated in R, outputs written as double.
 template <class R>
-void launch_near(const NearItem* items, int64_t nitems, const NearRow* mrows, int64_t nmrows, R* partial, int nrhs,
-                 const double* c, int64_t ldc, double* f, int64_t ldf, const R* r, const R* om, const R* jtab,
-                 int64_t jt_n, int deg, cudaStream_t st);
+void launch_near(const NearItem* items, int64_t nitems, const NearRow* mrows, int64_t nmrows, const int64_t* nend,
+                 int64_t N, R* partial, int nrhs, const double* c, int64_t ldc, double* f, int64_t ldf, const R* r,
+                 const R* om, const R* jtab, int64_t jt_n, int deg, cudaStream_t st);
 
 }  // namespace hk
