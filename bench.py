@@ -373,7 +373,7 @@ def run_ours(args):
                     "traffic_unit": "DRAM bytes per launch (ncu ratio x algorithmic bytes)",
                     "frac_of_measured_fp64": achieved / FP64_MEASURED_GFLOPS, "hbm_gbs_of_passes": pass_gbs,
                     "kernel": "k_fft_pass (FP64 Stockham passes, forward + inverse)",
-                    "flops_model": "5 F log2 F per column transform", "launches": fft_launches,
+                    "flops_model": "5 F log2 F per column transform, plus 6 F per spectrum product folded into an inverse transform", "launches": fft_launches,
                     "peak_source": "nominal FP64 from unit counts and clock (152 SM x 4 flop/clk x 2.07 GHz)"}
     if rank != 0:
         return

@@ -224,7 +224,8 @@ enum hankel_stage {
   HANKEL_STAGE_NEAR = 0,      /* near-field direct sum (and its partial-sum combine) */
   HANKEL_STAGE_GEN = 1,       /* far-field column generation */
   HANKEL_STAGE_FFT = 2,       /* forward and inverse multi-column FFT passes */
-  HANKEL_STAGE_POINTWISE = 3, /* product with the chirp spectrum */
+  HANKEL_STAGE_POINTWISE = 3, /* summed products of segment spectra and chirp spectra (column-segmented
+                                 blocks); the other products are folded into the inverse FFT loads */
   HANKEL_STAGE_OUT = 4,       /* row weights and accumulation into f */
   HANKEL_STAGE_COUNT = 5
 };

@@ -437,22 +437,32 @@ int run_block(DevicePlan* d, const DevBlock& db, const double* c, int64_t ldc, d
       sc.done(np, 5.0 * (double)b.F * (double)b.logF * (double)nfwd, 0.0, 2.0 * sizeof(C) * (double)b.F * nfwd * np);
     }
     C* other = (res == A) ? B : A;
-    C* spec = res;
-    {
-      StageScope sc(d, HANKEL_STAGE_POINTWISE, st, record);
-      if (rowseg) { launch_seg_mac<C>(res, H, other, b.F, b.nseg, nc, st); spec = other; }
-      else if (colseg) { launch_seg_expand<C>(res, H, other, b.F, b.nseg, nc, st); spec = other; }
-      else launch_pointwise<C>(res, H, b.F, nc, st);
-      HK_LAUNCHED();
-      sc.done(1, 0.0, 0.0);
-    }
     C* res2 = nullptr;
-    {
+    if (rowseg) {
+      // overlap-add: the segments' spectra times their chirp spectra, summed per column
+      {
+        StageScope sc(d, HANKEL_STAGE_POINTWISE, st, record);
+        launch_seg_mac<C>(res, H, other, b.F, b.nseg, nc, st);
+        HK_LAUNCHED();
+        sc.done(1, 0.0, 0.0);
+      }
       StageScope sc(d, HANKEL_STAGE_FFT, st, record);
       int np = 0;
-      HK_TRY(run_fft<C>(spec, spec == A ? B : A, b.logF, (int)ninv, true, tw, d->logFmax, st, &res2, &np));
+      HK_TRY(run_fft<C>(other, res, b.logF, (int)ninv, true, tw, d->logFmax, st, &res2, &np));
       HK_LAUNCHED();
       sc.done(np, 5.0 * (double)b.F * (double)b.logF * (double)ninv, 0.0, 2.0 * sizeof(C) * (double)b.F * ninv * np);
+    } else {
+      // full blocks: one product with the chirp spectrum; row segments (overlap-save): each
+      // column's spectrum times every segment's chirp spectrum -- both folded into the first
+      // loads of the inverse transform
+      StageScope sc(d, HANKEL_STAGE_FFT, st, record);
+      int np = 0;
+      HK_TRY(run_fft<C>(res, other, b.logF, (int)ninv, true, tw, d->logFmax, st, &res2, &np, H,
+                        colseg ? b.nseg : 1));
+      HK_LAUNCHED();
+      // 5 F log2 F per transform plus 6 F for the folded complex products
+      sc.done(np, (5.0 * (double)b.logF + 6.0) * (double)b.F * (double)ninv, 0.0,
+              2.0 * sizeof(C) * (double)b.F * ninv * np);
     }
     {
       StageScope sc(d, HANKEL_STAGE_OUT, st, record);
@@ -470,22 +480,23 @@ int run_block(DevicePlan* d, const DevBlock& db, const double* c, int64_t ldc, d
 int run_all(DevicePlan* d, const HostPlan& hp, const double* c, int64_t ldc, double* f, int64_t ldf, int nrhs,
             void* A, void* B, void* partial, size_t capacity_elems, bool chunk_from_capacity, cudaStream_t st,
             bool record) {
-  {
-    StageScope sc(d, HANKEL_STAGE_NEAR, st, record);
-    if (d->fp32)
-      launch_near<float>(d->items, d->nitems, d->mrows, d->nmrows, d->nend, d->hpN, (float*)partial, nrhs, c, ldc, f,
-                         ldf, d->rf, d->omf, d->jtabf, hp.jt_n, hp.jt_deg, st);
-    else
-      launch_near<double>(d->items, d->nitems, d->mrows, d->nmrows, d->nend, d->hpN, (double*)partial, nrhs, c, ldc,
-                          f, ldf, d->nodes.r_true, d->nodes.om_true, d->jtab, hp.jt_n, hp.jt_deg, st);
-    HK_LAUNCHED();
-    sc.done(d->nmrows > 0 ? 2 : 1, 0.0, (double)hp.near_count * nrhs);
-  }
-  if (d->cf && !d->blocks.empty()) {
+  if (d->cf) {
+    // FP32 plans with per-block tables: the coefficients rounded once, for every stage
     StageScope sc(d, HANKEL_STAGE_GEN, st, record);
     launch_coeffs_f32(c, ldc, d->cf, d->hpN, nrhs, st);
     HK_LAUNCHED();
     sc.done(1, 0.0, 0.0);
+  }
+  {
+    StageScope sc(d, HANKEL_STAGE_NEAR, st, record);
+    if (d->fp32)
+      launch_near<float>(d->items, d->nitems, d->mrows, d->nmrows, d->nend, d->hpN, (float*)partial, nrhs, c, ldc,
+                         d->cf, f, ldf, d->rf, d->omf, d->jtabf, hp.jt_n, hp.jt_deg, st);
+    else
+      launch_near<double>(d->items, d->nitems, d->mrows, d->nmrows, d->nend, d->hpN, (double*)partial, nrhs, c, ldc,
+                          nullptr, f, ldf, d->nodes.r_true, d->nodes.om_true, d->jtab, hp.jt_n, hp.jt_deg, st);
+    HK_LAUNCHED();
+    sc.done(d->nmrows > 0 ? 2 : 1, 0.0, (double)hp.near_count * nrhs);
   }
   for (const DevBlock& db : d->blocks) {
     const int64_t cap = chunk_from_capacity

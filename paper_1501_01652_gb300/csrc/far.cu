@@ -149,13 +149,14 @@ __global__ void __launch_bounds__(256) k_out(OutArgs a) {
   }
 }
 
-// FP32 plans with per-block tables: the sum over stacked columns in FP32, the row chirp and
+// FP32 plans with per-block tables: the sum over stacked columns and the row chirp in FP32,
 // the addition into f in FP64.
 __global__ void __launch_bounds__(256) k_out_f32(OutArgs a) {
   const int64_t kp = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (kp >= a.R) return;
   const int64_t i = a.k0 - 1 + kp;
-  const double2 wu = a.wU[kp];
+  const double2 wud = a.wU[kp];
+  const float2 wu = make_float2((float)wud.x, (float)wud.y);
   const int64_t sg = kp / a.Sr;
   const float2* Y = reinterpret_cast<const float2*>(a.Y) + sg * a.F + (kp - sg * a.Sr) + a.off;
   const int64_t r_first = a.c0 / a.ncols, r_last = (a.c0 + a.nc - 1) / a.ncols;
@@ -169,7 +170,7 @@ __global__ void __launch_bounds__(256) k_out_f32(OutArgs a) {
       ar = fmaf(wgt, y.x, ar);
       ai = fmaf(wgt, y.y, ai);
     }
-    a.f[rhs * a.ldf + i] += fma(wu.x, (double)ar, -wu.y * (double)ai);
+    a.f[rhs * a.ldf + i] += (double)fmaf(wu.x, ar, -wu.y * ai);
   }
 }
 
@@ -204,16 +205,6 @@ __global__ void __launch_bounds__(kMacPts* kMacLanes) k_seg_mac(const C* __restr
       ai += si[j][pt];
     }
     out[cc * F + t] = mkc(ar, ai);
-  }
-}
-
-template <class C>
-__global__ void k_seg_expand(const C* __restrict__ in, const C* __restrict__ H, C* __restrict__ out, int64_t F,
-                             int64_t nseg, int64_t total) {
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t t = e % F, q = e / F;
-    const int64_t cc = q / nseg, s = q - cc * nseg;
-    out[e] = cmul(in[cc * F + t], __ldg(&H[s * F + t]));
   }
 }
 
@@ -294,12 +285,6 @@ void launch_seg_mac(const C* in, const C* H, C* out, int64_t F, int64_t nseg, in
   k_seg_mac<C><<<(unsigned)blocks, kMacPts * kMacLanes, 0, st>>>(in, H, out, F, nseg);
 }
 
-template <class C>
-void launch_seg_expand(const C* in, const C* H, C* out, int64_t F, int64_t nseg, int nc, cudaStream_t st) {
-  const int64_t total = F * nseg * nc;
-  k_seg_expand<C><<<grid1d(total), 256, 0, st>>>(in, H, out, F, nseg, total);
-}
-
 void launch_build_tables(const TabArgs& a, cudaStream_t st) {
   k_build_tables<<<grid1d((int64_t)a.ncols * a.N), 256, 0, st>>>(a);
 }
@@ -330,8 +315,5 @@ template void launch_out<double2>(const OutArgs&, cudaStream_t);
 template void launch_out<float2>(const OutArgs&, cudaStream_t);
 template void launch_seg_mac<double2>(const double2*, const double2*, double2*, int64_t, int64_t, int, cudaStream_t);
 template void launch_seg_mac<float2>(const float2*, const float2*, float2*, int64_t, int64_t, int, cudaStream_t);
-template void launch_seg_expand<double2>(const double2*, const double2*, double2*, int64_t, int64_t, int,
-                                         cudaStream_t);
-template void launch_seg_expand<float2>(const float2*, const float2*, float2*, int64_t, int64_t, int, cudaStream_t);
 
 }  // namespace hk

@@ -217,7 +217,8 @@ __device__ __forceinline__ void reg_dft(C (&a)[1 << LQ], uint32_t base, const C*
 template <int LOGR, bool INV, class C>
 __global__ void __launch_bounds__(kFftThreads) k_fft_pass_reg(const C* __restrict__ src, C* __restrict__ dst,
                                                               int logF, int logS, const C* __restrict__ tw,
-                                                              int logFmax) {
+                                                              int logFmax, const C* __restrict__ hmul,
+                                                              int64_t nseg) {
   constexpr int R = 1 << LOGR;
   constexpr int L1 = (LOGR + 1) / 2, L2 = LOGR - L1;
   constexpr int Q1 = 1 << L1, Q2 = 1 << L2;
@@ -231,7 +232,11 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_pass_reg(const C* __restric
   const uint64_t G0 = (uint64_t)blockIdx.x * kTile;
   const uint64_t col = G0 >> logFR;
   const uint32_t pi0 = (uint32_t)(G0 & ((1ull << logFR) - 1));
-  const C* x = src + (col << logF);
+  // with hmul (first pass only, s >= kTile): column col reads source column col / nseg times
+  // spectrum col % nseg
+  const uint64_t scol = hmul ? col / (uint64_t)nseg : col;
+  const C* x = src + (scol << logF);
+  const C* hc = hmul ? hmul + ((col - scol * (uint64_t)nseg) << logF) : nullptr;
   C* y = dst + (col << logF);
   const uint32_t s = 1u << logS;
   const int fsh = logFmax - logF;
@@ -243,9 +248,14 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_pass_reg(const C* __restric
   if (s >= kTile) {
     if (act1) {
       const uint32_t p = pi0 >> logS, q0 = pi0 & (s - 1);
-      const C* xb = x + q0 + ((p << LOGR) << logS) + i;
+      const uint32_t off = q0 + ((p << LOGR) << logS) + i;
+      const C* xb = x + off;
 #pragma unroll
       for (int j = 0; j < Q1; ++j) a[j] = xb[(bf + Q2 * j) << logS];
+      if (hc) {
+#pragma unroll
+        for (int j = 0; j < Q1; ++j) a[j] = cmul(a[j], __ldg(&hc[off + ((bf + Q2 * j) << logS)]));
+      }
     }
   } else {
     const C* xb = x + (pi0 << LOGR);
@@ -349,7 +359,8 @@ __device__ __forceinline__ void small_stage(C* v, int lognn, const C* __restrict
 template <int LOGF, bool INV, class C>
 __global__ void __launch_bounds__(SmallSplit<LOGF>::NT) k_fft_small(const C* __restrict__ src, C* __restrict__ dst,
                                                                       int64_t ncols, const C* __restrict__ tw,
-                                                                      int logFmax) {
+                                                                      int logFmax, const C* __restrict__ hmul,
+                                                                      int64_t nseg) {
   typedef SmallSplit<LOGF> S;
   constexpr int F = 1 << LOGF;
   constexpr uint32_t Fp = F + F / 16;
@@ -362,10 +373,29 @@ __global__ void __launch_bounds__(SmallSplit<LOGF>::NT) k_fft_small(const C* __r
   const uint32_t fmask = (1u << logFmax) - 1u;
   const int64_t avail = (ncols - col0) * F;  // points of this CTA's columns that exist
   C t[PER];
+  if (hmul) {
+    // column col0 + c is source column (col0 + c) / nseg times spectrum (col0 + c) % nseg
+    __shared__ int64_t scol[NCOL];
+    __shared__ int64_t sseg[NCOL];
+    if (threadIdx.x < NCOL) {
+      const int64_t vc = col0 + threadIdx.x;
+      scol[threadIdx.x] = vc / nseg;
+      sseg[threadIdx.x] = vc - scol[threadIdx.x] * nseg;
+    }
+    __syncthreads();
 #pragma unroll
-  for (int u = 0; u < PER; ++u) {
-    const uint32_t idx = threadIdx.x + u * S::NT;
-    t[u] = (int64_t)idx < avail ? x[idx] : mkc((typename RealOf<C>::type)0, (typename RealOf<C>::type)0);
+    for (int u = 0; u < PER; ++u) {
+      const uint32_t idx = threadIdx.x + u * S::NT;
+      const uint32_t c = idx >> LOGF, e = idx & (F - 1);
+      t[u] = (int64_t)idx < avail ? cmul(src[scol[c] * F + e], __ldg(&hmul[sseg[c] * F + e]))
+                                  : mkc((typename RealOf<C>::type)0, (typename RealOf<C>::type)0);
+    }
+  } else {
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const uint32_t idx = threadIdx.x + u * S::NT;
+      t[u] = (int64_t)idx < avail ? x[idx] : mkc((typename RealOf<C>::type)0, (typename RealOf<C>::type)0);
+    }
   }
 #pragma unroll
   for (int u = 0; u < PER; ++u) {
@@ -384,7 +414,8 @@ __global__ void __launch_bounds__(SmallSplit<LOGF>::NT) k_fft_small(const C* __r
 }
 
 template <int LOGF, bool INV, class C>
-void launch_small(const C* src, C* dst, int ncols, const C* tw, int logFmax, cudaStream_t st) {
+void launch_small(const C* src, C* dst, int ncols, const C* tw, int logFmax, const C* hmul, int64_t nseg,
+                  cudaStream_t st) {
   constexpr int F = 1 << LOGF;
   constexpr int NCOL = kSmallPts / F;
   const size_t smem = (size_t)NCOL * (F + F / 16) * sizeof(C);
@@ -394,24 +425,27 @@ void launch_small(const C* src, C* dst, int ncols, const C* tw, int logFmax, cud
     configured = true;
   }
   const int64_t grid = ((int64_t)ncols + NCOL - 1) / NCOL;
-  k_fft_small<LOGF, INV, C><<<(unsigned)grid, SmallSplit<LOGF>::NT, smem, st>>>(src, dst, ncols, tw, logFmax);
+  k_fft_small<LOGF, INV, C><<<(unsigned)grid, SmallSplit<LOGF>::NT, smem, st>>>(src, dst, ncols, tw, logFmax, hmul,
+                                                                                nseg);
 }
 
 template <bool INV, class C>
-void launch_small_f(int logF, const C* src, C* dst, int ncols, const C* tw, int logFmax, cudaStream_t st) {
+void launch_small_f(int logF, const C* src, C* dst, int ncols, const C* tw, int logFmax, const C* hmul, int64_t nseg,
+                    cudaStream_t st) {
   switch (logF) {
-    case 6: launch_small<6, INV>(src, dst, ncols, tw, logFmax, st); break;
-    case 7: launch_small<7, INV>(src, dst, ncols, tw, logFmax, st); break;
-    case 8: launch_small<8, INV>(src, dst, ncols, tw, logFmax, st); break;
-    case 9: launch_small<9, INV>(src, dst, ncols, tw, logFmax, st); break;
-    case 10: launch_small<10, INV>(src, dst, ncols, tw, logFmax, st); break;
-    case 11: launch_small<11, INV>(src, dst, ncols, tw, logFmax, st); break;
-    default: launch_small<12, INV>(src, dst, ncols, tw, logFmax, st); break;
+    case 6: launch_small<6, INV>(src, dst, ncols, tw, logFmax, hmul, nseg, st); break;
+    case 7: launch_small<7, INV>(src, dst, ncols, tw, logFmax, hmul, nseg, st); break;
+    case 8: launch_small<8, INV>(src, dst, ncols, tw, logFmax, hmul, nseg, st); break;
+    case 9: launch_small<9, INV>(src, dst, ncols, tw, logFmax, hmul, nseg, st); break;
+    case 10: launch_small<10, INV>(src, dst, ncols, tw, logFmax, hmul, nseg, st); break;
+    case 11: launch_small<11, INV>(src, dst, ncols, tw, logFmax, hmul, nseg, st); break;
+    default: launch_small<12, INV>(src, dst, ncols, tw, logFmax, hmul, nseg, st); break;
   }
 }
 
 template <int LOGR, bool INV, class C>
-void launch_pass(const C* src, C* dst, int logF, int logS, int ncols, const C* tw, int logFmax, cudaStream_t st) {
+void launch_pass(const C* src, C* dst, int logF, int logS, int ncols, const C* tw, int logFmax, const C* hmul,
+                 int64_t nseg, cudaStream_t st) {
   constexpr int R = 1 << LOGR;
   const int64_t pairs = ((int64_t)ncols << logF) >> LOGR;
   const int64_t grid = pairs / kTile;
@@ -425,7 +459,8 @@ void launch_pass(const C* src, C* dst, int logF, int logS, int ncols, const C* t
       cudaFuncSetAttribute(k_fft_pass_reg<LOGR, INV, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       configured = true;
     }
-    k_fft_pass_reg<LOGR, INV, C><<<(unsigned)grid, threads, smem, st>>>(src, dst, logF, logS, tw, logFmax);
+    k_fft_pass_reg<LOGR, INV, C><<<(unsigned)grid, threads, smem, st>>>(src, dst, logF, logS, tw, logFmax, hmul,
+                                                                          nseg);
   } else {
     const size_t smem = 2 * (size_t)R * kRow * sizeof(C);
     static bool configured = false;
@@ -439,16 +474,16 @@ void launch_pass(const C* src, C* dst, int logF, int logS, int ncols, const C* t
 
 template <bool INV, class C>
 void launch_pass_r(int logR, const C* src, C* dst, int logF, int logS, int ncols, const C* tw, int logFmax,
-                   cudaStream_t st) {
+                   const C* hmul, int64_t nseg, cudaStream_t st) {
   switch (logR) {
-    case 1: launch_pass<1, INV>(src, dst, logF, logS, ncols, tw, logFmax, st); break;
-    case 2: launch_pass<2, INV>(src, dst, logF, logS, ncols, tw, logFmax, st); break;
-    case 3: launch_pass<3, INV>(src, dst, logF, logS, ncols, tw, logFmax, st); break;
-    case 4: launch_pass<4, INV>(src, dst, logF, logS, ncols, tw, logFmax, st); break;
-    case 5: launch_pass<5, INV>(src, dst, logF, logS, ncols, tw, logFmax, st); break;
-    case 6: launch_pass<6, INV>(src, dst, logF, logS, ncols, tw, logFmax, st); break;
-    case 7: launch_pass<7, INV>(src, dst, logF, logS, ncols, tw, logFmax, st); break;
-    default: launch_pass<8, INV>(src, dst, logF, logS, ncols, tw, logFmax, st); break;
+    case 1: launch_pass<1, INV>(src, dst, logF, logS, ncols, tw, logFmax, hmul, nseg, st); break;
+    case 2: launch_pass<2, INV>(src, dst, logF, logS, ncols, tw, logFmax, hmul, nseg, st); break;
+    case 3: launch_pass<3, INV>(src, dst, logF, logS, ncols, tw, logFmax, hmul, nseg, st); break;
+    case 4: launch_pass<4, INV>(src, dst, logF, logS, ncols, tw, logFmax, hmul, nseg, st); break;
+    case 5: launch_pass<5, INV>(src, dst, logF, logS, ncols, tw, logFmax, hmul, nseg, st); break;
+    case 6: launch_pass<6, INV>(src, dst, logF, logS, ncols, tw, logFmax, hmul, nseg, st); break;
+    case 7: launch_pass<7, INV>(src, dst, logF, logS, ncols, tw, logFmax, hmul, nseg, st); break;
+    default: launch_pass<8, INV>(src, dst, logF, logS, ncols, tw, logFmax, hmul, nseg, st); break;
   }
 }
 
@@ -491,11 +526,6 @@ __global__ void k_scale_copy(const double2* src, C* dst, int64_t n, double scale
     dst[t] = from_d2<C>(make_double2(src[t].x * scale, src[t].y * scale));
 }
 
-template <class C>
-__global__ void k_pointwise(C* y, const C* __restrict__ H, int64_t F, int64_t total) {
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x)
-    y[t] = cmul(y[t], __ldg(&H[t & (F - 1)]));
-}
 
 unsigned grid_for(int64_t n, int threads) {
   int64_t g = (n + threads - 1) / threads;
@@ -521,20 +551,15 @@ void launch_scale_copy(const double2* src, C* dst, int64_t n, double scale, cuda
   k_scale_copy<C><<<grid_for(n, 256), 256, 0, st>>>(src, dst, n, scale);
 }
 
-template <class C>
-void launch_pointwise(C* y, const C* H, int64_t F, int ncols, cudaStream_t st) {
-  const int64_t total = F * ncols;
-  k_pointwise<C><<<grid_for(total, 256), 256, 0, st>>>(y, H, F, total);
-}
 
 template <class C>
 int run_fft(C* a, C* b, int logF, int ncols, bool inverse, const C* tw, int logFmax, cudaStream_t st, C** result,
-            int* npasses) {
-  if (logF < 6 || logF > logFmax) return HANKEL_EINVAL;
+            int* npasses, const C* hmul, int64_t nseg) {
+  if (logF < 6 || logF > logFmax || nseg < 1) return HANKEL_EINVAL;
   if (logF <= kSmallLog) {
     // the whole transform in one launch
-    if (inverse) launch_small_f<true, C>(logF, a, b, ncols, tw, logFmax, st);
-    else launch_small_f<false, C>(logF, a, b, ncols, tw, logFmax, st);
+    if (inverse) launch_small_f<true, C>(logF, a, b, ncols, tw, logFmax, hmul, nseg, st);
+    else launch_small_f<false, C>(logF, a, b, ncols, tw, logFmax, hmul, nseg, st);
     *result = b;
     if (npasses) *npasses = 1;
     return HANKEL_OK;
@@ -542,6 +567,8 @@ int run_fft(C* a, C* b, int logF, int ncols, bool inverse, const C* tw, int logF
   const int maxlog = std::min(8, logF - 4);  // keeps F/R >= kTile pairs per column
   const int np = (logF + maxlog - 1) / maxlog;
   const int base = logF / np, extra = logF % np;
+  // the first pass (radix >= 2^5 here, stride F/R >= kTile) applies the input product
+  if (hmul && (base + (extra > 0 ? 1 : 0) < 5 || logF - (base + (extra > 0 ? 1 : 0)) < 4)) return HANKEL_EINVAL;
   C* src = a;
   C* dst = b;
   int done = 0;  // log2 of the sub-length transformed so far
@@ -549,8 +576,9 @@ int run_fft(C* a, C* b, int logF, int ncols, bool inverse, const C* tw, int logF
     const int lr = base + (i < extra ? 1 : 0);
     done += lr;
     const int logS = logF - done;
-    if (inverse) launch_pass_r<true, C>(lr, src, dst, logF, logS, ncols, tw, logFmax, st);
-    else launch_pass_r<false, C>(lr, src, dst, logF, logS, ncols, tw, logFmax, st);
+    const C* h = i == 0 ? hmul : nullptr;
+    if (inverse) launch_pass_r<true, C>(lr, src, dst, logF, logS, ncols, tw, logFmax, h, nseg, st);
+    else launch_pass_r<false, C>(lr, src, dst, logF, logS, ncols, tw, logFmax, h, nseg, st);
     std::swap(src, dst);
   }
   *result = src;
@@ -559,11 +587,10 @@ int run_fft(C* a, C* b, int logF, int ncols, bool inverse, const C* tw, int logF
 }
 
 template int run_fft<double2>(double2*, double2*, int, int, bool, const double2*, int, cudaStream_t, double2**,
-                              int*);
-template int run_fft<float2>(float2*, float2*, int, int, bool, const float2*, int, cudaStream_t, float2**, int*);
+                              int*, const double2*, int64_t);
+template int run_fft<float2>(float2*, float2*, int, int, bool, const float2*, int, cudaStream_t, float2**, int*,
+                             const float2*, int64_t);
 template void launch_scale_copy<double2>(const double2*, double2*, int64_t, double, cudaStream_t);
 template void launch_scale_copy<float2>(const double2*, float2*, int64_t, double, cudaStream_t);
-template void launch_pointwise<double2>(double2*, const double2*, int64_t, int, cudaStream_t);
-template void launch_pointwise<float2>(float2*, const float2*, int64_t, int, cudaStream_t);
 
 }  // namespace hk

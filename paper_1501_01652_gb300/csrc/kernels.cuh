@@ -143,19 +143,16 @@ void launch_seg_hh(const SegGeom& g, double2* hh, cudaStream_t st);
 // out[cc][t] = sum_s in[cc*nseg + s][t] * H[s][t]   (overlap-add of column segments)
 template <class C>
 void launch_seg_mac(const C* in, const C* H, C* out, int64_t F, int64_t nseg, int nc, cudaStream_t st);
-// out[cc*nseg + s][t] = in[cc][t] * H[s][t]         (overlap-save of row segments)
-template <class C>
-void launch_seg_expand(const C* in, const C* H, C* out, int64_t F, int64_t nseg, int nc, cudaStream_t st);
 // Out-of-place multi-column FFT of length 2^logF over ncols contiguous columns,
 // ping-ponging between a (input) and b; *result receives the buffer holding the output.
 // C is double2 (FP64) or float2 (FP32); tw is the matching twiddle table of 2^logFmax entries.
+// With hmul, column j transforms a[j / nseg] times hmul[j % nseg] elementwise (a holds
+// ncols / nseg columns; the products of the chirp spectra are folded into the first loads).
 template <class C>
 int run_fft(C* a, C* b, int logF, int ncols, bool inverse, const C* tw, int logFmax, cudaStream_t st, C** result,
-            int* npasses = nullptr);
+            int* npasses = nullptr, const C* hmul = nullptr, int64_t nseg = 1);
 template <class C>
 void launch_scale_copy(const double2* src, C* dst, int64_t n, double scale, cudaStream_t st);
-template <class C>
-void launch_pointwise(C* y, const C* H, int64_t F, int ncols, cudaStream_t st);
 template <class C>
 void launch_gen(const GenArgs& a, cudaStream_t st);
 template <class C>
@@ -163,8 +160,9 @@ void launch_out(const OutArgs& a, cudaStream_t st);
 // Near field in FP64 (R = double: r, omega, jtab from the FP64 tables) or FP32 (R = float:
 // rf, omf, jtabf single-precision copies); sums are accumulated in R, outputs written as double.
 template <class R>
+// cf: optional coefficients already rounded to FP32 ([nrhs][N]); used instead of c when given.
 void launch_near(const NearItem* items, int64_t nitems, const NearRow* mrows, int64_t nmrows, const int64_t* nend,
-                 int64_t N, R* partial, int nrhs, const double* c, int64_t ldc, double* f, int64_t ldf, const R* r,
-                 const R* om, const R* jtab, int64_t jt_n, int deg, cudaStream_t st);
+                 int64_t N, R* partial, int nrhs, const double* c, int64_t ldc, const float* cf, double* f,
+                 int64_t ldf, const R* r, const R* om, const R* jtab, int64_t jt_n, int deg, cudaStream_t st);
 
 }  // namespace hk

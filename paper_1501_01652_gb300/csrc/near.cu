@@ -34,10 +34,10 @@ __device__ __forceinline__ R table_j(const R* __restrict__ jtab, int64_t jt_n, i
 // Warp per tile, lane per row: every lane walks the same columns n (so the loads of omega_n and
 // of c_n for each vector are warp-wide broadcasts) and stops at its own prefix end; the sum
 // over n is the lane's own, in increasing n, with no cross-lane reduction.
-template <class R, int G>
+template <class R, int G, class CT>
 __global__ void __launch_bounds__(256) k_near(const NearItem* __restrict__ items, int64_t nitems,
                                               const int64_t* __restrict__ nend, int64_t N, R* partial, int nrhs,
-                                              const double* __restrict__ c, int64_t ldc, double* f, int64_t ldf,
+                                              const CT* __restrict__ c, int64_t ldc, double* f, int64_t ldf,
                                               const R* __restrict__ r_true, const R* __restrict__ om_true,
                                               const R* __restrict__ jtab, int64_t jt_n, int deg) {
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -82,10 +82,10 @@ __global__ void k_near_combine(const NearRow* __restrict__ rows, int64_t nrows, 
 
 }  // namespace
 
-template <class R>
-void launch_near(const NearItem* items, int64_t nitems, const NearRow* mrows, int64_t nmrows, const int64_t* nend,
-                 int64_t N, R* partial, int nrhs, const double* c, int64_t ldc, double* f, int64_t ldf, const R* r,
-                 const R* om, const R* jtab, int64_t jt_n, int deg, cudaStream_t st) {
+template <class R, class CT>
+void launch_near_t(const NearItem* items, int64_t nitems, const int64_t* nend, int64_t N, R* partial, int nrhs,
+                   const CT* c, int64_t ldc, double* f, int64_t ldf, const R* r, const R* om, const R* jtab,
+                   int64_t jt_n, int deg, cudaStream_t st) {
   const int64_t threads = nitems * 32;
   const unsigned grid = (unsigned)((threads + 255) / 256);
   if (nrhs <= 1)
@@ -99,6 +99,14 @@ void launch_near(const NearItem* items, int64_t nitems, const NearRow* mrows, in
   else
     k_near<R, kMaxRhsGroup><<<grid, 256, 0, st>>>(items, nitems, nend, N, partial, nrhs, c, ldc, f, ldf, r, om, jtab,
                                                   jt_n, deg);
+}
+
+template <class R>
+void launch_near(const NearItem* items, int64_t nitems, const NearRow* mrows, int64_t nmrows, const int64_t* nend,
+                 int64_t N, R* partial, int nrhs, const double* c, int64_t ldc, const float* cf, double* f,
+                 int64_t ldf, const R* r, const R* om, const R* jtab, int64_t jt_n, int deg, cudaStream_t st) {
+  if (cf) launch_near_t<R, float>(items, nitems, nend, N, partial, nrhs, cf, N, f, ldf, r, om, jtab, jt_n, deg, st);
+  else launch_near_t<R, double>(items, nitems, nend, N, partial, nrhs, c, ldc, f, ldf, r, om, jtab, jt_n, deg, st);
   if (nmrows > 0) {
     const int64_t n = nmrows * nrhs;
     k_near_combine<R><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(mrows, nmrows, partial, nrhs, f, ldf);
@@ -106,10 +114,10 @@ void launch_near(const NearItem* items, int64_t nitems, const NearRow* mrows, in
 }
 
 template void launch_near<double>(const NearItem*, int64_t, const NearRow*, int64_t, const int64_t*, int64_t,
-                                  double*, int, const double*, int64_t, double*, int64_t, const double*,
-                                  const double*, const double*, int64_t, int, cudaStream_t);
+                                  double*, int, const double*, int64_t, const float*, double*, int64_t,
+                                  const double*, const double*, const double*, int64_t, int, cudaStream_t);
 template void launch_near<float>(const NearItem*, int64_t, const NearRow*, int64_t, const int64_t*, int64_t, float*,
-                                 int, const double*, int64_t, double*, int64_t, const float*, const float*,
-                                 const float*, int64_t, int, cudaStream_t);
+                                 int, const double*, int64_t, const float*, double*, int64_t, const float*,
+                                 const float*, const float*, int64_t, int, cudaStream_t);
 
 }  // namespace hk
