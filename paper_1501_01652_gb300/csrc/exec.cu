@@ -65,8 +65,8 @@ struct DevicePlan {
   void* partial = nullptr;  // near-field partial sums (plan precision)
   int64_t nslots = 0;
   std::vector<DevBlock> blocks;
-  double2* tw = nullptr;   // W_{Fmax}^t in FP64 (plan-time spectra of every plan)
-  float2* twf = nullptr;   // the same table rounded to FP32 (FP32 plans)
+  double2* tw = nullptr;   // twiddle ladder in FP64: W_F^t at tw[F + t], F = 2^6 .. 2^logFmax
+  float2* twf = nullptr;   // the same ladder rounded to FP32 (FP32 plans)
   int logFmax = 6;
   void* bufA = nullptr;    // workspace, elements of the plan precision
   void* bufB = nullptr;
@@ -279,12 +279,14 @@ int dev_plan_create(hankel_plan_s* p) {
   int logFmax = 6;
   for (const Block& b : hp.blocks) logFmax = std::max(logFmax, b.logF);
   d->logFmax = logFmax;
-  HK_TRY(dalloc(d, &d->tw, (size_t)1 << logFmax));
-  launch_twiddles(d->tw, logFmax, 0);
+  // one compact table per transform length, so that a transform's twiddles stay together
+  // in cache instead of being spread over the table of the longest transform
+  HK_TRY(dalloc(d, &d->tw, (size_t)2 << logFmax));
+  for (int L = 6; L <= logFmax; ++L) launch_twiddles(d->tw + ((size_t)1 << L), L, 0);
   HK_LAUNCHED();
   if (d->fp32) {
-    HK_TRY(dalloc(d, &d->twf, (size_t)1 << logFmax));
-    launch_scale_copy<float2>(d->tw, d->twf, int64_t(1) << logFmax, 1.0, 0);
+    HK_TRY(dalloc(d, &d->twf, (size_t)2 << logFmax));
+    launch_scale_copy<float2>(d->tw + 64, d->twf + 64, (int64_t(2) << logFmax) - 64, 1.0, 0);
     HK_LAUNCHED();
   }
 

@@ -556,6 +556,9 @@ template <class C>
 int run_fft(C* a, C* b, int logF, int ncols, bool inverse, const C* tw, int logFmax, cudaStream_t st, C** result,
             int* npasses, const C* hmul, int64_t nseg) {
   if (logF < 6 || logF > logFmax || nseg < 1) return HANKEL_EINVAL;
+  // the ladder's table for this length: W_F^t at tw[F + t]
+  tw += (size_t)1 << logF;
+  logFmax = logF;
   if (logF <= kSmallLog) {
     // the whole transform in one launch
     if (inverse) launch_small_f<true, C>(logF, a, b, ncols, tw, logFmax, hmul, nseg, st);

@@ -145,7 +145,8 @@ template <class C>
 void launch_seg_mac(const C* in, const C* H, C* out, int64_t F, int64_t nseg, int nc, cudaStream_t st);
 // Out-of-place multi-column FFT of length 2^logF over ncols contiguous columns,
 // ping-ponging between a (input) and b; *result receives the buffer holding the output.
-// C is double2 (FP64) or float2 (FP32); tw is the matching twiddle table of 2^logFmax entries.
+// C is double2 (FP64) or float2 (FP32); tw is the matching twiddle ladder (W_F^t at tw[F + t]
+// for every power of two F = 2^6 .. 2^logFmax).
 // With hmul, column j transforms a[j / nseg] times hmul[j % nseg] elementwise (a holds
 // ncols / nseg columns; the products of the chirp spectra are folded into the first loads).
 template <class C>
