@@ -204,6 +204,55 @@ __device__ __forceinline__ void reg_dft(C (&a)[1 << LQ], uint32_t base, const C*
   for (int j = 0; j < Q; ++j) a[j] = b[j];
 }
 
+// reg_dft for base = 0 (the first sub-stage of the first pass of a transform): the twiddles
+// are the constants W_{2^s}^k. Those equal to 1 and -i (i for the inverse) become plain
+// additions; the others are folded into FMAs as in bfly2.
+// cos and sin of 2 pi t / 16, t = 0..7
+__host__ __device__ constexpr double cos16(int t) {
+  return t == 0 ? 1.0 : t == 1 ? 0.92387953251128675613 : t == 2 ? 0.7071067811865475244
+       : t == 3 ? 0.38268343236508977173 : t == 4 ? 0.0 : t == 5 ? -0.38268343236508977173
+       : t == 6 ? -0.7071067811865475244 : -0.92387953251128675613;
+}
+__host__ __device__ constexpr double sin16(int t) { return cos16(t < 4 ? 4 - t : t - 4); }
+
+template <int LQ, bool INV, class C>
+__device__ __forceinline__ void reg_dft_unit(C (&a)[1 << LQ]) {
+  typedef typename RealOf<C>::type R;
+  constexpr int Q = 1 << LQ;
+  C b[Q];
+#pragma unroll
+  for (int j = 0; j < Q; ++j) b[bitrev(j, LQ)] = a[j];
+#pragma unroll
+  for (int s = 1; s <= LQ; ++s) {
+    const int half = 1 << (s - 1);
+#pragma unroll
+    for (int k = 0; k < half; ++k) {
+      const int t16 = k << (4 - s);  // W_{2^s}^k = exp(-2 pi i t16 / 16)
+#pragma unroll
+      for (int g = 0; g < Q; g += 2 * half) {
+        C& x0 = b[g + k];
+        C& x1 = b[g + k + half];
+        if (t16 == 0) {
+          const C y0 = mkc(x0.x + x1.x, x0.y + x1.y);
+          x1 = mkc(x0.x - x1.x, x0.y - x1.y);
+          x0 = y0;
+        } else if (t16 == 4) {
+          // w x1 = -i x1 (forward) or i x1 (inverse)
+          const C wx = INV ? mkc(-x1.y, x1.x) : mkc(x1.y, -x1.x);
+          const C y0 = mkc(x0.x + wx.x, x0.y + wx.y);
+          x1 = mkc(x0.x - wx.x, x0.y - wx.y);
+          x0 = y0;
+        } else {
+          const C w = mkc((R)cos16(t16), INV ? (R)sin16(t16) : -(R)sin16(t16));
+          bfly2(x0, x1, w);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < Q; ++j) a[j] = b[j];
+}
+
 // The same pass as k_fft_pass for 5 <= log2 R <= 8, with the R-point DFTs done as two
 // Stockham sub-stages of radix Q1 = 2^L1 and Q2 = 2^L2 (L1 + L2 = log2 R) held in registers.
 // Sub-stage 1 (stride R/Q1 = Q2): butterfly qq of sequence i takes elements qq + Q2 j, which for
@@ -278,7 +327,9 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_pass_reg(const C* __restric
     __syncthreads();  // sub-stage 1 overwrites the tile in place
   }
   if (act1) {
-    reg_dft<L1, INV>(a, (pti << L2) << fsh, tw, logFmax, fmask);
+    // the first pass (p = 0, pti = 0) has only the constant twiddles of reg_dft_unit here
+    if (logS == logF - LOGR) reg_dft_unit<L1, INV>(a);
+    else reg_dft<L1, INV>(a, (pti << L2) << fsh, tw, logFmax, fmask);
 #pragma unroll
     for (int r = 0; r < Q1; ++r) v[(bf + Q2 * r) * kRow + i] = a[r];
   }
@@ -316,15 +367,16 @@ struct SmallSplit {
 
 __device__ __forceinline__ uint32_t spad(uint32_t e) { return e + (e >> 4); }
 
-// One in-place sub-stage over the tile (every butterfly of radix 2^LQ; lognn = log2 of the
-// sub-length after it). LAST writes to global memory instead.
-template <int LOGF, int LQ, bool LAST, bool INV, class C>
-__device__ __forceinline__ void small_stage(C* v, int lognn, const C* __restrict__ tw, int logFmax, uint32_t fmask,
-                                            C* __restrict__ y, int64_t col0, int64_t ncols) {
+// One in-place sub-stage over the tile (every butterfly of radix 2^LQ; LOGNN = log2 of the
+// sub-length after it). LAST writes to global memory instead. The first sub-stage (LOGNN = LQ)
+// has only the constant twiddles of reg_dft_unit. tw is the table of this length (2^LOGF).
+template <int LOGF, int LQ, int LOGNN, bool LAST, bool INV, class C>
+__device__ __forceinline__ void small_stage(C* v, const C* __restrict__ tw, C* __restrict__ y, int64_t col0,
+                                            int64_t ncols) {
   constexpr int F = 1 << LOGF, Q = 1 << LQ;
   constexpr uint32_t Fp = F + F / 16;
   constexpr int NB = kSmallPts / Q;
-  const int logs = LOGF - lognn, logm = lognn - LQ;
+  constexpr int logs = LOGF - LOGNN, logm = LOGNN - LQ;
   const uint32_t b = threadIdx.x;
   const bool act = b < NB;
   C a[Q];
@@ -340,7 +392,8 @@ __device__ __forceinline__ void small_stage(C* v, int lognn, const C* __restrict
   }
   if (!LAST) __syncthreads();  // the sub-stage works in place
   if (act) {
-    reg_dft<LQ, INV>(a, pp << (logFmax - lognn), tw, logFmax, fmask);
+    if (LOGNN == LQ) reg_dft_unit<LQ, INV>(a);
+    else reg_dft<LQ, INV>(a, pp << (LOGF - LOGNN), tw, LOGF, (uint32_t)F - 1u);
     if (LAST) {
       if (col0 + c < ncols) {
         C* yc = y + (col0 + c) * F;
@@ -370,7 +423,6 @@ __global__ void __launch_bounds__(SmallSplit<LOGF>::NT) k_fft_small(const C* __r
   C* v = reinterpret_cast<C*>(sm_raw);
   const int64_t col0 = (int64_t)blockIdx.x * NCOL;
   const C* x = src + col0 * F;
-  const uint32_t fmask = (1u << logFmax) - 1u;
   const int64_t avail = (ncols - col0) * F;  // points of this CTA's columns that exist
   C t[PER];
   if (hmul) {
@@ -403,13 +455,13 @@ __global__ void __launch_bounds__(SmallSplit<LOGF>::NT) k_fft_small(const C* __r
     v[(idx >> LOGF) * Fp + spad(idx & (F - 1))] = t[u];
   }
   __syncthreads();
-  if (S::NS == 2) {
-    small_stage<LOGF, S::L0, false, INV>(v, S::L0, tw, logFmax, fmask, dst, col0, ncols);
-    small_stage<LOGF, S::L1, true, INV>(v, S::L0 + S::L1, tw, logFmax, fmask, dst, col0, ncols);
+  if constexpr (S::NS == 2) {
+    small_stage<LOGF, S::L0, S::L0, false, INV>(v, tw, dst, col0, ncols);
+    small_stage<LOGF, S::L1, LOGF, true, INV>(v, tw, dst, col0, ncols);
   } else {
-    small_stage<LOGF, S::L0, false, INV>(v, S::L0, tw, logFmax, fmask, dst, col0, ncols);
-    small_stage<LOGF, S::L1, false, INV>(v, S::L0 + S::L1, tw, logFmax, fmask, dst, col0, ncols);
-    small_stage<LOGF, (S::L2 > 0 ? S::L2 : 1), true, INV>(v, LOGF, tw, logFmax, fmask, dst, col0, ncols);
+    small_stage<LOGF, S::L0, S::L0, false, INV>(v, tw, dst, col0, ncols);
+    small_stage<LOGF, S::L1, S::L0 + S::L1, false, INV>(v, tw, dst, col0, ncols);
+    small_stage<LOGF, S::L2, LOGF, true, INV>(v, tw, dst, col0, ncols);
   }
 }
 
