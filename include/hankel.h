@@ -203,6 +203,23 @@ int hankel_plan_info(hankel_plan_t p, hankel_info* out);
 /* Copy up to `cap` far-field blocks into out; *count receives the number of blocks. Host only. */
 int hankel_plan_blocks(hankel_plan_t p, hankel_block* out, int cap, int* count);
 
+/* Inverse DHT (a second workload of Section 6): c = j_{0,N+1}^{-2} D_v J_0(j_0 j_0^T/j_{0,N+1}) D_v f
+ * with v_n = 2/J_1(j_{0,n})^2, the self-inverse relation of the DHT matrix (Section 6, which
+ * uses it to test the transform). The relation holds as N -> infinity: for Gaussian f the
+ * round trip inverse(forward(c)) - c falls like O(N^-2) for small N and then grows like
+ * O(N^{3/2}) from rounding (the paper's Figure on this test). One forward DHT of v o f plus two
+ * diagonal scalings on `stream`; device arrays f [nrhs][ldf] (read) and c [nrhs][ldc]
+ * (written), which must not overlap. DHT plans only. The first call computes v on the host
+ * and allocates N*(1+max_nrhs) doubles on the device; it is blocking. Errors: EINVAL (not a
+ * DHT plan, host-only plan, bad sizes), ENOMEM, ECUDA. */
+int hankel_exec_inverse(hankel_plan_t p, const double* f, int64_t ldf, double* c, int64_t ldc, int nrhs,
+                        void* stream);
+
+/* v_n = 2/J_1(j_{0,n})^2 for n = 1..N (the weights of the inverse DHT), from j_{0,n} carried as
+ * (n, b_n): Eq. (4) for nu = 1 with its phase reduced to b_n for large roots, Miller's
+ * recurrence in double-double for small ones. Host only. Errors: EINVAL. */
+int hankel_dht_inverse_weights(int64_t N, double* v);
+
 /* Host evaluation of the plan's representation of matrix entry (k, n), 1-based:
  * *value receives the number the plan uses for J_nu(r_k omega_n) (the near-field
  * evaluator or the far-field expansion) and *is_far is 1 when (k, n) lies in a

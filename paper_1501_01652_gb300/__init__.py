@@ -64,6 +64,15 @@ def q_T(T, eps):
     return _lib.load().hankel_q_T(int(T), float(eps))
 
 
+def dht_inverse_weights(N):
+    """v_n = 2/J_1(j_{0,n})^2, n = 1..N (host), as a numpy array."""
+    lib = _lib.load()
+    v = np.empty(int(N), dtype=np.float64)
+    _lib.check(lib.hankel_dht_inverse_weights(int(N), v.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+               "hankel_dht_inverse_weights")
+    return v
+
+
 def j0_zero_offsets(count):
     """b_n = j_{0,n} - (n-1/4)pi, n = 1..count, from the library's node builder."""
     b = np.empty(int(count), dtype=np.float64)
@@ -144,32 +153,39 @@ class Plan:
         return {name: {"ms": a.ms, "flops": a.flops, "entries": a.entries, "bytes": a.bytes, "launches": a.launches}
                 for name, a in zip(_lib.STAGES, arr)}
 
-    def exec(self, c, f=None, stream=None):
-        """Run on torch CUDA float64 tensors of shape (N,) or (nrhs, N); returns f."""
+    def _run(self, fn, name, c, f, stream):
         import torch
 
         if not (c.is_cuda and c.dtype == torch.float64):
-            raise TypeError("c must be a CUDA float64 tensor")
+            raise TypeError("input must be a CUDA float64 tensor")
         single = c.dim() == 1
         c2 = c.reshape(1, -1) if single else c
         if c2.shape[-1] != self.N or c2.stride(-1) != 1:
-            raise ValueError("c must have N contiguous entries per row")
+            raise ValueError("input must have N contiguous entries per row")
         nrhs = c2.shape[0]
         if f is None:
             f2 = torch.empty((nrhs, self.N), dtype=torch.float64, device=c.device)
         else:
             f2 = f.reshape(1, -1) if f.dim() == 1 else f
             if not (f2.is_cuda and f2.dtype == torch.float64) or f2.shape != (nrhs, self.N) or f2.stride(-1) != 1:
-                raise ValueError("f must be a CUDA float64 tensor shaped like c")
+                raise ValueError("output must be a CUDA float64 tensor shaped like the input")
         if stream is None:
             stream = torch.cuda.current_stream(c.device)
-        st = self._lib.hankel_exec_batched(self._h, ctypes.c_void_p(c2.data_ptr()), c2.stride(0) if nrhs > 1 else self.N,
-                                           ctypes.c_void_p(f2.data_ptr()), f2.stride(0) if nrhs > 1 else self.N,
-                                           nrhs, ctypes.c_void_p(stream.cuda_stream))
-        _lib.check(st, "hankel_exec_batched")
+        st = fn(self._h, ctypes.c_void_p(c2.data_ptr()), c2.stride(0) if nrhs > 1 else self.N,
+                ctypes.c_void_p(f2.data_ptr()), f2.stride(0) if nrhs > 1 else self.N, nrhs,
+                ctypes.c_void_p(stream.cuda_stream))
+        _lib.check(st, name)
         if f is not None:
             return f
         return f2[0] if single else f2
+
+    def exec(self, c, f=None, stream=None):
+        """Run on torch CUDA float64 tensors of shape (N,) or (nrhs, N); returns f."""
+        return self._run(self._lib.hankel_exec_batched, "hankel_exec_batched", c, f, stream)
+
+    def exec_inverse(self, f, c=None, stream=None):
+        """Inverse DHT (DHT plans): c = j_{0,N+1}^-2 v o J(v o f), v_n = 2/J_1(j_{0,n})^2."""
+        return self._run(self._lib.hankel_exec_inverse, "hankel_exec_inverse", f, c, stream)
 
     def exec_host(self, c, out=None):
         """End-to-end call on host arrays (numpy float64, (N,) or (nrhs, N)); returns f."""

@@ -19,6 +19,7 @@ FLAG_NO_REFINE = 16
 EXPORTED = [
     "hankel_options_default", "hankel_plan", "hankel_plan_ex", "hankel_exec", "hankel_exec_batched",
     "hankel_exec_host", "hankel_plan_info", "hankel_plan_blocks", "hankel_plan_entry", "hankel_plan_expansion_entry",
+    "hankel_exec_inverse", "hankel_dht_inverse_weights",
     "hankel_plan_near_prefix", "hankel_destroy", "hankel_status_string", "hankel_s_nu_M",
     "hankel_t_nu_T", "hankel_neumann_radius", "hankel_p_K", "hankel_q_T", "hankel_params",
     "hankel_j0_zero_offsets", "hankel_plan_set_timing", "hankel_plan_stage_stats", "hankel_exec_static",
@@ -96,6 +97,8 @@ def load():
         "hankel_plan_blocks": (i32, [vp, ctypes.POINTER(Block), i32, ctypes.POINTER(i32)]),
         "hankel_plan_entry": (i32, [vp, i64, i64, dp, ctypes.POINTER(i32)]),
         "hankel_plan_expansion_entry": (i32, [vp, i64, i64, dp]),
+        "hankel_exec_inverse": (i32, [vp, vp, i64, vp, i64, i32, vp]),
+        "hankel_dht_inverse_weights": (i32, [i64, dp]),
         "hankel_plan_near_prefix": (i32, [vp, i64, ctypes.POINTER(i64)]),
         "hankel_destroy": (i32, [vp]),
         "hankel_status_string": (ctypes.c_char_p, [i32]),

@@ -3,6 +3,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <vector>
+
 #include <new>
 
 #include "device.h"
@@ -200,6 +202,22 @@ int hankel_exec_host(hankel_plan_t p, const double* c, int64_t ldc, double* f, i
   const int64_t N = p->hp.opt.N;
   if (nrhs < 1 || nrhs > p->hp.opt.max_nrhs || ldc < N || ldf < N) return HANKEL_EINVAL;
   return hk::dev_exec_host(p, c, ldc, f, ldf, nrhs);
+}
+
+int hankel_exec_inverse(hankel_plan_t p, const double* f, int64_t ldf, double* c, int64_t ldc, int nrhs,
+                        void* stream) {
+  if (!p || !c || !f || p->host_only || p->hp.opt.task != HANKEL_DHT) return HANKEL_EINVAL;
+  const int64_t N = p->hp.opt.N;
+  if (nrhs < 1 || nrhs > p->hp.opt.max_nrhs || ldc < N || ldf < N) return HANKEL_EINVAL;
+  return hk::dev_exec_inverse(p, f, ldf, c, ldc, nrhs, stream);
+}
+
+int hankel_dht_inverse_weights(int64_t N, double* v) {
+  if (N < 1 || !v) return HANKEL_EINVAL;
+  std::vector<double> b(N);
+  hk::j0_zero_offsets(N, b.data());
+  hk::dht_inverse_weights(N, b.data(), v);
+  return HANKEL_OK;
 }
 
 int hankel_exec_static(hankel_plan_t p, const double* c, double* f, void* stream) {

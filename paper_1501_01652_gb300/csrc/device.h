@@ -22,6 +22,7 @@ int dev_plan_destroy(hankel_plan_s* p);
 int dev_exec(hankel_plan_s* p, const double* c, int64_t ldc, double* f, int64_t ldf, int nrhs, void* stream);
 int dev_exec_host(hankel_plan_s* p, const double* c, int64_t ldc, double* f, int64_t ldf, int nrhs);
 int dev_exec_static(hankel_plan_s* p, const double* c, double* f, void* stream);
+int dev_exec_inverse(hankel_plan_s* p, const double* f, int64_t ldf, double* c, int64_t ldc, int nrhs, void* stream);
 int dev_set_timing(hankel_plan_s* p, int enable);
 int dev_stage_stats(hankel_plan_s* p, hankel_stage_stat* out);
 size_t dev_plan_bytes(const hankel_plan_s* p);

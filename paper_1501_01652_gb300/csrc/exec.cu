@@ -74,6 +74,8 @@ struct DevicePlan {
   size_t ws_elems = 0;
   double* c_stage = nullptr;
   double* f_stage = nullptr;
+  double* vinv = nullptr;     // DHT plans, first inverse call: v_n = 2 / J_1(j_{0,n})^2
+  double* inv_stage = nullptr;  // v o f for the inverse ([max_nrhs][N])
   double2* T = nullptr;  // column factor table (or nullptr; FP32 plans keep per-block tables instead)
   double* W = nullptr;   // row factor table (or nullptr)
   float* cf = nullptr;   // FP32 plans with per-block tables: the coefficients rounded to FP32 [max_nrhs][N]
@@ -568,6 +570,34 @@ int dev_exec_host(hankel_plan_s* p, const double* c, int64_t ldc, double* f, int
                         cudaMemcpyDeviceToHost, st) != cudaSuccess)
     return HANKEL_ECUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return HANKEL_ECUDA;
+  if (cur >= 0 && cur != d->device) cudaSetDevice(cur);
+  return HANKEL_OK;
+}
+
+// Inverse DHT through the self-inverse relation of Section 6:
+// c = j_{0,N+1}^{-2} v o (J (v o f)), v_n = 2 / J_1(j_{0,n})^2.
+int dev_exec_inverse(hankel_plan_s* p, const double* f, int64_t ldf, double* c, int64_t ldc, int nrhs,
+                     void* stream) {
+  const HostPlan& hp = p->hp;
+  const int64_t N = hp.opt.N;
+  DevicePlan* d = p->dev;
+  cudaStream_t st = (cudaStream_t)stream;
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (cur != d->device) cudaSetDevice(d->device);
+  if (!d->vinv) {  // made on first use (a host computation of J_1 at the roots)
+    std::vector<double> v(N);
+    dht_inverse_weights(N, hp.b.data(), v.data());
+    HK_TRY(upload(d, &d->vinv, v.data(), v.size()));
+    HK_TRY(dalloc(d, &d->inv_stage, (size_t)N * hp.opt.max_nrhs));
+  }
+  const double jN1 = (N + 0.75) * 3.14159265358979323846 + hp.b[N];
+  launch_diag_scale(f, ldf, d->vinv, 1.0, d->inv_stage, N, N, nrhs, st);
+  HK_LAUNCHED();
+  int s = dev_exec(p, d->inv_stage, N, c, ldc, nrhs, stream);
+  if (s != HANKEL_OK) return s;
+  launch_diag_scale(c, ldc, d->vinv, 1.0 / (jN1 * jN1), c, ldc, N, nrhs, st);
+  HK_LAUNCHED();
   if (cur >= 0 && cur != d->device) cudaSetDevice(cur);
   return HANKEL_OK;
 }

@@ -260,6 +260,14 @@ __global__ void __launch_bounds__(256) k_coeffs_f32(const double* __restrict__ c
   }
 }
 
+__global__ void __launch_bounds__(256) k_diag_scale(const double* x, int64_t ldx, const double* __restrict__ v,
+                                                    double scale, double* out, int64_t ldo, int64_t N, int64_t total) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / N, i = e - r * N;
+    out[r * ldo + i] = scale * v[i] * x[r * ldx + i];
+  }
+}
+
 unsigned grid1d(int64_t n) {
   int64_t g = (n + 255) / 256;
   return (unsigned)std::min<int64_t>(std::max<int64_t>(g, 1), int64_t(152) * 32);
@@ -302,6 +310,12 @@ void launch_block_tables_f32(const double2* T, const double* W, int64_t N, int n
                              float* Wf, cudaStream_t st) {
   k_block_tables_f32<<<grid1d((int64_t)nl * std::max(C, R)), 256, 0, st>>>(T, W, N, nl, lmap, n0, C, k0, R, scale,
                                                                             iscale, Tf, Wf);
+}
+
+void launch_diag_scale(const double* x, int64_t ldx, const double* v, double scale, double* out, int64_t ldo,
+                       int64_t N, int nrhs, cudaStream_t st) {
+  const int64_t total = N * nrhs;
+  k_diag_scale<<<grid1d(total), 256, 0, st>>>(x, ldx, v, scale, out, ldo, N, total);
 }
 
 void launch_coeffs_f32(const double* c, int64_t ldc, float* cf, int64_t N, int nrhs, cudaStream_t st) {

@@ -127,6 +127,9 @@ void launch_build_tables(const TabArgs& a, cudaStream_t st);
 void launch_block_tables_f32(const double2* T, const double* W, int64_t N, int nl, const int* lmap, int64_t n0,
                              int64_t C, int64_t k0, int64_t R, const double* scale, const double* iscale, float2* Tf,
                              float* Wf, cudaStream_t st);
+// out[r * ldo + i] = scale * v[i] * x[r * ldx + i] for r < nrhs, i < N (out may be x).
+void launch_diag_scale(const double* x, int64_t ldx, const double* v, double scale, double* out, int64_t ldo,
+                       int64_t N, int nrhs, cudaStream_t st);
 // cf[r * N + i] = (float) c[r * ldc + i] for r < nrhs, i < N.
 void launch_coeffs_f32(const double* c, int64_t ldc, float* cf, int64_t N, int nrhs, cudaStream_t st);
 

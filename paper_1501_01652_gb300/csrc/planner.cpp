@@ -215,6 +215,39 @@ void j0_zero_offsets(int64_t count, double* b) {
   for (int64_t n = 1; n <= count; ++n) b[n - 1] = ((n - 0.25) * kPi < 30.0) ? root_offset_small(n) : root_offset_large(n);
 }
 
+// |J_1(j_{0,n})| with j_{0,n} = (n-1/4)pi + b_n. Large roots: Eq. (4) with nu = 1, whose phase
+// z - 3pi/4 = (n-1)pi + b_n leaves |J_1| = sqrt(2/(pi z)) |P(z) cos b_n - Q(z) sin b_n| (P, Q the
+// even and odd parts of the Hankel series, summed to its smallest term); small roots: Miller's
+// recurrence in double-double at z.
+double j1_at_j0_zero(int64_t n, double b) {
+  if ((n - 0.25) * kPi < 30.0) {
+    std::vector<DD> J;
+    miller_all(dd_add(dd_mul(kPiDD, ddv(n - 0.25)), ddv(b)), 1, J);
+    return std::fabs(J[1].h + J[1].l);
+  }
+  const double z = (n - 0.25) * kPi + b;
+  double a[80];
+  hankel_a(1, 79, a);
+  double p = 0.0, q = 0.0, zm = 1.0, prev = INFINITY;
+  for (int m = 0; m < 79; ++m) {
+    const double term = a[m] * zm;
+    if (std::fabs(term) > prev) break;  // the asymptotic series starts to grow
+    prev = std::fabs(term);
+    const int r = m & 3;
+    if (r == 0) p += term; else if (r == 1) q += term; else if (r == 2) p -= term; else q -= term;
+    if (std::fabs(term) < 1e-20) break;
+    zm /= z;
+  }
+  return std::sqrt(2.0 / (kPi * z)) * std::fabs(p * std::cos(b) - q * std::sin(b));
+}
+
+void dht_inverse_weights(int64_t N, const double* b, double* v) {
+  for (int64_t n = 1; n <= N; ++n) {
+    const double j1 = j1_at_j0_zero(n, b[n - 1]);
+    v[n - 1] = 2.0 / (j1 * j1);
+  }
+}
+
 }  // namespace hk
 
 // ---------------------------------------------------------------------------

@@ -129,6 +129,19 @@ def test_fp32_workload_size_sampled_rows(eps):
     _check("dht", 0, N, eps, c, rows=rows)
 
 
+@pytest.mark.parametrize("task,nu,eps,kind", [
+    ("schlomilch", 1, 1e-15, "uniform"), ("fourier_bessel", 0, 1e-8, "uniform"),
+    ("dht", 0, 1e-15, "normal"), ("dht", 0, 1e-4, "normal"),
+])
+def test_largest_workload_size_sampled_rows(task, nu, eps, kind):
+    # N = 2^22, the largest size of the workload table; at eps = 1e-15 the DHT's factor tables
+    # exceed their limit and the factors are computed per use
+    N = 2 ** 22
+    c = coefficients(kind, N, 1, 4 * 1000 + 22)
+    rows = sample_rows(N, 40, 23)
+    _check(task, nu, N, eps, c, rows=rows)
+
+
 @pytest.mark.parametrize("tables", [True, False])
 def test_factor_tables_on_and_off(tables):
     # column/row factors from plan-time device tables or computed per use give the same bar
@@ -212,6 +225,31 @@ def test_dht_self_inverse_gpu():
     y = plan.exec(torch.from_numpy(v * c).cuda())
     ct = plan.exec(torch.from_numpy(v).cuda() * y).cpu().numpy() / j[N] ** 2
     assert np.max(np.abs(ct - c)) <= 2e-11
+    # the inverse entry point: one DHT of v o f between two diagonal scalings
+    f = plan.exec(torch.from_numpy(c).cuda())
+    ci = plan.exec_inverse(f).cpu().numpy()
+    assert np.max(np.abs(ci - c)) <= 2e-11
+
+
+@pytest.mark.parametrize("N,eps,nrhs", [(3000, 1e-15, 1), (5000, 1e-8, 3), (2 ** 16, 1e-15, 2), (20000, 1e-4, 2)])
+def test_dht_inverse_against_oracle(N, eps, nrhs):
+    # c = j_{0,N+1}^{-2} v o J(v o f) element by element against the oracle's DHT of v o f; the bar
+    # is the transform's, 10 eps ||v o f||_1, scaled by v_n / j_{0,N+1}^2
+    f = coefficients("normal", N, nrhs, 7100 + N)
+    b = oracle.j0_zero_offsets(N + 1)
+    jN1 = (N + 0.75) * math.pi + b[N]
+    v = np.array([2.0 / oracle.besselj_pi(1, 4 * n - 1, 4, b[n - 1]) ** 2 for n in range(1, N + 1)])
+    plan = hk.Plan("dht", 0, N, eps, max_nrhs=nrhs)
+    c = plan.exec_inverse(torch.from_numpy(f).cuda()).cpu().numpy().reshape(nrhs, N)
+    rows = None if N <= 5000 else sample_rows(N, 64, 29)
+    y = oracle.transform("dht", 0, N, v * f, rows=rows).reshape(nrhs, -1)
+    vv = v if rows is None else v[rows]
+    ref = vv * y / jN1 ** 2
+    got = c if rows is None else c[:, rows]
+    bound = 10 * eps * np.abs(v * f).sum(axis=1, keepdims=True) * vv / jN1 ** 2
+    assert np.all(np.abs(got - ref) <= bound)
+    with pytest.raises(RuntimeError, match="EINVAL"):
+        hk.Plan("schlomilch", 0, 100, 1e-8).exec_inverse(torch.zeros(100, dtype=torch.float64, device="cuda"))
 
 
 def test_rejects_bad_arguments():

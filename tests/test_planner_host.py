@@ -223,3 +223,19 @@ def test_expansion_without_the_partition_fails_the_bar(task, nu, N, eps, grid):
     far = np.array([[p.entry(k, n)[1] for n in range(1, N + 1)] for k in range(1, N + 1)])
     assert far.any()
     assert np.max(np.abs(A_exp[far] - A_plan[far])) <= eps
+
+
+def test_dht_inverse_weights():
+    # v_n = 2/J_1(j_{0,n})^2: J_1(j_{0,1}) = 0.5191474972894669 (the first extremum value of J_1 at
+    # the first zero of J_0); the rest against the oracle's exact-phase J_1 at (n-1/4)pi + b_n,
+    # across the switch from the small-root recurrence to the large-root expansion
+    N = 20000
+    v = hk.dht_inverse_weights(N)
+    assert abs(v[0] - 2.0 / 0.5191474972894669 ** 2) <= 4e-15 * v[0]
+    b = oracle.j0_zero_offsets(N)
+    idx = np.unique(np.concatenate([np.arange(1, 40), np.linspace(1, N, 300).astype(int)]))
+    ref = np.array([2.0 / oracle.besselj_pi(1, 4 * n - 1, 4, b[n - 1]) ** 2 for n in idx])
+    assert np.max(np.abs(v[idx - 1] / ref - 1)) <= 4e-15
+    # large-root limit: J_1(j_{0,n})^2 ~ 2/(pi j_{0,n}), so v_n ~ pi j_{0,n}
+    n = np.arange(N - 10, N + 1)
+    assert np.max(np.abs(v[n - 1] / (np.pi * ((n - 0.25) * np.pi + b[n - 1])) - 1)) < 1e-9
