@@ -33,9 +33,10 @@ FP64_PEAK_GFLOPS = 152 * 4 * 2.07  # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GH
 HBM_FALLBACK_GBS = 6800.0          # used only when MEASURED_PEAKS.json is absent
 FP64_MEASURED_GFLOPS = 1004.0      # DFMA microbenchmark on this part (2 x 502 G instructions/s)
 # DRAM bytes per algorithmic byte of an FP64 FFT pass launch, from an ncu capture of one
-# radix-128 inverse pass (k_fft_pass_reg, 4608 CTAs of 16 x 128 points: 151.0 MB read +
-# 104.7 MB written, 302.0 MB algorithmic; part of the output is still in L2 at kernel end).
-FFT_TRAFFIC_RATIO = (151.05 + 104.67) / 301.99
+# radix-128 inverse pass with the chirp-spectrum product folded into its loads (k_fft_pass_reg,
+# 4096 CTAs of 16 x 128 points: 145.1 MB read + 93.9 MB written, 268.4 MB algorithmic; the
+# spectrum is L2-resident and part of the output is still in L2 at kernel end).
+FFT_TRAFFIC_RATIO = (145.12 + 93.91) / 268.44
 METRIC = "DHT-0 coeffs/s at N=2^20 (eps=1e-8,1e-15) served vs plain FP64; p50/p99 ms"
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
