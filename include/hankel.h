@@ -83,12 +83,14 @@ enum hankel_status {
 /* Plan flags (hankel_options.flags). */
 #define HANKEL_FLAG_HOST_ONLY 1u   /* build host tables only; no CUDA call is made */
 #define HANKEL_FLAG_NO_SEGMENT 2u  /* one full-length chirp-z transform per block (no segmenting of thin blocks) */
-#define HANKEL_FLAG_NO_TABLES 4u   /* compute column/row factors per use instead of keeping tables of
-                                      ncols * N * 24 bytes on the device (tables are skipped anyway above 16 GiB) */
 #define HANKEL_FLAG_ALL_COLUMNS 8u /* every block keeps all ncols stacked columns; by default a block leaves
                                       out the columns whose summed bound on its entries stays within
                                       eps per entry, split over the blocks of a row (hankel_block.ncols,
                                       hankel_info.block_cols) */
+#define HANKEL_FLAG_NO_LOWRANK 32u /* every block transforms its kept stacked columns; by default a block whose
+                                      kernel has a low-rank form exact to eps/2 (Chebyshev interpolation
+                                      in log k, log n and cross approximation) transforms its rank instead
+                                      (hankel_block.ncols, .kept, .lowrank_err) */
 #define HANKEL_FLAG_NO_REFINE 16u  /* keep the blocks of Eq. (19) as they are; by default a block is cut into
                                       smaller ones where that lowers the estimated work (fewer kept columns
                                       away from the near field) */
@@ -129,7 +131,7 @@ typedef struct {
   double near_zmax;       /* largest argument r_k omega_n in the near field */
   size_t device_bytes;    /* device memory held by the plan (tables + workspace) */
   size_t workspace_bytes; /* part of device_bytes used as transform workspace */
-  int64_t block_cols;     /* stacked columns kept, summed over blocks (nblocks * ncols when none is left out) */
+  int64_t block_cols;     /* transforms per right-hand side summed over blocks (hankel_block.ncols) */
 } hankel_info;
 
 /* One far-field block of the partition, 1-based inclusive index ranges. */
@@ -141,8 +143,12 @@ typedef struct {
   int64_t nseg;    /* number of segments (1 = one transform with F >= rows + cols - 1) */
   int mode;        /* 0 unsegmented; 1 columns segmented (overlap-add), F >= rows + S - 1;
                       2 rows segmented (overlap-save), F >= S + cols - 1 */
-  int ncols;       /* stacked columns this block transforms per right-hand side (<= hankel_info.ncols) */
+  int ncols;       /* transforms this block runs per right-hand side: its low-rank form's rank, or its
+                      kept stacked columns when it has no low-rank form */
   double dropped;  /* bound on the change of any entry of the block from the columns it leaves out */
+  int kept;        /* stacked columns the block keeps (<= hankel_info.ncols) */
+  int lowrank;     /* 1 when the block runs its low-rank form */
+  double lowrank_err; /* largest error of the low-rank form on its validation entries (<= eps/2) */
 } hankel_block;
 
 /* Fill *o with defaults for (task, nu, N, eps). Host only. Returns HANKEL_OK or HANKEL_EINVAL (o == NULL). */

@@ -18,7 +18,7 @@ PRECISIONS = {"auto": 0, "fp64": 1, "fp32": 2}
 
 
 def _options(task, nu, N, eps, grid="unit", gamma=None, precision="auto", max_nrhs=1, workspace_limit=0,
-             host_only=False, segment=True, tables=True, prune=True, refine=True):
+             host_only=False, segment=True, prune=True, refine=True, lowrank=True):
     lib = _lib.load()
     o = _lib.Options()
     _lib.check(lib.hankel_options_default(ctypes.byref(o), TASKS[task], int(nu), int(N), float(eps)),
@@ -30,8 +30,8 @@ def _options(task, nu, N, eps, grid="unit", gamma=None, precision="auto", max_nr
     o.max_nrhs = int(max_nrhs)
     o.workspace_limit = int(workspace_limit)
     o.flags = ((_lib.FLAG_HOST_ONLY if host_only else 0) | (0 if segment else _lib.FLAG_NO_SEGMENT)
-               | (0 if tables else _lib.FLAG_NO_TABLES) | (0 if prune else _lib.FLAG_ALL_COLUMNS)
-               | (0 if refine else _lib.FLAG_NO_REFINE))
+               | (0 if prune else _lib.FLAG_ALL_COLUMNS)
+               | (0 if refine else _lib.FLAG_NO_REFINE) | (0 if lowrank else _lib.FLAG_NO_LOWRANK))
     return o
 
 
@@ -85,13 +85,13 @@ class Plan:
     """A transform plan: f = J_nu(r omega^T) c for one task, order, size and accuracy."""
 
     def __init__(self, task, nu, N, eps, grid="unit", gamma=None, precision="auto", max_nrhs=1,
-                 workspace_limit=0, host_only=False, segment=True, tables=True, prune=True, refine=True):
+                 workspace_limit=0, host_only=False, segment=True, prune=True, refine=True, lowrank=True):
         self._lib = _lib.load()
         self._h = ctypes.c_void_p()
         self.task, self.nu, self.N, self.eps = task, int(nu), int(N), float(eps)
         self.max_nrhs = int(max_nrhs)
         o = _options(task, nu, N, eps, grid, gamma, precision, max_nrhs, workspace_limit, host_only, segment,
-                     tables, prune, refine)
+                     prune, refine, lowrank)
         _lib.check(self._lib.hankel_plan_ex(ctypes.byref(self._h), ctypes.byref(o)), "hankel_plan_ex")
 
     def __del__(self):
@@ -119,7 +119,8 @@ class Plan:
         arr = (_lib.Block * max(cnt.value, 1))()
         _lib.check(self._lib.hankel_plan_blocks(self._h, arr, cnt.value, ctypes.byref(cnt)), "hankel_plan_blocks")
         return [dict(k0=b.k0, k1=b.k1, n0=b.n0, n1=b.n1, F=b.fft_len, S=b.seg_len, nseg=b.nseg, mode=b.mode,
-                     ncols=b.ncols, dropped=b.dropped)
+                     ncols=b.ncols, dropped=b.dropped, kept=b.kept, lowrank=bool(b.lowrank),
+                     lowrank_err=b.lowrank_err)
                 for b in arr[:cnt.value]]
 
     def entry(self, k, n):

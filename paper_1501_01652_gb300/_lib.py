@@ -11,9 +11,9 @@ STATUS_NAMES = {0: "HANKEL_OK", 1: "HANKEL_EINVAL", 2: "HANKEL_ENOMEM", 3: "HANK
                 4: "HANKEL_EUNSUPPORTED", 5: "HANKEL_ETIMEOUT"}
 FLAG_HOST_ONLY = 1
 FLAG_NO_SEGMENT = 2
-FLAG_NO_TABLES = 4
 FLAG_ALL_COLUMNS = 8
 FLAG_NO_REFINE = 16
+FLAG_NO_LOWRANK = 32
 
 # Every function include/hankel.h declares.
 EXPORTED = [
@@ -73,7 +73,8 @@ class ServerStats(ctypes.Structure):
 class Block(ctypes.Structure):
     _fields_ = [("k0", ctypes.c_int64), ("k1", ctypes.c_int64), ("n0", ctypes.c_int64), ("n1", ctypes.c_int64),
                 ("fft_len", ctypes.c_int64), ("seg_len", ctypes.c_int64), ("nseg", ctypes.c_int64),
-                ("mode", ctypes.c_int), ("ncols", ctypes.c_int), ("dropped", ctypes.c_double)]
+                ("mode", ctypes.c_int), ("ncols", ctypes.c_int), ("dropped", ctypes.c_double),
+                ("kept", ctypes.c_int), ("lowrank", ctypes.c_int), ("lowrank_err", ctypes.c_double)]
 
 
 def load():

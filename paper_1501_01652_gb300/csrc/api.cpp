@@ -71,7 +71,7 @@ static void fill_info(const hankel_plan_s* p, const hk::HostPlan& hp, hankel_inf
     out->ncols = hp.U1 * (2 * hp.M + hp.U2 - 1);
   }
   out->block_cols = 0;
-  for (const hk::Block& b : hp.blocks) out->block_cols += (int64_t)b.lcols.size();
+  for (const hk::Block& b : hp.blocks) out->block_cols += b.rank ? b.rank : (int64_t)b.lcols.size();
   out->near_count = hp.near_count;
   out->far_count = hp.far_count;
   out->near_zmax = hp.zmax;
@@ -158,8 +158,11 @@ int hankel_plan_blocks(hankel_plan_t p, hankel_block* out, int cap, int* count) 
     out[i].seg_len = bl[i].S;
     out[i].nseg = bl[i].nseg;
     out[i].mode = bl[i].mode;
-    out[i].ncols = (int)bl[i].lcols.size();
+    out[i].ncols = bl[i].rank ? bl[i].rank : (int)bl[i].lcols.size();
     out[i].dropped = bl[i].dropped;
+    out[i].kept = (int)bl[i].lcols.size();
+    out[i].lowrank = bl[i].rank ? 1 : 0;
+    out[i].lowrank_err = bl[i].lowrank_err;
   }
   return HANKEL_OK;
 }

@@ -24,8 +24,6 @@ namespace hk {
 namespace {
 
 constexpr size_t kDefaultWorkspace = size_t(4) << 30;
-// Largest size of the column/row factor tables a plan builds (beyond it, factors are computed per use).
-constexpr size_t kTableLimit = size_t(16) << 30;
 
 // Complex elements one stacked column occupies in a workspace buffer.
 size_t column_footprint(const Block& b) { return (size_t)b.F * (size_t)b.nseg; }
@@ -35,12 +33,9 @@ struct DevBlock {
   double2* wU = nullptr;  // exp(i pi U_k^2 / (2E)), k = k0..k1
   double2* wV = nullptr;  // exp(i pi V_n^2 / (2E)), n = n0..n1
   void* H = nullptr;      // per segment: FFT_F of the chirp exp(-i pi (U-V)^2 / (2E)), times 1/F (plan precision)
-  double* scale = nullptr;   // FP32 plans: per stacked column, power of two keeping generated values near 1
-  double* iscale = nullptr;  // its inverse, applied to the row factors
-  int* lmap = nullptr;       // the block's kept stacked columns (indices into the plan's columns)
-  int nl = 0;                // their number
-  float2* Tf = nullptr;      // FP32 plans with tables: [nl][C] column factors x chirp x scale
-  float* Wf = nullptr;       // FP32 plans with tables: [nl][R] row factors x iscale
+  int nl = 0;                // stacked columns (transforms) per right-hand side
+  void* Vt = nullptr;        // [nl][C] column functions x column chirp (x FP32 scale), plan precision
+  void* Ut = nullptr;        // [nl][R] row functions (/ FP32 scale), plan precision
   int64_t cap = 0;           // columns per chunk
 };
 
@@ -76,9 +71,7 @@ struct DevicePlan {
   double* f_stage = nullptr;
   double* vinv = nullptr;     // DHT plans, first inverse call: v_n = 2 / J_1(j_{0,n})^2
   double* inv_stage = nullptr;  // v o f for the inverse ([max_nrhs][N])
-  double2* T = nullptr;  // column factor table (or nullptr; FP32 plans keep per-block tables instead)
-  double* W = nullptr;   // row factor table (or nullptr)
-  float* cf = nullptr;   // FP32 plans with per-block tables: the coefficients rounded to FP32 [max_nrhs][N]
+  float* cf = nullptr;   // FP32 plans: the coefficients rounded to FP32 [max_nrhs][N]
   size_t bytes = 0;
   std::vector<void*> allocs;
   // stage statistics (hankel_plan_set_timing / hankel_plan_stage_stats)
@@ -110,7 +103,7 @@ int dalloc(DevicePlan* d, T** p, size_t count) {
   return HANKEL_OK;
 }
 
-// Releases one allocation made by dalloc.
+// Releases one allocation made by dalloc with count elements.
 template <class T>
 void dfree(DevicePlan* d, T** p, size_t count) {
   if (!*p) return;
@@ -233,15 +226,6 @@ int dev_plan_create(hankel_plan_s* p) {
     HK_TRY(upload(d, &d->jtabf, tf.data(), hp.jtab.size()));
   }
 
-  // Factor tables: the column and row functions of every stacked column at every index.
-  const size_t tab_bytes = (size_t)d->ncols * (size_t)N * (sizeof(double2) + sizeof(double));
-  if (!(hp.opt.flags & HANKEL_FLAG_NO_TABLES) && !hp.blocks.empty() && tab_bytes <= kTableLimit) {
-    HK_TRY(dalloc(d, &d->T, (size_t)d->ncols * N));
-    HK_TRY(dalloc(d, &d->W, (size_t)d->ncols * N));
-    TabArgs ta{d->T, d->W, N, d->ncols, d->nodes, d->cols, hp.Va, hp.Vb, hp.E};
-    launch_build_tables(ta, 0);
-    HK_LAUNCHED();
-  }
 
   // Near-field work list: groups of kNearRows rows, the group's longest prefix cut into tiles of
   // kNearCols columns; groups with more than one tile add up per-row partial sums.
@@ -301,7 +285,7 @@ int dev_plan_create(hankel_plan_s* p) {
   size_t need = dfac << logFmax;
   for (const Block& b : hp.blocks) {
     const size_t foot = column_footprint(b);
-    const int64_t total = (int64_t)d->ncols * hp.opt.max_nrhs;
+    const int64_t total = (int64_t)(b.rank ? b.rank : (int)b.lcols.size()) * hp.opt.max_nrhs;
     int64_t cap = (int64_t)(limit / (2 * esz * foot));
     cap = std::max<int64_t>(1, std::min<int64_t>(cap, total));
     need = std::max(need, (size_t)cap * foot);
@@ -317,51 +301,80 @@ int dev_plan_create(hankel_plan_s* p) {
   d->ws_bytes = 2 * need * esz;
   d->ws_elems = need;
 
-  // Per-block chirp vectors and the spectra of its convolution kernels (one per segment).
+  // Per block: chirp vectors, the spectra of its convolution kernels (one per segment) and its
+  // column and row tables (the low-rank form's terms, or its kept stacked columns).
   for (const Block& b : hp.blocks) {
     DevBlock db;
     db.b = b;
+    db.nl = b.rank ? b.rank : (int)b.lcols.size();
     db.cap = std::max<int64_t>(1, std::min<int64_t>((int64_t)(need / column_footprint(b)),
-                                                    (int64_t)d->ncols * hp.opt.max_nrhs));
+                                                    (int64_t)db.nl * hp.opt.max_nrhs));
     HK_TRY(dalloc(d, &db.wU, b.R));
     HK_TRY(dalloc(d, &db.wV, b.C));
-    db.nl = (int)b.lcols.size();
-    HK_TRY(upload(d, &db.lmap, b.lcols.data(), b.lcols.size()));
-    if (d->fp32) {
-      float2* h; HK_TRY(dalloc(d, &h, (size_t)b.nseg * b.F)); db.H = h;
-      // per stacked column: the power of two that brings max |colfun(n)| over the block to ~1
-      std::vector<double> sc(d->ncols), isc(d->ncols);
-      for (int l = 0; l < d->ncols; ++l) {
-        const ColSpec& csp = hp.cols[l];
-        double mag = 0.0;
-        for (int64_t n : {b.n0, b.n1}) {
-          const int64_t i = n - 1;
-          cplx poly(0.0, 0.0);
-          for (int u = csp.nterm - 1; u >= 0; --u) poly = poly * hp.betan[i] + csp.G[u];
-          double m = std::abs(poly) * std::pow(hp.omt[i], csp.delta - 0.5);
-          if (csp.u1) m *= std::pow(hp.colpow[i], csp.u1);
-          mag = std::max(mag, m);
-        }
-        const int e = (mag > 0.0 && std::isfinite(mag)) ? -(int)std::lround(std::log2(mag)) : 0;
-        sc[l] = std::ldexp(1.0, e);
-        isc[l] = std::ldexp(1.0, -e);
-      }
-      HK_TRY(upload(d, &db.scale, sc.data(), sc.size()));
-      HK_TRY(upload(d, &db.iscale, isc.data(), isc.size()));
-      if (d->T) {
-        HK_TRY(dalloc(d, &db.Tf, (size_t)db.nl * b.C));
-        HK_TRY(dalloc(d, &db.Wf, (size_t)db.nl * b.R));
-        launch_block_tables_f32(d->T, d->W, N, db.nl, db.lmap, b.n0, b.C, b.k0, b.R, db.scale, db.iscale, db.Tf,
-                                db.Wf, 0);
-        HK_LAUNCHED();
-      }
-    } else {
-      double2* h; HK_TRY(dalloc(d, &h, (size_t)b.nseg * b.F)); db.H = h;
-    }
-    d->blocks.push_back(db);
     ChirpGeom g{hp.Ua, hp.Ub, hp.Va, hp.Vb, hp.E, b.k0, b.n0, b.R, b.C, b.F};
     launch_chirps(g, db.wU, db.wV, 0);
     HK_LAUNCHED();
+    if (d->fp32) {
+      float2* h; HK_TRY(dalloc(d, &h, (size_t)b.nseg * b.F)); db.H = h;
+      float2* vt; HK_TRY(dalloc(d, &vt, (size_t)db.nl * b.C)); db.Vt = vt;
+      float2* ut; HK_TRY(dalloc(d, &ut, (size_t)db.nl * b.R)); db.Ut = ut;
+    } else {
+      double2* h; HK_TRY(dalloc(d, &h, (size_t)b.nseg * b.F)); db.H = h;
+      double2* vt; HK_TRY(dalloc(d, &vt, (size_t)db.nl * b.C)); db.Vt = vt;
+      double2* ut; HK_TRY(dalloc(d, &ut, (size_t)db.nl * b.R)); db.Ut = ut;
+    }
+    // FP32 plans: per stacked column, the power of two that brings max |colfun(n)| over the
+    // block to ~1 (its inverse goes to the row side)
+    std::vector<double> sc;
+    if (d->fp32) {
+      sc.assign(db.nl, 1.0);
+      for (int li = 0; li < db.nl; ++li) {
+        double mag = 0.0;
+        if (b.rank) {
+          for (int j = 0; j < b.P; ++j) mag = std::max(mag, std::abs(b.vcheb[(size_t)li * b.P + j]));
+        } else {
+          const ColSpec& csp = hp.cols[b.lcols[li]];
+          for (int64_t n : {b.n0, b.n1}) {
+            const int64_t i = n - 1;
+            cplx poly(0.0, 0.0);
+            for (int u = csp.nterm - 1; u >= 0; --u) poly = poly * hp.betan[i] + csp.G[u];
+            double m = std::abs(poly) * std::pow(hp.omt[i], csp.delta - 0.5);
+            if (csp.u1) m *= std::pow(hp.colpow[i], csp.u1);
+            mag = std::max(mag, m);
+          }
+        }
+        const int e = (mag > 0.0 && std::isfinite(mag)) ? -(int)std::lround(std::log2(mag)) : 0;
+        sc[li] = std::ldexp(1.0, e);
+      }
+    }
+    {
+      // inputs of the table kernels, freed once the tables are built
+      int* lmap = nullptr;
+      double2 *uc = nullptr, *vc = nullptr;
+      double* scd = nullptr;
+      if (b.rank) {
+        std::vector<double2> u(b.ucheb.size()), v(b.vcheb.size());
+        for (size_t j = 0; j < u.size(); ++j) u[j] = make_double2(b.ucheb[j].real(), b.ucheb[j].imag());
+        for (size_t j = 0; j < v.size(); ++j) v[j] = make_double2(b.vcheb[j].real(), b.vcheb[j].imag());
+        HK_TRY(upload(d, &uc, u.data(), u.size()));
+        HK_TRY(upload(d, &vc, v.data(), v.size()));
+      } else {
+        HK_TRY(upload(d, &lmap, b.lcols.data(), b.lcols.size()));
+      }
+      if (!sc.empty()) HK_TRY(upload(d, &scd, sc.data(), sc.size()));
+      BlockTabArgs ta{db.nl, b.k0, b.R, b.n0, b.C, lmap, b.rank ? b.P : 0, uc, vc,
+                      std::log((double)b.k0), std::log((double)b.k1), std::log((double)b.n0),
+                      std::log((double)b.n1), d->nodes, d->cols, db.wV, scd, db.Vt, db.Ut};
+      if (d->fp32) launch_block_tables<float2>(ta, 0);
+      else launch_block_tables<double2>(ta, 0);
+      HK_LAUNCHED();
+      if (cudaDeviceSynchronize() != cudaSuccess) return HANKEL_ECUDA;
+      dfree(d, &uc, b.ucheb.size());
+      dfree(d, &vc, b.vcheb.size());
+      dfree(d, &lmap, b.lcols.size());
+      dfree(d, &scd, sc.size());
+    }
+    d->blocks.push_back(db);
     SegGeom sg{hp.Ua, hp.Ub, hp.Vb, hp.E, b.k0, b.n0, b.R, b.C, 0, 0, 1, b.F};
     if (b.mode == kBlockRowSeg) { sg.Cc = b.S; sg.dn = b.S; sg.nseg = b.nseg; }
     if (b.mode == kBlockColSeg) { sg.Rr = b.S; sg.dk = b.S; sg.nseg = b.nseg; }
@@ -375,14 +388,7 @@ int dev_plan_create(hankel_plan_s* p) {
     else launch_scale_copy<double2>(res, (double2*)d->blocks.back().H, b.nseg * b.F, 1.0 / (double)b.F, 0);
     HK_LAUNCHED();
   }
-
-  if (d->fp32 && d->T) {
-    // FP32 plans run from the per-block FP32 tables alone
-    if (cudaDeviceSynchronize() != cudaSuccess) return HANKEL_ECUDA;
-    dfree(d, &d->T, (size_t)d->ncols * N);
-    dfree(d, &d->W, (size_t)d->ncols * N);
-    HK_TRY(dalloc(d, &d->cf, (size_t)hp.opt.max_nrhs * N));
-  }
+  if (d->fp32 && !hp.blocks.empty()) HK_TRY(dalloc(d, &d->cf, (size_t)hp.opt.max_nrhs * N));
 
   if (cudaDeviceSynchronize() != cudaSuccess) return HANKEL_ECUDA;
   return HANKEL_OK;
@@ -426,8 +432,8 @@ int run_block(DevicePlan* d, const DevBlock& db, const double* c, int64_t ldc, d
     const int64_t ninv = colseg ? (int64_t)nc * b.nseg : nc;  // inverse transforms
     {
       StageScope sc(d, HANKEL_STAGE_GEN, st, record);
-      GenArgs ga{A, b.F, b.C, b.n0, rowseg ? b.S : b.C, rowseg ? b.nseg : 1, nc, c0, db.nl, db.lmap, c, ldc,
-                 d->nodes, d->cols, db.wV, d->T, d->hpN, db.scale, d->cf, d->hpN, db.Tf};
+      GenArgs ga{A, b.F, b.C, b.n0, rowseg ? b.S : b.C, rowseg ? b.nseg : 1, nc, c0, db.nl, c, ldc, d->cf,
+                 d->hpN, db.Vt};
       launch_gen<C>(ga, st);
       HK_LAUNCHED();
       sc.done(1, 0.0, 0.0);
@@ -471,7 +477,7 @@ int run_block(DevicePlan* d, const DevBlock& db, const double* c, int64_t ldc, d
     {
       StageScope sc(d, HANKEL_STAGE_OUT, st, record);
       OutArgs oa{res2, b.F, b.R, b.k0, (rowseg ? b.S : b.C) - 1, colseg ? b.S : b.R, colseg ? b.nseg : 1,
-                 nc, c0, db.nl, db.lmap, f, ldf, d->nodes, d->cols, db.wU, d->W, d->hpN, db.iscale, db.Wf};
+                 nc, c0, db.nl, f, ldf, db.wU, db.Ut};
       launch_out<C>(oa, st);
       HK_LAUNCHED();
       sc.done(1, 0.0, 0.0);

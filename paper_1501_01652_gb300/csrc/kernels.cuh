@@ -42,8 +42,6 @@ struct DevColSpec {
   double2 G[kMaxU];
 };
 
-// Near-field work item: row k, columns n0..n1 (1-based, inclusive; empty when n0 > n1).
-// slot < 0: the item is the whole prefix of its row and writes f directly.
 // A near-field tile: rows k0..k0+31 (one lane each) over columns n0..n1, each lane stopping at
 // its row's prefix end. slot < 0: the tile covers the group's whole prefix and writes f;
 // otherwise lane j writes partial slot (slot + j * ntile + t).
@@ -63,6 +61,9 @@ struct ChirpGeom {
   int64_t Ua, Ub, Va, Vb, E, k0, n0, R, C, F;
 };
 
+// Column generation of one chunk of a block: stacked column li of right-hand side rhs is
+// g(n) = c_n * Vt[li][n - n0] (Vt: the block's column functions times its column chirp), cut
+// into segments of S columns each zero-padded to F points.
 struct GenArgs {
   void* A;            // [nc * nsegc][F] output columns (double2 or float2)
   int64_t F, C, n0;   // transform length, block columns, first column (1-based)
@@ -70,23 +71,15 @@ struct GenArgs {
   int64_t nsegc;      // column segments per stacked column (1 when not segmented)
   int nc;             // columns in this chunk
   int64_t c0;         // global index of the first column (rhs * ncols + li)
-  int ncols;          // stacked columns the block keeps per right-hand side
-  const int* lmap;    // li -> index of the stacked column in the plan's column list
-  const double* c;    // coefficients, c[rhs * ldc + n-1]
+  int ncols;          // stacked columns (transforms) of the block per right-hand side
+  const double* c;    // FP64 plans: coefficients, c[rhs * ldc + n-1]
   int64_t ldc;
-  NodeTables nodes;
-  const DevColSpec* cols;
-  const double2* wV;  // column chirp of the block
-  const double2* T;   // optional [ncols][N] column factors times the column chirp (nullptr: computed here)
-  int64_t N;
-  const double* scale;  // optional per stacked column: factor applied before rounding to FP32 (nullptr: 1)
-  // FP32 plans with factor tables: coefficients rounded to FP32, cf[rhs * ldcf + n-1], and the
-  // block's [ncols][C] column factors times the column chirp and scale, in FP32 (nullptr: unused)
-  const float* cf;
+  const float* cf;    // FP32 plans: coefficients rounded to FP32, cf[rhs * ldcf + n-1]
   int64_t ldcf;
-  const float2* Tf;
+  const void* Vt;     // [ncols][C] block column table (double2 or float2)
 };
 
+// Row accumulation of one chunk: f_k += Re[ w_U(k) sum_li Ut[li][k - k0] y_li(k) ].
 struct OutArgs {
   const void* Y;      // [nc * nsegr][F] inverse-transformed columns (double2 or float2)
   int64_t F, R, k0;
@@ -95,38 +88,35 @@ struct OutArgs {
   int64_t nsegr;      // row segments per stacked column
   int nc;
   int64_t c0;
-  int ncols;          // stacked columns the block keeps per right-hand side
-  const int* lmap;    // li -> index of the stacked column in the plan's column list
+  int ncols;          // stacked columns (transforms) of the block per right-hand side
   double* f;          // f[rhs * ldf + k-1] += ...
   int64_t ldf;
-  NodeTables nodes;
-  const DevColSpec* cols;
   const double2* wU;  // row chirp of the block
-  const double* W;    // optional [ncols][N] row factors (nullptr: computed here)
-  int64_t N;
-  const double* iscale;  // optional per stacked column: inverse of GenArgs::scale (nullptr: 1)
-  const float* Wf;       // FP32 plans with factor tables: the block's [ncols][R] row factors times iscale
+  const void* Ut;     // [ncols][R] block row table (double2 or float2)
 };
 
-// Plan-time tables of the factors that do not depend on c:
-// T[l][n-1] = colpow^u1 omt^(delta-1/2) poly_l(beta) exp(i pi V_n^2/(2E)),
-// W[l][k-1] = rowpert^u1 rowvar^(delta-1/2).
-struct TabArgs {
-  double2* T;
-  double* W;
-  int64_t N;
-  int ncols;
+// Plan-time block tables (computed in FP64, stored in the plan precision). For a block with a
+// low-rank form, column li is V_li (Chebyshev interpolation of vcheb[li] in log n) and row li is
+// U_li (of ucheb[li] in log k); otherwise column li is the stacked column lmap[li]:
+// colpow^u1 omt^(delta-1/2) poly(beta) and row li its rowpert^u1 rowvar^(delta-1/2).
+// Vt[li][np] = V_li(n0+np) wV[np] scale[li], Ut[li][kp] = U_li(k0+kp) / scale[li].
+struct BlockTabArgs {
+  int nl;
+  int64_t k0, R, n0, C;
+  const int* lmap;       // direct form: the stacked column of each li
+  int P;                 // low-rank form: Chebyshev points (0: direct form)
+  const double2* ucheb;  // [nl][P]
+  const double2* vcheb;  // [nl][P]
+  double lk0, lk1, ln0, ln1;  // log k0, log k1, log n0, log n1
   NodeTables nodes;
   const DevColSpec* cols;
-  int64_t Va, Vb, E;
+  const double2* wV;
+  const double* scale;   // per li (nullptr: 1)
+  void* Vt;
+  void* Ut;
 };
-void launch_build_tables(const TabArgs& a, cudaStream_t st);
-// Per-block FP32 factor tables (FP32 plans), for the block's kept columns l = lmap[li]:
-// Tf[li][np] = T[l][n0-1+np] scale[l] (np < C), Wf[li][kp] = W[l][k0-1+kp] iscale[l] (kp < R),
-// each rounded to FP32 once.
-void launch_block_tables_f32(const double2* T, const double* W, int64_t N, int nl, const int* lmap, int64_t n0,
-                             int64_t C, int64_t k0, int64_t R, const double* scale, const double* iscale, float2* Tf,
-                             float* Wf, cudaStream_t st);
+template <class C>
+void launch_block_tables(const BlockTabArgs& a, cudaStream_t st);
 // out[r * ldo + i] = scale * v[i] * x[r * ldx + i] for r < nrhs, i < N (out may be x).
 void launch_diag_scale(const double* x, int64_t ldx, const double* v, double scale, double* out, int64_t ldo,
                        int64_t N, int nrhs, cudaStream_t st);

@@ -36,6 +36,13 @@ struct Block {
   int64_t nseg;   // number of segments (1 for full blocks)
   std::vector<int> lcols;  // stacked columns this block keeps (indices into HostPlan::cols, ascending)
   double dropped = 0.0;    // bound on |entry change| from the stacked columns it leaves out
+  // Low-rank form of the block's kernel K(k, n) = sum_{l in lcols} rowfun_l(k) colfun_l(n):
+  // K ~ sum_{a < rank} U_a(k) V_a(n), with U_a and V_a given by their values at P Chebyshev
+  // points in log k and log n (rank = 0: the block transforms its kept columns).
+  int rank = 0;
+  int P = 0;
+  std::vector<cplx> ucheb, vcheb;  // [rank][P]
+  double lowrank_err = 0.0;        // largest error of the low-rank form on the validation entries
 };
 
 // One stacked column of a block: the row function rowpert(k)^u1 rowvar(k)^(delta-1/2)
@@ -86,6 +93,11 @@ int build_host_plan(const hankel_options& opt, HostPlan& hp);
 int choose_params(const hankel_options& opt, HostPlan& hp);
 // Host value of the plan's representation of entry (k, n), 1-based.
 double host_entry(const HostPlan& hp, int64_t k, int64_t n, int* is_far);
+// Barycentric interpolation at x in [-1, 1] of values at the P Chebyshev points (first kind)
+// cos(pi (i + 1/2) / P).
+cplx cheb_interp(const cplx* vals, int P, double x);
+// Position of index k of the range [k0, k1] on [-1, 1], linear in log k.
+double log_coord(double k, int64_t k0, int64_t k1);
 // The far-field expansion of entry (k, n) over the listed stacked columns (all when null),
 // wherever (k, n) lies.
 double expansion_entry(const HostPlan& hp, int64_t k, int64_t n, const std::vector<int>* lcols);

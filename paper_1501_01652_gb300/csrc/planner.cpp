@@ -148,7 +148,7 @@ double factorial(int n) {
 // Large roots: from Eq. (4) with lam = 0, J_0 ~ sqrt(2/(pi z)) (P cos mu - Q sin mu) and
 // mu = (n-1/2)pi + b, so J_0 = 0 <=> tan b = -Q(z)/P(z), z = (n-1/4)pi + b. The map
 // b -> atan(-Q/P) contracts by ~1/(8 z^2); its fixed point keeps b's full relative accuracy.
-double root_offset_large(int64_t n) {
+double root_offset_large(double n) {
   double beta = (n - 0.25) * kPi;
   double b = 0.125 / beta;
   double a[80];
@@ -734,6 +734,155 @@ void select_columns(HostPlan& hp) {
   for (Block& b : hp.blocks) block_columns(hp, nr, b, budget);
 }
 
+// ---------------------------------------------------------------------------
+// Low-rank form of a block (beyond the paper). Within a far block the kernel
+// K(k, n) = sum_l rowfun_l(k) colfun_l(n) -- the smooth envelope that multiplies the chirp
+// exp(i theta~_kn) -- is an analytic function of log k and log n of small numerical rank: its
+// singular values fall by orders of magnitude per term, because the Hankel tail and the
+// perturbation terms are smooth in z = r omega. It is sampled on a P x P Chebyshev grid in
+// (log k, log n), using the node functions at real k and n (their closed forms, and b(n) from
+// the root-offset fixed point), and factored there by cross approximation with complete
+// pivoting (Gaussian elimination stopped when the largest residual is below tol):
+// K_grid ~ sum_a u_a v_a^T. U_a and V_a interpolate u_a and v_a at any k and n. The form is
+// kept when it is exact to kLowRankFrac * eps on a validation set of entries of the block
+// (its corners, edges and pseudo-random entries, against the expansion at the integer nodes)
+// and has fewer terms than the block's kept columns; the block then runs rank transforms per
+// vector instead of lcols.size(). Entries carry at most eps (expansion) + eps (dropped
+// columns) + kLowRankFrac * eps (low-rank form).
+// ---------------------------------------------------------------------------
+constexpr double kLowRankFrac = 0.5;
+constexpr int kChebP0 = 32, kChebPMax = 64;
+
+void node_row(const HostPlan& hp, double k, double* rv, double* rp) {
+  const int64_t N = hp.opt.N;
+  if (hp.opt.task == HANKEL_DHT) {
+    const double bN1 = hp.b[N], jN1 = (N + 0.75) * kPi + bN1;
+    *rv = (4.0 * k - 1.0) / (4.0 * N + 3.0);
+    *rp = (root_offset_large(k) * (N + 0.75) - bN1 * (k - 0.25)) / (jN1 * (N + 0.75));
+  } else {
+    *rv = hp.opt.grid == HANKEL_GRID_UNIT ? (k - 1.0) / (double)(N - 1) : k / (double)N;
+    *rp = 0.0;
+  }
+}
+
+void node_col(const HostPlan& hp, double n, double* om, double* bt, double* cp) {
+  if (hp.opt.task == HANKEL_SCHLOMILCH) {
+    *om = (n + hp.opt.gamma) * kPi;
+    *bt = 0.0;
+    *cp = 1.0;
+  } else {
+    const double w = (n - 0.25) * kPi, bn = root_offset_large(n);
+    *om = w;
+    *bt = bn / w;
+    *cp = hp.opt.task == HANKEL_DHT ? w + bn : 1.0;
+  }
+}
+
+cplx kernel_sum(const HostPlan& hp, const std::vector<int>& lcols, double rv, double rp, double om, double bt,
+                double cp) {
+  cplx acc(0.0, 0.0);
+  for (int l : lcols) {
+    const ColSpec& cs = hp.cols[l];
+    cplx poly(0.0, 0.0);
+    for (int u = cs.nterm - 1; u >= 0; --u) poly = poly * bt + cs.G[u];
+    const double row = std::pow(rv, cs.delta - 0.5) * (cs.u1 ? std::pow(rp, cs.u1) : 1.0);
+    const double col = std::pow(om, cs.delta - 0.5) * (cs.u1 ? std::pow(cp, cs.u1) : 1.0);
+    acc += row * col * poly;
+  }
+  return acc;
+}
+
+double cheb_node(int i, int P) { return std::cos(kPi * (i + 0.5) / P); }
+
+bool try_lowrank(const HostPlan& hp, Block& b, int P, double tol) {
+  const int nl = (int)b.lcols.size();
+  const double lk0 = std::log((double)b.k0), lk1 = std::log((double)b.k1);
+  const double ln0 = std::log((double)b.n0), ln1 = std::log((double)b.n1);
+  std::vector<double> rv(P), rp(P), om(P), bt(P), cp(P);
+  for (int i = 0; i < P; ++i) {
+    const double x = cheb_node(i, P);
+    node_row(hp, std::exp(0.5 * (lk0 + lk1) + 0.5 * (lk1 - lk0) * x), &rv[i], &rp[i]);
+    node_col(hp, std::exp(0.5 * (ln0 + ln1) + 0.5 * (ln1 - ln0) * x), &om[i], &bt[i], &cp[i]);
+  }
+  std::vector<cplx> R((size_t)P * P);
+  for (int i = 0; i < P; ++i)
+    for (int j = 0; j < P; ++j) R[(size_t)i * P + j] = kernel_sum(hp, b.lcols, rv[i], rp[i], om[j], bt[j], cp[j]);
+  // cross approximation with complete pivoting
+  std::vector<cplx> u, v;
+  int rank = 0;
+  for (;;) {
+    size_t best = 0;
+    double m = -1.0;
+    for (size_t e = 0; e < R.size(); ++e)
+      if (std::abs(R[e]) > m) { m = std::abs(R[e]); best = e; }
+    if (m <= tol) break;
+    if (rank + 1 >= nl) return false;  // no fewer terms than the kept columns
+    const int is = (int)(best / P), js = (int)(best % P);
+    const cplx piv = R[best];
+    std::vector<cplx> ua(P), va(P);
+    for (int i = 0; i < P; ++i) ua[i] = R[(size_t)i * P + js] / piv;
+    for (int j = 0; j < P; ++j) va[j] = R[(size_t)is * P + j];
+    for (int i = 0; i < P; ++i)
+      for (int j = 0; j < P; ++j) R[(size_t)i * P + j] -= ua[i] * va[j];
+    u.insert(u.end(), ua.begin(), ua.end());
+    v.insert(v.end(), va.begin(), va.end());
+    ++rank;
+  }
+  if (rank == 0) return false;
+  // validation against the expansion at the integer nodes
+  auto approx = [&](int64_t k, int64_t n) {
+    const double x = log_coord((double)k, b.k0, b.k1), y = log_coord((double)n, b.n0, b.n1);
+    cplx acc(0.0, 0.0);
+    for (int a = 0; a < rank; ++a) acc += cheb_interp(&u[(size_t)a * P], P, x) * cheb_interp(&v[(size_t)a * P], P, y);
+    return acc;
+  };
+  auto exact = [&](int64_t k, int64_t n) {
+    return kernel_sum(hp, b.lcols, hp.rowvar[k - 1], hp.rowpert[k - 1], hp.omt[n - 1], hp.betan[n - 1],
+                      hp.colpow[n - 1]);
+  };
+  std::vector<std::pair<int64_t, int64_t>> pts;
+  const int64_t ks[3] = {b.k0, (b.k0 + b.k1) / 2, b.k1}, ns[3] = {b.n0, (b.n0 + b.n1) / 2, b.n1};
+  for (int64_t k : ks)
+    for (int64_t n : ns) pts.push_back({k, n});
+  uint64_t st = 0x9e3779b97f4a7c15ull ^ (uint64_t)(b.k0 * 1315423911u + b.n0);
+  auto rnd = [&]() {
+    st = st * 6364136223846793005ull + 1442695040888963407ull;
+    return (double)(st >> 11) * (1.0 / 9007199254740992.0);
+  };
+  for (int t = 0; t < 1536; ++t) {
+    double fk = rnd(), fn = rnd();
+    if (t & 1) {  // log-uniform: dense near the block's small-z corner
+      fk = std::exp(lk0 + (lk1 - lk0) * fk);
+      fn = std::exp(ln0 + (ln1 - ln0) * fn);
+    } else {
+      fk = b.k0 + (b.k1 - b.k0) * fk;
+      fn = b.n0 + (b.n1 - b.n0) * fn;
+    }
+    pts.push_back({std::min(b.k1, std::max(b.k0, (int64_t)std::llround(fk))),
+                   std::min(b.n1, std::max(b.n0, (int64_t)std::llround(fn)))});
+  }
+  double err = 0.0;
+  for (const auto& q : pts) err = std::max(err, std::abs(approx(q.first, q.second) - exact(q.first, q.second)));
+  if (err > kLowRankFrac * hp.opt.eps) return false;
+  b.rank = rank;
+  b.P = P;
+  b.ucheb = u;
+  b.vcheb = v;
+  b.lowrank_err = err;
+  return true;
+}
+
+void compress_blocks(HostPlan& hp) {
+  for (Block& b : hp.blocks) {
+    b.rank = 0;
+    if (hp.opt.flags & (HANKEL_FLAG_NO_LOWRANK | HANKEL_FLAG_ALL_COLUMNS)) continue;
+    if (b.R < 8 || b.C < 8 || b.lcols.size() < 3) continue;
+    double tol = 0.15 * hp.opt.eps;
+    for (int P = kChebP0; P <= kChebPMax; P += 16, tol *= 0.25)
+      if (try_lowrank(hp, b, P, tol)) break;
+  }
+}
+
 // Taylor polynomials of J_nu about z_c = i + 1/2 on [i, i+1). The coefficients follow from
 // the Neumann addition formula (Eq. 8) with each J_s(delta) expanded in its Taylor series
 // (Eq. 6) -- the same rearrangement as Section 5.1 with K and T unbounded:
@@ -777,6 +926,7 @@ int build_host_plan(const hankel_options& opt, HostPlan& hp) {
   if (hp.nend.empty()) return HANKEL_EINVAL;  // partition invariant violated
   build_columns(hp);
   select_columns(hp);
+  compress_blocks(hp);
   build_jtable(hp);
   return HANKEL_OK;
 }
@@ -815,6 +965,25 @@ double expansion_entry(const HostPlan& hp, int64_t k, int64_t n, const std::vect
   return (ph * acc).real();
 }
 
+double log_coord(double k, int64_t k0, int64_t k1) {
+  if (k1 <= k0) return 0.0;
+  const double l0 = std::log((double)k0), l1 = std::log((double)k1);
+  return (2.0 * std::log(k) - l0 - l1) / (l1 - l0);
+}
+
+cplx cheb_interp(const cplx* vals, int P, double x) {
+  cplx num(0.0, 0.0);
+  double den = 0.0;
+  for (int i = 0; i < P; ++i) {
+    const double d = x - cheb_node(i, P);
+    if (d == 0.0) return vals[i];
+    const double w = ((i & 1) ? -1.0 : 1.0) * std::sin(kPi * (i + 0.5) / P) / d;
+    num += w * vals[i];
+    den += w;
+  }
+  return num / den;
+}
+
 double host_entry(const HostPlan& hp, int64_t k, int64_t n, int* is_far) {
   *is_far = 0;
   if (n > hp.nend[k - 1]) {
@@ -822,7 +991,18 @@ double host_entry(const HostPlan& hp, int64_t k, int64_t n, int* is_far) {
     const Block* blk = nullptr;
     for (const Block& b : hp.blocks)
       if (k >= b.k0 && k <= b.k1 && n >= b.n0 && n <= b.n1) blk = &b;
-    return expansion_entry(hp, k, n, &blk->lcols);
+    if (blk->rank == 0) return expansion_entry(hp, k, n, &blk->lcols);
+    // low-rank form: Re[exp(i theta~_kn) sum_a U_a(k) V_a(n)]
+    __int128 U = (__int128)hp.Ua * k + hp.Ub, V = (__int128)hp.Va * n + hp.Vb;
+    __int128 num = (U * V) % ((__int128)2 * hp.E);
+    double s, c;
+    sincospi_ratio((int64_t)num, hp.E, &s, &c);
+    const double x = log_coord((double)k, blk->k0, blk->k1), y = log_coord((double)n, blk->n0, blk->n1);
+    cplx acc(0.0, 0.0);
+    for (int a = 0; a < blk->rank; ++a)
+      acc += cheb_interp(&blk->ucheb[(size_t)a * blk->P], blk->P, x) *
+             cheb_interp(&blk->vcheb[(size_t)a * blk->P], blk->P, y);
+    return (cplx(c, s) * acc).real();
   }
   return table_j(hp, hp.r_true[k - 1] * hp.om_true[n - 1]);
 }

@@ -134,23 +134,24 @@ def test_fp32_workload_size_sampled_rows(eps):
     ("dht", 0, 1e-15, "normal"), ("dht", 0, 1e-4, "normal"),
 ])
 def test_largest_workload_size_sampled_rows(task, nu, eps, kind):
-    # N = 2^22, the largest size of the workload table; at eps = 1e-15 the DHT's factor tables
-    # exceed their limit and the factors are computed per use
+    # N = 2^22, the largest size of the workload table
     N = 2 ** 22
     c = coefficients(kind, N, 1, 4 * 1000 + 22)
     rows = sample_rows(N, 40, 23)
     _check(task, nu, N, eps, c, rows=rows)
 
 
-@pytest.mark.parametrize("tables", [True, False])
-def test_factor_tables_on_and_off(tables):
-    # column/row factors from plan-time device tables or computed per use give the same bar
+@pytest.mark.parametrize("lowrank", [True, False])
+def test_lowrank_forms_on_and_off(lowrank):
+    # blocks run their low-rank forms or their kept stacked columns; both meet the bar
     N = 6000
     c = coefficients("normal", N, 2, 5600)
-    _check("dht", 0, N, 1e-15, c, tables=tables)
-    _check("fourier_bessel", 0, N, 1e-8, c, tables=tables)
-    _check("dht", 0, N, 1e-4, c, tables=tables, precision="fp32")
-    _check("schlomilch", 2, N, 1e-5, c, tables=tables, precision="fp32")
+    _check("dht", 0, N, 1e-15, c, lowrank=lowrank)
+    _check("fourier_bessel", 0, N, 1e-8, c, lowrank=lowrank)
+    _check("dht", 0, N, 1e-4, c, lowrank=lowrank, precision="fp32")
+    _check("schlomilch", 2, N, 1e-5, c, lowrank=lowrank, precision="fp32")
+    plan = hk.Plan("dht", 0, N, 1e-15, lowrank=lowrank, host_only=True)
+    assert any(b["lowrank"] for b in plan.blocks()) == lowrank
 
 
 @pytest.mark.parametrize("eps", [1e-15, 1e-8])

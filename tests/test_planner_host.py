@@ -140,7 +140,8 @@ def test_far_blocks_satisfy_criterion(case):
 def test_entries_against_oracle(case):
     # The plan's value for each entry (near-field evaluator or far-field expansion with every
     # stacked column) is within eps of J_nu(r_k omega_n) (Sections 3-6: each expansion is used
-    # only where it is eps-accurate); with the columns each block keeps it is within 2 eps.
+    # only where it is eps-accurate); with the columns each block keeps and its low-rank form
+    # it is within 2.5 eps.
     task, nu, N, eps, grid = case
     p = hk.Plan(task, nu, N, eps, grid=grid, host_only=True, prune=False)
     pk = hk.Plan(task, nu, N, eps, grid=grid, host_only=True)
@@ -155,7 +156,7 @@ def test_entries_against_oracle(case):
             tol = eps if far else near_tol
             assert abs(v - ref[n - 1]) <= tol, (k, n, far, v, ref[n - 1])
             vk, fk = pk.entry(k, n)
-            assert fk == far and abs(vk - ref[n - 1]) <= (2 * eps if far else near_tol), (k, n, vk)
+            assert fk == far and abs(vk - ref[n - 1]) <= (2.5 * eps if far else near_tol), (k, n, vk)
 
 
 @pytest.mark.parametrize("case", [c for c in CASES if c[0] != "schlomilch"] + [("dht", 0, 20000, 1e-15, "unit")],
@@ -165,7 +166,7 @@ def test_kept_columns_change_entries_within_their_bound(case):
     # eps split over the blocks of one row; the plan's far entries move by no more than that
     # (plus rounding) against the plan that keeps every column.
     task, nu, N, eps, grid = case
-    p = hk.Plan(task, nu, N, eps, grid=grid, host_only=True)
+    p = hk.Plan(task, nu, N, eps, grid=grid, host_only=True, lowrank=False)
     q = hk.Plan(task, nu, N, eps, grid=grid, host_only=True, prune=False)
     info, blocks = p.info, p.blocks()
     assert all(b["ncols"] == info["ncols"] for b in q.blocks())
@@ -194,14 +195,43 @@ def _fft_work(plan):
 def test_column_selection_shrinks_the_workload_transforms():
     # DHT-0 at N = 2^20: rows and columns far from the near field barely feel the perturbations
     # e_k omega_n and r b_n, so most of the 290 (eps = 1e-15) or 90 (1e-8) stacked columns go;
-    # cutting the blocks further from the near field drops more
+    # cutting the blocks further from the near field drops more, and the blocks' low-rank forms
+    # need fewer terms still
     for eps, full in [(1e-15, 290), (1e-8, 90)]:
-        p = hk.Plan("dht", 0, 2 ** 20, eps, host_only=True, refine=False)
-        r = hk.Plan("dht", 0, 2 ** 20, eps, host_only=True, max_nrhs=16)
+        p = hk.Plan("dht", 0, 2 ** 20, eps, host_only=True, refine=False, lowrank=False)
+        r = hk.Plan("dht", 0, 2 ** 20, eps, host_only=True, max_nrhs=16, lowrank=False)
+        lr = hk.Plan("dht", 0, 2 ** 20, eps, host_only=True, max_nrhs=16)
         q = hk.Plan("dht", 0, 2 ** 20, eps, host_only=True, prune=False)
         assert p.info["ncols"] == full and all(b["ncols"] == full for b in q.blocks())
         assert _fft_work(p) < 0.2 * _fft_work(q)
         assert _fft_work(r) < 0.7 * _fft_work(p)
+        assert _fft_work(lr) < 0.6 * _fft_work(r)
+        assert all(b["kept"] == rb["ncols"] for b, rb in zip(lr.blocks(), r.blocks()))
+
+
+@pytest.mark.parametrize("task,nu,N,eps", [("dht", 0, 20000, 1e-15), ("dht", 0, 2 ** 17, 1e-8),
+                                           ("fourier_bessel", 0, 20000, 1e-15), ("schlomilch", 1, 20000, 1e-15),
+                                           ("dht", 0, 20000, 1e-4)])
+def test_lowrank_forms_match_the_kept_columns(task, nu, N, eps):
+    # a block's low-rank form (Chebyshev interpolation in log k, log n of a cross approximation)
+    # agrees with the sum over its kept columns to eps/2 at entries other than the ones it was
+    # validated on
+    p = hk.Plan(task, nu, N, eps, host_only=True)
+    q = hk.Plan(task, nu, N, eps, host_only=True, lowrank=False)
+    blocks = p.blocks()
+    assert sum(b["lowrank"] for b in blocks) >= len(blocks) // 2
+    assert [(b["k0"], b["n0"]) for b in blocks] == [(b["k0"], b["n0"]) for b in q.blocks()]
+    rng = np.random.default_rng(19)
+    for b in blocks:
+        if not b["lowrank"]:
+            continue
+        assert b["ncols"] < b["kept"] and b["lowrank_err"] <= 0.5 * eps
+        ks = rng.integers(b["k0"], b["k1"] + 1, 40)
+        ns = rng.integers(b["n0"], b["n1"] + 1, 40)
+        for k, n in zip(ks, ns):
+            vp, _ = p.entry(k, n)
+            vq, _ = q.entry(k, n)
+            assert abs(vp - vq) <= 0.5 * eps + 4e-16, (k, n, vp, vq, b)
 
 
 @pytest.mark.parametrize("task,nu,N,eps,grid", [("dht", 0, 300, 1e-15, "unit"), ("schlomilch", 0, 300, 1e-8, "paper"),
