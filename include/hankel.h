@@ -315,9 +315,11 @@ int hankel_server_options_default(hankel_server_options* o);
 int hankel_server_create(hankel_server_t* out, const hankel_server_options* o);
 
 /* Queue one request: nrhs vectors of N coefficients in host array c (row r at c + r*N) and the
- * host output array f (same layout). Both must stay valid until the request completes. *ticket
- * receives the request's id. Never blocks on the GPU. Errors: EINVAL (arguments), EUNSUPPORTED
- * (a plan could not be built for these parameters, reported at completion as a failed request). */
+ * host output array f (same layout). Both must stay valid until the request completes. Page-locked
+ * arrays (cudaMallocHost, cudaHostRegister) are copied to and from the device directly; pageable
+ * ones through the server's page-locked staging buffers. *ticket receives the request's id.
+ * Never blocks on the GPU. Errors: EINVAL (arguments), EUNSUPPORTED (a plan could not be built
+ * for these parameters, reported at completion as a failed request). */
 int hankel_server_submit(hankel_server_t s, int task, int nu, int64_t N, double eps, const double* c, double* f,
                          int nrhs, int64_t* ticket);
 

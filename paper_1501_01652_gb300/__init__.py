@@ -224,11 +224,17 @@ class Server:
         _lib.check(self._lib.hankel_server_create(ctypes.byref(self._h), ctypes.byref(o)), "hankel_server_create")
         self._live = {}  # ticket -> (c, f) kept alive until completion
 
-    def submit(self, task, nu, N, eps, c):
-        """Queue c ((N,) or (nrhs, N) float64); returns (ticket, f) with f filled on completion."""
+    def submit(self, task, nu, N, eps, c, f=None):
+        """Queue c ((N,) or (nrhs, N) float64); returns (ticket, f) with f filled on completion.
+        f: optional output array shaped like c (page-locked arrays skip the staging copies)."""
         c = np.ascontiguousarray(c, dtype=np.float64)
         c2 = c.reshape(1, -1) if c.ndim == 1 else c
-        f = np.empty_like(c2)
+        if f is None:
+            f = np.empty_like(c2)
+        else:
+            if f.dtype != np.float64 or not f.flags["C_CONTIGUOUS"] or f.size != c2.size:
+                raise ValueError("f must be a contiguous float64 array shaped like c")
+            f = f.reshape(c2.shape)
         t = ctypes.c_int64()
         dp = ctypes.POINTER(ctypes.c_double)
         _lib.check(self._lib.hankel_server_submit(self._h, TASKS[task], int(nu), int(N), float(eps),

@@ -658,82 +658,6 @@ void block_columns(const HostPlan& hp, const NodeRanges& nr, Block& b, double bu
   if (b.lcols.empty()) b.lcols.push_back(bound.back().second);  // every block keeps one column
 }
 
-// Subdivision of the far blocks (an addition to the partition of Eq. 19). The blocks of
-// Eq. (19) touch the near field at one corner, where z~ ~ s and every stacked column is
-// needed, but stretch to z~ ~ N: away from that corner the Hankel tail and the perturbation
-// terms shrink and far fewer columns pass the drop bound. A block is cut in two, across its
-// rows or its columns at one of a few geometric points, when the cut lowers the estimated
-// work (kept columns x column_cost, plus a fixed cost per block execution spread over
-// max_nrhs vectors); the halves are refined again. The union of the blocks, hence the near
-// set, does not change.
-constexpr double kBlockLaunchOps = 1e7;  // FP64-operation equivalent of the launches of one block
-constexpr int64_t kMinSide = 64;
-
-double block_work(const HostPlan& hp, const Block& b) {
-  return (double)b.lcols.size() * column_cost(b) + kBlockLaunchOps / hp.opt.max_nrhs;
-}
-
-void refine(const HostPlan& hp, const NodeRanges& nr, Block b, double budget, int depth, std::vector<Block>& out) {
-  block_columns(hp, nr, b, budget);
-  const double w0 = block_work(hp, b);
-  double best = 0.97 * w0;
-  Block bl1, bl2;
-  bool found = false;
-  auto consider = [&](Block c1, Block c2) {
-    block_columns(hp, nr, c1, budget);
-    block_columns(hp, nr, c2, budget);
-    const double w = block_work(hp, c1) + block_work(hp, c2);
-    if (w < best) {
-      best = w;
-      bl1 = c1;
-      bl2 = c2;
-      found = true;
-    }
-  };
-  if (depth < 24) {
-    for (double t : {0.25, 0.5, 0.75}) {
-      if (b.R >= 2 * kMinSide) {
-        int64_t km = (int64_t)std::llround(std::exp((1 - t) * std::log((double)b.k0) + t * std::log((double)b.k1)));
-        km = std::min(std::max(km, b.k0 + kMinSide), b.k1 - kMinSide + 1);
-        consider(make_block(hp, b.k0, km - 1, b.n0, b.n1), make_block(hp, km, b.k1, b.n0, b.n1));
-      }
-      if (b.C >= 2 * kMinSide) {
-        int64_t nm = (int64_t)std::llround(std::exp((1 - t) * std::log((double)b.n0) + t * std::log((double)b.n1)));
-        nm = std::min(std::max(nm, b.n0 + kMinSide), b.n1 - kMinSide + 1);
-        consider(make_block(hp, b.k0, b.k1, b.n0, nm - 1), make_block(hp, b.k0, b.k1, nm, b.n1));
-      }
-    }
-  }
-  if (!found) {
-    out.push_back(b);
-    return;
-  }
-  refine(hp, nr, bl1, budget, depth + 1, out);
-  refine(hp, nr, bl2, budget, depth + 1, out);
-}
-
-void select_columns(HostPlan& hp) {
-  const int64_t N = hp.opt.N;
-  NodeRanges nr(hp);
-  double budget = kDropFrac * hp.opt.eps / kRowBlocks;
-  const bool subdivide = !(hp.opt.flags & (HANKEL_FLAG_NO_REFINE | HANKEL_FLAG_ALL_COLUMNS));
-  if (subdivide) {
-    std::vector<Block> out;
-    for (const Block& b : hp.blocks) refine(hp, nr, b, budget, 0, out);
-    hp.blocks = out;
-  }
-  // blocks meeting in one row; the budget must cover all of them
-  std::vector<int> per_row(N + 2, 0);
-  for (const Block& b : hp.blocks) {
-    per_row[b.k0] += 1;
-    per_row[b.k1 + 1] -= 1;
-  }
-  int maxrow = 1, run = 0;
-  for (int64_t k = 1; k <= N; ++k) maxrow = std::max(maxrow, run += per_row[k]);
-  budget = kDropFrac * hp.opt.eps / std::max(maxrow, subdivide ? kRowBlocks : 1);
-  for (Block& b : hp.blocks) block_columns(hp, nr, b, budget);
-}
-
 // ---------------------------------------------------------------------------
 // Low-rank form of a block (beyond the paper). Within a far block the kernel
 // K(k, n) = sum_l rowfun_l(k) colfun_l(n) -- the smooth envelope that multiplies the chirp
@@ -872,6 +796,41 @@ bool try_lowrank(const HostPlan& hp, Block& b, int P, double tol) {
   return true;
 }
 
+// Terms of the block's low-rank form on a coarse grid (no validation): the cost estimate of
+// the subdivision. Returns the kept columns when the form would not be shorter.
+int estimate_rank(const HostPlan& hp, const Block& b) {
+  const int nl = (int)b.lcols.size();
+  if (b.R < 8 || b.C < 8 || nl < 3) return nl;
+  constexpr int P = 24;
+  const double lk0 = std::log((double)b.k0), lk1 = std::log((double)b.k1);
+  const double ln0 = std::log((double)b.n0), ln1 = std::log((double)b.n1);
+  double rv[P], rp[P], om[P], bt[P], cp[P];
+  for (int i = 0; i < P; ++i) {
+    const double x = cheb_node(i, P);
+    node_row(hp, std::exp(0.5 * (lk0 + lk1) + 0.5 * (lk1 - lk0) * x), &rv[i], &rp[i]);
+    node_col(hp, std::exp(0.5 * (ln0 + ln1) + 0.5 * (ln1 - ln0) * x), &om[i], &bt[i], &cp[i]);
+  }
+  std::vector<cplx> R((size_t)P * P);
+  for (int i = 0; i < P; ++i)
+    for (int j = 0; j < P; ++j) R[(size_t)i * P + j] = kernel_sum(hp, b.lcols, rv[i], rp[i], om[j], bt[j], cp[j]);
+  const double tol = 0.15 * hp.opt.eps;
+  for (int rank = 0; rank < nl; ++rank) {
+    size_t best = 0;
+    double m = -1.0;
+    for (size_t e = 0; e < R.size(); ++e)
+      if (std::abs(R[e]) > m) { m = std::abs(R[e]); best = e; }
+    if (m <= tol) return std::max(rank, 1);
+    const int is = (int)(best / P), js = (int)(best % P);
+    const cplx piv = R[best];
+    for (int i = 0; i < P; ++i) {
+      const cplx ui = R[(size_t)i * P + js] / piv;
+      for (int j = 0; j < P; ++j) R[(size_t)i * P + j] -= ui * R[(size_t)is * P + j] * (i == is ? 0.0 : 1.0);
+    }
+    for (int j = 0; j < P; ++j) R[(size_t)is * P + j] = 0.0;
+  }
+  return nl;
+}
+
 void compress_blocks(HostPlan& hp) {
   for (Block& b : hp.blocks) {
     b.rank = 0;
@@ -881,6 +840,85 @@ void compress_blocks(HostPlan& hp) {
     for (int P = kChebP0; P <= kChebPMax; P += 16, tol *= 0.25)
       if (try_lowrank(hp, b, P, tol)) break;
   }
+}
+
+// Subdivision of the far blocks (an addition to the partition of Eq. 19). The blocks of
+// Eq. (19) touch the near field at one corner, where z~ ~ s and every stacked column is
+// needed, but stretch to z~ ~ N: away from that corner the Hankel tail and the perturbation
+// terms shrink and far fewer columns pass the drop bound. A block is cut in two, across its
+// rows or its columns at one of a few geometric points, when the cut lowers the estimated
+// work (transforms x column_cost, plus a fixed cost per block execution spread over max_nrhs
+// vectors; transforms = the low-rank form's terms on a coarse grid, or the kept columns when
+// low-rank forms are off); the halves are refined again. The union of the blocks, hence the
+// near set, does not change.
+constexpr double kBlockLaunchOps = 1e7;  // FP64-operation equivalent of the launches of one block
+constexpr int64_t kMinSide = 64;
+
+double block_work(const HostPlan& hp, const Block& b) {
+  const bool lowrank = !(hp.opt.flags & (HANKEL_FLAG_NO_LOWRANK | HANKEL_FLAG_ALL_COLUMNS));
+  const int terms = lowrank ? estimate_rank(hp, b) : (int)b.lcols.size();
+  return (double)terms * column_cost(b) + kBlockLaunchOps / hp.opt.max_nrhs;
+}
+
+void refine(const HostPlan& hp, const NodeRanges& nr, Block b, double budget, int depth, std::vector<Block>& out) {
+  block_columns(hp, nr, b, budget);
+  const double w0 = block_work(hp, b);
+  double best = 0.97 * w0;
+  Block bl1, bl2;
+  bool found = false;
+  auto consider = [&](Block c1, Block c2) {
+    block_columns(hp, nr, c1, budget);
+    block_columns(hp, nr, c2, budget);
+    const double w = block_work(hp, c1) + block_work(hp, c2);
+    if (w < best) {
+      best = w;
+      bl1 = c1;
+      bl2 = c2;
+      found = true;
+    }
+  };
+  if (depth < 24) {
+    for (double t : {0.25, 0.5, 0.75}) {
+      if (b.R >= 2 * kMinSide) {
+        int64_t km = (int64_t)std::llround(std::exp((1 - t) * std::log((double)b.k0) + t * std::log((double)b.k1)));
+        km = std::min(std::max(km, b.k0 + kMinSide), b.k1 - kMinSide + 1);
+        consider(make_block(hp, b.k0, km - 1, b.n0, b.n1), make_block(hp, km, b.k1, b.n0, b.n1));
+      }
+      if (b.C >= 2 * kMinSide) {
+        int64_t nm = (int64_t)std::llround(std::exp((1 - t) * std::log((double)b.n0) + t * std::log((double)b.n1)));
+        nm = std::min(std::max(nm, b.n0 + kMinSide), b.n1 - kMinSide + 1);
+        consider(make_block(hp, b.k0, b.k1, b.n0, nm - 1), make_block(hp, b.k0, b.k1, nm, b.n1));
+      }
+    }
+  }
+  if (!found) {
+    out.push_back(b);
+    return;
+  }
+  refine(hp, nr, bl1, budget, depth + 1, out);
+  refine(hp, nr, bl2, budget, depth + 1, out);
+}
+
+void select_columns(HostPlan& hp) {
+  const int64_t N = hp.opt.N;
+  NodeRanges nr(hp);
+  double budget = kDropFrac * hp.opt.eps / kRowBlocks;
+  const bool subdivide = !(hp.opt.flags & (HANKEL_FLAG_NO_REFINE | HANKEL_FLAG_ALL_COLUMNS));
+  if (subdivide) {
+    std::vector<Block> out;
+    for (const Block& b : hp.blocks) refine(hp, nr, b, budget, 0, out);
+    hp.blocks = out;
+  }
+  // blocks meeting in one row; the budget must cover all of them
+  std::vector<int> per_row(N + 2, 0);
+  for (const Block& b : hp.blocks) {
+    per_row[b.k0] += 1;
+    per_row[b.k1 + 1] -= 1;
+  }
+  int maxrow = 1, run = 0;
+  for (int64_t k = 1; k <= N; ++k) maxrow = std::max(maxrow, run += per_row[k]);
+  budget = kDropFrac * hp.opt.eps / std::max(maxrow, subdivide ? kRowBlocks : 1);
+  for (Block& b : hp.blocks) block_columns(hp, nr, b, budget);
 }
 
 // Taylor polynomials of J_nu about z_c = i + 1/2 on [i, i+1). The coefficients follow from

@@ -38,6 +38,7 @@ struct Request {
   const double* c;
   double* f;
   int nrhs;
+  bool c_pinned = false, f_pinned = false;  // page-locked host arrays: copied without staging
   Clock::time_point t_submit, t_done;
   int status = HANKEL_OK;
   bool done = false;
@@ -58,6 +59,7 @@ struct Item {
   const double* c;
   double* f;
   int nrhs;
+  bool c_pinned, f_pinned;
 };
 
 struct Slot {
@@ -185,41 +187,57 @@ int get_plan(hankel_server_s* s, const Key& key, PlanEntry** out) {
   return HANKEL_OK;
 }
 
-// Issue copy-in, execution and copy-out of a packed batch on slot i.
-int launch_batch(hankel_server_s* s, int i, PlanEntry& pe, int64_t N, int nrhs) {
+// Issue copy-in, execution and copy-out of a packed batch on slot i. Page-locked request
+// arrays are copied straight to and from the slot's device buffers; the others go through the
+// slot's staging buffers (filled by dispatch, emptied by retire). With graphs, the execution
+// alone is captured once per (slot, batch size) and replayed between the copies.
+int launch_batch(hankel_server_s* s, int i, PlanEntry& pe, int64_t N, int nrhs, const std::vector<Item>& batch) {
   Slot& sl = s->slots[i];
-  const size_t bytes = (size_t)N * nrhs * sizeof(double);
-  auto direct = [&]() -> int {
-    if (cudaMemcpyAsync(sl.c_dev, sl.c_pin, bytes, cudaMemcpyHostToDevice, sl.stream) != cudaSuccess)
+  size_t off = 0;
+  for (const Item& it : batch) {
+    const size_t n = (size_t)N * it.nrhs;
+    const double* src = it.c_pinned ? it.c : sl.c_pin + off;
+    if (cudaMemcpyAsync(sl.c_dev + off, src, n * sizeof(double), cudaMemcpyHostToDevice, sl.stream) != cudaSuccess)
       return HANKEL_ECUDA;
-    int st = hankel_exec_batched(pe.plan, sl.c_dev, N, sl.f_dev, N, nrhs, sl.stream);
-    if (st != HANKEL_OK) return st;
-    if (cudaMemcpyAsync(sl.f_pin, sl.f_dev, bytes, cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess)
-      return HANKEL_ECUDA;
-    return HANKEL_OK;
-  };
-  if (!s->opt.use_graphs || pe.runs == 0) return direct();  // first run configures kernels uncaptured
-  auto key = std::make_pair(i, nrhs);
-  auto it = pe.graphs.find(key);
-  if (it == pe.graphs.end()) {
-    cudaGraph_t g = nullptr;
-    if (cudaStreamBeginCapture(sl.stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return HANKEL_ECUDA;
-    int st = direct();
-    cudaError_t e = cudaStreamEndCapture(sl.stream, &g);
-    if (st != HANKEL_OK || e != cudaSuccess) {
-      if (g) cudaGraphDestroy(g);
-      cudaGetLastError();
-      return st != HANKEL_OK ? st : HANKEL_ECUDA;
-    }
-    cudaGraphExec_t ge = nullptr;
-    e = cudaGraphInstantiate(&ge, g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) return HANKEL_ECUDA;
-    it = pe.graphs.emplace(key, ge).first;
-    std::lock_guard<std::mutex> lk(s->mu);
-    s->stats.graphs_captured++;
+    off += n;
   }
-  return cudaGraphLaunch(it->second, sl.stream) == cudaSuccess ? HANKEL_OK : HANKEL_ECUDA;
+  auto exec = [&]() { return hankel_exec_batched(pe.plan, sl.c_dev, N, sl.f_dev, N, nrhs, sl.stream); };
+  int st = HANKEL_OK;
+  if (!s->opt.use_graphs || pe.runs == 0) {
+    st = exec();  // the first run configures kernels uncaptured
+  } else {
+    auto key = std::make_pair(i, nrhs);
+    auto it = pe.graphs.find(key);
+    if (it == pe.graphs.end()) {
+      cudaGraph_t g = nullptr;
+      if (cudaStreamBeginCapture(sl.stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return HANKEL_ECUDA;
+      st = exec();
+      cudaError_t e = cudaStreamEndCapture(sl.stream, &g);
+      if (st != HANKEL_OK || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return st != HANKEL_OK ? st : HANKEL_ECUDA;
+      }
+      cudaGraphExec_t ge = nullptr;
+      e = cudaGraphInstantiate(&ge, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return HANKEL_ECUDA;
+      it = pe.graphs.emplace(key, ge).first;
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->stats.graphs_captured++;
+    }
+    if (cudaGraphLaunch(it->second, sl.stream) != cudaSuccess) st = HANKEL_ECUDA;
+  }
+  if (st != HANKEL_OK) return st;
+  off = 0;
+  for (const Item& it : batch) {
+    const size_t n = (size_t)N * it.nrhs;
+    double* dst = it.f_pinned ? it.f : sl.f_pin + off;
+    if (cudaMemcpyAsync(dst, sl.f_dev + off, n * sizeof(double), cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess)
+      return HANKEL_ECUDA;
+    off += n;
+  }
+  return HANKEL_OK;
 }
 
 void finish(hankel_server_s* s, const std::vector<Item>& items, int status) {
@@ -253,7 +271,7 @@ bool retire(hankel_server_s* s) {
     if (status == HANKEL_OK) {
       size_t off = 0;
       for (const Item& it : sl.items) {
-        memcpy(it.f, sl.f_pin + off, (size_t)sl.N * it.nrhs * sizeof(double));
+        if (!it.f_pinned) memcpy(it.f, sl.f_pin + off, (size_t)sl.N * it.nrhs * sizeof(double));
         off += (size_t)sl.N * it.nrhs;
       }
     }
@@ -286,7 +304,7 @@ bool dispatch(hankel_server_s* s, int i) {
       const Request& r = s->reqs[*it];
       if (r.key == key && nrhs + r.nrhs <= s->opt.max_batch && (s->opt.pack_requests || batch.empty())) {
         nrhs += r.nrhs;
-        batch.push_back(Item{*it, r.c, r.f, r.nrhs});
+        batch.push_back(Item{*it, r.c, r.f, r.nrhs, r.c_pinned, r.f_pinned});
         it = s->queue.erase(it);
       } else {
         ++it;
@@ -304,10 +322,10 @@ bool dispatch(hankel_server_s* s, int i) {
   Slot& sl = s->slots[i];
   size_t off = 0;
   for (const Item& it : batch) {
-    memcpy(sl.c_pin + off, it.c, (size_t)N * it.nrhs * sizeof(double));
+    if (!it.c_pinned) memcpy(sl.c_pin + off, it.c, (size_t)N * it.nrhs * sizeof(double));
     off += (size_t)N * it.nrhs;
   }
-  st = launch_batch(s, i, *pe, N, nrhs);
+  st = launch_batch(s, i, *pe, N, nrhs, batch);
   if (st == HANKEL_OK && cudaEventRecord(sl.done, sl.stream) != cudaSuccess) st = HANKEL_ECUDA;
   if (st != HANKEL_OK) {
     cudaStreamSynchronize(sl.stream);
@@ -405,12 +423,24 @@ int hankel_server_submit(hankel_server_t s, int task, int nu, int64_t N, double 
   hankel_info info;
   int st = hankel_params(&o, &info);  // reject bad parameters now, without a GPU round trip
   if (st != HANKEL_OK) return st;
+  // page-locked arrays (allocated with cudaMallocHost or registered) skip the staging copies
+  auto pinned = [](const void* q) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, q) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+  };
+  const bool cp = pinned(c), fp = pinned(f);
   std::lock_guard<std::mutex> lk(s->mu);
   Request r;
   r.key = Key(task, nu, N, eps);
   r.c = c;
   r.f = f;
   r.nrhs = nrhs;
+  r.c_pinned = cp;
+  r.f_pinned = fp;
   r.t_submit = Clock::now();
   s->reqs.push_back(r);
   *ticket = (int64_t)s->reqs.size() - 1;

@@ -106,3 +106,19 @@ def test_rejects_invalid_requests():
     with pytest.raises(RuntimeError, match="EINVAL"):
         srv.submit("schlomilch", 0, 100, 1e-8, np.zeros((65, 100)))  # more vectors than max_batch
     srv.close()
+
+
+def test_page_locked_requests_match_pageable():
+    # page-locked request arrays bypass the staging buffers; results are the same either way
+    c = coefficients("normal", 4096, 3, 91)
+    ct = torch.from_numpy(c).pin_memory()
+    fpin = torch.empty((3, 4096), dtype=torch.float64).pin_memory()
+    srv = hk.Server(streams=2, max_batch=4, use_graphs=True)
+    t1, f1 = srv.submit("dht", 0, 4096, 1e-8, c)
+    t2, f2 = srv.submit("dht", 0, 4096, 1e-8, ct.numpy(), fpin.numpy())
+    srv.wait(t1)
+    srv.wait(t2)
+    t3, f3 = srv.submit("dht", 0, 4096, 1e-8, ct.numpy(), fpin.numpy())  # replay with graphs
+    srv.wait(t3)
+    assert np.array_equal(f1, f2) and np.array_equal(f2, f3) and np.array_equal(f3, fpin.numpy())
+    srv.close()

@@ -206,7 +206,7 @@ def test_column_selection_shrinks_the_workload_transforms():
         assert _fft_work(p) < 0.2 * _fft_work(q)
         assert _fft_work(r) < 0.7 * _fft_work(p)
         assert _fft_work(lr) < 0.6 * _fft_work(r)
-        assert all(b["kept"] == rb["ncols"] for b, rb in zip(lr.blocks(), r.blocks()))
+        assert all(b["ncols"] < b["kept"] for b in lr.blocks() if b["lowrank"])
 
 
 @pytest.mark.parametrize("task,nu,N,eps", [("dht", 0, 20000, 1e-15), ("dht", 0, 2 ** 17, 1e-8),
@@ -214,13 +214,11 @@ def test_column_selection_shrinks_the_workload_transforms():
                                            ("dht", 0, 20000, 1e-4)])
 def test_lowrank_forms_match_the_kept_columns(task, nu, N, eps):
     # a block's low-rank form (Chebyshev interpolation in log k, log n of a cross approximation)
-    # agrees with the sum over its kept columns to eps/2 at entries other than the ones it was
-    # validated on
+    # agrees with the expansion over every stacked column to eps/2 plus the block's drop bound
+    # at entries other than the ones it was validated on
     p = hk.Plan(task, nu, N, eps, host_only=True)
-    q = hk.Plan(task, nu, N, eps, host_only=True, lowrank=False)
     blocks = p.blocks()
     assert sum(b["lowrank"] for b in blocks) >= len(blocks) // 2
-    assert [(b["k0"], b["n0"]) for b in blocks] == [(b["k0"], b["n0"]) for b in q.blocks()]
     rng = np.random.default_rng(19)
     for b in blocks:
         if not b["lowrank"]:
@@ -229,9 +227,9 @@ def test_lowrank_forms_match_the_kept_columns(task, nu, N, eps):
         ks = rng.integers(b["k0"], b["k1"] + 1, 40)
         ns = rng.integers(b["n0"], b["n1"] + 1, 40)
         for k, n in zip(ks, ns):
-            vp, _ = p.entry(k, n)
-            vq, _ = q.entry(k, n)
-            assert abs(vp - vq) <= 0.5 * eps + 4e-16, (k, n, vp, vq, b)
+            vp, far = p.entry(k, n)
+            vq = p.expansion_entry(k, n)
+            assert far and abs(vp - vq) <= 0.5 * eps + b["dropped"] + 4e-16, (k, n, vp, vq, b)
 
 
 @pytest.mark.parametrize("task,nu,N,eps,grid", [("dht", 0, 300, 1e-15, "unit"), ("schlomilch", 0, 300, 1e-8, "paper"),
