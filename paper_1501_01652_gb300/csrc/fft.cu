@@ -1,11 +1,11 @@
 // Multi-column power-of-two FFT (Stockham autosort, decimation in time) in FP64
 // (double2) or FP32 (float2), and the chirp-z helpers of the far field.
 //
-// After passes with radices R_1 R_2 ... = F the output is in natural order. One
-// CTA handles kTile consecutive (p, q) pairs of a pass, so every global load and
-// store touches kTile or more consecutive elements. Radices R <= 16 do the R-point
-// DFT in shared memory with radix-4/radix-2 Stockham sub-steps; radices 32..256 in
-// two register sub-stages with one exchange through shared memory.
+// Transforms of F <= 4096 points run whole in one launch (k_fft_small). Longer ones take
+// passes of radix 32..256 (k_fft_pass_reg); after passes with radices R_1 R_2 ... = F the
+// output is in natural order. One CTA handles kTile consecutive (p, q) pairs of a pass, so
+// every global load and store touches kTile or more consecutive elements, and does the
+// R-point DFTs in two register sub-stages with one exchange through shared memory.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -28,36 +28,6 @@ __device__ __forceinline__ C twiddle(const C* __restrict__ tw, uint32_t idx) {
   return t;
 }
 
-// Radix-4 decimation-in-time butterfly on x_j = a_j w_j (w_0 = 1), written so that every
-// twiddle product is folded into an FMA: u0 = a0 + w2 a2, u1 = 2 a0 - u0, t = w1 a1,
-// v0 = t + w3 a3, v1 = 2t - v0; then y0 = u0 + v0, y2 = u0 - v0, y1 = u1 -/+ i v1,
-// y3 = u1 +/- i v1 (forward/inverse). 24 FP64 instructions for 4 points and 2 stages.
-template <bool INV, class C>
-__device__ __forceinline__ void bfly4(C& a0, C& a1, C& a2, C& a3, C w1, C w2, C w3) {
-  typedef typename RealOf<C>::type R;
-  const R two = (R)2;
-  C u0, u1, t, v0, v1;
-  u0.x = fmar(w2.x, a2.x, fmar(-w2.y, a2.y, a0.x));
-  u0.y = fmar(w2.x, a2.y, fmar(w2.y, a2.x, a0.y));
-  u1.x = fmar(two, a0.x, -u0.x);
-  u1.y = fmar(two, a0.y, -u0.y);
-  t.x = fmar(w1.x, a1.x, -w1.y * a1.y);
-  t.y = fmar(w1.x, a1.y, w1.y * a1.x);
-  v0.x = fmar(w3.x, a3.x, fmar(-w3.y, a3.y, t.x));
-  v0.y = fmar(w3.x, a3.y, fmar(w3.y, a3.x, t.y));
-  v1.x = fmar(two, t.x, -v0.x);
-  v1.y = fmar(two, t.y, -v0.y);
-  a0 = mkc(u0.x + v0.x, u0.y + v0.y);
-  a2 = mkc(u0.x - v0.x, u0.y - v0.y);
-  if (INV) {
-    a1 = mkc(u1.x - v1.y, u1.y + v1.x);
-    a3 = mkc(u1.x + v1.y, u1.y - v1.x);
-  } else {
-    a1 = mkc(u1.x + v1.y, u1.y - v1.x);
-    a3 = mkc(u1.x - v1.y, u1.y + v1.x);
-  }
-}
-
 // Radix-2 decimation-in-time butterfly on (a0, a1 w): y0 = a0 + w a1, y1 = 2 a0 - y0.
 template <class C>
 __device__ __forceinline__ void bfly2(C& a0, C& a1, C w) {
@@ -69,109 +39,13 @@ __device__ __forceinline__ void bfly2(C& a0, C& a1, C w) {
   a0 = y0;
 }
 
-// R-point DFTs of kTile sequences held as a[e * kRow + i] (element e, sequence i; rows padded
-// to kRow = kTile + 1 elements so that column-wise accesses do not hit one shared-memory bank),
-// each input e first multiplied by W_F^{pt[i] * e} (the pass twiddle; pt[i] = p*s of sequence i).
-// Decimation-in-time Stockham sub-steps of radix 2 (first, when log2 R is odd) and 4, with
-// stride s_k and sub-length n_k = R/s_k. The pass twiddle is never applied on its own: the
-// inputs e = qq + s_k (r pp + j) of a butterfly carry W_F^{pt (qq + s_k j)}; the common
-// factor W_F^{pt qq} moves to the butterfly's outputs (whose index is qq mod s_k again), and
-// W_F^{pt s_k j} joins the step's own twiddle W_{n_k}^{pp j} in one table lookup. At the last
-// step s_k = 1, so nothing is left over. Input j = 0 of every butterfly needs no twiddle.
-// Every index fits in 32 bits (F, Fmax <= 2^24).
-template <int LOGR, bool INV, class C>
-__device__ C* smem_dft(C* a, C* b, const C* __restrict__ tw, int logFmax, int logF, const uint32_t* pt) {
-  constexpr int R = 1 << LOGR;
-  const int fsh = logFmax - logF;
-  const uint32_t fmask = (1u << logFmax) - 1u;
-  int logn = 0;  // log2 of the sub-length transformed so far
-  if (LOGR & 1) {
-    // radix-2 sub-step: n = 2, s = R/2, m = 1
-    const int logs = LOGR - 1, s = 1 << logs;
-    for (uint32_t idx = threadIdx.x; idx < kTile * (R / 2); idx += blockDim.x) {
-      const uint32_t i = idx & (kTile - 1), q = idx / kTile;
-      C a0 = a[q * kRow + i], a1 = a[(q + s) * kRow + i];
-      const C w = twiddle<INV>(tw, ((pt[i] << logs) << fsh) & fmask);
-      bfly2(a0, a1, w);
-      b[q * kRow + i] = a0;
-      b[(q + s) * kRow + i] = a1;
-    }
-    __syncthreads();
-    C* t = a; a = b; b = t;
-    logn = 1;
-  }
-  while (logn < LOGR) {
-    // radix-4 sub-step: sub-length n' = 4 * 2^logn, stride s = R / n', m = 2^logn
-    const int lognn = logn + 2, logs = LOGR - lognn;
-    const uint32_t s = 1u << logs, m = 1u << logn;
-    for (uint32_t idx = threadIdx.x; idx < kTile * (R / 4); idx += blockDim.x) {
-      const uint32_t i = idx & (kTile - 1), bf = idx / kTile;
-      const uint32_t pp = bf >> logs, qq = bf & (s - 1);
-      const uint32_t e0 = qq + s * 4 * pp;  // inputs e0 + s*j, outputs qq + s*(pp + r m)
-      C a0 = a[e0 * kRow + i], a1 = a[(e0 + s) * kRow + i];
-      C a2 = a[(e0 + 2 * s) * kRow + i], a3 = a[(e0 + 3 * s) * kRow + i];
-      // W_{n'}^{pp j} W_F^{pt s j} = W_{Fmax}^{j * base}
-      const uint32_t base = (pp << (logFmax - lognn)) + ((pt[i] << logs) << fsh);
-      const C w1 = twiddle<INV>(tw, base & fmask);
-      const C w2 = twiddle<INV>(tw, (2 * base) & fmask);
-      const C w3 = twiddle<INV>(tw, (3 * base) & fmask);
-      bfly4<INV>(a0, a1, a2, a3, w1, w2, w3);
-      b[(qq + s * pp) * kRow + i] = a0;
-      b[(qq + s * (pp + m)) * kRow + i] = a1;
-      b[(qq + s * (pp + 2 * m)) * kRow + i] = a2;
-      b[(qq + s * (pp + 3 * m)) * kRow + i] = a3;
-    }
-    __syncthreads();
-    C* t = a; a = b; b = t;
-    logn = lognn;
-  }
-  return a;
-}
-
-// One decimation-in-time Stockham pass of sub-length n = F/s with radix R = 2^LOGR: for
-// pairs (p < n/R, q < s), z_j = y[q + s(R p + j)] W_n^{p j}, Z = DFT_R(z), x[q + s(p + r n/R)] = Z_r.
-// The store index is pi + r F/R with pi = p s + q, so a tile of kTile consecutive pairs writes
-// kTile consecutive elements per r; the loads are contiguous runs of kTile or s*R elements.
-template <int LOGR, bool INV, class C>
-__global__ void __launch_bounds__(kFftThreads) k_fft_pass(const C* __restrict__ src, C* __restrict__ dst, int logF,
-                                                          int logS, const C* __restrict__ tw, int logFmax) {
-  constexpr int R = 1 << LOGR;
-  extern __shared__ __align__(16) unsigned char sm_raw[];
-  __shared__ uint32_t pt[kTile];
-  C* v = reinterpret_cast<C*>(sm_raw);
-  C* w = v + R * kRow;
-  const int logFR = logF - LOGR;  // pairs per column (a multiple of kTile) = 2^logFR
-  const uint64_t G0 = (uint64_t)blockIdx.x * kTile;
-  const uint64_t col = G0 >> logFR;
-  const uint32_t pi0 = (uint32_t)(G0 & ((1ull << logFR) - 1));
-  const C* x = src + (col << logF);
-  C* y = dst + (col << logF);
-  const uint32_t s = 1u << logS;
-  if (threadIdx.x < kTile) pt[threadIdx.x] = ((pi0 + threadIdx.x) >> logS) << logS;  // p * s
-  if (s >= kTile) {
-    const uint32_t p = pi0 >> logS, q0 = pi0 & (s - 1);
-    const C* xb = x + q0 + ((p << LOGR) << logS);  // + s R p
-    for (uint32_t idx = threadIdx.x; idx < R * kTile; idx += blockDim.x) {
-      const uint32_t i = idx & (kTile - 1), j = idx / kTile;
-      v[j * kRow + i] = xb[i + (j << logS)];
-    }
-  } else {
-    const C* xb = x + (pi0 << LOGR);  // s R p0 with pi0 = s p0
-    const uint32_t srm = (s << LOGR) - 1;
-    for (uint32_t idx = threadIdx.x; idx < R * kTile; idx += blockDim.x) {
-      const uint32_t pl = idx >> (logS + LOGR), rem = idx & srm;
-      const uint32_t j = rem >> logS, q = rem & (s - 1);
-      v[j * kRow + ((pl << logS) + q)] = xb[idx];
-    }
-  }
-  __syncthreads();
-  const C* res = smem_dft<LOGR, INV>(v, w, tw, logFmax, logF, pt);
-  C* yb = y + pi0;
-  for (uint32_t idx = threadIdx.x; idx < R * kTile; idx += blockDim.x) {
-    const uint32_t i = idx & (kTile - 1), r = idx / kTile;
-    yb[i + (r << logFR)] = res[r * kRow + i];
-  }
-}
+// Twiddle deferral. A pass of radix R multiplies input e of the R-point DFT of sequence
+// (p, q) by the pass twiddle W_F^{pt e} (pt = p s). The pass twiddle is never applied on its
+// own: in a Stockham sub-stage of stride s_k, the inputs e = qq + s_k (Q pp + j) of a butterfly
+// carry W_F^{pt (qq + s_k j)}; the common factor W_F^{pt qq} moves to the butterfly's outputs
+// (whose index is qq mod s_k again), and W_F^{pt s_k j} joins the sub-stage's own twiddle
+// W_{n_k}^{pp j} in one table lookup. At the last sub-stage s_k = 1, so nothing is left over.
+// Every index fits in 32 bits (F <= 2^24).
 
 // Twiddled radix-2^LQ DFT in registers: on return a[r] = sum_j W_Q^{r j} w^j a_j (Q = 2^LQ),
 // where w^t is the table entry (t * base) mod Fmax. Iterative radix-2 decimation in time on the
@@ -261,7 +135,7 @@ __device__ __forceinline__ void reg_dft_unit(C (&a)[1 << LQ]) {
 // through shared memory. Its outputs go to shared memory; sub-stage 2 (stride 1) reads
 // elements Q2 pp + j there and writes its outputs pp + Q1 r straight to global memory, again
 // kTile-contiguous per element. The block has kTile Q1 threads, one butterfly per thread and
-// sub-stage. Twiddle deferral as in smem_dft; the pass twiddle exponent p s of a thread's
+// sub-stage. Twiddles are deferred as described above; the pass twiddle exponent p s of a thread's
 // sequence is recomputed per thread.
 template <int LOGR, bool INV, class C>
 __global__ void __launch_bounds__(kFftThreads) k_fft_pass_reg(const C* __restrict__ src, C* __restrict__ dst,
@@ -501,37 +375,23 @@ void launch_pass(const C* src, C* dst, int logF, int logS, int ncols, const C* t
   constexpr int R = 1 << LOGR;
   const int64_t pairs = ((int64_t)ncols << logF) >> LOGR;
   const int64_t grid = pairs / kTile;
-  if constexpr (LOGR >= 5) {
-    // one buffer (the sub-stages work in place); threads = butterflies of the wider sub-stage
-    constexpr int L2 = LOGR - (LOGR + 1) / 2;
-    constexpr int threads = kTile * (R >> L2);
-    const size_t smem = (size_t)R * kRow * sizeof(C);
-    static bool configured = false;
-    if (!configured) {
-      cudaFuncSetAttribute(k_fft_pass_reg<LOGR, INV, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      configured = true;
-    }
-    k_fft_pass_reg<LOGR, INV, C><<<(unsigned)grid, threads, smem, st>>>(src, dst, logF, logS, tw, logFmax, hmul,
-                                                                          nseg);
-  } else {
-    const size_t smem = 2 * (size_t)R * kRow * sizeof(C);
-    static bool configured = false;
-    if (!configured) {
-      cudaFuncSetAttribute(k_fft_pass<LOGR, INV, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      configured = true;
-    }
-    k_fft_pass<LOGR, INV, C><<<(unsigned)grid, kFftThreads, smem, st>>>(src, dst, logF, logS, tw, logFmax);
+  // one buffer (the sub-stages work in place); threads = butterflies of the wider sub-stage
+  constexpr int L2 = LOGR - (LOGR + 1) / 2;
+  constexpr int threads = kTile * (R >> L2);
+  const size_t smem = (size_t)R * kRow * sizeof(C);
+  static bool configured = false;
+  if (!configured) {
+    cudaFuncSetAttribute(k_fft_pass_reg<LOGR, INV, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    configured = true;
   }
+  k_fft_pass_reg<LOGR, INV, C><<<(unsigned)grid, threads, smem, st>>>(src, dst, logF, logS, tw, logFmax, hmul, nseg);
 }
 
 template <bool INV, class C>
 void launch_pass_r(int logR, const C* src, C* dst, int logF, int logS, int ncols, const C* tw, int logFmax,
                    const C* hmul, int64_t nseg, cudaStream_t st) {
+  // transforms longer than 4096 points split into passes of radix 2^5 .. 2^8
   switch (logR) {
-    case 1: launch_pass<1, INV>(src, dst, logF, logS, ncols, tw, logFmax, hmul, nseg, st); break;
-    case 2: launch_pass<2, INV>(src, dst, logF, logS, ncols, tw, logFmax, hmul, nseg, st); break;
-    case 3: launch_pass<3, INV>(src, dst, logF, logS, ncols, tw, logFmax, hmul, nseg, st); break;
-    case 4: launch_pass<4, INV>(src, dst, logF, logS, ncols, tw, logFmax, hmul, nseg, st); break;
     case 5: launch_pass<5, INV>(src, dst, logF, logS, ncols, tw, logFmax, hmul, nseg, st); break;
     case 6: launch_pass<6, INV>(src, dst, logF, logS, ncols, tw, logFmax, hmul, nseg, st); break;
     case 7: launch_pass<7, INV>(src, dst, logF, logS, ncols, tw, logFmax, hmul, nseg, st); break;
@@ -619,11 +479,12 @@ int run_fft(C* a, C* b, int logF, int ncols, bool inverse, const C* tw, int logF
     if (npasses) *npasses = 1;
     return HANKEL_OK;
   }
-  const int maxlog = std::min(8, logF - 4);  // keeps F/R >= kTile pairs per column
-  const int np = (logF + maxlog - 1) / maxlog;
+  // logF >= 13: passes of radix 2^5 .. 2^8 (logF <= 24 gives at most three of at least 2^5),
+  // each leaving F/R >= kTile pairs per column; the first (stride F/R >= kTile) applies the
+  // input product
+  const int np = (logF + 7) / 8;
   const int base = logF / np, extra = logF % np;
-  // the first pass (radix >= 2^5 here, stride F/R >= kTile) applies the input product
-  if (hmul && (base + (extra > 0 ? 1 : 0) < 5 || logF - (base + (extra > 0 ? 1 : 0)) < 4)) return HANKEL_EINVAL;
+  if (base < 5) return HANKEL_EINVAL;
   C* src = a;
   C* dst = b;
   int done = 0;  // log2 of the sub-length transformed so far

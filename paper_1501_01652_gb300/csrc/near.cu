@@ -2,9 +2,10 @@
 // leading rows/columns of Sections 5-6): f_k = sum_{n <= nend(k)} c_n J_nu(r_k omega_n)
 // with J evaluated per entry, over tiles of 32 rows x 512 columns of the near set.
 //
-// J_nu on [0, zmax] comes from a table of degree-15 Taylor polynomials about
-// the centres i + 1/2 of unit intervals (built at plan time from the Neumann
-// addition formula, Eq. 8), so one evaluation costs a table row load and 15 FMAs.
+// J_nu on [0, zmax] comes from a table of Taylor polynomials about the centres of
+// intervals of width 1/kJTabSub (built at plan time from the Neumann addition formula,
+// Eq. 8, with the degree set by eps), so one evaluation costs a table row load and
+// deg FMAs.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -22,9 +23,9 @@ constexpr int kMaxRhsGroup = 16;
 
 template <class R>
 __device__ __forceinline__ R table_j(const R* __restrict__ jtab, int64_t jt_n, int deg, R z) {
-  int64_t i = (int64_t)z;
+  int64_t i = (int64_t)(z * (R)kJTabSub);
   i = i < 0 ? 0 : (i >= jt_n ? jt_n - 1 : i);
-  const R d = z - ((R)i + (R)0.5);
+  const R d = z - ((R)i + (R)0.5) * ((R)1 / (R)kJTabSub);
   const R* t = jtab + i * (deg + 1);
   R v = __ldg(&t[deg]);
   for (int j = deg - 1; j >= 0; --j) v = fmar(v, d, __ldg(&t[j]));

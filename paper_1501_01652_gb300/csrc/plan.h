@@ -15,8 +15,8 @@ typedef std::complex<double> cplx;
 // by one stacked column (2T+K-2 of Section 5.1 at eps = 1e-16 is 10).
 constexpr int kMaxU = 16;
 // Near-field Bessel table: intervals of width 1 with Taylor polynomials of this degree.
-constexpr int kJTabDeg = 15;
-constexpr int kJTabDegF32 = 8;
+constexpr int kJTabSub = 8;      // near-field J table: Taylor intervals per unit of z
+constexpr int kJTabDegMax = 10;  // largest Taylor degree of the near-field J table
 
 // How a block's chirp-z convolution is carried out.
 enum BlockMode {
@@ -81,8 +81,10 @@ struct HostPlan {
   double zmax = 0;
   // stacked columns per block
   std::vector<ColSpec> cols;
-  // near-field J table: ntab intervals [i, i+1), centre i + 1/2, deg+1 Taylor coefficients each
-  int jt_deg = kJTabDeg;
+  // near-field J table: jt_n intervals [i/sub, (i+1)/sub), centre (i + 1/2)/sub, deg+1 Taylor
+  // coefficients each
+  int jt_deg = kJTabDegMax;
+  int jt_sub = kJTabSub;
   int64_t jt_n = 0;
   std::vector<double> jtab;
 };

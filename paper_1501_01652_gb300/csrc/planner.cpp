@@ -921,21 +921,27 @@ void select_columns(HostPlan& hp) {
   for (Block& b : hp.blocks) block_columns(hp, nr, b, budget);
 }
 
-// Taylor polynomials of J_nu about z_c = i + 1/2 on [i, i+1). The coefficients follow from
-// the Neumann addition formula (Eq. 8) with each J_s(delta) expanded in its Taylor series
-// (Eq. 6) -- the same rearrangement as Section 5.1 with K and T unbounded:
+// Taylor polynomials of J_nu about z_c = (i + 1/2)/sub on [i/sub, (i+1)/sub). The coefficients
+// follow from the Neumann addition formula (Eq. 8) with each J_s(delta) expanded in its Taylor
+// series (Eq. 6) -- the same rearrangement as Section 5.1 with K and T unbounded:
 // t_d = 2^{-d} sum_t (-1)^t / (t!(d-t)!) [J_{nu-s}(z_c) + (-1)^s J_{nu+s}(z_c)], s = d-2t,
-// the s = 0 term counted once.
+// the s = 0 term counted once. Every derivative of J_nu is at most 1 in size, so degree d on
+// half-width h = 1/(2 sub) errs by at most h^{d+1}/(d+1)!; the degree is the smallest that
+// keeps this below eps/100 (at most kJTabDegMax).
 void build_jtable(HostPlan& hp) {
   const int nu = hp.opt.nu;
-  const int deg = hp.fp32 ? kJTabDegF32 : kJTabDeg;
+  const int sub = kJTabSub;
+  const double h = 0.5 / sub;
+  int deg = 2;
+  for (double b = h * h * h / 6.0; deg < kJTabDegMax && b > 0.01 * hp.opt.eps; b *= h / (deg + 2)) ++deg;
   hp.jt_deg = deg;
-  hp.jt_n = (int64_t)std::ceil(hp.zmax) + 2;
+  hp.jt_sub = sub;
+  hp.jt_n = (int64_t)std::ceil(hp.zmax * sub) + 2;
   hp.jtab.assign((size_t)hp.jt_n * (deg + 1), 0.0);
   std::vector<DD> J;
   const int L = nu + deg + 1;
   for (int64_t i = 0; i < hp.jt_n; ++i) {
-    DD zc = ddv(i + 0.5);
+    DD zc = dd_div(ddv(i + 0.5), ddv((double)sub));
     miller_all(zc, L, J);
     auto jl = [&](int lam) -> DD {  // J_lam for any integer lam (DLMF 10.4.1)
       if (lam >= 0) return J[lam];
@@ -970,10 +976,10 @@ int build_host_plan(const hankel_options& opt, HostPlan& hp) {
 }
 
 double table_j(const HostPlan& hp, double z) {
-  int64_t i = (int64_t)z;
+  int64_t i = (int64_t)(z * hp.jt_sub);
   if (i < 0) i = 0;
   if (i >= hp.jt_n) i = hp.jt_n - 1;
-  double d = z - ((double)i + 0.5);
+  double d = z - ((double)i + 0.5) / hp.jt_sub;
   const double* t = &hp.jtab[(size_t)i * (hp.jt_deg + 1)];
   double v = t[hp.jt_deg];
   for (int j = hp.jt_deg - 1; j >= 0; --j) v = v * d + t[j];
