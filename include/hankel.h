@@ -66,9 +66,12 @@ enum hankel_grid {
 };
 
 enum hankel_precision {
-  HANKEL_PREC_AUTO = 0,  /* FP64 below eps = 1e-5, FP32 transform stages at eps >= 1e-5 */
+  HANKEL_PREC_AUTO = 0,  /* FP64 below eps = 1e-11, DF64 transforms for 1e-11 <= eps < 1e-5, FP32 stages at
+                            eps >= 1e-5 */
   HANKEL_PREC_FP64 = 1,  /* every stage in FP64 */
-  HANKEL_PREC_FP32 = 2   /* FP32 stages; refused (HANKEL_EUNSUPPORTED) when eps < 1e-5 */
+  HANKEL_PREC_FP32 = 2,  /* FP32 stages; refused (HANKEL_EUNSUPPORTED) when eps < 1e-5 */
+  HANKEL_PREC_DF64 = 3   /* transforms and spectrum products in double-float (pairs of FP32, ~48
+                            significant bits), everything else FP64; refused when eps < 1e-11 */
 };
 
 enum hankel_status {

@@ -14,7 +14,7 @@ from . import _lib
 
 TASKS = {"schlomilch": 0, "fourier_bessel": 1, "dht": 2}
 GRIDS = {"unit": 0, "paper": 1}
-PRECISIONS = {"auto": 0, "fp64": 1, "fp32": 2}
+PRECISIONS = {"auto": 0, "fp64": 1, "fp32": 2, "df64": 3}
 
 
 def _options(task, nu, N, eps, grid="unit", gamma=None, precision="auto", max_nrhs=1, workspace_limit=0,

@@ -45,7 +45,7 @@ static void fill_info(const hankel_plan_s* p, const hk::HostPlan& hp, hankel_inf
   out->task = hp.opt.task;
   out->nu = hp.opt.nu;
   out->grid = hp.opt.grid;
-  out->precision = hp.fp32 ? HANKEL_PREC_FP32 : HANKEL_PREC_FP64;
+  out->precision = hp.fp32 ? HANKEL_PREC_FP32 : hp.df64 ? HANKEL_PREC_DF64 : HANKEL_PREC_FP64;
   out->N = hp.opt.N;
   out->gamma = hp.opt.gamma;
   out->eps = hp.opt.eps;

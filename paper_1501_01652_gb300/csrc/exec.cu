@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "device.h"
+#include "cplx.cuh"
 #include "kernels.cuh"
 
 namespace hk {
@@ -62,6 +63,8 @@ struct DevicePlan {
   std::vector<DevBlock> blocks;
   double2* tw = nullptr;   // twiddle ladder in FP64: W_F^t at tw[F + t], F = 2^6 .. 2^logFmax
   float2* twf = nullptr;   // the same ladder rounded to FP32 (FP32 plans)
+  df64c* twd = nullptr;    // the same ladder in double-float (DF64 plans)
+  bool df64 = false;       // transforms in double-float
   int logFmax = 6;
   void* bufA = nullptr;    // workspace, elements of the plan precision
   void* bufB = nullptr;
@@ -215,6 +218,7 @@ int dev_plan_create(hankel_plan_s* p) {
   HK_TRY(upload(d, &d->cols, cs.data(), cs.size()));
   HK_TRY(upload(d, &d->jtab, hp.jtab.data(), hp.jtab.size()));
   d->fp32 = hp.fp32;
+  d->df64 = hp.df64;
   const size_t esz = d->fp32 ? sizeof(float2) : sizeof(double2);  // workspace element size
   if (d->fp32) {
     std::vector<float> tf(std::max<size_t>((size_t)N, hp.jtab.size()));
@@ -275,6 +279,11 @@ int dev_plan_create(hankel_plan_s* p) {
     launch_scale_copy<float2>(d->tw + 64, d->twf + 64, (int64_t(2) << logFmax) - 64, 1.0, 0);
     HK_LAUNCHED();
   }
+  if (d->df64) {
+    HK_TRY(dalloc(d, &d->twd, (size_t)2 << logFmax));
+    launch_scale_copy<df64c>(d->tw + 64, d->twd + 64, (int64_t(2) << logFmax) - 64, 1.0, 0);
+    HK_LAUNCHED();
+  }
 
   // Workspace: two ping-pong buffers, each holding a chunk of stacked columns of a block
   // (nseg transforms of length F per stacked column for segmented blocks).
@@ -318,6 +327,10 @@ int dev_plan_create(hankel_plan_s* p) {
       float2* h; HK_TRY(dalloc(d, &h, (size_t)b.nseg * b.F)); db.H = h;
       float2* vt; HK_TRY(dalloc(d, &vt, (size_t)db.nl * b.C)); db.Vt = vt;
       float2* ut; HK_TRY(dalloc(d, &ut, (size_t)db.nl * b.R)); db.Ut = ut;
+    } else if (d->df64) {
+      df64c* h; HK_TRY(dalloc(d, &h, (size_t)b.nseg * b.F)); db.H = h;
+      df64c* vt; HK_TRY(dalloc(d, &vt, (size_t)db.nl * b.C)); db.Vt = vt;
+      df64c* ut; HK_TRY(dalloc(d, &ut, (size_t)db.nl * b.R)); db.Ut = ut;
     } else {
       double2* h; HK_TRY(dalloc(d, &h, (size_t)b.nseg * b.F)); db.H = h;
       double2* vt; HK_TRY(dalloc(d, &vt, (size_t)db.nl * b.C)); db.Vt = vt;
@@ -366,6 +379,7 @@ int dev_plan_create(hankel_plan_s* p) {
                       std::log((double)b.k0), std::log((double)b.k1), std::log((double)b.n0),
                       std::log((double)b.n1), d->nodes, d->cols, db.wV, scd, db.Vt, db.Ut};
       if (d->fp32) launch_block_tables<float2>(ta, 0);
+      else if (d->df64) launch_block_tables<df64c>(ta, 0);
       else launch_block_tables<double2>(ta, 0);
       HK_LAUNCHED();
       if (cudaDeviceSynchronize() != cudaSuccess) return HANKEL_ECUDA;
@@ -385,6 +399,7 @@ int dev_plan_create(hankel_plan_s* p) {
     double2* res = nullptr;
     HK_TRY(run_fft<double2>(hA, hB, b.logF, (int)b.nseg, /*inverse=*/false, d->tw, d->logFmax, 0, &res));
     if (d->fp32) launch_scale_copy<float2>(res, (float2*)d->blocks.back().H, b.nseg * b.F, 1.0 / (double)b.F, 0);
+    else if (d->df64) launch_scale_copy<df64c>(res, (df64c*)d->blocks.back().H, b.nseg * b.F, 1.0 / (double)b.F, 0);
     else launch_scale_copy<double2>(res, (double2*)d->blocks.back().H, b.nseg * b.F, 1.0 / (double)b.F, 0);
     HK_LAUNCHED();
   }
@@ -417,12 +432,12 @@ namespace {
 // Far-field work of one block for nrhs vectors: chunks of `cap` stacked columns through
 // generation, forward FFTs, the product with the kernel spectra (summed over column segments
 // or replicated over row segments), inverse FFTs and the row accumulation into f.
-// C = double2 (FP64 plans) or float2 (FP32 plans).
+// C = double2 (FP64 plans), float2 (FP32 plans) or df64c (DF64 plans).
 template <class C>
 int run_block(DevicePlan* d, const DevBlock& db, const double* c, int64_t ldc, double* f, int64_t ldf, int nrhs,
               C* A, C* B, int64_t cap, cudaStream_t st, bool record) {
   const Block& b = db.b;
-  const C* tw = d->fp32 ? (const C*)d->twf : (const C*)d->tw;
+  const C* tw = (const C*)(d->fp32 ? (const void*)d->twf : d->df64 ? (const void*)d->twd : (const void*)d->tw);
   const C* H = (const C*)db.H;
   const int64_t total = (int64_t)db.nl * nrhs;
   const bool rowseg = b.mode == kBlockRowSeg, colseg = b.mode == kBlockColSeg;
@@ -513,6 +528,7 @@ int run_all(DevicePlan* d, const HostPlan& hp, const double* c, int64_t ldc, dou
                             ? std::max<int64_t>(1, (int64_t)(capacity_elems / column_footprint(db.b)))
                             : db.cap;
     if (d->fp32) HK_TRY(run_block<float2>(d, db, c, ldc, f, ldf, nrhs, (float2*)A, (float2*)B, cap, st, record));
+    else if (d->df64) HK_TRY(run_block<df64c>(d, db, c, ldc, f, ldf, nrhs, (df64c*)A, (df64c*)B, cap, st, record));
     else HK_TRY(run_block<double2>(d, db, c, ldc, f, ldf, nrhs, (double2*)A, (double2*)B, cap, st, record));
   }
   return HANKEL_OK;

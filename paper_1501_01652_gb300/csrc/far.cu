@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(kMacPts* kMacLanes) k_seg_mac(const C* __restr
   R ar = 0, ai = 0;
   for (int64_t s = lane; s < nseg; s += kMacLanes) {
     const C v = x[s * F];
-    const C h = __ldg(&H[s * F + t]);
+    const C h = ldgc(&H[s * F + t]);
     ar = fmar(v.x, h.x, fmar(-v.y, h.y, ar));
     ai = fmar(v.x, h.y, fmar(v.y, h.x, ai));
   }
@@ -301,6 +301,10 @@ void launch_coeffs_f32(const double* c, int64_t ldc, float* cf, int64_t N, int n
 
 template void launch_block_tables<double2>(const BlockTabArgs&, cudaStream_t);
 template void launch_block_tables<float2>(const BlockTabArgs&, cudaStream_t);
+template void launch_block_tables<df64c>(const BlockTabArgs&, cudaStream_t);
+template void launch_gen<df64c>(const GenArgs&, cudaStream_t);
+template void launch_out<df64c>(const OutArgs&, cudaStream_t);
+template void launch_seg_mac<df64c>(const df64c*, const df64c*, df64c*, int64_t, int64_t, int, cudaStream_t);
 template void launch_gen<double2>(const GenArgs&, cudaStream_t);
 template void launch_gen<float2>(const GenArgs&, cudaStream_t);
 template void launch_out<double2>(const OutArgs&, cudaStream_t);

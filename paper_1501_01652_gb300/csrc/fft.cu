@@ -23,7 +23,7 @@ constexpr int kFftThreads = 256;
 
 template <bool INV, class C>
 __device__ __forceinline__ C twiddle(const C* __restrict__ tw, uint32_t idx) {
-  C t = __ldg(&tw[idx]);
+  C t = ldgc(&tw[idx]);
   if (INV) t.y = -t.y;
   return t;
 }
@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_pass_reg(const C* __restric
       for (int j = 0; j < Q1; ++j) a[j] = xb[(bf + Q2 * j) << logS];
       if (hc) {
 #pragma unroll
-        for (int j = 0; j < Q1; ++j) a[j] = cmul(a[j], __ldg(&hc[off + ((bf + Q2 * j) << logS)]));
+        for (int j = 0; j < Q1; ++j) a[j] = cmul(a[j], ldgc(&hc[off + ((bf + Q2 * j) << logS)]));
       }
     }
   } else {
@@ -313,7 +313,7 @@ __global__ void __launch_bounds__(SmallSplit<LOGF>::NT) k_fft_small(const C* __r
     for (int u = 0; u < PER; ++u) {
       const uint32_t idx = threadIdx.x + u * S::NT;
       const uint32_t c = idx >> LOGF, e = idx & (F - 1);
-      t[u] = (int64_t)idx < avail ? cmul(src[scol[c] * F + e], __ldg(&hmul[sseg[c] * F + e]))
+      t[u] = (int64_t)idx < avail ? cmul(src[scol[c] * F + e], ldgc(&hmul[sseg[c] * F + e]))
                                   : mkc((typename RealOf<C>::type)0, (typename RealOf<C>::type)0);
     }
   } else {
@@ -506,7 +506,10 @@ template int run_fft<double2>(double2*, double2*, int, int, bool, const double2*
                               int*, const double2*, int64_t);
 template int run_fft<float2>(float2*, float2*, int, int, bool, const float2*, int, cudaStream_t, float2**, int*,
                              const float2*, int64_t);
+template int run_fft<df64c>(df64c*, df64c*, int, int, bool, const df64c*, int, cudaStream_t, df64c**, int*,
+                            const df64c*, int64_t);
 template void launch_scale_copy<double2>(const double2*, double2*, int64_t, double, cudaStream_t);
 template void launch_scale_copy<float2>(const double2*, float2*, int64_t, double, cudaStream_t);
+template void launch_scale_copy<df64c>(const double2*, df64c*, int64_t, double, cudaStream_t);
 
 }  // namespace hk

@@ -61,6 +61,7 @@ struct HostPlan {
   double s = 0, alpha = 0, beta = 1;
   int64_t nrd = 0, ncd = 0;  // direct rows / columns
   bool fp32 = false;
+  bool df64 = false;  // transforms in double-float
   // exact phase theta~_kn = pi U_k V_n / E with U_k = Ua k + Ub, V_n = Va n + Vb
   int64_t Ua = 1, Ub = 0, Va = 1, Vb = 0, E = 1;
   // partition coordinates X_k = k - x0, Y_n = n + y0, z~ = pi X Y / D

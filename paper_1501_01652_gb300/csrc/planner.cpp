@@ -302,13 +302,16 @@ int choose_params(const hankel_options& o, HostPlan& hp) {
   if (o.task == HANKEL_DHT && o.nu != 0) return HANKEL_EINVAL;
   if (o.grid != HANKEL_GRID_UNIT && o.grid != HANKEL_GRID_PAPER) return HANKEL_EINVAL;
   if (o.max_nrhs < 1) return HANKEL_EINVAL;
-  if (o.precision < HANKEL_PREC_AUTO || o.precision > HANKEL_PREC_FP32) return HANKEL_EINVAL;
+  if (o.precision < HANKEL_PREC_AUTO || o.precision > HANKEL_PREC_DF64) return HANKEL_EINVAL;
   if (o.task == HANKEL_SCHLOMILCH && (o.gamma < -1 || o.gamma > 1024)) return HANKEL_EINVAL;
   if (o.eps < 1e-16) return HANKEL_EUNSUPPORTED;
   if (o.precision == HANKEL_PREC_FP32 && o.eps < 1e-5) return HANKEL_EUNSUPPORTED;
-  // FP32 transform and near-field stages only where the accuracy goal allows them (eps >= 1e-5);
+  if (o.precision == HANKEL_PREC_DF64 && o.eps < 1e-11) return HANKEL_EUNSUPPORTED;
+  // FP32 transform and near-field stages only where the accuracy goal allows them (eps >= 1e-5),
+  // double-float transforms where their ~2^-48 rounding stays far below eps (eps >= 1e-11);
   // nodes, phases and all plan tables stay FP64.
   hp.fp32 = (o.precision == HANKEL_PREC_FP32) || (o.precision == HANKEL_PREC_AUTO && o.eps >= 1e-5);
+  hp.df64 = !hp.fp32 && ((o.precision == HANKEL_PREC_DF64) || (o.precision == HANKEL_PREC_AUTO && o.eps >= 1e-11));
 
   const int64_t N = o.N;
   // Table 4: M = max(floor(0.3 log(1/eps)), 3), natural logarithm.

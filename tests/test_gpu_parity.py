@@ -121,6 +121,23 @@ def test_fp32_stages_at_relaxed_accuracy(task, nu, kind, eps, precision):
     _check(task, nu, N, eps, c, precision=precision)
 
 
+@pytest.mark.parametrize("task,nu,kind", [("dht", 0, "normal"), ("schlomilch", 1, "uniform"),
+                                          ("fourier_bessel", 0, "uniform")])
+@pytest.mark.parametrize("eps", [1e-6, 1e-8, 1e-11])
+def test_df64_transforms(task, nu, kind, eps):
+    # double-float transforms (AUTO picks them for 1e-11 <= eps < 1e-5) meet the bar, and stay
+    # close to the FP64 plan's result
+    N = 7000
+    c = coefficients(kind, N, 2, 7300 + nu)
+    f, plan = _run(task, nu, N, eps, c, precision="df64")
+    assert plan.info["precision"] == 3
+    ref = oracle.transform(task, nu, N, c)
+    l1 = np.abs(c).sum(axis=1, keepdims=True)
+    assert np.all(np.abs(f - ref) <= 10 * eps * l1)
+    g, _ = _run(task, nu, N, eps, c, precision="fp64")
+    assert np.all(np.abs(f - g) <= 1e-12 * l1)
+
+
 @pytest.mark.parametrize("eps", [1e-4, 1e-5])
 def test_fp32_workload_size_sampled_rows(eps):
     N = 2 ** 20

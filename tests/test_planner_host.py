@@ -40,10 +40,18 @@ def test_status_strings():
 def test_precision_policy():
     assert hk.params("dht", 0, 4096, 1e-4)["precision"] == 2       # AUTO: FP32 stages at eps >= 1e-5
     assert hk.params("dht", 0, 4096, 1e-5)["precision"] == 2
-    assert hk.params("dht", 0, 4096, 9e-6)["precision"] == 1       # FP64 below
+    assert hk.params("dht", 0, 4096, 9e-6)["precision"] == 3       # double-float transforms below
+    assert hk.params("dht", 0, 4096, 1e-8)["precision"] == 3
+    assert hk.params("dht", 0, 4096, 1e-11)["precision"] == 3
+    assert hk.params("dht", 0, 4096, 9e-12)["precision"] == 1      # FP64 below 1e-11
+    assert hk.params("dht", 0, 4096, 1e-15)["precision"] == 1
     assert hk.params("dht", 0, 4096, 1e-4, precision="fp64")["precision"] == 1
+    assert hk.params("dht", 0, 4096, 1e-8, precision="fp64")["precision"] == 1
+    assert hk.params("dht", 0, 4096, 1e-4, precision="df64")["precision"] == 3
     with pytest.raises(RuntimeError, match="EUNSUPPORTED"):
         hk.params("dht", 0, 4096, 9e-6, precision="fp32")
+    with pytest.raises(RuntimeError, match="EUNSUPPORTED"):
+        hk.params("dht", 0, 4096, 9e-12, precision="df64")
 
 
 def test_thin_blocks_are_segmented_at_workload_size():
