@@ -208,7 +208,8 @@ class Server:
     ticket; the library's dispatcher batches waiting requests of the same plan, runs batches
     of different plans concurrently on its CUDA streams and writes each result into the array
     ``submit`` returned. ``precision="fp64"`` builds every plan in FP64 (the plain form);
-    ``"auto"`` admits FP32 stages at eps >= 1e-5.
+    ``"auto"`` picks per plan: FP64 below eps = 1e-11, double-float transforms for
+    1e-11 <= eps < 1e-5 and FP32 stages at eps >= 1e-5.
     """
 
     def __init__(self, streams=4, max_batch=64, use_graphs=False, precision="auto", memory_cap=0, pack=True):

@@ -53,6 +53,9 @@ struct DevicePlan {
   float* rf = nullptr;     // FP32 plans: r_k, omega_n and the J table in single precision
   float* omf = nullptr;
   float* jtabf = nullptr;
+  float2* rdf = nullptr;   // DF64 plans: r_k, omega_n and the J table as (high, low) float pairs
+  float2* omdf = nullptr;
+  float2* jtabdf = nullptr;
   NearItem* items = nullptr;
   int64_t nitems = 0;
   NearRow* mrows = nullptr;
@@ -75,6 +78,7 @@ struct DevicePlan {
   double* vinv = nullptr;     // DHT plans, first inverse call: v_n = 2 / J_1(j_{0,n})^2
   double* inv_stage = nullptr;  // v o f for the inverse ([max_nrhs][N])
   float* cf = nullptr;   // FP32 plans: the coefficients rounded to FP32 [max_nrhs][N]
+  float2* cdf = nullptr; // DF64 plans: the coefficients as (high, low) float pairs [max_nrhs][N]
   size_t bytes = 0;
   std::vector<void*> allocs;
   // stage statistics (hankel_plan_set_timing / hankel_plan_stage_stats)
@@ -228,6 +232,20 @@ int dev_plan_create(hankel_plan_s* p) {
     HK_TRY(upload(d, &d->omf, tf.data(), N));
     for (size_t i = 0; i < hp.jtab.size(); ++i) tf[i] = (float)hp.jtab[i];
     HK_TRY(upload(d, &d->jtabf, tf.data(), hp.jtab.size()));
+  }
+  if (d->df64) {
+    std::vector<float2> tp(std::max<size_t>((size_t)N, hp.jtab.size()));
+    auto pair = [](double x) {
+      const float h = (float)x;
+      return make_float2(h, (float)(x - (double)h));
+    };
+    for (int64_t i = 0; i < N; ++i) tp[i] = pair(hp.r_true[i]);
+    HK_TRY(upload(d, &d->rdf, tp.data(), N));
+    for (int64_t i = 0; i < N; ++i) tp[i] = pair(hp.om_true[i]);
+    HK_TRY(upload(d, &d->omdf, tp.data(), N));
+    for (size_t i = 0; i < hp.jtab.size(); ++i) tp[i] = pair(hp.jtab[i]);
+    HK_TRY(upload(d, &d->jtabdf, tp.data(), hp.jtab.size()));
+    HK_TRY(dalloc(d, &d->cdf, (size_t)hp.opt.max_nrhs * N));
   }
 
 
@@ -448,7 +466,7 @@ int run_block(DevicePlan* d, const DevBlock& db, const double* c, int64_t ldc, d
     {
       StageScope sc(d, HANKEL_STAGE_GEN, st, record);
       GenArgs ga{A, b.F, b.C, b.n0, rowseg ? b.S : b.C, rowseg ? b.nseg : 1, nc, c0, db.nl, c, ldc, d->cf,
-                 d->hpN, db.Vt};
+                 d->hpN, d->cdf, db.Vt};
       launch_gen<C>(ga, st);
       HK_LAUNCHED();
       sc.done(1, 0.0, 0.0);
@@ -512,9 +530,19 @@ int run_all(DevicePlan* d, const HostPlan& hp, const double* c, int64_t ldc, dou
     HK_LAUNCHED();
     sc.done(1, 0.0, 0.0);
   }
+  if (d->cdf) {
+    // DF64 plans: the coefficients split once into float pairs, for the near field and generation
+    StageScope sc(d, HANKEL_STAGE_GEN, st, record);
+    launch_coeffs_df64(c, ldc, d->cdf, d->hpN, nrhs, st);
+    HK_LAUNCHED();
+    sc.done(1, 0.0, 0.0);
+  }
   {
     StageScope sc(d, HANKEL_STAGE_NEAR, st, record);
-    if (d->fp32)
+    if (d->cdf)
+      launch_near_df(d->items, d->nitems, d->mrows, d->nmrows, d->nend, d->hpN, (double*)partial, nrhs, d->cdf, f,
+                     ldf, d->rdf, d->omdf, d->jtabdf, hp.jt_n, hp.jt_deg, st);
+    else if (d->fp32)
       launch_near<float>(d->items, d->nitems, d->mrows, d->nmrows, d->nend, d->hpN, (float*)partial, nrhs, c, ldc,
                          d->cf, f, ldf, d->rf, d->omf, d->jtabf, hp.jt_n, hp.jt_deg, st);
     else

@@ -44,7 +44,19 @@ __global__ void __launch_bounds__(256) k_gen(GenArgs a) {
     const int64_t nlo = sg * a.S;             // first column offset of this segment
     const int64_t lim = min(a.S, a.C - nlo);  // points t < lim carry data, the rest is padding
     const C* vr = Vt + li * a.C + nlo;
-    if (std::is_same<C, float2>::value) {
+    if constexpr (std::is_same<C, df64c>::value) {
+      const float2* cr = a.cdf + rhs * a.ldcf + (a.n0 - 1 + nlo);
+      for (int64_t t = t0; t < a.F; t += dt) {
+        C v = mkc(df64(0.0f, 0.0f), df64(0.0f, 0.0f));
+        if (t < lim) {
+          const float2 cc2 = __ldg(&cr[t]);
+          const df64 cv(cc2.x, cc2.y);
+          const C x = ldgc(&vr[t]);
+          v = mkc(cv * x.x, cv * x.y);
+        }
+        A[t] = v;
+      }
+    } else if constexpr (std::is_same<C, float2>::value) {
       const float* cr = a.cf + rhs * a.ldcf + (a.n0 - 1 + nlo);
       for (int64_t t = t0; t < a.F; t += dt) {
         C v = mkc((R)0, (R)0);
@@ -243,6 +255,16 @@ __global__ void __launch_bounds__(256) k_coeffs_f32(const double* __restrict__ c
   }
 }
 
+__global__ void __launch_bounds__(256) k_coeffs_df64(const double* __restrict__ c, int64_t ldc, float2* cd,
+                                                    int64_t N, int64_t total) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / N, i = e - r * N;
+    const double x = c[r * ldc + i];
+    const float h = (float)x;
+    cd[e] = make_float2(h, (float)(x - (double)h));
+  }
+}
+
 __global__ void __launch_bounds__(256) k_diag_scale(const double* x, int64_t ldx, const double* __restrict__ v,
                                                     double scale, double* out, int64_t ldo, int64_t N, int64_t total) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
@@ -297,6 +319,11 @@ void launch_diag_scale(const double* x, int64_t ldx, const double* v, double sca
 void launch_coeffs_f32(const double* c, int64_t ldc, float* cf, int64_t N, int nrhs, cudaStream_t st) {
   const int64_t total = N * nrhs;
   k_coeffs_f32<<<grid1d(total), 256, 0, st>>>(c, ldc, cf, N, total);
+}
+
+void launch_coeffs_df64(const double* c, int64_t ldc, float2* cd, int64_t N, int nrhs, cudaStream_t st) {
+  const int64_t total = N * (int64_t)nrhs;
+  k_coeffs_df64<<<grid1d(total), 256, 0, st>>>(c, ldc, cd, N, total);
 }
 
 template void launch_block_tables<double2>(const BlockTabArgs&, cudaStream_t);

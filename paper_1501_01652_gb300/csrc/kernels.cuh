@@ -76,6 +76,7 @@ struct GenArgs {
   int64_t ldc;
   const float* cf;    // FP32 plans: coefficients rounded to FP32, cf[rhs * ldcf + n-1]
   int64_t ldcf;
+  const float2* cdf;  // DF64 plans: coefficients as (high, low) float pairs, cdf[rhs * ldcf + n-1]
   const void* Vt;     // [ncols][C] block column table (double2 or float2)
 };
 
@@ -122,6 +123,8 @@ void launch_diag_scale(const double* x, int64_t ldx, const double* v, double sca
                        int64_t N, int nrhs, cudaStream_t st);
 // cf[r * N + i] = (float) c[r * ldc + i] for r < nrhs, i < N.
 void launch_coeffs_f32(const double* c, int64_t ldc, float* cf, int64_t N, int nrhs, cudaStream_t st);
+// cd[r * N + i] = (h, l): h = (float) c[r * ldc + i], l = (float)(c - h), for r < nrhs, i < N.
+void launch_coeffs_df64(const double* c, int64_t ldc, float2* cd, int64_t N, int nrhs, cudaStream_t st);
 
 // Convolution kernels of the segments of a block: for y < nseg and t < F,
 // hh[y*F + t] = exp(-i pi D^2 / (2E)), D = Ua (t - (Cc-1) + (k0 + y dk) - (n0 + y dn)) + Ub - Vb
@@ -158,5 +161,13 @@ template <class R>
 void launch_near(const NearItem* items, int64_t nitems, const NearRow* mrows, int64_t nmrows, const int64_t* nend,
                  int64_t N, R* partial, int nrhs, const double* c, int64_t ldc, const float* cf, double* f,
                  int64_t ldf, const R* r, const R* om, const R* jtab, int64_t jt_n, int deg, cudaStream_t st);
+
+// Near field of DF64 plans in double-float on the FP32 pipe: r, om and jtab hold (high, low)
+// float pairs of the FP64 tables, cd the coefficients as pairs ([nrhs][N]); partial sums and
+// outputs are FP64.
+void launch_near_df(const NearItem* items, int64_t nitems, const NearRow* mrows, int64_t nmrows,
+                    const int64_t* nend, int64_t N, double* partial, int nrhs, const float2* cd, double* f,
+                    int64_t ldf, const float2* r, const float2* om, const float2* jtab, int64_t jt_n, int deg,
+                    cudaStream_t st);
 
 }  // namespace hk

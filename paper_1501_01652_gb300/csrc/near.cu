@@ -68,6 +68,101 @@ __global__ void __launch_bounds__(256) k_near(const NearItem* __restrict__ items
   }
 }
 
+// Double-float near field (DF64 plans, 1e-11 <= eps < 1e-5). r_k, omega_n, the table and the
+// coefficients are (h, l) pairs of floats (about 48 significant bits), and every step runs on
+// the FP32 pipe:
+//  * z = r_k omega_n as an unnormalised pair (the exact product of the high parts plus the
+//    cross terms);
+//  * the interval from z.h, and d = z - centre with the rounding of z.h - centre kept (two-sum);
+//  * Taylor steps of degree >= 4 in float (their terms are below 16^-4 / 4! of the total, so
+//    float rounding there stays under 1e-13), the last four steps in double-float;
+//  * per vector, the exact product J.h c.h (FMA) and the cross terms, summed into a float sum
+//    whose every rounding error is kept in a second float (two-sum), renormalised every 16
+//    columns.
+__device__ __forceinline__ df64 table_j_df(const float2* __restrict__ jtab, int64_t jt_n, int deg, float zh,
+                                           float zl) {
+  int64_t i = (int64_t)(zh * (float)kJTabSub);
+  i = i < 0 ? 0 : (i >= jt_n ? jt_n - 1 : i);
+  const float ctr = ((float)i + 0.5f) * (1.0f / (float)kJTabSub);
+  const float s = zh - ctr;
+  const float bb = s - zh;
+  const float err = (zh - (s - bb)) + (-ctr - bb);
+  const df64 d = fast_two_sum(s, err + zl);
+  const float2* t = jtab + i * (deg + 1);
+  float v = __ldg(&t[deg]).x;
+  int j = deg - 1;
+  for (; j >= 4; --j) v = fmaf(v, d.h, __ldg(&t[j]).x);
+  df64 w(v, 0.0f);
+  if (deg < 4) {
+    const float2 a = __ldg(&t[deg]);
+    w = df64(a.x, a.y);
+    j = deg - 1;
+  }
+  for (; j >= 0; --j) {
+    const float2 a = __ldg(&t[j]);
+    w = fmar(w, d, df64(a.x, a.y));
+  }
+  return w;
+}
+
+template <int G>
+__global__ void __launch_bounds__(256) k_near_df(const NearItem* __restrict__ items, int64_t nitems,
+                                                 const int64_t* __restrict__ nend, int64_t N, double* partial,
+                                                 int nrhs, const float2* __restrict__ cd, double* f, int64_t ldf,
+                                                 const float2* __restrict__ r_true, const float2* __restrict__ om_true,
+                                                 const float2* __restrict__ jtab, int64_t jt_n, int deg) {
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= nitems) return;
+  const NearItem it = items[warp];
+  const int64_t k = it.k0 + lane;
+  if (k > N) return;
+  const int64_t nhi = min(it.n1, nend[k - 1]);
+  const float2 r = r_true[k - 1];
+  for (int r0 = 0; r0 < nrhs; r0 += G) {
+    float hi[G], lo[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) hi[g] = lo[g] = 0.0f;
+    for (int64_t n = it.n0; n <= nhi; ++n) {
+      const float2 om = __ldg(&om_true[n - 1]);
+      const float zh = r.x * om.x;
+      float zl = fmaf(r.x, om.x, -zh);
+      zl = fmaf(r.x, om.y, zl);
+      zl = fmaf(r.y, om.x, zl);
+      const df64 J = table_j_df(jtab, jt_n, deg, zh, zl);
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        if (r0 + g < nrhs) {
+          const float2 cv = __ldg(&cd[(int64_t)(r0 + g) * N + n - 1]);
+          const float p = J.h * cv.x;
+          float e = fmaf(J.h, cv.x, -p);
+          e = fmaf(J.h, cv.y, e);
+          e = fmaf(J.l, cv.x, e);
+          const float s = hi[g] + p;
+          const float bb = s - hi[g];
+          lo[g] += ((hi[g] - (s - bb)) + (p - bb)) + e;
+          hi[g] = s;
+        }
+      }
+      if (((n - it.n0) & 15) == 15) {
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+          const df64 q = fast_two_sum(hi[g], lo[g]);
+          hi[g] = q.h;
+          lo[g] = q.l;
+        }
+      }
+    }
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      if (r0 + g >= nrhs) break;
+      const double v = (double)hi[g] + (double)lo[g];
+      if (it.slot < 0) f[(int64_t)(r0 + g) * ldf + k - 1] = v;
+      else partial[(it.slot + (int64_t)lane * it.ntile + it.t) * nrhs + r0 + g] = v;
+    }
+  }
+}
+
 template <class R>
 __global__ void k_near_combine(const NearRow* __restrict__ rows, int64_t nrows, const R* __restrict__ partial,
                                int nrhs, double* f, int64_t ldf) {
@@ -111,6 +206,29 @@ void launch_near(const NearItem* items, int64_t nitems, const NearRow* mrows, in
   if (nmrows > 0) {
     const int64_t n = nmrows * nrhs;
     k_near_combine<R><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(mrows, nmrows, partial, nrhs, f, ldf);
+  }
+}
+
+void launch_near_df(const NearItem* items, int64_t nitems, const NearRow* mrows, int64_t nmrows,
+                    const int64_t* nend, int64_t N, double* partial, int nrhs, const float2* cd, double* f,
+                    int64_t ldf, const float2* r, const float2* om, const float2* jtab, int64_t jt_n, int deg,
+                    cudaStream_t st) {
+  const int64_t threads = nitems * 32;
+  const unsigned grid = (unsigned)((threads + 255) / 256);
+  if (nrhs <= 1)
+    k_near_df<1><<<grid, 256, 0, st>>>(items, nitems, nend, N, partial, nrhs, cd, f, ldf, r, om, jtab, jt_n, deg);
+  else if (nrhs <= 2)
+    k_near_df<2><<<grid, 256, 0, st>>>(items, nitems, nend, N, partial, nrhs, cd, f, ldf, r, om, jtab, jt_n, deg);
+  else if (nrhs <= 4)
+    k_near_df<4><<<grid, 256, 0, st>>>(items, nitems, nend, N, partial, nrhs, cd, f, ldf, r, om, jtab, jt_n, deg);
+  else if (nrhs <= 8)
+    k_near_df<8><<<grid, 256, 0, st>>>(items, nitems, nend, N, partial, nrhs, cd, f, ldf, r, om, jtab, jt_n, deg);
+  else
+    k_near_df<kMaxRhsGroup><<<grid, 256, 0, st>>>(items, nitems, nend, N, partial, nrhs, cd, f, ldf, r, om, jtab,
+                                                  jt_n, deg);
+  if (nmrows > 0) {
+    const int64_t n = nmrows * nrhs;
+    k_near_combine<double><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(mrows, nmrows, partial, nrhs, f, ldf);
   }
 }
 

@@ -138,6 +138,23 @@ def test_df64_transforms(task, nu, kind, eps):
     assert np.all(np.abs(f - g) <= 1e-12 * l1)
 
 
+@pytest.mark.parametrize("eps", [1e-6, 1e-11])
+def test_df64_sparse_vectors(eps):
+    # a few nonzero coefficients make ||c||_2 close to ||c||_1, the hardest input for
+    # reduced-precision stages; 16 vectors run the near field's widest vector group
+    N = 9000
+    rng = np.random.default_rng(7400)
+    c = np.zeros((16, N))
+    for r in range(16):
+        idx = rng.choice(N, size=1 + r % 4, replace=False)
+        c[r, idx] = rng.standard_normal(idx.size)
+    f, plan = _run("dht", 0, N, eps, c)
+    assert plan.info["precision"] == 3
+    ref = oracle.transform("dht", 0, N, c)
+    l1 = np.abs(c).sum(axis=1, keepdims=True)
+    assert np.all(np.abs(f - ref) <= 10 * eps * l1)
+
+
 @pytest.mark.parametrize("eps", [1e-4, 1e-5])
 def test_fp32_workload_size_sampled_rows(eps):
     N = 2 ** 20
