@@ -157,7 +157,7 @@ def workload_config(args):
     B = args.nrhs
     return {"workload": "dht0_N%d_eps%s_batch%d" % (args.N, "+".join(args.eps.split(",")), B),
             "N": args.N, "eps": [float(e) for e in args.eps.split(",")], "batch": B,
-            "form": "served/batched: %d vectors per execution per plan, precision by eps (FP64 below 1e-5)" % B,
+            "form": "served/batched: %d vectors per execution per plan, precision by eps (FP64 below 1e-11, double-float transforms below 1e-5, FP32 above)" % B,
             "l2": "flushed between timed steps (256 MB write)", "coefficients": "N(0,1) seeded"}
 
 
@@ -319,7 +319,7 @@ def run_ours(args):
         for p in plain:
             p.destroy()
 
-    # served form: batches of B vectors per plan, precision chosen by eps (FP64 below 1e-5)
+    # served form: batches of B vectors per plan, precision chosen by eps
     cB_host = coefficients("normal", N, B, seed_for(4, 100 + rank))
     cB = torch.from_numpy(cB_host).to(dev)
     plans = [hk.Plan("dht", 0, N, e, max_nrhs=B) for e in eps_list]

@@ -248,10 +248,12 @@ int hankel_plan_near_prefix(hankel_plan_t p, int64_t k, int64_t* nend);
 /* Execution stages of a plan, for hankel_plan_stage_stats(). */
 enum hankel_stage {
   HANKEL_STAGE_NEAR = 0,      /* near-field direct sum (and its partial-sum combine) */
-  HANKEL_STAGE_GEN = 1,       /* far-field column generation */
-  HANKEL_STAGE_FFT = 2,       /* forward and inverse multi-column FFT passes */
+  HANKEL_STAGE_GEN = 1,       /* per-execution coefficient conversion of FP32 and DF64 plans (the
+                                 far-field column generation itself runs in the first forward FFT loads) */
+  HANKEL_STAGE_FFT = 2,       /* forward and inverse multi-column FFT passes, with the column generation
+                                 and the single spectrum products folded into their first loads */
   HANKEL_STAGE_POINTWISE = 3, /* summed products of segment spectra and chirp spectra (column-segmented
-                                 blocks); the other products are folded into the inverse FFT loads */
+                                 blocks) */
   HANKEL_STAGE_OUT = 4,       /* row weights and accumulation into f */
   HANKEL_STAGE_COUNT = 5
 };
@@ -295,8 +297,8 @@ typedef struct {
   int streams;        /* CUDA streams, i.e. batches in flight at once (default 4, at most 16) */
   int max_batch;      /* most coefficient vectors packed into one execution (default 64) */
   int use_graphs;     /* 1: replay each (plan, batch size, stream) launch sequence from a captured CUDA graph */
-  int precision;      /* precision every plan is built with: HANKEL_PREC_AUTO (FP32 stages at eps >= 1e-5)
-                         or HANKEL_PREC_FP64 */
+  int precision;      /* precision every plan is built with: HANKEL_PREC_AUTO (chosen per eps as for a
+                         plan: FP64, DF64 transforms or FP32 stages) or HANKEL_PREC_FP64 */
   int pack_requests;  /* 1: pack waiting requests of one plan into one execution; 0: one request each */
 } hankel_server_options;
 

@@ -24,6 +24,11 @@ template <class C>
 __device__ __forceinline__ C cmul(C a, C b) {
   return mkc(fmar(a.x, b.x, -a.y * b.y), fmar(a.x, b.y, a.y * b.x));
 }
+// acc + a b
+template <class C>
+__device__ __forceinline__ C cmac(C a, C b, C acc) {
+  return mkc(fmar(a.x, b.x, fmar(-a.y, b.y, acc.x)), fmar(a.x, b.y, fmar(a.y, b.x, acc.y)));
+}
 
 // Double-float numbers (a value as the unevaluated sum h + l of two floats, |l| <= ulp(h)/2)
 // for the transform stages of DF64 plans: about 48 significant bits from FP32 arithmetic,

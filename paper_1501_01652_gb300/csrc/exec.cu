@@ -463,19 +463,15 @@ int run_block(DevicePlan* d, const DevBlock& db, const double* c, int64_t ldc, d
     const int nc = (int)std::min<int64_t>(cap, total - c0);
     const int64_t nfwd = rowseg ? (int64_t)nc * b.nseg : nc;  // forward transforms
     const int64_t ninv = colseg ? (int64_t)nc * b.nseg : nc;  // inverse transforms
-    {
-      StageScope sc(d, HANKEL_STAGE_GEN, st, record);
-      GenArgs ga{A, b.F, b.C, b.n0, rowseg ? b.S : b.C, rowseg ? b.nseg : 1, nc, c0, db.nl, c, ldc, d->cf,
-                 d->hpN, d->cdf, db.Vt};
-      launch_gen<C>(ga, st);
-      HK_LAUNCHED();
-      sc.done(1, 0.0, 0.0);
-    }
     C* res = nullptr;
     {
+      // column generation happens in the first loads of the forward transform
       StageScope sc(d, HANKEL_STAGE_FFT, st, record);
       int np = 0;
-      HK_TRY(run_fft<C>(A, B, b.logF, (int)nfwd, false, tw, d->logFmax, st, &res, &np));
+      const void* coef = d->fp32 ? (const void*)d->cf : d->df64 ? (const void*)d->cdf : (const void*)c;
+      const FftGen gen{rowseg ? b.nseg : 1, rowseg ? b.S : b.C, b.C, b.n0, c0, db.nl, coef,
+                       (d->fp32 || d->df64) ? d->hpN : ldc, db.Vt};
+      HK_TRY(run_fft<C>(A, B, b.logF, (int)nfwd, false, tw, d->logFmax, st, &res, &np, nullptr, 1, &gen));
       HK_LAUNCHED();
       sc.done(np, 5.0 * (double)b.F * (double)b.logF * (double)nfwd, 0.0, 2.0 * sizeof(C) * (double)b.F * nfwd * np);
     }

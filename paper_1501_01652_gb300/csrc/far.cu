@@ -1,4 +1,6 @@
-// Far-field column generation and row accumulation, and the plan-time block tables.
+// Far-field row accumulation, the overlap-add of column segments, the coefficient conversions
+// and the plan-time block tables (column generation runs inside the first forward FFT loads,
+// fft.cu).
 //
 // Column side (Sections 4.1, 5.1, 6): stacked column li of a block holds
 //   g_li(n) = c_n V_li(n) exp(i pi V_n^2/(2E)),
@@ -26,60 +28,6 @@ __device__ __forceinline__ double ipow(double x, int e) {
     e >>= 1;
   }
   return r;
-}
-
-// One CTA row (blockIdx.y) per stacked column at a time, so the column's indices are derived
-// once per column; the threads of the row stride over the F points of the column.
-template <class C>
-__global__ void __launch_bounds__(256) k_gen(GenArgs a) {
-  typedef typename RealOf<C>::type R;
-  const int64_t ncolumns = (int64_t)a.nc * a.nsegc;
-  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, dt = (int64_t)gridDim.x * blockDim.x;
-  const C* Vt = reinterpret_cast<const C*>(a.Vt);
-  for (int64_t y = blockIdx.y; y < ncolumns; y += gridDim.y) {
-    C* A = reinterpret_cast<C*>(a.A) + y * a.F;
-    const int64_t cc = y / a.nsegc, sg = y - cc * a.nsegc;
-    const int64_t g = a.c0 + cc;
-    const int64_t rhs = g / a.ncols, li = g - rhs * a.ncols;
-    const int64_t nlo = sg * a.S;             // first column offset of this segment
-    const int64_t lim = min(a.S, a.C - nlo);  // points t < lim carry data, the rest is padding
-    const C* vr = Vt + li * a.C + nlo;
-    if constexpr (std::is_same<C, df64c>::value) {
-      const float2* cr = a.cdf + rhs * a.ldcf + (a.n0 - 1 + nlo);
-      for (int64_t t = t0; t < a.F; t += dt) {
-        C v = mkc(df64(0.0f, 0.0f), df64(0.0f, 0.0f));
-        if (t < lim) {
-          const float2 cc2 = __ldg(&cr[t]);
-          const df64 cv(cc2.x, cc2.y);
-          const C x = ldgc(&vr[t]);
-          v = mkc(cv * x.x, cv * x.y);
-        }
-        A[t] = v;
-      }
-    } else if constexpr (std::is_same<C, float2>::value) {
-      const float* cr = a.cf + rhs * a.ldcf + (a.n0 - 1 + nlo);
-      for (int64_t t = t0; t < a.F; t += dt) {
-        C v = mkc((R)0, (R)0);
-        if (t < lim) {
-          const R cv = (R)__ldg(&cr[t]);
-          const C x = vr[t];
-          v = mkc(cv * x.x, cv * x.y);
-        }
-        A[t] = v;
-      }
-    } else {
-      const double* cr = a.c + rhs * a.ldc + (a.n0 - 1 + nlo);
-      for (int64_t t = t0; t < a.F; t += dt) {
-        C v = mkc((R)0, (R)0);
-        if (t < lim) {
-          const R cv = (R)cr[t];
-          const C x = vr[t];
-          v = mkc(cv * x.x, cv * x.y);
-        }
-        A[t] = v;
-      }
-    }
-  }
 }
 
 // Thread per output row and CTA row (blockIdx.y) per right-hand side of the chunk: the thread
@@ -112,6 +60,7 @@ __global__ void __launch_bounds__(256) k_out(OutArgs a) {
     a.f[rhs * a.ldf + i] += (double)fmar(wu.x, ar, -wu.y * ai);
   }
 }
+
 
 // Overlap-add of column segments: out[cc][t] = sum_s in[cc*nseg + s][t] H[s][t]. A CTA covers
 // kMacPts consecutive points of one column; its kMacLanes thread rows split the segments
@@ -280,22 +229,6 @@ unsigned grid1d(int64_t n) {
 
 }  // namespace
 
-// Each thread writes up to kGenPts points of a column.
-constexpr int64_t kGenPts = 4;
-
-template <class C>
-void launch_gen(const GenArgs& a, cudaStream_t st) {
-  const int64_t ny = std::min<int64_t>((int64_t)a.nc * a.nsegc, 65535);
-  dim3 grid((unsigned)((a.F + 256 * kGenPts - 1) / (256 * kGenPts)), (unsigned)ny);
-  k_gen<C><<<grid, 256, 0, st>>>(a);
-}
-
-template <class C>
-void launch_seg_mac(const C* in, const C* H, C* out, int64_t F, int64_t nseg, int nc, cudaStream_t st) {
-  // F >= 64 is a multiple of kMacPts
-  const int64_t blocks = (F / kMacPts) * nc;
-  k_seg_mac<C><<<(unsigned)blocks, kMacPts * kMacLanes, 0, st>>>(in, H, out, F, nseg);
-}
 
 template <class C>
 void launch_out(const OutArgs& a, cudaStream_t st) {
@@ -316,6 +249,13 @@ void launch_diag_scale(const double* x, int64_t ldx, const double* v, double sca
   k_diag_scale<<<grid1d(total), 256, 0, st>>>(x, ldx, v, scale, out, ldo, N, total);
 }
 
+template <class C>
+void launch_seg_mac(const C* in, const C* H, C* out, int64_t F, int64_t nseg, int nc, cudaStream_t st) {
+  // F >= 64 is a multiple of kMacPts
+  const int64_t blocks = (F / kMacPts) * nc;
+  k_seg_mac<C><<<(unsigned)blocks, kMacPts * kMacLanes, 0, st>>>(in, H, out, F, nseg);
+}
+
 void launch_coeffs_f32(const double* c, int64_t ldc, float* cf, int64_t N, int nrhs, cudaStream_t st) {
   const int64_t total = N * nrhs;
   k_coeffs_f32<<<grid1d(total), 256, 0, st>>>(c, ldc, cf, N, total);
@@ -326,17 +266,14 @@ void launch_coeffs_df64(const double* c, int64_t ldc, float2* cd, int64_t N, int
   k_coeffs_df64<<<grid1d(total), 256, 0, st>>>(c, ldc, cd, N, total);
 }
 
+template void launch_seg_mac<df64c>(const df64c*, const df64c*, df64c*, int64_t, int64_t, int, cudaStream_t);
+template void launch_seg_mac<double2>(const double2*, const double2*, double2*, int64_t, int64_t, int, cudaStream_t);
+template void launch_seg_mac<float2>(const float2*, const float2*, float2*, int64_t, int64_t, int, cudaStream_t);
 template void launch_block_tables<double2>(const BlockTabArgs&, cudaStream_t);
 template void launch_block_tables<float2>(const BlockTabArgs&, cudaStream_t);
 template void launch_block_tables<df64c>(const BlockTabArgs&, cudaStream_t);
-template void launch_gen<df64c>(const GenArgs&, cudaStream_t);
 template void launch_out<df64c>(const OutArgs&, cudaStream_t);
-template void launch_seg_mac<df64c>(const df64c*, const df64c*, df64c*, int64_t, int64_t, int, cudaStream_t);
-template void launch_gen<double2>(const GenArgs&, cudaStream_t);
-template void launch_gen<float2>(const GenArgs&, cudaStream_t);
 template void launch_out<double2>(const OutArgs&, cudaStream_t);
 template void launch_out<float2>(const OutArgs&, cudaStream_t);
-template void launch_seg_mac<double2>(const double2*, const double2*, double2*, int64_t, int64_t, int, cudaStream_t);
-template void launch_seg_mac<float2>(const float2*, const float2*, float2*, int64_t, int64_t, int, cudaStream_t);
 
 }  // namespace hk

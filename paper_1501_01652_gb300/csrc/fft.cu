@@ -39,6 +39,42 @@ __device__ __forceinline__ void bfly2(C& a0, C& a1, C w) {
   a0 = y0;
 }
 
+// Fused column generation (FftGen): where column y of the chunk takes its points from.
+template <class C>
+struct GenCol {
+  const C* v;   // the column's table row, from its segment's first point
+  int64_t cb;   // index of the segment's first coefficient
+  int64_t lim;  // points that carry data
+};
+template <class C>
+__device__ __forceinline__ GenCol<C> gen_col(const FftGen& g, uint64_t y) {
+  // chunk columns and stacked-column indices stay below 2^31
+  const uint32_t cc = (uint32_t)y / (uint32_t)g.nsegc;
+  const int64_t sg = (int64_t)y - (int64_t)cc * g.nsegc;
+  const uint32_t gi = (uint32_t)(g.c0 + cc);
+  const uint32_t rhs = gi / (uint32_t)g.ncols, li = gi - rhs * (uint32_t)g.ncols;
+  const int64_t nlo = sg * g.S;
+  GenCol<C> r;
+  r.v = reinterpret_cast<const C*>(g.Vt) + (int64_t)li * g.C + nlo;
+  r.cb = (int64_t)rhs * g.ldc + g.n0 - 1 + nlo;
+  r.lim = min(g.S, g.C - nlo);
+  return r;
+}
+// coefficient i (in the plan's coefficient format) times the table value v
+__device__ __forceinline__ double2 coef_times(const void* p, int64_t i, double2 v) {
+  const double c = __ldg(reinterpret_cast<const double*>(p) + i);
+  return make_double2(c * v.x, c * v.y);
+}
+__device__ __forceinline__ float2 coef_times(const void* p, int64_t i, float2 v) {
+  const float c = __ldg(reinterpret_cast<const float*>(p) + i);
+  return make_float2(c * v.x, c * v.y);
+}
+__device__ __forceinline__ df64c coef_times(const void* p, int64_t i, df64c v) {
+  const float2 q = __ldg(reinterpret_cast<const float2*>(p) + i);
+  const df64 c(q.x, q.y);
+  return mkc(c * v.x, c * v.y);
+}
+
 // Twiddle deferral. A pass of radix R multiplies input e of the R-point DFT of sequence
 // (p, q) by the pass twiddle W_F^{pt e} (pt = p s). The pass twiddle is never applied on its
 // own: in a Stockham sub-stage of stride s_k, the inputs e = qq + s_k (Q pp + j) of a butterfly
@@ -141,7 +177,7 @@ template <int LOGR, bool INV, class C>
 __global__ void __launch_bounds__(kFftThreads) k_fft_pass_reg(const C* __restrict__ src, C* __restrict__ dst,
                                                               int logF, int logS, const C* __restrict__ tw,
                                                               int logFmax, const C* __restrict__ hmul,
-                                                              int64_t nseg) {
+                                                              int64_t nseg, FftGen gen) {
   constexpr int R = 1 << LOGR;
   constexpr int L1 = (LOGR + 1) / 2, L2 = LOGR - L1;
   constexpr int Q1 = 1 << L1, Q2 = 1 << L2;
@@ -172,9 +208,20 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_pass_reg(const C* __restric
     if (act1) {
       const uint32_t p = pi0 >> logS, q0 = pi0 & (s - 1);
       const uint32_t off = q0 + ((p << LOGR) << logS) + i;
-      const C* xb = x + off;
+      if (gen.coef) {
+        // first pass of a forward transform with generated input (p = 0)
+        const GenCol<C> gc = gen_col<C>(gen, col);
 #pragma unroll
-      for (int j = 0; j < Q1; ++j) a[j] = xb[(bf + Q2 * j) << logS];
+        for (int j = 0; j < Q1; ++j) {
+          const uint32_t t = off + ((bf + Q2 * j) << logS);
+          a[j] = (int64_t)t < gc.lim ? coef_times(gen.coef, gc.cb + t, ldgc(gc.v + t))
+                                     : mkc((typename RealOf<C>::type)0, (typename RealOf<C>::type)0);
+        }
+      } else {
+        const C* xb = x + off;
+#pragma unroll
+        for (int j = 0; j < Q1; ++j) a[j] = xb[(bf + Q2 * j) << logS];
+      }
       if (hc) {
 #pragma unroll
         for (int j = 0; j < Q1; ++j) a[j] = cmul(a[j], ldgc(&hc[off + ((bf + Q2 * j) << logS)]));
@@ -287,7 +334,7 @@ template <int LOGF, bool INV, class C>
 __global__ void __launch_bounds__(SmallSplit<LOGF>::NT) k_fft_small(const C* __restrict__ src, C* __restrict__ dst,
                                                                       int64_t ncols, const C* __restrict__ tw,
                                                                       int logFmax, const C* __restrict__ hmul,
-                                                                      int64_t nseg) {
+                                                                      int64_t nseg, FftGen gen) {
   typedef SmallSplit<LOGF> S;
   constexpr int F = 1 << LOGF;
   constexpr uint32_t Fp = F + F / 16;
@@ -299,7 +346,27 @@ __global__ void __launch_bounds__(SmallSplit<LOGF>::NT) k_fft_small(const C* __r
   const C* x = src + col0 * F;
   const int64_t avail = (ncols - col0) * F;  // points of this CTA's columns that exist
   C t[PER];
-  if (hmul) {
+  if (gen.coef) {
+    // generated input: per column of the CTA, its table row, first coefficient and length
+    __shared__ const C* gv[NCOL];
+    __shared__ int64_t gcb[NCOL];
+    __shared__ int64_t glim[NCOL];
+    if (threadIdx.x < NCOL) {
+      const GenCol<C> q = gen_col<C>(gen, (uint64_t)(col0 + threadIdx.x));
+      gv[threadIdx.x] = q.v;
+      gcb[threadIdx.x] = q.cb;
+      glim[threadIdx.x] = q.lim;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const uint32_t idx = threadIdx.x + u * S::NT;
+      const uint32_t c = idx >> LOGF, e = idx & (F - 1);
+      t[u] = ((int64_t)idx < avail && (int64_t)e < glim[c])
+                 ? coef_times(gen.coef, gcb[c] + e, ldgc(gv[c] + e))
+                 : mkc((typename RealOf<C>::type)0, (typename RealOf<C>::type)0);
+    }
+  } else if (hmul) {
     // column col0 + c is source column (col0 + c) / nseg times spectrum (col0 + c) % nseg
     __shared__ int64_t scol[NCOL];
     __shared__ int64_t sseg[NCOL];
@@ -341,7 +408,7 @@ __global__ void __launch_bounds__(SmallSplit<LOGF>::NT) k_fft_small(const C* __r
 
 template <int LOGF, bool INV, class C>
 void launch_small(const C* src, C* dst, int ncols, const C* tw, int logFmax, const C* hmul, int64_t nseg,
-                  cudaStream_t st) {
+                  const FftGen& gen, cudaStream_t st) {
   constexpr int F = 1 << LOGF;
   constexpr int NCOL = kSmallPts / F;
   const size_t smem = (size_t)NCOL * (F + F / 16) * sizeof(C);
@@ -352,26 +419,26 @@ void launch_small(const C* src, C* dst, int ncols, const C* tw, int logFmax, con
   }
   const int64_t grid = ((int64_t)ncols + NCOL - 1) / NCOL;
   k_fft_small<LOGF, INV, C><<<(unsigned)grid, SmallSplit<LOGF>::NT, smem, st>>>(src, dst, ncols, tw, logFmax, hmul,
-                                                                                nseg);
+                                                                                nseg, gen);
 }
 
 template <bool INV, class C>
 void launch_small_f(int logF, const C* src, C* dst, int ncols, const C* tw, int logFmax, const C* hmul, int64_t nseg,
-                    cudaStream_t st) {
+                    const FftGen& gen, cudaStream_t st) {
   switch (logF) {
-    case 6: launch_small<6, INV>(src, dst, ncols, tw, logFmax, hmul, nseg, st); break;
-    case 7: launch_small<7, INV>(src, dst, ncols, tw, logFmax, hmul, nseg, st); break;
-    case 8: launch_small<8, INV>(src, dst, ncols, tw, logFmax, hmul, nseg, st); break;
-    case 9: launch_small<9, INV>(src, dst, ncols, tw, logFmax, hmul, nseg, st); break;
-    case 10: launch_small<10, INV>(src, dst, ncols, tw, logFmax, hmul, nseg, st); break;
-    case 11: launch_small<11, INV>(src, dst, ncols, tw, logFmax, hmul, nseg, st); break;
-    default: launch_small<12, INV>(src, dst, ncols, tw, logFmax, hmul, nseg, st); break;
+    case 6: launch_small<6, INV>(src, dst, ncols, tw, logFmax, hmul, nseg, gen, st); break;
+    case 7: launch_small<7, INV>(src, dst, ncols, tw, logFmax, hmul, nseg, gen, st); break;
+    case 8: launch_small<8, INV>(src, dst, ncols, tw, logFmax, hmul, nseg, gen, st); break;
+    case 9: launch_small<9, INV>(src, dst, ncols, tw, logFmax, hmul, nseg, gen, st); break;
+    case 10: launch_small<10, INV>(src, dst, ncols, tw, logFmax, hmul, nseg, gen, st); break;
+    case 11: launch_small<11, INV>(src, dst, ncols, tw, logFmax, hmul, nseg, gen, st); break;
+    default: launch_small<12, INV>(src, dst, ncols, tw, logFmax, hmul, nseg, gen, st); break;
   }
 }
 
 template <int LOGR, bool INV, class C>
 void launch_pass(const C* src, C* dst, int logF, int logS, int ncols, const C* tw, int logFmax, const C* hmul,
-                 int64_t nseg, cudaStream_t st) {
+                 int64_t nseg, const FftGen& gen, cudaStream_t st) {
   constexpr int R = 1 << LOGR;
   const int64_t pairs = ((int64_t)ncols << logF) >> LOGR;
   const int64_t grid = pairs / kTile;
@@ -384,18 +451,19 @@ void launch_pass(const C* src, C* dst, int logF, int logS, int ncols, const C* t
     cudaFuncSetAttribute(k_fft_pass_reg<LOGR, INV, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     configured = true;
   }
-  k_fft_pass_reg<LOGR, INV, C><<<(unsigned)grid, threads, smem, st>>>(src, dst, logF, logS, tw, logFmax, hmul, nseg);
+  k_fft_pass_reg<LOGR, INV, C><<<(unsigned)grid, threads, smem, st>>>(src, dst, logF, logS, tw, logFmax, hmul, nseg,
+                                                                      gen);
 }
 
 template <bool INV, class C>
 void launch_pass_r(int logR, const C* src, C* dst, int logF, int logS, int ncols, const C* tw, int logFmax,
-                   const C* hmul, int64_t nseg, cudaStream_t st) {
+                   const C* hmul, int64_t nseg, const FftGen& gen, cudaStream_t st) {
   // transforms longer than 4096 points split into passes of radix 2^5 .. 2^8
   switch (logR) {
-    case 5: launch_pass<5, INV>(src, dst, logF, logS, ncols, tw, logFmax, hmul, nseg, st); break;
-    case 6: launch_pass<6, INV>(src, dst, logF, logS, ncols, tw, logFmax, hmul, nseg, st); break;
-    case 7: launch_pass<7, INV>(src, dst, logF, logS, ncols, tw, logFmax, hmul, nseg, st); break;
-    default: launch_pass<8, INV>(src, dst, logF, logS, ncols, tw, logFmax, hmul, nseg, st); break;
+    case 5: launch_pass<5, INV>(src, dst, logF, logS, ncols, tw, logFmax, hmul, nseg, gen, st); break;
+    case 6: launch_pass<6, INV>(src, dst, logF, logS, ncols, tw, logFmax, hmul, nseg, gen, st); break;
+    case 7: launch_pass<7, INV>(src, dst, logF, logS, ncols, tw, logFmax, hmul, nseg, gen, st); break;
+    default: launch_pass<8, INV>(src, dst, logF, logS, ncols, tw, logFmax, hmul, nseg, gen, st); break;
   }
 }
 
@@ -466,15 +534,19 @@ void launch_scale_copy(const double2* src, C* dst, int64_t n, double scale, cuda
 
 template <class C>
 int run_fft(C* a, C* b, int logF, int ncols, bool inverse, const C* tw, int logFmax, cudaStream_t st, C** result,
-            int* npasses, const C* hmul, int64_t nseg) {
+            int* npasses, const C* hmul, int64_t nseg, const FftGen* gen) {
   if (logF < 6 || logF > logFmax || nseg < 1) return HANKEL_EINVAL;
+  if (gen && (inverse || hmul || gen->nsegc < 1 || gen->ncols < 1)) return HANKEL_EINVAL;
+  FftGen g0{};
+  if (gen) g0 = *gen;
+  const FftGen none{};
   // the ladder's table for this length: W_F^t at tw[F + t]
   tw += (size_t)1 << logF;
   logFmax = logF;
   if (logF <= kSmallLog) {
     // the whole transform in one launch
-    if (inverse) launch_small_f<true, C>(logF, a, b, ncols, tw, logFmax, hmul, nseg, st);
-    else launch_small_f<false, C>(logF, a, b, ncols, tw, logFmax, hmul, nseg, st);
+    if (inverse) launch_small_f<true, C>(logF, a, b, ncols, tw, logFmax, hmul, nseg, none, st);
+    else launch_small_f<false, C>(logF, a, b, ncols, tw, logFmax, hmul, nseg, g0, st);
     *result = b;
     if (npasses) *npasses = 1;
     return HANKEL_OK;
@@ -493,8 +565,8 @@ int run_fft(C* a, C* b, int logF, int ncols, bool inverse, const C* tw, int logF
     done += lr;
     const int logS = logF - done;
     const C* h = i == 0 ? hmul : nullptr;
-    if (inverse) launch_pass_r<true, C>(lr, src, dst, logF, logS, ncols, tw, logFmax, h, nseg, st);
-    else launch_pass_r<false, C>(lr, src, dst, logF, logS, ncols, tw, logFmax, h, nseg, st);
+    if (inverse) launch_pass_r<true, C>(lr, src, dst, logF, logS, ncols, tw, logFmax, h, nseg, none, st);
+    else launch_pass_r<false, C>(lr, src, dst, logF, logS, ncols, tw, logFmax, h, nseg, i == 0 ? g0 : none, st);
     std::swap(src, dst);
   }
   *result = src;
@@ -503,11 +575,11 @@ int run_fft(C* a, C* b, int logF, int ncols, bool inverse, const C* tw, int logF
 }
 
 template int run_fft<double2>(double2*, double2*, int, int, bool, const double2*, int, cudaStream_t, double2**,
-                              int*, const double2*, int64_t);
+                              int*, const double2*, int64_t, const FftGen*);
 template int run_fft<float2>(float2*, float2*, int, int, bool, const float2*, int, cudaStream_t, float2**, int*,
-                             const float2*, int64_t);
+                             const float2*, int64_t, const FftGen*);
 template int run_fft<df64c>(df64c*, df64c*, int, int, bool, const df64c*, int, cudaStream_t, df64c**, int*,
-                            const df64c*, int64_t);
+                            const df64c*, int64_t, const FftGen*);
 template void launch_scale_copy<double2>(const double2*, double2*, int64_t, double, cudaStream_t);
 template void launch_scale_copy<float2>(const double2*, float2*, int64_t, double, cudaStream_t);
 template void launch_scale_copy<df64c>(const double2*, df64c*, int64_t, double, cudaStream_t);

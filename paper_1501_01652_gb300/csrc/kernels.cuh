@@ -61,25 +61,6 @@ struct ChirpGeom {
   int64_t Ua, Ub, Va, Vb, E, k0, n0, R, C, F;
 };
 
-// Column generation of one chunk of a block: stacked column li of right-hand side rhs is
-// g(n) = c_n * Vt[li][n - n0] (Vt: the block's column functions times its column chirp), cut
-// into segments of S columns each zero-padded to F points.
-struct GenArgs {
-  void* A;            // [nc * nsegc][F] output columns (double2 or float2)
-  int64_t F, C, n0;   // transform length, block columns, first column (1-based)
-  int64_t S;          // columns per segment (C when the columns are not segmented)
-  int64_t nsegc;      // column segments per stacked column (1 when not segmented)
-  int nc;             // columns in this chunk
-  int64_t c0;         // global index of the first column (rhs * ncols + li)
-  int ncols;          // stacked columns (transforms) of the block per right-hand side
-  const double* c;    // FP64 plans: coefficients, c[rhs * ldc + n-1]
-  int64_t ldc;
-  const float* cf;    // FP32 plans: coefficients rounded to FP32, cf[rhs * ldcf + n-1]
-  int64_t ldcf;
-  const float2* cdf;  // DF64 plans: coefficients as (high, low) float pairs, cdf[rhs * ldcf + n-1]
-  const void* Vt;     // [ncols][C] block column table (double2 or float2)
-};
-
 // Row accumulation of one chunk: f_k += Re[ w_U(k) sum_li Ut[li][k - k0] y_li(k) ].
 struct OutArgs {
   const void* Y;      // [nc * nsegr][F] inverse-transformed columns (double2 or float2)
@@ -136,22 +117,36 @@ struct SegGeom {
 void launch_twiddles(double2* tw, int logF, cudaStream_t st);
 void launch_chirps(const ChirpGeom& g, double2* wU, double2* wV, cudaStream_t st);
 void launch_seg_hh(const SegGeom& g, double2* hh, cudaStream_t st);
-// out[cc][t] = sum_s in[cc*nseg + s][t] * H[s][t]   (overlap-add of column segments)
-template <class C>
-void launch_seg_mac(const C* in, const C* H, C* out, int64_t F, int64_t nseg, int nc, cudaStream_t st);
+// Far-field column generation fused into the first loads of a forward transform: column y of the
+// chunk is segment sg = y % nsegc of stacked column g = c0 + y / nsegc (right-hand side
+// g / ncols, table row li = g % ncols), and its point t < F is
+//   coef[rhs * ldc + n0 - 1 + sg S + t] * Vt[li][sg S + t]   for t < min(S, C - sg S), else 0.
+// coef holds double (FP64 plans), float (FP32) or (high, low) float pairs (DF64) coefficients.
+struct FftGen {
+  int64_t nsegc, S, C, n0;
+  int64_t c0;
+  int64_t ncols;
+  const void* coef;
+  int64_t ldc;
+  const void* Vt;
+};
+
 // Out-of-place multi-column FFT of length 2^logF over ncols contiguous columns,
 // ping-ponging between a (input) and b; *result receives the buffer holding the output.
 // C is double2 (FP64) or float2 (FP32); tw is the matching twiddle ladder (W_F^t at tw[F + t]
 // for every power of two F = 2^6 .. 2^logFmax).
 // With hmul, column j transforms a[j / nseg] times hmul[j % nseg] elementwise (a holds
 // ncols / nseg columns; the products of the chirp spectra are folded into the first loads).
+// With gen (forward transforms only), the input columns are generated by the first loads as
+// FftGen describes and a is used only as workspace.
 template <class C>
 int run_fft(C* a, C* b, int logF, int ncols, bool inverse, const C* tw, int logFmax, cudaStream_t st, C** result,
-            int* npasses = nullptr, const C* hmul = nullptr, int64_t nseg = 1);
+            int* npasses = nullptr, const C* hmul = nullptr, int64_t nseg = 1, const FftGen* gen = nullptr);
+// out[cc][t] = sum_s in[cc*nseg + s][t] * H[s][t]   (overlap-add of column segments)
+template <class C>
+void launch_seg_mac(const C* in, const C* H, C* out, int64_t F, int64_t nseg, int nc, cudaStream_t st);
 template <class C>
 void launch_scale_copy(const double2* src, C* dst, int64_t n, double scale, cudaStream_t st);
-template <class C>
-void launch_gen(const GenArgs& a, cudaStream_t st);
 template <class C>
 void launch_out(const OutArgs& a, cudaStream_t st);
 // Near field in FP64 (R = double: r, omega, jtab from the FP64 tables) or FP32 (R = float:
