@@ -335,27 +335,34 @@ def run_ours(args):
     coeffs_per_step = len(plans) * N * B
     value, total_ms = aggregate(world, coeffs_per_step, args.steps, sum(step_ms), dev)
 
-    # dominant kernel: the FFT passes of the FP64 plans (of the FP32 plans when all are FP32)
+    # dominant kernel: the FFT passes of the FP64 transforms (of the FP32 transforms when every
+    # plan is FP32); the double-float and FP32 transforms of the mixed plans are reported beside it
     precs = [p.info["precision"] for p in plans]
     fp32 = all(q == 2 for q in precs)
-    kind = 2 if fp32 else (1 if 1 in precs else precs[0])
-    sel = [st for st, q in zip(stats, precs) if q == kind]
-    fft_ms = sum(st["fft"]["ms"] for st in sel)
-    fft_flops = sum(st["fft"]["flops"] for st in sel)
-    fft_launches = sum(st["fft"]["launches"] for st in sel)
-    fft_bytes = sum(st["fft"]["bytes"] for st in sel)
+    key = "fft_fp32" if fp32 else "fft"
+    fft_ms = sum(st[key]["ms"] for st in stats)
+    fft_flops = sum(st[key]["flops"] for st in stats)
+    fft_launches = sum(st[key]["launches"] for st in stats)
+    fft_bytes = sum(st[key]["bytes"] for st in stats)
     achieved = fft_flops / (fft_ms / 1000.0) / 1e9 if fft_ms > 0 else 0.0
     launches = sum(st[k]["launches"] for st in stats for k in st)
     stage_ms = {k: round(sum(st[k]["ms"] for st in stats) / args.steps, 3) for k in stats[0]}
-    # the double-float transforms (the FP32 pipe's work) for context
-    dsel = [st for st, q in zip(stats, precs) if q == 3]
-    df64_ms = sum(st["fft"]["ms"] for st in dsel)
-    df64_info = None
-    if dsel and kind != 3 and df64_ms > 0:
-        df64_info = {"fft_ms_per_step": df64_ms / args.steps,
-                     "gflops_5FlogF": sum(st["fft"]["flops"] for st in dsel) / (df64_ms / 1000.0) / 1e9,
-                     "eps": [e for e, q in zip(eps_list, precs) if q == 3]}
-    dtype = "+".join(dict.fromkeys({1: "f64", 2: "f32", 3: "df64"}[q] for q in precs))
+    others = {}
+    for k2, name in (("fft_df64", "df64_transforms"), ("fft_fp32", "fp32_transforms")):
+        if k2 == key:
+            continue
+        ms2 = sum(st[k2]["ms"] for st in stats)
+        if ms2 > 0:
+            others[name] = {"fft_ms_per_step": ms2 / args.steps,
+                            "gflops_5FlogF": sum(st[k2]["flops"] for st in stats) / (ms2 / 1000.0) / 1e9}
+    terms = [0, 0, 0]
+    for p in plans:
+        for b in p.blocks():
+            for i in range(3):
+                terms[i] += b["terms"][i]
+    kinds = ["f64" if (1 in precs or terms[0]) else None, "df64" if (3 in precs or terms[1]) else None,
+             "f32" if (2 in precs or terms[2]) else None]
+    dtype = "+".join(k for k in kinds if k)
     # accuracy of the timed plans on the CPU baseline's vector and rows (checked by the oracle
     # there, outside every timed region)
     err_c = coefficients("normal", N, 1, seed_for(4, 99))
@@ -400,11 +407,12 @@ def run_ours(args):
                     "traffic_unit": "DRAM bytes per launch (ncu ratio x algorithmic bytes)",
                     "frac_of_measured_fp64": achieved / FP64_MEASURED_GFLOPS, "hbm_gbs_of_passes": pass_gbs,
                     "kernel": "k_fft_pass_reg / k_fft_small (FP64 transforms, forward + inverse)",
-                    "plans": "eps = %s (FP64)" % ",".join(str(e) for e, q in zip(eps_list, precs) if q == kind),
+                    "plans": "the FP64 transforms of every plan",
                     "flops_model": "5 F log2 F per column transform, plus 6 F per spectrum product folded into an inverse transform", "launches": fft_launches,
                     "peak_source": "nominal FP64 from unit counts and clock (152 SM x 4 flop/clk x 2.07 GHz)"}
-        if df64_info:
-            roofline["df64_transforms"] = df64_info
+        roofline.update(others)
+    term_split = {"fp64": terms[0], "df64": terms[1], "fp32": terms[2],
+                  "unit": "far-field transforms per right-hand side, summed over blocks and plans"}
     if rank != 0:
         return
     line = {
@@ -420,6 +428,7 @@ def run_ours(args):
                        "form": "one vector per execution, every stage FP64"},
         "served_over_plain": value / plain_cps if plain_cps else None,
         "stage_ms_per_step": stage_ms,
+        "term_precision": term_split,
         "roofline": roofline,
         "e2e": {"value": served_e2e, "unit": "coeffs/s", "h2d_bytes_per_step": coeffs_per_step * 8,
                 "d2h_bytes_per_step": coeffs_per_step * 8,

@@ -67,7 +67,10 @@ enum hankel_grid {
 
 enum hankel_precision {
   HANKEL_PREC_AUTO = 0,  /* FP64 below eps = 1e-11, DF64 transforms for 1e-11 <= eps < 1e-5, FP32 stages at
-                            eps >= 1e-5 */
+                            eps >= 1e-5; in FP64 and DF64 plans, each term of a block's low-rank form runs
+                            in the lowest precision whose rounding bound stays within a quarter of the
+                            block's leading term in the plan precision, or within eps / 200 of it
+                            (hankel_block.terms_*; HANKEL_FLAG_UNIFORM_TERMS turns this off) */
   HANKEL_PREC_FP64 = 1,  /* every stage in FP64 */
   HANKEL_PREC_FP32 = 2,  /* FP32 stages; refused (HANKEL_EUNSUPPORTED) when eps < 1e-5 */
   HANKEL_PREC_DF64 = 3   /* transforms and spectrum products in double-float (pairs of FP32, ~48
@@ -97,6 +100,8 @@ enum hankel_status {
 #define HANKEL_FLAG_NO_REFINE 16u  /* keep the blocks of Eq. (19) as they are; by default a block is cut into
                                       smaller ones where that lowers the estimated work (fewer kept columns
                                       away from the near field) */
+#define HANKEL_FLAG_UNIFORM_TERMS 64u /* AUTO plans: every far-field term in the plan precision (no per-term
+                                         lowering of small low-rank terms) */
 
 /* Options for hankel_plan_ex(). Fill with hankel_options_default() first. */
 typedef struct {
@@ -152,6 +157,9 @@ typedef struct {
   int kept;        /* stacked columns the block keeps (<= hankel_info.ncols) */
   int lowrank;     /* 1 when the block runs its low-rank form */
   double lowrank_err; /* largest error of the low-rank form on its validation entries (<= eps/2) */
+  int terms_fp64;  /* of its ncols transforms per right-hand side: those run in FP64, */
+  int terms_df64;  /* in double-float */
+  int terms_fp32;  /* and in FP32 */
 } hankel_block;
 
 /* Fill *o with defaults for (task, nu, N, eps). Host only. Returns HANKEL_OK or HANKEL_EINVAL (o == NULL). */
@@ -250,12 +258,15 @@ enum hankel_stage {
   HANKEL_STAGE_NEAR = 0,      /* near-field direct sum (and its partial-sum combine) */
   HANKEL_STAGE_GEN = 1,       /* per-execution coefficient conversion of FP32 and DF64 plans (the
                                  far-field column generation itself runs in the first forward FFT loads) */
-  HANKEL_STAGE_FFT = 2,       /* forward and inverse multi-column FFT passes, with the column generation
-                                 and the single spectrum products folded into their first loads */
+  HANKEL_STAGE_FFT = 2,       /* forward and inverse multi-column FFT passes of FP64 transforms, with the
+                                 column generation and the single spectrum products folded into their
+                                 first loads */
   HANKEL_STAGE_POINTWISE = 3, /* summed products of segment spectra and chirp spectra (column-segmented
                                  blocks) */
   HANKEL_STAGE_OUT = 4,       /* row weights and accumulation into f */
-  HANKEL_STAGE_COUNT = 5
+  HANKEL_STAGE_FFT_DF64 = 5,  /* the FFT passes of double-float transforms */
+  HANKEL_STAGE_FFT_FP32 = 6,  /* the FFT passes of FP32 transforms */
+  HANKEL_STAGE_COUNT = 7
 };
 
 /* Accumulated statistics of one stage since timing was (re)enabled. */

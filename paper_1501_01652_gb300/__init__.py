@@ -18,7 +18,7 @@ PRECISIONS = {"auto": 0, "fp64": 1, "fp32": 2, "df64": 3}
 
 
 def _options(task, nu, N, eps, grid="unit", gamma=None, precision="auto", max_nrhs=1, workspace_limit=0,
-             host_only=False, segment=True, prune=True, refine=True, lowrank=True):
+             host_only=False, segment=True, prune=True, refine=True, lowrank=True, mixed_terms=True):
     lib = _lib.load()
     o = _lib.Options()
     _lib.check(lib.hankel_options_default(ctypes.byref(o), TASKS[task], int(nu), int(N), float(eps)),
@@ -31,7 +31,8 @@ def _options(task, nu, N, eps, grid="unit", gamma=None, precision="auto", max_nr
     o.workspace_limit = int(workspace_limit)
     o.flags = ((_lib.FLAG_HOST_ONLY if host_only else 0) | (0 if segment else _lib.FLAG_NO_SEGMENT)
                | (0 if prune else _lib.FLAG_ALL_COLUMNS)
-               | (0 if refine else _lib.FLAG_NO_REFINE) | (0 if lowrank else _lib.FLAG_NO_LOWRANK))
+               | (0 if refine else _lib.FLAG_NO_REFINE) | (0 if lowrank else _lib.FLAG_NO_LOWRANK)
+               | (0 if mixed_terms else _lib.FLAG_UNIFORM_TERMS))
     return o
 
 
@@ -85,13 +86,14 @@ class Plan:
     """A transform plan: f = J_nu(r omega^T) c for one task, order, size and accuracy."""
 
     def __init__(self, task, nu, N, eps, grid="unit", gamma=None, precision="auto", max_nrhs=1,
-                 workspace_limit=0, host_only=False, segment=True, prune=True, refine=True, lowrank=True):
+                 workspace_limit=0, host_only=False, segment=True, prune=True, refine=True, lowrank=True,
+                 mixed_terms=True):
         self._lib = _lib.load()
         self._h = ctypes.c_void_p()
         self.task, self.nu, self.N, self.eps = task, int(nu), int(N), float(eps)
         self.max_nrhs = int(max_nrhs)
         o = _options(task, nu, N, eps, grid, gamma, precision, max_nrhs, workspace_limit, host_only, segment,
-                     prune, refine, lowrank)
+                     prune, refine, lowrank, mixed_terms)
         _lib.check(self._lib.hankel_plan_ex(ctypes.byref(self._h), ctypes.byref(o)), "hankel_plan_ex")
 
     def __del__(self):
@@ -120,7 +122,7 @@ class Plan:
         _lib.check(self._lib.hankel_plan_blocks(self._h, arr, cnt.value, ctypes.byref(cnt)), "hankel_plan_blocks")
         return [dict(k0=b.k0, k1=b.k1, n0=b.n0, n1=b.n1, F=b.fft_len, S=b.seg_len, nseg=b.nseg, mode=b.mode,
                      ncols=b.ncols, dropped=b.dropped, kept=b.kept, lowrank=bool(b.lowrank),
-                     lowrank_err=b.lowrank_err)
+                     lowrank_err=b.lowrank_err, terms=(b.terms_fp64, b.terms_df64, b.terms_fp32))
                 for b in arr[:cnt.value]]
 
     def entry(self, k, n):

@@ -14,6 +14,7 @@ FLAG_NO_SEGMENT = 2
 FLAG_ALL_COLUMNS = 8
 FLAG_NO_REFINE = 16
 FLAG_NO_LOWRANK = 32
+FLAG_UNIFORM_TERMS = 64
 
 # Every function include/hankel.h declares.
 EXPORTED = [
@@ -26,7 +27,7 @@ EXPORTED = [
     "hankel_server_options_default", "hankel_server_create", "hankel_server_submit", "hankel_server_wait",
     "hankel_server_drain", "hankel_server_get_stats", "hankel_server_destroy",
 ]
-STAGES = ["near", "gen", "fft", "pointwise", "out"]
+STAGES = ["near", "gen", "fft", "pointwise", "out", "fft_df64", "fft_fp32"]
 
 
 class Options(ctypes.Structure):
@@ -74,7 +75,8 @@ class Block(ctypes.Structure):
     _fields_ = [("k0", ctypes.c_int64), ("k1", ctypes.c_int64), ("n0", ctypes.c_int64), ("n1", ctypes.c_int64),
                 ("fft_len", ctypes.c_int64), ("seg_len", ctypes.c_int64), ("nseg", ctypes.c_int64),
                 ("mode", ctypes.c_int), ("ncols", ctypes.c_int), ("dropped", ctypes.c_double),
-                ("kept", ctypes.c_int), ("lowrank", ctypes.c_int), ("lowrank_err", ctypes.c_double)]
+                ("kept", ctypes.c_int), ("lowrank", ctypes.c_int), ("lowrank_err", ctypes.c_double),
+                ("terms_fp64", ctypes.c_int), ("terms_df64", ctypes.c_int), ("terms_fp32", ctypes.c_int)]
 
 
 def load():

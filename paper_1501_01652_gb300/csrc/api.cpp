@@ -163,6 +163,11 @@ int hankel_plan_blocks(hankel_plan_t p, hankel_block* out, int cap, int* count) 
     out[i].kept = (int)bl[i].lcols.size();
     out[i].lowrank = bl[i].rank ? 1 : 0;
     out[i].lowrank_err = bl[i].lowrank_err;
+    int cnt[3] = {0, 0, 0};
+    for (int8_t t : bl[i].tprec) cnt[t] += 1;
+    out[i].terms_fp64 = cnt[hk::kTermFP64];
+    out[i].terms_df64 = cnt[hk::kTermDF64];
+    out[i].terms_fp32 = cnt[hk::kTermFP32];
   }
   return HANKEL_OK;
 }

@@ -29,16 +29,32 @@ constexpr size_t kDefaultWorkspace = size_t(4) << 30;
 // Complex elements one stacked column occupies in a workspace buffer.
 size_t column_footprint(const Block& b) { return (size_t)b.F * (size_t)b.nseg; }
 
+// Element size of a term precision's complex type (double2, df64c, float2).
+size_t term_esz(int prec) { return prec == kTermFP32 ? sizeof(float2) : sizeof(double2); }
+
+// The transforms of a block that run in one precision.
+struct TermGroup {
+  int prec = kTermFP64;  // kTermFP64 (double2), kTermDF64 (df64c) or kTermFP32 (float2)
+  int nl = 0;            // transforms per right-hand side
+  void* H = nullptr;     // per segment: FFT_F of the chirp exp(-i pi (U-V)^2 / (2E)), times 1/F
+  void* Vt = nullptr;    // [nl][C] column functions x column chirp (x FP32 scale)
+  void* Ut = nullptr;    // [nl][R] row functions (/ FP32 scale)
+  int64_t cap = 0;       // stacked columns per chunk
+};
+
 struct DevBlock {
   Block b;
   double2* wU = nullptr;  // exp(i pi U_k^2 / (2E)), k = k0..k1
   double2* wV = nullptr;  // exp(i pi V_n^2 / (2E)), n = n0..n1
-  void* H = nullptr;      // per segment: FFT_F of the chirp exp(-i pi (U-V)^2 / (2E)), times 1/F (plan precision)
-  int nl = 0;                // stacked columns (transforms) per right-hand side
-  void* Vt = nullptr;        // [nl][C] column functions x column chirp (x FP32 scale), plan precision
-  void* Ut = nullptr;        // [nl][R] row functions (/ FP32 scale), plan precision
-  int64_t cap = 0;           // columns per chunk
+  TermGroup g[3];         // groups in the order FP64, DF64, FP32
+  int ng = 0;
 };
+
+// Indices li of the block's transforms per precision.
+void term_lists(const Block& b, std::vector<int> (&lists)[3]) {
+  for (auto& l : lists) l.clear();
+  for (size_t li = 0; li < b.tprec.size(); ++li) lists[b.tprec[li]].push_back((int)li);
+}
 
 }  // namespace
 
@@ -67,12 +83,13 @@ struct DevicePlan {
   double2* tw = nullptr;   // twiddle ladder in FP64: W_F^t at tw[F + t], F = 2^6 .. 2^logFmax
   float2* twf = nullptr;   // the same ladder rounded to FP32 (FP32 plans)
   df64c* twd = nullptr;    // the same ladder in double-float (DF64 plans)
-  bool df64 = false;       // transforms in double-float
+  bool df64 = false;       // plan precision double-float (transforms; near field on the FP32 pipe)
+  bool any_t[3] = {false, false, false};  // some block has transforms in this precision
   int logFmax = 6;
   void* bufA = nullptr;    // workspace, elements of the plan precision
   void* bufB = nullptr;
-  size_t ws_bytes = 0;
-  size_t ws_elems = 0;
+  size_t ws_bytes = 0;    // both buffers
+  size_t buf_bytes = 0;   // one buffer
   double* c_stage = nullptr;
   double* f_stage = nullptr;
   double* vinv = nullptr;     // DHT plans, first inverse call: v_n = 2 / J_1(j_{0,n})^2
@@ -223,7 +240,8 @@ int dev_plan_create(hankel_plan_s* p) {
   HK_TRY(upload(d, &d->jtab, hp.jtab.data(), hp.jtab.size()));
   d->fp32 = hp.fp32;
   d->df64 = hp.df64;
-  const size_t esz = d->fp32 ? sizeof(float2) : sizeof(double2);  // workspace element size
+  for (const Block& b : hp.blocks)
+    for (int8_t t : b.tprec) d->any_t[t] = true;
   if (d->fp32) {
     std::vector<float> tf(std::max<size_t>((size_t)N, hp.jtab.size()));
     for (int64_t i = 0; i < N; ++i) tf[i] = (float)hp.r_true[i];
@@ -245,8 +263,11 @@ int dev_plan_create(hankel_plan_s* p) {
     HK_TRY(upload(d, &d->omdf, tp.data(), N));
     for (size_t i = 0; i < hp.jtab.size(); ++i) tp[i] = pair(hp.jtab[i]);
     HK_TRY(upload(d, &d->jtabdf, tp.data(), hp.jtab.size()));
-    HK_TRY(dalloc(d, &d->cdf, (size_t)hp.opt.max_nrhs * N));
   }
+  // per-execution coefficient copies: double-float pairs for DF64 near fields and transforms,
+  // FP32 for FP32 transforms (FP32 near fields read them too)
+  if (d->df64 || d->any_t[kTermDF64]) HK_TRY(dalloc(d, &d->cdf, (size_t)hp.opt.max_nrhs * N));
+  if (d->any_t[kTermFP32]) HK_TRY(dalloc(d, &d->cf, (size_t)hp.opt.max_nrhs * N));
 
 
   // Near-field work list: groups of kNearRows rows, the group's longest prefix cut into tiles of
@@ -292,121 +313,140 @@ int dev_plan_create(hankel_plan_s* p) {
   HK_TRY(dalloc(d, &d->tw, (size_t)2 << logFmax));
   for (int L = 6; L <= logFmax; ++L) launch_twiddles(d->tw + ((size_t)1 << L), L, 0);
   HK_LAUNCHED();
-  if (d->fp32) {
+  if (d->any_t[kTermFP32]) {
     HK_TRY(dalloc(d, &d->twf, (size_t)2 << logFmax));
     launch_scale_copy<float2>(d->tw + 64, d->twf + 64, (int64_t(2) << logFmax) - 64, 1.0, 0);
     HK_LAUNCHED();
   }
-  if (d->df64) {
+  if (d->any_t[kTermDF64]) {
     HK_TRY(dalloc(d, &d->twd, (size_t)2 << logFmax));
     launch_scale_copy<df64c>(d->tw + 64, d->twd + 64, (int64_t(2) << logFmax) - 64, 1.0, 0);
     HK_LAUNCHED();
   }
 
-  // Workspace: two ping-pong buffers, each holding a chunk of stacked columns of a block
-  // (nseg transforms of length F per stacked column for segmented blocks).
-  // The plan-time spectra are computed in FP64 in the same buffers, so they hold at least
-  // nseg*F double2 values whatever the plan precision.
+  // Workspace: two ping-pong buffers, each holding a chunk of stacked columns of one term group
+  // of a block (nseg transforms of length F per stacked column for segmented blocks). The
+  // plan-time spectra are computed in FP64 in the same buffers, so each holds at least nseg F
+  // double2 values.
   size_t limit = hp.opt.workspace_limit ? hp.opt.workspace_limit : kDefaultWorkspace;
-  const size_t dfac = sizeof(double2) / esz;  // workspace elements per double2
-  size_t need = dfac << logFmax;
+  size_t need = sizeof(double2) << logFmax;  // bytes per buffer
+  std::vector<int> lists[3];
   for (const Block& b : hp.blocks) {
     const size_t foot = column_footprint(b);
-    const int64_t total = (int64_t)(b.rank ? b.rank : (int)b.lcols.size()) * hp.opt.max_nrhs;
-    int64_t cap = (int64_t)(limit / (2 * esz * foot));
-    cap = std::max<int64_t>(1, std::min<int64_t>(cap, total));
-    need = std::max(need, (size_t)cap * foot);
-    need = std::max(need, dfac * (size_t)b.nseg * (size_t)b.F);
+    term_lists(b, lists);
+    for (int t = 0; t < 3; ++t) {
+      if (lists[t].empty()) continue;
+      const size_t esz = term_esz(t);
+      const int64_t total = (int64_t)lists[t].size() * hp.opt.max_nrhs;
+      int64_t cap = (int64_t)(limit / (2 * esz * foot));
+      cap = std::max<int64_t>(1, std::min<int64_t>(cap, total));
+      need = std::max(need, (size_t)cap * foot * esz);
+    }
+    need = std::max(need, sizeof(double2) * (size_t)b.nseg * (size_t)b.F);
   }
   {
     char* qa; char* qb;
-    HK_TRY(dalloc(d, &qa, need * esz));
-    HK_TRY(dalloc(d, &qb, need * esz));
+    HK_TRY(dalloc(d, &qa, need));
+    HK_TRY(dalloc(d, &qb, need));
     d->bufA = qa;
     d->bufB = qb;
   }
-  d->ws_bytes = 2 * need * esz;
-  d->ws_elems = need;
+  d->ws_bytes = 2 * need;
+  d->buf_bytes = need;
 
-  // Per block: chirp vectors, the spectra of its convolution kernels (one per segment) and its
-  // column and row tables (the low-rank form's terms, or its kept stacked columns).
+  // Per block: chirp vectors, the spectra of its convolution kernels (one per segment) and per
+  // term group its column and row tables (the low-rank form's terms, or its kept stacked columns).
   for (const Block& b : hp.blocks) {
     DevBlock db;
     db.b = b;
-    db.nl = b.rank ? b.rank : (int)b.lcols.size();
-    db.cap = std::max<int64_t>(1, std::min<int64_t>((int64_t)(need / column_footprint(b)),
-                                                    (int64_t)db.nl * hp.opt.max_nrhs));
     HK_TRY(dalloc(d, &db.wU, b.R));
     HK_TRY(dalloc(d, &db.wV, b.C));
     ChirpGeom g{hp.Ua, hp.Ub, hp.Va, hp.Vb, hp.E, b.k0, b.n0, b.R, b.C, b.F};
     launch_chirps(g, db.wU, db.wV, 0);
     HK_LAUNCHED();
-    if (d->fp32) {
-      float2* h; HK_TRY(dalloc(d, &h, (size_t)b.nseg * b.F)); db.H = h;
-      float2* vt; HK_TRY(dalloc(d, &vt, (size_t)db.nl * b.C)); db.Vt = vt;
-      float2* ut; HK_TRY(dalloc(d, &ut, (size_t)db.nl * b.R)); db.Ut = ut;
-    } else if (d->df64) {
-      df64c* h; HK_TRY(dalloc(d, &h, (size_t)b.nseg * b.F)); db.H = h;
-      df64c* vt; HK_TRY(dalloc(d, &vt, (size_t)db.nl * b.C)); db.Vt = vt;
-      df64c* ut; HK_TRY(dalloc(d, &ut, (size_t)db.nl * b.R)); db.Ut = ut;
-    } else {
-      double2* h; HK_TRY(dalloc(d, &h, (size_t)b.nseg * b.F)); db.H = h;
-      double2* vt; HK_TRY(dalloc(d, &vt, (size_t)db.nl * b.C)); db.Vt = vt;
-      double2* ut; HK_TRY(dalloc(d, &ut, (size_t)db.nl * b.R)); db.Ut = ut;
-    }
-    // FP32 plans: per stacked column, the power of two that brings max |colfun(n)| over the
-    // block to ~1 (its inverse goes to the row side)
-    std::vector<double> sc;
-    if (d->fp32) {
-      sc.assign(db.nl, 1.0);
-      for (int li = 0; li < db.nl; ++li) {
-        double mag = 0.0;
-        if (b.rank) {
-          for (int j = 0; j < b.P; ++j) mag = std::max(mag, std::abs(b.vcheb[(size_t)li * b.P + j]));
-        } else {
-          const ColSpec& csp = hp.cols[b.lcols[li]];
-          for (int64_t n : {b.n0, b.n1}) {
-            const int64_t i = n - 1;
-            cplx poly(0.0, 0.0);
-            for (int u = csp.nterm - 1; u >= 0; --u) poly = poly * hp.betan[i] + csp.G[u];
-            double m = std::abs(poly) * std::pow(hp.omt[i], csp.delta - 0.5);
-            if (csp.u1) m *= std::pow(hp.colpow[i], csp.u1);
-            mag = std::max(mag, m);
-          }
-        }
-        const int e = (mag > 0.0 && std::isfinite(mag)) ? -(int)std::lround(std::log2(mag)) : 0;
-        sc[li] = std::ldexp(1.0, e);
+    term_lists(b, lists);
+    for (int t = 0; t < 3; ++t) {
+      if (lists[t].empty()) continue;
+      TermGroup& tg = db.g[db.ng++];
+      tg.prec = t;
+      tg.nl = (int)lists[t].size();
+      tg.cap = std::max<int64_t>(1, std::min<int64_t>((int64_t)(need / (column_footprint(b) * term_esz(t))),
+                                                      (int64_t)tg.nl * hp.opt.max_nrhs));
+      if (t == kTermFP32) {
+        float2* h; HK_TRY(dalloc(d, &h, (size_t)b.nseg * b.F)); tg.H = h;
+        float2* vt; HK_TRY(dalloc(d, &vt, (size_t)tg.nl * b.C)); tg.Vt = vt;
+        float2* ut; HK_TRY(dalloc(d, &ut, (size_t)tg.nl * b.R)); tg.Ut = ut;
+      } else if (t == kTermDF64) {
+        df64c* h; HK_TRY(dalloc(d, &h, (size_t)b.nseg * b.F)); tg.H = h;
+        df64c* vt; HK_TRY(dalloc(d, &vt, (size_t)tg.nl * b.C)); tg.Vt = vt;
+        df64c* ut; HK_TRY(dalloc(d, &ut, (size_t)tg.nl * b.R)); tg.Ut = ut;
+      } else {
+        double2* h; HK_TRY(dalloc(d, &h, (size_t)b.nseg * b.F)); tg.H = h;
+        double2* vt; HK_TRY(dalloc(d, &vt, (size_t)tg.nl * b.C)); tg.Vt = vt;
+        double2* ut; HK_TRY(dalloc(d, &ut, (size_t)tg.nl * b.R)); tg.Ut = ut;
       }
-    }
-    {
-      // inputs of the table kernels, freed once the tables are built
+      // FP32 transforms: per term, the power of two that brings max |colfun(n)| over the block
+      // to ~1 (its inverse goes to the row side)
+      std::vector<double> sc;
+      if (t == kTermFP32) {
+        sc.assign(tg.nl, 1.0);
+        for (int j = 0; j < tg.nl; ++j) {
+          const int li = lists[t][j];
+          double mag = 0.0;
+          if (b.rank) {
+            for (int q = 0; q < b.P; ++q) mag = std::max(mag, std::abs(b.vcheb[(size_t)li * b.P + q]));
+          } else {
+            const ColSpec& csp = hp.cols[b.lcols[li]];
+            for (int64_t n : {b.n0, b.n1}) {
+              const int64_t i = n - 1;
+              cplx poly(0.0, 0.0);
+              for (int u = csp.nterm - 1; u >= 0; --u) poly = poly * hp.betan[i] + csp.G[u];
+              double m = std::abs(poly) * std::pow(hp.omt[i], csp.delta - 0.5);
+              if (csp.u1) m *= std::pow(hp.colpow[i], csp.u1);
+              mag = std::max(mag, m);
+            }
+          }
+          const int e = (mag > 0.0 && std::isfinite(mag)) ? -(int)std::lround(std::log2(mag)) : 0;
+          sc[j] = std::ldexp(1.0, e);
+        }
+      }
+      // inputs of the table kernels (this group's terms), freed once the tables are built
       int* lmap = nullptr;
       double2 *uc = nullptr, *vc = nullptr;
       double* scd = nullptr;
+      size_t nuc = 0, nlm = 0;
       if (b.rank) {
-        std::vector<double2> u(b.ucheb.size()), v(b.vcheb.size());
-        for (size_t j = 0; j < u.size(); ++j) u[j] = make_double2(b.ucheb[j].real(), b.ucheb[j].imag());
-        for (size_t j = 0; j < v.size(); ++j) v[j] = make_double2(b.vcheb[j].real(), b.vcheb[j].imag());
+        std::vector<double2> u((size_t)tg.nl * b.P), v((size_t)tg.nl * b.P);
+        for (int j = 0; j < tg.nl; ++j)
+          for (int q = 0; q < b.P; ++q) {
+            const cplx cu = b.ucheb[(size_t)lists[t][j] * b.P + q], cv = b.vcheb[(size_t)lists[t][j] * b.P + q];
+            u[(size_t)j * b.P + q] = make_double2(cu.real(), cu.imag());
+            v[(size_t)j * b.P + q] = make_double2(cv.real(), cv.imag());
+          }
+        nuc = u.size();
         HK_TRY(upload(d, &uc, u.data(), u.size()));
         HK_TRY(upload(d, &vc, v.data(), v.size()));
       } else {
-        HK_TRY(upload(d, &lmap, b.lcols.data(), b.lcols.size()));
+        std::vector<int> lm(tg.nl);
+        for (int j = 0; j < tg.nl; ++j) lm[j] = b.lcols[lists[t][j]];
+        nlm = lm.size();
+        HK_TRY(upload(d, &lmap, lm.data(), lm.size()));
       }
       if (!sc.empty()) HK_TRY(upload(d, &scd, sc.data(), sc.size()));
-      BlockTabArgs ta{db.nl, b.k0, b.R, b.n0, b.C, lmap, b.rank ? b.P : 0, uc, vc,
+      BlockTabArgs ta{tg.nl, b.k0, b.R, b.n0, b.C, lmap, b.rank ? b.P : 0, uc, vc,
                       std::log((double)b.k0), std::log((double)b.k1), std::log((double)b.n0),
-                      std::log((double)b.n1), d->nodes, d->cols, db.wV, scd, db.Vt, db.Ut};
-      if (d->fp32) launch_block_tables<float2>(ta, 0);
-      else if (d->df64) launch_block_tables<df64c>(ta, 0);
+                      std::log((double)b.n1), d->nodes, d->cols, db.wV, scd, tg.Vt, tg.Ut};
+      if (t == kTermFP32) launch_block_tables<float2>(ta, 0);
+      else if (t == kTermDF64) launch_block_tables<df64c>(ta, 0);
       else launch_block_tables<double2>(ta, 0);
       HK_LAUNCHED();
       if (cudaDeviceSynchronize() != cudaSuccess) return HANKEL_ECUDA;
-      dfree(d, &uc, b.ucheb.size());
-      dfree(d, &vc, b.vcheb.size());
-      dfree(d, &lmap, b.lcols.size());
+      dfree(d, &uc, nuc);
+      dfree(d, &vc, nuc);
+      dfree(d, &lmap, nlm);
       dfree(d, &scd, sc.size());
     }
-    d->blocks.push_back(db);
+    // the chirp spectra in FP64, then rounded to each group's precision
     SegGeom sg{hp.Ua, hp.Ub, hp.Vb, hp.E, b.k0, b.n0, b.R, b.C, 0, 0, 1, b.F};
     if (b.mode == kBlockRowSeg) { sg.Cc = b.S; sg.dn = b.S; sg.nseg = b.nseg; }
     if (b.mode == kBlockColSeg) { sg.Rr = b.S; sg.dk = b.S; sg.nseg = b.nseg; }
@@ -416,12 +456,15 @@ int dev_plan_create(hankel_plan_s* p) {
     HK_LAUNCHED();
     double2* res = nullptr;
     HK_TRY(run_fft<double2>(hA, hB, b.logF, (int)b.nseg, /*inverse=*/false, d->tw, d->logFmax, 0, &res));
-    if (d->fp32) launch_scale_copy<float2>(res, (float2*)d->blocks.back().H, b.nseg * b.F, 1.0 / (double)b.F, 0);
-    else if (d->df64) launch_scale_copy<df64c>(res, (df64c*)d->blocks.back().H, b.nseg * b.F, 1.0 / (double)b.F, 0);
-    else launch_scale_copy<double2>(res, (double2*)d->blocks.back().H, b.nseg * b.F, 1.0 / (double)b.F, 0);
-    HK_LAUNCHED();
+    for (int j = 0; j < db.ng; ++j) {
+      const TermGroup& tg = db.g[j];
+      if (tg.prec == kTermFP32) launch_scale_copy<float2>(res, (float2*)tg.H, b.nseg * b.F, 1.0 / (double)b.F, 0);
+      else if (tg.prec == kTermDF64) launch_scale_copy<df64c>(res, (df64c*)tg.H, b.nseg * b.F, 1.0 / (double)b.F, 0);
+      else launch_scale_copy<double2>(res, (double2*)tg.H, b.nseg * b.F, 1.0 / (double)b.F, 0);
+      HK_LAUNCHED();
+    }
+    d->blocks.push_back(db);
   }
-  if (d->fp32 && !hp.blocks.empty()) HK_TRY(dalloc(d, &d->cf, (size_t)hp.opt.max_nrhs * N));
 
   if (cudaDeviceSynchronize() != cudaSuccess) return HANKEL_ECUDA;
   return HANKEL_OK;
@@ -451,13 +494,36 @@ namespace {
 // generation, forward FFTs, the product with the kernel spectra (summed over column segments
 // or replicated over row segments), inverse FFTs and the row accumulation into f.
 // C = double2 (FP64 plans), float2 (FP32 plans) or df64c (DF64 plans).
+// Per precision: twiddle ladder, coefficient copy (format of FftGen::coef) and FFT stage.
 template <class C>
-int run_block(DevicePlan* d, const DevBlock& db, const double* c, int64_t ldc, double* f, int64_t ldf, int nrhs,
-              C* A, C* B, int64_t cap, cudaStream_t st, bool record) {
+struct Prec;
+template <>
+struct Prec<double2> {
+  static const void* tw(const DevicePlan* d) { return d->tw; }
+  static const void* coef(const DevicePlan* d, const double* c) { return c; }
+  static constexpr int stage = HANKEL_STAGE_FFT;
+};
+template <>
+struct Prec<df64c> {
+  static const void* tw(const DevicePlan* d) { return d->twd; }
+  static const void* coef(const DevicePlan* d, const double*) { return d->cdf; }
+  static constexpr int stage = HANKEL_STAGE_FFT_DF64;
+};
+template <>
+struct Prec<float2> {
+  static const void* tw(const DevicePlan* d) { return d->twf; }
+  static const void* coef(const DevicePlan* d, const double*) { return d->cf; }
+  static constexpr int stage = HANKEL_STAGE_FFT_FP32;
+};
+
+template <class C>
+int run_block(DevicePlan* d, const DevBlock& db, const TermGroup& tg, const double* c, int64_t ldc, double* f,
+              int64_t ldf, int nrhs, C* A, C* B, int64_t cap, cudaStream_t st, bool record) {
   const Block& b = db.b;
-  const C* tw = (const C*)(d->fp32 ? (const void*)d->twf : d->df64 ? (const void*)d->twd : (const void*)d->tw);
-  const C* H = (const C*)db.H;
-  const int64_t total = (int64_t)db.nl * nrhs;
+  const C* tw = (const C*)Prec<C>::tw(d);
+  const C* H = (const C*)tg.H;
+  const int fst = Prec<C>::stage;
+  const int64_t total = (int64_t)tg.nl * nrhs;
   const bool rowseg = b.mode == kBlockRowSeg, colseg = b.mode == kBlockColSeg;
   for (int64_t c0 = 0; c0 < total; c0 += cap) {
     const int nc = (int)std::min<int64_t>(cap, total - c0);
@@ -466,11 +532,11 @@ int run_block(DevicePlan* d, const DevBlock& db, const double* c, int64_t ldc, d
     C* res = nullptr;
     {
       // column generation happens in the first loads of the forward transform
-      StageScope sc(d, HANKEL_STAGE_FFT, st, record);
+      StageScope sc(d, fst, st, record);
       int np = 0;
-      const void* coef = d->fp32 ? (const void*)d->cf : d->df64 ? (const void*)d->cdf : (const void*)c;
-      const FftGen gen{rowseg ? b.nseg : 1, rowseg ? b.S : b.C, b.C, b.n0, c0, db.nl, coef,
-                       (d->fp32 || d->df64) ? d->hpN : ldc, db.Vt};
+      const void* coef = Prec<C>::coef(d, c);
+      const FftGen gen{rowseg ? b.nseg : 1, rowseg ? b.S : b.C, b.C, b.n0, c0, tg.nl, coef,
+                       coef == (const void*)c ? ldc : d->hpN, tg.Vt};
       HK_TRY(run_fft<C>(A, B, b.logF, (int)nfwd, false, tw, d->logFmax, st, &res, &np, nullptr, 1, &gen));
       HK_LAUNCHED();
       sc.done(np, 5.0 * (double)b.F * (double)b.logF * (double)nfwd, 0.0, 2.0 * sizeof(C) * (double)b.F * nfwd * np);
@@ -483,9 +549,9 @@ int run_block(DevicePlan* d, const DevBlock& db, const double* c, int64_t ldc, d
         StageScope sc(d, HANKEL_STAGE_POINTWISE, st, record);
         launch_seg_mac<C>(res, H, other, b.F, b.nseg, nc, st);
         HK_LAUNCHED();
-        sc.done(1, 0.0, 0.0);
+        sc.done(1, 8.0 * (double)b.F * (double)b.nseg * nc, 0.0);
       }
-      StageScope sc(d, HANKEL_STAGE_FFT, st, record);
+      StageScope sc(d, fst, st, record);
       int np = 0;
       HK_TRY(run_fft<C>(other, res, b.logF, (int)ninv, true, tw, d->logFmax, st, &res2, &np));
       HK_LAUNCHED();
@@ -494,7 +560,7 @@ int run_block(DevicePlan* d, const DevBlock& db, const double* c, int64_t ldc, d
       // full blocks: one product with the chirp spectrum; row segments (overlap-save): each
       // column's spectrum times every segment's chirp spectrum -- both folded into the first
       // loads of the inverse transform
-      StageScope sc(d, HANKEL_STAGE_FFT, st, record);
+      StageScope sc(d, fst, st, record);
       int np = 0;
       HK_TRY(run_fft<C>(res, other, b.logF, (int)ninv, true, tw, d->logFmax, st, &res2, &np, H,
                         colseg ? b.nseg : 1));
@@ -506,7 +572,7 @@ int run_block(DevicePlan* d, const DevBlock& db, const double* c, int64_t ldc, d
     {
       StageScope sc(d, HANKEL_STAGE_OUT, st, record);
       OutArgs oa{res2, b.F, b.R, b.k0, (rowseg ? b.S : b.C) - 1, colseg ? b.S : b.R, colseg ? b.nseg : 1,
-                 nc, c0, db.nl, f, ldf, db.wU, db.Ut};
+                 nc, c0, tg.nl, f, ldf, db.wU, tg.Ut};
       launch_out<C>(oa, st);
       HK_LAUNCHED();
       sc.done(1, 0.0, 0.0);
@@ -515,19 +581,20 @@ int run_block(DevicePlan* d, const DevBlock& db, const double* c, int64_t ldc, d
   return HANKEL_OK;
 }
 
-// Near field of a plan in its precision, then every far block.
+// Near field of a plan in its precision, then every far block's term groups. capacity
+// (chunk_from_capacity): bytes of each of A and B.
 int run_all(DevicePlan* d, const HostPlan& hp, const double* c, int64_t ldc, double* f, int64_t ldf, int nrhs,
-            void* A, void* B, void* partial, size_t capacity_elems, bool chunk_from_capacity, cudaStream_t st,
+            void* A, void* B, void* partial, size_t capacity, bool chunk_from_capacity, cudaStream_t st,
             bool record) {
   if (d->cf) {
-    // FP32 plans with per-block tables: the coefficients rounded once, for every stage
+    // FP32 transforms (and FP32 near fields): the coefficients rounded once per execution
     StageScope sc(d, HANKEL_STAGE_GEN, st, record);
     launch_coeffs_f32(c, ldc, d->cf, d->hpN, nrhs, st);
     HK_LAUNCHED();
     sc.done(1, 0.0, 0.0);
   }
   if (d->cdf) {
-    // DF64 plans: the coefficients split once into float pairs, for the near field and generation
+    // DF64 near fields and transforms: the coefficients split once into float pairs
     StageScope sc(d, HANKEL_STAGE_GEN, st, record);
     launch_coeffs_df64(c, ldc, d->cdf, d->hpN, nrhs, st);
     HK_LAUNCHED();
@@ -535,7 +602,7 @@ int run_all(DevicePlan* d, const HostPlan& hp, const double* c, int64_t ldc, dou
   }
   {
     StageScope sc(d, HANKEL_STAGE_NEAR, st, record);
-    if (d->cdf)
+    if (d->df64)
       launch_near_df(d->items, d->nitems, d->mrows, d->nmrows, d->nend, d->hpN, (double*)partial, nrhs, d->cdf, f,
                      ldf, d->rdf, d->omdf, d->jtabdf, hp.jt_n, hp.jt_deg, st);
     else if (d->fp32)
@@ -548,12 +615,19 @@ int run_all(DevicePlan* d, const HostPlan& hp, const double* c, int64_t ldc, dou
     sc.done(d->nmrows > 0 ? 2 : 1, 0.0, (double)hp.near_count * nrhs);
   }
   for (const DevBlock& db : d->blocks) {
-    const int64_t cap = chunk_from_capacity
-                            ? std::max<int64_t>(1, (int64_t)(capacity_elems / column_footprint(db.b)))
-                            : db.cap;
-    if (d->fp32) HK_TRY(run_block<float2>(d, db, c, ldc, f, ldf, nrhs, (float2*)A, (float2*)B, cap, st, record));
-    else if (d->df64) HK_TRY(run_block<df64c>(d, db, c, ldc, f, ldf, nrhs, (df64c*)A, (df64c*)B, cap, st, record));
-    else HK_TRY(run_block<double2>(d, db, c, ldc, f, ldf, nrhs, (double2*)A, (double2*)B, cap, st, record));
+    for (int j = 0; j < db.ng; ++j) {
+      const TermGroup& tg = db.g[j];
+      const size_t esz = term_esz(tg.prec);
+      const int64_t cap = chunk_from_capacity
+                              ? std::max<int64_t>(1, (int64_t)(capacity / (column_footprint(db.b) * esz)))
+                              : tg.cap;
+      if (tg.prec == kTermFP32)
+        HK_TRY(run_block<float2>(d, db, tg, c, ldc, f, ldf, nrhs, (float2*)A, (float2*)B, cap, st, record));
+      else if (tg.prec == kTermDF64)
+        HK_TRY(run_block<df64c>(d, db, tg, c, ldc, f, ldf, nrhs, (df64c*)A, (df64c*)B, cap, st, record));
+      else
+        HK_TRY(run_block<double2>(d, db, tg, c, ldc, f, ldf, nrhs, (double2*)A, (double2*)B, cap, st, record));
+    }
   }
   return HANKEL_OK;
 }
@@ -694,15 +768,16 @@ int dev_exec_static(hankel_plan_s* p, const double* c, double* f, void* stream) 
   const HostPlan& hp = p->hp;
   DevicePlan* d = p->dev;
   const int64_t N = hp.opt.N;
-  // Layout of the static array (bytes): [bufA | bufB | near partial sums], elements of the
-  // plan's precision.
-  const size_t esz = d->fp32 ? sizeof(float2) : sizeof(double2);
-  const size_t total_elems = (size_t)HANKEL_STATIC_SCRATCH_BYTES / esz;
-  const size_t partial_elems = ((size_t)d->nslots + 1) / 2 + 1;
+  // Layout of the static array (bytes): [bufA | bufB | near partial sums]; the partial sums
+  // are doubles (floats for FP32 plans).
+  const size_t total_bytes = (size_t)HANKEL_STATIC_SCRATCH_BYTES;
+  const size_t partial_bytes = ((size_t)d->nslots + 1) * sizeof(double);
   size_t foot_max = 0;
-  for (const DevBlock& db : d->blocks) foot_max = std::max(foot_max, column_footprint(db.b));
-  if (2 * foot_max + partial_elems > total_elems) return HANKEL_EUNSUPPORTED;
-  const size_t per_buf = (total_elems - partial_elems) / 2;
+  for (const DevBlock& db : d->blocks)
+    for (int j = 0; j < db.ng; ++j)
+      foot_max = std::max(foot_max, column_footprint(db.b) * term_esz(db.g[j].prec));
+  if (2 * foot_max + partial_bytes > total_bytes) return HANKEL_EUNSUPPORTED;
+  const size_t per_buf = ((total_bytes - partial_bytes) / 2) & ~(size_t)255;
 
   int cur = -1;
   cudaGetDevice(&cur);
@@ -715,8 +790,8 @@ int dev_exec_static(hankel_plan_s* p, const double* c, double* f, void* stream) 
   }
   char* bytes = (char*)base;
   void* sA = bytes;
-  void* sB = bytes + per_buf * esz;
-  void* spartial = bytes + 2 * per_buf * esz;
+  void* sB = bytes + per_buf;
+  void* spartial = bytes + 2 * per_buf;
   cudaStream_t st = (cudaStream_t)stream;
   const int s = run_all(d, hp, c, N, f, N, 1, sA, sB, spartial, per_buf, true, st, false);
   if (s != HANKEL_OK) {

@@ -43,7 +43,11 @@ struct Block {
   int P = 0;
   std::vector<cplx> ucheb, vcheb;  // [rank][P]
   double lowrank_err = 0.0;        // largest error of the low-rank form on the validation entries
+  // Precision of each transform (li < rank, or < lcols.size() for direct blocks): kTermFP64,
+  // kTermDF64 or kTermFP32.
+  std::vector<int8_t> tprec;
 };
+enum TermPrecision { kTermFP64 = 0, kTermDF64 = 1, kTermFP32 = 2 };
 
 // One stacked column of a block: the row function rowpert(k)^u1 rowvar(k)^(delta-1/2)
 // times the column function colpow(n)^u1 omt(n)^(delta-1/2) sum_u2 G[u2] beta(n)^u2.

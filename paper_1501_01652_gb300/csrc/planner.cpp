@@ -845,6 +845,52 @@ void compress_blocks(HostPlan& hp) {
   }
 }
 
+// Precision of each transform of a block. The rounding error of a term computed in precision
+// u grows with u times the size of its contribution, max_k |U_l(k)| max_n |V_l(n)| (per unit of
+// ||c||_1; bounded above by the Chebyshev grid maxima times the squared Lebesgue constant
+// (2/pi) ln P + 1 of the interpolants, below by the grid maxima). In AUTO plans of FP64 or DF64
+// precision a term takes the lowest precision whose bound stays within
+//   max(u_plan / 4, eps / 200) x (the largest grid size of the block's terms),
+// i.e. a quarter of the rounding bound of the block's leading term in the plan precision, or
+// a two-hundredth of the requested accuracy; the terms of a low-rank form shrink geometrically
+// (about 1e-4 per term for the DHT), so only the leading ones keep the plan precision. Direct
+// blocks (no low-rank form) and FP32 plans keep one precision for every transform.
+constexpr double kUnitFP64 = 1.1102230246251565e-16;  // 2^-53
+constexpr double kUnitDF64 = 1.4210854715202004e-14;  // 2^-46: double-float with sloppy sums
+constexpr double kUnitFP32 = 5.9604644775390625e-08;  // 2^-24
+
+void assign_term_precision(HostPlan& hp) {
+  const int base = hp.fp32 ? kTermFP32 : hp.df64 ? kTermDF64 : kTermFP64;
+  const bool mixed =
+      hp.opt.precision == HANKEL_PREC_AUTO && !hp.fp32 && !(hp.opt.flags & HANKEL_FLAG_UNIFORM_TERMS);
+  for (Block& b : hp.blocks) {
+    const int nl = b.rank ? b.rank : (int)b.lcols.size();
+    b.tprec.assign((size_t)nl, (int8_t)base);
+    if (!mixed || !b.rank) continue;
+    std::vector<double> lo(nl), hi(nl);
+    const double lam = 2.0 / kPi * std::log((double)b.P) + 1.0;
+    double A = 0.0;
+    for (int li = 0; li < nl; ++li) {
+      double mu = 0.0, mv = 0.0;
+      for (int j = 0; j < b.P; ++j) {
+        mu = std::max(mu, std::abs(b.ucheb[(size_t)li * b.P + j]));
+        mv = std::max(mv, std::abs(b.vcheb[(size_t)li * b.P + j]));
+      }
+      lo[li] = mu * mv;
+      hi[li] = lam * lam * mu * mv;
+      A = std::max(A, lo[li]);
+    }
+    const double ub = base == kTermFP64 ? kUnitFP64 : kUnitDF64;
+    const double tau = std::max(0.25 * ub, hp.opt.eps / 200.0) * A;
+    for (int li = 0; li < nl; ++li) {
+      int p = base;
+      if (base == kTermFP64 && kUnitDF64 * hi[li] <= tau) p = kTermDF64;
+      if (kUnitFP32 * hi[li] <= tau) p = kTermFP32;
+      b.tprec[li] = (int8_t)p;
+    }
+  }
+}
+
 // Subdivision of the far blocks (an addition to the partition of Eq. 19). The blocks of
 // Eq. (19) touch the near field at one corner, where z~ ~ s and every stacked column is
 // needed, but stretch to z~ ~ N: away from that corner the Hankel tail and the perturbation
@@ -974,6 +1020,7 @@ int build_host_plan(const hankel_options& opt, HostPlan& hp) {
   build_columns(hp);
   select_columns(hp);
   compress_blocks(hp);
+  assign_term_precision(hp);
   build_jtable(hp);
   return HANKEL_OK;
 }

@@ -155,6 +155,40 @@ def test_df64_sparse_vectors(eps):
     assert np.all(np.abs(f - ref) <= 10 * eps * l1)
 
 
+@pytest.mark.parametrize("eps", [1e-15, 1e-12, 1e-8])
+def test_mixed_term_precision(eps):
+    # the small low-rank terms in double-float and FP32 (AUTO) against every term in the plan
+    # precision: both meet the bar, and they differ by far less than it
+    N = 2 ** 17
+    c = coefficients("normal", N, 4, 7500)
+    rows = sample_rows(N, 64, 29)
+    f, plan = _run("dht", 0, N, eps, c)
+    terms = [sum(b["terms"][i] for b in plan.blocks()) for i in range(3)]
+    assert terms[1] + terms[2] > 0 and terms[2] > 0
+    g, _ = _run("dht", 0, N, eps, c, mixed_terms=False)
+    ref = oracle.transform("dht", 0, N, c, rows=rows)
+    l1 = np.abs(c).sum(axis=1, keepdims=True)
+    assert np.all(np.abs(f[:, rows] - ref) <= 10 * eps * l1)
+    assert np.all(np.abs(g[:, rows] - ref) <= 10 * eps * l1)
+    assert np.all(np.abs(f - g) <= eps * l1)
+
+
+@pytest.mark.parametrize("eps", [1e-15, 1e-12])
+def test_mixed_terms_sparse_vectors(eps):
+    # spikes: every term's rounding sits on a few columns
+    N = 20000
+    rng = np.random.default_rng(7600)
+    c = np.zeros((8, N))
+    for r in range(8):
+        idx = rng.choice(N, size=1 + r % 3, replace=False)
+        c[r, idx] = rng.standard_normal(idx.size)
+    f, plan = _run("dht", 0, N, eps, c)
+    assert sum(b["terms"][2] for b in plan.blocks()) > 0
+    ref = oracle.transform("dht", 0, N, c)
+    l1 = np.abs(c).sum(axis=1, keepdims=True)
+    assert np.all(np.abs(f - ref) <= 10 * eps * l1)
+
+
 @pytest.mark.parametrize("eps", [1e-4, 1e-5])
 def test_fp32_workload_size_sampled_rows(eps):
     N = 2 ** 20

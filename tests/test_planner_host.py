@@ -54,6 +54,29 @@ def test_precision_policy():
         hk.params("dht", 0, 4096, 9e-12, precision="df64")
 
 
+@pytest.mark.parametrize("eps,base", [(1e-15, 0), (1e-12, 0), (1e-8, 1), (1e-4, 2)])
+def test_term_precision_split(eps, base):
+    # AUTO plans run the small terms of a block's low-rank form in a lower precision; the
+    # largest term of every block keeps the plan precision, and no term goes above it; uniform
+    # plans and forced precisions keep one precision for every transform
+    N = 2 ** 18
+    bl = hk.Plan("dht", 0, N, eps, host_only=True).blocks()
+    for b in bl:
+        assert sum(b["terms"]) == b["ncols"]
+        if not b["lowrank"] or base == 2:
+            assert b["terms"][base] == b["ncols"]
+        else:
+            assert b["terms"][base] >= 1
+            assert all(b["terms"][q] == 0 for q in range(base))
+    if base < 2:
+        assert sum(b["terms"][q] for b in bl for q in range(base + 1, 3)) > 0
+    u = hk.Plan("dht", 0, N, eps, host_only=True, mixed_terms=False)
+    assert all(b["terms"][base] == b["ncols"] for b in u.blocks())
+    if base == 0:
+        f = hk.Plan("dht", 0, N, eps, host_only=True, precision="fp64")
+        assert all(b["terms"][0] == b["ncols"] for b in f.blocks())
+
+
 def test_thin_blocks_are_segmented_at_workload_size():
     # Eq. (19) at N = 2^20 (P = 3): one square block and three thin ones on each side
     p = hk.Plan("dht", 0, 2 ** 20, 1e-15, host_only=True, refine=False)
