@@ -75,6 +75,40 @@ __device__ __forceinline__ df64c coef_times(const void* p, int64_t i, df64c v) {
   return mkc(c * v.x, c * v.y);
 }
 
+// The double-float butterfly: t = w a1 once, with the exact products of the high parts (FMA),
+// their difference by two-sum and the cross terms added into the low part, left unnormalised
+// (|low| << |high|); then y0 = a0 + t and y1 = a0 - t, each a two-sum of the high parts with
+// the low parts added and one renormalisation. About 76 FP32 operations against 90 for the
+// FMA-folded form with double-float fmar.
+__device__ __forceinline__ df64 df_add_pair(df64 a, float sh, float sl) {
+  const float u = a.h + sh;
+  const float bb = u - a.h;
+  float v = (a.h - (u - bb)) + (sh - bb);
+  v += a.l + sl;
+  return fast_two_sum(u, v);
+}
+// x0 y0 - x1 y1 (sign = -1) or x0 y0 + x1 y1 (sign = +1) as an unnormalised pair (h, l)
+__device__ __forceinline__ void df_dot2(df64 x0, df64 y0, df64 x1, df64 y1, float sign, float& h, float& l) {
+  const float p = x0.h * y0.h, q = sign * (x1.h * y1.h);
+  const float ep = fmaf(x0.h, y0.h, -p), eq = sign * fmaf(x1.h, y1.h, -sign * q);
+  h = p + q;
+  const float bb = h - p;
+  l = ((p - (h - bb)) + (q - bb)) + (ep + eq);
+  l = fmaf(x0.h, y0.l, l);
+  l = fmaf(x0.l, y0.h, l);
+  l = fmaf(sign * x1.h, y1.l, l);
+  l = fmaf(sign * x1.l, y1.h, l);
+}
+template <>
+__device__ __forceinline__ void bfly2<df64c>(df64c& a0, df64c& a1, df64c w) {
+  float tx, lx, ty, ly;
+  df_dot2(w.x, a1.x, w.y, a1.y, -1.0f, tx, lx);
+  df_dot2(w.x, a1.y, w.y, a1.x, 1.0f, ty, ly);
+  const df64c y0 = mkc(df_add_pair(a0.x, tx, lx), df_add_pair(a0.y, ty, ly));
+  a1 = mkc(df_add_pair(a0.x, -tx, -lx), df_add_pair(a0.y, -ty, -ly));
+  a0 = y0;
+}
+
 // Twiddle deferral. A pass of radix R multiplies input e of the R-point DFT of sequence
 // (p, q) by the pass twiddle W_F^{pt e} (pt = p s). The pass twiddle is never applied on its
 // own: in a Stockham sub-stage of stride s_k, the inputs e = qq + s_k (Q pp + j) of a butterfly

@@ -44,7 +44,8 @@ struct DevColSpec {
 
 // A near-field tile: rows k0..k0+31 (one lane each) over columns n0..n1, each lane stopping at
 // its row's prefix end. slot < 0: the tile covers the group's whole prefix and writes f;
-// otherwise lane j writes partial slot (slot + j * ntile + t).
+// otherwise lane j writes its sum for vector r to partial[(slot + j ntile) nrhs + r ntile + t]
+// (the pieces of one row and vector are consecutive).
 struct NearItem {
   int64_t k0, n0, n1, slot;
   int32_t ntile, t;

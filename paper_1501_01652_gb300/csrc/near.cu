@@ -23,12 +23,38 @@ constexpr int kMaxRhsGroup = 16;
 
 template <class R>
 __device__ __forceinline__ R table_j(const R* __restrict__ jtab, int64_t jt_n, int deg, R z) {
-  int64_t i = (int64_t)(z * (R)kJTabSub);
-  i = i < 0 ? 0 : (i >= jt_n ? jt_n - 1 : i);
+  int i = (int)(z * (R)kJTabSub);
+  i = i < 0 ? 0 : (i >= jt_n ? (int)jt_n - 1 : i);
   const R d = z - ((R)i + (R)0.5) * ((R)1 / (R)kJTabSub);
-  const R* t = jtab + i * (deg + 1);
+  const R* t = jtab + (int64_t)i * (deg + 1);
   R v = __ldg(&t[deg]);
   for (int j = deg - 1; j >= 0; --j) v = fmar(v, d, __ldg(&t[j]));
+  return v;
+}
+
+// FP64: the interval i = floor(z 2^kJTabLog) and its left end come from the bits of z (z >= 0)
+// with integer operations, so the FP64 pipe only computes d = z - left - 1/(2 kJTabSub) and
+// the polynomial.
+template <>
+__device__ __forceinline__ double table_j<double>(const double* __restrict__ jtab, int64_t jt_n, int deg, double z) {
+  const long long bits = __double_as_longlong(z);
+  const int sh = 52 + 1023 - kJTabLog - (int)((bits >> 52) & 0x7ff);  // mantissa bits below 1/kJTabSub
+  long long i = 0;
+  double left = 0.0;  // z < 1/kJTabSub (and z = 0)
+  if (sh <= 0) {
+    i = jt_n;  // z >= 2^(52 - kJTabLog): beyond any table
+  } else if (sh <= 52) {
+    i = ((bits & 0xfffffffffffffLL) | (1LL << 52)) >> sh;
+    left = __longlong_as_double(bits & ~((1LL << sh) - 1));
+  }
+  if (i >= jt_n) {
+    i = jt_n - 1;
+    left = (double)i * (1.0 / kJTabSub);
+  }
+  const double d = (z - left) - 0.5 / kJTabSub;
+  const double* t = jtab + i * (deg + 1);
+  double v = __ldg(&t[deg]);
+  for (int j = deg - 1; j >= 0; --j) v = fma(v, d, __ldg(&t[j]));
   return v;
 }
 
@@ -63,7 +89,7 @@ __global__ void __launch_bounds__(256) k_near(const NearItem* __restrict__ items
     for (int g = 0; g < G; ++g) {
       if (r0 + g >= nrhs) break;
       if (it.slot < 0) f[(int64_t)(r0 + g) * ldf + k - 1] = acc[g];
-      else partial[(it.slot + (int64_t)lane * it.ntile + it.t) * nrhs + r0 + g] = acc[g];
+      else partial[(it.slot + (int64_t)lane * it.ntile) * nrhs + (int64_t)(r0 + g) * it.ntile + it.t] = acc[g];
     }
   }
 }
@@ -158,22 +184,30 @@ __global__ void __launch_bounds__(256) k_near_df(const NearItem* __restrict__ it
       if (r0 + g >= nrhs) break;
       const double v = (double)hi[g] + (double)lo[g];
       if (it.slot < 0) f[(int64_t)(r0 + g) * ldf + k - 1] = v;
-      else partial[(it.slot + (int64_t)lane * it.ntile + it.t) * nrhs + r0 + g] = v;
+      else partial[(it.slot + (int64_t)lane * it.ntile) * nrhs + (int64_t)(r0 + g) * it.ntile + it.t] = v;
     }
   }
 }
 
+// Rows whose prefix spans several tiles: the partial sums of row k and vector rr are the
+// npieces consecutive values at slot0 nrhs + rr npieces. A warp per row; lane l adds the
+// pieces l, l + 32, ... in order and the lanes combine in a fixed shuffle tree, so the result
+// does not depend on scheduling.
 template <class R>
 __global__ void k_near_combine(const NearRow* __restrict__ rows, int64_t nrows, const R* __restrict__ partial,
                                int nrhs, double* f, int64_t ldf) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nrows * nrhs) return;
-  const int64_t i = t / nrhs;
-  const int rr = (int)(t - i * nrhs);
-  const NearRow row = rows[i];
-  R s = 0;
-  for (int j = 0; j < row.npieces; ++j) s += partial[(row.slot0 + j) * nrhs + rr];
-  f[(int64_t)rr * ldf + row.k - 1] = (double)s;
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= nrows) return;
+  const NearRow row = rows[w];
+  for (int rr = 0; rr < nrhs; ++rr) {
+    const R* p = partial + row.slot0 * nrhs + (int64_t)rr * row.npieces;
+    R s = 0;
+    for (int j = lane; j < row.npieces; j += 32) s += p[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) f[(int64_t)rr * ldf + row.k - 1] = (double)s;
+  }
 }
 
 }  // namespace
@@ -203,10 +237,8 @@ void launch_near(const NearItem* items, int64_t nitems, const NearRow* mrows, in
                  int64_t ldf, const R* r, const R* om, const R* jtab, int64_t jt_n, int deg, cudaStream_t st) {
   if (cf) launch_near_t<R, float>(items, nitems, nend, N, partial, nrhs, cf, N, f, ldf, r, om, jtab, jt_n, deg, st);
   else launch_near_t<R, double>(items, nitems, nend, N, partial, nrhs, c, ldc, f, ldf, r, om, jtab, jt_n, deg, st);
-  if (nmrows > 0) {
-    const int64_t n = nmrows * nrhs;
-    k_near_combine<R><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(mrows, nmrows, partial, nrhs, f, ldf);
-  }
+  if (nmrows > 0)
+    k_near_combine<R><<<(unsigned)((nmrows * 32 + 255) / 256), 256, 0, st>>>(mrows, nmrows, partial, nrhs, f, ldf);
 }
 
 void launch_near_df(const NearItem* items, int64_t nitems, const NearRow* mrows, int64_t nmrows,
@@ -226,10 +258,9 @@ void launch_near_df(const NearItem* items, int64_t nitems, const NearRow* mrows,
   else
     k_near_df<kMaxRhsGroup><<<grid, 256, 0, st>>>(items, nitems, nend, N, partial, nrhs, cd, f, ldf, r, om, jtab,
                                                   jt_n, deg);
-  if (nmrows > 0) {
-    const int64_t n = nmrows * nrhs;
-    k_near_combine<double><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(mrows, nmrows, partial, nrhs, f, ldf);
-  }
+  if (nmrows > 0)
+    k_near_combine<double><<<(unsigned)((nmrows * 32 + 255) / 256), 256, 0, st>>>(mrows, nmrows, partial, nrhs, f,
+                                                                                ldf);
 }
 
 template void launch_near<double>(const NearItem*, int64_t, const NearRow*, int64_t, const int64_t*, int64_t,

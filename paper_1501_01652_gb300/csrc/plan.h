@@ -15,7 +15,8 @@ typedef std::complex<double> cplx;
 // by one stacked column (2T+K-2 of Section 5.1 at eps = 1e-16 is 10).
 constexpr int kMaxU = 16;
 // Near-field Bessel table: intervals of width 1 with Taylor polynomials of this degree.
-constexpr int kJTabSub = 8;      // near-field J table: Taylor intervals per unit of z
+constexpr int kJTabLog = 4;                 // near-field J table: 2^kJTabLog Taylor intervals
+constexpr int kJTabSub = 1 << kJTabLog;     // per unit of z
 constexpr int kJTabDegMax = 10;  // largest Taylor degree of the near-field J table
 
 // How a block's chirp-z convolution is carried out.
