@@ -68,8 +68,9 @@ enum hankel_grid {
 enum hankel_precision {
   HANKEL_PREC_AUTO = 0,  /* FP64 below eps = 1e-11, DF64 transforms for 1e-11 <= eps < 1e-5, FP32 stages at
                             eps >= 1e-5; in FP64 and DF64 plans, each term of a block's low-rank form runs
-                            in the lowest precision whose rounding bound stays within a quarter of the
-                            block's leading term in the plan precision, or within eps / 200 of it
+                            in the lowest precision whose rounding bound (from the sums of the absolute
+                            Chebyshev coefficients of its factors) stays within a quarter of the block's
+                            leading term in the plan precision, or within eps / 200 of it
                             (hankel_block.terms_*; HANKEL_FLAG_UNIFORM_TERMS turns this off) */
   HANKEL_PREC_FP64 = 1,  /* every stage in FP64 */
   HANKEL_PREC_FP32 = 2,  /* FP32 stages; refused (HANKEL_EUNSUPPORTED) when eps < 1e-5 */

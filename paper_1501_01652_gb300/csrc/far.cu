@@ -41,8 +41,7 @@ __global__ void __launch_bounds__(256) k_out(OutArgs a) {
   const int64_t kp = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (kp >= a.R) return;
   const int64_t i = a.k0 - 1 + kp;
-  const double2 wud = a.wU[kp];
-  const C wu = mkc((R)wud.x, (R)wud.y);
+  const C wu = ldgc(reinterpret_cast<const C*>(a.wU) + kp);
   const int64_t sg = kp / a.Sr;
   const C* Y = reinterpret_cast<const C*>(a.Y) + sg * a.F + (kp - sg * a.Sr) + a.off;
   const C* Ut = reinterpret_cast<const C*>(a.Ut) + kp;

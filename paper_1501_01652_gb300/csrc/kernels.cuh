@@ -74,7 +74,7 @@ struct OutArgs {
   int ncols;          // stacked columns (transforms) of the block per right-hand side
   double* f;          // f[rhs * ldf + k-1] += ...
   int64_t ldf;
-  const double2* wU;  // row chirp of the block
+  const void* wU;     // row chirp of the block in the plan precision (double2, df64c or float2)
   const void* Ut;     // [ncols][R] block row table (double2 or float2)
 };
 

@@ -847,9 +847,10 @@ void compress_blocks(HostPlan& hp) {
 
 // Precision of each transform of a block. The rounding error of a term computed in precision
 // u grows with u times the size of its contribution, max_k |U_l(k)| max_n |V_l(n)| (per unit of
-// ||c||_1; bounded above by the Chebyshev grid maxima times the squared Lebesgue constant
-// (2/pi) ln P + 1 of the interpolants, below by the grid maxima). In AUTO plans of FP64 or DF64
-// precision a term takes the lowest precision whose bound stays within
+// ||c||_1). Each factor is a polynomial interpolant p = sum_j a_j T_j in the Chebyshev
+// variable, so max |p| <= sum_j |a_j| bounds it above, and the largest value at the Chebyshev
+// points bounds it below. In AUTO plans of FP64 or DF64 precision a term takes the lowest
+// precision whose upper bound stays within
 //   max(u_plan / 4, eps / 200) x (the largest grid size of the block's terms),
 // i.e. a quarter of the rounding bound of the block's leading term in the plan precision, or
 // a two-hundredth of the requested accuracy; the terms of a low-rank form shrink geometrically
@@ -868,7 +869,17 @@ void assign_term_precision(HostPlan& hp) {
     b.tprec.assign((size_t)nl, (int8_t)base);
     if (!mixed || !b.rank) continue;
     std::vector<double> lo(nl), hi(nl);
-    const double lam = 2.0 / kPi * std::log((double)b.P) + 1.0;
+    // sum_j |a_j| of the interpolant through values f_i at the points cos(pi (i + 1/2) / P):
+    // a_j = (2 - [j = 0]) / P sum_i f_i cos(pi j (i + 1/2) / P)
+    auto coef_sum = [&](const std::vector<cplx>& vals, int li) {
+      double tot = 0.0;
+      for (int j = 0; j < b.P; ++j) {
+        cplx aj(0.0, 0.0);
+        for (int i = 0; i < b.P; ++i) aj += vals[(size_t)li * b.P + i] * std::cos(kPi * j * (i + 0.5) / b.P);
+        tot += std::abs(aj) * (j == 0 ? 1.0 : 2.0) / b.P;
+      }
+      return tot;
+    };
     double A = 0.0;
     for (int li = 0; li < nl; ++li) {
       double mu = 0.0, mv = 0.0;
@@ -877,7 +888,8 @@ void assign_term_precision(HostPlan& hp) {
         mv = std::max(mv, std::abs(b.vcheb[(size_t)li * b.P + j]));
       }
       lo[li] = mu * mv;
-      hi[li] = lam * lam * mu * mv;
+      // slightly above the coefficient sums, for their own rounding
+      hi[li] = (1.0 + 1e-12) * coef_sum(b.ucheb, li) * coef_sum(b.vcheb, li);
       A = std::max(A, lo[li]);
     }
     const double ub = base == kTermFP64 ? kUnitFP64 : kUnitDF64;
