@@ -37,6 +37,13 @@ FP64_MEASURED_GFLOPS = 1004.0      # DFMA microbenchmark on this part (2 x 502 G
 # 4096 CTAs of 16 x 128 points: 145.1 MB read + 93.9 MB written, 268.4 MB algorithmic; the
 # spectrum is L2-resident and part of the output is still in L2 at kernel end).
 FFT_TRAFFIC_RATIO = (145.12 + 93.91) / 268.44
+# The double-float transforms are bound by the FP32 pipe: 152 SMs x 128 lanes x 2.07 GHz =
+# 40.3 T instructions/s. Their radix-2 butterfly (two double-float dot products of 16 FP32
+# instructions each, four renormalised sums of 11) takes 76 FP32 instructions for the 10 flops
+# of the 5 F log2 F model, so the pipe bounds the model rate at 40.3 T / 7.6.
+FP32_ISSUE_PEAK = 152 * 128 * 2.07e9
+DF64_INSTR_PER_FLOP = 7.6
+DF64_PEAK_GFLOPS = FP32_ISSUE_PEAK / DF64_INSTR_PER_FLOP / 1e9
 METRIC = "DHT-0 coeffs/s at N=2^20 (eps=1e-8,1e-15) served vs plain FP64; p50/p99 ms"
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -337,26 +344,48 @@ def run_ours(args):
     coeffs_per_step = len(plans) * N * B
     value, total_ms = aggregate(world, coeffs_per_step, args.steps, sum(step_ms), dev)
 
-    # dominant kernel: the FFT passes of the FP64 transforms (of the FP32 transforms when every
-    # plan is FP32); the double-float and FP32 transforms of the mixed plans are reported beside it
+    # dominant kernel: the FFT passes of the transform class (FP64, double-float or FP32) that
+    # takes the most time; the other classes are reported beside it
     precs = [p.info["precision"] for p in plans]
-    fp32 = all(q == 2 for q in precs)
-    key = "fft_fp32" if fp32 else "fft"
-    fft_ms = sum(st[key]["ms"] for st in stats)
-    fft_flops = sum(st[key]["flops"] for st in stats)
-    fft_launches = sum(st[key]["launches"] for st in stats)
-    fft_bytes = sum(st[key]["bytes"] for st in stats)
-    achieved = fft_flops / (fft_ms / 1000.0) / 1e9 if fft_ms > 0 else 0.0
     launches = sum(st[k]["launches"] for st in stats for k in st)
     stage_ms = {k: round(sum(st[k]["ms"] for st in stats) / args.steps, 3) for k in stats[0]}
-    others = {}
-    for k2, name in (("fft_df64", "df64_transforms"), ("fft_fp32", "fp32_transforms")):
-        if k2 == key:
-            continue
+
+    def fft_entry(k2):
         ms2 = sum(st[k2]["ms"] for st in stats)
-        if ms2 > 0:
-            others[name] = {"fft_ms_per_step": ms2 / args.steps,
-                            "gflops_5FlogF": sum(st[k2]["flops"] for st in stats) / (ms2 / 1000.0) / 1e9}
+        fl = sum(st[k2]["flops"] for st in stats)
+        nl = sum(st[k2]["launches"] for st in stats)
+        by = sum(st[k2]["bytes"] for st in stats)
+        ach = fl / (ms2 / 1000.0) / 1e9 if ms2 > 0 else 0.0
+        gbs = by / (ms2 / 1000.0) / 1e9 if ms2 > 0 else None
+        common = {"fft_ms_per_step": ms2 / args.steps, "launches": nl, "hbm_gbs_of_passes": gbs,
+                  "flops_model": "5 F log2 F per column transform, plus 6 F per spectrum product folded "
+                                 "into an inverse transform"}
+        if k2 == "fft":
+            e = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                 "frac": ach / FP64_PEAK_GFLOPS,
+                 "traffic": FFT_TRAFFIC_RATIO * by / nl if nl else None,
+                 "traffic_unit": "DRAM bytes per launch (ncu ratio x algorithmic bytes)",
+                 "frac_of_measured_fp64": ach / FP64_MEASURED_GFLOPS,
+                 "kernel": "k_fft_pass_reg / k_fft_small<double2> (FP64 transforms, forward + inverse)",
+                 "peak_source": "nominal FP64 from unit counts and clock (152 SM x 4 flop/clk x 2.07 GHz)"}
+        elif k2 == "fft_df64":
+            e = {"bound": "alu", "achieved": ach, "peak": DF64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                 "frac": ach / DF64_PEAK_GFLOPS, "traffic": None,
+                 "kernel": "k_fft_pass_reg / k_fft_small<df64c> (double-float transforms, forward + inverse)",
+                 "peak_source": "FP32 pipe (152 SM x 128 lanes x 2.07 GHz) / 7.6 FP32 instructions per "
+                                "double-float flop of the butterfly"}
+        else:
+            peak, src = hbm_peak()
+            e = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": (gbs or 0.0) / peak,
+                 "traffic": None, "peak_source": src,
+                 "kernel": "k_fft_pass_reg / k_fft_small<float2> (FP32 transforms, forward + inverse)",
+                 "bytes_model": "each pass reads and writes every point once (16 B per complex float)",
+                 "gflops_5FlogF": ach}
+        e.update(common)
+        return e
+
+    classes = [k2 for k2 in ("fft", "fft_df64", "fft_fp32") if sum(st[k2]["ms"] for st in stats) > 0]
+    dominant = max(classes, key=lambda k2: sum(st[k2]["ms"] for st in stats)) if classes else "fft"
     terms = [0, 0, 0]
     for p in plans:
         for b in p.blocks():
@@ -394,25 +423,9 @@ def run_ours(args):
         served_cps_p, served_lat = serve_stream(hk, served_kw, reqs, rate, 2)
         plain_cps_p, plain_lat = serve_stream(hk, plain_kw, reqs, rate, 2)
 
-    pass_gbs = fft_bytes / (fft_ms / 1000.0) / 1e9 if fft_ms > 0 else None
-    if fp32:
-        peak, src = hbm_peak()
-        roofline = {"bound": "hbm", "achieved": pass_gbs, "peak": peak, "unit": "GB/s",
-                    "frac": (pass_gbs or 0.0) / peak, "traffic": None, "peak_source": src,
-                    "kernel": "k_fft_pass_reg / k_fft_small (FP32 transforms, forward + inverse)",
-                    "bytes_model": "each pass reads and writes every point once (16 B per complex float)",
-                    "launches": fft_launches}
-    else:
-        roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                    "frac": achieved / FP64_PEAK_GFLOPS,
-                    "traffic": FFT_TRAFFIC_RATIO * fft_bytes / fft_launches if fft_launches else None,
-                    "traffic_unit": "DRAM bytes per launch (ncu ratio x algorithmic bytes)",
-                    "frac_of_measured_fp64": achieved / FP64_MEASURED_GFLOPS, "hbm_gbs_of_passes": pass_gbs,
-                    "kernel": "k_fft_pass_reg / k_fft_small (FP64 transforms, forward + inverse)",
-                    "plans": "the FP64 transforms of every plan",
-                    "flops_model": "5 F log2 F per column transform, plus 6 F per spectrum product folded into an inverse transform", "launches": fft_launches,
-                    "peak_source": "nominal FP64 from unit counts and clock (152 SM x 4 flop/clk x 2.07 GHz)"}
-        roofline.update(others)
+    roofline = fft_entry(dominant)
+    names = {"fft": "fp64_transforms", "fft_df64": "df64_transforms", "fft_fp32": "fp32_transforms"}
+    roofline["others"] = {names[k2]: fft_entry(k2) for k2 in classes if k2 != dominant}
     term_split = {"fp64": terms[0], "df64": terms[1], "fp32": terms[2],
                   "unit": "far-field transforms per right-hand side, summed over blocks and plans"}
     if rank != 0:

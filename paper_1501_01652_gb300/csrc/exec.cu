@@ -51,6 +51,35 @@ struct DevBlock {
   int ng = 0;
 };
 
+// Chebyshev coefficients of the interpolant through the values f_i at cos(pi (i + 1/2) / P):
+// a_j = (2 - [j = 0]) / P sum_i f_i cos(pi j (2i + 1) / (2P)). The angle is reduced in integers
+// (m = j (2i + 1) mod 4P, then to a quadrant and an angle below pi/2) and the sums are
+// compensated (Neumaier), so each coefficient is good to a few units in the last place.
+void cheb_coeffs(const cplx* f, int P, double2* a) {
+  const double pi = 3.14159265358979323846;
+  std::vector<double> cs(4 * (size_t)P);  // cos(pi m / (2P)), m < 4P
+  for (int m = 0; m < 4 * P; ++m) {
+    const int q = m / P, r = m % P;
+    const double th = pi * r / (2.0 * P);
+    cs[m] = q == 0 ? std::cos(th) : q == 1 ? -std::sin(th) : q == 2 ? -std::cos(th) : std::sin(th);
+  }
+  auto add = [](double& sum, double& comp, double x) {
+    const double t = sum + x;
+    comp += std::fabs(sum) >= std::fabs(x) ? (sum - t) + x : (x - t) + sum;
+    sum = t;
+  };
+  for (int j = 0; j < P; ++j) {
+    double sr = 0.0, cr = 0.0, si = 0.0, ci = 0.0;
+    for (int i = 0; i < P; ++i) {
+      const double c = cs[((int64_t)j * (2 * i + 1)) % (4 * P)];
+      add(sr, cr, f[i].real() * c);
+      add(si, ci, f[i].imag() * c);
+    }
+    const double w = (j == 0 ? 1.0 : 2.0) / P;
+    a[j] = make_double2(w * (sr + cr), w * (si + ci));
+  }
+}
+
 // Indices li of the block's transforms per precision.
 void term_lists(const Block& b, std::vector<int> (&lists)[3]) {
   for (auto& l : lists) l.clear();
@@ -423,13 +452,12 @@ int dev_plan_create(hankel_plan_s* p) {
       double* scd = nullptr;
       size_t nuc = 0, nlm = 0;
       if (b.rank) {
+        // the interpolants' Chebyshev coefficients (the kernels sum the series by Clenshaw)
         std::vector<double2> u((size_t)tg.nl * b.P), v((size_t)tg.nl * b.P);
-        for (int j = 0; j < tg.nl; ++j)
-          for (int q = 0; q < b.P; ++q) {
-            const cplx cu = b.ucheb[(size_t)lists[t][j] * b.P + q], cv = b.vcheb[(size_t)lists[t][j] * b.P + q];
-            u[(size_t)j * b.P + q] = make_double2(cu.real(), cu.imag());
-            v[(size_t)j * b.P + q] = make_double2(cv.real(), cv.imag());
-          }
+        for (int j = 0; j < tg.nl; ++j) {
+          cheb_coeffs(&b.ucheb[(size_t)lists[t][j] * b.P], b.P, &u[(size_t)j * b.P]);
+          cheb_coeffs(&b.vcheb[(size_t)lists[t][j] * b.P], b.P, &v[(size_t)j * b.P]);
+        }
         nuc = u.size();
         HK_TRY(upload(d, &uc, u.data(), u.size()));
         HK_TRY(upload(d, &vc, v.data(), v.size()));

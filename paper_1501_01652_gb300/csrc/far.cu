@@ -95,27 +95,22 @@ __global__ void __launch_bounds__(kMacPts* kMacLanes) k_seg_mac(const C* __restr
   }
 }
 
-// Barycentric interpolation at x of values at the P Chebyshev points cos(pi (i + 1/2) / P)
-// (first kind), for nl value sets [nl][P] at once: out[li] for li < nl.
-__device__ __forceinline__ double cheb_weights(double x, int P, double* lam) {
-  double den = 0.0;
-  int hit = -1;
-  for (int i = 0; i < P; ++i) {
-    double sn, cs;
-    sincospi((i + 0.5) / P, &sn, &cs);
-    const double d = x - cs;
-    if (d == 0.0) hit = i;
-    lam[i] = ((i & 1) ? -sn : sn) / (d == 0.0 ? 1.0 : d);
-    den += lam[i];
+// Chebyshev series sum_{j < P} a_j T_j(x) by Clenshaw's recurrence (complex a_j):
+// b_j = a_j + 2 x b_{j+1} - b_{j+2}, value a_0 + x b_1 - b_2.
+__device__ __forceinline__ double2 cheb_series(const double2* __restrict__ a, int P, double x) {
+  const double x2 = 2.0 * x;
+  double br = 0.0, bi = 0.0, cr = 0.0, ci = 0.0;  // b_{j+1}, b_{j+2}
+  for (int j = P - 1; j >= 1; --j) {
+    const double2 aj = __ldg(&a[j]);
+    const double tr = fma(x2, br, aj.x - cr), ti = fma(x2, bi, aj.y - ci);
+    cr = br;
+    ci = bi;
+    br = tr;
+    bi = ti;
   }
-  if (hit >= 0) {
-    for (int i = 0; i < P; ++i) lam[i] = i == hit ? 1.0 : 0.0;
-    return 1.0;
-  }
-  return den;
+  const double2 a0 = __ldg(&a[0]);
+  return make_double2(fma(x, br, a0.x - cr), fma(x, bi, a0.y - ci));
 }
-
-constexpr int kChebPMaxDev = 64;
 
 // The column table of a block: thread per column n, every li of the block.
 template <class C>
@@ -125,18 +120,10 @@ __global__ void __launch_bounds__(128) k_block_cols(BlockTabArgs a) {
     const int64_t i = a.n0 - 1 + np;
     const double2 w = a.wV[np];
     if (a.P > 0) {
-      double lam[kChebPMaxDev];
       const double x = a.ln1 > a.ln0 ? (2.0 * log((double)(a.n0 + np)) - a.ln0 - a.ln1) / (a.ln1 - a.ln0) : 0.0;
-      const double den = cheb_weights(x, a.P, lam);
       for (int li = 0; li < a.nl; ++li) {
-        const double2* v = a.vcheb + (int64_t)li * a.P;
-        double vr = 0.0, vi = 0.0;
-        for (int j = 0; j < a.P; ++j) {
-          vr = fma(lam[j], v[j].x, vr);
-          vi = fma(lam[j], v[j].y, vi);
-        }
-        vr /= den;
-        vi /= den;
+        const double2 v = cheb_series(a.vcheb + (int64_t)li * a.P, a.P, x);
+        const double vr = v.x, vi = v.y;
         const double sc = a.scale ? a.scale[li] : 1.0;
         Vt[(int64_t)li * a.C + np] = from_d2<C>(make_double2(sc * fma(vr, w.x, -vi * w.y), sc * fma(vr, w.y, vi * w.x)));
       }
@@ -167,18 +154,11 @@ __global__ void __launch_bounds__(128) k_block_rows(BlockTabArgs a) {
   for (int64_t kp = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; kp < a.R; kp += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = a.k0 - 1 + kp;
     if (a.P > 0) {
-      double lam[kChebPMaxDev];
       const double x = a.lk1 > a.lk0 ? (2.0 * log((double)(a.k0 + kp)) - a.lk0 - a.lk1) / (a.lk1 - a.lk0) : 0.0;
-      const double den = cheb_weights(x, a.P, lam);
       for (int li = 0; li < a.nl; ++li) {
-        const double2* u = a.ucheb + (int64_t)li * a.P;
-        double ur = 0.0, ui = 0.0;
-        for (int j = 0; j < a.P; ++j) {
-          ur = fma(lam[j], u[j].x, ur);
-          ui = fma(lam[j], u[j].y, ui);
-        }
+        const double2 u = cheb_series(a.ucheb + (int64_t)li * a.P, a.P, x);
         const double isc = a.scale ? 1.0 / a.scale[li] : 1.0;
-        Ut[(int64_t)li * a.R + kp] = from_d2<C>(make_double2(isc * ur / den, isc * ui / den));
+        Ut[(int64_t)li * a.R + kp] = from_d2<C>(make_double2(isc * u.x, isc * u.y));
       }
     } else {
       const double rv = a.nodes.rowvar[i], irv = a.nodes.inv_rowvar[i], rs = a.nodes.rs_rowvar[i];

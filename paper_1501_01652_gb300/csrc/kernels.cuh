@@ -79,8 +79,9 @@ struct OutArgs {
 };
 
 // Plan-time block tables (computed in FP64, stored in the plan precision). For a block with a
-// low-rank form, column li is V_li (Chebyshev interpolation of vcheb[li] in log n) and row li is
-// U_li (of ucheb[li] in log k); otherwise column li is the stacked column lmap[li]:
+// low-rank form, column li is V_li (the Chebyshev series vcheb[li] in the variable of log n on
+// [log n0, log n1]) and row li is U_li (ucheb[li] in log k); otherwise column li is the stacked
+// column lmap[li]:
 // colpow^u1 omt^(delta-1/2) poly(beta) and row li its rowpert^u1 rowvar^(delta-1/2).
 // Vt[li][np] = V_li(n0+np) wV[np] scale[li], Ut[li][kp] = U_li(k0+kp) / scale[li].
 struct BlockTabArgs {
@@ -88,8 +89,8 @@ struct BlockTabArgs {
   int64_t k0, R, n0, C;
   const int* lmap;       // direct form: the stacked column of each li
   int P;                 // low-rank form: Chebyshev points (0: direct form)
-  const double2* ucheb;  // [nl][P]
-  const double2* vcheb;  // [nl][P]
+  const double2* ucheb;  // [nl][P] Chebyshev coefficients of U_li
+  const double2* vcheb;  // [nl][P] Chebyshev coefficients of V_li
   double lk0, lk1, ln0, ln1;  // log k0, log k1, log n0, log n1
   NodeTables nodes;
   const DevColSpec* cols;
