@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "cplx.cuh"
 #include "kernels.cuh"
@@ -310,66 +311,111 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_pass_reg(const C* __restric
 constexpr int kSmallPts = 4096;
 constexpr int kSmallLog = 12;  // longest transform done by k_fft_small
 
-template <int LOGF>
+// Sub-stage radices 2^L(i), i < NS, as equal as possible with the larger first and L <= LQMAX:
+// 16 for FP64 and FP32, 8 for double-float (whose 16-point register DFTs need 112 registers a
+// thread and leave two CTAs per SM stalled at the barriers). FP64/FP32 CTAs have one thread per
+// butterfly of the narrowest sub-stage; double-float CTAs one per butterfly of the widest
+// (512 threads), each taking several butterflies of the narrower sub-stages, within 64
+// registers so that two CTAs share an SM.
+template <int LOGF, class C>
 struct SmallSplit {
-  static constexpr int NS = LOGF <= 8 ? 2 : 3;
-  static constexpr int L0 = NS == 2 ? (LOGF + 1) / 2 : (LOGF + 2) / 3;
-  static constexpr int L1 = NS == 2 ? LOGF - L0 : (LOGF - L0 + 1) / 2;
-  static constexpr int L2 = NS == 2 ? 0 : LOGF - L0 - L1;
-  static constexpr int LMIN = NS == 2 ? L1 : L2;
-  static constexpr int NT = kSmallPts >> LMIN;  // threads: butterflies of the narrowest sub-stage
+  static constexpr bool DF = std::is_same<C, df64c>::value;
+  static constexpr int LQMAX = DF ? 3 : 4;
+  static constexpr int NS = (LOGF + LQMAX - 1) / LQMAX < 2 ? 2 : (LOGF + LQMAX - 1) / LQMAX;
+  __host__ __device__ static constexpr int L(int i) { return LOGF / NS + (i < LOGF % NS ? 1 : 0); }
+  static constexpr int NT = kSmallPts >> (DF ? L(0) : L(NS - 1));
+  static constexpr int MINB = DF ? 2 : 0;  // CTAs per SM the registers must allow (0: no bound)
 };
 
 __device__ __forceinline__ uint32_t spad(uint32_t e) { return e + (e >> 4); }
 
 // One in-place sub-stage over the tile (every butterfly of radix 2^LQ; LOGNN = log2 of the
-// sub-length after it). LAST writes to global memory instead. The first sub-stage (LOGNN = LQ)
-// has only the constant twiddles of reg_dft_unit. tw is the table of this length (2^LOGF).
-template <int LOGF, int LQ, int LOGNN, bool LAST, bool INV, class C>
+// sub-length after it), NT threads taking butterflies b = thread + u NT. LAST writes to global
+// memory instead. The first sub-stage (LOGNN = LQ) has only the constant twiddles of
+// reg_dft_unit. tw is the table of this length (2^LOGF).
+template <int LOGF, int LQ, int LOGNN, bool LAST, bool INV, int NT, class C>
 __device__ __forceinline__ void small_stage(C* v, const C* __restrict__ tw, C* __restrict__ y, int64_t col0,
                                             int64_t ncols) {
   constexpr int F = 1 << LOGF, Q = 1 << LQ;
   constexpr uint32_t Fp = F + F / 16;
   constexpr int NB = kSmallPts / Q;
+  constexpr int BPT = (NB + NT - 1) / NT;  // butterflies per thread
   constexpr int logs = LOGF - LOGNN, logm = LOGNN - LQ;
-  const uint32_t b = threadIdx.x;
-  const bool act = b < NB;
-  C a[Q];
-  uint32_t c = 0, pp = 0, qq = 0;
-  if (act) {
-    c = b >> (LOGF - LQ);
-    const uint32_t bb = b & ((F >> LQ) - 1);
-    pp = bb >> logs;
-    qq = bb & ((1u << logs) - 1);
-    const C* vc = v + c * Fp;
+  if constexpr (BPT == 1) {
+    const uint32_t b = threadIdx.x;
+    const bool act = b < NB;
+    C a[Q];
+    uint32_t c = 0, pp = 0, qq = 0;
+    if (act) {
+      c = b >> (LOGF - LQ);
+      const uint32_t bb = b & ((F >> LQ) - 1);
+      pp = bb >> logs;
+      qq = bb & ((1u << logs) - 1);
+      const C* vc = v + c * Fp;
 #pragma unroll
-    for (int j = 0; j < Q; ++j) a[j] = vc[spad(qq + ((pp * Q + j) << logs))];
-  }
-  if (!LAST) __syncthreads();  // the sub-stage works in place
-  if (act) {
-    if (LOGNN == LQ) reg_dft_unit<LQ, INV>(a);
-    else reg_dft<LQ, INV>(a, pp << (LOGF - LOGNN), tw, LOGF, (uint32_t)F - 1u);
-    if (LAST) {
-      if (col0 + c < ncols) {
-        C* yc = y + (col0 + c) * F;
-#pragma unroll
-        for (int r = 0; r < Q; ++r) yc[pp + (r << logm)] = a[r];
-      }
-    } else {
-      C* vc = v + c * Fp;
-#pragma unroll
-      for (int r = 0; r < Q; ++r) vc[spad(qq + ((pp + (r << logm)) << logs))] = a[r];
+      for (int j = 0; j < Q; ++j) a[j] = vc[spad(qq + ((pp * Q + j) << logs))];
     }
+    if (!LAST) __syncthreads();  // the sub-stage works in place
+    if (act) {
+      if (LOGNN == LQ) reg_dft_unit<LQ, INV>(a);
+      else reg_dft<LQ, INV>(a, pp << (LOGF - LOGNN), tw, LOGF, (uint32_t)F - 1u);
+      if (LAST) {
+        if (col0 + c < ncols) {
+          C* yc = y + (col0 + c) * F;
+#pragma unroll
+          for (int r = 0; r < Q; ++r) yc[pp + (r << logm)] = a[r];
+        }
+      } else {
+        C* vc = v + c * Fp;
+#pragma unroll
+        for (int r = 0; r < Q; ++r) vc[spad(qq + ((pp + (r << logm)) << logs))] = a[r];
+      }
+    }
+    if (!LAST) __syncthreads();
+  } else {
+    C a[BPT][Q];
+    uint32_t c[BPT], pp[BPT], qq[BPT];
+#pragma unroll
+    for (int u = 0; u < BPT; ++u) {
+      const uint32_t b = threadIdx.x + u * NT;
+      c[u] = pp[u] = qq[u] = 0;
+      if (b < NB) {
+        c[u] = b >> (LOGF - LQ);
+        const uint32_t bb = b & ((F >> LQ) - 1);
+        pp[u] = bb >> logs;
+        qq[u] = bb & ((1u << logs) - 1);
+        const C* vc = v + c[u] * Fp;
+#pragma unroll
+        for (int j = 0; j < Q; ++j) a[u][j] = vc[spad(qq[u] + ((pp[u] * Q + j) << logs))];
+      }
+    }
+    if (!LAST) __syncthreads();  // the sub-stage works in place
+#pragma unroll
+    for (int u = 0; u < BPT; ++u) {
+      if (threadIdx.x + u * NT >= NB) continue;
+      if (LOGNN == LQ) reg_dft_unit<LQ, INV>(a[u]);
+      else reg_dft<LQ, INV>(a[u], pp[u] << (LOGF - LOGNN), tw, LOGF, (uint32_t)F - 1u);
+      if (LAST) {
+        if (col0 + c[u] < ncols) {
+          C* yc = y + (col0 + c[u]) * F;
+#pragma unroll
+          for (int r = 0; r < Q; ++r) yc[pp[u] + (r << logm)] = a[u][r];
+        }
+      } else {
+        C* vc = v + c[u] * Fp;
+#pragma unroll
+        for (int r = 0; r < Q; ++r) vc[spad(qq[u] + ((pp[u] + (r << logm)) << logs))] = a[u][r];
+      }
+    }
+    if (!LAST) __syncthreads();
   }
-  if (!LAST) __syncthreads();
 }
 
 template <int LOGF, bool INV, class C>
-__global__ void __launch_bounds__(SmallSplit<LOGF>::NT) k_fft_small(const C* __restrict__ src, C* __restrict__ dst,
-                                                                      int64_t ncols, const C* __restrict__ tw,
-                                                                      int logFmax, const C* __restrict__ hmul,
-                                                                      int64_t nseg, FftGen gen) {
-  typedef SmallSplit<LOGF> S;
+__global__ void __launch_bounds__(SmallSplit<LOGF, C>::NT, SmallSplit<LOGF, C>::MINB)
+    k_fft_small(const C* __restrict__ src, C* __restrict__ dst, int64_t ncols, const C* __restrict__ tw, int logFmax,
+                const C* __restrict__ hmul, int64_t nseg, FftGen gen) {
+  typedef SmallSplit<LOGF, C> S;
   constexpr int F = 1 << LOGF;
   constexpr uint32_t Fp = F + F / 16;
   constexpr int NCOL = kSmallPts / F;
@@ -430,13 +476,20 @@ __global__ void __launch_bounds__(SmallSplit<LOGF>::NT) k_fft_small(const C* __r
     v[(idx >> LOGF) * Fp + spad(idx & (F - 1))] = t[u];
   }
   __syncthreads();
+  constexpr int L0 = S::L(0), L1 = S::L(1), L2 = S::L(2), L3 = S::L(3), NT = S::NT;
   if constexpr (S::NS == 2) {
-    small_stage<LOGF, S::L0, S::L0, false, INV>(v, tw, dst, col0, ncols);
-    small_stage<LOGF, S::L1, LOGF, true, INV>(v, tw, dst, col0, ncols);
+    small_stage<LOGF, L0, L0, false, INV, NT>(v, tw, dst, col0, ncols);
+    small_stage<LOGF, L1, LOGF, true, INV, NT>(v, tw, dst, col0, ncols);
+  } else if constexpr (S::NS == 3) {
+    small_stage<LOGF, L0, L0, false, INV, NT>(v, tw, dst, col0, ncols);
+    small_stage<LOGF, L1, L0 + L1, false, INV, NT>(v, tw, dst, col0, ncols);
+    small_stage<LOGF, L2, LOGF, true, INV, NT>(v, tw, dst, col0, ncols);
   } else {
-    small_stage<LOGF, S::L0, S::L0, false, INV>(v, tw, dst, col0, ncols);
-    small_stage<LOGF, S::L1, S::L0 + S::L1, false, INV>(v, tw, dst, col0, ncols);
-    small_stage<LOGF, S::L2, LOGF, true, INV>(v, tw, dst, col0, ncols);
+    static_assert(S::NS == 4, "at most four sub-stages");
+    small_stage<LOGF, L0, L0, false, INV, NT>(v, tw, dst, col0, ncols);
+    small_stage<LOGF, L1, L0 + L1, false, INV, NT>(v, tw, dst, col0, ncols);
+    small_stage<LOGF, L2, L0 + L1 + L2, false, INV, NT>(v, tw, dst, col0, ncols);
+    small_stage<LOGF, L3, LOGF, true, INV, NT>(v, tw, dst, col0, ncols);
   }
 }
 
@@ -452,8 +505,8 @@ void launch_small(const C* src, C* dst, int ncols, const C* tw, int logFmax, con
     configured = true;
   }
   const int64_t grid = ((int64_t)ncols + NCOL - 1) / NCOL;
-  k_fft_small<LOGF, INV, C><<<(unsigned)grid, SmallSplit<LOGF>::NT, smem, st>>>(src, dst, ncols, tw, logFmax, hmul,
-                                                                                nseg, gen);
+  k_fft_small<LOGF, INV, C><<<(unsigned)grid, SmallSplit<LOGF, C>::NT, smem, st>>>(src, dst, ncols, tw, logFmax,
+                                                                                   hmul, nseg, gen);
 }
 
 template <bool INV, class C>
@@ -585,12 +638,15 @@ int run_fft(C* a, C* b, int logF, int ncols, bool inverse, const C* tw, int logF
     if (npasses) *npasses = 1;
     return HANKEL_OK;
   }
-  // logF >= 13: passes of radix 2^5 .. 2^8 (logF <= 24 gives at most three of at least 2^5),
-  // each leaving F/R >= kTile pairs per column; the first (stride F/R >= kTile) applies the
-  // input product
-  const int np = (logF + 7) / 8;
+  // logF >= 13: passes of radix 2^5 .. 2^8, each leaving F/R >= kTile pairs per column; the
+  // first (stride F/R >= kTile) applies the input product. FP64 and FP32 take the fewest
+  // passes (radix up to 256); double-float keeps to radix 64 where 2^5 .. 2^6 can make up F (its
+  // radix-128 pass needs 112 registers a thread and issues on half the cycles of radix 64)
+  const int maxlog = std::is_same<C, df64c>::value ? 6 : 8;
+  int np = (logF + maxlog - 1) / maxlog;
+  while (np > 1 && logF / np < 5) --np;
   const int base = logF / np, extra = logF % np;
-  if (base < 5) return HANKEL_EINVAL;
+  if (base < 5 || base + (extra ? 1 : 0) > 8) return HANKEL_EINVAL;
   C* src = a;
   C* dst = b;
   int done = 0;  // log2 of the sub-length transformed so far
