@@ -116,10 +116,28 @@ struct DevicePlan {
   bool df64 = false;       // plan precision double-float (transforms; near field on the FP32 pipe)
   bool any_t[3] = {false, false, false};  // some block has transforms in this precision
   int logFmax = 6;
-  void* bufA = nullptr;    // workspace, elements of the plan precision
+  void* bufA = nullptr;    // workspace of lane 0 (bytes; holds elements of any precision)
   void* bufB = nullptr;
-  size_t ws_bytes = 0;    // both buffers
-  size_t buf_bytes = 0;   // one buffer
+  size_t ws_bytes = 0;    // workspace of every lane
+  size_t buf_bytes = 0;   // one buffer of lane 0
+  // Lanes: the term groups of one precision run on a stream of their own, so that the FP64,
+  // double-float and FP32 transforms (different pipes, many small launches) overlap. Lane 0 is
+  // the caller's stream (the near field and the plan precision's groups, adding into f); lane
+  // l >= 1 has its own stream, workspace and accumulator acc ([nrhs][N], zeroed per execution),
+  // added into f in a fixed order at the end. Stage timing runs the lanes one after another on
+  // the caller's stream.
+  struct Lane {
+    cudaStream_t s = nullptr;
+    cudaEvent_t done = nullptr;
+    void* A = nullptr;
+    void* B = nullptr;
+    size_t buf_bytes = 0;
+    double* acc = nullptr;
+  };
+  int nlanes = 1;
+  int lane_of[3] = {0, 0, 0};  // lane of each term precision
+  Lane lanes[3];
+  cudaEvent_t fork = nullptr;
   double* c_stage = nullptr;
   double* f_stage = nullptr;
   double* vinv = nullptr;     // DHT plans, first inverse call: v_n = 2 / J_1(j_{0,n})^2
@@ -358,8 +376,16 @@ int dev_plan_create(hankel_plan_s* p) {
   // of a block (nseg transforms of length F per stacked column for segmented blocks). The
   // plan-time spectra are computed in FP64 in the same buffers, so each holds at least nseg F
   // double2 values.
+  // lanes: the plan precision's groups in lane 0, each other precision present in a lane of
+  // its own
+  {
+    const int base = d->fp32 ? kTermFP32 : d->df64 ? kTermDF64 : kTermFP64;
+    d->lane_of[base] = 0;
+    for (int t = 0; t < 3; ++t)
+      if (t != base && d->any_t[t]) d->lane_of[t] = d->nlanes++;
+  }
   size_t limit = hp.opt.workspace_limit ? hp.opt.workspace_limit : kDefaultWorkspace;
-  size_t need = sizeof(double2) << logFmax;  // bytes per buffer
+  size_t need[3] = {sizeof(double2) << logFmax, 0, 0};  // bytes per buffer, per lane
   std::vector<int> lists[3];
   for (const Block& b : hp.blocks) {
     const size_t foot = column_footprint(b);
@@ -370,19 +396,31 @@ int dev_plan_create(hankel_plan_s* p) {
       const int64_t total = (int64_t)lists[t].size() * hp.opt.max_nrhs;
       int64_t cap = (int64_t)(limit / (2 * esz * foot));
       cap = std::max<int64_t>(1, std::min<int64_t>(cap, total));
-      need = std::max(need, (size_t)cap * foot * esz);
+      need[d->lane_of[t]] = std::max(need[d->lane_of[t]], (size_t)cap * foot * esz);
     }
-    need = std::max(need, sizeof(double2) * (size_t)b.nseg * (size_t)b.F);
+    need[0] = std::max(need[0], sizeof(double2) * (size_t)b.nseg * (size_t)b.F);
   }
-  {
+  d->ws_bytes = 0;
+  for (int l = 0; l < d->nlanes; ++l) {
     char* qa; char* qb;
-    HK_TRY(dalloc(d, &qa, need));
-    HK_TRY(dalloc(d, &qb, need));
-    d->bufA = qa;
-    d->bufB = qb;
+    HK_TRY(dalloc(d, &qa, need[l]));
+    HK_TRY(dalloc(d, &qb, need[l]));
+    d->lanes[l].A = qa;
+    d->lanes[l].B = qb;
+    d->lanes[l].buf_bytes = need[l];
+    d->ws_bytes += 2 * need[l];
+    if (l > 0) {
+      HK_TRY(dalloc(d, &d->lanes[l].acc, (size_t)hp.opt.max_nrhs * N));
+      if (cudaStreamCreateWithFlags(&d->lanes[l].s, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&d->lanes[l].done, cudaEventDisableTiming) != cudaSuccess)
+        return HANKEL_ECUDA;
+    }
   }
-  d->ws_bytes = 2 * need;
-  d->buf_bytes = need;
+  if (d->nlanes > 1 && cudaEventCreateWithFlags(&d->fork, cudaEventDisableTiming) != cudaSuccess)
+    return HANKEL_ECUDA;
+  d->bufA = d->lanes[0].A;
+  d->bufB = d->lanes[0].B;
+  d->buf_bytes = need[0];
 
   // Per block: chirp vectors, the spectra of its convolution kernels (one per segment) and per
   // term group its column and row tables (the low-rank form's terms, or its kept stacked columns).
@@ -400,8 +438,9 @@ int dev_plan_create(hankel_plan_s* p) {
       TermGroup& tg = db.g[db.ng++];
       tg.prec = t;
       tg.nl = (int)lists[t].size();
-      tg.cap = std::max<int64_t>(1, std::min<int64_t>((int64_t)(need / (column_footprint(b) * term_esz(t))),
-                                                      (int64_t)tg.nl * hp.opt.max_nrhs));
+      tg.cap = std::max<int64_t>(1, std::min<int64_t>(
+                                        (int64_t)(need[d->lane_of[t]] / (column_footprint(b) * term_esz(t))),
+                                        (int64_t)tg.nl * hp.opt.max_nrhs));
       if (t == kTermFP32) {
         float2* h; HK_TRY(dalloc(d, &h, (size_t)b.nseg * b.F)); tg.H = h;
         float2* vt; HK_TRY(dalloc(d, &vt, (size_t)tg.nl * b.C)); tg.Vt = vt;
@@ -513,6 +552,11 @@ int dev_plan_destroy(hankel_plan_s* p) {
   cudaSetDevice(d->device);
   cudaDeviceSynchronize();
   for (cudaEvent_t e : d->pool) cudaEventDestroy(e);
+  for (int l = 1; l < 3; ++l) {
+    if (d->lanes[l].done) cudaEventDestroy(d->lanes[l].done);
+    if (d->lanes[l].s) cudaStreamDestroy(d->lanes[l].s);
+  }
+  if (d->fork) cudaEventDestroy(d->fork);
   for (void* q : d->allocs) cudaFree(q);
   cudaSetDevice(cur);
   delete d;
@@ -617,10 +661,11 @@ int run_block(DevicePlan* d, const DevBlock& db, const TermGroup& tg, const doub
 }
 
 // Near field of a plan in its precision, then every far block's term groups. capacity
-// (chunk_from_capacity): bytes of each of A and B.
+// (chunk_from_capacity): bytes of each of A and B. use_lanes: the groups of other precisions
+// run in their lanes (otherwise every group runs on st in A and B, adding into f).
 int run_all(DevicePlan* d, const HostPlan& hp, const double* c, int64_t ldc, double* f, int64_t ldf, int nrhs,
             void* A, void* B, void* partial, size_t capacity, bool chunk_from_capacity, cudaStream_t st,
-            bool record) {
+            bool record, bool use_lanes) {
   if (d->cf) {
     // FP32 transforms (and FP32 near fields): the coefficients rounded once per execution
     StageScope sc(d, HANKEL_STAGE_GEN, st, record);
@@ -634,6 +679,21 @@ int run_all(DevicePlan* d, const HostPlan& hp, const double* c, int64_t ldc, dou
     launch_coeffs_df64(c, ldc, d->cdf, d->hpN, nrhs, st);
     HK_LAUNCHED();
     sc.done(1, 0.0, 0.0);
+  }
+  const bool lanes_on = use_lanes && d->nlanes > 1;
+  const bool par = lanes_on && !d->timing;
+  auto lane_stream = [&](int l) { return (par && l > 0) ? d->lanes[l].s : st; };
+  if (lanes_on) {
+    if (par) {
+      // the other lanes start once the coefficient copies above are written
+      if (cudaEventRecord(d->fork, st) != cudaSuccess) return HANKEL_ECUDA;
+      for (int l = 1; l < d->nlanes; ++l)
+        if (cudaStreamWaitEvent(d->lanes[l].s, d->fork, 0) != cudaSuccess) return HANKEL_ECUDA;
+    }
+    for (int l = 1; l < d->nlanes; ++l)
+      if (cudaMemsetAsync(d->lanes[l].acc, 0, sizeof(double) * (size_t)nrhs * (size_t)d->hpN, lane_stream(l)) !=
+          cudaSuccess)
+        return HANKEL_ECUDA;
   }
   {
     StageScope sc(d, HANKEL_STAGE_NEAR, st, record);
@@ -653,16 +713,34 @@ int run_all(DevicePlan* d, const HostPlan& hp, const double* c, int64_t ldc, dou
     for (int j = 0; j < db.ng; ++j) {
       const TermGroup& tg = db.g[j];
       const size_t esz = term_esz(tg.prec);
+      const int l = lanes_on ? d->lane_of[tg.prec] : 0;
+      const cudaStream_t ls = lane_stream(l);
+      void* la = l ? d->lanes[l].A : A;
+      void* lb = l ? d->lanes[l].B : B;
+      double* lf = l ? d->lanes[l].acc : f;
+      const int64_t lld = l ? d->hpN : ldf;
       const int64_t cap = chunk_from_capacity
                               ? std::max<int64_t>(1, (int64_t)(capacity / (column_footprint(db.b) * esz)))
                               : tg.cap;
       if (tg.prec == kTermFP32)
-        HK_TRY(run_block<float2>(d, db, tg, c, ldc, f, ldf, nrhs, (float2*)A, (float2*)B, cap, st, record));
+        HK_TRY(run_block<float2>(d, db, tg, c, ldc, lf, lld, nrhs, (float2*)la, (float2*)lb, cap, ls, record));
       else if (tg.prec == kTermDF64)
-        HK_TRY(run_block<df64c>(d, db, tg, c, ldc, f, ldf, nrhs, (df64c*)A, (df64c*)B, cap, st, record));
+        HK_TRY(run_block<df64c>(d, db, tg, c, ldc, lf, lld, nrhs, (df64c*)la, (df64c*)lb, cap, ls, record));
       else
-        HK_TRY(run_block<double2>(d, db, tg, c, ldc, f, ldf, nrhs, (double2*)A, (double2*)B, cap, st, record));
+        HK_TRY(run_block<double2>(d, db, tg, c, ldc, lf, lld, nrhs, (double2*)la, (double2*)lb, cap, ls, record));
     }
+  }
+  if (lanes_on) {
+    if (par)
+      for (int l = 1; l < d->nlanes; ++l)
+        if (cudaEventRecord(d->lanes[l].done, d->lanes[l].s) != cudaSuccess ||
+            cudaStreamWaitEvent(st, d->lanes[l].done, 0) != cudaSuccess)
+          return HANKEL_ECUDA;
+    StageScope sc(d, HANKEL_STAGE_OUT, st, record);
+    const double* acc[2] = {d->lanes[1].acc, d->nlanes > 2 ? d->lanes[2].acc : nullptr};
+    launch_add_lanes(f, ldf, acc, d->nlanes - 1, d->hpN, nrhs, st);
+    HK_LAUNCHED();
+    sc.done(1, 0.0, 0.0);
   }
   return HANKEL_OK;
 }
@@ -676,7 +754,7 @@ int dev_exec(hankel_plan_s* p, const double* c, int64_t ldc, double* f, int64_t 
   cudaGetDevice(&cur);
   if (cur != d->device) cudaSetDevice(d->device);
   // near field overwrites f; far blocks add to it
-  const int s = run_all(d, p->hp, c, ldc, f, ldf, nrhs, d->bufA, d->bufB, d->partial, 0, false, st, true);
+  const int s = run_all(d, p->hp, c, ldc, f, ldf, nrhs, d->bufA, d->bufB, d->partial, 0, false, st, true, true);
   if (cur >= 0 && cur != d->device) cudaSetDevice(cur);
   return s;
 }
@@ -828,7 +906,7 @@ int dev_exec_static(hankel_plan_s* p, const double* c, double* f, void* stream) 
   void* sB = bytes + per_buf;
   void* spartial = bytes + 2 * per_buf;
   cudaStream_t st = (cudaStream_t)stream;
-  const int s = run_all(d, hp, c, N, f, N, 1, sA, sB, spartial, per_buf, true, st, false);
+  const int s = run_all(d, hp, c, N, f, N, 1, sA, sB, spartial, per_buf, true, st, false, false);
   if (s != HANKEL_OK) {
     if (cur >= 0 && cur != d->device) cudaSetDevice(cur);
     return s;

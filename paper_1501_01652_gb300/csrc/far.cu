@@ -193,6 +193,16 @@ __global__ void __launch_bounds__(256) k_coeffs_df64(const double* __restrict__ 
   }
 }
 
+__global__ void __launch_bounds__(256) k_add_lanes(double* f, int64_t ldf, const double* __restrict__ a0,
+                                                   const double* __restrict__ a1, int64_t N, int64_t total) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / N, i = e - r * N;
+    double v = f[r * ldf + i] + a0[e];
+    if (a1) v += a1[e];
+    f[r * ldf + i] = v;
+  }
+}
+
 __global__ void __launch_bounds__(256) k_diag_scale(const double* x, int64_t ldx, const double* __restrict__ v,
                                                     double scale, double* out, int64_t ldo, int64_t N, int64_t total) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
@@ -233,6 +243,12 @@ void launch_seg_mac(const C* in, const C* H, C* out, int64_t F, int64_t nseg, in
   // F >= 64 is a multiple of kMacPts
   const int64_t blocks = (F / kMacPts) * nc;
   k_seg_mac<C><<<(unsigned)blocks, kMacPts * kMacLanes, 0, st>>>(in, H, out, F, nseg);
+}
+
+void launch_add_lanes(double* f, int64_t ldf, const double* const* acc, int nacc, int64_t N, int nrhs,
+                      cudaStream_t st) {
+  const int64_t total = N * (int64_t)nrhs;
+  k_add_lanes<<<grid1d(total), 256, 0, st>>>(f, ldf, acc[0], nacc > 1 ? acc[1] : nullptr, N, total);
 }
 
 void launch_coeffs_f32(const double* c, int64_t ldc, float* cf, int64_t N, int nrhs, cudaStream_t st) {

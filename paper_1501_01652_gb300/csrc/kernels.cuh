@@ -104,6 +104,9 @@ void launch_block_tables(const BlockTabArgs& a, cudaStream_t st);
 // out[r * ldo + i] = scale * v[i] * x[r * ldx + i] for r < nrhs, i < N (out may be x).
 void launch_diag_scale(const double* x, int64_t ldx, const double* v, double scale, double* out, int64_t ldo,
                        int64_t N, int nrhs, cudaStream_t st);
+// f[r * ldf + i] += acc[0][r * N + i] (+ acc[1][r * N + i]) for r < nrhs, i < N, nacc <= 2.
+void launch_add_lanes(double* f, int64_t ldf, const double* const* acc, int nacc, int64_t N, int nrhs,
+                      cudaStream_t st);
 // cf[r * N + i] = (float) c[r * ldc + i] for r < nrhs, i < N.
 void launch_coeffs_f32(const double* c, int64_t ldc, float* cf, int64_t N, int nrhs, cudaStream_t st);
 // cd[r * N + i] = (h, l): h = (float) c[r * ldc + i], l = (float)(c - h), for r < nrhs, i < N.
