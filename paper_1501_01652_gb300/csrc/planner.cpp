@@ -441,7 +441,8 @@ void choose_segments(Block& b) {
   const int64_t thin = std::min(b.R, b.C), wide = std::max(b.R, b.C);
   const double kStage = kStageOps, kMac = kMacOps;
   double best = full_column_cost(b);
-  for (int lf = 6; lf < b.logF; ++lf) {
+  const int lfull = b.logF;  // b.logF changes when a shorter length wins
+  for (int lf = 6; lf < lfull; ++lf) {
     const int64_t Fs = int64_t(1) << lf;
     if (Fs < 2 * thin) continue;
     const int64_t S = Fs - thin + 1;
