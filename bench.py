@@ -58,10 +58,11 @@ def parse_args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--N", type=int, default=2 ** 20)
     ap.add_argument("--nrhs", type=int, default=16, help="vectors per batched execution (served form)")
-    ap.add_argument("--requests", type=int, default=16, help="requests per serving run")
+    ap.add_argument("--requests", type=int, default=0,
+                    help="single-vector requests per serving run (0: nrhs per eps, the batched step's vectors)")
     ap.add_argument("--rate", type=float, default=0.0, help="Poisson request rate (0: 70%% of plain capacity)")
     ap.add_argument("--eps", default="1e-15,1e-8")
-    ap.add_argument("--cpu-rows", type=int, default=1024, help="oracle rows per sample")
+    ap.add_argument("--cpu-rows", type=int, default=4096, help="oracle rows per sample (about 10 s on 16 cores)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="dht", choices=["dht", "mix"], help="mix: the serving-mix workload")
     ap.add_argument("--quick", action="store_true", help="batched form only (no plain form, serving runs or CPU leg)")
@@ -408,7 +409,8 @@ def run_ours(args):
 
     # request streams through the library's server: end to end with host arrays
     reqs = []
-    for i in range(args.requests):
+    nreq = args.requests if args.requests > 0 else B * len(eps_list)
+    for i in range(nreq):
         e = eps_list[i % len(eps_list)]
         reqs.append((e, pinned_like(coefficients("normal", N, 1, seed_for(4, 200 + i))[0])))
     served_kw = dict(streams=4, max_batch=B, use_graphs=True, precision="auto")
@@ -448,7 +450,8 @@ def run_ours(args):
         "roofline": roofline,
         "e2e": {"value": served_e2e, "unit": "coeffs/s", "h2d_bytes_per_step": coeffs_per_step * 8,
                 "d2h_bytes_per_step": coeffs_per_step * 8,
-                "form": "hankel_server, %d single-vector requests submitted at once, page-locked host arrays (inputs and outputs)" % len(reqs),
+                "form": "hankel_server, %d single-vector requests (%d per eps) submitted at once, page-locked host "
+                        "arrays (inputs and outputs)" % (len(reqs), len(reqs) // len(eps_list)),
                 "plain_value": plain_e2e},
         "latency_ms": {"rate_per_s": rate, "requests": len(reqs),
                        "served": {"p50": pct(served_lat, 50), "p99": pct(served_lat, 99),

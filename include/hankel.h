@@ -312,6 +312,8 @@ typedef struct {
   int precision;      /* precision every plan is built with: HANKEL_PREC_AUTO (chosen per eps as for a
                          plan: FP64, DF64 transforms or FP32 stages) or HANKEL_PREC_FP64 */
   int pack_requests;  /* 1: pack waiting requests of one plan into one execution; 0: one request each */
+  int batch_window_us; /* a plan's batch with fewer than max_batch vectors waits until its oldest request
+                          is this old, to take requests submitted together (default 200; 0: none) */
 } hankel_server_options;
 
 /* Statistics since the server was created. */
@@ -325,7 +327,8 @@ typedef struct {
   size_t device_bytes;                   /* device memory held now */
 } hankel_server_stats;
 
-/* Defaults: 120 GiB cap, 4 streams, batches of up to 64 vectors, no graphs, AUTO precision, packing on. */
+/* Defaults: 120 GiB cap, 4 streams, batches of up to 64 vectors, no graphs, AUTO precision, packing on,
+ * a 200 us batch window. */
 int hankel_server_options_default(hankel_server_options* o);
 
 /* Create a server on the current CUDA device and start its dispatcher. */

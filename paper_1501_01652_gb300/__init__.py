@@ -214,13 +214,16 @@ class Server:
     1e-11 <= eps < 1e-5 and FP32 stages at eps >= 1e-5.
     """
 
-    def __init__(self, streams=4, max_batch=64, use_graphs=False, precision="auto", memory_cap=0, pack=True):
+    def __init__(self, streams=4, max_batch=64, use_graphs=False, precision="auto", memory_cap=0, pack=True,
+                 batch_window_us=None):
         self._lib = _lib.load()
         o = _lib.ServerOptions()
         _lib.check(self._lib.hankel_server_options_default(ctypes.byref(o)), "hankel_server_options_default")
         o.streams, o.max_batch, o.use_graphs = int(streams), int(max_batch), int(bool(use_graphs))
         o.precision = PRECISIONS[precision]
         o.pack_requests = 1 if pack else 0
+        if batch_window_us is not None:
+            o.batch_window_us = int(batch_window_us)
         if memory_cap:
             o.memory_cap = int(memory_cap)
         self._h = ctypes.c_void_p()

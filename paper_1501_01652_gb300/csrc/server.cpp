@@ -296,8 +296,22 @@ bool dispatch(hankel_server_s* s, int i) {
       auto it = s->plans.find(k);
       return it != s->plans.end() && it->second.busy;
     };
+    // the oldest queued request whose plan is idle and whose batch is ready: full, packing off,
+    // or its oldest request has waited the batch window
+    const Clock::time_point now = Clock::now();
+    const auto window = std::chrono::microseconds(std::max(0, s->opt.batch_window_us));
+    std::vector<Key> seen;
     auto q = s->queue.begin();
-    while (q != s->queue.end() && busy(s->reqs[*q].key)) ++q;
+    for (; q != s->queue.end(); ++q) {
+      const Request& r0 = s->reqs[*q];
+      if (busy(r0.key) || std::find(seen.begin(), seen.end(), r0.key) != seen.end()) continue;
+      seen.push_back(r0.key);
+      if (!s->opt.pack_requests || now - r0.t_submit >= window) break;
+      int queued = 0;
+      for (int64_t t : s->queue)
+        if (s->reqs[t].key == r0.key) queued += s->reqs[t].nrhs;
+      if (queued >= s->opt.max_batch) break;
+    }
     if (q == s->queue.end()) return false;
     key = s->reqs[*q].key;
     for (auto it = s->queue.begin(); it != s->queue.end();) {
@@ -356,8 +370,9 @@ void run(hankel_server_s* s) {
     std::unique_lock<std::mutex> lk(s->mu);
     if (s->stop && s->queue.empty() && !inflight) break;
     if (progressed) continue;
-    if (inflight) {
-      // batches are running: poll their events again shortly, or sooner if work arrives
+    if (inflight || !s->queue.empty()) {
+      // batches are running, or queued requests wait for their batch window: look again
+      // shortly, or sooner if work arrives
       s->cv_work.wait_for(lk, std::chrono::microseconds(20));
     } else {
       s->cv_work.wait(lk, [&] { return s->stop || !s->queue.empty(); });
@@ -378,6 +393,7 @@ int hankel_server_options_default(hankel_server_options* o) {
   o->use_graphs = 0;
   o->precision = HANKEL_PREC_AUTO;
   o->pack_requests = 1;
+  o->batch_window_us = 200;
   return HANKEL_OK;
 }
 
@@ -388,7 +404,7 @@ int hankel_server_create(hankel_server_t* out, const hankel_server_options* o) {
   hankel_server_options_default(&opt);
   if (o) opt = *o;
   if (opt.memory_cap == 0) opt.memory_cap = kDefaultCap;
-  if (opt.streams < 1 || opt.streams > 16 || opt.max_batch < 1) return HANKEL_EINVAL;
+  if (opt.streams < 1 || opt.streams > 16 || opt.max_batch < 1 || opt.batch_window_us < 0) return HANKEL_EINVAL;
   if (opt.precision != HANKEL_PREC_AUTO && opt.precision != HANKEL_PREC_FP64) return HANKEL_EINVAL;
   hankel_server_s* s = new hankel_server_s();
   s->opt = opt;
