@@ -165,7 +165,8 @@ def workload_config(args):
     B = args.nrhs
     return {"workload": "dht0_N%d_eps%s_batch%d" % (args.N, "+".join(args.eps.split(",")), B),
             "N": args.N, "eps": [float(e) for e in args.eps.split(",")], "batch": B,
-            "form": "served/batched: %d vectors per execution per plan, precision by eps (FP64 below 1e-11, double-float transforms below 1e-5, FP32 above)" % B,
+            "form": "served/batched: %d vectors per execution per plan, precision by eps (FP64 below 1e-11, "
+                    "double-float transforms below 1e-5, FP32 above)" % B,
             "l2": "flushed between timed steps (256 MB write)", "coefficients": "N(0,1) seeded"}
 
 
@@ -216,16 +217,40 @@ def aggregate(world, coeffs_per_step, steps, total_ms, device):
     return world * coeffs_per_step * steps / (total_ms / 1000.0), total_ms
 
 
-def timed_steps(plans, c, fs, stream, steps, warmup, flush, timing):
+def timed_steps(plans, c, fs, stream, steps, warmup, flush, timing, concurrent=False):
     """Warm up, then time `steps` steps (each: every plan once) with CUDA events on `stream`.
 
-    L2 is flushed between steps, outside the step events. Returns per-step ms, per-plan ms
-    lists and (when timing) the plans' stage statistics."""
+    L2 is flushed between steps, outside the step events. With `concurrent`, each plan runs on
+    a stream of its own, forked from and joined back to `stream` (as the request loop runs
+    different plans); otherwise the plans run one after another on `stream`. Returns per-step
+    ms, per-plan ms lists and (when timing) the plans' stage statistics."""
     import torch
 
+    pstreams = [torch.cuda.Stream() for _ in plans] if concurrent else [stream for _ in plans]
+
+    def one_step(pev=None):
+        if concurrent:
+            fork = torch.cuda.Event()
+            fork.record(stream)
+        joins = []
+        for i, (p, f) in enumerate(zip(plans, fs)):
+            ps = pstreams[i]
+            if concurrent:
+                ps.wait_event(fork)
+            if pev is not None:
+                pev[i][0].record(ps)
+            p.exec(c, f, stream=ps)
+            if pev is not None:
+                pev[i][1].record(ps)
+            if concurrent:
+                j = torch.cuda.Event()
+                j.record(ps)
+                joins.append(j)
+        for j in joins:
+            stream.wait_event(j)
+
     for _ in range(warmup):
-        for p, f in zip(plans, fs):
-            p.exec(c, f, stream=stream)
+        one_step()
     torch.cuda.synchronize()
     if timing:
         for p in plans:
@@ -235,12 +260,10 @@ def timed_steps(plans, c, fs, stream, steps, warmup, flush, timing):
            for _ in range(steps)]
     torch.cuda.synchronize()
     for s in range(steps):
-        flush.zero_()
+        with torch.cuda.stream(stream):
+            flush.zero_()
         ev[s][0].record(stream)
-        for i, (p, f) in enumerate(zip(plans, fs)):
-            pev[s][i][0].record(stream)
-            p.exec(c, f, stream=stream)
-            pev[s][i][1].record(stream)
+        one_step(pev[s])
         ev[s][1].record(stream)
     torch.cuda.synchronize()
     step_ms = [a.elapsed_time(b) for a, b in ev]
