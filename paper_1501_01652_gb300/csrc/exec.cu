@@ -38,8 +38,7 @@ struct TermGroup {
   int nl = 0;            // transforms per right-hand side
   void* H = nullptr;     // per segment: FFT_F of the chirp exp(-i pi (U-V)^2 / (2E)), times 1/F
   void* Vt = nullptr;    // [nl][C] column functions x column chirp (x FP32 scale)
-  void* Ut = nullptr;    // [nl][R] row functions (/ FP32 scale)
-  const void* wU = nullptr;  // the block's row chirp in this precision
+  void* Ut = nullptr;    // [nl][R] row functions times the row chirp (/ FP32 scale)
   int64_t cap = 0;       // stacked columns per chunk
 };
 
@@ -445,19 +444,14 @@ int dev_plan_create(hankel_plan_s* p) {
         float2* h; HK_TRY(dalloc(d, &h, (size_t)b.nseg * b.F)); tg.H = h;
         float2* vt; HK_TRY(dalloc(d, &vt, (size_t)tg.nl * b.C)); tg.Vt = vt;
         float2* ut; HK_TRY(dalloc(d, &ut, (size_t)tg.nl * b.R)); tg.Ut = ut;
-        float2* wu; HK_TRY(dalloc(d, &wu, (size_t)b.R)); tg.wU = wu;
-        launch_scale_copy<float2>(db.wU, wu, b.R, 1.0, 0);
       } else if (t == kTermDF64) {
         df64c* h; HK_TRY(dalloc(d, &h, (size_t)b.nseg * b.F)); tg.H = h;
         df64c* vt; HK_TRY(dalloc(d, &vt, (size_t)tg.nl * b.C)); tg.Vt = vt;
         df64c* ut; HK_TRY(dalloc(d, &ut, (size_t)tg.nl * b.R)); tg.Ut = ut;
-        df64c* wu; HK_TRY(dalloc(d, &wu, (size_t)b.R)); tg.wU = wu;
-        launch_scale_copy<df64c>(db.wU, wu, b.R, 1.0, 0);
       } else {
         double2* h; HK_TRY(dalloc(d, &h, (size_t)b.nseg * b.F)); tg.H = h;
         double2* vt; HK_TRY(dalloc(d, &vt, (size_t)tg.nl * b.C)); tg.Vt = vt;
         double2* ut; HK_TRY(dalloc(d, &ut, (size_t)tg.nl * b.R)); tg.Ut = ut;
-        tg.wU = db.wU;
       }
       HK_LAUNCHED();
       // FP32 transforms: per term, the power of two that brings max |colfun(n)| over the block
@@ -509,7 +503,7 @@ int dev_plan_create(hankel_plan_s* p) {
       if (!sc.empty()) HK_TRY(upload(d, &scd, sc.data(), sc.size()));
       BlockTabArgs ta{tg.nl, b.k0, b.R, b.n0, b.C, lmap, b.rank ? b.P : 0, uc, vc,
                       std::log((double)b.k0), std::log((double)b.k1), std::log((double)b.n0),
-                      std::log((double)b.n1), d->nodes, d->cols, db.wV, scd, tg.Vt, tg.Ut};
+                      std::log((double)b.n1), d->nodes, d->cols, db.wV, db.wU, scd, tg.Vt, tg.Ut};
       if (t == kTermFP32) launch_block_tables<float2>(ta, 0);
       else if (t == kTermDF64) launch_block_tables<df64c>(ta, 0);
       else launch_block_tables<double2>(ta, 0);
@@ -651,7 +645,7 @@ int run_block(DevicePlan* d, const DevBlock& db, const TermGroup& tg, const doub
     {
       StageScope sc(d, HANKEL_STAGE_OUT, st, record);
       OutArgs oa{res2, b.F, b.R, b.k0, (rowseg ? b.S : b.C) - 1, colseg ? b.S : b.R, colseg ? b.nseg : 1,
-                 nc, c0, tg.nl, f, ldf, tg.wU, tg.Ut};
+                 nc, c0, tg.nl, f, ldf, tg.Ut};
       launch_out<C>(oa, st);
       HK_LAUNCHED();
       sc.done(1, 0.0, 0.0);

@@ -31,35 +31,31 @@ __device__ __forceinline__ double ipow(double x, int e) {
 }
 
 // Thread per output row and CTA row (blockIdx.y) per right-hand side of the chunk: the thread
-// adds up that right-hand side's stacked columns of the chunk in order li = lo..hi-1 (complex
-// weights Ut in the plan precision), so every f entry has one writer per chunk and the sum
-// order is fixed; the row chirp and the real part follow in the plan precision, the addition
-// into f in FP64.
+// adds up that right-hand side's stacked columns of the chunk in order li = lo..hi-1, only the
+// real part (the row chirp is folded into the weights Ut), in the plan precision; the addition
+// into f is FP64. Every f entry has one writer per chunk and the sum order is fixed.
 template <class C>
 __global__ void __launch_bounds__(256) k_out(OutArgs a) {
   typedef typename RealOf<C>::type R;
   const int64_t kp = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (kp >= a.R) return;
   const int64_t i = a.k0 - 1 + kp;
-  const C wu = ldgc(reinterpret_cast<const C*>(a.wU) + kp);
   const int64_t sg = kp / a.Sr;
   const C* Y = reinterpret_cast<const C*>(a.Y) + sg * a.F + (kp - sg * a.Sr) + a.off;
   const C* Ut = reinterpret_cast<const C*>(a.Ut) + kp;
   const int64_t r_first = a.c0 / a.ncols, r_last = (a.c0 + a.nc - 1) / a.ncols;
   for (int64_t rhs = r_first + blockIdx.y; rhs <= r_last; rhs += gridDim.y) {
     const int64_t lo = max(a.c0, rhs * a.ncols), hi = min(a.c0 + a.nc, (rhs + 1) * a.ncols);
-    R ar = 0, ai = 0;
+    R ar = 0;
     for (int64_t g = lo; g < hi; ++g) {
       const int64_t li = g - rhs * a.ncols;
-      const C w = Ut[li * a.R];
+      const C w = ldgc(&Ut[li * a.R]);
       const C y = Y[(g - a.c0) * a.nsegr * a.F];
       ar = fmar(w.x, y.x, fmar(-w.y, y.y, ar));
-      ai = fmar(w.x, y.y, fmar(w.y, y.x, ai));
     }
-    a.f[rhs * a.ldf + i] += (double)fmar(wu.x, ar, -wu.y * ai);
+    a.f[rhs * a.ldf + i] += (double)ar;
   }
 }
-
 
 // Overlap-add of column segments: out[cc][t] = sum_s in[cc*nseg + s][t] H[s][t]. A CTA covers
 // kMacPts consecutive points of one column; its kMacLanes thread rows split the segments
@@ -153,12 +149,14 @@ __global__ void __launch_bounds__(128) k_block_rows(BlockTabArgs a) {
   C* Ut = reinterpret_cast<C*>(a.Ut);
   for (int64_t kp = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; kp < a.R; kp += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = a.k0 - 1 + kp;
+    const double2 w = a.wU[kp];
     if (a.P > 0) {
       const double x = a.lk1 > a.lk0 ? (2.0 * log((double)(a.k0 + kp)) - a.lk0 - a.lk1) / (a.lk1 - a.lk0) : 0.0;
       for (int li = 0; li < a.nl; ++li) {
         const double2 u = cheb_series(a.ucheb + (int64_t)li * a.P, a.P, x);
         const double isc = a.scale ? 1.0 / a.scale[li] : 1.0;
-        Ut[(int64_t)li * a.R + kp] = from_d2<C>(make_double2(isc * u.x, isc * u.y));
+        Ut[(int64_t)li * a.R + kp] = from_d2<C>(
+            make_double2(isc * fma(u.x, w.x, -u.y * w.y), isc * fma(u.x, w.y, u.y * w.x)));
       }
     } else {
       const double rv = a.nodes.rowvar[i], irv = a.nodes.inv_rowvar[i], rs = a.nodes.rs_rowvar[i];
@@ -169,7 +167,7 @@ __global__ void __launch_bounds__(128) k_block_rows(BlockTabArgs a) {
         double wgt = rs * ipow(d >= 0 ? rv : irv, d >= 0 ? d : -d);
         if (cs.u1) wgt *= ipow(rp, cs.u1);
         if (a.scale) wgt /= a.scale[li];
-        Ut[(int64_t)li * a.R + kp] = from_d2<C>(make_double2(wgt, 0.0));
+        Ut[(int64_t)li * a.R + kp] = from_d2<C>(make_double2(wgt * w.x, wgt * w.y));
       }
     }
   }

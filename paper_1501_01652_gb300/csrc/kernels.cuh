@@ -62,7 +62,8 @@ struct ChirpGeom {
   int64_t Ua, Ub, Va, Vb, E, k0, n0, R, C, F;
 };
 
-// Row accumulation of one chunk: f_k += Re[ w_U(k) sum_li Ut[li][k - k0] y_li(k) ].
+// Row accumulation of one chunk: f_k += Re[ sum_li Ut[li][k - k0] y_li(k) ] (the row chirp w_U(k)
+// is folded into Ut).
 struct OutArgs {
   const void* Y;      // [nc * nsegr][F] inverse-transformed columns (double2 or float2)
   int64_t F, R, k0;
@@ -74,8 +75,7 @@ struct OutArgs {
   int ncols;          // stacked columns (transforms) of the block per right-hand side
   double* f;          // f[rhs * ldf + k-1] += ...
   int64_t ldf;
-  const void* wU;     // row chirp of the block in the plan precision (double2, df64c or float2)
-  const void* Ut;     // [ncols][R] block row table (double2 or float2)
+  const void* Ut;     // [ncols][R] block row table times the row chirp (double2, df64c or float2)
 };
 
 // Plan-time block tables (computed in FP64, stored in the plan precision). For a block with a
@@ -83,7 +83,7 @@ struct OutArgs {
 // [log n0, log n1]) and row li is U_li (ucheb[li] in log k); otherwise column li is the stacked
 // column lmap[li]:
 // colpow^u1 omt^(delta-1/2) poly(beta) and row li its rowpert^u1 rowvar^(delta-1/2).
-// Vt[li][np] = V_li(n0+np) wV[np] scale[li], Ut[li][kp] = U_li(k0+kp) / scale[li].
+// Vt[li][np] = V_li(n0+np) wV[np] scale[li], Ut[li][kp] = U_li(k0+kp) wU[kp] / scale[li].
 struct BlockTabArgs {
   int nl;
   int64_t k0, R, n0, C;
@@ -95,6 +95,7 @@ struct BlockTabArgs {
   NodeTables nodes;
   const DevColSpec* cols;
   const double2* wV;
+  const double2* wU;
   const double* scale;   // per li (nullptr: 1)
   void* Vt;
   void* Ut;
