@@ -32,11 +32,11 @@ from hankel_inputs import coefficients, sample_rows, seed_for  # noqa: E402
 FP64_PEAK_GFLOPS = 152 * 4 * 2.07  # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz = 1258 GFLOP/s
 HBM_FALLBACK_GBS = 6800.0          # used only when MEASURED_PEAKS.json is absent
 FP64_MEASURED_GFLOPS = 1004.0      # DFMA microbenchmark on this part (2 x 502 G instructions/s)
-# DRAM bytes per algorithmic byte of an FP64 FFT pass launch, from an ncu capture of one
-# radix-128 inverse pass with the chirp-spectrum product folded into its loads (k_fft_pass_reg,
-# 4096 CTAs of 16 x 128 points: 145.1 MB read + 93.9 MB written, 268.4 MB algorithmic; the
-# spectrum is L2-resident and part of the output is still in L2 at kernel end).
-FFT_TRAFFIC_RATIO = (145.12 + 93.91) / 268.44
+# DRAM bytes per algorithmic byte of an FP64 FFT pass launch, from an ncu capture of two
+# radix-128 inverse passes of 2^24 points (k_fft_pass_reg<7, 1, double2>, 8192 CTAs; the first
+# with the chirp-spectrum product folded into its loads): 310.2 + 230.8 MB and 269.7 + 222.5 MB
+# of DRAM reads + writes against 536.9 MB algorithmic each.
+FFT_TRAFFIC_RATIO = (310.218 + 230.828 + 269.726 + 222.462) / (2 * 536.871)
 # The double-float transforms are bound by the FP32 pipe: 152 SMs x 128 lanes x 2.07 GHz =
 # 40.3 T instructions/s. Their radix-2 butterfly (two double-float dot products of 16 FP32
 # instructions each, four renormalised sums of 11) takes 76 FP32 instructions for the 10 flops
