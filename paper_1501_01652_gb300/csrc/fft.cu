@@ -630,7 +630,11 @@ int run_fft(C* a, C* b, int logF, int ncols, bool inverse, const C* tw, int logF
   // the ladder's table for this length: W_F^t at tw[F + t]
   tw += (size_t)1 << logF;
   logFmax = logF;
-  if (logF <= kSmallLog) {
+  // few columns of 2^10 .. 2^12 points would give the one-launch kernel only a few CTAs (a CTA
+  // holds 4096 points): two passes spread them over 8 to 32 times as many
+  const int64_t small_ctas = ((int64_t)ncols + (kSmallPts >> logF) - 1) / (kSmallPts >> logF);
+  const bool few = logF >= 10 && small_ctas < 152;
+  if (logF <= kSmallLog && !few) {
     // the whole transform in one launch
     if (inverse) launch_small_f<true, C>(logF, a, b, ncols, tw, logFmax, hmul, nseg, none, st);
     else launch_small_f<false, C>(logF, a, b, ncols, tw, logFmax, hmul, nseg, g0, st);
@@ -638,7 +642,7 @@ int run_fft(C* a, C* b, int logF, int ncols, bool inverse, const C* tw, int logF
     if (npasses) *npasses = 1;
     return HANKEL_OK;
   }
-  // logF >= 13: passes of radix 2^5 .. 2^8, each leaving F/R >= kTile pairs per column; the
+  // passes of radix 2^5 .. 2^8 (logF >= 10), each leaving F/R >= kTile pairs per column; the
   // first (stride F/R >= kTile) applies the input product. FP64 and FP32 take the fewest
   // passes (radix up to 256); double-float keeps to radix 64 where 2^5 .. 2^6 can make up F (its
   // radix-128 pass needs 112 registers a thread and issues on half the cycles of radix 64)
