@@ -39,10 +39,10 @@ FP64_MEASURED_GFLOPS = 1004.0      # DFMA microbenchmark on this part (2 x 502 G
 FFT_TRAFFIC_RATIO = (310.218 + 230.828 + 269.726 + 222.462) / (2 * 536.871)
 # The double-float transforms are bound by the FP32 pipe: 152 SMs x 128 lanes x 2.07 GHz =
 # 40.3 T instructions/s. Their radix-2 butterfly (two double-float dot products of 16 FP32
-# instructions each, four renormalised sums of 11) takes 76 FP32 instructions for the 10 flops
-# of the 5 F log2 F model, so the pipe bounds the model rate at 40.3 T / 7.6.
+# instructions each, four sums of 8) takes 64 FP32 instructions for the 10 flops of the
+# 5 F log2 F model, so the pipe bounds the model rate at 40.3 T / 6.4.
 FP32_ISSUE_PEAK = 152 * 128 * 2.07e9
-DF64_INSTR_PER_FLOP = 7.6
+DF64_INSTR_PER_FLOP = 6.4
 DF64_PEAK_GFLOPS = FP32_ISSUE_PEAK / DF64_INSTR_PER_FLOP / 1e9
 METRIC = "DHT-0 coeffs/s at N=2^20 (eps=1e-8,1e-15) served vs plain FP64; p50/p99 ms"
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -396,7 +396,7 @@ def run_ours(args):
             e = {"bound": "alu", "achieved": ach, "peak": DF64_PEAK_GFLOPS, "unit": "GFLOP/s",
                  "frac": ach / DF64_PEAK_GFLOPS, "traffic": None,
                  "kernel": "k_fft_pass_reg / k_fft_small<df64c> (double-float transforms, forward + inverse)",
-                 "peak_source": "FP32 pipe (152 SM x 128 lanes x 2.07 GHz) / 7.6 FP32 instructions per "
+                 "peak_source": "FP32 pipe (152 SM x 128 lanes x 2.07 GHz) / 6.4 FP32 instructions per "
                                 "double-float flop of the butterfly"}
         else:
             peak, src = hbm_peak()

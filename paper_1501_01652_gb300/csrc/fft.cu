@@ -79,14 +79,16 @@ __device__ __forceinline__ df64c coef_times(const void* p, int64_t i, df64c v) {
 // The double-float butterfly: t = w a1 once, with the exact products of the high parts (FMA),
 // their difference by two-sum and the cross terms added into the low part, left unnormalised
 // (|low| << |high|); then y0 = a0 + t and y1 = a0 - t, each a two-sum of the high parts with
-// the low parts added and one renormalisation. About 76 FP32 operations against 90 for the
-// FMA-folded form with double-float fmar.
+// the low parts added. About 64 FP32 operations against 90 for the FMA-folded form with
+// double-float fmar.
 __device__ __forceinline__ df64 df_add_pair(df64 a, float sh, float sl) {
   const float u = a.h + sh;
   const float bb = u - a.h;
   float v = (a.h - (u - bb)) + (sh - bb);
   v += a.l + sl;
-  return fast_two_sum(u, v);
+  // left unnormalised: |v| stays within a few units in the last place of u, and every later
+  // operation takes the high parts through a two-sum or an exact product again
+  return df64(u, v);
 }
 // x0 y0 - x1 y1 (sign = -1) or x0 y0 + x1 y1 (sign = +1) as an unnormalised pair (h, l)
 __device__ __forceinline__ void df_dot2(df64 x0, df64 y0, df64 x1, df64 y1, float sign, float& h, float& l) {
