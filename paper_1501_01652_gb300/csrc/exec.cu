@@ -143,6 +143,9 @@ struct DevicePlan {
   double* inv_stage = nullptr;  // v o f for the inverse ([max_nrhs][N])
   float* cf = nullptr;   // FP32 plans: the coefficients rounded to FP32 [max_nrhs][N]
   float2* cdf = nullptr; // DF64 plans: the coefficients as (high, low) float pairs [max_nrhs][N]
+  void* tcd = nullptr;   // FP64 plans, 8+ vectors: coefficient digits of the tensor-core near field
+  int* tce = nullptr;    // and their per-chunk exponents
+  int64_t tc_npad = 0;
   size_t bytes = 0;
   std::vector<void*> allocs;
   // stage statistics (hankel_plan_set_timing / hankel_plan_stage_stats)
@@ -314,6 +317,13 @@ int dev_plan_create(hankel_plan_s* p) {
   // per-execution coefficient copies: double-float pairs for DF64 near fields and transforms,
   // FP32 for FP32 transforms (FP32 near fields read them too)
   if (d->df64 || d->any_t[kTermDF64]) HK_TRY(dalloc(d, &d->cdf, (size_t)hp.opt.max_nrhs * N));
+  if (!d->fp32 && !d->df64 && hp.opt.max_nrhs >= kNearTcMinRhs) {
+    d->tc_npad = (N + 511) / 512 * 512;
+    uint16_t* q = nullptr;
+    HK_TRY(dalloc(d, &q, (size_t)8 * 16 * d->tc_npad));
+    d->tcd = q;
+    HK_TRY(dalloc(d, &d->tce, (size_t)(d->tc_npad / 512) * 16));
+  }
   if (d->any_t[kTermFP32]) HK_TRY(dalloc(d, &d->cf, (size_t)hp.opt.max_nrhs * N));
 
 
@@ -697,6 +707,10 @@ int run_all(DevicePlan* d, const HostPlan& hp, const double* c, int64_t ldc, dou
     else if (d->fp32)
       launch_near<float>(d->items, d->nitems, d->mrows, d->nmrows, d->nend, d->hpN, (float*)partial, nrhs, c, ldc,
                          d->cf, f, ldf, d->rf, d->omf, d->jtabf, hp.jt_n, hp.jt_deg, st);
+    else if (d->tcd && nrhs >= kNearTcMinRhs)
+      launch_near_tc(d->items, d->nitems, d->mrows, d->nmrows, d->nend, d->hpN, (double*)partial, nrhs, c, ldc,
+                     d->tcd, d->tce, d->tc_npad, f, ldf, d->nodes.r_true, d->nodes.om_true, d->jtab, hp.jt_n,
+                     hp.jt_deg, st);
     else
       launch_near<double>(d->items, d->nitems, d->mrows, d->nmrows, d->nend, d->hpN, (double*)partial, nrhs, c, ldc,
                           nullptr, f, ldf, d->nodes.r_true, d->nodes.om_true, d->jtab, hp.jt_n, hp.jt_deg, st);

@@ -6,6 +6,7 @@
 // intervals of width 1/kJTabSub (built at plan time from the Neumann addition formula,
 // Eq. 8, with the degree set by eps), so one evaluation costs a table row load and
 // deg FMAs.
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -193,6 +194,171 @@ __global__ void __launch_bounds__(256) k_near_df(const NearItem* __restrict__ it
 // npieces consecutive values at slot0 nrhs + rr npieces. A warp per row; lane l adds the
 // pieces l, l + 32, ... in order and the lanes combine in a fixed shuffle tree, so the result
 // does not depend on scheduling.
+// FP64 near field with the per-vector products on the tensor cores (FP64 plans, 8 to 16 vectors):
+// split-digit products (the Ozaki scheme). J (|J| <= 1) and, per 512-column chunk and vector,
+// the coefficients scaled by 2^-e (2^e bounds the chunk's largest |c|) are rounded to the
+// integers J 2^53 and C 2^54 (below 2^54 in size) and written as 8 balanced base-128 digits in
+// [-64, 63], exact in fp16. The digit products of one diagonal D = i + j carry the weight
+// 2^(-9 - 7D); fp16 MMAs
+// with fp32 accumulation add them up: each product is an integer of at most 2^12 and a
+// diagonal of a 512-column tile sums at most 8 x 512 of them, so every partial sum is an
+// integer of at most 2^24 and exact (checked on this GPU: the first rounding appears past
+// 2^24). Diagonals D <= 8 are kept (the others add at most 2^-57 of the chunk's scale per entry);
+// they are combined in FP64 once per tile. The rounding of J and C to the digit grid is 2^-54
+// and 2^-55 of their scales: the products are as accurate as FP64 ones, and the sums exact.
+constexpr int kTcDig = 8, kTcDiag = 9, kTcChunk = 512;
+
+__device__ __forceinline__ void digits8(long long X, int (&d)[kTcDig]) {
+#pragma unroll
+  for (int i = kTcDig - 1; i >= 0; --i) {
+    const int v = (int)(((X + 64) & 127) - 64);
+    d[i] = v;
+    X = (X - v) >> 7;
+  }
+}
+
+__device__ __forceinline__ unsigned pack_h2(int lo, int hi) {
+  __half2 v = __halves2half2(__int2half_rn(lo), __int2half_rn(hi));
+  return *reinterpret_cast<unsigned*>(&v);
+}
+
+__device__ __forceinline__ void mma_f16(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// Coefficient digits: one CTA of kTcChunk threads per chunk t; Ce[t * 16 + g] = e and
+// Cd[(j * 16 + g) * Npad + n - 1] = digit j of round(c_n^g 2^-e 2^54) (zeros for g >= nrhs and
+// n > N).
+__global__ void __launch_bounds__(kTcChunk) k_near_cdigits(const double* __restrict__ c, int64_t ldc, int nrhs,
+                                                          int64_t N, int64_t Npad, __half* Cd, int* Ce) {
+  const int64_t t = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int64_t n = t * kTcChunk + tid;  // 0-based column
+  __shared__ double wmax[kTcChunk / 32][16];
+  __shared__ int sexp[16];
+  double v[16];
+#pragma unroll
+  for (int g = 0; g < 16; ++g) {
+    v[g] = (g < nrhs && n < N) ? c[(int64_t)g * ldc + n] : 0.0;
+    double m = fabs(v[g]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) wmax[w][g] = m;
+  }
+  __syncthreads();
+  if (tid < 16) {
+    double m = 0.0;
+    for (int j = 0; j < kTcChunk / 32; ++j) m = fmax(m, wmax[j][tid]);
+    const int e = m > 0.0 ? ilogb(m) + 1 : 0;
+    sexp[tid] = e;
+    Ce[t * 16 + tid] = e;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int g = 0; g < 16; ++g) {
+    const long long X = __double2ll_rn(ldexp(v[g], 54 - sexp[g]));
+    int d[kTcDig];
+    digits8(X, d);
+#pragma unroll
+    for (int j = 0; j < kTcDig; ++j) Cd[((int64_t)j * 16 + g) * Npad + n] = __int2half_rn(d[j]);
+  }
+}
+
+// A CTA of two warps per near-field tile (NearItem); warp w takes rows k0 + 16w .. k0 + 16w + 15
+// and all 16 vector slots, as two m16n8 output tiles. Thread (gq, tq) of a warp evaluates J at
+// rows gq, gq + 8 and columns 2tq, 2tq + 1, 2tq + 8, 2tq + 9 of each 16-column step (its A
+// fragment) and loads the coefficient digits of columns 2tq, 2tq + 1, 2tq + 8, 2tq + 9 for
+// vectors gq and gq + 8 (its B fragments).
+__global__ void __launch_bounds__(64) k_near_tc(const NearItem* __restrict__ items, const int64_t* __restrict__ nend,
+                                               int64_t N, double* partial, int nrhs, const __half* __restrict__ Cd,
+                                               const int* __restrict__ Ce, int64_t Npad, double* f, int64_t ldf,
+                                               const double* __restrict__ r_true,
+                                               const double* __restrict__ om_true, const double* __restrict__ jtab,
+                                               int64_t jt_n, int deg) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, gq = lane >> 2, tq = lane & 3;
+  const NearItem it = items[blockIdx.x];
+  const int64_t kb = it.k0 + 16 * warp;
+  int64_t rend[2];
+  double rr[2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int64_t k = kb + gq + 8 * q;
+    rend[q] = k <= N ? min(it.n1, nend[k - 1]) : 0;
+    rr[q] = k <= N ? r_true[k - 1] : 0.0;
+  }
+  int64_t wend = max(rend[0], rend[1]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) wend = max(wend, (int64_t)__shfl_xor_sync(0xffffffffu, (long long)wend, o));
+  float acc[kTcDiag][2][4];
+#pragma unroll
+  for (int D = 0; D < kTcDiag; ++D)
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[D][u][q] = 0.0f;
+  const unsigned* Cw = reinterpret_cast<const unsigned*>(Cd);  // pairs of digits (columns 2m, 2m+1)
+  for (int64_t n0 = it.n0; n0 <= wend; n0 += 16) {
+    // A: 8 entries, register r = (row q = r & 1) x (column block r >> 1), half h = column 2tq + h
+    unsigned a[kTcDig][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      int dl[kTcDig], dh[kTcDig];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int q = r & 1;
+        const int64_t col = n0 + 2 * tq + h + ((r >> 1) ? 8 : 0);
+        double J = 0.0;
+        if (col <= rend[q]) J = table_j<double>(jtab, jt_n, deg, rr[q] * __ldg(&om_true[col - 1]));
+        const long long X = __double2ll_rn(J * 9007199254740992.0);  // J 2^53
+        if (h == 0) digits8(X, dl);
+        else digits8(X, dh);
+      }
+#pragma unroll
+      for (int i = 0; i < kTcDig; ++i) a[i][r] = pack_h2(dl[i], dh[i]);
+    }
+    // B: digit j, vector tile u: columns (n0 + 2tq, +1) and (n0 + 2tq + 8, +9) of vector 8u + gq
+    unsigned b[kTcDig][2][2];
+    const int64_t c0 = (n0 - 1 + 2 * tq) >> 1;  // index of the digit pair
+#pragma unroll
+    for (int j = 0; j < kTcDig; ++j)
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int64_t row = ((int64_t)j * 16 + 8 * u + gq) * (Npad >> 1);
+        b[j][u][0] = __ldg(&Cw[row + c0]);
+        b[j][u][1] = __ldg(&Cw[row + c0 + 4]);
+      }
+#pragma unroll
+    for (int D = 0; D < kTcDiag; ++D)
+#pragma unroll
+      for (int i = 0; i < kTcDig; ++i) {
+        const int j = D - i;
+        if (j < 0 || j >= kTcDig) continue;
+#pragma unroll
+        for (int u = 0; u < 2; ++u) mma_f16(acc[D][u], a[i], b[j][u][0], b[j][u][1]);
+      }
+  }
+  // combine the diagonals in FP64 and write: output (row gq + 8 (q >> 1), vector 8u + 2tq + (q & 1))
+  const int64_t t = (it.n0 - 1) / kTcChunk;
+#pragma unroll
+  for (int u = 0; u < 2; ++u)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int g = 8 * u + 2 * tq + (q & 1);
+      const int rowoff = 16 * warp + gq + 8 * (q >> 1);
+      const int64_t k = it.k0 + rowoff;
+      double v = 0.0;
+#pragma unroll
+      for (int D = kTcDiag - 1; D >= 0; --D) v = fma(v, 1.0 / 128.0, (double)acc[D][u][q]);
+      v = ldexp(v, Ce[t * 16 + g] - 9);
+      if (k > N || g >= nrhs) continue;
+      if (it.slot < 0) f[(int64_t)g * ldf + k - 1] = v;
+      else partial[(it.slot + (int64_t)rowoff * it.ntile) * nrhs + (int64_t)g * it.ntile + it.t] = v;
+    }
+}
+
 template <class R>
 __global__ void k_near_combine(const NearRow* __restrict__ rows, int64_t nrows, const R* __restrict__ partial,
                                int nrhs, double* f, int64_t ldf) {
@@ -258,6 +424,19 @@ void launch_near_df(const NearItem* items, int64_t nitems, const NearRow* mrows,
   else
     k_near_df<kMaxRhsGroup><<<grid, 256, 0, st>>>(items, nitems, nend, N, partial, nrhs, cd, f, ldf, r, om, jtab,
                                                   jt_n, deg);
+  if (nmrows > 0)
+    k_near_combine<double><<<(unsigned)((nmrows * 32 + 255) / 256), 256, 0, st>>>(mrows, nmrows, partial, nrhs, f,
+                                                                                ldf);
+}
+
+void launch_near_tc(const NearItem* items, int64_t nitems, const NearRow* mrows, int64_t nmrows,
+                    const int64_t* nend, int64_t N, double* partial, int nrhs, const double* c, int64_t ldc,
+                    void* Cdv, int* Ce, int64_t Npad, double* f, int64_t ldf, const double* r, const double* om,
+                    const double* jtab, int64_t jt_n, int deg, cudaStream_t st) {
+  __half* Cd = reinterpret_cast<__half*>(Cdv);
+  k_near_cdigits<<<(unsigned)(Npad / kTcChunk), kTcChunk, 0, st>>>(c, ldc, nrhs, N, Npad, Cd, Ce);
+  k_near_tc<<<(unsigned)nitems, 64, 0, st>>>(items, nend, N, partial, nrhs, Cd, Ce, Npad, f, ldf, r, om, jtab, jt_n,
+                                            deg);
   if (nmrows > 0)
     k_near_combine<double><<<(unsigned)((nmrows * 32 + 255) / 256), 256, 0, st>>>(mrows, nmrows, partial, nrhs, f,
                                                                                 ldf);
