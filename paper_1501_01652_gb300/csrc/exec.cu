@@ -317,7 +317,7 @@ int dev_plan_create(hankel_plan_s* p) {
   // per-execution coefficient copies: double-float pairs for DF64 near fields and transforms,
   // FP32 for FP32 transforms (FP32 near fields read them too)
   if (d->df64 || d->any_t[kTermDF64]) HK_TRY(dalloc(d, &d->cdf, (size_t)hp.opt.max_nrhs * N));
-  if (!d->fp32 && !d->df64 && hp.opt.max_nrhs >= kNearTcMinRhs) {
+  if (!d->fp32 && hp.opt.max_nrhs >= kNearTcMinRhs) {
     d->tc_npad = (N + 511) / 512 * 512;
     uint16_t* q = nullptr;
     HK_TRY(dalloc(d, &q, (size_t)8 * 16 * d->tc_npad));
@@ -701,15 +701,18 @@ int run_all(DevicePlan* d, const HostPlan& hp, const double* c, int64_t ldc, dou
   }
   {
     StageScope sc(d, HANKEL_STAGE_NEAR, st, record);
-    if (d->df64)
+    if (d->df64 && d->tcd && nrhs >= kNearTcMinRhs)
+      launch_near_tc(true, d->items, d->nitems, d->mrows, d->nmrows, d->nend, d->hpN, (double*)partial, nrhs, c,
+                     ldc, d->tcd, d->tce, d->tc_npad, f, ldf, d->rdf, d->omdf, d->jtabdf, hp.jt_n, hp.jt_deg, st);
+    else if (d->df64)
       launch_near_df(d->items, d->nitems, d->mrows, d->nmrows, d->nend, d->hpN, (double*)partial, nrhs, d->cdf, f,
                      ldf, d->rdf, d->omdf, d->jtabdf, hp.jt_n, hp.jt_deg, st);
     else if (d->fp32)
       launch_near<float>(d->items, d->nitems, d->mrows, d->nmrows, d->nend, d->hpN, (float*)partial, nrhs, c, ldc,
                          d->cf, f, ldf, d->rf, d->omf, d->jtabf, hp.jt_n, hp.jt_deg, st);
     else if (d->tcd && nrhs >= kNearTcMinRhs)
-      launch_near_tc(d->items, d->nitems, d->mrows, d->nmrows, d->nend, d->hpN, (double*)partial, nrhs, c, ldc,
-                     d->tcd, d->tce, d->tc_npad, f, ldf, d->nodes.r_true, d->nodes.om_true, d->jtab, hp.jt_n,
+      launch_near_tc(false, d->items, d->nitems, d->mrows, d->nmrows, d->nend, d->hpN, (double*)partial, nrhs, c,
+                     ldc, d->tcd, d->tce, d->tc_npad, f, ldf, d->nodes.r_true, d->nodes.om_true, d->jtab, hp.jt_n,
                      hp.jt_deg, st);
     else
       launch_near<double>(d->items, d->nitems, d->mrows, d->nmrows, d->nend, d->hpN, (double*)partial, nrhs, c, ldc,

@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "cplx.cuh"
 #include "kernels.cuh"
@@ -272,22 +273,28 @@ __global__ void __launch_bounds__(kTcChunk) k_near_cdigits(const double* __restr
 // rows gq, gq + 8 and columns 2tq, 2tq + 1, 2tq + 8, 2tq + 9 of each 16-column step (its A
 // fragment) and loads the coefficient digits of columns 2tq, 2tq + 1, 2tq + 8, 2tq + 9 for
 // vectors gq and gq + 8 (its B fragments).
+// DF: J in double-float (DF64 plans: r, om and jtab are float pairs), converted to the same
+// integer grid J 2^53 from its high and low parts (each conversion exact to half a unit).
+template <bool DF>
 __global__ void __launch_bounds__(64) k_near_tc(const NearItem* __restrict__ items, const int64_t* __restrict__ nend,
                                                int64_t N, double* partial, int nrhs, const __half* __restrict__ Cd,
                                                const int* __restrict__ Ce, int64_t Npad, double* f, int64_t ldf,
-                                               const double* __restrict__ r_true,
-                                               const double* __restrict__ om_true, const double* __restrict__ jtab,
-                                               int64_t jt_n, int deg) {
+                                               const void* __restrict__ rv, const void* __restrict__ omv,
+                                               const void* __restrict__ jtv, int64_t jt_n, int deg) {
+  typedef typename std::conditional<DF, float2, double>::type T;
+  const T* r_true = reinterpret_cast<const T*>(rv);
+  const T* om_true = reinterpret_cast<const T*>(omv);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, gq = lane >> 2, tq = lane & 3;
   const NearItem it = items[blockIdx.x];
   const int64_t kb = it.k0 + 16 * warp;
   int64_t rend[2];
-  double rr[2];
+  T rr[2];
 #pragma unroll
   for (int q = 0; q < 2; ++q) {
     const int64_t k = kb + gq + 8 * q;
     rend[q] = k <= N ? min(it.n1, nend[k - 1]) : 0;
-    rr[q] = k <= N ? r_true[k - 1] : 0.0;
+    if (k <= N) rr[q] = r_true[k - 1];
+    else rr[q] = T{};
   }
   int64_t wend = max(rend[0], rend[1]);
 #pragma unroll
@@ -310,9 +317,22 @@ __global__ void __launch_bounds__(64) k_near_tc(const NearItem* __restrict__ ite
       for (int h = 0; h < 2; ++h) {
         const int q = r & 1;
         const int64_t col = n0 + 2 * tq + h + ((r >> 1) ? 8 : 0);
-        double J = 0.0;
-        if (col <= rend[q]) J = table_j<double>(jtab, jt_n, deg, rr[q] * __ldg(&om_true[col - 1]));
-        const long long X = __double2ll_rn(J * 9007199254740992.0);  // J 2^53
+        long long X = 0;  // J 2^53
+        if (col <= rend[q]) {
+          if constexpr (DF) {
+            const float2 om = __ldg(&om_true[col - 1]);
+            const float zh = rr[q].x * om.x;
+            float zl = fmaf(rr[q].x, om.x, -zh);
+            zl = fmaf(rr[q].x, om.y, zl);
+            zl = fmaf(rr[q].y, om.x, zl);
+            const df64 J = table_j_df(reinterpret_cast<const float2*>(jtv), jt_n, deg, zh, zl);
+            X = __float2ll_rn(J.h * 9007199254740992.0f) + __float2ll_rn(J.l * 9007199254740992.0f);
+          } else {
+            const double J = table_j<double>(reinterpret_cast<const double*>(jtv), jt_n, deg,
+                                             rr[q] * __ldg(&om_true[col - 1]));
+            X = __double2ll_rn(J * 9007199254740992.0);
+          }
+        }
         if (h == 0) digits8(X, dl);
         else digits8(X, dh);
       }
@@ -429,14 +449,18 @@ void launch_near_df(const NearItem* items, int64_t nitems, const NearRow* mrows,
                                                                                 ldf);
 }
 
-void launch_near_tc(const NearItem* items, int64_t nitems, const NearRow* mrows, int64_t nmrows,
+void launch_near_tc(bool df, const NearItem* items, int64_t nitems, const NearRow* mrows, int64_t nmrows,
                     const int64_t* nend, int64_t N, double* partial, int nrhs, const double* c, int64_t ldc,
-                    void* Cdv, int* Ce, int64_t Npad, double* f, int64_t ldf, const double* r, const double* om,
-                    const double* jtab, int64_t jt_n, int deg, cudaStream_t st) {
+                    void* Cdv, int* Ce, int64_t Npad, double* f, int64_t ldf, const void* r, const void* om,
+                    const void* jtab, int64_t jt_n, int deg, cudaStream_t st) {
   __half* Cd = reinterpret_cast<__half*>(Cdv);
   k_near_cdigits<<<(unsigned)(Npad / kTcChunk), kTcChunk, 0, st>>>(c, ldc, nrhs, N, Npad, Cd, Ce);
-  k_near_tc<<<(unsigned)nitems, 64, 0, st>>>(items, nend, N, partial, nrhs, Cd, Ce, Npad, f, ldf, r, om, jtab, jt_n,
-                                            deg);
+  if (df)
+    k_near_tc<true><<<(unsigned)nitems, 64, 0, st>>>(items, nend, N, partial, nrhs, Cd, Ce, Npad, f, ldf, r, om, jtab,
+                                                    jt_n, deg);
+  else
+    k_near_tc<false><<<(unsigned)nitems, 64, 0, st>>>(items, nend, N, partial, nrhs, Cd, Ce, Npad, f, ldf, r, om,
+                                                     jtab, jt_n, deg);
   if (nmrows > 0)
     k_near_combine<double><<<(unsigned)((nmrows * 32 + 255) / 256), 256, 0, st>>>(mrows, nmrows, partial, nrhs, f,
                                                                                 ldf);
