@@ -164,14 +164,14 @@ void launch_near(const NearItem* items, int64_t nitems, const NearRow* mrows, in
                  int64_t ldf, const R* r, const R* om, const R* jtab, int64_t jt_n, int deg, cudaStream_t st);
 
 // Near field with the per-vector products as exact split-digit fp16 tensor-core products
-// (8 <= nrhs <= 16), J evaluated in FP64 (r, om, jtab: double) or, with df, in double-float
-// (float pairs): Cd holds 8 x 16 x Npad fp16 digits and Ce (Npad / 512) x 16 exponents, both
-// written here from c (Npad = N rounded up to a multiple of 512).
+// (8 <= nrhs <= 16), FP64 and double-float plans: z = r_n om_n in FP64, J from the Q62
+// fixed-point table jtabq on the integer pipe. Cd holds 8 x 16 x Npad fp16 digits and Ce
+// (Npad / 512) x 16 exponents, both written here from c (Npad = N rounded up to a multiple of 512).
 constexpr int kNearTcMinRhs = 8;
-void launch_near_tc(bool df, const NearItem* items, int64_t nitems, const NearRow* mrows, int64_t nmrows,
-                    const int64_t* nend, int64_t N, double* partial, int nrhs, const double* c, int64_t ldc,
-                    void* Cd, int* Ce, int64_t Npad, double* f, int64_t ldf, const void* r, const void* om,
-                    const void* jtab, int64_t jt_n, int deg, cudaStream_t st);
+void launch_near_tc(const NearItem* items, int64_t nitems, const NearRow* mrows, int64_t nmrows, const int64_t* nend,
+                    int64_t N, double* partial, int nrhs, const double* c, int64_t ldc, void* Cd, int* Ce,
+                    int64_t Npad, double* f, int64_t ldf, const double* r, const double* om, const long long* jtabq,
+                    int64_t jt_n, int deg, cudaStream_t st);
 // Near field of DF64 plans in double-float on the FP32 pipe: r, om and jtab hold (high, low)
 // float pairs of the FP64 tables, cd the coefficients as pairs ([nrhs][N]); partial sums and
 // outputs are FP64.

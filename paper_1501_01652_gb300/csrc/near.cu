@@ -218,9 +218,49 @@ __device__ __forceinline__ void digits8(long long X, int (&d)[kTcDig]) {
   }
 }
 
-__device__ __forceinline__ unsigned pack_h2(int lo, int hi) {
-  __half2 v = __halves2half2(__int2half_rn(lo), __int2half_rn(hi));
-  return *reinterpret_cast<unsigned*>(&v);
+// The balanced digits of X (|X| <= 2^54) are the base-128 digits of X + kDigOff, less 64
+// (kDigOff has every digit 64). Digit i (weight 128^(7 - i)) of two values Yl, Yh = X + kDigOff,
+// as an fp16 pair: the bits 0x6400 + e are the fp16 value 1024 + e for 0 <= e < 1024, so one
+// packed subtraction of 1088 leaves the digits e - 64, exactly.
+constexpr unsigned long long kDigOff = 0x0081020408102040ULL;
+
+template <int I>
+__device__ __forceinline__ unsigned digit_pair(unsigned long long Yl, unsigned long long Yh) {
+  constexpr int s = 7 * (kTcDig - 1 - I);
+  const unsigned el = (unsigned)(Yl >> s) & 127u, eh = (unsigned)(Yh >> s) & 127u;
+  const unsigned w = 0x64006400u | el | (eh << 16);
+  const __half2 v = __hsub2(*reinterpret_cast<const __half2*>(&w), __half2(__float2half(1088.0f), __float2half(1088.0f)));
+  return *reinterpret_cast<const unsigned*>(&v);
+}
+
+// J_nu(z) from the Q62 table, in two parts. q62_interval finds the interval i = floor(z kJTabSub)
+// and U = (z kJTabSub - i - 1/2) 2^64 from the bits of z (z >= 0) by integer operations; the
+// caller runs Horner's rule in Q62 with the signed high halves of 64 x 64-bit products (each
+// step truncating by less than 2^-62) and rounds to J 2^53. Every operation but z = r omega is
+// on the integer pipe.
+__device__ __forceinline__ long long q62_interval(int64_t jt_n, double z, long long& U) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(z);
+  const int E = (int)(bits >> 52) & 0x7ff;
+  const unsigned long long M = (bits & 0xfffffffffffffULL) | (E ? (1ULL << 52) : 0ULL);
+  const int sh = 52 + 1023 - kJTabLog - E;  // mantissa bits below 1/kJTabSub
+  long long i;
+  unsigned long long F;  // the fraction z kJTabSub - i, times 2^64
+  if (sh <= 0) {
+    i = jt_n;
+    F = 0;
+  } else if (sh <= 52) {
+    i = (long long)(M >> sh);
+    F = M << (64 - sh);
+  } else {
+    i = 0;
+    F = sh - 53 < 64 ? (M << 11) >> (sh - 53) : 0ULL;
+  }
+  if (i >= jt_n) {  // beyond the table (the near field stays below zmax < jt_n / kJTabSub)
+    i = jt_n - 1;
+    F = ~0ULL;
+  }
+  U = (long long)(F ^ (1ULL << 63));
+  return i;
 }
 
 __device__ __forceinline__ void mma_f16(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
@@ -272,29 +312,23 @@ __global__ void __launch_bounds__(kTcChunk) k_near_cdigits(const double* __restr
 // and all 16 vector slots, as two m16n8 output tiles. Thread (gq, tq) of a warp evaluates J at
 // rows gq, gq + 8 and columns 2tq, 2tq + 1, 2tq + 8, 2tq + 9 of each 16-column step (its A
 // fragment) and loads the coefficient digits of columns 2tq, 2tq + 1, 2tq + 8, 2tq + 9 for
-// vectors gq and gq + 8 (its B fragments).
-// DF: J in double-float (DF64 plans: r, om and jtab are float pairs), converted to the same
-// integer grid J 2^53 from its high and low parts (each conversion exact to half a unit).
-template <bool DF>
+// vectors gq and gq + 8 (its B fragments). J comes from the fixed-point table (FP64 and
+// double-float plans alike: it is exact to the digit grid either way).
 __global__ void __launch_bounds__(64) k_near_tc(const NearItem* __restrict__ items, const int64_t* __restrict__ nend,
                                                int64_t N, double* partial, int nrhs, const __half* __restrict__ Cd,
                                                const int* __restrict__ Ce, int64_t Npad, double* f, int64_t ldf,
-                                               const void* __restrict__ rv, const void* __restrict__ omv,
-                                               const void* __restrict__ jtv, int64_t jt_n, int deg) {
-  typedef typename std::conditional<DF, float2, double>::type T;
-  const T* r_true = reinterpret_cast<const T*>(rv);
-  const T* om_true = reinterpret_cast<const T*>(omv);
+                                               const double* __restrict__ r_true, const double* __restrict__ om_true,
+                                               const long long* __restrict__ jq, int64_t jt_n, int deg) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, gq = lane >> 2, tq = lane & 3;
   const NearItem it = items[blockIdx.x];
   const int64_t kb = it.k0 + 16 * warp;
   int64_t rend[2];
-  T rr[2];
+  double rr[2];
 #pragma unroll
   for (int q = 0; q < 2; ++q) {
     const int64_t k = kb + gq + 8 * q;
     rend[q] = k <= N ? min(it.n1, nend[k - 1]) : 0;
-    if (k <= N) rr[q] = r_true[k - 1];
-    else rr[q] = T{};
+    rr[q] = k <= N ? r_true[k - 1] : 0.0;
   }
   int64_t wend = max(rend[0], rend[1]);
 #pragma unroll
@@ -308,36 +342,40 @@ __global__ void __launch_bounds__(64) k_near_tc(const NearItem* __restrict__ ite
       for (int q = 0; q < 4; ++q) acc[D][u][q] = 0.0f;
   const unsigned* Cw = reinterpret_cast<const unsigned*>(Cd);  // pairs of digits (columns 2m, 2m+1)
   for (int64_t n0 = it.n0; n0 <= wend; n0 += 16) {
-    // A: 8 entries, register r = (row q = r & 1) x (column block r >> 1), half h = column 2tq + h
+    // A: 8 entries e = 2r + h, register r = (row q = r & 1) x (column block r >> 1), half
+    // h = column 2tq + h; their Horner chains advance together (8 independent chains a thread)
+    const long long* tp[8];
+    long long U[8], v[8];
+    bool on[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int r = e >> 1, h = e & 1, q = r & 1;
+      const int64_t col = n0 + 2 * tq + h + ((r >> 1) ? 8 : 0);
+      on[e] = col <= rend[q];
+      const double z = on[e] ? rr[q] * __ldg(&om_true[col - 1]) : 0.0;
+      tp[e] = jq + q62_interval(jt_n, z, U[e]) * (deg + 1);
+      v[e] = __ldg(&tp[e][deg]);
+    }
+    for (int j = deg - 1; j >= 0; --j)
+#pragma unroll
+      for (int e = 0; e < 8; ++e) v[e] = __mul64hi(v[e], U[e]) + __ldg(&tp[e][j]);
     unsigned a[kTcDig][4];
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
-      int dl[kTcDig], dh[kTcDig];
+      unsigned long long Y[2];  // J 2^53 (0 outside the row's prefix) + kDigOff
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        const int q = r & 1;
-        const int64_t col = n0 + 2 * tq + h + ((r >> 1) ? 8 : 0);
-        long long X = 0;  // J 2^53
-        if (col <= rend[q]) {
-          if constexpr (DF) {
-            const float2 om = __ldg(&om_true[col - 1]);
-            const float zh = rr[q].x * om.x;
-            float zl = fmaf(rr[q].x, om.x, -zh);
-            zl = fmaf(rr[q].x, om.y, zl);
-            zl = fmaf(rr[q].y, om.x, zl);
-            const df64 J = table_j_df(reinterpret_cast<const float2*>(jtv), jt_n, deg, zh, zl);
-            X = __float2ll_rn(J.h * 9007199254740992.0f) + __float2ll_rn(J.l * 9007199254740992.0f);
-          } else {
-            const double J = table_j<double>(reinterpret_cast<const double*>(jtv), jt_n, deg,
-                                             rr[q] * __ldg(&om_true[col - 1]));
-            X = __double2ll_rn(J * 9007199254740992.0);
-          }
-        }
-        if (h == 0) digits8(X, dl);
-        else digits8(X, dh);
+        const int e = 2 * r + h;
+        Y[h] = (unsigned long long)(on[e] ? (v[e] + 256) >> 9 : 0LL) + kDigOff;
       }
-#pragma unroll
-      for (int i = 0; i < kTcDig; ++i) a[i][r] = pack_h2(dl[i], dh[i]);
+      a[0][r] = digit_pair<0>(Y[0], Y[1]);
+      a[1][r] = digit_pair<1>(Y[0], Y[1]);
+      a[2][r] = digit_pair<2>(Y[0], Y[1]);
+      a[3][r] = digit_pair<3>(Y[0], Y[1]);
+      a[4][r] = digit_pair<4>(Y[0], Y[1]);
+      a[5][r] = digit_pair<5>(Y[0], Y[1]);
+      a[6][r] = digit_pair<6>(Y[0], Y[1]);
+      a[7][r] = digit_pair<7>(Y[0], Y[1]);
     }
     // B: digit j, vector tile u: columns (n0 + 2tq, +1) and (n0 + 2tq + 8, +9) of vector 8u + gq
     unsigned b[kTcDig][2][2];
@@ -449,18 +487,14 @@ void launch_near_df(const NearItem* items, int64_t nitems, const NearRow* mrows,
                                                                                 ldf);
 }
 
-void launch_near_tc(bool df, const NearItem* items, int64_t nitems, const NearRow* mrows, int64_t nmrows,
-                    const int64_t* nend, int64_t N, double* partial, int nrhs, const double* c, int64_t ldc,
-                    void* Cdv, int* Ce, int64_t Npad, double* f, int64_t ldf, const void* r, const void* om,
-                    const void* jtab, int64_t jt_n, int deg, cudaStream_t st) {
+void launch_near_tc(const NearItem* items, int64_t nitems, const NearRow* mrows, int64_t nmrows, const int64_t* nend,
+                    int64_t N, double* partial, int nrhs, const double* c, int64_t ldc, void* Cdv, int* Ce,
+                    int64_t Npad, double* f, int64_t ldf, const double* r, const double* om, const long long* jtabq,
+                    int64_t jt_n, int deg, cudaStream_t st) {
   __half* Cd = reinterpret_cast<__half*>(Cdv);
   k_near_cdigits<<<(unsigned)(Npad / kTcChunk), kTcChunk, 0, st>>>(c, ldc, nrhs, N, Npad, Cd, Ce);
-  if (df)
-    k_near_tc<true><<<(unsigned)nitems, 64, 0, st>>>(items, nend, N, partial, nrhs, Cd, Ce, Npad, f, ldf, r, om, jtab,
-                                                    jt_n, deg);
-  else
-    k_near_tc<false><<<(unsigned)nitems, 64, 0, st>>>(items, nend, N, partial, nrhs, Cd, Ce, Npad, f, ldf, r, om,
-                                                     jtab, jt_n, deg);
+  k_near_tc<<<(unsigned)nitems, 64, 0, st>>>(items, nend, N, partial, nrhs, Cd, Ce, Npad, f, ldf, r, om, jtabq, jt_n,
+                                             deg);
   if (nmrows > 0)
     k_near_combine<double><<<(unsigned)((nmrows * 32 + 255) / 256), 256, 0, st>>>(mrows, nmrows, partial, nrhs, f,
                                                                                 ldf);

@@ -93,6 +93,9 @@ struct HostPlan {
   int jt_sub = kJTabSub;
   int64_t jt_n = 0;
   std::vector<double> jtab;
+  // the same polynomials in the variable u = sub (z - z_c) in [-1/2, 1/2), as Q62 fixed-point
+  // integers: jtabq[i (deg+1) + d] = round(t_d sub^-d 2^62), rounded from the double-double sums
+  std::vector<long long> jtabq;
 };
 
 // Builds every host table of a plan. Returns a hankel_status code.

@@ -1000,6 +1000,7 @@ void build_jtable(HostPlan& hp) {
   hp.jt_sub = sub;
   hp.jt_n = (int64_t)std::ceil(hp.zmax * sub) + 2;
   hp.jtab.assign((size_t)hp.jt_n * (deg + 1), 0.0);
+  hp.jtabq.assign((size_t)hp.jt_n * (deg + 1), 0);
   std::vector<DD> J;
   const int L = nu + deg + 1;
   for (int64_t i = 0; i < hp.jt_n; ++i) {
@@ -1018,6 +1019,9 @@ void build_jtable(HostPlan& hp) {
         acc = dd_add(acc, dd_mul(ddv(coef), term));
       }
       hp.jtab[(size_t)i * (deg + 1) + d] = acc.h + acc.l;
+      // |t_d sub^-d| < 2: the scaled value fits a signed 64-bit integer; x - rint(x) is exact
+      const double x = std::ldexp(acc.h, 62 - kJTabLog * d), y = std::ldexp(acc.l, 62 - kJTabLog * d);
+      hp.jtabq[(size_t)i * (deg + 1) + d] = std::llrint(x) + std::llrint((x - std::rint(x)) + y);
     }
   }
 }
