@@ -192,9 +192,9 @@ __global__ void __launch_bounds__(256) k_near_df(const NearItem* __restrict__ it
 }
 
 // Rows whose prefix spans several tiles: the partial sums of row k and vector rr are the
-// npieces consecutive values at slot0 nrhs + rr npieces. A warp per row; lane l adds the
-// pieces l, l + 32, ... in order and the lanes combine in a fixed shuffle tree, so the result
-// does not depend on scheduling.
+// npieces consecutive values at slot0 nrhs + rr npieces. A warp per row and 16 vectors at a
+// time; lane l adds, in order, the pieces l >> 4, (l >> 4) + 2, ... of vector l & 15 and one
+// shuffle adds the two halves, so the result does not depend on scheduling.
 // FP64 near field with the per-vector products on the tensor cores (FP64 plans, 8 to 16 vectors):
 // split-digit products (the Ozaki scheme). J (|J| <= 1) and, per 512-column chunk and vector,
 // the coefficients scaled by 2^-e (2^e bounds the chunk's largest |c|) are rounded to the
@@ -208,15 +208,6 @@ __global__ void __launch_bounds__(256) k_near_df(const NearItem* __restrict__ it
 // they are combined in FP64 once per tile. The rounding of J and C to the digit grid is 2^-54
 // and 2^-55 of their scales: the products are as accurate as FP64 ones, and the sums exact.
 constexpr int kTcDig = 8, kTcDiag = 9, kTcChunk = 512;
-
-__device__ __forceinline__ void digits8(long long X, int (&d)[kTcDig]) {
-#pragma unroll
-  for (int i = kTcDig - 1; i >= 0; --i) {
-    const int v = (int)(((X + 64) & 127) - 64);
-    d[i] = v;
-    X = (X - v) >> 7;
-  }
-}
 
 // The balanced digits of X (|X| <= 2^54) are the base-128 digits of X + kDigOff, less 64
 // (kDigOff has every digit 64). Digit i (weight 128^(7 - i)) of two values Yl, Yh = X + kDigOff,
@@ -264,7 +255,7 @@ __device__ __forceinline__ long long q62_interval(int64_t jt_n, double z, long l
 }
 
 __device__ __forceinline__ void mma_f16(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
-  asm volatile(
+  asm(
       "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
       : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
@@ -272,40 +263,62 @@ __device__ __forceinline__ void mma_f16(float (&d)[4], const unsigned (&a)[4], u
 
 // Coefficient digits: one CTA of kTcChunk threads per chunk t; Ce[t * 16 + g] = e and
 // Cd[(j * 16 + g) * Npad + n - 1] = digit j of round(c_n^g 2^-e 2^54) (zeros for g >= nrhs and
-// n > N).
+// n > N), 2^e the smallest power of two above the chunk's largest |c_n^g| (2^-1021 at least).
+// Integer operations throughout: the maximum of |c| is the maximum of its bit patterns, e
+// comes from the exponent field, and c 2^(54 - e) (below 2^54) from the mantissa shifted right
+// with rounding to nearest (ties up).
 __global__ void __launch_bounds__(kTcChunk) k_near_cdigits(const double* __restrict__ c, int64_t ldc, int nrhs,
                                                           int64_t N, int64_t Npad, __half* Cd, int* Ce) {
   const int64_t t = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int64_t n = t * kTcChunk + tid;  // 0-based column
-  __shared__ double wmax[kTcChunk / 32][16];
+  __shared__ long long wmax[kTcChunk / 32][16];
   __shared__ int sexp[16];
-  double v[16];
+  long long b[16];
 #pragma unroll
   for (int g = 0; g < 16; ++g) {
-    v[g] = (g < nrhs && n < N) ? c[(int64_t)g * ldc + n] : 0.0;
-    double m = fabs(v[g]);
+    b[g] = (g < nrhs && n < N) ? __double_as_longlong(c[(int64_t)g * ldc + n]) : 0LL;
+    long long m = b[g] & 0x7fffffffffffffffLL;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    for (int o = 16; o > 0; o >>= 1) m = max(m, (long long)__shfl_xor_sync(0xffffffffu, m, o));
     if (lane == 0) wmax[w][g] = m;
   }
   __syncthreads();
   if (tid < 16) {
-    double m = 0.0;
-    for (int j = 0; j < kTcChunk / 32; ++j) m = fmax(m, wmax[j][tid]);
-    const int e = m > 0.0 ? ilogb(m) + 1 : 0;
+    long long m = 0;
+    for (int j = 0; j < kTcChunk / 32; ++j) m = max(m, wmax[j][tid]);
+    const int ef = max((int)(m >> 52), 1);      // |c| < 2^(ef - 1022)
+    const int e = m > 0 ? ef - 1022 : 0;
     sexp[tid] = e;
     Ce[t * 16 + tid] = e;
   }
   __syncthreads();
 #pragma unroll
   for (int g = 0; g < 16; ++g) {
-    const long long X = __double2ll_rn(ldexp(v[g], 54 - sexp[g]));
-    int d[kTcDig];
-    digits8(X, d);
+    const int ef = (int)((b[g] >> 52) & 0x7ff);
+    const long long M = (b[g] & 0xfffffffffffffLL) | (ef ? (1LL << 52) : 0LL);
+    // c = M 2^(max(ef, 1) - 1075), so c 2^(54 - e) = M 2^-s with s = 1021 + e - max(ef, 1) >= -1
+    const int sft = 1021 + sexp[g] - max(ef, 1);
+    long long X = sft < 0 ? M << 1 : (sft == 0 ? M : (sft < 63 ? (M + (1LL << (sft - 1))) >> sft : 0LL));
+    if (b[g] < 0) X = -X;
+    const unsigned long long Y = (unsigned long long)X + kDigOff;
 #pragma unroll
-    for (int j = 0; j < kTcDig; ++j) Cd[((int64_t)j * 16 + g) * Npad + n] = __int2half_rn(d[j]);
+    for (int j = 0; j < kTcDig; ++j)
+      Cd[((int64_t)j * 16 + g) * Npad + n] = __int2half_rn((int)((Y >> (7 * (kTcDig - 1 - j))) & 127u) - 64);
   }
+}
+
+// The A fragment of J digit i (register r: entries 2r, 2r + 1) and its products with the
+// coefficient digits j = 0 .. min(7, 8 - i), diagonal D = i + j.
+template <int I>
+__device__ __forceinline__ void tc_digit(float (&acc)[kTcDiag][2][4], const unsigned long long (&Y)[8],
+                                         const unsigned (&b)[kTcDig][2][2]) {
+  const unsigned a[4] = {digit_pair<I>(Y[0], Y[1]), digit_pair<I>(Y[2], Y[3]), digit_pair<I>(Y[4], Y[5]),
+                         digit_pair<I>(Y[6], Y[7])};
+#pragma unroll
+  for (int j = 0; j < kTcDig && I + j < kTcDiag; ++j)
+#pragma unroll
+    for (int u = 0; u < 2; ++u) mma_f16(acc[I + j][u], a, b[j][u][0], b[j][u][1]);
 }
 
 // A CTA of two warps per near-field tile (NearItem); warp w takes rows k0 + 16w .. k0 + 16w + 15
@@ -314,7 +327,7 @@ __global__ void __launch_bounds__(kTcChunk) k_near_cdigits(const double* __restr
 // fragment) and loads the coefficient digits of columns 2tq, 2tq + 1, 2tq + 8, 2tq + 9 for
 // vectors gq and gq + 8 (its B fragments). J comes from the fixed-point table (FP64 and
 // double-float plans alike: it is exact to the digit grid either way).
-__global__ void __launch_bounds__(64) k_near_tc(const NearItem* __restrict__ items, const int64_t* __restrict__ nend,
+__global__ void __launch_bounds__(64, 6) k_near_tc(const NearItem* __restrict__ items, const int64_t* __restrict__ nend,
                                                int64_t N, double* partial, int nrhs, const __half* __restrict__ Cd,
                                                const int* __restrict__ Ce, int64_t Npad, double* f, int64_t ldf,
                                                const double* __restrict__ r_true, const double* __restrict__ om_true,
@@ -359,24 +372,9 @@ __global__ void __launch_bounds__(64) k_near_tc(const NearItem* __restrict__ ite
     for (int j = deg - 1; j >= 0; --j)
 #pragma unroll
       for (int e = 0; e < 8; ++e) v[e] = __mul64hi(v[e], U[e]) + __ldg(&tp[e][j]);
-    unsigned a[kTcDig][4];
+    unsigned long long Y[8];  // J 2^53 (0 outside the row's prefix) + kDigOff
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      unsigned long long Y[2];  // J 2^53 (0 outside the row's prefix) + kDigOff
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int e = 2 * r + h;
-        Y[h] = (unsigned long long)(on[e] ? (v[e] + 256) >> 9 : 0LL) + kDigOff;
-      }
-      a[0][r] = digit_pair<0>(Y[0], Y[1]);
-      a[1][r] = digit_pair<1>(Y[0], Y[1]);
-      a[2][r] = digit_pair<2>(Y[0], Y[1]);
-      a[3][r] = digit_pair<3>(Y[0], Y[1]);
-      a[4][r] = digit_pair<4>(Y[0], Y[1]);
-      a[5][r] = digit_pair<5>(Y[0], Y[1]);
-      a[6][r] = digit_pair<6>(Y[0], Y[1]);
-      a[7][r] = digit_pair<7>(Y[0], Y[1]);
-    }
+    for (int e = 0; e < 8; ++e) Y[e] = (unsigned long long)(on[e] ? (v[e] + 256) >> 9 : 0LL) + kDigOff;
     // B: digit j, vector tile u: columns (n0 + 2tq, +1) and (n0 + 2tq + 8, +9) of vector 8u + gq
     unsigned b[kTcDig][2][2];
     const int64_t c0 = (n0 - 1 + 2 * tq) >> 1;  // index of the digit pair
@@ -388,15 +386,16 @@ __global__ void __launch_bounds__(64) k_near_tc(const NearItem* __restrict__ ite
         b[j][u][0] = __ldg(&Cw[row + c0]);
         b[j][u][1] = __ldg(&Cw[row + c0 + 4]);
       }
-#pragma unroll
-    for (int D = 0; D < kTcDiag; ++D)
-#pragma unroll
-      for (int i = 0; i < kTcDig; ++i) {
-        const int j = D - i;
-        if (j < 0 || j >= kTcDig) continue;
-#pragma unroll
-        for (int u = 0; u < 2; ++u) mma_f16(acc[D][u], a[i], b[j][u][0], b[j][u][1]);
-      }
+    // digit i of J against digits j <= 8 - i of the coefficients: consecutive products go to
+    // different diagonals, so they do not wait on one another
+    tc_digit<0>(acc, Y, b);
+    tc_digit<1>(acc, Y, b);
+    tc_digit<2>(acc, Y, b);
+    tc_digit<3>(acc, Y, b);
+    tc_digit<4>(acc, Y, b);
+    tc_digit<5>(acc, Y, b);
+    tc_digit<6>(acc, Y, b);
+    tc_digit<7>(acc, Y, b);
   }
   // combine the diagonals in FP64 and write: output (row gq + 8 (q >> 1), vector 8u + 2tq + (q & 1))
   const int64_t t = (it.n0 - 1) / kTcChunk;
@@ -421,16 +420,18 @@ template <class R>
 __global__ void k_near_combine(const NearRow* __restrict__ rows, int64_t nrows, const R* __restrict__ partial,
                                int nrhs, double* f, int64_t ldf) {
   const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, g = lane & 15, h = lane >> 4;
   if (w >= nrows) return;
   const NearRow row = rows[w];
-  for (int rr = 0; rr < nrhs; ++rr) {
-    const R* p = partial + row.slot0 * nrhs + (int64_t)rr * row.npieces;
+  for (int r0 = 0; r0 < nrhs; r0 += 16) {
+    const int rr = r0 + g;
     R s = 0;
-    for (int j = lane; j < row.npieces; j += 32) s += p[j];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (lane == 0) f[(int64_t)rr * ldf + row.k - 1] = (double)s;
+    if (rr < nrhs) {
+      const R* p = partial + row.slot0 * nrhs + (int64_t)rr * row.npieces;
+      for (int64_t j = h; j < row.npieces; j += 2) s += p[j];
+    }
+    s += __shfl_down_sync(0xffffffffu, s, 16);
+    if (h == 0 && rr < nrhs) f[(int64_t)rr * ldf + row.k - 1] = (double)s;
   }
 }
 
