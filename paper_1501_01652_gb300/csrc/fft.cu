@@ -210,18 +210,32 @@ __device__ __forceinline__ void reg_dft_unit(C (&a)[1 << LQ]) {
 // kTile-contiguous per element. The block has kTile Q1 threads, one butterfly per thread and
 // sub-stage. Twiddles are deferred as described above; the pass twiddle exponent p s of a thread's
 // sequence is recomputed per thread.
+// Thread shape of a pass of radix 2^LOGR = Q1 Q2 (L1 = ceil(LOGR / 2)). Sub-stage 1 has kTile Q2
+// butterflies of radix Q1, sub-stage 2 kTile Q1 of radix Q2. FP64 passes (bound by the FP64
+// pipe) take a thread per butterfly of sub-stage 2, so for odd LOGR half the threads wait out
+// sub-stage 1; double-float and FP32 passes (bound by issue and memory) take a thread per
+// butterfly of sub-stage 1 and B2 = Q1 / Q2 butterflies of sub-stage 2 each, keeping every warp busy.
+template <int LOGR, class C>
+struct PassShape {
+  static constexpr int L1 = (LOGR + 1) / 2, L2 = LOGR - L1;
+  static constexpr int Q1 = 1 << L1, Q2 = 1 << L2;
+  static constexpr bool BAL = !std::is_same<C, double2>::value;
+  static constexpr int NT = BAL ? kTile * Q2 : kTile * Q1;  // threads
+  static constexpr int NB1 = kTile * Q2;                    // butterflies of sub-stage 1 (<= NT)
+  static constexpr int B2 = kTile * Q1 / NT;                // butterflies of sub-stage 2 per thread
+};
+
 template <int LOGR, bool INV, class C>
 __global__ void __launch_bounds__(kFftThreads) k_fft_pass_reg(const C* __restrict__ src, C* __restrict__ dst,
                                                               int logF, int logS, const C* __restrict__ tw,
                                                               int logFmax, const C* __restrict__ hmul,
                                                               int64_t nseg, FftGen gen) {
+  typedef PassShape<LOGR, C> PS;
   constexpr int R = 1 << LOGR;
-  constexpr int L1 = (LOGR + 1) / 2, L2 = LOGR - L1;
-  constexpr int Q1 = 1 << L1, Q2 = 1 << L2;
-  constexpr int NT = kTile * Q1;                     // threads = butterflies of sub-stage 2
-  constexpr int NB1 = kTile * Q2;                    // butterflies of sub-stage 1 (<= NT)
+  constexpr int L1 = PS::L1, L2 = PS::L2, Q1 = PS::Q1, Q2 = PS::Q2;
+  constexpr int NT = PS::NT, NB1 = PS::NB1, B2 = PS::B2;
   constexpr int PER = R * kTile / NT;                // points per thread in the transposing fill
-  static_assert(NT <= kFftThreads && NB1 <= NT, "one butterfly per thread and sub-stage");
+  static_assert(NT <= kFftThreads && NB1 <= NT && B2 * NT == kTile * Q1, "thread shape");
   extern __shared__ __align__(16) unsigned char sm_raw[];
   C* v = reinterpret_cast<C*>(sm_raw);
   const int logFR = logF - LOGR;
@@ -292,14 +306,16 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_pass_reg(const C* __restric
     for (int r = 0; r < Q1; ++r) v[(bf + Q2 * r) * kRow + i] = a[r];
   }
   __syncthreads();
-  {
+#pragma unroll
+  for (int u = 0; u < B2; ++u) {
+    const uint32_t b2 = bf + u * (NT / kTile);  // this thread's butterfly of sub-stage 2
     C b[Q2];
 #pragma unroll
-    for (int j = 0; j < Q2; ++j) b[j] = v[(Q2 * bf + j) * kRow + i];
-    reg_dft<L2, INV>(b, (bf << (logFmax - LOGR)) + (pti << fsh), tw, logFmax, fmask);
+    for (int j = 0; j < Q2; ++j) b[j] = v[(Q2 * b2 + j) * kRow + i];
+    reg_dft<L2, INV>(b, (b2 << (logFmax - LOGR)) + (pti << fsh), tw, logFmax, fmask);
     C* yb = y + pi0 + i;
 #pragma unroll
-    for (int r = 0; r < Q2; ++r) yb[(bf + Q1 * r) << logFR] = b[r];
+    for (int r = 0; r < Q2; ++r) yb[(b2 + Q1 * r) << logFR] = b[r];
   }
 }
 
@@ -531,9 +547,8 @@ void launch_pass(const C* src, C* dst, int logF, int logS, int ncols, const C* t
   constexpr int R = 1 << LOGR;
   const int64_t pairs = ((int64_t)ncols << logF) >> LOGR;
   const int64_t grid = pairs / kTile;
-  // one buffer (the sub-stages work in place); threads = butterflies of the wider sub-stage
-  constexpr int L2 = LOGR - (LOGR + 1) / 2;
-  constexpr int threads = kTile * (R >> L2);
+  // one buffer (the sub-stages work in place)
+  constexpr int threads = PassShape<LOGR, C>::NT;
   const size_t smem = (size_t)R * kRow * sizeof(C);
   static bool configured = false;
   if (!configured) {
