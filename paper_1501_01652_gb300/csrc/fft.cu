@@ -207,22 +207,19 @@ __device__ __forceinline__ void reg_dft_unit(C (&a)[1 << LQ]) {
 // registers (Q1 independent loads per thread); for s < kTile the tile is first transposed
 // through shared memory. Its outputs go to shared memory; sub-stage 2 (stride 1) reads
 // elements Q2 pp + j there and writes its outputs pp + Q1 r straight to global memory, again
-// kTile-contiguous per element. The block has kTile Q1 threads, one butterfly per thread and
-// sub-stage. Twiddles are deferred as described above; the pass twiddle exponent p s of a thread's
-// sequence is recomputed per thread.
+// kTile-contiguous per element. The block has kTile Q2 threads (PassShape). Twiddles are deferred
+// as described above; the pass twiddle exponent p s of a thread's sequence is recomputed per
+// thread.
 // Thread shape of a pass of radix 2^LOGR = Q1 Q2 (L1 = ceil(LOGR / 2)). Sub-stage 1 has kTile Q2
-// butterflies of radix Q1, sub-stage 2 kTile Q1 of radix Q2. FP64 passes (bound by the FP64
-// pipe) take a thread per butterfly of sub-stage 2, so for odd LOGR half the threads wait out
-// sub-stage 1; double-float and FP32 passes (bound by issue and memory) take a thread per
-// butterfly of sub-stage 1 and B2 = Q1 / Q2 butterflies of sub-stage 2 each, keeping every warp busy.
-template <int LOGR, class C>
+// butterflies of radix Q1, sub-stage 2 kTile Q1 of radix Q2. A thread takes one butterfly of
+// sub-stage 1 and B2 = Q1 / Q2 (1 or 2) of sub-stage 2, so no warp waits out a sub-stage (with a
+// thread per butterfly of sub-stage 2, half the warps of an odd-LOGR pass idled through sub-stage 1).
+template <int LOGR>
 struct PassShape {
   static constexpr int L1 = (LOGR + 1) / 2, L2 = LOGR - L1;
   static constexpr int Q1 = 1 << L1, Q2 = 1 << L2;
-  static constexpr bool BAL = !std::is_same<C, double2>::value;
-  static constexpr int NT = BAL ? kTile * Q2 : kTile * Q1;  // threads
-  static constexpr int NB1 = kTile * Q2;                    // butterflies of sub-stage 1 (<= NT)
-  static constexpr int B2 = kTile * Q1 / NT;                // butterflies of sub-stage 2 per thread
+  static constexpr int NT = kTile * Q2;       // threads = butterflies of sub-stage 1
+  static constexpr int B2 = kTile * Q1 / NT;  // butterflies of sub-stage 2 per thread
 };
 
 template <int LOGR, bool INV, class C>
@@ -230,12 +227,12 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_pass_reg(const C* __restric
                                                               int logF, int logS, const C* __restrict__ tw,
                                                               int logFmax, const C* __restrict__ hmul,
                                                               int64_t nseg, FftGen gen) {
-  typedef PassShape<LOGR, C> PS;
+  typedef PassShape<LOGR> PS;
   constexpr int R = 1 << LOGR;
   constexpr int L1 = PS::L1, L2 = PS::L2, Q1 = PS::Q1, Q2 = PS::Q2;
-  constexpr int NT = PS::NT, NB1 = PS::NB1, B2 = PS::B2;
+  constexpr int NT = PS::NT, B2 = PS::B2;
   constexpr int PER = R * kTile / NT;                // points per thread in the transposing fill
-  static_assert(NT <= kFftThreads && NB1 <= NT && B2 * NT == kTile * Q1, "thread shape");
+  static_assert(NT <= kFftThreads && B2 * NT == kTile * Q1, "thread shape");
   extern __shared__ __align__(16) unsigned char sm_raw[];
   C* v = reinterpret_cast<C*>(sm_raw);
   const int logFR = logF - LOGR;
@@ -253,30 +250,27 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_pass_reg(const C* __restric
   const uint32_t fmask = (1u << logFmax) - 1u;
   const uint32_t i = threadIdx.x & (kTile - 1), bf = threadIdx.x / kTile;
   const uint32_t pti = ((pi0 + i) >> logS) << logS;  // p * s of this thread's sequence
-  const bool act1 = threadIdx.x < NB1;
   C a[Q1];
   if (s >= kTile) {
-    if (act1) {
-      const uint32_t p = pi0 >> logS, q0 = pi0 & (s - 1);
-      const uint32_t off = q0 + ((p << LOGR) << logS) + i;
-      if (gen.coef) {
-        // first pass of a forward transform with generated input (p = 0)
-        const GenCol<C> gc = gen_col<C>(gen, col);
+    const uint32_t p = pi0 >> logS, q0 = pi0 & (s - 1);
+    const uint32_t off = q0 + ((p << LOGR) << logS) + i;
+    if (gen.coef) {
+      // first pass of a forward transform with generated input (p = 0)
+      const GenCol<C> gc = gen_col<C>(gen, col);
 #pragma unroll
-        for (int j = 0; j < Q1; ++j) {
-          const uint32_t t = off + ((bf + Q2 * j) << logS);
-          a[j] = (int64_t)t < gc.lim ? coef_times(gen.coef, gc.cb + t, ldgc(gc.v + t))
-                                     : mkc((typename RealOf<C>::type)0, (typename RealOf<C>::type)0);
-        }
-      } else {
-        const C* xb = x + off;
-#pragma unroll
-        for (int j = 0; j < Q1; ++j) a[j] = xb[(bf + Q2 * j) << logS];
+      for (int j = 0; j < Q1; ++j) {
+        const uint32_t t = off + ((bf + Q2 * j) << logS);
+        a[j] = (int64_t)t < gc.lim ? coef_times(gen.coef, gc.cb + t, ldgc(gc.v + t))
+                                   : mkc((typename RealOf<C>::type)0, (typename RealOf<C>::type)0);
       }
-      if (hc) {
+    } else {
+      const C* xb = x + off;
 #pragma unroll
-        for (int j = 0; j < Q1; ++j) a[j] = cmul(a[j], ldgc(&hc[off + ((bf + Q2 * j) << logS)]));
-      }
+      for (int j = 0; j < Q1; ++j) a[j] = xb[(bf + Q2 * j) << logS];
+    }
+    if (hc) {
+#pragma unroll
+      for (int j = 0; j < Q1; ++j) a[j] = cmul(a[j], ldgc(&hc[off + ((bf + Q2 * j) << logS)]));
     }
   } else {
     const C* xb = x + (pi0 << LOGR);
@@ -292,19 +286,15 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_pass_reg(const C* __restric
       v[j * kRow + ((pl << logS) + q)] = t[u];
     }
     __syncthreads();
-    if (act1) {
 #pragma unroll
-      for (int j = 0; j < Q1; ++j) a[j] = v[(bf + Q2 * j) * kRow + i];
-    }
+    for (int j = 0; j < Q1; ++j) a[j] = v[(bf + Q2 * j) * kRow + i];
     __syncthreads();  // sub-stage 1 overwrites the tile in place
   }
-  if (act1) {
-    // the first pass (p = 0, pti = 0) has only the constant twiddles of reg_dft_unit here
-    if (logS == logF - LOGR) reg_dft_unit<L1, INV>(a);
-    else reg_dft<L1, INV>(a, (pti << L2) << fsh, tw, logFmax, fmask);
+  // the first pass (p = 0, pti = 0) has only the constant twiddles of reg_dft_unit here
+  if (logS == logF - LOGR) reg_dft_unit<L1, INV>(a);
+  else reg_dft<L1, INV>(a, (pti << L2) << fsh, tw, logFmax, fmask);
 #pragma unroll
-    for (int r = 0; r < Q1; ++r) v[(bf + Q2 * r) * kRow + i] = a[r];
-  }
+  for (int r = 0; r < Q1; ++r) v[(bf + Q2 * r) * kRow + i] = a[r];
   __syncthreads();
 #pragma unroll
   for (int u = 0; u < B2; ++u) {
@@ -548,7 +538,7 @@ void launch_pass(const C* src, C* dst, int logF, int logS, int ncols, const C* t
   const int64_t pairs = ((int64_t)ncols << logF) >> LOGR;
   const int64_t grid = pairs / kTile;
   // one buffer (the sub-stages work in place)
-  constexpr int threads = PassShape<LOGR, C>::NT;
+  constexpr int threads = PassShape<LOGR>::NT;
   const size_t smem = (size_t)R * kRow * sizeof(C);
   static bool configured = false;
   if (!configured) {

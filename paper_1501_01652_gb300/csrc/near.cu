@@ -327,7 +327,7 @@ __device__ __forceinline__ void tc_digit(float (&acc)[kTcDiag][2][4], const unsi
 // fragment) and loads the coefficient digits of columns 2tq, 2tq + 1, 2tq + 8, 2tq + 9 for
 // vectors gq and gq + 8 (its B fragments). J comes from the fixed-point table (FP64 and
 // double-float plans alike: it is exact to the digit grid either way).
-__global__ void __launch_bounds__(64, 6) k_near_tc(const NearItem* __restrict__ items, const int64_t* __restrict__ nend,
+__global__ void __launch_bounds__(64, 7) k_near_tc(const NearItem* __restrict__ items, const int64_t* __restrict__ nend,
                                                int64_t N, double* partial, int nrhs, const __half* __restrict__ Cd,
                                                const int* __restrict__ Ce, int64_t Npad, double* f, int64_t ldf,
                                                const double* __restrict__ r_true, const double* __restrict__ om_true,
