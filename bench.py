@@ -34,9 +34,9 @@ HBM_FALLBACK_GBS = 6800.0          # used only when MEASURED_PEAKS.json is absen
 FP64_MEASURED_GFLOPS = 1004.0      # DFMA microbenchmark on this part (2 x 502 G instructions/s)
 # DRAM bytes per algorithmic byte of an FP64 FFT pass launch, from an ncu capture of two
 # radix-128 inverse passes of 2^24 points (k_fft_pass_reg<7, 1, double2>, 8192 CTAs; the first
-# with the chirp-spectrum product folded into its loads): 310.2 + 230.8 MB and 269.7 + 222.5 MB
+# with the chirp-spectrum product folded into its loads): 310.7 + 226.0 MB and 270.2 + 217.5 MB
 # of DRAM reads + writes against 536.9 MB algorithmic each.
-FFT_TRAFFIC_RATIO = (310.218 + 230.828 + 269.726 + 222.462) / (2 * 536.871)
+FFT_TRAFFIC_RATIO = (310.663 + 225.980 + 270.203 + 217.533) / (2 * 536.871)
 # The double-float transforms are bound by the FP32 pipe: 152 SMs x 128 lanes x 2.07 GHz =
 # 40.3 T instructions/s. Their radix-2 butterfly (two double-float dot products of 16 FP32
 # instructions each, four sums of 8) takes 64 FP32 instructions for the 10 flops of the
