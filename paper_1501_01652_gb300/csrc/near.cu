@@ -192,9 +192,12 @@ __global__ void __launch_bounds__(256) k_near_df(const NearItem* __restrict__ it
 }
 
 // Rows whose prefix spans several tiles: the partial sums of row k and vector rr are the
-// npieces consecutive values at slot0 nrhs + rr npieces. A warp per row and 16 vectors at a
-// time; lane l adds, in order, the pieces l >> 4, (l >> 4) + 2, ... of vector l & 15 and one
-// shuffle adds the two halves, so the result does not depend on scheduling.
+// npieces consecutive values at slot0 nrhs + rr npieces. A warp per row. Rows of up to 32
+// pieces take 16 vectors at a time: lane l adds, in order, the pieces l >> 4, (l >> 4) + 2, ...
+// of vector l & 15 and one shuffle adds the two halves. Longer rows (the first rows, up to
+// N / 512 pieces) take one vector at a time: lane l adds the pieces l, l + 32, ... and the lanes
+// combine in a fixed shuffle tree, which keeps the rounding of these long sums at that of
+// 64-term sums. Either way the result does not depend on scheduling.
 // FP64 near field with the per-vector products on the tensor cores (FP64 plans, 8 to 16 vectors):
 // split-digit products (the Ozaki scheme). J (|J| <= 1) and, per 512-column chunk and vector,
 // the coefficients scaled by 2^-e (2^e bounds the chunk's largest |c|) are rounded to the
@@ -423,12 +426,23 @@ __global__ void k_near_combine(const NearRow* __restrict__ rows, int64_t nrows, 
   const int lane = threadIdx.x & 31, g = lane & 15, h = lane >> 4;
   if (w >= nrows) return;
   const NearRow row = rows[w];
+  if (row.npieces > 32) {
+    for (int rr = 0; rr < nrhs; ++rr) {
+      const R* p = partial + row.slot0 * nrhs + (int64_t)rr * row.npieces;
+      R s = 0;
+      for (int j = lane; j < row.npieces; j += 32) s += p[j];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+      if (lane == 0) f[(int64_t)rr * ldf + row.k - 1] = (double)s;
+    }
+    return;
+  }
   for (int r0 = 0; r0 < nrhs; r0 += 16) {
     const int rr = r0 + g;
     R s = 0;
     if (rr < nrhs) {
       const R* p = partial + row.slot0 * nrhs + (int64_t)rr * row.npieces;
-      for (int64_t j = h; j < row.npieces; j += 2) s += p[j];
+      for (int j = h; j < row.npieces; j += 2) s += p[j];
     }
     s += __shfl_down_sync(0xffffffffu, s, 16);
     if (h == 0 && rr < nrhs) f[(int64_t)rr * ldf + row.k - 1] = (double)s;
