@@ -312,8 +312,9 @@ typedef struct {
   int precision;      /* precision every plan is built with: HANKEL_PREC_AUTO (chosen per eps as for a
                          plan: FP64, DF64 transforms or FP32 stages) or HANKEL_PREC_FP64 */
   int pack_requests;  /* 1: pack waiting requests of one plan into one execution; 0: one request each */
-  int batch_window_us; /* a plan's batch with fewer than max_batch vectors waits until its oldest request
-                          is this old, to take requests submitted together (default 200; 0: none) */
+  int batch_window_us; /* a plan's batch with fewer than max_batch vectors waits until no request of the
+                          plan has arrived for this long (so a burst of submissions stays one batch),
+                          or until its oldest request has waited ten times this (default 200; 0: none) */
 } hankel_server_options;
 
 /* Statistics since the server was created. */

@@ -69,7 +69,8 @@ struct Slot {
   double* f_pin = nullptr;
   double* c_dev = nullptr;
   double* f_dev = nullptr;
-  size_t cap = 0;  // doubles in each buffer
+  size_t cap = 0;      // doubles in each device buffer
+  size_t pin_cap = 0;  // doubles in each staging buffer (allocated only for pageable requests)
   bool busy = false;
   std::vector<Item> items;
   Key key;
@@ -117,26 +118,46 @@ void free_slot_buffers(Slot& sl) {
   if (sl.c_dev) cudaFree(sl.c_dev);
   if (sl.f_dev) cudaFree(sl.f_dev);
   sl.c_pin = sl.f_pin = sl.c_dev = sl.f_dev = nullptr;
-  sl.cap = 0;
+  sl.cap = sl.pin_cap = 0;
 }
 
-int ensure_slot_capacity(hankel_server_s* s, int i, size_t need) {
+// Device buffers of slot i for need doubles each (growing drops the slot's graphs, which hold
+// the buffers' addresses) and, with staging, page-locked staging buffers of the same size.
+// The slot is idle, so nothing in flight uses the buffers being replaced.
+int ensure_slot_capacity(hankel_server_s* s, int i, size_t need, bool staging) {
   Slot& sl = s->slots[i];
-  if (sl.cap >= need) return HANKEL_OK;
-  drop_slot_graphs(s, i);
-  s->slot_bytes -= 2 * sl.cap * sizeof(double);
-  free_slot_buffers(sl);
-  size_t cap = std::max(need, size_t(1) << 16);
-  if (cudaMallocHost((void**)&sl.c_pin, cap * sizeof(double)) != cudaSuccess ||
-      cudaMallocHost((void**)&sl.f_pin, cap * sizeof(double)) != cudaSuccess ||
-      cudaMalloc((void**)&sl.c_dev, cap * sizeof(double)) != cudaSuccess ||
-      cudaMalloc((void**)&sl.f_dev, cap * sizeof(double)) != cudaSuccess) {
-    cudaGetLastError();
-    free_slot_buffers(sl);
-    return HANKEL_ENOMEM;
+  const size_t cap = std::max(need, size_t(1) << 16);
+  if (sl.cap < need) {
+    drop_slot_graphs(s, i);
+    s->slot_bytes -= 2 * sl.cap * sizeof(double);
+    if (sl.c_dev) cudaFree(sl.c_dev);
+    if (sl.f_dev) cudaFree(sl.f_dev);
+    sl.c_dev = sl.f_dev = nullptr;
+    sl.cap = 0;
+    if (cudaMalloc((void**)&sl.c_dev, cap * sizeof(double)) != cudaSuccess ||
+        cudaMalloc((void**)&sl.f_dev, cap * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      free_slot_buffers(sl);
+      return HANKEL_ENOMEM;
+    }
+    sl.cap = cap;
+    s->slot_bytes += 2 * cap * sizeof(double);
   }
-  sl.cap = cap;
-  s->slot_bytes += 2 * cap * sizeof(double);
+  if (staging && sl.pin_cap < need) {
+    if (sl.c_pin) cudaFreeHost(sl.c_pin);
+    if (sl.f_pin) cudaFreeHost(sl.f_pin);
+    sl.c_pin = sl.f_pin = nullptr;
+    sl.pin_cap = 0;
+    if (cudaMallocHost((void**)&sl.c_pin, cap * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost((void**)&sl.f_pin, cap * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      s->slot_bytes -= 2 * sl.cap * sizeof(double);
+      drop_slot_graphs(s, i);
+      free_slot_buffers(sl);
+      return HANKEL_ENOMEM;
+    }
+    sl.pin_cap = cap;
+  }
   return HANKEL_OK;
 }
 
@@ -297,7 +318,8 @@ bool dispatch(hankel_server_s* s, int i) {
       return it != s->plans.end() && it->second.busy;
     };
     // the oldest queued request whose plan is idle and whose batch is ready: full, packing off,
-    // or its oldest request has waited the batch window
+    // no request of the plan arrived within the batch window (a burst of submissions stays one
+    // batch), or its oldest request has waited ten windows
     const Clock::time_point now = Clock::now();
     const auto window = std::chrono::microseconds(std::max(0, s->opt.batch_window_us));
     std::vector<Key> seen;
@@ -306,11 +328,15 @@ bool dispatch(hankel_server_s* s, int i) {
       const Request& r0 = s->reqs[*q];
       if (busy(r0.key) || std::find(seen.begin(), seen.end(), r0.key) != seen.end()) continue;
       seen.push_back(r0.key);
-      if (!s->opt.pack_requests || now - r0.t_submit >= window) break;
+      if (!s->opt.pack_requests) break;
       int queued = 0;
+      Clock::time_point newest = r0.t_submit;
       for (int64_t t : s->queue)
-        if (s->reqs[t].key == r0.key) queued += s->reqs[t].nrhs;
-      if (queued >= s->opt.max_batch) break;
+        if (s->reqs[t].key == r0.key) {
+          queued += s->reqs[t].nrhs;
+          newest = std::max(newest, s->reqs[t].t_submit);
+        }
+      if (queued >= s->opt.max_batch || now - newest >= window || now - r0.t_submit >= 10 * window) break;
     }
     if (q == s->queue.end()) return false;
     key = s->reqs[*q].key;
@@ -328,7 +354,9 @@ bool dispatch(hankel_server_s* s, int i) {
   PlanEntry* pe = nullptr;
   int st = get_plan(s, key, &pe);
   const int64_t N = std::get<2>(key);
-  if (st == HANKEL_OK) st = ensure_slot_capacity(s, i, (size_t)N * nrhs);
+  bool staging = false;
+  for (const Item& it : batch) staging = staging || !it.c_pinned || !it.f_pinned;
+  if (st == HANKEL_OK) st = ensure_slot_capacity(s, i, (size_t)N * nrhs, staging);
   if (st != HANKEL_OK) {
     finish(s, batch, st);
     return true;

@@ -122,3 +122,28 @@ def test_page_locked_requests_match_pageable():
     srv.wait(t3)
     assert np.array_equal(f1, f2) and np.array_equal(f2, f3) and np.array_equal(f3, fpin.numpy())
     srv.close()
+
+
+def test_burst_of_submissions_stays_one_batch():
+    # a partial batch leaves once no request of its plan has arrived for batch_window_us: five
+    # requests 1.5 ms apart under a 5 ms window form one batch (timing from their oldest request
+    # would have dispatched the first four alone)
+    import time
+
+    N = 4096
+    cs = [coefficients("normal", N, 1, 300 + i) for i in range(5)]
+    srv = hk.Server(streams=2, max_batch=16, batch_window_us=5000)
+    t, _ = srv.submit("dht", 0, N, 1e-8, cs[0])  # build the plan outside the measured burst
+    srv.wait(t)
+    b0 = srv.stats()["batches"]
+    tickets = []
+    for c in cs:
+        tickets.append(srv.submit("dht", 0, N, 1e-8, c))
+        time.sleep(0.0015)
+    for tk, f in tickets:
+        srv.wait(tk)
+    assert srv.stats()["batches"] - b0 == 1
+    ref = _alone("dht", 0, N, 1e-8, np.concatenate(cs))
+    for i, (_, f) in enumerate(tickets):
+        assert np.all(np.abs(f - ref[i]) <= 10 * 1e-8 * np.abs(cs[i]).sum())
+    srv.close()
