@@ -20,6 +20,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -71,6 +72,8 @@ def parse_args():
     ap.add_argument("--mix-nmin", type=int, default=10)
     ap.add_argument("--mix-nmax", type=int, default=16)
     ap.add_argument("--mix-vmax", type=int, default=64)
+    ap.add_argument("--clocks-csv", default=None,
+                    help="keep the nvidia-smi samples of the timed region in this file (default: a temporary file)")
     return ap.parse_args()
 
 
@@ -84,14 +87,19 @@ def dist_env():
 class ClockSampler:
     """Samples SM clocks and throttle reasons with nvidia-smi while the timed region runs."""
 
-    def __init__(self, index):
+    def __init__(self, index, path=None):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "bench_clocks_%d.csv" % index)
+        self.keep = path is not None
+        if path is None:
+            fd, path = tempfile.mkstemp(prefix="bench_clocks_%d_" % index, suffix=".csv")
+            os.close(fd)
+        self.path = path
 
     def __enter__(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            if os.path.dirname(self.path):
+                os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + CLOCK_FIELDS,
                                           "--format=csv,noheader,nounits", "-lms", "200"],
@@ -126,6 +134,8 @@ class ClockSampler:
             for name, val in zip(names, parts[5:9]):
                 if val.lower() == "active":
                     reasons.add(name)
+        if not self.keep:
+            os.remove(self.path)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
                 "reasons": sorted(reasons), "samples": len(sm)}
 
@@ -357,7 +367,7 @@ def run_ours(args):
     fs = [torch.empty((B, N), dtype=torch.float64, device=dev) for _ in plans]
     if world > 1:
         torch.distributed.barrier()
-    with ClockSampler(local) as clocks:
+    with ClockSampler(local, args.clocks_csv) as clocks:
         wall0 = time.perf_counter()
         step_ms, plan_ms, _ = timed_steps(plans, cB, fs, stream, args.steps, args.warmup, flush, False)
         wall = time.perf_counter() - wall0
