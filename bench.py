@@ -295,34 +295,38 @@ def pinned_like(a):
     return out
 
 
-def serve_stream(hk, server_kw, requests, rate, seed):
+def serve_stream(hk, server_kw, requests, rate, seed, rounds=1):
     """Feed `requests` [(eps, c)] to a server with Poisson arrivals at `rate` per second
-    (rate <= 0: all at once). Returns (coefficients/s over the makespan, latencies in ms)."""
+    (rate <= 0: all at once), `rounds` times. Returns (coefficients/s over the summed makespans,
+    latencies in ms of every request)."""
     srv = hk.Server(**server_kw)
-    # warm the plan cache and, with graphs, the captured launch sequences
     outs = [pinned_like(c) for _, c in requests]
-    # warm-up (untimed): build the plans and, with graphs, capture the batch sizes of an
-    # all-at-once arrival and of single requests
-    warm = [srv.submit("dht", 0, c.shape[-1], eps, c, f)[0] for (eps, c), f in zip(requests, outs)]
-    for t in warm:
-        srv.wait(t)
+    # warm-up (untimed): two all-at-once rounds build the plans and (a plan's first run is not
+    # captured) capture the graphs of the batch sizes an all-at-once arrival forms; then single
+    # requests for the sizes of spread-out arrivals
+    for _ in range(2):
+        warm = [srv.submit("dht", 0, c.shape[-1], eps, c, f)[0] for (eps, c), f in zip(requests, outs)]
+        for t in warm:
+            srv.wait(t)
     for _ in range(2):
         for (eps, c), f in zip(requests[:2], outs):
             t, _ = srv.submit("dht", 0, c.shape[-1], eps, c, f)
             srv.wait(t)
     rng = np.random.default_rng(seed)
-    gaps = rng.exponential(1.0 / rate, size=len(requests)) if rate > 0 else np.zeros(len(requests))
-    t0 = time.perf_counter()
-    due = t0
-    tickets = []
-    for (eps, c), gap in zip(requests, gaps):
-        due += gap
-        while time.perf_counter() < due:
-            time.sleep(min(0.001, max(0.0, due - time.perf_counter())))
-        tickets.append(srv.submit("dht", 0, c.shape[-1], eps, c, outs[len(tickets)])[0])
-    lat = [srv.wait(t) for t in tickets]
-    makespan = time.perf_counter() - t0
-    coeffs = sum(c.size for _, c in requests)
+    lat, makespan = [], 0.0
+    for _ in range(rounds):
+        gaps = rng.exponential(1.0 / rate, size=len(requests)) if rate > 0 else np.zeros(len(requests))
+        t0 = time.perf_counter()
+        due = t0
+        tickets = []
+        for (eps, c), gap in zip(requests, gaps):
+            due += gap
+            while time.perf_counter() < due:
+                time.sleep(min(0.001, max(0.0, due - time.perf_counter())))
+            tickets.append(srv.submit("dht", 0, c.shape[-1], eps, c, outs[len(tickets)])[0])
+        lat += [srv.wait(t) for t in tickets]
+        makespan += time.perf_counter() - t0
+    coeffs = rounds * sum(c.size for _, c in requests)
     srv.close()
     return coeffs / makespan, lat
 
@@ -452,8 +456,8 @@ def run_ours(args):
         served_e2e = plain_e2e = served_cps_p = plain_cps_p = rate = None
         served_sat_lat = plain_sat_lat = served_lat = plain_lat = []
     else:
-        served_e2e, served_sat_lat = serve_stream(hk, served_kw, reqs, 0.0, 1)
-        plain_e2e, plain_sat_lat = serve_stream(hk, plain_kw, reqs, 0.0, 1)
+        served_e2e, served_sat_lat = serve_stream(hk, served_kw, reqs, 0.0, 1, rounds=args.steps)
+        plain_e2e, plain_sat_lat = serve_stream(hk, plain_kw, reqs, 0.0, 1, rounds=args.steps)
         rate = args.rate if args.rate > 0 else 0.7 * plain_e2e / N  # 70 % of the plain form's capacity
         served_cps_p, served_lat = serve_stream(hk, served_kw, reqs, rate, 2)
         plain_cps_p, plain_lat = serve_stream(hk, plain_kw, reqs, rate, 2)
@@ -484,7 +488,8 @@ def run_ours(args):
         "e2e": {"value": served_e2e, "unit": "coeffs/s", "h2d_bytes_per_step": coeffs_per_step * 8,
                 "d2h_bytes_per_step": coeffs_per_step * 8,
                 "form": "hankel_server, %d single-vector requests (%d per eps) submitted at once, page-locked host "
-                        "arrays (inputs and outputs)" % (len(reqs), len(reqs) // len(eps_list)),
+                        "arrays (inputs and outputs); %d such rounds after 2 untimed ones"
+                        % (len(reqs), len(reqs) // len(eps_list), args.steps),
                 "plain_value": plain_e2e},
         "latency_ms": {"rate_per_s": rate, "requests": len(reqs),
                        "served": {"p50": pct(served_lat, 50), "p99": pct(served_lat, 99),
