@@ -182,7 +182,11 @@ int hankel_plan_ex(hankel_plan_t* out, const hankel_options* opts);
 int hankel_exec(hankel_plan_t p, const double* c, double* f, void* stream);
 
 /* Batched form: for r < nrhs, f[r*ldf + k-1] = sum_n c[r*ldc + n-1] J_nu(r_k omega_n).
- * Device arrays; ldc, ldf >= N; 1 <= nrhs <= max_nrhs of the plan. Asynchronous. */
+ * Device arrays; ldc, ldf >= N; 1 <= nrhs <= max_nrhs of the plan. Asynchronous.
+ * FP64 and DF64 plans built with max_nrhs >= 8 sum the near field of calls with nrhs >= 8 as
+ * exact split-digit products on the tensor cores (J and each 512-column chunk of c rounded to
+ * 2^-53 and 2^-54 of their scales): the results differ from a call with fewer vectors in the
+ * last bits, and are at least as close to the exact sums (checked against the oracle). */
 int hankel_exec_batched(hankel_plan_t p, const double* c, int64_t ldc, double* f, int64_t ldf,
                         int nrhs, void* stream);
 
