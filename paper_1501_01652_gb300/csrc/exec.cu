@@ -146,7 +146,7 @@ struct DevicePlan {
   void* tcd = nullptr;   // FP64 plans, 8+ vectors: coefficient digits of the tensor-core near field
   int* tce = nullptr;    // and their per-chunk exponents
   int64_t tc_npad = 0;
-  long long* jtabq = nullptr;  // the J table in Q62 fixed point, for the tensor-core near field
+  long long* jtabq = nullptr;  // the J table in Q62 fixed point (FP64 and DF64 plans)
   size_t bytes = 0;
   std::vector<void*> allocs;
   // stage statistics (hankel_plan_set_timing / hankel_plan_stage_stats)
@@ -324,8 +324,8 @@ int dev_plan_create(hankel_plan_s* p) {
     HK_TRY(dalloc(d, &q, (size_t)8 * 16 * d->tc_npad));
     d->tcd = q;
     HK_TRY(dalloc(d, &d->tce, (size_t)(d->tc_npad / 512) * 16));
-    HK_TRY(upload(d, &d->jtabq, hp.jtabq.data(), hp.jtabq.size()));
   }
+  if (!d->fp32) HK_TRY(upload(d, &d->jtabq, hp.jtabq.data(), hp.jtabq.size()));
   if (d->any_t[kTermFP32]) HK_TRY(dalloc(d, &d->cf, (size_t)hp.opt.max_nrhs * N));
 
 
@@ -712,10 +712,11 @@ int run_all(DevicePlan* d, const HostPlan& hp, const double* c, int64_t ldc, dou
                      ldf, d->rdf, d->omdf, d->jtabdf, hp.jt_n, hp.jt_deg, st);
     else if (d->fp32)
       launch_near<float>(d->items, d->nitems, d->mrows, d->nmrows, d->nend, d->hpN, (float*)partial, nrhs, c, ldc,
-                         d->cf, f, ldf, d->rf, d->omf, d->jtabf, hp.jt_n, hp.jt_deg, st);
+                         d->cf, f, ldf, d->rf, d->omf, d->jtabf, nullptr, hp.jt_n, hp.jt_deg, st);
     else
       launch_near<double>(d->items, d->nitems, d->mrows, d->nmrows, d->nend, d->hpN, (double*)partial, nrhs, c, ldc,
-                          nullptr, f, ldf, d->nodes.r_true, d->nodes.om_true, d->jtab, hp.jt_n, hp.jt_deg, st);
+                          nullptr, f, ldf, d->nodes.r_true, d->nodes.om_true, d->jtab, d->jtabq, hp.jt_n,
+                          hp.jt_deg, st);
     HK_LAUNCHED();
     sc.done(d->nmrows > 0 ? 2 : 1, 0.0, (double)hp.near_count * nrhs);
   }

@@ -159,9 +159,12 @@ void launch_out(const OutArgs& a, cudaStream_t st);
 // rf, omf, jtabf single-precision copies); sums are accumulated in R, outputs written as double.
 template <class R>
 // cf: optional coefficients already rounded to FP32 ([nrhs][N]); used instead of c when given.
+// jtabq: the J table in Q62 fixed point; FP64 near fields (R = double) evaluate J from it on
+// the integer pipe, FP32 ones (R = float, jtabq unused) from jtab.
 void launch_near(const NearItem* items, int64_t nitems, const NearRow* mrows, int64_t nmrows, const int64_t* nend,
                  int64_t N, R* partial, int nrhs, const double* c, int64_t ldc, const float* cf, double* f,
-                 int64_t ldf, const R* r, const R* om, const R* jtab, int64_t jt_n, int deg, cudaStream_t st);
+                 int64_t ldf, const R* r, const R* om, const R* jtab, const long long* jtabq, int64_t jt_n, int deg,
+                 cudaStream_t st);
 
 // Near field with the per-vector products as exact split-digit fp16 tensor-core products
 // (8 <= nrhs <= 16), FP64 and double-float plans: z = r_n om_n in FP64, J from the Q62

@@ -34,30 +34,43 @@ __device__ __forceinline__ R table_j(const R* __restrict__ jtab, int64_t jt_n, i
   return v;
 }
 
-// FP64: the interval i = floor(z 2^kJTabLog) and its left end come from the bits of z (z >= 0)
-// with integer operations, so the FP64 pipe only computes d = z - left - 1/(2 kJTabSub) and
-// the polynomial.
-template <>
-__device__ __forceinline__ double table_j<double>(const double* __restrict__ jtab, int64_t jt_n, int deg, double z) {
-  const long long bits = __double_as_longlong(z);
-  const int sh = 52 + 1023 - kJTabLog - (int)((bits >> 52) & 0x7ff);  // mantissa bits below 1/kJTabSub
-  long long i = 0;
-  double left = 0.0;  // z < 1/kJTabSub (and z = 0)
+// J_nu(z) from the Q62 table, in two parts. q62_interval finds the interval i = floor(z kJTabSub)
+// and U = (z kJTabSub - i - 1/2) 2^64 from the bits of z (z >= 0) by integer operations; the
+// caller runs Horner's rule in Q62 with the signed high halves of 64 x 64-bit products (each
+// step truncating by less than 2^-62) and rounds to J 2^53. Every operation but z = r omega is
+// on the integer pipe.
+__device__ __forceinline__ long long q62_interval(int64_t jt_n, double z, long long& U) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(z);
+  const int E = (int)(bits >> 52) & 0x7ff;
+  const unsigned long long M = (bits & 0xfffffffffffffULL) | (E ? (1ULL << 52) : 0ULL);
+  const int sh = 52 + 1023 - kJTabLog - E;  // mantissa bits below 1/kJTabSub
+  long long i;
+  unsigned long long F;  // the fraction z kJTabSub - i, times 2^64
   if (sh <= 0) {
-    i = jt_n;  // z >= 2^(52 - kJTabLog): beyond any table
+    i = jt_n;
+    F = 0;
   } else if (sh <= 52) {
-    i = ((bits & 0xfffffffffffffLL) | (1LL << 52)) >> sh;
-    left = __longlong_as_double(bits & ~((1LL << sh) - 1));
+    i = (long long)(M >> sh);
+    F = M << (64 - sh);
+  } else {
+    i = 0;
+    F = sh - 53 < 64 ? (M << 11) >> (sh - 53) : 0ULL;
   }
-  if (i >= jt_n) {
+  if (i >= jt_n) {  // beyond the table (the near field stays below zmax < jt_n / kJTabSub)
     i = jt_n - 1;
-    left = (double)i * (1.0 / kJTabSub);
+    F = ~0ULL;
   }
-  const double d = (z - left) - 0.5 / kJTabSub;
-  const double* t = jtab + i * (deg + 1);
-  double v = __ldg(&t[deg]);
-  for (int j = deg - 1; j >= 0; --j) v = fma(v, d, __ldg(&t[j]));
-  return v;
+  U = (long long)(F ^ (1ULL << 63));
+  return i;
+}
+
+// J_nu(z) in FP64 from the Q62 table: Horner's rule on the integer pipe, one rounding to double.
+__device__ __forceinline__ double q62_j(const long long* __restrict__ jq, int64_t jt_n, int deg, double z) {
+  long long U;
+  const long long* t = jq + q62_interval(jt_n, z, U) * (deg + 1);
+  long long v = __ldg(&t[deg]);
+  for (int j = deg - 1; j >= 0; --j) v = __mul64hi(v, U) + __ldg(&t[j]);
+  return __ll2double_rn(v) * 0x1p-62;
 }
 
 // Warp per tile, lane per row: every lane walks the same columns n (so the loads of omega_n and
@@ -68,7 +81,8 @@ __global__ void __launch_bounds__(256) k_near(const NearItem* __restrict__ items
                                               const int64_t* __restrict__ nend, int64_t N, R* partial, int nrhs,
                                               const CT* __restrict__ c, int64_t ldc, double* f, int64_t ldf,
                                               const R* __restrict__ r_true, const R* __restrict__ om_true,
-                                              const R* __restrict__ jtab, int64_t jt_n, int deg) {
+                                              const R* __restrict__ jtab, const long long* __restrict__ jq,
+                                              int64_t jt_n, int deg) {
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= nitems) return;
@@ -82,7 +96,9 @@ __global__ void __launch_bounds__(256) k_near(const NearItem* __restrict__ items
 #pragma unroll
     for (int g = 0; g < G; ++g) acc[g] = 0;
     for (int64_t n = it.n0; n <= nhi; ++n) {
-      const R J = table_j(jtab, jt_n, deg, r * __ldg(&om_true[n - 1]));
+      R J;
+      if constexpr (std::is_same<R, double>::value) J = q62_j(jq, jt_n, deg, r * __ldg(&om_true[n - 1]));
+      else J = table_j(jtab, jt_n, deg, r * __ldg(&om_true[n - 1]));
 #pragma unroll
       for (int g = 0; g < G; ++g)
         if (r0 + g < nrhs) acc[g] = fmar((R)__ldg(&c[(int64_t)(r0 + g) * ldc + n - 1]), J, acc[g]);
@@ -225,36 +241,6 @@ __device__ __forceinline__ unsigned digit_pair(unsigned long long Yl, unsigned l
   const unsigned w = 0x64006400u | el | (eh << 16);
   const __half2 v = __hsub2(*reinterpret_cast<const __half2*>(&w), __half2(__float2half(1088.0f), __float2half(1088.0f)));
   return *reinterpret_cast<const unsigned*>(&v);
-}
-
-// J_nu(z) from the Q62 table, in two parts. q62_interval finds the interval i = floor(z kJTabSub)
-// and U = (z kJTabSub - i - 1/2) 2^64 from the bits of z (z >= 0) by integer operations; the
-// caller runs Horner's rule in Q62 with the signed high halves of 64 x 64-bit products (each
-// step truncating by less than 2^-62) and rounds to J 2^53. Every operation but z = r omega is
-// on the integer pipe.
-__device__ __forceinline__ long long q62_interval(int64_t jt_n, double z, long long& U) {
-  const unsigned long long bits = (unsigned long long)__double_as_longlong(z);
-  const int E = (int)(bits >> 52) & 0x7ff;
-  const unsigned long long M = (bits & 0xfffffffffffffULL) | (E ? (1ULL << 52) : 0ULL);
-  const int sh = 52 + 1023 - kJTabLog - E;  // mantissa bits below 1/kJTabSub
-  long long i;
-  unsigned long long F;  // the fraction z kJTabSub - i, times 2^64
-  if (sh <= 0) {
-    i = jt_n;
-    F = 0;
-  } else if (sh <= 52) {
-    i = (long long)(M >> sh);
-    F = M << (64 - sh);
-  } else {
-    i = 0;
-    F = sh - 53 < 64 ? (M << 11) >> (sh - 53) : 0ULL;
-  }
-  if (i >= jt_n) {  // beyond the table (the near field stays below zmax < jt_n / kJTabSub)
-    i = jt_n - 1;
-    F = ~0ULL;
-  }
-  U = (long long)(F ^ (1ULL << 63));
-  return i;
 }
 
 __device__ __forceinline__ void mma_f16(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
@@ -454,28 +440,32 @@ __global__ void k_near_combine(const NearRow* __restrict__ rows, int64_t nrows, 
 template <class R, class CT>
 void launch_near_t(const NearItem* items, int64_t nitems, const int64_t* nend, int64_t N, R* partial, int nrhs,
                    const CT* c, int64_t ldc, double* f, int64_t ldf, const R* r, const R* om, const R* jtab,
-                   int64_t jt_n, int deg, cudaStream_t st) {
+                   const long long* jq, int64_t jt_n, int deg, cudaStream_t st) {
   const int64_t threads = nitems * 32;
   const unsigned grid = (unsigned)((threads + 255) / 256);
   if (nrhs <= 1)
-    k_near<R, 1><<<grid, 256, 0, st>>>(items, nitems, nend, N, partial, nrhs, c, ldc, f, ldf, r, om, jtab, jt_n, deg);
+    k_near<R, 1><<<grid, 256, 0, st>>>(items, nitems, nend, N, partial, nrhs, c, ldc, f, ldf, r, om, jtab, jq, jt_n, deg);
   else if (nrhs <= 2)
-    k_near<R, 2><<<grid, 256, 0, st>>>(items, nitems, nend, N, partial, nrhs, c, ldc, f, ldf, r, om, jtab, jt_n, deg);
+    k_near<R, 2><<<grid, 256, 0, st>>>(items, nitems, nend, N, partial, nrhs, c, ldc, f, ldf, r, om, jtab, jq, jt_n, deg);
   else if (nrhs <= 4)
-    k_near<R, 4><<<grid, 256, 0, st>>>(items, nitems, nend, N, partial, nrhs, c, ldc, f, ldf, r, om, jtab, jt_n, deg);
+    k_near<R, 4><<<grid, 256, 0, st>>>(items, nitems, nend, N, partial, nrhs, c, ldc, f, ldf, r, om, jtab, jq, jt_n, deg);
   else if (nrhs <= 8)
-    k_near<R, 8><<<grid, 256, 0, st>>>(items, nitems, nend, N, partial, nrhs, c, ldc, f, ldf, r, om, jtab, jt_n, deg);
+    k_near<R, 8><<<grid, 256, 0, st>>>(items, nitems, nend, N, partial, nrhs, c, ldc, f, ldf, r, om, jtab, jq, jt_n, deg);
   else
     k_near<R, kMaxRhsGroup><<<grid, 256, 0, st>>>(items, nitems, nend, N, partial, nrhs, c, ldc, f, ldf, r, om, jtab,
-                                                  jt_n, deg);
+                                                  jq, jt_n, deg);
 }
 
 template <class R>
 void launch_near(const NearItem* items, int64_t nitems, const NearRow* mrows, int64_t nmrows, const int64_t* nend,
                  int64_t N, R* partial, int nrhs, const double* c, int64_t ldc, const float* cf, double* f,
-                 int64_t ldf, const R* r, const R* om, const R* jtab, int64_t jt_n, int deg, cudaStream_t st) {
-  if (cf) launch_near_t<R, float>(items, nitems, nend, N, partial, nrhs, cf, N, f, ldf, r, om, jtab, jt_n, deg, st);
-  else launch_near_t<R, double>(items, nitems, nend, N, partial, nrhs, c, ldc, f, ldf, r, om, jtab, jt_n, deg, st);
+                 int64_t ldf, const R* r, const R* om, const R* jtab, const long long* jtabq, int64_t jt_n, int deg,
+                 cudaStream_t st) {
+  if (cf)
+    launch_near_t<R, float>(items, nitems, nend, N, partial, nrhs, cf, N, f, ldf, r, om, jtab, jtabq, jt_n, deg, st);
+  else
+    launch_near_t<R, double>(items, nitems, nend, N, partial, nrhs, c, ldc, f, ldf, r, om, jtab, jtabq, jt_n, deg,
+                             st);
   if (nmrows > 0)
     k_near_combine<R><<<(unsigned)((nmrows * 32 + 255) / 256), 256, 0, st>>>(mrows, nmrows, partial, nrhs, f, ldf);
 }
@@ -517,9 +507,10 @@ void launch_near_tc(const NearItem* items, int64_t nitems, const NearRow* mrows,
 
 template void launch_near<double>(const NearItem*, int64_t, const NearRow*, int64_t, const int64_t*, int64_t,
                                   double*, int, const double*, int64_t, const float*, double*, int64_t,
-                                  const double*, const double*, const double*, int64_t, int, cudaStream_t);
+                                  const double*, const double*, const double*, const long long*, int64_t, int,
+                                  cudaStream_t);
 template void launch_near<float>(const NearItem*, int64_t, const NearRow*, int64_t, const int64_t*, int64_t, float*,
                                  int, const double*, int64_t, const float*, double*, int64_t, const float*,
-                                 const float*, const float*, int64_t, int, cudaStream_t);
+                                 const float*, const float*, const long long*, int64_t, int, cudaStream_t);
 
 }  // namespace hk
