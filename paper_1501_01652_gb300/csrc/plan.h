@@ -114,6 +114,7 @@ double log_coord(double k, int64_t k0, int64_t k1);
 double expansion_entry(const HostPlan& hp, int64_t k, int64_t n, const std::vector<int>* lcols);
 // Near-field J from the Taylor table (host copy of the device evaluator).
 double table_j(const HostPlan& hp, double z);
+double table_j_q62(const HostPlan& hp, double z);
 // j_{0,n} - (n-1/4)pi for n = 1..count.
 void j0_zero_offsets(int64_t count, double* b);
 // v_n = 2 / J_1(j_{0,n})^2, n = 1..N, from the offsets b_n (Section 6, the self-inverse relation).

@@ -1053,6 +1053,38 @@ double table_j(const HostPlan& hp, double z) {
   return v;
 }
 
+// The fixed-point evaluation FP64 near fields use on the device, restated on the host: the
+// interval i = floor(z sub) and U = (z sub - i - 1/2) 2^64 from the bits of z (z >= 0), Horner's
+// rule in Q62 with the floor of each signed 128-bit product over 2^64, one rounding to double.
+double table_j_q62(const HostPlan& hp, double z) {
+  uint64_t bits;
+  memcpy(&bits, &z, sizeof bits);
+  const int E = (int)(bits >> 52) & 0x7ff;
+  const uint64_t M = (bits & 0xfffffffffffffULL) | (E ? (1ULL << 52) : 0ULL);
+  const int sh = 52 + 1023 - kJTabLog - E;
+  int64_t i;
+  uint64_t F;
+  if (sh <= 0) {
+    i = hp.jt_n;
+    F = 0;
+  } else if (sh <= 52) {
+    i = (int64_t)(M >> sh);
+    F = M << (64 - sh);
+  } else {
+    i = 0;
+    F = sh - 53 < 64 ? (M << 11) >> (sh - 53) : 0ULL;
+  }
+  if (i >= hp.jt_n) {
+    i = hp.jt_n - 1;
+    F = ~0ULL;
+  }
+  const int64_t U = (int64_t)(F ^ (1ULL << 63));
+  const long long* t = &hp.jtabq[(size_t)i * (hp.jt_deg + 1)];
+  int64_t v = t[hp.jt_deg];
+  for (int j = hp.jt_deg - 1; j >= 0; --j) v = (int64_t)(((__int128)v * U) >> 64) + t[j];
+  return std::ldexp((double)v, -62);
+}
+
 // The far-field representation of entry (k, n) summed over the given stacked columns:
 // Re[ exp(i theta~_kn) sum_l rowfun_l(k) colfun_l(n) ].
 double expansion_entry(const HostPlan& hp, int64_t k, int64_t n, const std::vector<int>* lcols) {
@@ -1115,7 +1147,10 @@ double host_entry(const HostPlan& hp, int64_t k, int64_t n, int* is_far) {
              cheb_interp(&blk->vcheb[(size_t)a * blk->P], blk->P, y);
     return (cplx(c, s) * acc).real();
   }
-  return table_j(hp, hp.r_true[k - 1] * hp.om_true[n - 1]);
+  // FP64 plans evaluate near-field J in fixed point on the device; FP32 and DF64 plans (whose
+  // small batches use their own float tables) are represented by the FP64 table
+  const double z = hp.r_true[k - 1] * hp.om_true[n - 1];
+  return (hp.fp32 || hp.df64) ? table_j(hp, z) : table_j_q62(hp, z);
 }
 
 }  // namespace hk

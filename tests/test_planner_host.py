@@ -298,3 +298,28 @@ def test_dht_inverse_weights():
     # large-root limit: J_1(j_{0,n})^2 ~ 2/(pi j_{0,n}), so v_n ~ pi j_{0,n}
     n = np.arange(N - 10, N + 1)
     assert np.max(np.abs(v[n - 1] / (np.pi * ((n - 0.25) * np.pi + b[n - 1])) - 1)) < 1e-9
+
+
+@pytest.mark.parametrize("N,eps", [(2000, 1e-15), (3000, 1e-12)])
+def test_near_entries_match_oracle_j(N, eps):
+    # An FP64 plan's near-field entries are J_0(z) from the Q62 fixed-point Taylor table (the
+    # host restatement of the device evaluation). Schlomilch on the paper grid has
+    # z = (k/N)(n pi) exactly as the plan forms it, so each entry is checked against the oracle's
+    # double-double J_0(z): within half an ulp of rounding, the truncation of the fixed-point
+    # Horner rule (< 2^-61), the table's Taylor remainder (eps/100) and the oracle's own rounding.
+    p = hk.Plan("schlomilch", 0, N, eps, grid="paper", host_only=True)
+    assert p.info["precision"] == 1  # FP64 below eps = 1e-11
+    rng = np.random.default_rng(23)
+    checked = 0
+    for k in rng.integers(1, N + 1, 60):
+        ne = p.near_prefix(int(k))
+        if ne == 0:
+            continue
+        for n in rng.integers(1, ne + 1, 12):
+            v, far = p.entry(int(k), int(n))
+            assert not far
+            z = (int(k) / N) * (int(n) * math.pi)
+            ref = oracle.besselj_dd(0, z)
+            assert abs(v - ref) <= 2.5e-16 + eps / 100, (k, n, z, v, ref)
+            checked += 1
+    assert checked > 100
