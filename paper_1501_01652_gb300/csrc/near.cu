@@ -4,8 +4,10 @@
 //
 // J_nu on [0, zmax] comes from a table of Taylor polynomials about the centres of
 // intervals of width 1/kJTabSub (built at plan time from the Neumann addition formula,
-// Eq. 8, with the degree set by eps), so one evaluation costs a table row load and
-// deg FMAs.
+// Eq. 8, with the degree set by eps), so one evaluation costs a table row load and deg
+// Horner steps: FMAs in float for FP32 plans and in double-float for DF64 plans of few
+// vectors; 64-bit integer steps on a Q62 copy of the table for FP64 plans and for every
+// tensor-core near field (FP64 is the scarce pipe on this part).
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -37,7 +39,8 @@ __device__ __forceinline__ R table_j(const R* __restrict__ jtab, int64_t jt_n, i
 // J_nu(z) from the Q62 table, in two parts. q62_interval finds the interval i = floor(z kJTabSub)
 // and U = (z kJTabSub - i - 1/2) 2^64 from the bits of z (z >= 0) by integer operations; the
 // caller runs Horner's rule in Q62 with the signed high halves of 64 x 64-bit products (each
-// step truncating by less than 2^-62) and rounds to J 2^53. Every operation but z = r omega is
+// step truncating by less than 2^-62) and rounds (to J 2^53 for the digit split, to double
+// otherwise). Every operation but z = r omega is
 // on the integer pipe.
 __device__ __forceinline__ long long q62_interval(int64_t jt_n, double z, long long& U) {
   const unsigned long long bits = (unsigned long long)__double_as_longlong(z);
