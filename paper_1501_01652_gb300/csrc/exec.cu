@@ -704,7 +704,7 @@ int run_all(DevicePlan* d, const HostPlan& hp, const double* c, int64_t ldc, dou
   {
     StageScope sc(d, HANKEL_STAGE_NEAR, st, record);
     if (d->tcd && nrhs >= kNearTcMinRhs)
-      launch_near_tc(d->items, d->nitems, d->mrows, d->nmrows, d->nend, d->hpN, (double*)partial, nrhs, c, ldc,
+      launch_near_tc(d->df64, d->items, d->nitems, d->mrows, d->nmrows, d->nend, d->hpN, (double*)partial, nrhs, c, ldc,
                      d->tcd, d->tce, d->tc_npad, f, ldf, d->nodes.r_true, d->nodes.om_true, d->jtabq, hp.jt_n,
                      hp.jt_deg, st);
     else if (d->df64)

@@ -171,10 +171,11 @@ void launch_near(const NearItem* items, int64_t nitems, const NearRow* mrows, in
 // fixed-point table jtabq on the integer pipe. Cd holds 8 x 16 x Npad fp16 digits and Ce
 // (Npad / 512) x 16 exponents, both written here from c (Npad = N rounded up to a multiple of 512).
 constexpr int kNearTcMinRhs = 8;
-void launch_near_tc(const NearItem* items, int64_t nitems, const NearRow* mrows, int64_t nmrows, const int64_t* nend,
-                    int64_t N, double* partial, int nrhs, const double* c, int64_t ldc, void* Cd, int* Ce,
-                    int64_t Npad, double* f, int64_t ldf, const double* r, const double* om, const long long* jtabq,
-                    int64_t jt_n, int deg, cudaStream_t st);
+// df: a DF64 plan (7 digits and 7 diagonals: products to about 2^-46 of the chunk scale).
+void launch_near_tc(bool df, const NearItem* items, int64_t nitems, const NearRow* mrows, int64_t nmrows,
+                    const int64_t* nend, int64_t N, double* partial, int nrhs, const double* c, int64_t ldc, void* Cd,
+                    int* Ce, int64_t Npad, double* f, int64_t ldf, const double* r, const double* om,
+                    const long long* jtabq, int64_t jt_n, int deg, cudaStream_t st);
 // Near field of DF64 plans in double-float on the FP32 pipe: r, om and jtab hold (high, low)
 // float pairs of the FP64 tables, cd the coefficients as pairs ([nrhs][N]); partial sums and
 // outputs are FP64.

@@ -242,7 +242,8 @@ __device__ __forceinline__ unsigned digit_pair(unsigned long long Yl, unsigned l
   constexpr int s = 7 * (kTcDig - 1 - I);
   const unsigned el = (unsigned)(Yl >> s) & 127u, eh = (unsigned)(Yh >> s) & 127u;
   const unsigned w = 0x64006400u | el | (eh << 16);
-  const __half2 v = __hsub2(*reinterpret_cast<const __half2*>(&w), __half2(__float2half(1088.0f), __float2half(1088.0f)));
+  const __half2 off = __half2(__float2half(1088.0f), __float2half(1088.0f));
+  const __half2 v = __hsub2(*reinterpret_cast<const __half2*>(&w), off);
   return *reinterpret_cast<const unsigned*>(&v);
 }
 
@@ -301,14 +302,14 @@ __global__ void __launch_bounds__(kTcChunk) k_near_cdigits(const double* __restr
 }
 
 // The A fragment of J digit i (register r: entries 2r, 2r + 1) and its products with the
-// coefficient digits j = 0 .. min(7, 8 - i), diagonal D = i + j.
-template <int I>
-__device__ __forceinline__ void tc_digit(float (&acc)[kTcDiag][2][4], const unsigned long long (&Y)[8],
-                                         const unsigned (&b)[kTcDig][2][2]) {
+// coefficient digits j < ND with diagonal D = i + j < NG.
+template <int I, int ND, int NG>
+__device__ __forceinline__ void tc_digit(float (&acc)[NG][2][4], const unsigned long long (&Y)[8],
+                                         const unsigned (&b)[ND][2][2]) {
   const unsigned a[4] = {digit_pair<I>(Y[0], Y[1]), digit_pair<I>(Y[2], Y[3]), digit_pair<I>(Y[4], Y[5]),
                          digit_pair<I>(Y[6], Y[7])};
 #pragma unroll
-  for (int j = 0; j < kTcDig && I + j < kTcDiag; ++j)
+  for (int j = 0; j < ND && I + j < NG; ++j)
 #pragma unroll
     for (int u = 0; u < 2; ++u) mma_f16(acc[I + j][u], a, b[j][u][0], b[j][u][1]);
 }
@@ -319,6 +320,11 @@ __device__ __forceinline__ void tc_digit(float (&acc)[kTcDiag][2][4], const unsi
 // fragment) and loads the coefficient digits of columns 2tq, 2tq + 1, 2tq + 8, 2tq + 9 for
 // vectors gq and gq + 8 (its B fragments). J comes from the fixed-point table (FP64 and
 // double-float plans alike: it is exact to the digit grid either way).
+// ND, NG: digits of J and c used (the leading ND of the 8) and diagonals kept. FP64 plans take
+// 8 and 9 (86 MMAs per 16-column step, products as accurate as FP64 ones); DF64 plans take 7
+// and 7 (56 MMAs): dropping the last digit of each and the diagonals D >= 7 costs at most about
+// 2^-46 of the chunk's scale per entry, the accuracy of double-float products.
+template <int ND, int NG>
 __global__ void __launch_bounds__(64, 7) k_near_tc(const NearItem* __restrict__ items, const int64_t* __restrict__ nend,
                                                int64_t N, double* partial, int nrhs, const __half* __restrict__ Cd,
                                                const int* __restrict__ Ce, int64_t Npad, double* f, int64_t ldf,
@@ -338,9 +344,9 @@ __global__ void __launch_bounds__(64, 7) k_near_tc(const NearItem* __restrict__ 
   int64_t wend = max(rend[0], rend[1]);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) wend = max(wend, (int64_t)__shfl_xor_sync(0xffffffffu, (long long)wend, o));
-  float acc[kTcDiag][2][4];
+  float acc[NG][2][4];
 #pragma unroll
-  for (int D = 0; D < kTcDiag; ++D)
+  for (int D = 0; D < NG; ++D)
 #pragma unroll
     for (int u = 0; u < 2; ++u)
 #pragma unroll
@@ -368,10 +374,10 @@ __global__ void __launch_bounds__(64, 7) k_near_tc(const NearItem* __restrict__ 
 #pragma unroll
     for (int e = 0; e < 8; ++e) Y[e] = (unsigned long long)(on[e] ? (v[e] + 256) >> 9 : 0LL) + kDigOff;
     // B: digit j, vector tile u: columns (n0 + 2tq, +1) and (n0 + 2tq + 8, +9) of vector 8u + gq
-    unsigned b[kTcDig][2][2];
+    unsigned b[ND][2][2];
     const int64_t c0 = (n0 - 1 + 2 * tq) >> 1;  // index of the digit pair
 #pragma unroll
-    for (int j = 0; j < kTcDig; ++j)
+    for (int j = 0; j < ND; ++j)
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
         const int64_t row = ((int64_t)j * 16 + 8 * u + gq) * (Npad >> 1);
@@ -380,14 +386,14 @@ __global__ void __launch_bounds__(64, 7) k_near_tc(const NearItem* __restrict__ 
       }
     // digit i of J against digits j <= 8 - i of the coefficients: consecutive products go to
     // different diagonals, so they do not wait on one another
-    tc_digit<0>(acc, Y, b);
-    tc_digit<1>(acc, Y, b);
-    tc_digit<2>(acc, Y, b);
-    tc_digit<3>(acc, Y, b);
-    tc_digit<4>(acc, Y, b);
-    tc_digit<5>(acc, Y, b);
-    tc_digit<6>(acc, Y, b);
-    tc_digit<7>(acc, Y, b);
+    tc_digit<0, ND, NG>(acc, Y, b);
+    tc_digit<1, ND, NG>(acc, Y, b);
+    tc_digit<2, ND, NG>(acc, Y, b);
+    tc_digit<3, ND, NG>(acc, Y, b);
+    tc_digit<4, ND, NG>(acc, Y, b);
+    tc_digit<5, ND, NG>(acc, Y, b);
+    tc_digit<6, ND, NG>(acc, Y, b);
+    if constexpr (ND > 7) tc_digit<7, ND, NG>(acc, Y, b);
   }
   // combine the diagonals in FP64 and write: output (row gq + 8 (q >> 1), vector 8u + 2tq + (q & 1))
   const int64_t t = (it.n0 - 1) / kTcChunk;
@@ -400,7 +406,7 @@ __global__ void __launch_bounds__(64, 7) k_near_tc(const NearItem* __restrict__ 
       const int64_t k = it.k0 + rowoff;
       double v = 0.0;
 #pragma unroll
-      for (int D = kTcDiag - 1; D >= 0; --D) v = fma(v, 1.0 / 128.0, (double)acc[D][u][q]);
+      for (int D = NG - 1; D >= 0; --D) v = fma(v, 1.0 / 128.0, (double)acc[D][u][q]);
       v = ldexp(v, Ce[t * 16 + g] - 9);
       if (k > N || g >= nrhs) continue;
       if (it.slot < 0) f[(int64_t)g * ldf + k - 1] = v;
@@ -447,13 +453,17 @@ void launch_near_t(const NearItem* items, int64_t nitems, const int64_t* nend, i
   const int64_t threads = nitems * 32;
   const unsigned grid = (unsigned)((threads + 255) / 256);
   if (nrhs <= 1)
-    k_near<R, 1><<<grid, 256, 0, st>>>(items, nitems, nend, N, partial, nrhs, c, ldc, f, ldf, r, om, jtab, jq, jt_n, deg);
+    k_near<R, 1><<<grid, 256, 0, st>>>(items, nitems, nend, N, partial, nrhs, c, ldc, f, ldf, r, om, jtab, jq, jt_n,
+                                        deg);
   else if (nrhs <= 2)
-    k_near<R, 2><<<grid, 256, 0, st>>>(items, nitems, nend, N, partial, nrhs, c, ldc, f, ldf, r, om, jtab, jq, jt_n, deg);
+    k_near<R, 2><<<grid, 256, 0, st>>>(items, nitems, nend, N, partial, nrhs, c, ldc, f, ldf, r, om, jtab, jq, jt_n,
+                                        deg);
   else if (nrhs <= 4)
-    k_near<R, 4><<<grid, 256, 0, st>>>(items, nitems, nend, N, partial, nrhs, c, ldc, f, ldf, r, om, jtab, jq, jt_n, deg);
+    k_near<R, 4><<<grid, 256, 0, st>>>(items, nitems, nend, N, partial, nrhs, c, ldc, f, ldf, r, om, jtab, jq, jt_n,
+                                        deg);
   else if (nrhs <= 8)
-    k_near<R, 8><<<grid, 256, 0, st>>>(items, nitems, nend, N, partial, nrhs, c, ldc, f, ldf, r, om, jtab, jq, jt_n, deg);
+    k_near<R, 8><<<grid, 256, 0, st>>>(items, nitems, nend, N, partial, nrhs, c, ldc, f, ldf, r, om, jtab, jq, jt_n,
+                                        deg);
   else
     k_near<R, kMaxRhsGroup><<<grid, 256, 0, st>>>(items, nitems, nend, N, partial, nrhs, c, ldc, f, ldf, r, om, jtab,
                                                   jq, jt_n, deg);
@@ -495,14 +505,18 @@ void launch_near_df(const NearItem* items, int64_t nitems, const NearRow* mrows,
                                                                                 ldf);
 }
 
-void launch_near_tc(const NearItem* items, int64_t nitems, const NearRow* mrows, int64_t nmrows, const int64_t* nend,
-                    int64_t N, double* partial, int nrhs, const double* c, int64_t ldc, void* Cdv, int* Ce,
-                    int64_t Npad, double* f, int64_t ldf, const double* r, const double* om, const long long* jtabq,
-                    int64_t jt_n, int deg, cudaStream_t st) {
+void launch_near_tc(bool df, const NearItem* items, int64_t nitems, const NearRow* mrows, int64_t nmrows,
+                    const int64_t* nend, int64_t N, double* partial, int nrhs, const double* c, int64_t ldc, void* Cdv,
+                    int* Ce, int64_t Npad, double* f, int64_t ldf, const double* r, const double* om,
+                    const long long* jtabq, int64_t jt_n, int deg, cudaStream_t st) {
   __half* Cd = reinterpret_cast<__half*>(Cdv);
   k_near_cdigits<<<(unsigned)(Npad / kTcChunk), kTcChunk, 0, st>>>(c, ldc, nrhs, N, Npad, Cd, Ce);
-  k_near_tc<<<(unsigned)nitems, 64, 0, st>>>(items, nend, N, partial, nrhs, Cd, Ce, Npad, f, ldf, r, om, jtabq, jt_n,
-                                             deg);
+  if (df)
+    k_near_tc<7, 7><<<(unsigned)nitems, 64, 0, st>>>(items, nend, N, partial, nrhs, Cd, Ce, Npad, f, ldf, r, om, jtabq,
+                                                     jt_n, deg);
+  else
+    k_near_tc<kTcDig, kTcDiag><<<(unsigned)nitems, 64, 0, st>>>(items, nend, N, partial, nrhs, Cd, Ce, Npad, f, ldf,
+                                                                r, om, jtabq, jt_n, deg);
   if (nmrows > 0)
     k_near_combine<double><<<(unsigned)((nmrows * 32 + 255) / 256), 256, 0, st>>>(mrows, nmrows, partial, nrhs, f,
                                                                                 ldf);
