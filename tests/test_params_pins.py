@@ -1,23 +1,30 @@
 """Planner parameters against the values the paper prints (Tables 1-3, Section 5, Section 4.3)."""
 import math
+import os
 
 import pytest
 
 import paper_1501_01652_gb300 as hk
 
-TABLE1 = {  # s_{nu,M}(1e-15), M = 3..12 (Table 1)
-    0: [180.5, 70.5, 41.5, 30.0, 24.3, 21.1, 19.1, 17.8, 17.0, 16.5],
-    1: [185.2, 71.5, 41.9, 30.2, 24.4, 21.1, 19.2, 17.9, 17.1, 16.5],
-    2: [200.2, 74.8, 43.1, 30.8, 24.8, 21.4, 19.3, 18.0, 17.2, 16.6],
-    10: [2330.7, 500.0, 149.0, 64.6, 41.4, 31.4, 26.0, 22.9, 20.9, 19.6],
-}
-TABLE2 = {  # t_{nu,T}(1e-15), T = 1..9, printed to three decimals or one significant digit (Table 2)
-    0: ["6e-8", 0.001, 0.011, 0.059, 0.165, 0.337, 0.573, 0.869, 1.217],
-    1: ["3e-5", 0.003, 0.029, 0.104, 0.243, 0.449, 0.716, 1.039, 1.411],
-    2: [0.001, 0.012, 0.061, 0.168, 0.341, 0.579, 0.876, 1.225, 1.618],
-    10: [0.484, 0.743, 1.058, 1.420, 1.823, 2.262, 2.733, 3.230, 3.750],
-}
-TABLE3 = ["4e-6", "9e-5", 0.001, 0.002, 0.004, 0.008, 0.013, 0.020]  # Eq. (10), K = 3..10 (Table 3)
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    """Rows of a fixture under tests/golden: first column an int key, the rest printed values
+    (floats; tokens in e-notation stay strings, the paper's one-significant-digit entries)."""
+    rows = {}
+    with open(os.path.join(GOLDEN, name)) as fh:
+        for line in fh:
+            line = line.split("#", 1)[0].split()
+            if not line:
+                continue
+            rows[int(line[0])] = [t if "e" in t else float(t) for t in line[1:]]
+    return rows
+
+
+TABLE1 = _golden("table1_s_nu_M_1e-15.txt")  # s_{nu,M}(1e-15), M = 3..12 (Table 1)
+TABLE2 = _golden("table2_t_nu_T_1e-15.txt")  # t_{nu,T}(1e-15), T = 1..9 (Table 2)
+TABLE3 = [v[0] for _, v in sorted(_golden("table3_neumann_radius_1e-15.txt").items())]  # K = 3..10 (Table 3)
 
 
 def _matches_printed(value, printed):
@@ -50,12 +57,19 @@ def test_lemma31_radius_meets_bound():
 
 
 def test_section5_worked_numbers():
-    # p_6(1e-15) ~ 22.7 and q_3(1e-15) ~ 3.7; K = 6, T = 3 at 1e-15; (2K-1)T = 33 vs 2T+K-2 = 10.
-    assert 22.7 <= hk.p_K(6, 1e-15) < 22.8
-    assert 3.7 <= hk.q_T(3, 1e-15) < 3.8
+    # p_6(1e-15) ~ 22.7 and q_3(1e-15) ~ 3.7; K = 6, T = 3 at 1e-15; (2K-1)T = 33 vs 2T+K-2 = 10
+    # (printed to one decimal: the value lies in [printed, printed + 0.1))
+    w = {}
+    with open(os.path.join(GOLDEN, "section5_worked_numbers_1e-15.txt")) as fh:
+        for line in fh:
+            t = line.split("#", 1)[0].split()
+            if t:
+                w[t[0]] = float(t[1])
+    assert w["p_6"] <= hk.p_K(6, 1e-15) < w["p_6"] + 0.1
+    assert w["q_3"] <= hk.q_T(3, 1e-15) < w["q_3"] + 0.1
     p = hk.params("fourier_bessel", 0, 4096, 1e-15)
-    assert (p["K"], p["T"]) == (6, 3)
-    assert p["npairs"] == 10 and (2 * p["K"] - 1) * p["T"] == 33
+    assert (p["K"], p["T"]) == (int(w["K"]), int(w["T"]))
+    assert p["npairs"] == int(w["rearranged_count"]) and (2 * p["K"] - 1) * p["T"] == int(w["full_count"])
     assert p["direct_cols"] == 22  # the first floor(p_6) columns are summed directly
     assert hk.p_K(5, 1e-15) > 30 and hk.q_T(2, 1e-15) > 30
 
