@@ -20,14 +20,18 @@ constexpr double kPi = 3.14159265358979323846;
 
 // ---------------------------------------------------------------------------
 // Double-double arithmetic (head + tail), used for plan-time Bessel values.
+// Sums renormalise once (head two-sum, tails added); products take the exact
+// head product from an FMA and fold the cross terms into its error by FMAs;
+// quotients multiply by a reciprocal refined with one Newton step.
 // ---------------------------------------------------------------------------
 struct DD {
   double h, l;
 };
 inline DD ddv(double a) { return DD{a, 0.0}; }
-inline DD dd_fast(double a, double b) {
-  double s = a + b;
-  return DD{s, b - (s - a)};
+// (s, e) with |e| small against s, renormalised so that h = fl(s + e)
+inline DD dd_fast(double s, double e) {
+  const double h = s + e;
+  return DD{h, e - (h - s)};
 }
 inline DD dd_add(DD a, DD b) {
   double s = a.h + b.h, v = s - a.h;
@@ -37,48 +41,45 @@ inline DD dd_add(DD a, DD b) {
 }
 inline DD dd_neg(DD a) { return DD{-a.h, -a.l}; }
 inline DD dd_mul(DD a, DD b) {
-  double p = a.h * b.h;
-  double e = std::fma(a.h, b.h, -p) + (a.h * b.l + a.l * b.h);
-  return dd_fast(p, e);
+  const double p = a.h * b.h;
+  return dd_fast(p, std::fma(a.l, b.h, std::fma(a.h, b.l, std::fma(a.h, b.h, -p))));
 }
-inline DD dd_div(DD a, DD b) {
-  double q1 = a.h / b.h;
-  DD r = dd_add(a, dd_neg(dd_mul(ddv(q1), b)));
-  double q2 = r.h / b.h;
-  r = dd_add(r, dd_neg(dd_mul(ddv(q2), b)));
-  double q3 = r.h / b.h;
-  return dd_add(dd_fast(q1, q2), ddv(q3));
+// 1/b: x0 = fl(1/b.h), then x1 = x0 + x0 (1 - b x0); the residual 1 - b x0 is ~2^-53, so one step
+// leaves a relative error of order 2^-104.
+inline DD dd_recip(DD b) {
+  const double x0 = 1.0 / b.h;
+  const DD res = dd_add(ddv(1.0), dd_neg(dd_mul(b, ddv(x0))));
+  return dd_add(ddv(x0), dd_mul(ddv(x0), res));
 }
 inline DD dd_scale(DD a, double p2) { return DD{a.h * p2, a.l * p2}; }
 const DD kPiDD = {3.141592653589793116, 1.2246467991473532072e-16};
 
 // J_lambda(z) for lambda = 0..L (z > 0) by Miller's backward recurrence
-// J_{k-1} = (2k/z) J_k - J_{k+1} (DLMF 3.6(vi)), normalised with
-// J_0 + 2 sum_{k>=1} J_{2k} = 1 (DLMF 10.12.4). Double-double throughout.
+// J_{k-1} = (2k/z) J_k - J_{k+1} (DLMF 3.6(vi)), started from zero above max(z, L). The scale
+// comes from the sum of squares J_0^2 + 2 sum_{k>=1} J_k^2 = 1 (DLMF 10.23.3), whose terms are
+// all positive; its sign from J_0 + 2 sum_{k>=1} J_{2k} = 1 (DLMF 10.12.4). Double-double.
 void miller_all(DD z, int L, std::vector<DD>& out) {
-  int start = (int)z.h + 90 + L;
-  if (start & 1) ++start;
-  std::vector<DD> v(L + 1, ddv(0.0));
-  DD twoz = dd_div(ddv(2.0), z);
-  DD jp1 = ddv(0.0), j = ddv(1e-40), norm = ddv(0.0);
-  for (int k = start; k >= 1; --k) {
-    if (k <= L) v[k] = j;
-    if ((k & 1) == 0) norm = dd_add(norm, dd_scale(j, 2.0));
-    DD jm1 = dd_add(dd_mul(dd_mul(ddv((double)k), twoz), j), dd_neg(jp1));
-    jp1 = j;
-    j = jm1;
-    if (std::fabs(j.h) > 1e200) {
-      const double sc = 0x1p-700;
-      j = dd_scale(j, sc);
-      jp1 = dd_scale(jp1, sc);
-      norm = dd_scale(norm, sc);
-      for (int i = k; i <= L; ++i) v[i] = dd_scale(v[i], sc);
-    }
+  const int top = 2 * (((int)z.h + 90 + L) / 2 + 1);
+  std::vector<DD> v((size_t)top + 2, ddv(0.0));
+  const DD twoz = dd_scale(dd_recip(z), 2.0);
+  v[top] = ddv(0x1p-140);
+  for (int k = top; k >= 1; --k) {
+    v[k - 1] = dd_add(dd_mul(dd_mul(ddv((double)k), twoz), v[k]), dd_neg(v[k + 1]));
+    if (std::fabs(v[k - 1].h) > 1e100)  // keeps the squares below in range
+      for (int i = k - 1; i <= top; ++i) v[i] = dd_scale(v[i], 0x1p-400);
   }
-  v[0] = j;
-  norm = dd_add(norm, j);
+  DD sq = dd_mul(v[0], v[0]), lin = v[0];
+  for (int k = 1; k <= top; ++k) {
+    sq = dd_add(sq, dd_scale(dd_mul(v[k], v[k]), 2.0));
+    if ((k & 1) == 0) lin = dd_add(lin, dd_scale(v[k], 2.0));
+  }
+  // 1/sqrt(sq): from the FP64 root, one Newton step y1 = y0 (3 - sq y0^2) / 2
+  const double y0 = 1.0 / std::sqrt(sq.h);
+  const DD t = dd_add(ddv(3.0), dd_neg(dd_mul(sq, dd_mul(ddv(y0), ddv(y0)))));
+  DD inv = dd_scale(dd_mul(ddv(y0), t), 0.5);
+  if (lin.h < 0) inv = dd_neg(inv);
   out.resize(L + 1);
-  for (int i = 0; i <= L; ++i) out[i] = dd_div(v[i], norm);
+  for (int i = 0; i <= L; ++i) out[i] = dd_mul(v[i], inv);
 }
 
 // ---------------------------------------------------------------------------
@@ -145,59 +146,97 @@ double factorial(int n) {
 // ---------------------------------------------------------------------------
 // Bessel roots j_{0,n} as b_n = j_{0,n} - (n-1/4)pi (Lemma 3.2)
 // ---------------------------------------------------------------------------
-// Large roots: from Eq. (4) with lam = 0, J_0 ~ sqrt(2/(pi z)) (P cos mu - Q sin mu) and
-// mu = (n-1/2)pi + b, so J_0 = 0 <=> tan b = -Q(z)/P(z), z = (n-1/4)pi + b. The map
-// b -> atan(-Q/P) contracts by ~1/(8 z^2); its fixed point keeps b's full relative accuracy.
+// The two series of Eq. (4) at once: S(z) = sum_{m<=L} a_m(lam) (i/z)^m, so that Re S = P(z)
+// (the cosine series, sum (-1)^k a_2k z^-2k) and Im S = Q(z) (the sine series,
+// sum (-1)^k a_2k+1 z^-2k-1). L is the last index before the terms stop shrinking or drop below
+// 2^-70; S is summed by Horner's rule in the complex variable w = i/z, from the smallest term
+// up: S <- a_m + w S, where multiplying by w maps (x, y) to (-y/z, x/z).
+struct HankelA {
+  double a[96];
+  explicit HankelA(int lam) { hankel_a(lam, 95, a); }
+};
+cplx hankel_pq(int lam, double z) {
+  static const HankelA a0(0), a1(1);  // the orders used here: roots of J_0, J_1 at those roots
+  HankelA own(lam < 2 ? 0 : lam);
+  const double* a = lam == 0 ? a0.a : lam == 1 ? a1.a : own.a;
+  const double iz = 1.0 / z;
+  int L = 0;
+  double mag = std::fabs(a[0]), zm = 1.0;
+  for (int m = 1; m < 95; ++m) {
+    zm *= iz;
+    const double next = std::fabs(a[m]) * zm;
+    if (next > mag || mag < 0x1p-70) break;
+    mag = next;
+    L = m;
+  }
+  double x = a[L], y = 0.0;
+  for (int m = L - 1; m >= 0; --m) {
+    const double nx = a[m] - y * iz;
+    y = x * iz;
+    x = nx;
+  }
+  return cplx(x, y);
+}
+
+// Large roots: from Eq. (4) with lam = 0, J_0(z) ~ sqrt(2/(pi z)) Re[e^{i mu} S(z)] with
+// mu = z - pi/4 = (n-1/2)pi + b, so J_0 = 0 <=> Re[i e^{ib} S] = 0 <=> b = atan(-Q/P),
+// z = (n-1/4)pi + b. The map b -> atan(-Q/P) contracts by ~1/(8 z^2); its fixed point keeps
+// b's full relative accuracy.
 double root_offset_large(double n) {
-  double beta = (n - 0.25) * kPi;
+  const double beta = (n - 0.25) * kPi;
   double b = 0.125 / beta;
-  double a[80];
-  hankel_a(0, 79, a);
   for (int it = 0; it < 12; ++it) {
-    double z = beta + b;
-    double iz = 1.0 / z, p = 0.0, q = 0.0, zm = 1.0;
-    for (int m = 0; m < 79; ++m) {
-      double term = a[m] * zm;
-      if (m > 2 && std::fabs(term) < 1e-21) break;
-      int r = m & 3;
-      if (r == 0) p += term; else if (r == 1) q += term; else if (r == 2) p -= term; else q -= term;
-      zm *= iz;
-    }
-    double nb = std::atan(-q / p);
-    if (std::fabs(nb - b) <= 1e-19 * b) { b = nb; break; }
+    const cplx S = hankel_pq(0, beta + b);
+    const double nb = std::atan(-S.imag() / S.real());
+    const bool done = std::fabs(nb - b) <= 1e-19 * b;
     b = nb;
+    if (done) break;
   }
   return b;
 }
 
-// Small roots: Newton on J_0 in double-double from the large-root formula's guess.
+// Small roots (z < 30, where Eq. (4) is not accurate to double-double): Halley's iteration on
+// J_0 in double-double from the large-root formula's guess. With f = J_0, f' = -J_1 and
+// f'' = J_1/z - J_0 (Bessel's equation), the step is -2 f f' / (2 f'^2 - f f''); J_0 and J_1
+// come from Miller's recurrence at z = (n-1/4)pi + b.
 double root_offset_small(int64_t n) {
-  DD base = dd_mul(kPiDD, ddv(n - 0.25));
+  const DD base = dd_mul(kPiDD, ddv(n - 0.25));
   DD b = ddv(root_offset_large(n));
   std::vector<DD> J;
-  for (int it = 0; it < 10; ++it) {
-    miller_all(dd_add(base, b), 1, J);
-    DD step = dd_div(J[0], J[1]);  // J_0' = -J_1
+  for (int it = 0; it < 8; ++it) {
+    const DD z = dd_add(base, b);
+    miller_all(z, 1, J);
+    const DD f = J[0], fp = dd_neg(J[1]);
+    const DD fpp = dd_add(dd_mul(J[1], dd_recip(z)), dd_neg(J[0]));
+    const DD num = dd_scale(dd_mul(f, fp), -2.0);
+    const DD den = dd_add(dd_scale(dd_mul(fp, fp), 2.0), dd_neg(dd_mul(f, fpp)));
+    const DD step = dd_mul(num, dd_recip(den));
     b = dd_add(b, step);
     if (std::fabs(step.h) < 1e-32 * std::fabs(b.h)) break;
   }
   return b.h + b.l;
 }
 
-// sin and cos of pi*A/B (integers, B > 0), reduced in integers to a quarter turn.
+// sin and cos of pi*A/B (integers, B > 0). The angle is reduced in integers to an octant:
+// with a = A mod 2B, the angle is (pi/4)(o + r/B), o = floor(4a/B) in 0..7, r = 4a - oB in
+// [0, B). In an even octant it is o/2 quarter turns plus theta = (pi/4)(r/B); in an odd one,
+// (o+1)/2 quarter turns minus theta' = (pi/4)((B-r)/B); both angles lie in [0, pi/4], where
+// sin and cos keep full relative accuracy.
 void sincospi_ratio(int64_t A, int64_t B, double* s, double* c) {
-  int64_t a = A % (2 * B);
-  if (a < 0) a += 2 * B;
-  int64_t q = (4 * a + B) / (2 * B);  // round(2a/B)
-  int64_t y = 2 * a - q * B;          // angle = pi*(q/2 + y/(2B)), |y/(2B)| <= 1/4
-  double t = kPi * ((double)y / (double)(2 * B));
-  double ct = std::cos(t), st = std::sin(t);
-  switch (q & 3) {
-    case 0: *c = ct; *s = st; break;
-    case 1: *c = -st; *s = ct; break;
-    case 2: *c = -ct; *s = -st; break;
-    default: *c = st; *s = -ct; break;
+  const int64_t twoB = 2 * B;
+  const int64_t a = ((A % twoB) + twoB) % twoB;
+  const int64_t o = (4 * a) / B;
+  const int64_t r = 4 * a - o * B;
+  const bool odd = (o & 1) != 0;
+  const double th = 0.25 * kPi * ((double)(odd ? B - r : r) / (double)B);
+  double x = std::cos(th), y = odd ? -std::sin(th) : std::sin(th);  // e^{+-i theta}
+  for (int64_t k = (o + (odd ? 1 : 0)) / 2 % 4; k > 0; --k) {  // times i per quarter turn
+    const double t = x;
+    x = -y;
+    y = t;
   }
+  *c = x;
+  *s = y;
 }
 
 int64_t ceil_index(double tau, double shift) {
@@ -225,20 +264,11 @@ double j1_at_j0_zero(int64_t n, double b) {
     miller_all(dd_add(dd_mul(kPiDD, ddv(n - 0.25)), ddv(b)), 1, J);
     return std::fabs(J[1].h + J[1].l);
   }
+  // Eq. (4), nu = 1: J_1(z) ~ sqrt(2/(pi z)) Re[e^{i mu} S(z)], mu = z - 3pi/4 = (n-1)pi + b,
+  // and e^{i (n-1) pi} = +-1 drops out of the absolute value
   const double z = (n - 0.25) * kPi + b;
-  double a[80];
-  hankel_a(1, 79, a);
-  double p = 0.0, q = 0.0, zm = 1.0, prev = INFINITY;
-  for (int m = 0; m < 79; ++m) {
-    const double term = a[m] * zm;
-    if (std::fabs(term) > prev) break;  // the asymptotic series starts to grow
-    prev = std::fabs(term);
-    const int r = m & 3;
-    if (r == 0) p += term; else if (r == 1) q += term; else if (r == 2) p -= term; else q -= term;
-    if (std::fabs(term) < 1e-20) break;
-    zm /= z;
-  }
-  return std::sqrt(2.0 / (kPi * z)) * std::fabs(p * std::cos(b) - q * std::sin(b));
+  const cplx S = hankel_pq(1, z);
+  return std::sqrt(2.0 / (kPi * z)) * std::fabs((std::polar(1.0, b) * S).real());
 }
 
 void dht_inverse_weights(int64_t N, const double* b, double* v) {
@@ -1004,7 +1034,7 @@ void build_jtable(HostPlan& hp) {
   std::vector<DD> J;
   const int L = nu + deg + 1;
   for (int64_t i = 0; i < hp.jt_n; ++i) {
-    DD zc = dd_div(ddv(i + 0.5), ddv((double)sub));
+    const DD zc = dd_scale(ddv(i + 0.5), 1.0 / sub);  // sub is a power of two
     miller_all(zc, L, J);
     auto jl = [&](int lam) -> DD {  // J_lam for any integer lam (DLMF 10.4.1)
       if (lam >= 0) return J[lam];
