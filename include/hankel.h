@@ -66,16 +66,20 @@ enum hankel_grid {
 };
 
 enum hankel_precision {
-  HANKEL_PREC_AUTO = 0,  /* FP64 below eps = 1e-11, DF64 transforms for 1e-11 <= eps < 1e-5, FP32 stages at
-                            eps >= 1e-5; in FP64 and DF64 plans, each term of a block's low-rank form runs
-                            in the lowest precision whose rounding bound (from the sums of the absolute
-                            Chebyshev coefficients of its factors) stays within a quarter of the block's
-                            leading term in the plan precision, or within eps / 200 of it
-                            (hankel_block.terms_*; HANKEL_FLAG_UNIFORM_TERMS turns this off) */
+  HANKEL_PREC_AUTO = 0,  /* every stage in FP64 below eps = 1e-5; FP32 transform and near-field stages at
+                            eps >= 1e-5 (the accuracy goal then admits FP32 rounding); nodes, phases and
+                            plan tables are FP64 in every plan */
   HANKEL_PREC_FP64 = 1,  /* every stage in FP64 */
   HANKEL_PREC_FP32 = 2,  /* FP32 stages; refused (HANKEL_EUNSUPPORTED) when eps < 1e-5 */
-  HANKEL_PREC_DF64 = 3   /* transforms and spectrum products in double-float (pairs of FP32, ~48
+  HANKEL_PREC_DF64 = 3,  /* transforms and spectrum products in double-float (pairs of FP32, ~48
                             significant bits), everything else FP64; refused when eps < 1e-11 */
+  HANKEL_PREC_MIXED = 4  /* opt-in arithmetic narrower than FP64 below eps = 1e-5: DF64 plans for
+                            1e-11 <= eps < 1e-5, FP64 plans below, FP32 stages at eps >= 1e-5; in FP64 and
+                            DF64 plans each term of a block's low-rank form runs in the lowest precision
+                            whose rounding bound (from the sums of the absolute Chebyshev coefficients of
+                            its factors) stays within a quarter of the block's leading term in the plan
+                            precision, or within eps / 200 of it (hankel_block.terms_*;
+                            HANKEL_FLAG_UNIFORM_TERMS turns this lowering off) */
 };
 
 enum hankel_status {
@@ -101,7 +105,7 @@ enum hankel_status {
 #define HANKEL_FLAG_NO_REFINE 16u  /* keep the blocks of Eq. (19) as they are; by default a block is cut into
                                       smaller ones where that lowers the estimated work (fewer kept columns
                                       away from the near field) */
-#define HANKEL_FLAG_UNIFORM_TERMS 64u /* AUTO plans: every far-field term in the plan precision (no per-term
+#define HANKEL_FLAG_UNIFORM_TERMS 64u /* MIXED plans: every far-field term in the plan precision (no per-term
                                          lowering of small low-rank terms) */
 
 /* Options for hankel_plan_ex(). Fill with hankel_options_default() first. */
@@ -313,8 +317,9 @@ typedef struct {
   int streams;        /* CUDA streams, i.e. batches in flight at once (default 4, at most 16) */
   int max_batch;      /* most coefficient vectors packed into one execution (default 64) */
   int use_graphs;     /* 1: replay each (plan, batch size, stream) launch sequence from a captured CUDA graph */
-  int precision;      /* precision every plan is built with: HANKEL_PREC_AUTO (chosen per eps as for a
-                         plan: FP64, DF64 transforms or FP32 stages) or HANKEL_PREC_FP64 */
+  int precision;      /* precision every plan is built with: HANKEL_PREC_AUTO (FP64 below eps = 1e-5, FP32
+                         stages at or above), HANKEL_PREC_FP64, or HANKEL_PREC_MIXED (chosen per eps and
+                         per term as for a MIXED plan) */
   int pack_requests;  /* 1: pack waiting requests of one plan into one execution; 0: one request each */
   int batch_window_us; /* a plan's batch with fewer than max_batch vectors waits until no request of the
                           plan has arrived for this long (so a burst of submissions stays one batch),

@@ -14,7 +14,7 @@ from . import _lib
 
 TASKS = {"schlomilch": 0, "fourier_bessel": 1, "dht": 2}
 GRIDS = {"unit": 0, "paper": 1}
-PRECISIONS = {"auto": 0, "fp64": 1, "fp32": 2, "df64": 3}
+PRECISIONS = {"auto": 0, "fp64": 1, "fp32": 2, "df64": 3, "mixed": 4}
 
 
 def _options(task, nu, N, eps, grid="unit", gamma=None, precision="auto", max_nrhs=1, workspace_limit=0,
@@ -210,8 +210,9 @@ class Server:
     ticket; the library's dispatcher batches waiting requests of the same plan, runs batches
     of different plans concurrently on its CUDA streams and writes each result into the array
     ``submit`` returned. ``precision="fp64"`` builds every plan in FP64 (the plain form);
-    ``"auto"`` picks per plan: FP64 below eps = 1e-11, double-float transforms for
-    1e-11 <= eps < 1e-5 and FP32 stages at eps >= 1e-5.
+    ``"auto"`` picks per plan: FP64 below eps = 1e-5 and FP32 stages at eps >= 1e-5;
+    ``"mixed"`` opts into narrower arithmetic below 1e-5 (double-float transforms for
+    1e-11 <= eps < 1e-5, small low-rank terms in double-float or FP32).
     """
 
     def __init__(self, streams=4, max_batch=64, use_graphs=False, precision="auto", memory_cap=0, pack=True,

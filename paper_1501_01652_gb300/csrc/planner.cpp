@@ -332,16 +332,18 @@ int choose_params(const hankel_options& o, HostPlan& hp) {
   if (o.task == HANKEL_DHT && o.nu != 0) return HANKEL_EINVAL;
   if (o.grid != HANKEL_GRID_UNIT && o.grid != HANKEL_GRID_PAPER) return HANKEL_EINVAL;
   if (o.max_nrhs < 1) return HANKEL_EINVAL;
-  if (o.precision < HANKEL_PREC_AUTO || o.precision > HANKEL_PREC_DF64) return HANKEL_EINVAL;
+  if (o.precision < HANKEL_PREC_AUTO || o.precision > HANKEL_PREC_MIXED) return HANKEL_EINVAL;
   if (o.task == HANKEL_SCHLOMILCH && (o.gamma < -1 || o.gamma > 1024)) return HANKEL_EINVAL;
   if (o.eps < 1e-16) return HANKEL_EUNSUPPORTED;
   if (o.precision == HANKEL_PREC_FP32 && o.eps < 1e-5) return HANKEL_EUNSUPPORTED;
   if (o.precision == HANKEL_PREC_DF64 && o.eps < 1e-11) return HANKEL_EUNSUPPORTED;
-  // FP32 transform and near-field stages only where the accuracy goal allows them (eps >= 1e-5),
-  // double-float transforms where their ~2^-48 rounding stays far below eps (eps >= 1e-11);
-  // nodes, phases and all plan tables stay FP64.
-  hp.fp32 = (o.precision == HANKEL_PREC_FP32) || (o.precision == HANKEL_PREC_AUTO && o.eps >= 1e-5);
-  hp.df64 = !hp.fp32 && ((o.precision == HANKEL_PREC_DF64) || (o.precision == HANKEL_PREC_AUTO && o.eps >= 1e-11));
+  // FP32 transform and near-field stages only where the accuracy goal allows them (eps >= 1e-5);
+  // below that every stage is FP64 unless the caller opts into narrower arithmetic: double-float
+  // transforms where their ~2^-48 rounding stays far below eps (DF64, or MIXED at eps >= 1e-11).
+  // Nodes, phases and all plan tables stay FP64.
+  const bool wide = o.precision == HANKEL_PREC_AUTO || o.precision == HANKEL_PREC_MIXED;
+  hp.fp32 = (o.precision == HANKEL_PREC_FP32) || (wide && o.eps >= 1e-5);
+  hp.df64 = !hp.fp32 && ((o.precision == HANKEL_PREC_DF64) || (o.precision == HANKEL_PREC_MIXED && o.eps >= 1e-11));
 
   const int64_t N = o.N;
   // Table 4: M = max(floor(0.3 log(1/eps)), 3), natural logarithm.
@@ -880,7 +882,7 @@ void compress_blocks(HostPlan& hp) {
 // u grows with u times the size of its contribution, max_k |U_l(k)| max_n |V_l(n)| (per unit of
 // ||c||_1). Each factor is a polynomial interpolant p = sum_j a_j T_j in the Chebyshev
 // variable, so max |p| <= sum_j |a_j| bounds it above, and the largest value at the Chebyshev
-// points bounds it below. In AUTO plans of FP64 or DF64 precision a term takes the lowest
+// points bounds it below. In MIXED plans of FP64 or DF64 precision a term takes the lowest
 // precision whose upper bound stays within
 //   max(u_plan / 4, eps / 200) x (the largest grid size of the block's terms),
 // i.e. a quarter of the rounding bound of the block's leading term in the plan precision, or
@@ -894,7 +896,7 @@ constexpr double kUnitFP32 = 5.9604644775390625e-08;  // 2^-24
 void assign_term_precision(HostPlan& hp) {
   const int base = hp.fp32 ? kTermFP32 : hp.df64 ? kTermDF64 : kTermFP64;
   const bool mixed =
-      hp.opt.precision == HANKEL_PREC_AUTO && !hp.fp32 && !(hp.opt.flags & HANKEL_FLAG_UNIFORM_TERMS);
+      hp.opt.precision == HANKEL_PREC_MIXED && !hp.fp32 && !(hp.opt.flags & HANKEL_FLAG_UNIFORM_TERMS);
   for (Block& b : hp.blocks) {
     const int nl = b.rank ? b.rank : (int)b.lcols.size();
     b.tprec.assign((size_t)nl, (int8_t)base);

@@ -433,7 +433,8 @@ int hankel_server_create(hankel_server_t* out, const hankel_server_options* o) {
   if (o) opt = *o;
   if (opt.memory_cap == 0) opt.memory_cap = kDefaultCap;
   if (opt.streams < 1 || opt.streams > 16 || opt.max_batch < 1 || opt.batch_window_us < 0) return HANKEL_EINVAL;
-  if (opt.precision != HANKEL_PREC_AUTO && opt.precision != HANKEL_PREC_FP64) return HANKEL_EINVAL;
+  if (opt.precision != HANKEL_PREC_AUTO && opt.precision != HANKEL_PREC_FP64 && opt.precision != HANKEL_PREC_MIXED)
+    return HANKEL_EINVAL;
   hankel_server_s* s = new hankel_server_s();
   s->opt = opt;
   if (cudaGetDevice(&s->device) != cudaSuccess) {

@@ -125,7 +125,7 @@ def test_fp32_stages_at_relaxed_accuracy(task, nu, kind, eps, precision):
                                           ("fourier_bessel", 0, "uniform")])
 @pytest.mark.parametrize("eps", [1e-6, 1e-8, 1e-11])
 def test_df64_transforms(task, nu, kind, eps):
-    # double-float transforms (AUTO picks them for 1e-11 <= eps < 1e-5) meet the bar, and stay
+    # double-float transforms (MIXED picks them for 1e-11 <= eps < 1e-5) meet the bar, and stay
     # close to the FP64 plan's result
     N = 7000
     c = coefficients(kind, N, 2, 7300 + nu)
@@ -148,7 +148,7 @@ def test_df64_sparse_vectors(eps):
     for r in range(16):
         idx = rng.choice(N, size=1 + r % 4, replace=False)
         c[r, idx] = rng.standard_normal(idx.size)
-    f, plan = _run("dht", 0, N, eps, c)
+    f, plan = _run("dht", 0, N, eps, c, precision="mixed")
     assert plan.info["precision"] == 3
     ref = oracle.transform("dht", 0, N, c)
     l1 = np.abs(c).sum(axis=1, keepdims=True)
@@ -157,15 +157,15 @@ def test_df64_sparse_vectors(eps):
 
 @pytest.mark.parametrize("eps", [1e-15, 1e-12, 1e-8])
 def test_mixed_term_precision(eps):
-    # the small low-rank terms in double-float and FP32 (AUTO) against every term in the plan
+    # the small low-rank terms in double-float and FP32 (MIXED) against every term in the plan
     # precision: both meet the bar, and they differ by far less than it
     N = 2 ** 17
     c = coefficients("normal", N, 4, 7500)
     rows = sample_rows(N, 64, 29)
-    f, plan = _run("dht", 0, N, eps, c)
+    f, plan = _run("dht", 0, N, eps, c, precision="mixed")
     terms = [sum(b["terms"][i] for b in plan.blocks()) for i in range(3)]
     assert terms[1] + terms[2] > 0 and terms[2] > 0
-    g, _ = _run("dht", 0, N, eps, c, mixed_terms=False)
+    g, _ = _run("dht", 0, N, eps, c, precision="mixed", mixed_terms=False)
     ref = oracle.transform("dht", 0, N, c, rows=rows)
     l1 = np.abs(c).sum(axis=1, keepdims=True)
     assert np.all(np.abs(f[:, rows] - ref) <= 10 * eps * l1)
@@ -173,14 +173,15 @@ def test_mixed_term_precision(eps):
     assert np.all(np.abs(f - g) <= eps * l1)
 
 
-@pytest.mark.parametrize("kind,eps", [("normal", 1e-15), ("decaying", 1e-15), ("normal", 1e-8)])
-def test_tensor_core_near_field(kind, eps):
+@pytest.mark.parametrize("kind,eps,precision", [("normal", 1e-15, "auto"), ("decaying", 1e-15, "auto"),
+                                                ("normal", 1e-8, "auto"), ("normal", 1e-8, "mixed")])
+def test_tensor_core_near_field(kind, eps, precision):
     # FP64 and DF64 plans run the near field's products as exact split-digit fp16 MMAs for 8+
     # vectors and as FMAs below; both meet the bar (rows up to 40 tiles long, ragged prefixes, a
     # coefficient scale that varies along the row)
     N = 20000
     c = coefficients(kind, N, 16, 7700)
-    plan = hk.Plan("dht", 0, N, eps, max_nrhs=16)
+    plan = hk.Plan("dht", 0, N, eps, max_nrhs=16, precision=precision)
     cd = torch.from_numpy(c).cuda()
     f16 = plan.exec(cd).cpu().numpy()
     f4 = plan.exec(cd[:4].contiguous()).cpu().numpy()
@@ -203,7 +204,7 @@ def test_mixed_terms_sparse_vectors(eps):
     for r in range(8):
         idx = rng.choice(N, size=1 + r % 3, replace=False)
         c[r, idx] = rng.standard_normal(idx.size)
-    f, plan = _run("dht", 0, N, eps, c)
+    f, plan = _run("dht", 0, N, eps, c, precision="mixed")
     assert sum(b["terms"][2] for b in plan.blocks()) > 0
     ref = oracle.transform("dht", 0, N, c)
     l1 = np.abs(c).sum(axis=1, keepdims=True)

@@ -38,13 +38,17 @@ def test_status_strings():
 
 
 def test_precision_policy():
-    assert hk.params("dht", 0, 4096, 1e-4)["precision"] == 2       # AUTO: FP32 stages at eps >= 1e-5
+    # AUTO: every stage FP64 below eps = 1e-5, FP32 stages at and above it
+    assert hk.params("dht", 0, 4096, 1e-4)["precision"] == 2
     assert hk.params("dht", 0, 4096, 1e-5)["precision"] == 2
-    assert hk.params("dht", 0, 4096, 9e-6)["precision"] == 3       # double-float transforms below
-    assert hk.params("dht", 0, 4096, 1e-8)["precision"] == 3
-    assert hk.params("dht", 0, 4096, 1e-11)["precision"] == 3
-    assert hk.params("dht", 0, 4096, 9e-12)["precision"] == 1      # FP64 below 1e-11
-    assert hk.params("dht", 0, 4096, 1e-15)["precision"] == 1
+    for eps in (9e-6, 1e-8, 1e-11, 9e-12, 1e-15):
+        assert hk.params("dht", 0, 4096, eps)["precision"] == 1
+    # MIXED (opt-in): double-float transforms for 1e-11 <= eps < 1e-5, FP64 below, FP32 above
+    assert hk.params("dht", 0, 4096, 1e-4, precision="mixed")["precision"] == 2
+    assert hk.params("dht", 0, 4096, 9e-6, precision="mixed")["precision"] == 3
+    assert hk.params("dht", 0, 4096, 1e-8, precision="mixed")["precision"] == 3
+    assert hk.params("dht", 0, 4096, 1e-11, precision="mixed")["precision"] == 3
+    assert hk.params("dht", 0, 4096, 9e-12, precision="mixed")["precision"] == 1
     assert hk.params("dht", 0, 4096, 1e-4, precision="fp64")["precision"] == 1
     assert hk.params("dht", 0, 4096, 1e-8, precision="fp64")["precision"] == 1
     assert hk.params("dht", 0, 4096, 1e-4, precision="df64")["precision"] == 3
@@ -54,13 +58,20 @@ def test_precision_policy():
         hk.params("dht", 0, 4096, 9e-12, precision="df64")
 
 
+@pytest.mark.parametrize("eps", [1e-15, 1e-8])
+def test_auto_plans_keep_every_term_fp64(eps):
+    # below eps = 1e-5 an AUTO plan runs every far-field transform in FP64
+    bl = hk.Plan("dht", 0, 2 ** 18, eps, host_only=True).blocks()
+    assert all(b["terms"][0] == b["ncols"] for b in bl)
+
+
 @pytest.mark.parametrize("eps,base", [(1e-15, 0), (1e-12, 0), (1e-8, 1), (1e-4, 2)])
 def test_term_precision_split(eps, base):
-    # AUTO plans run the small terms of a block's low-rank form in a lower precision; the
+    # MIXED plans run the small terms of a block's low-rank form in a lower precision; the
     # largest term of every block keeps the plan precision, and no term goes above it; uniform
     # plans and forced precisions keep one precision for every transform
     N = 2 ** 18
-    bl = hk.Plan("dht", 0, N, eps, host_only=True).blocks()
+    bl = hk.Plan("dht", 0, N, eps, host_only=True, precision="mixed").blocks()
     for b in bl:
         assert sum(b["terms"]) == b["ncols"]
         if not b["lowrank"] or base == 2:
@@ -70,7 +81,7 @@ def test_term_precision_split(eps, base):
             assert all(b["terms"][q] == 0 for q in range(base))
     if base < 2:
         assert sum(b["terms"][q] for b in bl for q in range(base + 1, 3)) > 0
-    u = hk.Plan("dht", 0, N, eps, host_only=True, mixed_terms=False)
+    u = hk.Plan("dht", 0, N, eps, host_only=True, precision="mixed", mixed_terms=False)
     assert all(b["terms"][base] == b["ncols"] for b in u.blocks())
     if base == 0:
         f = hk.Plan("dht", 0, N, eps, host_only=True, precision="fp64")
