@@ -189,8 +189,11 @@ int hankel_exec(hankel_plan_t p, const double* c, double* f, void* stream);
  * Device arrays; ldc, ldf >= N; 1 <= nrhs <= max_nrhs of the plan. Asynchronous.
  * FP64 and DF64 plans built with max_nrhs >= 8 sum the near field of calls with nrhs >= 8 as
  * exact split-digit products on the tensor cores (J and each 512-column chunk of c rounded to
- * 2^-53 and 2^-54 of their scales): the results differ from a call with fewer vectors in the
- * last bits, and are at least as close to the exact sums (checked against the oracle). */
+ * 2^-53 and 2^-54 of their scales), 16 vectors per launch, a last group of fewer than 8 vectors
+ * on the FMA kernels: the results differ from a call with fewer vectors in the last bits, and
+ * are at least as close to the exact sums (checked against the oracle). FP32 and double-float
+ * stages work on each vector scaled by a power of two from its largest |c_n| and scale their
+ * sums back, so their range does not depend on the input's. */
 int hankel_exec_batched(hankel_plan_t p, const double* c, int64_t ldc, double* f, int64_t ldf,
                         int nrhs, void* stream);
 
@@ -202,16 +205,23 @@ int hankel_exec_batched(hankel_plan_t p, const double* c, int64_t ldc, double* f
  * doubles, asynchronous on `stream`), but the call itself allocates no memory: it calls no
  * cudaMalloc, cudaFree or other allocating routine. The transform workspace (the FFT column
  * buffers and the near-field partial sums) comes from one file-scope device array of
- * HANKEL_STATIC_SCRATCH_BYTES that every GPU loading this library holds until the process
- * exits. It is meant for callers that cannot allocate device memory when they run a
- * transform: services whose device memory is all handed to their own pool allocator, and
- * latency-critical loops that must not enter the CUDA allocator. The plan's own tables are
+ * HANKEL_STATIC_SCRATCH_BYTES. It is meant for callers that cannot allocate device memory when
+ * they run a transform: services whose device memory is all handed to their own pool allocator,
+ * and latency-critical loops that must not enter the CUDA allocator. The plan's own tables are
  * still made by hankel_plan*, ahead of time.
- *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
- *    with that device current; make that first call before any stream capture begins.
+ *  - Where the array lives: a device holds it from the moment this library's module is loaded
+ *    there until the process exits. With eager module loading that is context creation; with
+ *    lazy loading (the CUDA default) it is the first lookup of the array's address, which
+ *    hankel_plan* does on the plan's device, with that device current. Create the plan before
+ *    handing the device's memory to a pool.
+ *  - Should that lookup fail at plan creation (the plan is still made), the first
+ *    hankel_exec_static call on the device retries it; that call then does the set-up and must
+ *    come before any stream capture begins.
  *  - All calls share the array and its contents persist between calls; every element a call
  *    reads is written earlier in the same call, so no clearing is needed. Calls that overlap
- *    on the GPU (other streams, other plans) race on the array: order them on one stream.
+ *    on the GPU (other streams, other plans) race on the array, and any two calls on one plan
+ *    (through this or another execution entry point) share the plan's coefficient copies: order
+ *    them on one stream.
  *  - Returns HANKEL_EUNSUPPORTED when the plan's largest transform needs more than the array
  *    holds (two columns of F complex values of the plan's precision plus the near-field
  *    partial sums; in practice N up to about 2^20 for an FP64 DHT, twice that for FP32 plans),

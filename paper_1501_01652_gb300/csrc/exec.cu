@@ -14,6 +14,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "device.h"
@@ -143,6 +144,7 @@ struct DevicePlan {
   double* inv_stage = nullptr;  // v o f for the inverse ([max_nrhs][N])
   float* cf = nullptr;   // FP32 plans: the coefficients rounded to FP32 [max_nrhs][N]
   float2* cdf = nullptr; // DF64 plans: the coefficients as (high, low) float pairs [max_nrhs][N]
+  int* cexp = nullptr;   // with cf or cdf: per vector, the power of two those copies are scaled by
   void* tcd = nullptr;   // FP64 plans, 8+ vectors: coefficient digits of the tensor-core near field
   int* tce = nullptr;    // and their per-chunk exponents
   int64_t tc_npad = 0;
@@ -162,6 +164,9 @@ struct DevicePlan {
 };
 
 namespace {
+
+// Device address of the static scratch array of hankel_exec_static on `device` (defined below).
+int static_scratch_address(int device, double2** out);
 
 template <class T>
 int dalloc(DevicePlan* d, T** p, size_t count) {
@@ -258,6 +263,14 @@ int dev_plan_create(hankel_plan_s* p) {
   if (cudaGetDevice(&d->device) != cudaSuccess) return HANKEL_ECUDA;
   const int64_t N = hp.opt.N;
   d->hpN = N;
+  {
+    // Look up the allocation-free entry point's static array on this device now, so that it is
+    // placed before the caller hands its memory to a pool and before any stream capture (with
+    // lazy module loading the array is placed at this first lookup). A failure here is not the
+    // plan's: hankel_exec_static retries the lookup and reports it.
+    double2* scratch = nullptr;
+    if (static_scratch_address(d->device, &scratch) != HANKEL_OK) cudaGetLastError();
+  }
 
   // Node tables and their derived powers.
   std::vector<double> tmp(N);
@@ -327,6 +340,7 @@ int dev_plan_create(hankel_plan_s* p) {
   }
   if (!d->fp32) HK_TRY(upload(d, &d->jtabq, hp.jtabq.data(), hp.jtabq.size()));
   if (d->any_t[kTermFP32]) HK_TRY(dalloc(d, &d->cf, (size_t)hp.opt.max_nrhs * N));
+  if (d->cf || d->cdf) HK_TRY(dalloc(d, &d->cexp, (size_t)hp.opt.max_nrhs));
 
 
   // Near-field work list: groups of kNearRows rows, the group's longest prefix cut into tiles of
@@ -657,7 +671,7 @@ int run_block(DevicePlan* d, const DevBlock& db, const TermGroup& tg, const doub
     {
       StageScope sc(d, HANKEL_STAGE_OUT, st, record);
       OutArgs oa{res2, b.F, b.R, b.k0, (rowseg ? b.S : b.C) - 1, colseg ? b.S : b.R, colseg ? b.nseg : 1,
-                 nc, c0, tg.nl, f, ldf, tg.Ut};
+                 nc, c0, tg.nl, f, ldf, tg.Ut, std::is_same<C, double2>::value ? nullptr : d->cexp};
       launch_out<C>(oa, st);
       HK_LAUNCHED();
       sc.done(1, 0.0, 0.0);
@@ -672,17 +686,25 @@ int run_block(DevicePlan* d, const DevBlock& db, const TermGroup& tg, const doub
 int run_all(DevicePlan* d, const HostPlan& hp, const double* c, int64_t ldc, double* f, int64_t ldf, int nrhs,
             void* A, void* B, void* partial, size_t capacity, bool chunk_from_capacity, cudaStream_t st,
             bool record, bool use_lanes) {
-  if (d->cf) {
-    // FP32 transforms (and FP32 near fields): the coefficients rounded once per execution
+  if (d->cexp) {
+    // FP32 and double-float stages run on the coefficients scaled by a power of two per vector
+    // (from its largest |c_n|), so their range does not depend on the input's; FP64 stages use c
     StageScope sc(d, HANKEL_STAGE_GEN, st, record);
-    launch_coeffs_f32(c, ldc, d->cf, d->hpN, nrhs, st);
+    launch_coef_exponent(c, ldc, d->hpN, nrhs, d->cexp, st);
+    HK_LAUNCHED();
+    sc.done(2, 0.0, 0.0);
+  }
+  if (d->cf) {
+    // FP32 transforms (and FP32 near fields): the scaled coefficients rounded once per execution
+    StageScope sc(d, HANKEL_STAGE_GEN, st, record);
+    launch_coeffs_f32(c, ldc, d->cf, d->hpN, nrhs, d->cexp, st);
     HK_LAUNCHED();
     sc.done(1, 0.0, 0.0);
   }
   if (d->cdf) {
-    // DF64 near fields and transforms: the coefficients split once into float pairs
+    // DF64 near fields and transforms: the scaled coefficients split once into float pairs
     StageScope sc(d, HANKEL_STAGE_GEN, st, record);
-    launch_coeffs_df64(c, ldc, d->cdf, d->hpN, nrhs, st);
+    launch_coeffs_df64(c, ldc, d->cdf, d->hpN, nrhs, d->cexp, st);
     HK_LAUNCHED();
     sc.done(1, 0.0, 0.0);
   }
@@ -703,22 +725,45 @@ int run_all(DevicePlan* d, const HostPlan& hp, const double* c, int64_t ldc, dou
   }
   {
     StageScope sc(d, HANKEL_STAGE_NEAR, st, record);
-    if (d->tcd && nrhs >= kNearTcMinRhs)
-      launch_near_tc(d->df64, d->items, d->nitems, d->mrows, d->nmrows, d->nend, d->hpN, (double*)partial, nrhs, c, ldc,
-                     d->tcd, d->tce, d->tc_npad, f, ldf, d->nodes.r_true, d->nodes.om_true, d->jtabq, hp.jt_n,
-                     hp.jt_deg, st);
-    else if (d->df64)
+    int64_t near_launches = d->nmrows > 0 ? 2 : 1;
+    if (d->tcd && nrhs >= kNearTcMinRhs) {
+      // the tensor-core near field takes 16 vectors per launch: groups of 16, and a last group of
+      // fewer than kNearTcMinRhs vectors on the FMA kernels; the groups run one after another on
+      // st and share the digit and partial-sum buffers
+      near_launches = 0;
+      for (int g0 = 0; g0 < nrhs; g0 += kNearTcRhs) {
+        const int ng = std::min(kNearTcRhs, nrhs - g0);
+        const double* cg = c + (int64_t)g0 * ldc;
+        double* fg = f + (int64_t)g0 * ldf;
+        if (ng >= kNearTcMinRhs) {
+          launch_near_tc(d->df64, d->items, d->nitems, d->mrows, d->nmrows, d->nend, d->hpN, (double*)partial, ng,
+                         cg, ldc, d->tcd, d->tce, d->tc_npad, fg, ldf, d->nodes.r_true, d->nodes.om_true, d->jtabq,
+                         hp.jt_n, hp.jt_deg, st);
+          near_launches += d->nmrows > 0 ? 3 : 2;
+        } else if (d->df64) {
+          launch_near_df(d->items, d->nitems, d->mrows, d->nmrows, d->nend, d->hpN, (double*)partial, ng,
+                         d->cdf + (int64_t)g0 * d->hpN, fg, ldf, d->rdf, d->omdf, d->jtabdf, hp.jt_n, hp.jt_deg,
+                         d->cexp + g0, st);
+          near_launches += d->nmrows > 0 ? 2 : 1;
+        } else {
+          launch_near<double>(d->items, d->nitems, d->mrows, d->nmrows, d->nend, d->hpN, (double*)partial, ng, cg,
+                              ldc, nullptr, fg, ldf, d->nodes.r_true, d->nodes.om_true, d->jtab, d->jtabq, hp.jt_n,
+                              hp.jt_deg, nullptr, st);
+          near_launches += d->nmrows > 0 ? 2 : 1;
+        }
+      }
+    } else if (d->df64)
       launch_near_df(d->items, d->nitems, d->mrows, d->nmrows, d->nend, d->hpN, (double*)partial, nrhs, d->cdf, f,
-                     ldf, d->rdf, d->omdf, d->jtabdf, hp.jt_n, hp.jt_deg, st);
+                     ldf, d->rdf, d->omdf, d->jtabdf, hp.jt_n, hp.jt_deg, d->cexp, st);
     else if (d->fp32)
       launch_near<float>(d->items, d->nitems, d->mrows, d->nmrows, d->nend, d->hpN, (float*)partial, nrhs, c, ldc,
-                         d->cf, f, ldf, d->rf, d->omf, d->jtabf, nullptr, hp.jt_n, hp.jt_deg, st);
+                         d->cf, f, ldf, d->rf, d->omf, d->jtabf, nullptr, hp.jt_n, hp.jt_deg, d->cexp, st);
     else
       launch_near<double>(d->items, d->nitems, d->mrows, d->nmrows, d->nend, d->hpN, (double*)partial, nrhs, c, ldc,
                           nullptr, f, ldf, d->nodes.r_true, d->nodes.om_true, d->jtab, d->jtabq, hp.jt_n,
-                          hp.jt_deg, st);
+                          hp.jt_deg, nullptr, st);
     HK_LAUNCHED();
-    sc.done(d->nmrows > 0 ? 2 : 1, 0.0, (double)hp.near_count * nrhs);
+    sc.done(near_launches, 0.0, (double)hp.near_count * nrhs);
   }
   for (const DevBlock& db : d->blocks) {
     for (int j = 0; j < db.ng; ++j) {
@@ -852,11 +897,13 @@ int dev_exec_inverse(hankel_plan_s* p, const double* f, int64_t ldf, double* c, 
 // The same near-field and far-field launches as dev_exec for one vector, but the
 // transform workspace -- the two FFT ping-pong column buffers and the near-field
 // partial sums -- lives in the file-scope array below instead of memory the plan
-// allocated. The array is placed on every device that loads this library and is
-// kept until the process exits. Every element the launches read is written by an
-// earlier launch of the same call, so nothing needs clearing between calls. All
-// calls share the array: calls that overlap on the GPU (on different streams, or
-// from different plans) race on it.
+// allocated. The array is placed on a device when this library's module is loaded
+// there (at context creation with eager module loading, at the first lookup of its
+// address with lazy loading, which plan creation does) and is kept until the process
+// exits. Every element the launches read is written by an earlier launch of the
+// same call, so nothing needs clearing between calls. All calls share the array:
+// calls that overlap on the GPU (on different streams, or from different plans) race
+// on it, and calls on one plan also share the plan's coefficient copies.
 // ---------------------------------------------------------------------------
 namespace {
 

@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(256) k_out(OutArgs a) {
       const C y = Y[(g - a.c0) * a.nsegr * a.F];
       ar = fmar(w.x, y.x, fmar(-w.y, y.y, ar));
     }
-    a.f[rhs * a.ldf + i] += (double)ar;
+    a.f[rhs * a.ldf + i] += a.cexp ? ldexp((double)ar, a.cexp[rhs]) : (double)ar;
   }
 }
 
@@ -173,19 +173,35 @@ __global__ void __launch_bounds__(128) k_block_rows(BlockTabArgs a) {
   }
 }
 
+__global__ void __launch_bounds__(256) k_coef_exponent(const double* __restrict__ c, int64_t ldc, int64_t N,
+                                                       int* cexp) {
+  const int64_t r = blockIdx.y;
+  int m = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    m = max(m, (int)(((unsigned long long)__double_as_longlong(c[r * ldc + i]) >> 52) & 0x7ff));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  // cexp[r] starts at -1022 (E = 0); the biased exponent E maps to E - 1022
+  if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(&cexp[r], m - 1022);
+}
+
+__global__ void k_coef_exponent_init(int* cexp, int nrhs) {
+  for (int r = threadIdx.x; r < nrhs; r += blockDim.x) cexp[r] = -1022;
+}
+
 __global__ void __launch_bounds__(256) k_coeffs_f32(const double* __restrict__ c, int64_t ldc, float* cf, int64_t N,
-                                                   int64_t total) {
+                                                   int64_t total, const int* __restrict__ cexp) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = e / N, i = e - r * N;
-    cf[e] = (float)c[r * ldc + i];
+    cf[e] = (float)ldexp(c[r * ldc + i], -cexp[r]);
   }
 }
 
 __global__ void __launch_bounds__(256) k_coeffs_df64(const double* __restrict__ c, int64_t ldc, float2* cd,
-                                                    int64_t N, int64_t total) {
+                                                    int64_t N, int64_t total, const int* __restrict__ cexp) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = e / N, i = e - r * N;
-    const double x = c[r * ldc + i];
+    const double x = ldexp(c[r * ldc + i], -cexp[r]);
     const float h = (float)x;
     cd[e] = make_float2(h, (float)(x - (double)h));
   }
@@ -249,14 +265,22 @@ void launch_add_lanes(double* f, int64_t ldf, const double* const* acc, int nacc
   k_add_lanes<<<grid1d(total), 256, 0, st>>>(f, ldf, acc[0], nacc > 1 ? acc[1] : nullptr, N, total);
 }
 
-void launch_coeffs_f32(const double* c, int64_t ldc, float* cf, int64_t N, int nrhs, cudaStream_t st) {
-  const int64_t total = N * nrhs;
-  k_coeffs_f32<<<grid1d(total), 256, 0, st>>>(c, ldc, cf, N, total);
+void launch_coef_exponent(const double* c, int64_t ldc, int64_t N, int nrhs, int* cexp, cudaStream_t st) {
+  k_coef_exponent_init<<<1, 256, 0, st>>>(cexp, nrhs);
+  const unsigned bx = (unsigned)std::min<int64_t>((N + 255) / 256, std::max<int64_t>(1, 608 / nrhs));
+  k_coef_exponent<<<dim3(bx, (unsigned)nrhs), 256, 0, st>>>(c, ldc, N, cexp);
 }
 
-void launch_coeffs_df64(const double* c, int64_t ldc, float2* cd, int64_t N, int nrhs, cudaStream_t st) {
+void launch_coeffs_f32(const double* c, int64_t ldc, float* cf, int64_t N, int nrhs, const int* cexp,
+                       cudaStream_t st) {
+  const int64_t total = N * nrhs;
+  k_coeffs_f32<<<grid1d(total), 256, 0, st>>>(c, ldc, cf, N, total, cexp);
+}
+
+void launch_coeffs_df64(const double* c, int64_t ldc, float2* cd, int64_t N, int nrhs, const int* cexp,
+                        cudaStream_t st) {
   const int64_t total = N * (int64_t)nrhs;
-  k_coeffs_df64<<<grid1d(total), 256, 0, st>>>(c, ldc, cd, N, total);
+  k_coeffs_df64<<<grid1d(total), 256, 0, st>>>(c, ldc, cd, N, total, cexp);
 }
 
 template void launch_seg_mac<df64c>(const df64c*, const df64c*, df64c*, int64_t, int64_t, int, cudaStream_t);

@@ -76,6 +76,8 @@ struct OutArgs {
   double* f;          // f[rhs * ldf + k-1] += ...
   int64_t ldf;
   const void* Ut;     // [ncols][R] block row table times the row chirp (double2, df64c or float2)
+  const int* cexp;    // FP32 and double-float groups: the columns were generated from coefficients scaled by
+                      // 2^-cexp[rhs], so the row sums are scaled back by 2^cexp[rhs] (nullptr: FP64 groups)
 };
 
 // Plan-time block tables (computed in FP64, stored in the plan precision). For a block with a
@@ -108,10 +110,17 @@ void launch_diag_scale(const double* x, int64_t ldx, const double* v, double sca
 // f[r * ldf + i] += acc[0][r * N + i] (+ acc[1][r * N + i]) for r < nrhs, i < N, nacc <= 2.
 void launch_add_lanes(double* f, int64_t ldf, const double* const* acc, int nacc, int64_t N, int nrhs,
                       cudaStream_t st);
-// cf[r * N + i] = (float) c[r * ldc + i] for r < nrhs, i < N.
-void launch_coeffs_f32(const double* c, int64_t ldc, float* cf, int64_t N, int nrhs, cudaStream_t st);
-// cd[r * N + i] = (h, l): h = (float) c[r * ldc + i], l = (float)(c - h), for r < nrhs, i < N.
-void launch_coeffs_df64(const double* c, int64_t ldc, float2* cd, int64_t N, int nrhs, cudaStream_t st);
+// Per vector r < nrhs: cexp[r] = E - 1022, E the largest biased FP64 exponent of c[r * ldc + i], i < N
+// (E = 0 for a vector of zeros and subnormals), so that |c| 2^-cexp[r] < 1 for every entry. The
+// transform is linear, so the FP32 and double-float stages run on the coefficients scaled by that
+// power of two (exactly) and scale their sums back: their range then does not depend on the input's.
+void launch_coef_exponent(const double* c, int64_t ldc, int64_t N, int nrhs, int* cexp, cudaStream_t st);
+// cf[r * N + i] = (float) (c[r * ldc + i] 2^-cexp[r]) for r < nrhs, i < N.
+void launch_coeffs_f32(const double* c, int64_t ldc, float* cf, int64_t N, int nrhs, const int* cexp,
+                       cudaStream_t st);
+// cd[r * N + i] = (h, l): x = c[r * ldc + i] 2^-cexp[r], h = (float) x, l = (float)(x - h), for r < nrhs, i < N.
+void launch_coeffs_df64(const double* c, int64_t ldc, float2* cd, int64_t N, int nrhs, const int* cexp,
+                        cudaStream_t st);
 
 // Convolution kernels of the segments of a block: for y < nseg and t < F,
 // hh[y*F + t] = exp(-i pi D^2 / (2E)), D = Ua (t - (Cc-1) + (k0 + y dk) - (n0 + y dn)) + Ub - Vb
@@ -161,27 +170,29 @@ template <class R>
 // cf: optional coefficients already rounded to FP32 ([nrhs][N]); used instead of c when given.
 // jtabq: the J table in Q62 fixed point; FP64 near fields (R = double) evaluate J from it on
 // the integer pipe, FP32 ones (R = float, jtabq unused) from jtab.
+// cexp: with cf, the exponents of its scaling (launch_coef_exponent), applied to the sums.
 void launch_near(const NearItem* items, int64_t nitems, const NearRow* mrows, int64_t nmrows, const int64_t* nend,
                  int64_t N, R* partial, int nrhs, const double* c, int64_t ldc, const float* cf, double* f,
                  int64_t ldf, const R* r, const R* om, const R* jtab, const long long* jtabq, int64_t jt_n, int deg,
-                 cudaStream_t st);
+                 const int* cexp, cudaStream_t st);
 
 // Near field with the per-vector products as exact split-digit fp16 tensor-core products
 // (8 <= nrhs <= 16), FP64 and double-float plans: z = r_n om_n in FP64, J from the Q62
 // fixed-point table jtabq on the integer pipe. Cd holds 8 x 16 x Npad fp16 digits and Ce
 // (Npad / 512) x 16 exponents, both written here from c (Npad = N rounded up to a multiple of 512).
 constexpr int kNearTcMinRhs = 8;
+constexpr int kNearTcRhs = 16;  // vectors per tensor-core near-field launch
 // df: a DF64 plan (7 digits and 7 diagonals: products to about 2^-46 of the chunk scale).
 void launch_near_tc(bool df, const NearItem* items, int64_t nitems, const NearRow* mrows, int64_t nmrows,
                     const int64_t* nend, int64_t N, double* partial, int nrhs, const double* c, int64_t ldc, void* Cd,
                     int* Ce, int64_t Npad, double* f, int64_t ldf, const double* r, const double* om,
                     const long long* jtabq, int64_t jt_n, int deg, cudaStream_t st);
 // Near field of DF64 plans in double-float on the FP32 pipe: r, om and jtab hold (high, low)
-// float pairs of the FP64 tables, cd the coefficients as pairs ([nrhs][N]); partial sums and
-// outputs are FP64.
+// float pairs of the FP64 tables, cd the coefficients as pairs ([nrhs][N]) scaled by 2^-cexp[r];
+// partial sums and outputs are FP64, scaled back.
 void launch_near_df(const NearItem* items, int64_t nitems, const NearRow* mrows, int64_t nmrows,
                     const int64_t* nend, int64_t N, double* partial, int nrhs, const float2* cd, double* f,
                     int64_t ldf, const float2* r, const float2* om, const float2* jtab, int64_t jt_n, int deg,
-                    cudaStream_t st);
+                    const int* cexp, cudaStream_t st);
 
 }  // namespace hk

@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(256) k_near(const NearItem* __restrict__ items
                                               const CT* __restrict__ c, int64_t ldc, double* f, int64_t ldf,
                                               const R* __restrict__ r_true, const R* __restrict__ om_true,
                                               const R* __restrict__ jtab, const long long* __restrict__ jq,
-                                              int64_t jt_n, int deg) {
+                                              int64_t jt_n, int deg, const int* __restrict__ cexp) {
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= nitems) return;
@@ -109,7 +109,9 @@ __global__ void __launch_bounds__(256) k_near(const NearItem* __restrict__ items
 #pragma unroll
     for (int g = 0; g < G; ++g) {
       if (r0 + g >= nrhs) break;
-      if (it.slot < 0) f[(int64_t)(r0 + g) * ldf + k - 1] = acc[g];
+      // scaled coefficients (cexp): f gets the sum times 2^e; partial sums stay in the scaled
+      // range of R and the combine applies 2^e
+      if (it.slot < 0) f[(int64_t)(r0 + g) * ldf + k - 1] = cexp ? ldexp((double)acc[g], cexp[r0 + g]) : (double)acc[g];
       else partial[(it.slot + (int64_t)lane * it.ntile) * nrhs + (int64_t)(r0 + g) * it.ntile + it.t] = acc[g];
     }
   }
@@ -157,7 +159,8 @@ __global__ void __launch_bounds__(256) k_near_df(const NearItem* __restrict__ it
                                                  const int64_t* __restrict__ nend, int64_t N, double* partial,
                                                  int nrhs, const float2* __restrict__ cd, double* f, int64_t ldf,
                                                  const float2* __restrict__ r_true, const float2* __restrict__ om_true,
-                                                 const float2* __restrict__ jtab, int64_t jt_n, int deg) {
+                                                 const float2* __restrict__ jtab, int64_t jt_n, int deg,
+                                                 const int* __restrict__ cexp) {
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= nitems) return;
@@ -203,7 +206,7 @@ __global__ void __launch_bounds__(256) k_near_df(const NearItem* __restrict__ it
 #pragma unroll
     for (int g = 0; g < G; ++g) {
       if (r0 + g >= nrhs) break;
-      const double v = (double)hi[g] + (double)lo[g];
+      const double v = ldexp((double)hi[g] + (double)lo[g], cexp[r0 + g]);  // back from the scaled coefficients
       if (it.slot < 0) f[(int64_t)(r0 + g) * ldf + k - 1] = v;
       else partial[(it.slot + (int64_t)lane * it.ntile) * nrhs + (int64_t)(r0 + g) * it.ntile + it.t] = v;
     }
@@ -414,9 +417,11 @@ __global__ void __launch_bounds__(64, 7) k_near_tc(const NearItem* __restrict__ 
     }
 }
 
+// cexp (FP32 near fields of scaled coefficients): the partial sums of vector rr are in units of
+// 2^cexp[rr], applied to the row's total.
 template <class R>
 __global__ void k_near_combine(const NearRow* __restrict__ rows, int64_t nrows, const R* __restrict__ partial,
-                               int nrhs, double* f, int64_t ldf) {
+                               int nrhs, double* f, int64_t ldf, const int* __restrict__ cexp) {
   const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31, g = lane & 15, h = lane >> 4;
   if (w >= nrows) return;
@@ -428,7 +433,7 @@ __global__ void k_near_combine(const NearRow* __restrict__ rows, int64_t nrows, 
       for (int j = lane; j < row.npieces; j += 32) s += p[j];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-      if (lane == 0) f[(int64_t)rr * ldf + row.k - 1] = (double)s;
+      if (lane == 0) f[(int64_t)rr * ldf + row.k - 1] = cexp ? ldexp((double)s, cexp[rr]) : (double)s;
     }
     return;
   }
@@ -440,7 +445,7 @@ __global__ void k_near_combine(const NearRow* __restrict__ rows, int64_t nrows, 
       for (int j = h; j < row.npieces; j += 2) s += p[j];
     }
     s += __shfl_down_sync(0xffffffffu, s, 16);
-    if (h == 0 && rr < nrhs) f[(int64_t)rr * ldf + row.k - 1] = (double)s;
+    if (h == 0 && rr < nrhs) f[(int64_t)rr * ldf + row.k - 1] = cexp ? ldexp((double)s, cexp[rr]) : (double)s;
   }
 }
 
@@ -449,60 +454,62 @@ __global__ void k_near_combine(const NearRow* __restrict__ rows, int64_t nrows, 
 template <class R, class CT>
 void launch_near_t(const NearItem* items, int64_t nitems, const int64_t* nend, int64_t N, R* partial, int nrhs,
                    const CT* c, int64_t ldc, double* f, int64_t ldf, const R* r, const R* om, const R* jtab,
-                   const long long* jq, int64_t jt_n, int deg, cudaStream_t st) {
+                   const long long* jq, int64_t jt_n, int deg, const int* cexp, cudaStream_t st) {
   const int64_t threads = nitems * 32;
   const unsigned grid = (unsigned)((threads + 255) / 256);
   if (nrhs <= 1)
     k_near<R, 1><<<grid, 256, 0, st>>>(items, nitems, nend, N, partial, nrhs, c, ldc, f, ldf, r, om, jtab, jq, jt_n,
-                                        deg);
+                                        deg, cexp);
   else if (nrhs <= 2)
     k_near<R, 2><<<grid, 256, 0, st>>>(items, nitems, nend, N, partial, nrhs, c, ldc, f, ldf, r, om, jtab, jq, jt_n,
-                                        deg);
+                                        deg, cexp);
   else if (nrhs <= 4)
     k_near<R, 4><<<grid, 256, 0, st>>>(items, nitems, nend, N, partial, nrhs, c, ldc, f, ldf, r, om, jtab, jq, jt_n,
-                                        deg);
+                                        deg, cexp);
   else if (nrhs <= 8)
     k_near<R, 8><<<grid, 256, 0, st>>>(items, nitems, nend, N, partial, nrhs, c, ldc, f, ldf, r, om, jtab, jq, jt_n,
-                                        deg);
+                                        deg, cexp);
   else
     k_near<R, kMaxRhsGroup><<<grid, 256, 0, st>>>(items, nitems, nend, N, partial, nrhs, c, ldc, f, ldf, r, om, jtab,
-                                                  jq, jt_n, deg);
+                                                  jq, jt_n, deg, cexp);
 }
 
 template <class R>
 void launch_near(const NearItem* items, int64_t nitems, const NearRow* mrows, int64_t nmrows, const int64_t* nend,
                  int64_t N, R* partial, int nrhs, const double* c, int64_t ldc, const float* cf, double* f,
                  int64_t ldf, const R* r, const R* om, const R* jtab, const long long* jtabq, int64_t jt_n, int deg,
-                 cudaStream_t st) {
+                 const int* cexp, cudaStream_t st) {
   if (cf)
-    launch_near_t<R, float>(items, nitems, nend, N, partial, nrhs, cf, N, f, ldf, r, om, jtab, jtabq, jt_n, deg, st);
+    launch_near_t<R, float>(items, nitems, nend, N, partial, nrhs, cf, N, f, ldf, r, om, jtab, jtabq, jt_n, deg, cexp,
+                            st);
   else
     launch_near_t<R, double>(items, nitems, nend, N, partial, nrhs, c, ldc, f, ldf, r, om, jtab, jtabq, jt_n, deg,
-                             st);
+                             nullptr, st);
   if (nmrows > 0)
-    k_near_combine<R><<<(unsigned)((nmrows * 32 + 255) / 256), 256, 0, st>>>(mrows, nmrows, partial, nrhs, f, ldf);
+    k_near_combine<R><<<(unsigned)((nmrows * 32 + 255) / 256), 256, 0, st>>>(mrows, nmrows, partial, nrhs, f, ldf,
+                                                                           cf ? cexp : nullptr);
 }
 
 void launch_near_df(const NearItem* items, int64_t nitems, const NearRow* mrows, int64_t nmrows,
                     const int64_t* nend, int64_t N, double* partial, int nrhs, const float2* cd, double* f,
                     int64_t ldf, const float2* r, const float2* om, const float2* jtab, int64_t jt_n, int deg,
-                    cudaStream_t st) {
+                    const int* cexp, cudaStream_t st) {
   const int64_t threads = nitems * 32;
   const unsigned grid = (unsigned)((threads + 255) / 256);
   if (nrhs <= 1)
-    k_near_df<1><<<grid, 256, 0, st>>>(items, nitems, nend, N, partial, nrhs, cd, f, ldf, r, om, jtab, jt_n, deg);
+    k_near_df<1><<<grid, 256, 0, st>>>(items, nitems, nend, N, partial, nrhs, cd, f, ldf, r, om, jtab, jt_n, deg, cexp);
   else if (nrhs <= 2)
-    k_near_df<2><<<grid, 256, 0, st>>>(items, nitems, nend, N, partial, nrhs, cd, f, ldf, r, om, jtab, jt_n, deg);
+    k_near_df<2><<<grid, 256, 0, st>>>(items, nitems, nend, N, partial, nrhs, cd, f, ldf, r, om, jtab, jt_n, deg, cexp);
   else if (nrhs <= 4)
-    k_near_df<4><<<grid, 256, 0, st>>>(items, nitems, nend, N, partial, nrhs, cd, f, ldf, r, om, jtab, jt_n, deg);
+    k_near_df<4><<<grid, 256, 0, st>>>(items, nitems, nend, N, partial, nrhs, cd, f, ldf, r, om, jtab, jt_n, deg, cexp);
   else if (nrhs <= 8)
-    k_near_df<8><<<grid, 256, 0, st>>>(items, nitems, nend, N, partial, nrhs, cd, f, ldf, r, om, jtab, jt_n, deg);
+    k_near_df<8><<<grid, 256, 0, st>>>(items, nitems, nend, N, partial, nrhs, cd, f, ldf, r, om, jtab, jt_n, deg, cexp);
   else
     k_near_df<kMaxRhsGroup><<<grid, 256, 0, st>>>(items, nitems, nend, N, partial, nrhs, cd, f, ldf, r, om, jtab,
-                                                  jt_n, deg);
+                                                  jt_n, deg, cexp);
   if (nmrows > 0)
     k_near_combine<double><<<(unsigned)((nmrows * 32 + 255) / 256), 256, 0, st>>>(mrows, nmrows, partial, nrhs, f,
-                                                                                ldf);
+                                                                                ldf, nullptr);
 }
 
 void launch_near_tc(bool df, const NearItem* items, int64_t nitems, const NearRow* mrows, int64_t nmrows,
@@ -519,15 +526,16 @@ void launch_near_tc(bool df, const NearItem* items, int64_t nitems, const NearRo
                                                                 r, om, jtabq, jt_n, deg);
   if (nmrows > 0)
     k_near_combine<double><<<(unsigned)((nmrows * 32 + 255) / 256), 256, 0, st>>>(mrows, nmrows, partial, nrhs, f,
-                                                                                ldf);
+                                                                                ldf, nullptr);
 }
 
 template void launch_near<double>(const NearItem*, int64_t, const NearRow*, int64_t, const int64_t*, int64_t,
                                   double*, int, const double*, int64_t, const float*, double*, int64_t,
                                   const double*, const double*, const double*, const long long*, int64_t, int,
-                                  cudaStream_t);
+                                  const int*, cudaStream_t);
 template void launch_near<float>(const NearItem*, int64_t, const NearRow*, int64_t, const int64_t*, int64_t, float*,
                                  int, const double*, int64_t, const float*, double*, int64_t, const float*,
-                                 const float*, const float*, const long long*, int64_t, int, cudaStream_t);
+                                 const float*, const float*, const long long*, int64_t, int, const int*,
+                                 cudaStream_t);
 
 }  // namespace hk

@@ -349,3 +349,94 @@ def test_rejects_bad_arguments():
         plan.exec(torch.zeros(100, dtype=torch.float32, device="cuda"))
     with pytest.raises(RuntimeError, match="EINVAL"):
         plan.exec(torch.zeros((2, 100), dtype=torch.float64, device="cuda"))  # nrhs > max_nrhs
+
+
+# ---------------------------------------------------------------------------------------------
+# Scale: the transform is linear, so c 2^s must give f 2^s within the same relative bar in every
+# precision. FP32 and double-float stages scale each vector by a power of two from its largest
+# |c_n|; without that, 2^120 overflows FP32 and 2^-120 sinks into its subnormals.
+# ---------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("nrhs", [1, 16])
+@pytest.mark.parametrize("eps,precision", [(1e-15, "auto"), (1e-8, "auto"), (1e-4, "auto"), (1e-15, "mixed"),
+                                           (1e-8, "mixed"), (1e-5, "fp32")])
+def test_scaled_coefficients(eps, precision, nrhs):
+    N = 9000
+    c = coefficients("normal", N, nrhs, 7800)
+    ref = oracle.transform("dht", 0, N, c)
+    l1 = np.abs(c).sum(axis=1, keepdims=True)
+    plan = hk.Plan("dht", 0, N, eps, max_nrhs=nrhs, precision=precision)
+    for s in (120, 60, -60, -120):
+        f = plan.exec(torch.from_numpy(np.ldexp(c, s)).cuda()).cpu().numpy()
+        err = np.abs(np.ldexp(f, -s) - ref)
+        assert np.all(np.isfinite(f)), s
+        assert np.all(err <= 10 * eps * l1), (s, (err / (eps * l1)).max())
+
+
+@pytest.mark.parametrize("eps,precision", [(1e-15, "auto"), (1e-4, "auto"), (1e-8, "mixed")])
+def test_coefficients_spanning_2p200(eps, precision):
+    # one vector whose entries range over 2^-100 .. 2^100 (uniform exponents)
+    N = 6000
+    rng = np.random.default_rng(7900)
+    c = (rng.uniform(0.5, 1.0, N) * np.where(rng.random(N) < 0.5, -1.0, 1.0)
+         * np.ldexp(1.0, rng.integers(-100, 101, N))).reshape(1, N)
+    f, plan = _run("dht", 0, N, eps, c, precision=precision)
+    ref = oracle.transform("dht", 0, N, c)
+    assert np.all(np.isfinite(f))
+    assert np.all(np.abs(f - ref) <= 10 * eps * np.abs(c).sum())
+
+
+# ---------------------------------------------------------------------------------------------
+# The workload table at its stated sizes and batches
+# ---------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("precision", ["auto", "mixed"])
+@pytest.mark.parametrize("eps", [1e-15, 1e-8])
+def test_benchmarked_configuration(eps, precision):
+    # DHT-0 at N = 2^20 with 16 standard normal vectors per execution (the tensor-core near field,
+    # the low-rank blocks and, for MIXED, the precision lanes), on 64 seeded rows
+    N, B = 2 ** 20, 16
+    c = coefficients("normal", N, B, 4 * 1000 + 100)
+    rows = sample_rows(N, 64, 31)
+    _check("dht", 0, N, eps, c, rows=rows, precision=precision)
+
+
+@pytest.mark.parametrize("eps", [1e-15, 1e-4])
+def test_dht_128_vectors(eps):
+    # DHT-0, N = 2^16, 128 vectors in one execution: eight tensor-core groups of 16
+    N = 2 ** 16
+    c = coefficients("normal", N, 128, 4 * 1000 + 128)
+    rows = sample_rows(N, 64, 37)
+    _check("dht", 0, N, eps, c, rows=rows)
+
+
+@pytest.mark.parametrize("nu,eps,kind", [(0, 1e-15, "uniform"), (4, 1e-15, "decaying"), (0, 1e-8, "uniform"),
+                                         (4, 1e-4, "uniform")])
+def test_schlomilch_2p20_32_vectors(nu, eps, kind):
+    # Schlomilch omega_n = (n + nu) pi at N = 2^20 with a batch of 32 vectors
+    N = 2 ** 20
+    c = coefficients(kind, N, 32, 2 * 1000 + 20 + nu)
+    rows = sample_rows(N, 64, 41)
+    _check("schlomilch", nu, N, eps, c, rows=rows)
+
+
+def test_group_remainder_below_tensor_core_minimum():
+    # 21 vectors: one tensor-core group of 16 and a remainder of 5 on the FMA kernels
+    N = 20000
+    c = coefficients("normal", N, 21, 7950)
+    _check("dht", 0, N, 1e-15, c)
+
+
+@pytest.mark.parametrize("nu", [1, 2])
+@pytest.mark.parametrize("eps,grid", [(1e-15, "unit"), (1e-8, "unit"), (1e-15, "paper")])
+def test_fourier_bessel_higher_orders(nu, eps, grid):
+    # Fourier-Bessel with nu > 0 (Section 5: J_nu at the roots of J_0), every output
+    N = 5000
+    c = coefficients("uniform", N, 2, 3100 + nu)
+    _check("fourier_bessel", nu, N, eps, c, grid=grid)
+
+
+@pytest.mark.parametrize("nu", [1, 2])
+def test_fourier_bessel_higher_orders_large(nu):
+    N = 2 ** 18
+    c = coefficients("uniform", N, 4, 3200 + nu)
+    rows = sample_rows(N, 48, 43)
+    _check("fourier_bessel", nu, N, 1e-15, c, rows=rows)

@@ -3,6 +3,7 @@ requests run alone, within 10 eps sum|c_n|; graph replay, eviction and rejection
 import numpy as np
 import pytest
 
+import oracle
 from hankel_inputs import coefficients
 
 torch = pytest.importorskip("torch")
@@ -146,4 +147,20 @@ def test_burst_of_submissions_stays_one_batch():
     ref = _alone("dht", 0, N, 1e-8, np.concatenate(cs))
     for i, (_, f) in enumerate(tickets):
         assert np.all(np.abs(f - ref[i]) <= 10 * 1e-8 * np.abs(cs[i]).sum())
+    srv.close()
+
+
+@pytest.mark.parametrize("precision", ["auto", "mixed"])
+def test_served_results_against_oracle(precision):
+    # every request of a mixed stream, served in packed batches on several streams with graph
+    # replay, against the oracle directly
+    reqs = _requests(11, 24)
+    srv = hk.Server(streams=4, max_batch=8, use_graphs=True, precision=precision)
+    tickets = [srv.submit(t, nu, N, eps, c) for (t, nu, N, eps, c) in reqs]
+    for tk, _ in tickets:
+        srv.wait(tk)
+    for (task, nu, N, eps, c), (_, f) in zip(reqs, tickets):
+        ref = oracle.transform(task, nu, N, c)
+        bound = 10 * eps * np.abs(c).sum(axis=1, keepdims=True)
+        assert np.all(np.abs(f.reshape(c.shape) - ref) <= bound), (task, N, eps)
     srv.close()

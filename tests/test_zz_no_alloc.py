@@ -3,9 +3,9 @@
 Callers whose device memory all belongs to their own pool allocator, or whose transform loop
 must never enter the CUDA allocator, cannot have the library allocate when they run a
 transform. hankel_exec_static serves them from a static device array inside the library.
-These tests call it through the C ABI, twice in a row on the same plan, and compare each
-result with hankel_exec's within the parity tolerance 10 eps sum|c_n|. The file is named to
-be collected last.
+These tests call it through the C ABI, three times in a row on the same plan, compare each
+result with hankel_exec's within the parity tolerance 10 eps sum|c_n|, and check that the
+device's free memory stays the same across the calls. The file is named to be collected last.
 """
 import ctypes
 
@@ -36,13 +36,19 @@ def test_static_scratch_matches_exec(task, nu, N, eps):
     _lib.check(lib.hankel_exec(plan.handle, ctypes.c_void_p(c.data_ptr()), ctypes.c_void_p(ref.data_ptr()), sp),
                "hankel_exec")
     tol = 10.0 * eps * float(c.abs().sum())
-    for _ in range(2):
+    free_after_first = None
+    for _ in range(3):
         out.fill_(float("nan"))  # a result left over from an earlier call cannot pass
         _lib.check(lib.hankel_exec_static(plan.handle, ctypes.c_void_p(c.data_ptr()),
                                           ctypes.c_void_p(out.data_ptr()), sp), "hankel_exec_static")
         torch.cuda.synchronize()
         err = float((out - ref).abs().max())
         assert np.isfinite(err) and err <= tol, (err, tol)
+        # the calls allocate nothing: the device's free memory does not move after the first
+        free = torch.cuda.mem_get_info()[0]
+        if free_after_first is None:
+            free_after_first = free
+        assert free == free_after_first
 
 
 def test_static_scratch_rejects_oversized_plans():
