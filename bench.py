@@ -3,11 +3,13 @@
 
 One step = one discrete Hankel transform of order 0 (Section 6, Eq. 25) at eps = 1e-15 plus
 one at eps = 1e-8, each over a batch of ``--nrhs`` seeded standard-normal coefficient vectors
-(the paper's Gaussian experiments): the served/batched form. value = coefficients transformed /
-device time with the inputs resident. The line also carries the plain form (one vector per
-execution, FP64) measured the same way, and both forms driven through the library's request
-loop with host arrays: throughput when all requests arrive at once (e2e) and p50/p99 latency
-under Poisson arrivals.
+(the paper's Gaussian experiments): the served/batched form, every stage FP64 (the AUTO
+precision below eps = 1e-5). value = coefficients transformed / device time with the inputs
+resident. The line also carries the plain form (one vector per execution, FP64) measured the
+same way, the opt-in mixed-precision batched form (double-float and FP32 terms) as a separate
+key with its own error against the oracle, and both FP64 forms driven through the library's
+request loop with host arrays: throughput when all requests arrive at once (e2e) and p50/p99
+latency under Poisson arrivals.
 
 Prints one JSON line (rank 0). ``--impl reference`` times the CPU oracle instead (direct
 O(N^2) FP64 summation on this host's cores) on a bounded sample of rows of the same workload.
@@ -67,6 +69,7 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="dht", choices=["dht", "mix"], help="mix: the serving-mix workload")
     ap.add_argument("--quick", action="store_true", help="batched form only (no plain form, serving runs or CPU leg)")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the opt-in mixed-precision batched form")
     ap.add_argument("--mix-requests", type=int, default=150)
     ap.add_argument("--mix-rate", type=float, default=100.0, help="Poisson arrivals per second")
     ap.add_argument("--mix-nmin", type=int, default=10)
@@ -175,8 +178,8 @@ def workload_config(args):
     B = args.nrhs
     return {"workload": "dht0_N%d_eps%s_batch%d" % (args.N, "+".join(args.eps.split(",")), B),
             "N": args.N, "eps": [float(e) for e in args.eps.split(",")], "batch": B,
-            "form": "served/batched: %d vectors per execution per plan, precision by eps (FP64 below 1e-11, "
-                    "double-float transforms below 1e-5, FP32 above)" % B,
+            "form": "served/batched: %d vectors per execution per plan, every stage FP64 (AUTO precision "
+                    "below eps = 1e-5)" % B,
             "l2": "flushed between timed steps (256 MB write)", "coefficients": "N(0,1) seeded"}
 
 
@@ -364,7 +367,7 @@ def run_ours(args):
         for p in plain:
             p.destroy()
 
-    # served form: batches of B vectors per plan, precision chosen by eps
+    # served form: batches of B vectors per plan, every stage FP64 (AUTO below eps = 1e-5)
     cB_host = coefficients("normal", N, B, seed_for(4, 100 + rank))
     cB = torch.from_numpy(cB_host).to(dev)
     plans = [hk.Plan("dht", 0, N, e, max_nrhs=B) for e in eps_list]
@@ -382,11 +385,137 @@ def run_ours(args):
     coeffs_per_step = len(plans) * N * B
     value, total_ms = aggregate(world, coeffs_per_step, args.steps, sum(step_ms), dev)
 
-    # dominant kernel: the FFT passes of the transform class (FP64, double-float or FP32) that
-    # takes the most time; the other classes are reported beside it
-    precs = [p.info["precision"] for p in plans]
+    # launches of the stage-timed steps, as many as the timed region's
     launches = sum(st[k]["launches"] for st in stats for k in st)
     stage_ms = {k: round(sum(st[k]["ms"] for st in stats) / args.steps, 3) for k in stats[0]}
+    roofline = fft_roofline(stats, args.steps)
+    precs = [p.info["precision"] for p in plans]
+    terms = term_counts(plans)
+    dtype = dtype_of(precs, terms)
+    # accuracy of the timed plans on the CPU baseline's vector and rows (checked by the oracle
+    # there, outside every timed region)
+    err_c = coefficients("normal", N, 1, seed_for(4, 99))
+    want_err = world == 1 and not args.no_cpu_baseline and not args.quick
+    ce = torch.from_numpy(err_c).to(dev)
+    f_err = [p.exec(ce).cpu().numpy()[0] for p in plans] if want_err else []
+    for p in plans:
+        p.destroy()
+
+    # the opt-in mixed-precision batched form (double-float plans at 1e-8, double-float and FP32
+    # low-rank terms): reported beside the FP64 value, never as it
+    mixed = None
+    if not args.no_mixed:
+        mplans = [hk.Plan("dht", 0, N, e, max_nrhs=B, precision="mixed") for e in eps_list]
+        m_step, m_plan, _ = timed_steps(mplans, cB, fs, stream, args.steps, args.warmup, flush, False)
+        _, _, m_stats = timed_steps(mplans, cB, fs, stream, 1, 0, flush, True)
+        m_value = coeffs_per_step * len(m_step) / (sum(m_step) / 1000.0)
+        m_terms = term_counts(mplans)
+        m_err = [p.exec(ce).cpu().numpy()[0] for p in mplans] if want_err else []
+        mixed = {"value": m_value, "unit": "coeffs/s", "ms_per_step": sum(m_step) / len(m_step),
+                 "dtype": dtype_of([p.info["precision"] for p in mplans], m_terms),
+                 "over_fp64_value": m_value / value,
+                 "per_eps_ms": {str(e): statistics.mean(m) for e, m in zip(eps_list, m_plan)},
+                 "term_precision": {"fp64": m_terms[0], "df64": m_terms[1], "fp32": m_terms[2]},
+                 "stage_ms_per_step": {k: round(sum(st[k]["ms"] for st in m_stats), 3) for k in m_stats[0]},
+                 "form": "precision='mixed': narrower than FP64 below eps = 1e-5 by explicit opt-in"}
+        for p in mplans:
+            p.destroy()
+    del fs
+
+    # request streams through the library's server: end to end with host arrays
+    reqs = []
+    nreq = args.requests if args.requests > 0 else B * len(eps_list)
+    for i in range(nreq):
+        e = eps_list[i % len(eps_list)]
+        reqs.append((e, pinned_like(coefficients("normal", N, 1, seed_for(4, 200 + i))[0])))
+    served_kw = dict(streams=4, max_batch=B, use_graphs=True, precision="auto")
+    plain_kw = dict(streams=1, max_batch=1, use_graphs=False, precision="fp64", pack=False)
+    if args.quick:
+        served_e2e = plain_e2e = served_cps_p = plain_cps_p = rate = None
+        served_sat_lat = plain_sat_lat = served_lat = plain_lat = []
+    else:
+        served_e2e, served_sat_lat = serve_stream(hk, served_kw, reqs, 0.0, 1, rounds=args.steps)
+        plain_e2e, plain_sat_lat = serve_stream(hk, plain_kw, reqs, 0.0, 1, rounds=args.steps)
+        rate = args.rate if args.rate > 0 else 0.7 * plain_e2e / N  # 70 % of the plain form's capacity
+        served_cps_p, served_lat = serve_stream(hk, served_kw, reqs, rate, 2)
+        plain_cps_p, plain_lat = serve_stream(hk, plain_kw, reqs, rate, 2)
+
+    term_split = {"fp64": terms[0], "df64": terms[1], "fp32": terms[2],
+                  "unit": "far-field transforms per right-hand side, summed over blocks and plans"}
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": "coeffs/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+        "config": workload_config(args),
+        "per_eps": {str(e): {"batch_ms": statistics.mean(m),
+                             "coeffs_per_s": N * B / (statistics.mean(m) / 1000.0),
+                             "plain_ms": statistics.mean(pm) if plain_cps else None,
+                             "plain_coeffs_per_s": N / (statistics.mean(pm) / 1000.0) if plain_cps else None,
+                             "mixed_batch_ms": mixed["per_eps_ms"][str(e)] if mixed else None}
+                    for e, m, pm in zip(eps_list, plan_ms, p_plan)},
+        "plain_fp64": {"coeffs_per_s": plain_cps, "ms_per_step": (sum(p_step) / len(p_step)) if plain_cps else None,
+                       "form": "one vector per execution, every stage FP64"},
+        "served_over_plain": value / plain_cps if plain_cps else None,
+        "mixed_precision": mixed,
+        "stage_ms_per_step": stage_ms,
+        "stage_steps_ms": sum(ev_step_ms) / len(ev_step_ms),
+        "term_precision": term_split,
+        "roofline": roofline,
+        "e2e": {"value": served_e2e, "unit": "coeffs/s", "h2d_bytes_per_step": coeffs_per_step * 8,
+                "d2h_bytes_per_step": coeffs_per_step * 8,
+                "form": "hankel_server (FP64 plans), %d single-vector requests (%d per eps) submitted at once, "
+                        "page-locked host arrays (inputs and outputs); %d such rounds after 2 untimed ones"
+                        % (len(reqs), len(reqs) // len(eps_list), args.steps),
+                "plain_value": plain_e2e},
+        "latency_ms": {"rate_per_s": rate, "requests": len(reqs),
+                       "served": {"p50": pct(served_lat, 50), "p99": pct(served_lat, 99),
+                                  "coeffs_per_s": served_cps_p},
+                       "plain": {"p50": pct(plain_lat, 50), "p99": pct(plain_lat, 99),
+                                 "coeffs_per_s": plain_cps_p},
+                       "saturated": {"served_p50": pct(served_sat_lat, 50), "served_p99": pct(served_sat_lat, 99),
+                                     "plain_p50": pct(plain_sat_lat, 50), "plain_p99": pct(plain_sat_lat, 99)}},
+        "gpu_launches": launches,
+        "clocks": clocks.summary(),
+        "wall_s_timed": wall,
+    }
+    if want_err:
+        base = cpu_baseline(N, args.cpu_rows, seed_for(4, 99))
+        ref = base.pop("f")
+        line["cpu_baseline"] = base
+        # max over the sampled rows of |f - f_oracle| / (eps sum|c|); the parity bar is 10
+        l1 = float(np.abs(err_c).sum())
+        rows = base_rows(N, args.cpu_rows, seed_for(4, 99))
+        line["error_vs_oracle"] = {str(e): float(np.max(np.abs(f[rows] - ref)) / (e * l1))
+                                   for e, f in zip(eps_list, f_err)}
+        if mixed:
+            mixed["error_vs_oracle"] = {str(e): float(np.max(np.abs(f[rows] - ref)) / (e * l1))
+                                        for e, f in zip(eps_list, m_err)}
+    print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def term_counts(plans):
+    """Far-field transforms per right-hand side in FP64, double-float and FP32, over all plans."""
+    terms = [0, 0, 0]
+    for p in plans:
+        for b in p.blocks():
+            for i in range(3):
+                terms[i] += b["terms"][i]
+    return terms
+
+
+def dtype_of(precs, terms):
+    kinds = ["f64" if (1 in precs or terms[0]) else None, "df64" if (3 in precs or terms[1]) else None,
+             "f32" if (2 in precs or terms[2]) else None]
+    return "+".join(k for k in kinds if k)
+
+
+def fft_roofline(stats, steps):
+    """Roofline entry of the transform class (FP64, double-float or FP32 passes) that takes the
+    most time, with the other classes under "others"."""
 
     def fft_entry(k2):
         ms2 = sum(st[k2]["ms"] for st in stats)
@@ -395,7 +524,7 @@ def run_ours(args):
         by = sum(st[k2]["bytes"] for st in stats)
         ach = fl / (ms2 / 1000.0) / 1e9 if ms2 > 0 else 0.0
         gbs = by / (ms2 / 1000.0) / 1e9 if ms2 > 0 else None
-        common = {"fft_ms_per_step": ms2 / args.steps, "launches": nl, "hbm_gbs_of_passes": gbs,
+        common = {"fft_ms_per_step": ms2 / steps, "launches": nl, "hbm_gbs_of_passes": gbs,
                   "flops_model": "5 F log2 F per column transform, plus 6 F per spectrum product folded "
                                  "into an inverse transform"}
         if k2 == "fft":
@@ -424,95 +553,10 @@ def run_ours(args):
 
     classes = [k2 for k2 in ("fft", "fft_df64", "fft_fp32") if sum(st[k2]["ms"] for st in stats) > 0]
     dominant = max(classes, key=lambda k2: sum(st[k2]["ms"] for st in stats)) if classes else "fft"
-    terms = [0, 0, 0]
-    for p in plans:
-        for b in p.blocks():
-            for i in range(3):
-                terms[i] += b["terms"][i]
-    kinds = ["f64" if (1 in precs or terms[0]) else None, "df64" if (3 in precs or terms[1]) else None,
-             "f32" if (2 in precs or terms[2]) else None]
-    dtype = "+".join(k for k in kinds if k)
-    # accuracy of the timed plans on the CPU baseline's vector and rows (checked by the oracle
-    # there, outside every timed region)
-    err_c = coefficients("normal", N, 1, seed_for(4, 99))
-    f_err = []
-    if world == 1 and not args.no_cpu_baseline and not args.quick:
-        ce = torch.from_numpy(err_c).to(dev)
-        for p in plans:
-            f_err.append(p.exec(ce).cpu().numpy()[0])
-    for p in plans:
-        p.destroy()
-    del fs
-
-    # request streams through the library's server: end to end with host arrays
-    reqs = []
-    nreq = args.requests if args.requests > 0 else B * len(eps_list)
-    for i in range(nreq):
-        e = eps_list[i % len(eps_list)]
-        reqs.append((e, pinned_like(coefficients("normal", N, 1, seed_for(4, 200 + i))[0])))
-    served_kw = dict(streams=4, max_batch=B, use_graphs=True, precision="auto")
-    plain_kw = dict(streams=1, max_batch=1, use_graphs=False, precision="fp64", pack=False)
-    if args.quick:
-        served_e2e = plain_e2e = served_cps_p = plain_cps_p = rate = None
-        served_sat_lat = plain_sat_lat = served_lat = plain_lat = []
-    else:
-        served_e2e, served_sat_lat = serve_stream(hk, served_kw, reqs, 0.0, 1, rounds=args.steps)
-        plain_e2e, plain_sat_lat = serve_stream(hk, plain_kw, reqs, 0.0, 1, rounds=args.steps)
-        rate = args.rate if args.rate > 0 else 0.7 * plain_e2e / N  # 70 % of the plain form's capacity
-        served_cps_p, served_lat = serve_stream(hk, served_kw, reqs, rate, 2)
-        plain_cps_p, plain_lat = serve_stream(hk, plain_kw, reqs, rate, 2)
-
     roofline = fft_entry(dominant)
     names = {"fft": "fp64_transforms", "fft_df64": "df64_transforms", "fft_fp32": "fp32_transforms"}
     roofline["others"] = {names[k2]: fft_entry(k2) for k2 in classes if k2 != dominant}
-    term_split = {"fp64": terms[0], "df64": terms[1], "fp32": terms[2],
-                  "unit": "far-field transforms per right-hand side, summed over blocks and plans"}
-    if rank != 0:
-        return
-    line = {
-        "metric": METRIC, "value": value, "unit": "coeffs/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
-        "config": workload_config(args),
-        "per_eps": {str(e): {"batch_ms": statistics.mean(m),
-                             "coeffs_per_s": N * B / (statistics.mean(m) / 1000.0),
-                             "plain_ms": statistics.mean(pm) if plain_cps else None}
-                    for e, m, pm in zip(eps_list, plan_ms, p_plan)},
-        "plain_fp64": {"coeffs_per_s": plain_cps, "ms_per_step": (sum(p_step) / len(p_step)) if plain_cps else None,
-                       "form": "one vector per execution, every stage FP64"},
-        "served_over_plain": value / plain_cps if plain_cps else None,
-        "stage_ms_per_step": stage_ms,
-        "stage_steps_ms": sum(ev_step_ms) / len(ev_step_ms),
-        "term_precision": term_split,
-        "roofline": roofline,
-        "e2e": {"value": served_e2e, "unit": "coeffs/s", "h2d_bytes_per_step": coeffs_per_step * 8,
-                "d2h_bytes_per_step": coeffs_per_step * 8,
-                "form": "hankel_server, %d single-vector requests (%d per eps) submitted at once, page-locked host "
-                        "arrays (inputs and outputs); %d such rounds after 2 untimed ones"
-                        % (len(reqs), len(reqs) // len(eps_list), args.steps),
-                "plain_value": plain_e2e},
-        "latency_ms": {"rate_per_s": rate, "requests": len(reqs),
-                       "served": {"p50": pct(served_lat, 50), "p99": pct(served_lat, 99),
-                                  "coeffs_per_s": served_cps_p},
-                       "plain": {"p50": pct(plain_lat, 50), "p99": pct(plain_lat, 99),
-                                 "coeffs_per_s": plain_cps_p},
-                       "saturated": {"served_p50": pct(served_sat_lat, 50), "served_p99": pct(served_sat_lat, 99),
-                                     "plain_p50": pct(plain_sat_lat, 50), "plain_p99": pct(plain_sat_lat, 99)}},
-        "gpu_launches": launches,
-        "clocks": clocks.summary(),
-        "wall_s_timed": wall,
-    }
-    if world == 1 and not args.no_cpu_baseline and not args.quick:
-        base = cpu_baseline(N, args.cpu_rows, seed_for(4, 99))
-        ref = base.pop("f")
-        line["cpu_baseline"] = base
-        # max over the sampled rows of |f - f_oracle| / (eps sum|c|); the parity bar is 10
-        l1 = float(np.abs(err_c).sum())
-        line["error_vs_oracle"] = {str(e): float(np.max(np.abs(f[base_rows(N, args.cpu_rows, seed_for(4, 99))] - ref))
-                                                / (e * l1)) for e, f in zip(eps_list, f_err)}
-    print(json.dumps(line))
-    if world > 1:
-        torch.distributed.destroy_process_group()
+    return roofline
 
 
 MIX_TASKS = [("schlomilch", 0), ("schlomilch", 1), ("fourier_bessel", 0), ("dht", 0)]
