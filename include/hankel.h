@@ -107,6 +107,9 @@ enum hankel_status {
                                       away from the near field) */
 #define HANKEL_FLAG_UNIFORM_TERMS 64u /* MIXED plans: every far-field term in the plan precision (no per-term
                                          lowering of small low-rank terms) */
+#define HANKEL_FLAG_NO_AUTOTUNE 128u /* split every transform into launches by the built-in rule; by default
+                                        the plan measures the candidate splits of each transform length it
+                                        runs (hankel_fft_shape) once per GPU model and uses the fastest */
 
 /* Options for hankel_plan_ex(). Fill with hankel_options_default() first. */
 typedef struct {
@@ -145,7 +148,23 @@ typedef struct {
   size_t device_bytes;    /* device memory held by the plan (tables + workspace) */
   size_t workspace_bytes; /* part of device_bytes used as transform workspace */
   int64_t block_cols;     /* transforms per right-hand side summed over blocks (hankel_block.ncols) */
+  int fft_shapes;         /* distinct (precision, length, column bucket) transform shapes the plan runs
+                             (hankel_plan_fft_shapes) */
 } hankel_info;
+
+/* How one kind of multi-column FFT of the far field is split into kernel launches. Not a step of
+ * the paper (whose transforms are DCT/DST library calls); the autotuner of this library measures
+ * the candidates on the GPU. */
+typedef struct {
+  int precision;       /* arithmetic of the transform: HANKEL_PREC_FP64, _DF64 or _FP32 */
+  int log2_len;        /* log2 of the transform length F */
+  int col_bucket;      /* floor(log2(columns per launch)), clamped to 0..16 (hankel_tune_bucket) */
+  int one_launch;      /* 1: the whole transform in one launch (F <= 4096) */
+  int npass;           /* otherwise 2..4 passes, */
+  int log2_radix[4];   /* of radix 2^log2_radix[i] (5..8 each, summing to log2_len), first to last */
+  double ms_default;   /* measured time of the built-in split on the tuning columns (0: not measured) */
+  double ms_chosen;    /* measured time of the chosen split */
+} hankel_fft_shape;
 
 /* One far-field block of the partition, 1-based inclusive index ranges. */
 typedef struct {
@@ -268,6 +287,26 @@ int hankel_plan_entry(hankel_plan_t p, int64_t k, int64_t n, double* value, int*
  * to every entry. Where z = r_k omega_n is below s_{nu,M} it is not eps-accurate (Section 3.1;
  * at r_k = 0 it is not finite). For tests of the partition. Host only. Errors: EINVAL. */
 int hankel_plan_expansion_entry(hankel_plan_t p, int64_t k, int64_t n, double* value);
+
+/* The transform shapes a plan runs: up to `cap` entries into out, *count receives the number.
+ * Each says how the plan's transforms of one precision, length and column bucket are split into
+ * launches, and the times the autotuner measured (zero when the shape came from the built-in rule
+ * or from the cache without a measurement in this process). Host only. */
+int hankel_plan_fft_shapes(hankel_plan_t p, hankel_fft_shape* out, int cap, int* count);
+
+/* The autotuner's shape cache, keyed by (GPU name, precision, log2_len, col_bucket). Plans look a
+ * key up before measuring it, and store what they measure. When the environment variable
+ * HANKEL_TUNE_CACHE names a file, the first plan of the process loads it and every new entry is
+ * appended to it. Host only; no GPU needed. Errors: EINVAL (NULL or empty name, a name with a
+ * newline, an unreadable or unwritable path). */
+int hankel_tune_cache_put(const char* gpu_name, const hankel_fft_shape* s);
+int hankel_tune_cache_get(const char* gpu_name, int precision, int log2_len, int col_bucket, hankel_fft_shape* out,
+                          int* found);
+int hankel_tune_cache_save(const char* path);
+int hankel_tune_cache_load(const char* path);
+int hankel_tune_cache_clear(void);
+/* The column bucket of a launch of ncols columns: floor(log2(ncols)) clamped to 0..16. */
+int hankel_tune_bucket(int64_t ncols);
 
 /* Near-field prefix of row k (1-based): columns 1..*nend are summed directly. Host only. */
 int hankel_plan_near_prefix(hankel_plan_t p, int64_t k, int64_t* nend);

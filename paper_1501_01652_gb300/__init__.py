@@ -18,7 +18,7 @@ PRECISIONS = {"auto": 0, "fp64": 1, "fp32": 2, "df64": 3, "mixed": 4}
 
 
 def _options(task, nu, N, eps, grid="unit", gamma=None, precision="auto", max_nrhs=1, workspace_limit=0,
-             host_only=False, segment=True, prune=True, refine=True, lowrank=True, mixed_terms=True):
+             host_only=False, segment=True, prune=True, refine=True, lowrank=True, mixed_terms=True, autotune=True):
     lib = _lib.load()
     o = _lib.Options()
     _lib.check(lib.hankel_options_default(ctypes.byref(o), TASKS[task], int(nu), int(N), float(eps)),
@@ -32,7 +32,7 @@ def _options(task, nu, N, eps, grid="unit", gamma=None, precision="auto", max_nr
     o.flags = ((_lib.FLAG_HOST_ONLY if host_only else 0) | (0 if segment else _lib.FLAG_NO_SEGMENT)
                | (0 if prune else _lib.FLAG_ALL_COLUMNS)
                | (0 if refine else _lib.FLAG_NO_REFINE) | (0 if lowrank else _lib.FLAG_NO_LOWRANK)
-               | (0 if mixed_terms else _lib.FLAG_UNIFORM_TERMS))
+               | (0 if mixed_terms else _lib.FLAG_UNIFORM_TERMS) | (0 if autotune else _lib.FLAG_NO_AUTOTUNE))
     return o
 
 
@@ -82,18 +82,57 @@ def j0_zero_offsets(count):
     return b
 
 
+def tune_cache_put(gpu, precision, log2_len, col_bucket, radices=None, one_launch=False, ms_default=0.0,
+                   ms_chosen=0.0):
+    """Store an FFT launch split in the autotuner's cache (precision: "fp64", "df64" or "fp32")."""
+    s = _lib.FftShape()
+    s.precision, s.log2_len, s.col_bucket = PRECISIONS[precision], int(log2_len), int(col_bucket)
+    s.one_launch = 1 if one_launch else 0
+    radices = list(radices or [])
+    s.npass = len(radices)
+    for i, r in enumerate(radices[:4]):
+        s.log2_radix[i] = int(r)
+    s.ms_default, s.ms_chosen = float(ms_default), float(ms_chosen)
+    _lib.check(_lib.load().hankel_tune_cache_put(gpu.encode(), ctypes.byref(s)), "hankel_tune_cache_put")
+
+
+def tune_cache_get(gpu, precision, log2_len, col_bucket):
+    """The cached split for the key as a dict, or None."""
+    s = _lib.FftShape()
+    found = ctypes.c_int(0)
+    _lib.check(_lib.load().hankel_tune_cache_get(gpu.encode(), PRECISIONS[precision], int(log2_len), int(col_bucket),
+                                                 ctypes.byref(s), ctypes.byref(found)), "hankel_tune_cache_get")
+    return s.as_dict() if found.value else None
+
+
+def tune_cache_save(path):
+    _lib.check(_lib.load().hankel_tune_cache_save(str(path).encode()), "hankel_tune_cache_save")
+
+
+def tune_cache_load(path):
+    _lib.check(_lib.load().hankel_tune_cache_load(str(path).encode()), "hankel_tune_cache_load")
+
+
+def tune_cache_clear():
+    _lib.check(_lib.load().hankel_tune_cache_clear(), "hankel_tune_cache_clear")
+
+
+def tune_bucket(ncols):
+    return _lib.load().hankel_tune_bucket(int(ncols))
+
+
 class Plan:
     """A transform plan: f = J_nu(r omega^T) c for one task, order, size and accuracy."""
 
     def __init__(self, task, nu, N, eps, grid="unit", gamma=None, precision="auto", max_nrhs=1,
                  workspace_limit=0, host_only=False, segment=True, prune=True, refine=True, lowrank=True,
-                 mixed_terms=True):
+                 mixed_terms=True, autotune=True):
         self._lib = _lib.load()
         self._h = ctypes.c_void_p()
         self.task, self.nu, self.N, self.eps = task, int(nu), int(N), float(eps)
         self.max_nrhs = int(max_nrhs)
         o = _options(task, nu, N, eps, grid, gamma, precision, max_nrhs, workspace_limit, host_only, segment,
-                     prune, refine, lowrank, mixed_terms)
+                     prune, refine, lowrank, mixed_terms, autotune)
         _lib.check(self._lib.hankel_plan_ex(ctypes.byref(self._h), ctypes.byref(o)), "hankel_plan_ex")
 
     def __del__(self):
@@ -124,6 +163,15 @@ class Plan:
                      ncols=b.ncols, dropped=b.dropped, kept=b.kept, lowrank=bool(b.lowrank),
                      lowrank_err=b.lowrank_err, terms=(b.terms_fp64, b.terms_df64, b.terms_fp32))
                 for b in arr[:cnt.value]]
+
+    def fft_shapes(self):
+        """The transform shapes the plan runs (autotuned launch splits), as dicts."""
+        cnt = ctypes.c_int(0)
+        _lib.check(self._lib.hankel_plan_fft_shapes(self._h, None, 0, ctypes.byref(cnt)), "hankel_plan_fft_shapes")
+        arr = (_lib.FftShape * max(cnt.value, 1))()
+        _lib.check(self._lib.hankel_plan_fft_shapes(self._h, arr, cnt.value, ctypes.byref(cnt)),
+                   "hankel_plan_fft_shapes")
+        return [a.as_dict() for a in arr[:cnt.value]]
 
     def entry(self, k, n):
         """(value, is_far) of the plan's representation of matrix entry (k, n), 1-based."""

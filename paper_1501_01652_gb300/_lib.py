@@ -15,6 +15,7 @@ FLAG_ALL_COLUMNS = 8
 FLAG_NO_REFINE = 16
 FLAG_NO_LOWRANK = 32
 FLAG_UNIFORM_TERMS = 64
+FLAG_NO_AUTOTUNE = 128
 
 # Every function include/hankel.h declares.
 EXPORTED = [
@@ -26,6 +27,8 @@ EXPORTED = [
     "hankel_j0_zero_offsets", "hankel_plan_set_timing", "hankel_plan_stage_stats", "hankel_exec_static",
     "hankel_server_options_default", "hankel_server_create", "hankel_server_submit", "hankel_server_wait",
     "hankel_server_drain", "hankel_server_get_stats", "hankel_server_destroy",
+    "hankel_plan_fft_shapes", "hankel_tune_cache_put", "hankel_tune_cache_get", "hankel_tune_cache_save",
+    "hankel_tune_cache_load", "hankel_tune_cache_clear", "hankel_tune_bucket",
 ]
 STAGES = ["near", "gen", "fft", "pointwise", "out", "fft_df64", "fft_fp32"]
 
@@ -45,10 +48,22 @@ class Info(ctypes.Structure):
                 ("direct_cols", ctypes.c_int64), ("nblocks", ctypes.c_int), ("ncols", ctypes.c_int),
                 ("npairs", ctypes.c_int), ("near_count", ctypes.c_int64), ("far_count", ctypes.c_int64),
                 ("near_zmax", ctypes.c_double), ("device_bytes", ctypes.c_size_t),
-                ("workspace_bytes", ctypes.c_size_t), ("block_cols", ctypes.c_int64)]
+                ("workspace_bytes", ctypes.c_size_t), ("block_cols", ctypes.c_int64), ("fft_shapes", ctypes.c_int)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class FftShape(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("log2_len", ctypes.c_int), ("col_bucket", ctypes.c_int),
+                ("one_launch", ctypes.c_int), ("npass", ctypes.c_int), ("log2_radix", ctypes.c_int * 4),
+                ("ms_default", ctypes.c_double), ("ms_chosen", ctypes.c_double)]
+
+    def as_dict(self):
+        return {"precision": self.precision, "log2_len": self.log2_len, "col_bucket": self.col_bucket,
+                "one_launch": bool(self.one_launch),
+                "radices": [] if self.one_launch else list(self.log2_radix[:self.npass]),
+                "ms_default": self.ms_default, "ms_chosen": self.ms_chosen}
 
 
 class StageStat(ctypes.Structure):
@@ -123,6 +138,14 @@ def load():
         "hankel_server_get_stats": (i32, [vp, ctypes.POINTER(ServerStats)]),
         "hankel_server_destroy": (i32, [vp]),
         "hankel_plan_stage_stats": (i32, [vp, ctypes.POINTER(StageStat)]),
+        "hankel_plan_fft_shapes": (i32, [vp, ctypes.POINTER(FftShape), i32, ctypes.POINTER(i32)]),
+        "hankel_tune_cache_put": (i32, [ctypes.c_char_p, ctypes.POINTER(FftShape)]),
+        "hankel_tune_cache_get": (i32, [ctypes.c_char_p, i32, i32, i32, ctypes.POINTER(FftShape),
+                                        ctypes.POINTER(i32)]),
+        "hankel_tune_cache_save": (i32, [ctypes.c_char_p]),
+        "hankel_tune_cache_load": (i32, [ctypes.c_char_p]),
+        "hankel_tune_cache_clear": (i32, []),
+        "hankel_tune_bucket": (i32, [i64]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

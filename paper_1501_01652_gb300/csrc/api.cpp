@@ -78,6 +78,7 @@ static void fill_info(const hankel_plan_s* p, const hk::HostPlan& hp, hankel_inf
   if (p) {
     out->device_bytes = hk::dev_plan_bytes(p);
     out->workspace_bytes = hk::dev_workspace_bytes(p);
+    hk::dev_plan_shapes(p, nullptr, 0, &out->fft_shapes);
   }
 }
 
@@ -170,6 +171,15 @@ int hankel_plan_blocks(hankel_plan_t p, hankel_block* out, int cap, int* count) 
     out[i].terms_fp32 = cnt[hk::kTermFP32];
   }
   return HANKEL_OK;
+}
+
+int hankel_plan_fft_shapes(hankel_plan_t p, hankel_fft_shape* out, int cap, int* count) {
+  if (!p || !count || cap < 0 || (cap > 0 && !out)) return HANKEL_EINVAL;
+  if (p->host_only) {
+    *count = 0;
+    return HANKEL_OK;
+  }
+  return hk::dev_plan_shapes(p, out, cap, count);
 }
 
 int hankel_plan_entry(hankel_plan_t p, int64_t k, int64_t n, double* value, int* is_far) {

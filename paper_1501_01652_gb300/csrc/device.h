@@ -27,4 +27,5 @@ int dev_set_timing(hankel_plan_s* p, int enable);
 int dev_stage_stats(hankel_plan_s* p, hankel_stage_stat* out);
 size_t dev_plan_bytes(const hankel_plan_s* p);
 size_t dev_workspace_bytes(const hankel_plan_s* p);
+int dev_plan_shapes(const hankel_plan_s* p, hankel_fft_shape* out, int cap, int* count);
 }  // namespace hk

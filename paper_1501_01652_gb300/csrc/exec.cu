@@ -14,12 +14,14 @@
 
 #include <algorithm>
 #include <mutex>
+#include <string>
 #include <type_traits>
 #include <vector>
 
 #include "device.h"
 #include "cplx.cuh"
 #include "kernels.cuh"
+#include "tune.h"
 
 namespace hk {
 
@@ -41,6 +43,7 @@ struct TermGroup {
   void* Vt = nullptr;    // [nl][C] column functions x column chirp (x FP32 scale)
   void* Ut = nullptr;    // [nl][R] row functions times the row chirp (/ FP32 scale)
   int64_t cap = 0;       // stacked columns per chunk
+  FftShape fwd{}, inv{}; // launch split of its forward and inverse transforms (autotuned)
 };
 
 struct DevBlock {
@@ -161,6 +164,7 @@ struct DevicePlan {
   std::vector<Rec> pending;
   std::vector<cudaEvent_t> pool;
   size_t pool_used = 0;
+  std::vector<hankel_fft_shape> shapes;  // the transform shapes the plan runs (hankel_plan_fft_shapes)
 };
 
 namespace {
@@ -253,6 +257,145 @@ struct StageScope {
   do {                                                             \
     if (cudaGetLastError() != cudaSuccess) return HANKEL_ECUDA;    \
   } while (0)
+
+int public_precision(int t) { return t == kTermFP32 ? HANKEL_PREC_FP32 : t == kTermDF64 ? HANKEL_PREC_DF64 : HANKEL_PREC_FP64; }
+
+// Candidate launch splits of a transform of 2^logF points: the built-in one first, then one
+// launch (logF <= 12) and every ordered split into 2..4 passes of radix 2^5 .. 2^8 (2^7 for
+// double-float, whose larger passes spill), fewest passes first, at most 24.
+std::vector<FftShape> shape_candidates(int logF, int ncols, int prec) {
+  std::vector<FftShape> out{default_fft_shape(logF, ncols, prec)};
+  auto add = [&](const FftShape& sh) {
+    for (const FftShape& o : out)
+      if (o.one_launch == sh.one_launch && o.npass == sh.npass &&
+          std::equal(o.logr, o.logr + o.npass, sh.logr))
+        return;
+    if (out.size() < 24 && valid_fft_shape(sh, logF)) out.push_back(sh);
+  };
+  if (logF <= 12) {
+    FftShape one{};
+    one.one_launch = 1;
+    add(one);
+  }
+  const int hi = prec == kTermDF64 ? 7 : 8;
+  for (int np = 2; np <= 4; ++np) {
+    int r[4] = {5, 5, 5, 5};
+    for (;;) {
+      int sum = 0;
+      for (int i = 0; i < np; ++i) sum += r[i];
+      if (sum == logF) {
+        FftShape sh{};
+        sh.npass = np;
+        for (int i = 0; i < np; ++i) sh.logr[i] = r[i];
+        add(sh);
+      }
+      int i = 0;  // next tuple in [5, hi]^np
+      while (i < np && r[i] == hi) r[i++] = 5;
+      if (i == np) break;
+      ++r[i];
+    }
+  }
+  return out;
+}
+
+// The fastest of three runs after one warm-up, in ms (1e30 when a launch is refused).
+template <class C>
+double time_shape(C* A, C* B, int logF, int ncols, const C* tw, int logFmax, const FftShape& sh, cudaEvent_t e0,
+                  cudaEvent_t e1) {
+  double best = 1e30;
+  for (int it = 0; it < 4; ++it) {
+    C* res = nullptr;
+    cudaEventRecord(e0, 0);
+    if (run_fft<C>(A, B, logF, ncols, false, tw, logFmax, 0, &res, nullptr, nullptr, 1, nullptr, &sh) != HANKEL_OK ||
+        cudaGetLastError() != cudaSuccess)  // a split whose launch is refused is not a candidate
+      return 1e30;
+    cudaEventRecord(e1, 0);
+    if (cudaEventSynchronize(e1) != cudaSuccess) return 1e30;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (it > 0) best = std::min(best, (double)ms);
+  }
+  return best;
+}
+
+// The shape of transforms of 2^logF points in precision prec over ncols columns per launch:
+// from the plan's list, the process cache (keyed by GPU model) or a measurement of the
+// candidates on the lane's workspace buffers A, B (bytes each), recorded in the plan's list.
+int plan_shape(DevicePlan* d, const std::string& gpu, bool tune, int prec, int logF, int64_t ncols, void* A, void* B,
+               size_t bytes, FftShape* out) {
+  const int bucket = tune_bucket(ncols);
+  const int pp = public_precision(prec);
+  for (const hankel_fft_shape& h : d->shapes)
+    if (h.precision == pp && h.log2_len == logF && h.col_bucket == bucket) {
+      out->one_launch = h.one_launch;
+      out->npass = h.npass;
+      std::copy(h.log2_radix, h.log2_radix + 4, out->logr);
+      return HANKEL_OK;
+    }
+  hankel_fft_shape h{};
+  h.precision = pp;
+  h.log2_len = logF;
+  h.col_bucket = bucket;
+  FftShape sh = default_fft_shape(logF, (int)ncols, prec);
+  bool cached = false;
+  if (tune) {
+    hankel_fft_shape c{};
+    if (tune_get(gpu, pp, logF, bucket, &c)) {
+      FftShape cs{c.one_launch, c.npass, {c.log2_radix[0], c.log2_radix[1], c.log2_radix[2], c.log2_radix[3]}};
+      if (valid_fft_shape(cs, logF)) {
+        sh = cs;
+        cached = true;
+      }
+    }
+  }
+  if (tune && !cached) {
+    const size_t esz = term_esz(prec);
+    const int64_t F = int64_t(1) << logF;
+    // enough columns to fill the GPU as the real launches do, at most 2^25 points
+    int64_t nt = std::min<int64_t>(ncols, std::max<int64_t>(1, (int64_t(1) << 25) / F));
+    nt = std::min<int64_t>(nt, (int64_t)(bytes / (F * esz)));
+    if (nt >= 1) {
+      if (cudaMemset(A, 0, (size_t)nt * F * esz) != cudaSuccess) return HANKEL_ECUDA;
+      cudaEvent_t e0 = nullptr, e1 = nullptr;
+      if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return HANKEL_ECUDA;
+      const std::vector<FftShape> cand = shape_candidates(logF, (int)ncols, prec);
+      double tdef = 0.0, tbest = 1e30;
+      FftShape best = cand[0];
+      for (size_t i = 0; i < cand.size(); ++i) {
+        double t;
+        if (prec == kTermFP32)
+          t = time_shape<float2>((float2*)A, (float2*)B, logF, (int)nt, d->twf, d->logFmax, cand[i], e0, e1);
+        else if (prec == kTermDF64)
+          t = time_shape<df64c>((df64c*)A, (df64c*)B, logF, (int)nt, d->twd, d->logFmax, cand[i], e0, e1);
+        else
+          t = time_shape<double2>((double2*)A, (double2*)B, logF, (int)nt, d->tw, d->logFmax, cand[i], e0, e1);
+        if (i == 0) tdef = t;
+        if (t < tbest) {
+          tbest = t;
+          best = cand[i];
+        }
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      if (cudaGetLastError() != cudaSuccess) return HANKEL_ECUDA;
+      // keep the built-in split unless another is clearly faster (2 %)
+      if (!(tbest < 0.98 * tdef)) {
+        best = cand[0];
+        tbest = tdef;
+      }
+      sh = best;
+      h.ms_default = tdef;
+      h.ms_chosen = tbest;
+    }
+  }
+  h.one_launch = sh.one_launch;
+  h.npass = sh.npass;
+  std::copy(sh.logr, sh.logr + 4, h.log2_radix);
+  if (tune && !cached && h.ms_chosen > 0) tune_put(gpu, h);
+  d->shapes.push_back(h);
+  *out = sh;
+  return HANKEL_OK;
+}
 
 }  // namespace
 
@@ -559,8 +702,36 @@ int dev_plan_create(hankel_plan_s* p) {
     }
     d->blocks.push_back(db);
   }
-
   if (cudaDeviceSynchronize() != cudaSuccess) return HANKEL_ECUDA;
+
+  // Launch split of every term group's forward and inverse transforms (autotuned per GPU model)
+  const bool tune = !(hp.opt.flags & HANKEL_FLAG_NO_AUTOTUNE);
+  std::string gpu;
+  if (tune) {
+    tune_load_env();
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, d->device) != cudaSuccess) return HANKEL_ECUDA;
+    gpu = prop.name;
+  }
+  for (DevBlock& db : d->blocks)
+    for (int j = 0; j < db.ng; ++j) {
+      TermGroup& tg = db.g[j];
+      const int l = d->lane_of[tg.prec];
+      const int64_t nfwd = tg.cap * (db.b.mode == kBlockRowSeg ? db.b.nseg : 1);
+      const int64_t ninv = tg.cap * (db.b.mode == kBlockColSeg ? db.b.nseg : 1);
+      HK_TRY(plan_shape(d, gpu, tune, tg.prec, db.b.logF, nfwd, d->lanes[l].A, d->lanes[l].B, d->lanes[l].buf_bytes,
+                        &tg.fwd));
+      HK_TRY(plan_shape(d, gpu, tune, tg.prec, db.b.logF, ninv, d->lanes[l].A, d->lanes[l].B, d->lanes[l].buf_bytes,
+                        &tg.inv));
+    }
+  if (cudaDeviceSynchronize() != cudaSuccess) return HANKEL_ECUDA;
+  return HANKEL_OK;
+}
+
+int dev_plan_shapes(const hankel_plan_s* p, hankel_fft_shape* out, int cap, int* count) {
+  const DevicePlan* d = p->dev;
+  *count = d ? (int)d->shapes.size() : 0;
+  for (int i = 0; i < cap && i < *count; ++i) out[i] = d->shapes[i];
   return HANKEL_OK;
 }
 
@@ -636,7 +807,7 @@ int run_block(DevicePlan* d, const DevBlock& db, const TermGroup& tg, const doub
       const void* coef = Prec<C>::coef(d, c);
       const FftGen gen{rowseg ? b.nseg : 1, rowseg ? b.S : b.C, b.C, b.n0, c0, tg.nl, coef,
                        coef == (const void*)c ? ldc : d->hpN, tg.Vt};
-      HK_TRY(run_fft<C>(A, B, b.logF, (int)nfwd, false, tw, d->logFmax, st, &res, &np, nullptr, 1, &gen));
+      HK_TRY(run_fft<C>(A, B, b.logF, (int)nfwd, false, tw, d->logFmax, st, &res, &np, nullptr, 1, &gen, &tg.fwd));
       HK_LAUNCHED();
       sc.done(np, 5.0 * (double)b.F * (double)b.logF * (double)nfwd, 0.0, 2.0 * sizeof(C) * (double)b.F * nfwd * np);
     }
@@ -652,7 +823,8 @@ int run_block(DevicePlan* d, const DevBlock& db, const TermGroup& tg, const doub
       }
       StageScope sc(d, fst, st, record);
       int np = 0;
-      HK_TRY(run_fft<C>(other, res, b.logF, (int)ninv, true, tw, d->logFmax, st, &res2, &np));
+      HK_TRY(run_fft<C>(other, res, b.logF, (int)ninv, true, tw, d->logFmax, st, &res2, &np, nullptr, 1, nullptr,
+                        &tg.inv));
       HK_LAUNCHED();
       sc.done(np, 5.0 * (double)b.F * (double)b.logF * (double)ninv, 0.0, 2.0 * sizeof(C) * (double)b.F * ninv * np);
     } else {
@@ -662,7 +834,7 @@ int run_block(DevicePlan* d, const DevBlock& db, const TermGroup& tg, const doub
       StageScope sc(d, fst, st, record);
       int np = 0;
       HK_TRY(run_fft<C>(res, other, b.logF, (int)ninv, true, tw, d->logFmax, st, &res2, &np, H,
-                        colseg ? b.nseg : 1));
+                        colseg ? b.nseg : 1, nullptr, &tg.inv));
       HK_LAUNCHED();
       // 5 F log2 F per transform plus 6 F for the folded complex products
       sc.done(np, (5.0 * (double)b.logF + 6.0) * (double)b.F * (double)ninv, 0.0,

@@ -626,9 +626,43 @@ void launch_scale_copy(const double2* src, C* dst, int64_t n, double scale, cuda
 }
 
 
+FftShape default_fft_shape(int logF, int ncols, int prec) {
+  FftShape sh{};
+  // few columns of 2^10 .. 2^12 points would give the one-launch kernel only a few CTAs (a CTA
+  // holds 4096 points): two passes spread them over 8 to 32 times as many
+  const int64_t small_ctas = logF <= kSmallLog ? ((int64_t)ncols + (kSmallPts >> logF) - 1) / (kSmallPts >> logF) : 0;
+  const bool few = logF >= 10 && small_ctas < 152;
+  if (logF <= kSmallLog && !few) {
+    sh.one_launch = 1;
+    return sh;
+  }
+  // passes of radix 2^5 .. 2^8 (logF >= 10), each leaving F/R >= kTile pairs per column. FP64 and
+  // FP32 take the fewest passes (radix up to 256); double-float keeps to radix 64 where 2^5 .. 2^6
+  // can make up F (its radix-128 pass needs 112 registers a thread and issues on half the cycles
+  // of radix 64)
+  const int maxlog = prec == kTermDF64 ? 6 : 8;
+  int np = (logF + maxlog - 1) / maxlog;
+  while (np > 1 && logF / np < 5) --np;
+  const int base = logF / np, extra = logF % np;
+  sh.npass = np;
+  for (int i = 0; i < np && i < 4; ++i) sh.logr[i] = base + (i < extra ? 1 : 0);
+  return sh;
+}
+
+bool valid_fft_shape(const FftShape& sh, int logF) {
+  if (sh.one_launch) return logF >= 6 && logF <= kSmallLog;
+  if (sh.npass < 2 || sh.npass > 4) return false;  // a pass leaves F / R >= kTile sequences
+  int sum = 0;
+  for (int i = 0; i < sh.npass; ++i) {
+    if (sh.logr[i] < 5 || sh.logr[i] > 8) return false;
+    sum += sh.logr[i];
+  }
+  return sum == logF;
+}
+
 template <class C>
 int run_fft(C* a, C* b, int logF, int ncols, bool inverse, const C* tw, int logFmax, cudaStream_t st, C** result,
-            int* npasses, const C* hmul, int64_t nseg, const FftGen* gen) {
+            int* npasses, const C* hmul, int64_t nseg, const FftGen* gen, const FftShape* shape) {
   if (logF < 6 || logF > logFmax || nseg < 1) return HANKEL_EINVAL;
   if (gen && (inverse || hmul || gen->nsegc < 1 || gen->ncols < 1)) return HANKEL_EINVAL;
   FftGen g0{};
@@ -637,11 +671,9 @@ int run_fft(C* a, C* b, int logF, int ncols, bool inverse, const C* tw, int logF
   // the ladder's table for this length: W_F^t at tw[F + t]
   tw += (size_t)1 << logF;
   logFmax = logF;
-  // few columns of 2^10 .. 2^12 points would give the one-launch kernel only a few CTAs (a CTA
-  // holds 4096 points): two passes spread them over 8 to 32 times as many
-  const int64_t small_ctas = ((int64_t)ncols + (kSmallPts >> logF) - 1) / (kSmallPts >> logF);
-  const bool few = logF >= 10 && small_ctas < 152;
-  if (logF <= kSmallLog && !few) {
+  const int prec = std::is_same<C, df64c>::value ? kTermDF64 : std::is_same<C, float2>::value ? kTermFP32 : kTermFP64;
+  const FftShape sh = (shape && valid_fft_shape(*shape, logF)) ? *shape : default_fft_shape(logF, ncols, prec);
+  if (sh.one_launch) {
     // the whole transform in one launch
     if (inverse) launch_small_f<true, C>(logF, a, b, ncols, tw, logFmax, hmul, nseg, none, st);
     else launch_small_f<false, C>(logF, a, b, ncols, tw, logFmax, hmul, nseg, g0, st);
@@ -649,20 +681,12 @@ int run_fft(C* a, C* b, int logF, int ncols, bool inverse, const C* tw, int logF
     if (npasses) *npasses = 1;
     return HANKEL_OK;
   }
-  // passes of radix 2^5 .. 2^8 (logF >= 10), each leaving F/R >= kTile pairs per column; the
-  // first (stride F/R >= kTile) applies the input product. FP64 and FP32 take the fewest
-  // passes (radix up to 256); double-float keeps to radix 64 where 2^5 .. 2^6 can make up F (its
-  // radix-128 pass needs 112 registers a thread and issues on half the cycles of radix 64)
-  const int maxlog = std::is_same<C, df64c>::value ? 6 : 8;
-  int np = (logF + maxlog - 1) / maxlog;
-  while (np > 1 && logF / np < 5) --np;
-  const int base = logF / np, extra = logF % np;
-  if (base < 5 || base + (extra ? 1 : 0) > 8) return HANKEL_EINVAL;
+  // the first pass (stride F/R >= kTile) applies the input product or generates the input
   C* src = a;
   C* dst = b;
   int done = 0;  // log2 of the sub-length transformed so far
-  for (int i = 0; i < np; ++i) {
-    const int lr = base + (i < extra ? 1 : 0);
+  for (int i = 0; i < sh.npass; ++i) {
+    const int lr = sh.logr[i];
     done += lr;
     const int logS = logF - done;
     const C* h = i == 0 ? hmul : nullptr;
@@ -671,16 +695,16 @@ int run_fft(C* a, C* b, int logF, int ncols, bool inverse, const C* tw, int logF
     std::swap(src, dst);
   }
   *result = src;
-  if (npasses) *npasses = np;
+  if (npasses) *npasses = sh.npass;
   return HANKEL_OK;
 }
 
 template int run_fft<double2>(double2*, double2*, int, int, bool, const double2*, int, cudaStream_t, double2**,
-                              int*, const double2*, int64_t, const FftGen*);
+                              int*, const double2*, int64_t, const FftGen*, const FftShape*);
 template int run_fft<float2>(float2*, float2*, int, int, bool, const float2*, int, cudaStream_t, float2**, int*,
-                             const float2*, int64_t, const FftGen*);
+                             const float2*, int64_t, const FftGen*, const FftShape*);
 template int run_fft<df64c>(df64c*, df64c*, int, int, bool, const df64c*, int, cudaStream_t, df64c**, int*,
-                            const df64c*, int64_t, const FftGen*);
+                            const df64c*, int64_t, const FftGen*, const FftShape*);
 template void launch_scale_copy<double2>(const double2*, double2*, int64_t, double, cudaStream_t);
 template void launch_scale_copy<float2>(const double2*, float2*, int64_t, double, cudaStream_t);
 template void launch_scale_copy<df64c>(const double2*, df64c*, int64_t, double, cudaStream_t);

@@ -137,6 +137,12 @@ void launch_seg_hh(const SegGeom& g, double2* hh, cudaStream_t st);
 // g / ncols, table row li = g % ncols), and its point t < F is
 //   coef[rhs * ldc + n0 - 1 + sg S + t] * Vt[li][sg S + t]   for t < min(S, C - sg S), else 0.
 // coef holds double (FP64 plans), float (FP32) or (high, low) float pairs (DF64) coefficients.
+struct FftShape {
+  int one_launch;  // 1: the whole transform in one launch (2^6 .. 2^12 points)
+  int npass;       // otherwise passes of radix 2^logr[i], first to last
+  int logr[4];
+};
+
 struct FftGen {
   int64_t nsegc, S, C, n0;
   int64_t c0;
@@ -154,9 +160,20 @@ struct FftGen {
 // ncols / nseg columns; the products of the chirp spectra are folded into the first loads).
 // With gen (forward transforms only), the input columns are generated by the first loads as
 // FftGen describes and a is used only as workspace.
+// shape: how the transform is split into launches (one launch of k_fft_small, or passes of the
+// listed radices); nullptr takes default_fft_shape.
 template <class C>
 int run_fft(C* a, C* b, int logF, int ncols, bool inverse, const C* tw, int logFmax, cudaStream_t st, C** result,
-            int* npasses = nullptr, const C* hmul = nullptr, int64_t nseg = 1, const FftGen* gen = nullptr);
+            int* npasses = nullptr, const C* hmul = nullptr, int64_t nseg = 1, const FftGen* gen = nullptr,
+            const FftShape* shape = nullptr);
+// The built-in choice for a transform of 2^logF points over ncols columns in precision prec
+// (kTermFP64, kTermDF64, kTermFP32): one launch up to 4096 points unless that gives fewer CTAs
+// than SMs; otherwise the fewest passes of radix 2^5 .. 2^8 (2^6 for double-float), as equal
+// as possible, the larger first.
+FftShape default_fft_shape(int logF, int ncols, int prec);
+// Whether shape is a valid split of 2^logF points (passes of radix 2^5 .. 2^8 summing to logF,
+// or one launch for logF <= 12).
+bool valid_fft_shape(const FftShape& shape, int logF);
 // out[cc][t] = sum_s in[cc*nseg + s][t] * H[s][t]   (overlap-add of column segments)
 template <class C>
 void launch_seg_mac(const C* in, const C* H, C* out, int64_t F, int64_t nseg, int nc, cudaStream_t st);

@@ -440,3 +440,35 @@ def test_fourier_bessel_higher_orders_large(nu):
     c = coefficients("uniform", N, 4, 3200 + nu)
     rows = sample_rows(N, 48, 43)
     _check("fourier_bessel", nu, N, 1e-15, c, rows=rows)
+
+
+# ---------------------------------------------------------------------------------------------
+# The FFT autotuner: measured launch splits, used by the plan, with the same results
+# ---------------------------------------------------------------------------------------------
+def test_autotuned_shapes_are_recorded_and_exact():
+    N = 2 ** 17
+    c = coefficients("normal", N, 4, 8100)
+    hk.tune_cache_clear()
+    tuned = hk.Plan("dht", 0, N, 1e-15, max_nrhs=4)
+    shapes = tuned.fft_shapes()
+    assert shapes and tuned.info["fft_shapes"] == len(shapes)
+    for s in shapes:
+        assert s["one_launch"] or (2 <= len(s["radices"]) <= 4 and sum(s["radices"]) == s["log2_len"]
+                                   and all(5 <= r <= 8 for r in s["radices"]))
+        # measured in this process (the cache was cleared): the chosen split is no slower
+        assert s["ms_chosen"] > 0 and s["ms_chosen"] <= s["ms_default"]
+    # a second plan takes the cached splits without measuring
+    again = hk.Plan("dht", 0, N, 1e-15, max_nrhs=4)
+    assert [(s["log2_len"], s["radices"]) for s in again.fft_shapes()] == [(s["log2_len"], s["radices"])
+                                                                            for s in shapes]
+    fixed = hk.Plan("dht", 0, N, 1e-15, max_nrhs=4, autotune=False)
+    assert all(s["ms_chosen"] == 0 for s in fixed.fft_shapes())
+    cd = torch.from_numpy(c).cuda()
+    ft = tuned.exec(cd).cpu().numpy()
+    ff = fixed.exec(cd).cpu().numpy()
+    rows = sample_rows(N, 64, 47)
+    ref = oracle.transform("dht", 0, N, c, rows=rows)
+    l1 = np.abs(c).sum(axis=1, keepdims=True)
+    assert np.all(np.abs(ft[:, rows] - ref) <= 10 * 1e-15 * l1)
+    # another split changes only the rounding of the transforms
+    assert np.all(np.abs(ft - ff) <= 1e-15 * l1)
