@@ -387,6 +387,14 @@ def run_ours(args):
 
     # launches of the stage-timed steps, as many as the timed region's
     launches = sum(st[k]["launches"] for st in stats for k in st)
+    # the autotuner's launch splits of the timed plans, with its own measurements (default vs chosen)
+    tuned = [dict(sh, plan_eps=e) for p, e in zip(plans, eps_list) for sh in p.fft_shapes()]
+    measured = [t for t in tuned if t["ms_default"] > 0]
+    autotune = {"shapes": tuned,
+                "chosen_over_default": (sum(t["ms_chosen"] for t in measured) / sum(t["ms_default"] for t in measured))
+                if measured else None,
+                "note": "per (precision, log2 length, column bucket): the built-in split and the chosen one, timed "
+                        "at plan creation on the plan's workspace (ms of one launch sequence)"}
     stage_ms = {k: round(sum(st[k]["ms"] for st in stats) / args.steps, 3) for k in stats[0]}
     roofline = fft_roofline(stats, args.steps)
     precs = [p.info["precision"] for p in plans]
@@ -463,6 +471,7 @@ def run_ours(args):
         "stage_steps_ms": sum(ev_step_ms) / len(ev_step_ms),
         "term_precision": term_split,
         "roofline": roofline,
+        "fft_autotune": autotune,
         "e2e": {"value": served_e2e, "unit": "coeffs/s", "h2d_bytes_per_step": coeffs_per_step * 8,
                 "d2h_bytes_per_step": coeffs_per_step * 8,
                 "form": "hankel_server (FP64 plans), %d single-vector requests (%d per eps) submitted at once, "
