@@ -37,9 +37,12 @@
  *    stream). Device-pointer calls are asynchronous and stream-ordered.
  *  - Return values are hankel_status codes; nothing is thrown across the ABI.
  *    On any code other than HANKEL_OK, output buffers hold unspecified data.
- *  - A plan serialises its own executions: it owns one workspace, so two
- *    executions of the same plan must not overlap on the GPU. Distinct
- *    plans are independent.
+ *  - Executions of one plan serialise on its execution contexts: context 0
+ *    (made with the plan, used by every call without a context argument)
+ *    holds the workspace, so two executions on the same context must not
+ *    overlap on the GPU. hankel_plan_add_context makes more contexts for
+ *    executions in flight at once (hankel_exec_batched_ctx). Distinct plans
+ *    are independent.
  */
 #ifndef HANKEL_H
 #define HANKEL_H
@@ -88,7 +91,8 @@ enum hankel_status {
   HANKEL_ENOMEM = 2,        /* a host or device allocation failed */
   HANKEL_ECUDA = 3,         /* a CUDA runtime call or kernel launch failed */
   HANKEL_EUNSUPPORTED = 4,  /* a valid request this build does not serve */
-  HANKEL_ETIMEOUT = 5       /* a bounded device wait expired */
+  HANKEL_ETIMEOUT = 5,      /* a bounded device wait expired */
+  HANKEL_ECANCELED = 6      /* a queued request was cancelled before it ran (hankel_server_cancel) */
 };
 
 /* Plan flags (hankel_options.flags). */
@@ -150,6 +154,9 @@ typedef struct {
   int64_t block_cols;     /* transforms per right-hand side summed over blocks (hankel_block.ncols) */
   int fft_shapes;         /* distinct (precision, length, column bucket) transform shapes the plan runs
                              (hankel_plan_fft_shapes) */
+  int contexts;           /* execution contexts (1 + those added by hankel_plan_add_context) */
+  size_t context_bytes;   /* device bytes of one execution context (workspace, partial sums, coefficient
+                             copies), included in device_bytes */
 } hankel_info;
 
 /* How one kind of multi-column FFT of the far field is split into kernel launches. Not a step of
@@ -215,6 +222,19 @@ int hankel_exec(hankel_plan_t p, const double* c, double* f, void* stream);
  * sums back, so their range does not depend on the input's. */
 int hankel_exec_batched(hankel_plan_t p, const double* c, int64_t ldc, double* f, int64_t ldf,
                         int nrhs, void* stream);
+
+/* Another execution context for the plan: a second copy of the per-execution scratch (transform
+ * workspace, lane streams and accumulators, near-field partial sums, coefficient copies; the
+ * plan's tables are shared). Executions on different contexts of one plan may be in flight at
+ * the same time, on different streams. *index receives the new context's index (1, 2, ...).
+ * Blocking (allocates device memory). Errors: EINVAL (NULL, host-only plan), ENOMEM, ECUDA;
+ * after an error the plan and its earlier contexts stay usable. This is a service of the library
+ * (a serving layer runs batches of one plan side by side); the paper has no counterpart. */
+int hankel_plan_add_context(hankel_plan_t p, int* index);
+
+/* hankel_exec_batched on execution context ctx (0 <= ctx < hankel_info.contexts). */
+int hankel_exec_batched_ctx(hankel_plan_t p, int ctx, const double* c, int64_t ldc, double* f, int64_t ldf,
+                            int nrhs, void* stream);
 
 /* Size of the library's static device scratch array used by hankel_exec_static (96 MiB). */
 #define HANKEL_STATIC_SCRATCH_BYTES (96u << 20)
@@ -355,8 +375,9 @@ const char* hankel_status_string(int status);
  * A server owns a dispatcher thread, a set of CUDA streams and a cache of plans keyed by
  * (task, nu, N, eps). Requests carry host arrays of coefficients; the dispatcher admits them
  * by device memory, packs the waiting requests of one plan (up to max_batch vectors) into
- * one batched execution, and runs batches of different plans concurrently on its streams.
- * A plan executes one batch at a time (it owns one workspace). Completed results are copied
+ * one batched execution, and runs batches concurrently on its streams: batches of different
+ * plans, and up to contexts_per_plan batches of one plan, each on an execution context of its
+ * own (so a request for a plan already on the GPU is admitted as a stream and a context free up). Completed results are copied
  * to the request's host output array and the request's latency (submit to completion) is
  * recorded. This layer is a service around the paper's transform, not part of the paper. */
 typedef struct hankel_server_s* hankel_server_t;
@@ -373,21 +394,26 @@ typedef struct {
   int batch_window_us; /* a plan's batch with fewer than max_batch vectors waits until no request of the
                           plan has arrived for this long (so a burst of submissions stays one batch),
                           or until its oldest request has waited ten times this (default 200; 0: none) */
+  int contexts_per_plan; /* batches of one plan in flight at once, each on an execution context of its own
+                            (hankel_plan_add_context; made when needed and the memory cap allows; default
+                            2, 1..8) */
 } hankel_server_options;
 
 /* Statistics since the server was created. */
 typedef struct {
-  int64_t submitted, completed, failed;  /* requests */
+  int64_t submitted, completed, failed;  /* requests (failed includes cancelled) */
   int64_t batches;                       /* batched executions launched */
   int64_t vectors;                       /* coefficient vectors transformed */
   double coefficients;                   /* sum over completed requests of N * nrhs */
   int64_t plans_built, plans_evicted;    /* plan cache activity */
   int64_t graphs_captured;               /* CUDA graphs captured */
   size_t device_bytes;                   /* device memory held now */
+  int64_t contexts_added;                /* execution contexts added to cached plans (beyond their first) */
+  int64_t cancelled;                     /* requests cancelled before they ran */
 } hankel_server_stats;
 
 /* Defaults: 120 GiB cap, 4 streams, batches of up to 64 vectors, no graphs, AUTO precision, packing on,
- * a 200 us batch window. */
+ * a 200 us batch window, 2 contexts per plan. */
 int hankel_server_options_default(hankel_server_options* o);
 
 /* Create a server on the current CUDA device and start its dispatcher. */
@@ -406,6 +432,11 @@ int hankel_server_submit(hankel_server_t s, int task, int nu, int64_t N, double 
  * time from submission to completion (either pointer may be NULL). */
 int hankel_server_wait(hankel_server_t s, int64_t ticket, int* status, double* latency_ms);
 
+/* Cancel a request that is still waiting for dispatch: it completes at once with status
+ * HANKEL_ECANCELED and its arrays are not touched again. A request already in a batch on the GPU
+ * (or finished) is not affected; *cancelled (may be NULL) tells which happened. Errors: EINVAL. */
+int hankel_server_cancel(hankel_server_t s, int64_t ticket, int* cancelled);
+
 /* Block until every submitted request has completed. */
 int hankel_server_drain(hankel_server_t s);
 
@@ -413,6 +444,13 @@ int hankel_server_get_stats(hankel_server_t s, hankel_server_stats* out);
 
 /* Stop the dispatcher after draining, and free every plan, stream and buffer. NULL is accepted. */
 int hankel_server_destroy(hankel_server_t s);
+
+/* ---- Fault injection for tests (host side; no GPU fault is made) ----
+ * After `after` more successful device or page-locked allocations by this library, the next
+ * `count` allocations report failure as if the CUDA allocator had refused them (the call returns
+ * HANKEL_ENOMEM, or a server request completes with it). count = 0 turns injection off.
+ * Process-wide; for tests of the error paths of plan creation and request admission. */
+int hankel_debug_fail_allocs(int64_t after, int64_t count);
 
 /* ---- Host-only parameter formulas (no plan, no GPU) ---- */
 

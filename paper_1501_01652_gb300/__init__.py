@@ -121,6 +121,12 @@ def tune_bucket(ncols):
     return _lib.load().hankel_tune_bucket(int(ncols))
 
 
+def debug_fail_allocs(after, count):
+    """Make the library's next `count` device or page-locked allocations, after `after` successful
+    ones, report failure (host-side fault injection for tests; count = 0 turns it off)."""
+    _lib.check(_lib.load().hankel_debug_fail_allocs(int(after), int(count)), "hankel_debug_fail_allocs")
+
+
 class Plan:
     """A transform plan: f = J_nu(r omega^T) c for one task, order, size and accuracy."""
 
@@ -230,9 +236,19 @@ class Plan:
             return f
         return f2[0] if single else f2
 
-    def exec(self, c, f=None, stream=None):
-        """Run on torch CUDA float64 tensors of shape (N,) or (nrhs, N); returns f."""
-        return self._run(self._lib.hankel_exec_batched, "hankel_exec_batched", c, f, stream)
+    def exec(self, c, f=None, stream=None, context=0):
+        """Run on torch CUDA float64 tensors of shape (N,) or (nrhs, N); returns f. context selects the
+        execution context (add_context); executions on different contexts may overlap."""
+        if context == 0:
+            return self._run(self._lib.hankel_exec_batched, "hankel_exec_batched", c, f, stream)
+        fn = self._lib.hankel_exec_batched_ctx
+        return self._run(lambda h, *a: fn(h, int(context), *a), "hankel_exec_batched_ctx", c, f, stream)
+
+    def add_context(self):
+        """Another execution context (workspace) for executions in flight at once; returns its index."""
+        idx = ctypes.c_int(0)
+        _lib.check(self._lib.hankel_plan_add_context(self._h, ctypes.byref(idx)), "hankel_plan_add_context")
+        return idx.value
 
     def exec_inverse(self, f, c=None, stream=None):
         """Inverse DHT (DHT plans): c = j_{0,N+1}^-2 v o J(v o f), v_n = 2/J_1(j_{0,n})^2."""
@@ -264,7 +280,7 @@ class Server:
     """
 
     def __init__(self, streams=4, max_batch=64, use_graphs=False, precision="auto", memory_cap=0, pack=True,
-                 batch_window_us=None):
+                 batch_window_us=None, contexts_per_plan=None):
         self._lib = _lib.load()
         o = _lib.ServerOptions()
         _lib.check(self._lib.hankel_server_options_default(ctypes.byref(o)), "hankel_server_options_default")
@@ -273,6 +289,8 @@ class Server:
         o.pack_requests = 1 if pack else 0
         if batch_window_us is not None:
             o.batch_window_us = int(batch_window_us)
+        if contexts_per_plan is not None:
+            o.contexts_per_plan = int(contexts_per_plan)
         if memory_cap:
             o.memory_cap = int(memory_cap)
         self._h = ctypes.c_void_p()
@@ -307,6 +325,22 @@ class Server:
         self._live.pop(int(ticket), None)
         _lib.check(st.value, "request %d" % ticket)
         return lat.value
+
+    def cancel(self, ticket):
+        """Cancel a request still waiting for dispatch; returns True if it was cancelled (it then
+        completes with HANKEL_ECANCELED and wait() raises)."""
+        done = ctypes.c_int(0)
+        _lib.check(self._lib.hankel_server_cancel(self._h, int(ticket), ctypes.byref(done)), "hankel_server_cancel")
+        return bool(done.value)
+
+    def status(self, ticket):
+        """Block until `ticket` completes; returns (status name, latency ms) without raising."""
+        st = ctypes.c_int()
+        lat = ctypes.c_double()
+        _lib.check(self._lib.hankel_server_wait(self._h, int(ticket), ctypes.byref(st), ctypes.byref(lat)),
+                   "hankel_server_wait")
+        self._live.pop(int(ticket), None)
+        return _lib.STATUS_NAMES.get(st.value, str(st.value)), lat.value
 
     def drain(self):
         _lib.check(self._lib.hankel_server_drain(self._h), "hankel_server_drain")

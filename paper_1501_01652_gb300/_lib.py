@@ -8,7 +8,7 @@ _lib = None
 
 HANKEL_OK = 0
 STATUS_NAMES = {0: "HANKEL_OK", 1: "HANKEL_EINVAL", 2: "HANKEL_ENOMEM", 3: "HANKEL_ECUDA",
-                4: "HANKEL_EUNSUPPORTED", 5: "HANKEL_ETIMEOUT"}
+                4: "HANKEL_EUNSUPPORTED", 5: "HANKEL_ETIMEOUT", 6: "HANKEL_ECANCELED"}
 FLAG_HOST_ONLY = 1
 FLAG_NO_SEGMENT = 2
 FLAG_ALL_COLUMNS = 8
@@ -28,7 +28,8 @@ EXPORTED = [
     "hankel_server_options_default", "hankel_server_create", "hankel_server_submit", "hankel_server_wait",
     "hankel_server_drain", "hankel_server_get_stats", "hankel_server_destroy",
     "hankel_plan_fft_shapes", "hankel_tune_cache_put", "hankel_tune_cache_get", "hankel_tune_cache_save",
-    "hankel_tune_cache_load", "hankel_tune_cache_clear", "hankel_tune_bucket",
+    "hankel_tune_cache_load", "hankel_tune_cache_clear", "hankel_tune_bucket", "hankel_plan_add_context",
+    "hankel_exec_batched_ctx", "hankel_server_cancel", "hankel_debug_fail_allocs",
 ]
 STAGES = ["near", "gen", "fft", "pointwise", "out", "fft_df64", "fft_fp32"]
 
@@ -48,7 +49,8 @@ class Info(ctypes.Structure):
                 ("direct_cols", ctypes.c_int64), ("nblocks", ctypes.c_int), ("ncols", ctypes.c_int),
                 ("npairs", ctypes.c_int), ("near_count", ctypes.c_int64), ("far_count", ctypes.c_int64),
                 ("near_zmax", ctypes.c_double), ("device_bytes", ctypes.c_size_t),
-                ("workspace_bytes", ctypes.c_size_t), ("block_cols", ctypes.c_int64), ("fft_shapes", ctypes.c_int)]
+                ("workspace_bytes", ctypes.c_size_t), ("block_cols", ctypes.c_int64), ("fft_shapes", ctypes.c_int),
+                ("contexts", ctypes.c_int), ("context_bytes", ctypes.c_size_t)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -74,14 +76,15 @@ class StageStat(ctypes.Structure):
 class ServerOptions(ctypes.Structure):
     _fields_ = [("memory_cap", ctypes.c_size_t), ("streams", ctypes.c_int), ("max_batch", ctypes.c_int),
                 ("use_graphs", ctypes.c_int), ("precision", ctypes.c_int), ("pack_requests", ctypes.c_int),
-                ("batch_window_us", ctypes.c_int)]
+                ("batch_window_us", ctypes.c_int), ("contexts_per_plan", ctypes.c_int)]
 
 
 class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
                 ("batches", ctypes.c_int64), ("vectors", ctypes.c_int64), ("coefficients", ctypes.c_double),
                 ("plans_built", ctypes.c_int64), ("plans_evicted", ctypes.c_int64),
-                ("graphs_captured", ctypes.c_int64), ("device_bytes", ctypes.c_size_t)]
+                ("graphs_captured", ctypes.c_int64), ("device_bytes", ctypes.c_size_t),
+                ("contexts_added", ctypes.c_int64), ("cancelled", ctypes.c_int64)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -146,6 +149,10 @@ def load():
         "hankel_tune_cache_load": (i32, [ctypes.c_char_p]),
         "hankel_tune_cache_clear": (i32, []),
         "hankel_tune_bucket": (i32, [i64]),
+        "hankel_plan_add_context": (i32, [vp, ctypes.POINTER(i32)]),
+        "hankel_exec_batched_ctx": (i32, [vp, i32, vp, i64, vp, i64, i32, vp]),
+        "hankel_server_cancel": (i32, [vp, i64, ctypes.POINTER(i32)]),
+        "hankel_debug_fail_allocs": (i32, [i64, i64]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

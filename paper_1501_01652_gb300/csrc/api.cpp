@@ -5,12 +5,33 @@
 
 #include <vector>
 
+#include <atomic>
 #include <new>
 
 #include "device.h"
 #include "plan.h"
 
+namespace hk {
+namespace {
+std::atomic<int64_t> g_fault_after{0}, g_fault_count{0};
+}
+bool alloc_fault() {
+  if (g_fault_count.load() <= 0) return false;
+  if (g_fault_after.fetch_sub(1) > 0) return false;
+  g_fault_after.store(0);
+  return g_fault_count.fetch_sub(1) > 0;
+}
+}  // namespace hk
+
 extern "C" {
+
+int hankel_debug_fail_allocs(int64_t after, int64_t count) {
+  if (after < 0 || count < 0) return HANKEL_EINVAL;
+  hk::g_fault_count.store(0);
+  hk::g_fault_after.store(after);
+  hk::g_fault_count.store(count);
+  return HANKEL_OK;
+}
 
 const char* hankel_status_string(int status) {
   switch (status) {
@@ -20,6 +41,7 @@ const char* hankel_status_string(int status) {
     case HANKEL_ECUDA: return "CUDA error";
     case HANKEL_EUNSUPPORTED: return "unsupported request";
     case HANKEL_ETIMEOUT: return "device wait timed out";
+    case HANKEL_ECANCELED: return "request cancelled";
     default: return "unknown status";
   }
 }
@@ -79,6 +101,7 @@ static void fill_info(const hankel_plan_s* p, const hk::HostPlan& hp, hankel_inf
     out->device_bytes = hk::dev_plan_bytes(p);
     out->workspace_bytes = hk::dev_workspace_bytes(p);
     hk::dev_plan_shapes(p, nullptr, 0, &out->fft_shapes);
+    out->contexts = hk::dev_contexts(p, &out->context_bytes);
   }
 }
 
@@ -213,6 +236,19 @@ int hankel_exec_batched(hankel_plan_t p, const double* c, int64_t ldc, double* f
   const int64_t N = p->hp.opt.N;
   if (nrhs < 1 || nrhs > p->hp.opt.max_nrhs || ldc < N || ldf < N) return HANKEL_EINVAL;
   return hk::dev_exec(p, c, ldc, f, ldf, nrhs, stream);
+}
+
+int hankel_plan_add_context(hankel_plan_t p, int* index) {
+  if (!p || !index || p->host_only) return HANKEL_EINVAL;
+  return hk::dev_add_context(p, index);
+}
+
+int hankel_exec_batched_ctx(hankel_plan_t p, int ctx, const double* c, int64_t ldc, double* f, int64_t ldf,
+                            int nrhs, void* stream) {
+  if (!p || !c || !f || p->host_only) return HANKEL_EINVAL;
+  const int64_t N = p->hp.opt.N;
+  if (nrhs < 1 || nrhs > p->hp.opt.max_nrhs || ldc < N || ldf < N) return HANKEL_EINVAL;
+  return hk::dev_exec_ctx(p, ctx, c, ldc, f, ldf, nrhs, stream);
 }
 
 int hankel_exec_host(hankel_plan_t p, const double* c, int64_t ldc, double* f, int64_t ldf, int nrhs) {

@@ -15,11 +15,18 @@ struct hankel_plan_s {
 };
 
 namespace hk {
+// Fault injection (hankel_debug_fail_allocs): true when this allocation is to be reported failed.
+bool alloc_fault();
 // Allocate device tables and workspace and build the chirp spectra.
 int dev_plan_create(hankel_plan_s* p);
 // Free everything dev_plan_create made (also after a partial failure).
 int dev_plan_destroy(hankel_plan_s* p);
 int dev_exec(hankel_plan_s* p, const double* c, int64_t ldc, double* f, int64_t ldf, int nrhs, void* stream);
+int dev_exec_ctx(hankel_plan_s* p, int k, const double* c, int64_t ldc, double* f, int64_t ldf, int nrhs,
+                 void* stream);
+int dev_add_context(hankel_plan_s* p, int* index);
+// Number of execution contexts; *ctx_bytes (optional) receives the device bytes of one.
+int dev_contexts(const hankel_plan_s* p, size_t* ctx_bytes);
 int dev_exec_host(hankel_plan_s* p, const double* c, int64_t ldc, double* f, int64_t ldf, int nrhs);
 int dev_exec_static(hankel_plan_s* p, const double* c, double* f, void* stream);
 int dev_exec_inverse(hankel_plan_s* p, const double* f, int64_t ldf, double* c, int64_t ldc, int nrhs, void* stream);

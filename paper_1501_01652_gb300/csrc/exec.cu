@@ -110,8 +110,7 @@ struct DevicePlan {
   NearRow* mrows = nullptr;
   int64_t nmrows = 0;
   int64_t* nend = nullptr;  // near prefix end per row
-  void* partial = nullptr;  // near-field partial sums (plan precision)
-  int64_t nslots = 0;
+  int64_t nslots = 0;       // near-field partial-sum slots per vector
   std::vector<DevBlock> blocks;
   double2* tw = nullptr;   // twiddle ladder in FP64: W_F^t at tw[F + t], F = 2^6 .. 2^logFmax
   float2* twf = nullptr;   // the same ladder rounded to FP32 (FP32 plans)
@@ -119,10 +118,7 @@ struct DevicePlan {
   bool df64 = false;       // plan precision double-float (transforms; near field on the FP32 pipe)
   bool any_t[3] = {false, false, false};  // some block has transforms in this precision
   int logFmax = 6;
-  void* bufA = nullptr;    // workspace of lane 0 (bytes; holds elements of any precision)
-  void* bufB = nullptr;
-  size_t ws_bytes = 0;    // workspace of every lane
-  size_t buf_bytes = 0;   // one buffer of lane 0
+  size_t ws_bytes = 0;    // workspace (FFT column buffers) of one execution context
   // Lanes: the term groups of one precision run on a stream of their own, so that the FP64,
   // double-float and FP32 transforms (different pipes, many small launches) overlap. Lane 0 is
   // the caller's stream (the near field and the plan precision's groups, adding into f); lane
@@ -139,17 +135,28 @@ struct DevicePlan {
   };
   int nlanes = 1;
   int lane_of[3] = {0, 0, 0};  // lane of each term precision
-  Lane lanes[3];
-  cudaEvent_t fork = nullptr;
+  size_t lane_bytes[3] = {0, 0, 0};  // one workspace buffer of each lane
+  // The scratch of one execution: the lanes' buffers, streams and accumulators, the near-field
+  // partial sums and the per-execution coefficient copies. Context 0 is made with the plan;
+  // hankel_plan_add_context makes more, so that executions of one plan on different contexts
+  // may be in flight at once. The tables above are shared and only read.
+  struct ExecCtx {
+    Lane lanes[3];
+    cudaEvent_t fork = nullptr;
+    void* partial = nullptr;  // near-field partial sums (plan precision)
+    float* cf = nullptr;      // the scaled coefficients rounded to FP32 [max_nrhs][N]
+    float2* cdf = nullptr;    // the scaled coefficients as (high, low) float pairs [max_nrhs][N]
+    int* cexp = nullptr;      // with cf or cdf: per vector, the power of two they are scaled by
+    void* tcd = nullptr;      // 8+ vectors: coefficient digits of the tensor-core near field
+    int* tce = nullptr;       // and their per-chunk exponents
+  };
+  std::vector<ExecCtx*> ctx;
+  size_t ctx_bytes = 0;       // device bytes of one context
+  bool want_cf = false, want_cdf = false;
   double* c_stage = nullptr;
   double* f_stage = nullptr;
   double* vinv = nullptr;     // DHT plans, first inverse call: v_n = 2 / J_1(j_{0,n})^2
   double* inv_stage = nullptr;  // v o f for the inverse ([max_nrhs][N])
-  float* cf = nullptr;   // FP32 plans: the coefficients rounded to FP32 [max_nrhs][N]
-  float2* cdf = nullptr; // DF64 plans: the coefficients as (high, low) float pairs [max_nrhs][N]
-  int* cexp = nullptr;   // with cf or cdf: per vector, the power of two those copies are scaled by
-  void* tcd = nullptr;   // FP64 plans, 8+ vectors: coefficient digits of the tensor-core near field
-  int* tce = nullptr;    // and their per-chunk exponents
   int64_t tc_npad = 0;
   long long* jtabq = nullptr;  // the J table in Q62 fixed point (FP64 and DF64 plans)
   size_t bytes = 0;
@@ -177,7 +184,7 @@ int dalloc(DevicePlan* d, T** p, size_t count) {
   *p = nullptr;
   if (count == 0) count = 1;
   void* q = nullptr;
-  if (cudaMalloc(&q, count * sizeof(T)) != cudaSuccess) {
+  if (alloc_fault() || cudaMalloc(&q, count * sizeof(T)) != cudaSuccess) {
     cudaGetLastError();
     return HANKEL_ENOMEM;
   }
@@ -257,6 +264,54 @@ struct StageScope {
   do {                                                             \
     if (cudaGetLastError() != cudaSuccess) return HANKEL_ECUDA;    \
   } while (0)
+
+// One execution context of the plan (DevicePlan::ExecCtx), allocated after the plan's tables and
+// lane layout are known; its bytes are tracked with the plan's.
+int ctx_create(DevicePlan* d, const HostPlan& hp) {
+  DevicePlan::ExecCtx* x = new DevicePlan::ExecCtx();
+  d->ctx.push_back(x);
+  const size_t before = d->bytes;
+  const int64_t N = hp.opt.N;
+  const size_t R = (size_t)hp.opt.max_nrhs;
+  if (d->want_cdf) HK_TRY(dalloc(d, &x->cdf, R * N));
+  if (d->want_cf) HK_TRY(dalloc(d, &x->cf, R * N));
+  if (x->cf || x->cdf) HK_TRY(dalloc(d, &x->cexp, R));
+  if (d->tc_npad) {
+    uint16_t* q = nullptr;
+    HK_TRY(dalloc(d, &q, (size_t)8 * kNearTcRhs * d->tc_npad));
+    x->tcd = q;
+    HK_TRY(dalloc(d, &x->tce, (size_t)(d->tc_npad / 512) * kNearTcRhs));
+  }
+  const size_t cnt = (size_t)std::max<int64_t>(d->nslots, 1) * R;
+  if (d->fp32) {
+    float* pf;
+    HK_TRY(dalloc(d, &pf, cnt));
+    x->partial = pf;
+  } else {
+    double* pd;
+    HK_TRY(dalloc(d, &pd, cnt));
+    x->partial = pd;
+  }
+  for (int l = 0; l < d->nlanes; ++l) {
+    char* qa;
+    char* qb;
+    HK_TRY(dalloc(d, &qa, d->lane_bytes[l]));
+    HK_TRY(dalloc(d, &qb, d->lane_bytes[l]));
+    x->lanes[l].A = qa;
+    x->lanes[l].B = qb;
+    x->lanes[l].buf_bytes = d->lane_bytes[l];
+    if (l > 0) {
+      HK_TRY(dalloc(d, &x->lanes[l].acc, R * N));
+      if (cudaStreamCreateWithFlags(&x->lanes[l].s, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&x->lanes[l].done, cudaEventDisableTiming) != cudaSuccess)
+        return HANKEL_ECUDA;
+    }
+  }
+  if (d->nlanes > 1 && cudaEventCreateWithFlags(&x->fork, cudaEventDisableTiming) != cudaSuccess)
+    return HANKEL_ECUDA;
+  d->ctx_bytes = d->bytes - before;
+  return HANKEL_OK;
+}
 
 int public_precision(int t) { return t == kTermFP32 ? HANKEL_PREC_FP32 : t == kTermDF64 ? HANKEL_PREC_DF64 : HANKEL_PREC_FP64; }
 
@@ -471,20 +526,13 @@ int dev_plan_create(hankel_plan_s* p) {
     for (size_t i = 0; i < hp.jtab.size(); ++i) tp[i] = pair(hp.jtab[i]);
     HK_TRY(upload(d, &d->jtabdf, tp.data(), hp.jtab.size()));
   }
-  // per-execution coefficient copies: double-float pairs for DF64 near fields and transforms,
-  // FP32 for FP32 transforms (FP32 near fields read them too)
-  if (d->df64 || d->any_t[kTermDF64]) HK_TRY(dalloc(d, &d->cdf, (size_t)hp.opt.max_nrhs * N));
-  if (!d->fp32 && hp.opt.max_nrhs >= kNearTcMinRhs) {
-    d->tc_npad = (N + 511) / 512 * 512;
-    uint16_t* q = nullptr;
-    HK_TRY(dalloc(d, &q, (size_t)8 * 16 * d->tc_npad));
-    d->tcd = q;
-    HK_TRY(dalloc(d, &d->tce, (size_t)(d->tc_npad / 512) * 16));
-  }
+  // per-execution coefficient copies (made per context): double-float pairs for DF64 near fields
+  // and transforms, FP32 for FP32 transforms (FP32 near fields read them too), digits for the
+  // tensor-core near field
+  d->want_cdf = d->df64 || d->any_t[kTermDF64];
+  d->want_cf = d->any_t[kTermFP32];
+  if (!d->fp32 && hp.opt.max_nrhs >= kNearTcMinRhs) d->tc_npad = (N + 511) / 512 * 512;
   if (!d->fp32) HK_TRY(upload(d, &d->jtabq, hp.jtabq.data(), hp.jtabq.size()));
-  if (d->any_t[kTermFP32]) HK_TRY(dalloc(d, &d->cf, (size_t)hp.opt.max_nrhs * N));
-  if (d->cf || d->cdf) HK_TRY(dalloc(d, &d->cexp, (size_t)hp.opt.max_nrhs));
-
 
   // Near-field work list: groups of kNearRows rows, the group's longest prefix cut into tiles of
   // kNearCols columns; groups with more than one tile add up per-row partial sums.
@@ -512,13 +560,6 @@ int dev_plan_create(hankel_plan_s* p) {
   HK_TRY(upload(d, &d->items, items.data(), items.size()));
   HK_TRY(upload(d, &d->nend, hp.nend.data(), hp.nend.size()));
   if (!mrows.empty()) HK_TRY(upload(d, &d->mrows, mrows.data(), mrows.size()));
-  {
-    void* q = nullptr;
-    const size_t cnt = (size_t)std::max<int64_t>(slot, 1) * hp.opt.max_nrhs;
-    if (d->fp32) { float* pf; HK_TRY(dalloc(d, &pf, cnt)); q = pf; }
-    else { double* pd; HK_TRY(dalloc(d, &pd, cnt)); q = pd; }
-    d->partial = q;
-  }
 
   // Twiddle table W_{Fmax}^t = exp(-2 pi i t / Fmax).
   int logFmax = 6;
@@ -570,25 +611,12 @@ int dev_plan_create(hankel_plan_s* p) {
   }
   d->ws_bytes = 0;
   for (int l = 0; l < d->nlanes; ++l) {
-    char* qa; char* qb;
-    HK_TRY(dalloc(d, &qa, need[l]));
-    HK_TRY(dalloc(d, &qb, need[l]));
-    d->lanes[l].A = qa;
-    d->lanes[l].B = qb;
-    d->lanes[l].buf_bytes = need[l];
+    d->lane_bytes[l] = need[l];
     d->ws_bytes += 2 * need[l];
-    if (l > 0) {
-      HK_TRY(dalloc(d, &d->lanes[l].acc, (size_t)hp.opt.max_nrhs * N));
-      if (cudaStreamCreateWithFlags(&d->lanes[l].s, cudaStreamNonBlocking) != cudaSuccess ||
-          cudaEventCreateWithFlags(&d->lanes[l].done, cudaEventDisableTiming) != cudaSuccess)
-        return HANKEL_ECUDA;
-    }
   }
-  if (d->nlanes > 1 && cudaEventCreateWithFlags(&d->fork, cudaEventDisableTiming) != cudaSuccess)
-    return HANKEL_ECUDA;
-  d->bufA = d->lanes[0].A;
-  d->bufB = d->lanes[0].B;
-  d->buf_bytes = need[0];
+  HK_TRY(ctx_create(d, hp));
+  void* bufA = d->ctx[0]->lanes[0].A;
+  void* bufB = d->ctx[0]->lanes[0].B;
 
   // Per block: chirp vectors, the spectra of its convolution kernels (one per segment) and per
   // term group its column and row tables (the low-rank form's terms, or its kept stacked columns).
@@ -687,8 +715,8 @@ int dev_plan_create(hankel_plan_s* p) {
     SegGeom sg{hp.Ua, hp.Ub, hp.Vb, hp.E, b.k0, b.n0, b.R, b.C, 0, 0, 1, b.F};
     if (b.mode == kBlockRowSeg) { sg.Cc = b.S; sg.dn = b.S; sg.nseg = b.nseg; }
     if (b.mode == kBlockColSeg) { sg.Rr = b.S; sg.dk = b.S; sg.nseg = b.nseg; }
-    double2* hA = (double2*)d->bufA;
-    double2* hB = (double2*)d->bufB;
+    double2* hA = (double2*)bufA;
+    double2* hB = (double2*)bufB;
     launch_seg_hh(sg, hA, 0);
     HK_LAUNCHED();
     double2* res = nullptr;
@@ -719,10 +747,9 @@ int dev_plan_create(hankel_plan_s* p) {
       const int l = d->lane_of[tg.prec];
       const int64_t nfwd = tg.cap * (db.b.mode == kBlockRowSeg ? db.b.nseg : 1);
       const int64_t ninv = tg.cap * (db.b.mode == kBlockColSeg ? db.b.nseg : 1);
-      HK_TRY(plan_shape(d, gpu, tune, tg.prec, db.b.logF, nfwd, d->lanes[l].A, d->lanes[l].B, d->lanes[l].buf_bytes,
-                        &tg.fwd));
-      HK_TRY(plan_shape(d, gpu, tune, tg.prec, db.b.logF, ninv, d->lanes[l].A, d->lanes[l].B, d->lanes[l].buf_bytes,
-                        &tg.inv));
+      const DevicePlan::Lane& ln = d->ctx[0]->lanes[l];
+      HK_TRY(plan_shape(d, gpu, tune, tg.prec, db.b.logF, nfwd, ln.A, ln.B, ln.buf_bytes, &tg.fwd));
+      HK_TRY(plan_shape(d, gpu, tune, tg.prec, db.b.logF, ninv, ln.A, ln.B, ln.buf_bytes, &tg.inv));
     }
   if (cudaDeviceSynchronize() != cudaSuccess) return HANKEL_ECUDA;
   return HANKEL_OK;
@@ -743,11 +770,15 @@ int dev_plan_destroy(hankel_plan_s* p) {
   cudaSetDevice(d->device);
   cudaDeviceSynchronize();
   for (cudaEvent_t e : d->pool) cudaEventDestroy(e);
-  for (int l = 1; l < 3; ++l) {
-    if (d->lanes[l].done) cudaEventDestroy(d->lanes[l].done);
-    if (d->lanes[l].s) cudaStreamDestroy(d->lanes[l].s);
+  for (DevicePlan::ExecCtx* x : d->ctx) {
+    for (int l = 1; l < 3; ++l) {
+      if (x->lanes[l].done) cudaEventDestroy(x->lanes[l].done);
+      if (x->lanes[l].s) cudaStreamDestroy(x->lanes[l].s);
+    }
+    if (x->fork) cudaEventDestroy(x->fork);
+    delete x;
   }
-  if (d->fork) cudaEventDestroy(d->fork);
+  d->ctx.clear();
   for (void* q : d->allocs) cudaFree(q);
   cudaSetDevice(cur);
   delete d;
@@ -770,25 +801,25 @@ struct Prec;
 template <>
 struct Prec<double2> {
   static const void* tw(const DevicePlan* d) { return d->tw; }
-  static const void* coef(const DevicePlan* d, const double* c) { return c; }
+  static const void* coef(const DevicePlan::ExecCtx*, const double* c) { return c; }
   static constexpr int stage = HANKEL_STAGE_FFT;
 };
 template <>
 struct Prec<df64c> {
   static const void* tw(const DevicePlan* d) { return d->twd; }
-  static const void* coef(const DevicePlan* d, const double*) { return d->cdf; }
+  static const void* coef(const DevicePlan::ExecCtx* x, const double*) { return x->cdf; }
   static constexpr int stage = HANKEL_STAGE_FFT_DF64;
 };
 template <>
 struct Prec<float2> {
   static const void* tw(const DevicePlan* d) { return d->twf; }
-  static const void* coef(const DevicePlan* d, const double*) { return d->cf; }
+  static const void* coef(const DevicePlan::ExecCtx* x, const double*) { return x->cf; }
   static constexpr int stage = HANKEL_STAGE_FFT_FP32;
 };
 
 template <class C>
-int run_block(DevicePlan* d, const DevBlock& db, const TermGroup& tg, const double* c, int64_t ldc, double* f,
-              int64_t ldf, int nrhs, C* A, C* B, int64_t cap, cudaStream_t st, bool record) {
+int run_block(DevicePlan* d, const DevicePlan::ExecCtx* x, const DevBlock& db, const TermGroup& tg, const double* c,
+              int64_t ldc, double* f, int64_t ldf, int nrhs, C* A, C* B, int64_t cap, cudaStream_t st, bool record) {
   const Block& b = db.b;
   const C* tw = (const C*)Prec<C>::tw(d);
   const C* H = (const C*)tg.H;
@@ -804,7 +835,7 @@ int run_block(DevicePlan* d, const DevBlock& db, const TermGroup& tg, const doub
       // column generation happens in the first loads of the forward transform
       StageScope sc(d, fst, st, record);
       int np = 0;
-      const void* coef = Prec<C>::coef(d, c);
+      const void* coef = Prec<C>::coef(x, c);
       const FftGen gen{rowseg ? b.nseg : 1, rowseg ? b.S : b.C, b.C, b.n0, c0, tg.nl, coef,
                        coef == (const void*)c ? ldc : d->hpN, tg.Vt};
       HK_TRY(run_fft<C>(A, B, b.logF, (int)nfwd, false, tw, d->logFmax, st, &res, &np, nullptr, 1, &gen, &tg.fwd));
@@ -843,7 +874,7 @@ int run_block(DevicePlan* d, const DevBlock& db, const TermGroup& tg, const doub
     {
       StageScope sc(d, HANKEL_STAGE_OUT, st, record);
       OutArgs oa{res2, b.F, b.R, b.k0, (rowseg ? b.S : b.C) - 1, colseg ? b.S : b.R, colseg ? b.nseg : 1,
-                 nc, c0, tg.nl, f, ldf, tg.Ut, std::is_same<C, double2>::value ? nullptr : d->cexp};
+                 nc, c0, tg.nl, f, ldf, tg.Ut, std::is_same<C, double2>::value ? nullptr : x->cexp};
       launch_out<C>(oa, st);
       HK_LAUNCHED();
       sc.done(1, 0.0, 0.0);
@@ -855,50 +886,50 @@ int run_block(DevicePlan* d, const DevBlock& db, const TermGroup& tg, const doub
 // Near field of a plan in its precision, then every far block's term groups. capacity
 // (chunk_from_capacity): bytes of each of A and B. use_lanes: the groups of other precisions
 // run in their lanes (otherwise every group runs on st in A and B, adding into f).
-int run_all(DevicePlan* d, const HostPlan& hp, const double* c, int64_t ldc, double* f, int64_t ldf, int nrhs,
-            void* A, void* B, void* partial, size_t capacity, bool chunk_from_capacity, cudaStream_t st,
-            bool record, bool use_lanes) {
-  if (d->cexp) {
+int run_all(DevicePlan* d, DevicePlan::ExecCtx* x, const HostPlan& hp, const double* c, int64_t ldc, double* f,
+            int64_t ldf, int nrhs, void* A, void* B, void* partial, size_t capacity, bool chunk_from_capacity,
+            cudaStream_t st, bool record, bool use_lanes) {
+  if (x->cexp) {
     // FP32 and double-float stages run on the coefficients scaled by a power of two per vector
     // (from its largest |c_n|), so their range does not depend on the input's; FP64 stages use c
     StageScope sc(d, HANKEL_STAGE_GEN, st, record);
-    launch_coef_exponent(c, ldc, d->hpN, nrhs, d->cexp, st);
+    launch_coef_exponent(c, ldc, d->hpN, nrhs, x->cexp, st);
     HK_LAUNCHED();
     sc.done(2, 0.0, 0.0);
   }
-  if (d->cf) {
+  if (x->cf) {
     // FP32 transforms (and FP32 near fields): the scaled coefficients rounded once per execution
     StageScope sc(d, HANKEL_STAGE_GEN, st, record);
-    launch_coeffs_f32(c, ldc, d->cf, d->hpN, nrhs, d->cexp, st);
+    launch_coeffs_f32(c, ldc, x->cf, d->hpN, nrhs, x->cexp, st);
     HK_LAUNCHED();
     sc.done(1, 0.0, 0.0);
   }
-  if (d->cdf) {
+  if (x->cdf) {
     // DF64 near fields and transforms: the scaled coefficients split once into float pairs
     StageScope sc(d, HANKEL_STAGE_GEN, st, record);
-    launch_coeffs_df64(c, ldc, d->cdf, d->hpN, nrhs, d->cexp, st);
+    launch_coeffs_df64(c, ldc, x->cdf, d->hpN, nrhs, x->cexp, st);
     HK_LAUNCHED();
     sc.done(1, 0.0, 0.0);
   }
   const bool lanes_on = use_lanes && d->nlanes > 1;
   const bool par = lanes_on && !d->timing;
-  auto lane_stream = [&](int l) { return (par && l > 0) ? d->lanes[l].s : st; };
+  auto lane_stream = [&](int l) { return (par && l > 0) ? x->lanes[l].s : st; };
   if (lanes_on) {
     if (par) {
       // the other lanes start once the coefficient copies above are written
-      if (cudaEventRecord(d->fork, st) != cudaSuccess) return HANKEL_ECUDA;
+      if (cudaEventRecord(x->fork, st) != cudaSuccess) return HANKEL_ECUDA;
       for (int l = 1; l < d->nlanes; ++l)
-        if (cudaStreamWaitEvent(d->lanes[l].s, d->fork, 0) != cudaSuccess) return HANKEL_ECUDA;
+        if (cudaStreamWaitEvent(x->lanes[l].s, x->fork, 0) != cudaSuccess) return HANKEL_ECUDA;
     }
     for (int l = 1; l < d->nlanes; ++l)
-      if (cudaMemsetAsync(d->lanes[l].acc, 0, sizeof(double) * (size_t)nrhs * (size_t)d->hpN, lane_stream(l)) !=
+      if (cudaMemsetAsync(x->lanes[l].acc, 0, sizeof(double) * (size_t)nrhs * (size_t)d->hpN, lane_stream(l)) !=
           cudaSuccess)
         return HANKEL_ECUDA;
   }
   {
     StageScope sc(d, HANKEL_STAGE_NEAR, st, record);
     int64_t near_launches = d->nmrows > 0 ? 2 : 1;
-    if (d->tcd && nrhs >= kNearTcMinRhs) {
+    if (x->tcd && nrhs >= kNearTcMinRhs) {
       // the tensor-core near field takes 16 vectors per launch: groups of 16, and a last group of
       // fewer than kNearTcMinRhs vectors on the FMA kernels; the groups run one after another on
       // st and share the digit and partial-sum buffers
@@ -909,13 +940,13 @@ int run_all(DevicePlan* d, const HostPlan& hp, const double* c, int64_t ldc, dou
         double* fg = f + (int64_t)g0 * ldf;
         if (ng >= kNearTcMinRhs) {
           launch_near_tc(d->df64, d->items, d->nitems, d->mrows, d->nmrows, d->nend, d->hpN, (double*)partial, ng,
-                         cg, ldc, d->tcd, d->tce, d->tc_npad, fg, ldf, d->nodes.r_true, d->nodes.om_true, d->jtabq,
+                         cg, ldc, x->tcd, x->tce, d->tc_npad, fg, ldf, d->nodes.r_true, d->nodes.om_true, d->jtabq,
                          hp.jt_n, hp.jt_deg, st);
           near_launches += d->nmrows > 0 ? 3 : 2;
         } else if (d->df64) {
           launch_near_df(d->items, d->nitems, d->mrows, d->nmrows, d->nend, d->hpN, (double*)partial, ng,
-                         d->cdf + (int64_t)g0 * d->hpN, fg, ldf, d->rdf, d->omdf, d->jtabdf, hp.jt_n, hp.jt_deg,
-                         d->cexp + g0, st);
+                         x->cdf + (int64_t)g0 * d->hpN, fg, ldf, d->rdf, d->omdf, d->jtabdf, hp.jt_n, hp.jt_deg,
+                         x->cexp + g0, st);
           near_launches += d->nmrows > 0 ? 2 : 1;
         } else {
           launch_near<double>(d->items, d->nitems, d->mrows, d->nmrows, d->nend, d->hpN, (double*)partial, ng, cg,
@@ -925,11 +956,11 @@ int run_all(DevicePlan* d, const HostPlan& hp, const double* c, int64_t ldc, dou
         }
       }
     } else if (d->df64)
-      launch_near_df(d->items, d->nitems, d->mrows, d->nmrows, d->nend, d->hpN, (double*)partial, nrhs, d->cdf, f,
-                     ldf, d->rdf, d->omdf, d->jtabdf, hp.jt_n, hp.jt_deg, d->cexp, st);
+      launch_near_df(d->items, d->nitems, d->mrows, d->nmrows, d->nend, d->hpN, (double*)partial, nrhs, x->cdf, f,
+                     ldf, d->rdf, d->omdf, d->jtabdf, hp.jt_n, hp.jt_deg, x->cexp, st);
     else if (d->fp32)
       launch_near<float>(d->items, d->nitems, d->mrows, d->nmrows, d->nend, d->hpN, (float*)partial, nrhs, c, ldc,
-                         d->cf, f, ldf, d->rf, d->omf, d->jtabf, nullptr, hp.jt_n, hp.jt_deg, d->cexp, st);
+                         x->cf, f, ldf, d->rf, d->omf, d->jtabf, nullptr, hp.jt_n, hp.jt_deg, x->cexp, st);
     else
       launch_near<double>(d->items, d->nitems, d->mrows, d->nmrows, d->nend, d->hpN, (double*)partial, nrhs, c, ldc,
                           nullptr, f, ldf, d->nodes.r_true, d->nodes.om_true, d->jtab, d->jtabq, hp.jt_n,
@@ -943,29 +974,29 @@ int run_all(DevicePlan* d, const HostPlan& hp, const double* c, int64_t ldc, dou
       const size_t esz = term_esz(tg.prec);
       const int l = lanes_on ? d->lane_of[tg.prec] : 0;
       const cudaStream_t ls = lane_stream(l);
-      void* la = l ? d->lanes[l].A : A;
-      void* lb = l ? d->lanes[l].B : B;
-      double* lf = l ? d->lanes[l].acc : f;
+      void* la = l ? x->lanes[l].A : A;
+      void* lb = l ? x->lanes[l].B : B;
+      double* lf = l ? x->lanes[l].acc : f;
       const int64_t lld = l ? d->hpN : ldf;
       const int64_t cap = chunk_from_capacity
                               ? std::max<int64_t>(1, (int64_t)(capacity / (column_footprint(db.b) * esz)))
                               : tg.cap;
       if (tg.prec == kTermFP32)
-        HK_TRY(run_block<float2>(d, db, tg, c, ldc, lf, lld, nrhs, (float2*)la, (float2*)lb, cap, ls, record));
+        HK_TRY(run_block<float2>(d, x, db, tg, c, ldc, lf, lld, nrhs, (float2*)la, (float2*)lb, cap, ls, record));
       else if (tg.prec == kTermDF64)
-        HK_TRY(run_block<df64c>(d, db, tg, c, ldc, lf, lld, nrhs, (df64c*)la, (df64c*)lb, cap, ls, record));
+        HK_TRY(run_block<df64c>(d, x, db, tg, c, ldc, lf, lld, nrhs, (df64c*)la, (df64c*)lb, cap, ls, record));
       else
-        HK_TRY(run_block<double2>(d, db, tg, c, ldc, lf, lld, nrhs, (double2*)la, (double2*)lb, cap, ls, record));
+        HK_TRY(run_block<double2>(d, x, db, tg, c, ldc, lf, lld, nrhs, (double2*)la, (double2*)lb, cap, ls, record));
     }
   }
   if (lanes_on) {
     if (par)
       for (int l = 1; l < d->nlanes; ++l)
-        if (cudaEventRecord(d->lanes[l].done, d->lanes[l].s) != cudaSuccess ||
-            cudaStreamWaitEvent(st, d->lanes[l].done, 0) != cudaSuccess)
+        if (cudaEventRecord(x->lanes[l].done, x->lanes[l].s) != cudaSuccess ||
+            cudaStreamWaitEvent(st, x->lanes[l].done, 0) != cudaSuccess)
           return HANKEL_ECUDA;
     StageScope sc(d, HANKEL_STAGE_OUT, st, record);
-    const double* acc[2] = {d->lanes[1].acc, d->nlanes > 2 ? d->lanes[2].acc : nullptr};
+    const double* acc[2] = {x->lanes[1].acc, d->nlanes > 2 ? x->lanes[2].acc : nullptr};
     launch_add_lanes(f, ldf, acc, d->nlanes - 1, d->hpN, nrhs, st);
     HK_LAUNCHED();
     sc.done(1, 0.0, 0.0);
@@ -975,16 +1006,45 @@ int run_all(DevicePlan* d, const HostPlan& hp, const double* c, int64_t ldc, dou
 
 }  // namespace
 
-int dev_exec(hankel_plan_s* p, const double* c, int64_t ldc, double* f, int64_t ldf, int nrhs, void* stream) {
+int dev_exec_ctx(hankel_plan_s* p, int k, const double* c, int64_t ldc, double* f, int64_t ldf, int nrhs,
+                 void* stream) {
   DevicePlan* d = p->dev;
+  if (k < 0 || k >= (int)d->ctx.size()) return HANKEL_EINVAL;
+  DevicePlan::ExecCtx* x = d->ctx[k];
   cudaStream_t st = (cudaStream_t)stream;
   int cur = -1;
   cudaGetDevice(&cur);
   if (cur != d->device) cudaSetDevice(d->device);
   // near field overwrites f; far blocks add to it
-  const int s = run_all(d, p->hp, c, ldc, f, ldf, nrhs, d->bufA, d->bufB, d->partial, 0, false, st, true, true);
+  const int s = run_all(d, x, p->hp, c, ldc, f, ldf, nrhs, x->lanes[0].A, x->lanes[0].B, x->partial, 0, false, st, true,
+                        true);
   if (cur >= 0 && cur != d->device) cudaSetDevice(cur);
   return s;
+}
+
+int dev_exec(hankel_plan_s* p, const double* c, int64_t ldc, double* f, int64_t ldf, int nrhs, void* stream) {
+  return dev_exec_ctx(p, 0, c, ldc, f, ldf, nrhs, stream);
+}
+
+int dev_add_context(hankel_plan_s* p, int* index) {
+  DevicePlan* d = p->dev;
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (cur != d->device) cudaSetDevice(d->device);
+  const int st = ctx_create(d, p->hp);
+  if (cur >= 0 && cur != d->device) cudaSetDevice(cur);
+  if (st != HANKEL_OK) {
+    // the partial context keeps what it allocated until the plan is destroyed, but is never used
+    cudaGetLastError();
+    return st;
+  }
+  *index = (int)d->ctx.size() - 1;
+  return HANKEL_OK;
+}
+
+int dev_contexts(const hankel_plan_s* p, size_t* ctx_bytes) {
+  if (ctx_bytes) *ctx_bytes = p->dev ? p->dev->ctx_bytes : 0;
+  return p->dev ? (int)p->dev->ctx.size() : 0;
 }
 
 int dev_set_timing(hankel_plan_s* p, int enable) {
@@ -1136,7 +1196,7 @@ int dev_exec_static(hankel_plan_s* p, const double* c, double* f, void* stream) 
   void* sB = bytes + per_buf;
   void* spartial = bytes + 2 * per_buf;
   cudaStream_t st = (cudaStream_t)stream;
-  const int s = run_all(d, hp, c, N, f, N, 1, sA, sB, spartial, per_buf, true, st, false, false);
+  const int s = run_all(d, d->ctx[0], hp, c, N, f, N, 1, sA, sB, spartial, per_buf, true, st, false, false);
   if (s != HANKEL_OK) {
     if (cur >= 0 && cur != d->device) cudaSetDevice(cur);
     return s;

@@ -4,12 +4,14 @@
 // the request table and the queue under the lock; the dispatcher
 //  1. retires finished batches (event query), copies results to the callers' host arrays and
 //     records each request's latency;
-//  2. fills idle streams: it takes the oldest queued request whose plan is idle, gathers the
-//     queued requests of the same plan (FIFO, up to max_batch vectors), builds the plan if it
-//     is not cached (evicting idle plans, least recently used first, while the device memory
-//     held exceeds the cap), packs the coefficients into the stream's pinned buffer and issues
-//     copy-in, batched execution and copy-out on the stream (or replays them from a captured
-//     CUDA graph).
+//  2. fills idle streams: it takes the oldest queued request whose plan has an idle execution
+//     context (or may get one more: up to contexts_per_plan, while the device memory allows),
+//     gathers the queued requests of the same plan (FIFO, up to max_batch vectors), builds the
+//     plan if it is not cached (evicting idle plans, least recently used first, while the device
+//     memory held exceeds the cap), packs the coefficients into the stream's pinned buffer and
+//     issues copy-in, batched execution on that context and copy-out on the stream (or replays
+//     them from a captured CUDA graph). So a request for a plan whose batch is on the GPU is
+//     admitted as soon as a stream and a context are free, and its work overlaps the other's.
 #include <cuda_runtime_api.h>
 #include <string.h>
 
@@ -24,6 +26,10 @@
 #include <vector>
 
 #include "hankel.h"
+
+namespace hk {
+bool alloc_fault();  // api.cpp: hankel_debug_fail_allocs
+}
 
 namespace {
 
@@ -47,10 +53,22 @@ struct Request {
 struct PlanEntry {
   hankel_plan_t plan = nullptr;
   size_t bytes = 0;
-  bool busy = false;
+  size_t ctx_bytes = 0;         // device bytes of one more execution context
+  std::vector<char> ctx_busy;   // per execution context: a batch is in flight on it
+  int ctx_limit = 1 << 30;      // contexts the memory cap allowed at the last failed attempt to add one
   int64_t runs = 0;
   uint64_t last_used = 0;
-  std::map<std::pair<int, int>, cudaGraphExec_t> graphs;  // (stream slot, nrhs) -> graph
+  std::map<std::tuple<int, int, int>, cudaGraphExec_t> graphs;  // (stream slot, context, nrhs) -> graph
+  bool any_busy() const {
+    for (char b : ctx_busy)
+      if (b) return true;
+    return false;
+  }
+  int idle_ctx() const {
+    for (size_t i = 0; i < ctx_busy.size(); ++i)
+      if (!ctx_busy[i]) return (int)i;
+    return -1;
+  }
 };
 
 // A request as the dispatcher carries it through a batch (copied under the lock).
@@ -74,6 +92,7 @@ struct Slot {
   bool busy = false;
   std::vector<Item> items;
   Key key;
+  int ctx = 0;  // the plan's execution context the batch runs on
   int64_t N = 0;
 };
 
@@ -102,7 +121,7 @@ namespace {
 void drop_slot_graphs(hankel_server_s* s, int slot) {
   for (auto& kv : s->plans) {
     for (auto it = kv.second.graphs.begin(); it != kv.second.graphs.end();) {
-      if (it->first.first == slot) {
+      if (std::get<0>(it->first) == slot) {
         cudaGraphExecDestroy(it->second);
         it = kv.second.graphs.erase(it);
       } else {
@@ -134,8 +153,8 @@ int ensure_slot_capacity(hankel_server_s* s, int i, size_t need, bool staging) {
     if (sl.f_dev) cudaFree(sl.f_dev);
     sl.c_dev = sl.f_dev = nullptr;
     sl.cap = 0;
-    if (cudaMalloc((void**)&sl.c_dev, cap * sizeof(double)) != cudaSuccess ||
-        cudaMalloc((void**)&sl.f_dev, cap * sizeof(double)) != cudaSuccess) {
+    if (hk::alloc_fault() || cudaMalloc((void**)&sl.c_dev, cap * sizeof(double)) != cudaSuccess ||
+        hk::alloc_fault() || cudaMalloc((void**)&sl.f_dev, cap * sizeof(double)) != cudaSuccess) {
       cudaGetLastError();
       free_slot_buffers(sl);
       return HANKEL_ENOMEM;
@@ -148,8 +167,8 @@ int ensure_slot_capacity(hankel_server_s* s, int i, size_t need, bool staging) {
     if (sl.f_pin) cudaFreeHost(sl.f_pin);
     sl.c_pin = sl.f_pin = nullptr;
     sl.pin_cap = 0;
-    if (cudaMallocHost((void**)&sl.c_pin, cap * sizeof(double)) != cudaSuccess ||
-        cudaMallocHost((void**)&sl.f_pin, cap * sizeof(double)) != cudaSuccess) {
+    if (hk::alloc_fault() || cudaMallocHost((void**)&sl.c_pin, cap * sizeof(double)) != cudaSuccess ||
+        hk::alloc_fault() || cudaMallocHost((void**)&sl.f_pin, cap * sizeof(double)) != cudaSuccess) {
       cudaGetLastError();
       s->slot_bytes -= 2 * sl.cap * sizeof(double);
       drop_slot_graphs(s, i);
@@ -167,6 +186,7 @@ void destroy_plan(hankel_server_s* s, PlanEntry& pe) {
   hankel_destroy(pe.plan);
   s->plan_bytes -= pe.bytes;
   pe.plan = nullptr;
+  for (auto& kv : s->plans) kv.second.ctx_limit = 1 << 30;  // memory was freed: contexts may be added again
 }
 
 // Cached plan for key, built on a miss; idle plans are evicted (LRU) while over the cap.
@@ -186,6 +206,8 @@ int get_plan(hankel_server_s* s, const Key& key, PlanEntry** out) {
     PlanEntry pe;
     pe.plan = p;
     pe.bytes = info.device_bytes;
+    pe.ctx_bytes = info.context_bytes;
+    pe.ctx_busy.assign((size_t)info.contexts, 0);
     s->plan_bytes += pe.bytes;
     it = s->plans.emplace(key, pe).first;
     std::lock_guard<std::mutex> lk(s->mu);
@@ -196,7 +218,8 @@ int get_plan(hankel_server_s* s, const Key& key, PlanEntry** out) {
   while (s->plan_bytes + s->slot_bytes > cap) {
     auto victim = s->plans.end();
     for (auto jt = s->plans.begin(); jt != s->plans.end(); ++jt)
-      if (jt != it && !jt->second.busy && (victim == s->plans.end() || jt->second.last_used < victim->second.last_used))
+      if (jt != it && !jt->second.any_busy() &&
+          (victim == s->plans.end() || jt->second.last_used < victim->second.last_used))
         victim = jt;
     if (victim == s->plans.end()) break;  // only busy plans left: admit and let them retire
     destroy_plan(s, victim->second);
@@ -208,11 +231,50 @@ int get_plan(hankel_server_s* s, const Key& key, PlanEntry** out) {
   return HANKEL_OK;
 }
 
+// An idle execution context of pe: an existing one, or a new one while the plan has fewer than
+// contexts_per_plan and the device memory cap allows it (idle plans are evicted to make room).
+// Returns -1 when every context is busy and no other can be made now.
+int take_context(hankel_server_s* s, const Key& key, PlanEntry& pe) {
+  int k = pe.idle_ctx();
+  if (k >= 0) return k;
+  if ((int)pe.ctx_busy.size() >= std::min(s->opt.contexts_per_plan, pe.ctx_limit)) return -1;
+  while (s->plan_bytes + s->slot_bytes + pe.ctx_bytes > s->opt.memory_cap) {
+    auto victim = s->plans.end();
+    for (auto jt = s->plans.begin(); jt != s->plans.end(); ++jt)
+      if (jt->first != key && !jt->second.any_busy() &&
+          (victim == s->plans.end() || jt->second.last_used < victim->second.last_used))
+        victim = jt;
+    if (victim == s->plans.end()) {
+      pe.ctx_limit = (int)pe.ctx_busy.size();
+      return -1;
+    }
+    destroy_plan(s, victim->second);
+    s->plans.erase(victim);
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stats.plans_evicted++;
+  }
+  int idx = -1;
+  const int st = hankel_plan_add_context(pe.plan, &idx);
+  hankel_info info;
+  hankel_plan_info(pe.plan, &info);  // a failed attempt may still hold some of its memory
+  s->plan_bytes += info.device_bytes - pe.bytes;
+  pe.bytes = info.device_bytes;
+  if (st != HANKEL_OK) {
+    pe.ctx_limit = (int)pe.ctx_busy.size();  // until memory is freed by an eviction
+    return -1;
+  }
+  pe.ctx_busy.resize((size_t)info.contexts, 0);
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->stats.contexts_added++;
+  return idx;
+}
+
 // Issue copy-in, execution and copy-out of a packed batch on slot i. Page-locked request
 // arrays are copied straight to and from the slot's device buffers; the others go through the
 // slot's staging buffers (filled by dispatch, emptied by retire). With graphs, the execution
 // alone is captured once per (slot, batch size) and replayed between the copies.
-int launch_batch(hankel_server_s* s, int i, PlanEntry& pe, int64_t N, int nrhs, const std::vector<Item>& batch) {
+int launch_batch(hankel_server_s* s, int i, PlanEntry& pe, int ctx, int64_t N, int nrhs,
+                 const std::vector<Item>& batch) {
   Slot& sl = s->slots[i];
   size_t off = 0;
   for (const Item& it : batch) {
@@ -222,12 +284,12 @@ int launch_batch(hankel_server_s* s, int i, PlanEntry& pe, int64_t N, int nrhs, 
       return HANKEL_ECUDA;
     off += n;
   }
-  auto exec = [&]() { return hankel_exec_batched(pe.plan, sl.c_dev, N, sl.f_dev, N, nrhs, sl.stream); };
+  auto exec = [&]() { return hankel_exec_batched_ctx(pe.plan, ctx, sl.c_dev, N, sl.f_dev, N, nrhs, sl.stream); };
   int st = HANKEL_OK;
   if (!s->opt.use_graphs || pe.runs == 0) {
     st = exec();  // the first run configures kernels uncaptured
   } else {
-    auto key = std::make_pair(i, nrhs);
+    auto key = std::make_tuple(i, ctx, nrhs);
     auto it = pe.graphs.find(key);
     if (it == pe.graphs.end()) {
       cudaGraph_t g = nullptr;
@@ -297,7 +359,7 @@ bool retire(hankel_server_s* s) {
       }
     }
     auto pit = s->plans.find(sl.key);
-    if (pit != s->plans.end()) pit->second.busy = false;
+    if (pit != s->plans.end() && sl.ctx < (int)pit->second.ctx_busy.size()) pit->second.ctx_busy[sl.ctx] = 0;
     finish(s, sl.items, status);
     sl.items.clear();
     sl.busy = false;
@@ -313,9 +375,11 @@ bool dispatch(hankel_server_s* s, int i) {
   int nrhs = 0;
   {
     std::lock_guard<std::mutex> lk(s->mu);
+    // a plan is busy when every context it has or may still get carries a batch
     auto busy = [&](const Key& k) {
       auto it = s->plans.find(k);
-      return it != s->plans.end() && it->second.busy;
+      return it != s->plans.end() && it->second.idle_ctx() < 0 &&
+             (int)it->second.ctx_busy.size() >= std::min(s->opt.contexts_per_plan, it->second.ctx_limit);
     };
     // the oldest queued request whose plan is idle and whose batch is ready: full, packing off,
     // no request of the plan arrived within the batch window (a burst of submissions stays one
@@ -356,6 +420,17 @@ bool dispatch(hankel_server_s* s, int i) {
   const int64_t N = std::get<2>(key);
   bool staging = false;
   for (const Item& it : batch) staging = staging || !it.c_pinned || !it.f_pinned;
+  int ctx = -1;
+  if (st == HANKEL_OK) {
+    ctx = take_context(s, key, *pe);
+    if (ctx < 0) {
+      // no context can be had now (memory): put the batch back at the front of the queue; it
+      // is dispatched once a batch of this plan retires
+      std::lock_guard<std::mutex> lk(s->mu);
+      for (auto it = batch.rbegin(); it != batch.rend(); ++it) s->queue.push_front(it->ticket);
+      return false;
+    }
+  }
   if (st == HANKEL_OK) st = ensure_slot_capacity(s, i, (size_t)N * nrhs, staging);
   if (st != HANKEL_OK) {
     finish(s, batch, st);
@@ -367,7 +442,7 @@ bool dispatch(hankel_server_s* s, int i) {
     if (!it.c_pinned) memcpy(sl.c_pin + off, it.c, (size_t)N * it.nrhs * sizeof(double));
     off += (size_t)N * it.nrhs;
   }
-  st = launch_batch(s, i, *pe, N, nrhs, batch);
+  st = launch_batch(s, i, *pe, ctx, N, nrhs, batch);
   if (st == HANKEL_OK && cudaEventRecord(sl.done, sl.stream) != cudaSuccess) st = HANKEL_ECUDA;
   if (st != HANKEL_OK) {
     cudaStreamSynchronize(sl.stream);
@@ -375,11 +450,12 @@ bool dispatch(hankel_server_s* s, int i) {
     finish(s, batch, st);
     return true;
   }
-  pe->busy = true;
+  pe->ctx_busy[ctx] = 1;
   pe->runs++;
   sl.busy = true;
   sl.items = batch;
   sl.key = key;
+  sl.ctx = ctx;
   sl.N = N;
   std::lock_guard<std::mutex> lk(s->mu);
   s->stats.batches++;
@@ -422,6 +498,7 @@ int hankel_server_options_default(hankel_server_options* o) {
   o->precision = HANKEL_PREC_AUTO;
   o->pack_requests = 1;
   o->batch_window_us = 200;
+  o->contexts_per_plan = 2;
   return HANKEL_OK;
 }
 
@@ -433,6 +510,7 @@ int hankel_server_create(hankel_server_t* out, const hankel_server_options* o) {
   if (o) opt = *o;
   if (opt.memory_cap == 0) opt.memory_cap = kDefaultCap;
   if (opt.streams < 1 || opt.streams > 16 || opt.max_batch < 1 || opt.batch_window_us < 0) return HANKEL_EINVAL;
+  if (opt.contexts_per_plan < 1 || opt.contexts_per_plan > 8) return HANKEL_EINVAL;
   if (opt.precision != HANKEL_PREC_AUTO && opt.precision != HANKEL_PREC_FP64 && opt.precision != HANKEL_PREC_MIXED)
     return HANKEL_EINVAL;
   hankel_server_s* s = new hankel_server_s();
@@ -504,6 +582,26 @@ int hankel_server_wait(hankel_server_t s, int64_t ticket, int* status, double* l
   const Request& r = s->reqs[ticket];
   if (status) *status = r.status;
   if (latency_ms) *latency_ms = std::chrono::duration<double, std::milli>(r.t_done - r.t_submit).count();
+  return HANKEL_OK;
+}
+
+int hankel_server_cancel(hankel_server_t s, int64_t ticket, int* cancelled) {
+  if (!s) return HANKEL_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (ticket < 0 || ticket >= (int64_t)s->reqs.size()) return HANKEL_EINVAL;
+  if (cancelled) *cancelled = 0;
+  auto it = std::find(s->queue.begin(), s->queue.end(), ticket);
+  if (it == s->queue.end()) return HANKEL_OK;  // in a batch already, or done
+  s->queue.erase(it);
+  Request& r = s->reqs[ticket];
+  r.done = true;
+  r.status = HANKEL_ECANCELED;
+  r.t_done = Clock::now();
+  s->outstanding--;
+  s->stats.failed++;
+  s->stats.cancelled++;
+  if (cancelled) *cancelled = 1;
+  s->cv_done.notify_all();
   return HANKEL_OK;
 }
 

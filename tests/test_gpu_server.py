@@ -164,3 +164,104 @@ def test_served_results_against_oracle(precision):
         bound = 10 * eps * np.abs(c).sum(axis=1, keepdims=True)
         assert np.all(np.abs(f.reshape(c.shape) - ref) <= bound), (task, N, eps)
     srv.close()
+
+
+def test_plan_contexts_run_side_by_side():
+    # two execution contexts of one plan on two streams at once: each result equals the one run
+    # alone on context 0 (same plan, same arithmetic: bitwise)
+    N = 2 ** 15
+    plan = hk.Plan("dht", 0, N, 1e-15, max_nrhs=4)
+    assert plan.info["contexts"] == 1
+    assert plan.add_context() == 1
+    info = plan.info
+    assert info["contexts"] == 2 and 0 < info["context_bytes"] < info["device_bytes"]
+    a = torch.from_numpy(coefficients("normal", N, 4, 950)).cuda()
+    b = torch.from_numpy(coefficients("normal", N, 3, 951)).cuda()
+    ra = plan.exec(a).clone()
+    rb = plan.exec(b).clone()
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    torch.cuda.synchronize()
+    for _ in range(3):
+        fa = plan.exec(a, stream=s1, context=0)
+        fb = plan.exec(b, stream=s2, context=1)
+        torch.cuda.synchronize()
+        assert torch.equal(fa, ra) and torch.equal(fb, rb)
+
+
+def test_two_batches_of_one_plan_in_flight():
+    # a burst for one plan with small batches: the server adds a second context to the plan and
+    # runs two of its batches at once; every result meets the bar against the oracle
+    N = 2 ** 16
+    srv = hk.Server(streams=4, max_batch=2, use_graphs=True, batch_window_us=0, contexts_per_plan=2)
+    cs = [coefficients("normal", N, 1, 960 + i) for i in range(12)]
+    tickets = [srv.submit("dht", 0, N, 1e-8, c) for c in cs]
+    for tk, _ in tickets:
+        srv.wait(tk)
+    st = srv.stats()
+    assert st["contexts_added"] >= 1 and st["failed"] == 0
+    rows = np.arange(0, N, 97)
+    for c, (_, f) in zip(cs, tickets):
+        ref = oracle.transform("dht", 0, N, c, rows=rows)
+        assert np.all(np.abs(f.reshape(1, N)[:, rows] - ref) <= 10 * 1e-8 * np.abs(c).sum())
+    srv.close()
+
+
+def test_injected_allocation_failure_in_admission():
+    # a plan build (or slot buffer) that cannot get device memory fails that request with ENOMEM;
+    # the server keeps serving the others, and the same request succeeds once memory is there
+    srv = hk.Server(streams=2, max_batch=4)
+    try:
+        c = coefficients("uniform", 3000, 1, 970)
+        t, f = srv.submit("schlomilch", 0, 3000, 1e-8, c)
+        srv.wait(t)  # plan cached, slot buffers made
+        hk.debug_fail_allocs(0, 1)
+        c2 = coefficients("uniform", 5000, 2, 971)
+        t2, _ = srv.submit("fourier_bessel", 0, 5000, 1e-8, c2)  # a new plan: its first allocation fails
+        assert srv.status(t2)[0] == "HANKEL_ENOMEM"
+        hk.debug_fail_allocs(0, 0)
+        t3, f3 = srv.submit("schlomilch", 0, 3000, 1e-8, c)  # the cached plan still serves
+        srv.wait(t3)
+        assert np.array_equal(f3, f)
+        t4, f4 = srv.submit("fourier_bessel", 0, 5000, 1e-8, c2)
+        srv.wait(t4)
+        ref = oracle.transform("fourier_bessel", 0, 5000, c2)
+        assert np.all(np.abs(f4 - ref) <= 10 * 1e-8 * np.abs(c2).sum(axis=1, keepdims=True))
+        st = srv.stats()
+        assert st["failed"] == 1 and st["completed"] == 3
+    finally:
+        hk.debug_fail_allocs(0, 0)
+        srv.close()
+
+
+@pytest.mark.parametrize("after", [0, 5, 20])
+def test_injected_allocation_failure_in_plan_creation(after):
+    # plan creation that runs out of device memory part way returns ENOMEM and frees what it made
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    hk.debug_fail_allocs(after, 1)
+    try:
+        with pytest.raises(RuntimeError, match="ENOMEM"):
+            hk.Plan("dht", 0, 20000, 1e-15, max_nrhs=8)
+    finally:
+        hk.debug_fail_allocs(0, 0)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    p = hk.Plan("dht", 0, 20000, 1e-15, max_nrhs=8)
+    assert p.info["device_bytes"] > 0
+
+
+def test_cancel_queued_requests():
+    # one stream, one request at a time: requests behind the first can still be cancelled
+    N = 2 ** 17
+    srv = hk.Server(streams=1, max_batch=1, pack=False)
+    cs = [coefficients("normal", N, 1, 980 + i) for i in range(10)]
+    tickets = [srv.submit("dht", 0, N, 1e-15, c)[0] for c in cs]
+    cancelled = [srv.cancel(t) for t in tickets[5:]]
+    assert any(cancelled)
+    for t, cn in zip(tickets[5:], cancelled):
+        assert srv.status(t)[0] == ("HANKEL_ECANCELED" if cn else "HANKEL_OK")
+    for t in tickets[:5]:
+        assert srv.status(t)[0] == "HANKEL_OK"
+    st = srv.stats()
+    assert st["cancelled"] == sum(cancelled) and st["completed"] == 10 - sum(cancelled)
+    srv.close()

@@ -5,6 +5,7 @@ import os
 import pytest
 
 import paper_1501_01652_gb300 as hk
+from paper_1501_01652_gb300 import _lib
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -119,3 +120,11 @@ def test_unsupported_requests():
         hk.params("schlomilch", 0, 100, 1e-17)
     with pytest.raises(RuntimeError, match="EUNSUPPORTED"):
         hk.params("schlomilch", 0, 100, 1e-8, precision="fp32")
+
+
+def test_status_strings_and_fault_injection_arguments():
+    lib = _lib.load()
+    assert lib.hankel_status_string(6) == b"request cancelled"
+    assert lib.hankel_status_string(99) == b"unknown status"
+    assert lib.hankel_debug_fail_allocs(-1, 1) == 1   # EINVAL
+    assert lib.hankel_debug_fail_allocs(0, 0) == 0
