@@ -114,6 +114,10 @@ enum hankel_status {
 #define HANKEL_FLAG_NO_AUTOTUNE 128u /* split every transform into launches by the built-in rule; by default
                                         the plan measures the candidate splits of each transform length it
                                         runs (hankel_fft_shape) once per GPU model and uses the fastest */
+#define HANKEL_FLAG_TENSOR_FFT 256u  /* FP64 transforms of 2^12 points or more run as many of their passes as
+                                        their length allows as radix-32 passes on the tensor cores (split-digit
+                                        products in FP64 accuracy), the rest on the FP64 pipe, without
+                                        autotuning; the autotuner otherwise weighs these splits with the others */
 
 /* Options for hankel_plan_ex(). Fill with hankel_options_default() first. */
 typedef struct {
@@ -169,6 +173,8 @@ typedef struct {
   int one_launch;      /* 1: the whole transform in one launch (F <= 4096) */
   int npass;           /* otherwise 2..4 passes, */
   int log2_radix[4];   /* of radix 2^log2_radix[i] (5..8 each, summing to log2_len), first to last */
+  int tensor_passes;   /* bit i: pass i runs on the tensor cores (radix 32, FP64 transforms of 2^12 points or
+                          more; split-digit products in FP64 accuracy), else on the FP64 pipe */
   double ms_default;   /* measured time of the built-in split on the tuning columns (0: not measured) */
   double ms_chosen;    /* measured time of the chosen split */
 } hankel_fft_shape;
@@ -314,6 +320,11 @@ int hankel_plan_expansion_entry(hankel_plan_t p, int64_t k, int64_t n, double* v
  * or from the cache without a measurement in this process). Host only. */
 int hankel_plan_fft_shapes(hankel_plan_t p, hankel_fft_shape* out, int cap, int* count);
 
+/* Status of the plan's bounded device waits since the last call: HANKEL_OK, or HANKEL_ETIMEOUT when a
+ * tensor-core transform pass gave up waiting for its operand copy or its products (its outputs
+ * are then unspecified). Blocking (reads one word from the device); clears the status. */
+int hankel_plan_device_status(hankel_plan_t p);
+
 /* The autotuner's shape cache, keyed by (GPU name, precision, log2_len, col_bucket). Plans look a
  * key up before measuring it, and store what they measure. When the environment variable
  * HANKEL_TUNE_CACHE names a file, the first plan of the process loads it and every new entry is
@@ -451,6 +462,16 @@ int hankel_server_destroy(hankel_server_t s);
  * HANKEL_ENOMEM, or a server request completes with it). count = 0 turns injection off.
  * Process-wide; for tests of the error paths of plan creation and request admission. */
 int hankel_debug_fail_allocs(int64_t after, int64_t count);
+
+/* Test access to the multi-column FFT of the far field: ncols columns of 2^log2_len seeded
+ * pseudo-random FP64 complex values are transformed (forward, or inverse when inverse != 0) by the
+ * built-in FP64 split and by the given one (npass passes of radix 2^log2_radix[i], tensor_passes a
+ * bit mask of passes on the tensor cores, as in hankel_fft_shape). *err receives
+ * max |difference| / max |built-in result|, *ms the time of the given split (fastest of three
+ * runs). Allocates and frees its own device memory; blocking. Errors: EINVAL (a split that is not
+ * valid for the length), ENOMEM, ECUDA, ETIMEOUT (a tensor-core pass gave up a wait). */
+int hankel_debug_fft_compare(int log2_len, int ncols, int inverse, int npass, const int* log2_radix,
+                             int tensor_passes, double* err, double* ms);
 
 /* ---- Host-only parameter formulas (no plan, no GPU) ---- */
 

@@ -18,7 +18,8 @@ PRECISIONS = {"auto": 0, "fp64": 1, "fp32": 2, "df64": 3, "mixed": 4}
 
 
 def _options(task, nu, N, eps, grid="unit", gamma=None, precision="auto", max_nrhs=1, workspace_limit=0,
-             host_only=False, segment=True, prune=True, refine=True, lowrank=True, mixed_terms=True, autotune=True):
+             host_only=False, segment=True, prune=True, refine=True, lowrank=True, mixed_terms=True, autotune=True,
+             tensor_fft=False):
     lib = _lib.load()
     o = _lib.Options()
     _lib.check(lib.hankel_options_default(ctypes.byref(o), TASKS[task], int(nu), int(N), float(eps)),
@@ -32,7 +33,8 @@ def _options(task, nu, N, eps, grid="unit", gamma=None, precision="auto", max_nr
     o.flags = ((_lib.FLAG_HOST_ONLY if host_only else 0) | (0 if segment else _lib.FLAG_NO_SEGMENT)
                | (0 if prune else _lib.FLAG_ALL_COLUMNS)
                | (0 if refine else _lib.FLAG_NO_REFINE) | (0 if lowrank else _lib.FLAG_NO_LOWRANK)
-               | (0 if mixed_terms else _lib.FLAG_UNIFORM_TERMS) | (0 if autotune else _lib.FLAG_NO_AUTOTUNE))
+               | (0 if mixed_terms else _lib.FLAG_UNIFORM_TERMS) | (0 if autotune else _lib.FLAG_NO_AUTOTUNE)
+               | (_lib.FLAG_TENSOR_FFT if tensor_fft else 0))
     return o
 
 
@@ -83,7 +85,7 @@ def j0_zero_offsets(count):
 
 
 def tune_cache_put(gpu, precision, log2_len, col_bucket, radices=None, one_launch=False, ms_default=0.0,
-                   ms_chosen=0.0):
+                   ms_chosen=0.0, tensor_passes=0):
     """Store an FFT launch split in the autotuner's cache (precision: "fp64", "df64" or "fp32")."""
     s = _lib.FftShape()
     s.precision, s.log2_len, s.col_bucket = PRECISIONS[precision], int(log2_len), int(col_bucket)
@@ -93,6 +95,7 @@ def tune_cache_put(gpu, precision, log2_len, col_bucket, radices=None, one_launc
     for i, r in enumerate(radices[:4]):
         s.log2_radix[i] = int(r)
     s.ms_default, s.ms_chosen = float(ms_default), float(ms_chosen)
+    s.tensor_passes = int(tensor_passes)
     _lib.check(_lib.load().hankel_tune_cache_put(gpu.encode(), ctypes.byref(s)), "hankel_tune_cache_put")
 
 
@@ -121,6 +124,17 @@ def tune_bucket(ncols):
     return _lib.load().hankel_tune_bucket(int(ncols))
 
 
+def debug_fft_compare(log2_len, ncols, radices, tensor_passes=0, inverse=False):
+    """Test access: seeded FP64 data through the built-in FFT split and through the given one
+    (radices, bit mask of tensor-core passes); returns (max |diff| / max |ref|, ms of the given split)."""
+    arr = (ctypes.c_int * 4)(*(list(radices) + [0] * (4 - len(radices))))
+    err, ms = ctypes.c_double(), ctypes.c_double()
+    _lib.check(_lib.load().hankel_debug_fft_compare(int(log2_len), int(ncols), int(bool(inverse)), len(radices), arr,
+                                                    int(tensor_passes), ctypes.byref(err), ctypes.byref(ms)),
+               "hankel_debug_fft_compare")
+    return err.value, ms.value
+
+
 def debug_fail_allocs(after, count):
     """Make the library's next `count` device or page-locked allocations, after `after` successful
     ones, report failure (host-side fault injection for tests; count = 0 turns it off)."""
@@ -132,13 +146,13 @@ class Plan:
 
     def __init__(self, task, nu, N, eps, grid="unit", gamma=None, precision="auto", max_nrhs=1,
                  workspace_limit=0, host_only=False, segment=True, prune=True, refine=True, lowrank=True,
-                 mixed_terms=True, autotune=True):
+                 mixed_terms=True, autotune=True, tensor_fft=False):
         self._lib = _lib.load()
         self._h = ctypes.c_void_p()
         self.task, self.nu, self.N, self.eps = task, int(nu), int(N), float(eps)
         self.max_nrhs = int(max_nrhs)
         o = _options(task, nu, N, eps, grid, gamma, precision, max_nrhs, workspace_limit, host_only, segment,
-                     prune, refine, lowrank, mixed_terms, autotune)
+                     prune, refine, lowrank, mixed_terms, autotune, tensor_fft)
         _lib.check(self._lib.hankel_plan_ex(ctypes.byref(self._h), ctypes.byref(o)), "hankel_plan_ex")
 
     def __del__(self):
@@ -198,6 +212,11 @@ class Plan:
         ne = ctypes.c_int64()
         _lib.check(self._lib.hankel_plan_near_prefix(self._h, int(k), ctypes.byref(ne)), "hankel_plan_near_prefix")
         return ne.value
+
+    def device_status(self):
+        """Status of the plan's bounded device waits since the last call ("HANKEL_OK" or
+        "HANKEL_ETIMEOUT"); blocking."""
+        return _lib.STATUS_NAMES[self._lib.hankel_plan_device_status(self._h)]
 
     def set_timing(self, enable=True):
         """Turn per-stage CUDA-event timing on or off and reset the stage statistics."""

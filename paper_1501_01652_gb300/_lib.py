@@ -16,6 +16,7 @@ FLAG_NO_REFINE = 16
 FLAG_NO_LOWRANK = 32
 FLAG_UNIFORM_TERMS = 64
 FLAG_NO_AUTOTUNE = 128
+FLAG_TENSOR_FFT = 256
 
 # Every function include/hankel.h declares.
 EXPORTED = [
@@ -29,7 +30,8 @@ EXPORTED = [
     "hankel_server_drain", "hankel_server_get_stats", "hankel_server_destroy",
     "hankel_plan_fft_shapes", "hankel_tune_cache_put", "hankel_tune_cache_get", "hankel_tune_cache_save",
     "hankel_tune_cache_load", "hankel_tune_cache_clear", "hankel_tune_bucket", "hankel_plan_add_context",
-    "hankel_exec_batched_ctx", "hankel_server_cancel", "hankel_debug_fail_allocs",
+    "hankel_exec_batched_ctx", "hankel_server_cancel", "hankel_debug_fail_allocs", "hankel_plan_device_status",
+    "hankel_debug_fft_compare",
 ]
 STAGES = ["near", "gen", "fft", "pointwise", "out", "fft_df64", "fft_fp32"]
 
@@ -59,12 +61,14 @@ class Info(ctypes.Structure):
 class FftShape(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("log2_len", ctypes.c_int), ("col_bucket", ctypes.c_int),
                 ("one_launch", ctypes.c_int), ("npass", ctypes.c_int), ("log2_radix", ctypes.c_int * 4),
-                ("ms_default", ctypes.c_double), ("ms_chosen", ctypes.c_double)]
+                ("tensor_passes", ctypes.c_int), ("ms_default", ctypes.c_double), ("ms_chosen", ctypes.c_double)]
 
     def as_dict(self):
         return {"precision": self.precision, "log2_len": self.log2_len, "col_bucket": self.col_bucket,
                 "one_launch": bool(self.one_launch),
                 "radices": [] if self.one_launch else list(self.log2_radix[:self.npass]),
+                "tensor_passes": [] if self.one_launch else [bool((self.tensor_passes >> i) & 1)
+                                                             for i in range(self.npass)],
                 "ms_default": self.ms_default, "ms_chosen": self.ms_chosen}
 
 
@@ -153,6 +157,8 @@ def load():
         "hankel_exec_batched_ctx": (i32, [vp, i32, vp, i64, vp, i64, i32, vp]),
         "hankel_server_cancel": (i32, [vp, i64, ctypes.POINTER(i32)]),
         "hankel_debug_fail_allocs": (i32, [i64, i64]),
+        "hankel_plan_device_status": (i32, [vp]),
+        "hankel_debug_fft_compare": (i32, [i32, i32, i32, i32, ctypes.POINTER(i32), i32, dp, dp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

@@ -17,7 +17,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(OUT_DIR, "libhankel.so")
 HOST_SOURCES = ["api.cpp", "planner.cpp", "server.cpp", "tune_cache.cpp"]
-CUDA_SOURCES = ["exec.cu", "fft.cu", "far.cu", "near.cu"]
+CUDA_SOURCES = ["exec.cu", "fft.cu", "far.cu", "near.cu", "tcfft.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

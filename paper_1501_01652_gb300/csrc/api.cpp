@@ -196,6 +196,18 @@ int hankel_plan_blocks(hankel_plan_t p, hankel_block* out, int cap, int* count) 
   return HANKEL_OK;
 }
 
+int hankel_debug_fft_compare(int log2_len, int ncols, int inverse, int npass, const int* log2_radix,
+                             int tensor_passes, double* err, double* ms) {
+  if (!log2_radix || !err || !ms || npass < 2 || npass > 4 || ncols < 1 || log2_len < 6 || log2_len > 24)
+    return HANKEL_EINVAL;
+  return hk::debug_fft_compare_host(log2_len, ncols, inverse, npass, log2_radix, tensor_passes, err, ms);
+}
+
+int hankel_plan_device_status(hankel_plan_t p) {
+  if (!p || p->host_only) return HANKEL_EINVAL;
+  return hk::dev_device_status(p);
+}
+
 int hankel_plan_fft_shapes(hankel_plan_t p, hankel_fft_shape* out, int cap, int* count) {
   if (!p || !count || cap < 0 || (cap > 0 && !out)) return HANKEL_EINVAL;
   if (p->host_only) {

@@ -35,4 +35,8 @@ int dev_stage_stats(hankel_plan_s* p, hankel_stage_stat* out);
 size_t dev_plan_bytes(const hankel_plan_s* p);
 size_t dev_workspace_bytes(const hankel_plan_s* p);
 int dev_plan_shapes(const hankel_plan_s* p, hankel_fft_shape* out, int cap, int* count);
+int dev_device_status(hankel_plan_s* p);
+// hankel_debug_fft_compare on the current device.
+int debug_fft_compare_host(int logF, int ncols, int inverse, int npass, const int* logr, int tc, double* err,
+                           double* ms);
 }  // namespace hk

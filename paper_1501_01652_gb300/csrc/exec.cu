@@ -172,6 +172,11 @@ struct DevicePlan {
   std::vector<cudaEvent_t> pool;
   size_t pool_used = 0;
   std::vector<hankel_fft_shape> shapes;  // the transform shapes the plan runs (hankel_plan_fft_shapes)
+  // tensor-core FP64 passes: the DFT digit planes (forward, inverse) and the device error word
+  void* tcB = nullptr;
+  unsigned* tc_err = nullptr;
+  TcTables tct{};
+  const TcTables* tc() const { return tcB ? &tct : nullptr; }
 };
 
 namespace {
@@ -318,20 +323,35 @@ int public_precision(int t) { return t == kTermFP32 ? HANKEL_PREC_FP32 : t == kT
 // Candidate launch splits of a transform of 2^logF points: the built-in one first, then one
 // launch (logF <= 12) and every ordered split into 2..4 passes of radix 2^5 .. 2^8 (2^7 for
 // double-float, whose larger passes spill), fewest passes first, at most 24.
-std::vector<FftShape> shape_candidates(int logF, int ncols, int prec) {
+std::vector<FftShape> shape_candidates(int logF, int ncols, int prec, bool tc) {
   std::vector<FftShape> out{default_fft_shape(logF, ncols, prec)};
-  auto add = [&](const FftShape& sh) {
+  auto add1 = [&](const FftShape& sh) {
     for (const FftShape& o : out)
-      if (o.one_launch == sh.one_launch && o.npass == sh.npass &&
+      if (o.one_launch == sh.one_launch && o.npass == sh.npass && o.tc == sh.tc &&
           std::equal(o.logr, o.logr + o.npass, sh.logr))
         return;
-    if (out.size() < 24 && valid_fft_shape(sh, logF)) out.push_back(sh);
+    if (out.size() < 40 && valid_fft_shape(sh, logF)) out.push_back(sh);
+  };
+  // FP64 transforms of 2^12 points and more: also the variant with every radix-32 pass on the
+  // tensor cores
+  auto add = [&](FftShape sh) {
+    add1(sh);
+    if (tc && prec == kTermFP64 && !sh.one_launch && logF >= 12) {
+      int m = 0;
+      for (int i = 0; i < sh.npass; ++i)
+        if (sh.logr[i] == 5) m |= 1 << i;
+      if (m) {
+        sh.tc = m;
+        add1(sh);
+      }
+    }
   };
   if (logF <= 12) {
     FftShape one{};
     one.one_launch = 1;
     add(one);
   }
+  if (out.size() == 1) add(out[0]);  // the default's own tensor-core variant
   const int hi = prec == kTermDF64 ? 7 : 8;
   for (int np = 2; np <= 4; ++np) {
     int r[4] = {5, 5, 5, 5};
@@ -356,12 +376,12 @@ std::vector<FftShape> shape_candidates(int logF, int ncols, int prec) {
 // The fastest of three runs after one warm-up, in ms (1e30 when a launch is refused).
 template <class C>
 double time_shape(C* A, C* B, int logF, int ncols, const C* tw, int logFmax, const FftShape& sh, cudaEvent_t e0,
-                  cudaEvent_t e1) {
+                  cudaEvent_t e1, const TcTables* tc = nullptr) {
   double best = 1e30;
   for (int it = 0; it < 4; ++it) {
     C* res = nullptr;
     cudaEventRecord(e0, 0);
-    if (run_fft<C>(A, B, logF, ncols, false, tw, logFmax, 0, &res, nullptr, nullptr, 1, nullptr, &sh) != HANKEL_OK ||
+    if (run_fft<C>(A, B, logF, ncols, false, tw, logFmax, 0, &res, nullptr, nullptr, 1, nullptr, &sh, tc) != HANKEL_OK ||
         cudaGetLastError() != cudaSuccess)  // a split whose launch is refused is not a candidate
       return 1e30;
     cudaEventRecord(e1, 0);
@@ -376,8 +396,32 @@ double time_shape(C* A, C* B, int logF, int ncols, const C* tw, int logFmax, con
 // The shape of transforms of 2^logF points in precision prec over ncols columns per launch:
 // from the plan's list, the process cache (keyed by GPU model) or a measurement of the
 // candidates on the lane's workspace buffers A, B (bytes each), recorded in the plan's list.
+// The split with the most radix-32 tensor-core passes a length allows (the rest of its bits in 1-3
+// FP64 passes of radix 2^5..2^8 after them), or none.
+bool tensor_shape(int logF, FftShape* out) {
+  if (logF < 12) return false;
+  for (int n5 = std::min(4, logF / 5); n5 >= 1; --n5) {
+    const int rem = logF - 5 * n5, slots = 4 - n5;
+    int k = 0;
+    if (rem == 0) k = 0;
+    else if (slots >= 1 && rem >= 5 && rem <= 8) k = 1;
+    else if (slots >= 2 && rem >= 10 && rem <= 16) k = 2;
+    else if (slots >= 3 && rem >= 15 && rem <= 24) k = 3;
+    else continue;
+    FftShape sh{};
+    sh.npass = n5 + k;
+    for (int i = 0; i < n5; ++i) sh.logr[i] = 5;
+    for (int i = 0; i < k; ++i) sh.logr[n5 + i] = rem / k + (i < rem % k ? 1 : 0);
+    sh.tc = (1 << n5) - 1;
+    if (!valid_fft_shape(sh, logF)) continue;
+    *out = sh;
+    return true;
+  }
+  return false;
+}
+
 int plan_shape(DevicePlan* d, const std::string& gpu, bool tune, int prec, int logF, int64_t ncols, void* A, void* B,
-               size_t bytes, FftShape* out) {
+               size_t bytes, FftShape* out, bool force_tc = false) {
   const int bucket = tune_bucket(ncols);
   const int pp = public_precision(prec);
   for (const hankel_fft_shape& h : d->shapes)
@@ -385,6 +429,7 @@ int plan_shape(DevicePlan* d, const std::string& gpu, bool tune, int prec, int l
       out->one_launch = h.one_launch;
       out->npass = h.npass;
       std::copy(h.log2_radix, h.log2_radix + 4, out->logr);
+      out->tc = h.tensor_passes;
       return HANKEL_OK;
     }
   hankel_fft_shape h{};
@@ -393,10 +438,13 @@ int plan_shape(DevicePlan* d, const std::string& gpu, bool tune, int prec, int l
   h.col_bucket = bucket;
   FftShape sh = default_fft_shape(logF, (int)ncols, prec);
   bool cached = false;
+  if (force_tc && prec == kTermFP64 && d->tc() && tensor_shape(logF, &sh)) tune = false;
   if (tune) {
     hankel_fft_shape c{};
     if (tune_get(gpu, pp, logF, bucket, &c)) {
-      FftShape cs{c.one_launch, c.npass, {c.log2_radix[0], c.log2_radix[1], c.log2_radix[2], c.log2_radix[3]}};
+      FftShape cs{c.one_launch, c.npass, {c.log2_radix[0], c.log2_radix[1], c.log2_radix[2], c.log2_radix[3]},
+                  c.tensor_passes};
+      if (cs.tc && !d->tc()) cs.tc = 0;
       if (valid_fft_shape(cs, logF)) {
         sh = cs;
         cached = true;
@@ -413,7 +461,7 @@ int plan_shape(DevicePlan* d, const std::string& gpu, bool tune, int prec, int l
       if (cudaMemset(A, 0, (size_t)nt * F * esz) != cudaSuccess) return HANKEL_ECUDA;
       cudaEvent_t e0 = nullptr, e1 = nullptr;
       if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return HANKEL_ECUDA;
-      const std::vector<FftShape> cand = shape_candidates(logF, (int)ncols, prec);
+      const std::vector<FftShape> cand = shape_candidates(logF, (int)ncols, prec, d->tc() != nullptr);
       double tdef = 0.0, tbest = 1e30;
       FftShape best = cand[0];
       for (size_t i = 0; i < cand.size(); ++i) {
@@ -423,7 +471,8 @@ int plan_shape(DevicePlan* d, const std::string& gpu, bool tune, int prec, int l
         else if (prec == kTermDF64)
           t = time_shape<df64c>((df64c*)A, (df64c*)B, logF, (int)nt, d->twd, d->logFmax, cand[i], e0, e1);
         else
-          t = time_shape<double2>((double2*)A, (double2*)B, logF, (int)nt, d->tw, d->logFmax, cand[i], e0, e1);
+          t = time_shape<double2>((double2*)A, (double2*)B, logF, (int)nt, d->tw, d->logFmax, cand[i], e0, e1,
+                                  d->tc());
         if (i == 0) tdef = t;
         if (t < tbest) {
           tbest = t;
@@ -446,6 +495,7 @@ int plan_shape(DevicePlan* d, const std::string& gpu, bool tune, int prec, int l
   h.one_launch = sh.one_launch;
   h.npass = sh.npass;
   std::copy(sh.logr, sh.logr + 4, h.log2_radix);
+  h.tensor_passes = sh.tc;
   if (tune && !cached && h.ms_chosen > 0) tune_put(gpu, h);
   d->shapes.push_back(h);
   *out = sh;
@@ -570,6 +620,23 @@ int dev_plan_create(hankel_plan_s* p) {
   HK_TRY(dalloc(d, &d->tw, (size_t)2 << logFmax));
   for (int L = 6; L <= logFmax; ++L) launch_twiddles(d->tw + ((size_t)1 << L), L, 0);
   HK_LAUNCHED();
+  if (d->any_t[kTermFP64] && logFmax >= 12) {
+    // digit planes of the 32-point DFT for the tensor-core passes of FP64 transforms
+    const size_t nb = tc_dft_digits_bytes();
+    std::vector<unsigned char> host(2 * nb);
+    tc_dft_digits(0, host.data());
+    tc_dft_digits(1, host.data() + nb);
+    unsigned char* q = nullptr;
+    HK_TRY(upload(d, &q, host.data(), host.size()));
+    d->tcB = q;
+    HK_TRY(dalloc(d, &d->tc_err, 1));
+    if (cudaMemset(d->tc_err, 0, sizeof(unsigned)) != cudaSuccess) return HANKEL_ECUDA;
+    longlong2* twq = nullptr;
+    HK_TRY(dalloc(d, &twq, (size_t)2 << logFmax));
+    launch_twiddles_q62(d->tw + 64, twq + 64, (int64_t(2) << logFmax) - 64, 0);
+    HK_LAUNCHED();
+    d->tct = TcTables{q, q + nb, d->tc_err, twq};
+  }
   if (d->any_t[kTermFP32]) {
     HK_TRY(dalloc(d, &d->twf, (size_t)2 << logFmax));
     launch_scale_copy<float2>(d->tw + 64, d->twf + 64, (int64_t(2) << logFmax) - 64, 1.0, 0);
@@ -748,11 +815,118 @@ int dev_plan_create(hankel_plan_s* p) {
       const int64_t nfwd = tg.cap * (db.b.mode == kBlockRowSeg ? db.b.nseg : 1);
       const int64_t ninv = tg.cap * (db.b.mode == kBlockColSeg ? db.b.nseg : 1);
       const DevicePlan::Lane& ln = d->ctx[0]->lanes[l];
-      HK_TRY(plan_shape(d, gpu, tune, tg.prec, db.b.logF, nfwd, ln.A, ln.B, ln.buf_bytes, &tg.fwd));
-      HK_TRY(plan_shape(d, gpu, tune, tg.prec, db.b.logF, ninv, ln.A, ln.B, ln.buf_bytes, &tg.inv));
+      const bool ftc = (hp.opt.flags & HANKEL_FLAG_TENSOR_FFT) != 0;
+      HK_TRY(plan_shape(d, gpu, tune, tg.prec, db.b.logF, nfwd, ln.A, ln.B, ln.buf_bytes, &tg.fwd, ftc));
+      HK_TRY(plan_shape(d, gpu, tune, tg.prec, db.b.logF, ninv, ln.A, ln.B, ln.buf_bytes, &tg.inv, ftc));
     }
   if (cudaDeviceSynchronize() != cudaSuccess) return HANKEL_ECUDA;
   return HANKEL_OK;
+}
+
+int dev_fft_compare(int logF, int ncols, int inverse, const FftShape& sh, double* err, double* ms) {
+  const int64_t F = int64_t(1) << logF;
+  const size_t n = (size_t)ncols * F;
+  double2 *x = nullptr, *a = nullptr, *b = nullptr, *tw = nullptr;
+  longlong2* twq = nullptr;
+  void* bd = nullptr;
+  unsigned* flag = nullptr;
+  std::vector<double2> hx(n), h1(n), h2(n);
+  uint64_t st = 0x2545F4914F6CDD1DULL;
+  for (size_t i = 0; i < n; ++i) {
+    st = st * 6364136223846793005ULL + 1442695040888963407ULL;
+    const double re = (double)(st >> 11) * 0x1p-53 - 0.5;
+    st = st * 6364136223846793005ULL + 1442695040888963407ULL;
+    hx[i] = make_double2(re, (double)(st >> 11) * 0x1p-53 - 0.5);
+  }
+  const size_t nb = tc_dft_digits_bytes();
+  std::vector<unsigned char> hb(2 * nb);
+  tc_dft_digits(0, hb.data());
+  tc_dft_digits(1, hb.data() + nb);
+  int rc = HANKEL_OK;
+  auto cleanup = [&]() {
+    cudaFree(x);
+    cudaFree(a);
+    cudaFree(b);
+    cudaFree(tw);
+    cudaFree(twq);
+    cudaFree(bd);
+    cudaFree(flag);
+  };
+  if (cudaMalloc(&x, n * sizeof(double2)) != cudaSuccess || cudaMalloc(&a, n * sizeof(double2)) != cudaSuccess ||
+      cudaMalloc(&b, n * sizeof(double2)) != cudaSuccess || cudaMalloc(&tw, (size_t)2 * F * sizeof(double2)) != cudaSuccess ||
+      cudaMalloc(&bd, 2 * nb) != cudaSuccess || cudaMalloc(&flag, sizeof(unsigned)) != cudaSuccess ||
+      cudaMalloc(&twq, (size_t)2 * F * sizeof(longlong2)) != cudaSuccess) {
+    cudaGetLastError();
+    cleanup();
+    return HANKEL_ENOMEM;
+  }
+  for (int L = 6; L <= logF; ++L) launch_twiddles(tw + ((size_t)1 << L), L, 0);
+  launch_twiddles_q62(tw + 64, twq + 64, 2 * F - 64, 0);
+  cudaMemcpy(x, hx.data(), n * sizeof(double2), cudaMemcpyHostToDevice);
+  cudaMemcpy(bd, hb.data(), 2 * nb, cudaMemcpyHostToDevice);
+  cudaMemset(flag, 0, sizeof(unsigned));
+  const TcTables tt{bd, (unsigned char*)bd + nb, flag, twq};
+  double2* res = nullptr;
+  // reference: the built-in split
+  cudaMemcpy(a, x, n * sizeof(double2), cudaMemcpyDeviceToDevice);
+  if (run_fft<double2>(a, b, logF, ncols, inverse != 0, tw, logF, 0, &res) != HANKEL_OK) rc = HANKEL_EINVAL;
+  if (rc == HANKEL_OK) cudaMemcpy(h1.data(), res, n * sizeof(double2), cudaMemcpyDeviceToHost);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  double best = 1e30;
+  for (int it = 0; it < 4 && rc == HANKEL_OK; ++it) {
+    cudaMemcpy(a, x, n * sizeof(double2), cudaMemcpyDeviceToDevice);
+    cudaEventRecord(e0, 0);
+    if (run_fft<double2>(a, b, logF, ncols, inverse != 0, tw, logF, 0, &res, nullptr, nullptr, 1, nullptr, &sh, &tt) !=
+        HANKEL_OK)
+      rc = HANKEL_EINVAL;
+    cudaEventRecord(e1, 0);
+    if (cudaEventSynchronize(e1) != cudaSuccess) rc = HANKEL_ECUDA;
+    float t = 0.f;
+    cudaEventElapsedTime(&t, e0, e1);
+    if (it > 0) best = std::min(best, (double)t);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc == HANKEL_OK && cudaGetLastError() != cudaSuccess) rc = HANKEL_ECUDA;
+  if (rc == HANKEL_OK) {
+    cudaMemcpy(h2.data(), res, n * sizeof(double2), cudaMemcpyDeviceToHost);
+    unsigned fl = 0;
+    cudaMemcpy(&fl, flag, sizeof fl, cudaMemcpyDeviceToHost);
+    if (fl) rc = HANKEL_ETIMEOUT;
+  }
+  if (rc == HANKEL_OK) {
+    double dmax = 0.0, rmax = 0.0;
+    for (size_t i = 0; i < n; ++i) {
+      dmax = std::max(dmax, std::max(std::fabs(h1[i].x - h2[i].x), std::fabs(h1[i].y - h2[i].y)));
+      rmax = std::max(rmax, std::max(std::fabs(h1[i].x), std::fabs(h1[i].y)));
+    }
+    *err = rmax > 0 ? dmax / rmax : dmax;
+    *ms = best;
+  }
+  cleanup();
+  return rc;
+}
+
+int debug_fft_compare_host(int logF, int ncols, int inverse, int npass, const int* logr, int tc, double* err,
+                           double* ms) {
+  FftShape sh{};
+  sh.npass = npass;
+  for (int i = 0; i < npass; ++i) sh.logr[i] = logr[i];
+  sh.tc = tc;
+  if (!valid_fft_shape(sh, logF)) return HANKEL_EINVAL;
+  return dev_fft_compare(logF, ncols, inverse, sh, err, ms);
+}
+
+int dev_device_status(hankel_plan_s* p) {
+  DevicePlan* d = p->dev;
+  if (!d || !d->tc_err) return HANKEL_OK;
+  unsigned v = 0;
+  if (cudaMemcpy(&v, d->tc_err, sizeof v, cudaMemcpyDeviceToHost) != cudaSuccess) return HANKEL_ECUDA;
+  if (v == 0) return HANKEL_OK;
+  if (cudaMemset(d->tc_err, 0, sizeof(unsigned)) != cudaSuccess) return HANKEL_ECUDA;
+  return HANKEL_ETIMEOUT;
 }
 
 int dev_plan_shapes(const hankel_plan_s* p, hankel_fft_shape* out, int cap, int* count) {
@@ -838,7 +1012,8 @@ int run_block(DevicePlan* d, const DevicePlan::ExecCtx* x, const DevBlock& db, c
       const void* coef = Prec<C>::coef(x, c);
       const FftGen gen{rowseg ? b.nseg : 1, rowseg ? b.S : b.C, b.C, b.n0, c0, tg.nl, coef,
                        coef == (const void*)c ? ldc : d->hpN, tg.Vt};
-      HK_TRY(run_fft<C>(A, B, b.logF, (int)nfwd, false, tw, d->logFmax, st, &res, &np, nullptr, 1, &gen, &tg.fwd));
+      HK_TRY(run_fft<C>(A, B, b.logF, (int)nfwd, false, tw, d->logFmax, st, &res, &np, nullptr, 1, &gen, &tg.fwd,
+                        d->tc()));
       HK_LAUNCHED();
       sc.done(np, 5.0 * (double)b.F * (double)b.logF * (double)nfwd, 0.0, 2.0 * sizeof(C) * (double)b.F * nfwd * np);
     }
@@ -855,7 +1030,7 @@ int run_block(DevicePlan* d, const DevicePlan::ExecCtx* x, const DevBlock& db, c
       StageScope sc(d, fst, st, record);
       int np = 0;
       HK_TRY(run_fft<C>(other, res, b.logF, (int)ninv, true, tw, d->logFmax, st, &res2, &np, nullptr, 1, nullptr,
-                        &tg.inv));
+                        &tg.inv, d->tc()));
       HK_LAUNCHED();
       sc.done(np, 5.0 * (double)b.F * (double)b.logF * (double)ninv, 0.0, 2.0 * sizeof(C) * (double)b.F * ninv * np);
     } else {
@@ -865,7 +1040,7 @@ int run_block(DevicePlan* d, const DevicePlan::ExecCtx* x, const DevBlock& db, c
       StageScope sc(d, fst, st, record);
       int np = 0;
       HK_TRY(run_fft<C>(res, other, b.logF, (int)ninv, true, tw, d->logFmax, st, &res2, &np, H,
-                        colseg ? b.nseg : 1, nullptr, &tg.inv));
+                        colseg ? b.nseg : 1, nullptr, &tg.inv, d->tc()));
       HK_LAUNCHED();
       // 5 F log2 F per transform plus 6 F for the folded complex products
       sc.done(np, (5.0 * (double)b.logF + 6.0) * (double)b.F * (double)ninv, 0.0,

@@ -650,11 +650,14 @@ FftShape default_fft_shape(int logF, int ncols, int prec) {
 }
 
 bool valid_fft_shape(const FftShape& sh, int logF) {
-  if (sh.one_launch) return logF >= 6 && logF <= kSmallLog;
+  if (sh.one_launch) return logF >= 6 && logF <= kSmallLog && sh.tc == 0;
   if (sh.npass < 2 || sh.npass > 4) return false;  // a pass leaves F / R >= kTile sequences
+  if (sh.tc & ~((1 << sh.npass) - 1)) return false;
   int sum = 0;
   for (int i = 0; i < sh.npass; ++i) {
     if (sh.logr[i] < 5 || sh.logr[i] > 8) return false;
+    // a tensor-core pass has radix 32 and tiles of 128 sequences within a column
+    if (((sh.tc >> i) & 1) && (sh.logr[i] != 5 || logF < 12)) return false;
     sum += sh.logr[i];
   }
   return sum == logF;
@@ -662,7 +665,7 @@ bool valid_fft_shape(const FftShape& sh, int logF) {
 
 template <class C>
 int run_fft(C* a, C* b, int logF, int ncols, bool inverse, const C* tw, int logFmax, cudaStream_t st, C** result,
-            int* npasses, const C* hmul, int64_t nseg, const FftGen* gen, const FftShape* shape) {
+            int* npasses, const C* hmul, int64_t nseg, const FftGen* gen, const FftShape* shape, const TcTables* tc) {
   if (logF < 6 || logF > logFmax || nseg < 1) return HANKEL_EINVAL;
   if (gen && (inverse || hmul || gen->nsegc < 1 || gen->ncols < 1)) return HANKEL_EINVAL;
   FftGen g0{};
@@ -672,7 +675,8 @@ int run_fft(C* a, C* b, int logF, int ncols, bool inverse, const C* tw, int logF
   tw += (size_t)1 << logF;
   logFmax = logF;
   const int prec = std::is_same<C, df64c>::value ? kTermDF64 : std::is_same<C, float2>::value ? kTermFP32 : kTermFP64;
-  const FftShape sh = (shape && valid_fft_shape(*shape, logF)) ? *shape : default_fft_shape(logF, ncols, prec);
+  FftShape sh = (shape && valid_fft_shape(*shape, logF)) ? *shape : default_fft_shape(logF, ncols, prec);
+  if (!tc || !std::is_same<C, double2>::value) sh.tc = 0;  // tensor-core passes: FP64 transforms with tables
   if (sh.one_launch) {
     // the whole transform in one launch
     if (inverse) launch_small_f<true, C>(logF, a, b, ncols, tw, logFmax, hmul, nseg, none, st);
@@ -690,8 +694,15 @@ int run_fft(C* a, C* b, int logF, int ncols, bool inverse, const C* tw, int logF
     done += lr;
     const int logS = logF - done;
     const C* h = i == 0 ? hmul : nullptr;
-    if (inverse) launch_pass_r<true, C>(lr, src, dst, logF, logS, ncols, tw, logFmax, h, nseg, none, st);
-    else launch_pass_r<false, C>(lr, src, dst, logF, logS, ncols, tw, logFmax, h, nseg, i == 0 ? g0 : none, st);
+    if ((sh.tc >> i) & 1) {
+      if constexpr (std::is_same<C, double2>::value)
+        launch_pass_tc(inverse, src, dst, logF, logS, ncols, tc->twq + ((size_t)1 << logF), h, nseg,
+                       (!inverse && i == 0) ? g0 : none, inverse ? tc->inv : tc->fwd, tc->err, st);
+    } else if (inverse) {
+      launch_pass_r<true, C>(lr, src, dst, logF, logS, ncols, tw, logFmax, h, nseg, none, st);
+    } else {
+      launch_pass_r<false, C>(lr, src, dst, logF, logS, ncols, tw, logFmax, h, nseg, i == 0 ? g0 : none, st);
+    }
     std::swap(src, dst);
   }
   *result = src;
@@ -700,11 +711,11 @@ int run_fft(C* a, C* b, int logF, int ncols, bool inverse, const C* tw, int logF
 }
 
 template int run_fft<double2>(double2*, double2*, int, int, bool, const double2*, int, cudaStream_t, double2**,
-                              int*, const double2*, int64_t, const FftGen*, const FftShape*);
+                              int*, const double2*, int64_t, const FftGen*, const FftShape*, const TcTables*);
 template int run_fft<float2>(float2*, float2*, int, int, bool, const float2*, int, cudaStream_t, float2**, int*,
-                             const float2*, int64_t, const FftGen*, const FftShape*);
+                             const float2*, int64_t, const FftGen*, const FftShape*, const TcTables*);
 template int run_fft<df64c>(df64c*, df64c*, int, int, bool, const df64c*, int, cudaStream_t, df64c**, int*,
-                            const df64c*, int64_t, const FftGen*, const FftShape*);
+                            const df64c*, int64_t, const FftGen*, const FftShape*, const TcTables*);
 template void launch_scale_copy<double2>(const double2*, double2*, int64_t, double, cudaStream_t);
 template void launch_scale_copy<float2>(const double2*, float2*, int64_t, double, cudaStream_t);
 template void launch_scale_copy<df64c>(const double2*, df64c*, int64_t, double, cudaStream_t);

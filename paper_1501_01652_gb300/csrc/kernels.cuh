@@ -141,8 +141,17 @@ struct FftShape {
   int one_launch;  // 1: the whole transform in one launch (2^6 .. 2^12 points)
   int npass;       // otherwise passes of radix 2^logr[i], first to last
   int logr[4];
+  int tc;          // bit i: pass i (radix 32, FP64 transforms of 2^12 or more points) runs on the tensor cores
 };
 
+// Tables of the tensor-core passes (tcfft.cu): the digit planes of the 32-point DFT matrix,
+// forward and inverse, in their shared-memory layout, and the plan's device error word.
+struct TcTables {
+  const void* fwd;
+  const void* inv;
+  unsigned* err;
+  const longlong2* twq;  // the twiddle ladder in Q62 integers (W_F^t at twq[F + t])
+};
 struct FftGen {
   int64_t nsegc, S, C, n0;
   int64_t c0;
@@ -151,6 +160,19 @@ struct FftGen {
   int64_t ldc;
   const void* Vt;
 };
+// Digit planes of the real 64 x 64 form of the 32-point DFT matrix (inverse: conjugated), written
+// into out (tc_dft_digits_bytes() bytes), host side.
+void tc_dft_digits(int inverse, void* out);
+size_t tc_dft_digits_bytes();
+// One radix-32 Stockham pass of 2^logF-point FP64 transforms (logF >= 12) over ncols columns on
+// the tensor cores: the mapping of k_fft_pass_reg<5>, with hmul or gen on its loads as there
+// (first passes only); twq is the Q62 twiddle table of this length (W_F^t at twq[t]).
+void launch_pass_tc(bool inverse, const double2* src, double2* dst, int logF, int logS, int ncols, const longlong2* twq,
+                    const double2* hmul, int64_t nseg, const FftGen& gen, const void* bdig, unsigned* err,
+                    cudaStream_t st);
+// twq[t] = round(tw[t] 2^62) (both parts), t < n.
+void launch_twiddles_q62(const double2* tw, longlong2* twq, int64_t n, cudaStream_t st);
+
 
 // Out-of-place multi-column FFT of length 2^logF over ncols contiguous columns,
 // ping-ponging between a (input) and b; *result receives the buffer holding the output.
@@ -165,14 +187,14 @@ struct FftGen {
 template <class C>
 int run_fft(C* a, C* b, int logF, int ncols, bool inverse, const C* tw, int logFmax, cudaStream_t st, C** result,
             int* npasses = nullptr, const C* hmul = nullptr, int64_t nseg = 1, const FftGen* gen = nullptr,
-            const FftShape* shape = nullptr);
+            const FftShape* shape = nullptr, const TcTables* tc = nullptr);
 // The built-in choice for a transform of 2^logF points over ncols columns in precision prec
 // (kTermFP64, kTermDF64, kTermFP32): one launch up to 4096 points unless that gives fewer CTAs
 // than SMs; otherwise the fewest passes of radix 2^5 .. 2^8 (2^6 for double-float), as equal
 // as possible, the larger first.
 FftShape default_fft_shape(int logF, int ncols, int prec);
 // Whether shape is a valid split of 2^logF points (passes of radix 2^5 .. 2^8 summing to logF,
-// or one launch for logF <= 12).
+// or one launch for logF <= 12; tensor-core passes only of radix 32 with logF >= 12).
 bool valid_fft_shape(const FftShape& shape, int logF);
 // out[cc][t] = sum_s in[cc*nseg + s][t] * H[s][t]   (overlap-add of column segments)
 template <class C>

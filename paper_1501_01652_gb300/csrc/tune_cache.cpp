@@ -3,7 +3,7 @@
 // Keys are (GPU name, precision, log2 length, column bucket): a shape measured on one GPU model
 // is reused by every later plan on that model in the process, and across processes through a
 // text file (HANKEL_TUNE_CACHE, or hankel_tune_cache_save/load). One line per entry:
-//   gpu name | precision log2_len col_bucket one_launch npass r0 r1 r2 r3 ms_default ms_chosen
+//   gpu name | precision log2_len col_bucket one_launch npass r0 r1 r2 r3 tensor_passes ms_default ms_chosen
 // The name goes first and ends at the last '|', so names with spaces are kept whole.
 #include <stdio.h>
 #include <stdlib.h>
@@ -32,16 +32,16 @@ bool parse_line(const char* line, std::string* gpu, hankel_fft_shape* s) {
   if (!bar || bar == line) return false;
   gpu->assign(line, (size_t)(bar - line));
   memset(s, 0, sizeof(*s));
-  const int n = sscanf(bar + 1, "%d %d %d %d %d %d %d %d %d %lf %lf", &s->precision, &s->log2_len, &s->col_bucket,
+  const int n = sscanf(bar + 1, "%d %d %d %d %d %d %d %d %d %d %lf %lf", &s->precision, &s->log2_len, &s->col_bucket,
                        &s->one_launch, &s->npass, &s->log2_radix[0], &s->log2_radix[1], &s->log2_radix[2],
-                       &s->log2_radix[3], &s->ms_default, &s->ms_chosen);
-  return n == 11 && !gpu->empty();
+                       &s->log2_radix[3], &s->tensor_passes, &s->ms_default, &s->ms_chosen);
+  return n == 12 && !gpu->empty();
 }
 
 void format_line(FILE* fh, const std::string& gpu, const hankel_fft_shape& s) {
-  fprintf(fh, "%s|%d %d %d %d %d %d %d %d %d %.6g %.6g\n", gpu.c_str(), s.precision, s.log2_len, s.col_bucket,
-          s.one_launch, s.npass, s.log2_radix[0], s.log2_radix[1], s.log2_radix[2], s.log2_radix[3], s.ms_default,
-          s.ms_chosen);
+  fprintf(fh, "%s|%d %d %d %d %d %d %d %d %d %d %.6g %.6g\n", gpu.c_str(), s.precision, s.log2_len, s.col_bucket,
+          s.one_launch, s.npass, s.log2_radix[0], s.log2_radix[1], s.log2_radix[2], s.log2_radix[3], s.tensor_passes,
+          s.ms_default, s.ms_chosen);
 }
 
 int load_file(const char* path) {

@@ -472,3 +472,38 @@ def test_autotuned_shapes_are_recorded_and_exact():
     assert np.all(np.abs(ft[:, rows] - ref) <= 10 * 1e-15 * l1)
     # another split changes only the rounding of the transforms
     assert np.all(np.abs(ft - ff) <= 1e-15 * l1)
+
+
+# ---------------------------------------------------------------------------------------------
+# Radix-32 FFT passes on the tensor cores (split-digit products in FP64 accuracy)
+# ---------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("logF,ncols,radices,tc", [
+    (12, 4, [5, 7], 0b01), (12, 4, [7, 5], 0b10), (15, 8, [5, 5, 5], 0b111), (17, 4, [5, 6, 6], 0b001),
+    (20, 8, [5, 5, 5, 5], 0b1111), (21, 16, [5, 5, 5, 6], 0b0111), (22, 2, [5, 5, 5, 7], 0b0111),
+])
+@pytest.mark.parametrize("inverse", [False, True])
+def test_tensor_core_fft_passes(logF, ncols, radices, tc, inverse):
+    # the same seeded columns through the FP64 passes and through a split with tensor-core passes:
+    # they agree to FP64 rounding (max |difference| / max |output|)
+    err, ms = hk.debug_fft_compare(logF, ncols, radices, tc, inverse=inverse)
+    assert err <= 2e-15 and ms > 0
+
+
+@pytest.mark.parametrize("task,nu,N,eps,kind,nrhs", [
+    ("dht", 0, 2 ** 17, 1e-15, "normal", 4), ("dht", 0, 2 ** 16, 1e-8, "normal", 16),
+    ("fourier_bessel", 0, 2 ** 17, 1e-15, "uniform", 2), ("schlomilch", 1, 2 ** 17, 1e-15, "uniform", 2),
+    ("dht", 0, 2 ** 20, 1e-15, "normal", 16),
+])
+def test_tensor_core_fft_in_the_transform(task, nu, N, eps, kind, nrhs):
+    # FP64 transforms forced onto the tensor-core split (HANKEL_FLAG_TENSOR_FFT), element by element
+    # against the oracle on sampled rows, and within eps ||c||_1 of the FP64-pipe plan
+    c = coefficients(kind, N, nrhs, 8200 + N % 991)
+    rows = sample_rows(N, 64, 53)
+    f, plan = _run(task, nu, N, eps, c, tensor_fft=True)
+    assert any(any(s["tensor_passes"]) for s in plan.fft_shapes())
+    assert plan.device_status() == "HANKEL_OK"
+    ref = oracle.transform(task, nu, N, c, rows=rows)
+    l1 = np.abs(c).sum(axis=1, keepdims=True)
+    assert np.all(np.abs(f[:, rows] - ref) <= 10 * eps * l1)
+    g, _ = _run(task, nu, N, eps, c, autotune=False)
+    assert np.all(np.abs(f - g) <= eps * l1)
