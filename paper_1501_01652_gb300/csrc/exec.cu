@@ -458,7 +458,8 @@ int plan_shape(DevicePlan* d, const std::string& gpu, bool tune, int prec, int l
     int64_t nt = std::min<int64_t>(ncols, std::max<int64_t>(1, (int64_t(1) << 25) / F));
     nt = std::min<int64_t>(nt, (int64_t)(bytes / (F * esz)));
     if (nt >= 1) {
-      if (cudaMemset(A, 0, (size_t)nt * F * esz) != cudaSuccess) return HANKEL_ECUDA;
+      // measured on seeded values of unit size (zeros would take other paths in some kernels)
+      launch_fill_pattern(A, (size_t)nt * F * esz / sizeof(float), prec == kTermFP32 ? 1 : 0, 0);
       cudaEvent_t e0 = nullptr, e1 = nullptr;
       if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return HANKEL_ECUDA;
       const std::vector<FftShape> cand = shape_candidates(logF, (int)ncols, prec, d->tc() != nullptr);

@@ -225,6 +225,19 @@ __global__ void __launch_bounds__(256) k_diag_scale(const double* x, int64_t ldx
   }
 }
 
+// Seeded values in [-1/2, 1/2): doubles (as_float = 0) or floats over n 4-byte words.
+__global__ void k_fill_pattern(void* p, int64_t n, int as_float) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    unsigned long long h = (unsigned long long)t * 0x9E3779B97F4A7C15ULL;
+    h ^= h >> 29;
+    h *= 0xBF58476D1CE4E5B9ULL;
+    h ^= h >> 32;
+    const double v = (double)(h >> 11) * 0x1p-53 - 0.5;
+    if (as_float) reinterpret_cast<float*>(p)[t] = (float)v;
+    else if ((t & 1) == 0 && t + 1 < n) reinterpret_cast<double*>(p)[t >> 1] = v;
+  }
+}
+
 unsigned grid1d(int64_t n) {
   int64_t g = (n + 255) / 256;
   return (unsigned)std::min<int64_t>(std::max<int64_t>(g, 1), int64_t(152) * 32);
@@ -263,6 +276,10 @@ void launch_add_lanes(double* f, int64_t ldf, const double* const* acc, int nacc
                       cudaStream_t st) {
   const int64_t total = N * (int64_t)nrhs;
   k_add_lanes<<<grid1d(total), 256, 0, st>>>(f, ldf, acc[0], nacc > 1 ? acc[1] : nullptr, N, total);
+}
+
+void launch_fill_pattern(void* p, size_t words, int as_float, cudaStream_t st) {
+  k_fill_pattern<<<grid1d((int64_t)words), 256, 0, st>>>(p, (int64_t)words, as_float);
 }
 
 void launch_coef_exponent(const double* c, int64_t ldc, int64_t N, int nrhs, int* cexp, cudaStream_t st) {

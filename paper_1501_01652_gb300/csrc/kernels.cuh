@@ -115,6 +115,8 @@ void launch_add_lanes(double* f, int64_t ldf, const double* const* acc, int nacc
 // transform is linear, so the FP32 and double-float stages run on the coefficients scaled by that
 // power of two (exactly) and scale their sums back: their range then does not depend on the input's.
 void launch_coef_exponent(const double* c, int64_t ldc, int64_t N, int nrhs, int* cexp, cudaStream_t st);
+// Seeded values in [-1/2, 1/2) over `words` 4-byte words: floats (as_float) or doubles.
+void launch_fill_pattern(void* p, size_t words, int as_float, cudaStream_t st);
 // cf[r * N + i] = (float) (c[r * ldc + i] 2^-cexp[r]) for r < nrhs, i < N.
 void launch_coeffs_f32(const double* c, int64_t ldc, float* cf, int64_t N, int nrhs, const int* cexp,
                        cudaStream_t st);

@@ -267,9 +267,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int j = 0; j < 8; ++j) {
         const longlong2 w = __ldg(&twq[ps * (uint32_t)(8 * qd + j)]);
         const long long wi = INV ? -w.y : w.y;
-        const long long ar = xr[j] << 8, ai = xi[j] << 8;  // |X| <= 2^54: no overflow
-        const long long re = __mul64hi(ar, w.x) - __mul64hi(ai, wi);  // (X w) 2^6, within 2 units
-        const long long im = __mul64hi(ar, wi) + __mul64hi(ai, w.x);
+        // three products (Gauss): re = a c - b d, im = (a + b)(c + d) - a c - b d, with a, b the
+        // parts of X shifted left by 7 (at most 2^61 each, their sum at most 2^62) and c, d the
+        // twiddle's (|c + d| <= 2^62.5): no product or sum overflows
+        const long long ar = xr[j] << 7, ai = xi[j] << 7;
+        const long long ac = __mul64hi(ar, w.x), bd = __mul64hi(ai, wi);
+        const long long re = (ac - bd) << 1;  // (X w) 2^6, within 4 units
+        const long long im = (__mul64hi(ar + ai, w.x + wi) - ac - bd) << 1;
         xr[j] = (re + 32) >> 6;
         xi[j] = (im + 32) >> 6;
       }
@@ -370,9 +374,14 @@ __global__ void __launch_bounds__(kThreads, 1)
       long long Ys[8];
 #pragma unroll
       for (int n = 0; n < 8; ++n) {
+        // diagonals 0-3 hold at most 1, 2, 3, 4 x 2^20 in size: adding 1.5 2^23 puts the integer in
+        // the low mantissa bits exactly (|x| <= 2^22); the larger ones convert on the F2I path
         long long Y = 0;
 #pragma unroll
-        for (int s = 0; s < 6; ++s) Y += (long long)__float2int_rn(__uint_as_float(d[s][n])) << (43 - 8 * s);
+        for (int s = 0; s < 4; ++s)
+          Y += (long long)(__float_as_int(__uint_as_float(d[s][n]) + 12582912.0f) - 0x4B400000) << (43 - 8 * s);
+#pragma unroll
+        for (int s = 4; s < 6; ++s) Y += (long long)__float2int_rn(__uint_as_float(d[s][n])) << (43 - 8 * s);
         // D_6 2^-5 + D_7 2^-13, exact as an integer over 2^13 and rounded to the nearest unit
         const long long t = ((long long)__float2int_rn(__uint_as_float(d[6][n])) << 8) +
                             (long long)__float2int_rn(__uint_as_float(d[7][n]));
