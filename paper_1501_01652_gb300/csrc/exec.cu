@@ -339,7 +339,7 @@ std::vector<FftShape> shape_candidates(int logF, int ncols, int prec, bool tc) {
     if (tc && prec == kTermFP64 && !sh.one_launch && logF >= 12) {
       int m = 0;
       for (int i = 0; i < sh.npass; ++i)
-        if (sh.logr[i] == 5) m |= 1 << i;
+        if (sh.logr[i] == 5 || sh.logr[i] == 6) m |= 1 << i;
       if (m) {
         sh.tc = m;
         add1(sh);
@@ -396,28 +396,45 @@ double time_shape(C* A, C* B, int logF, int ncols, const C* tw, int logFmax, con
 // The shape of transforms of 2^logF points in precision prec over ncols columns per launch:
 // from the plan's list, the process cache (keyed by GPU model) or a measurement of the
 // candidates on the lane's workspace buffers A, B (bytes each), recorded in the plan's list.
-// The split with the most radix-32 tensor-core passes a length allows (the rest of its bits in 1-3
-// FP64 passes of radix 2^5..2^8 after them), or none.
+// The split of a length with the most of its bits in tensor-core passes (radix 32 or 64), fewest
+// passes on ties; the other passes (radix 2^7, 2^8) on the FP64 pipe, after them.
 bool tensor_shape(int logF, FftShape* out) {
   if (logF < 12) return false;
-  for (int n5 = std::min(4, logF / 5); n5 >= 1; --n5) {
-    const int rem = logF - 5 * n5, slots = 4 - n5;
-    int k = 0;
-    if (rem == 0) k = 0;
-    else if (slots >= 1 && rem >= 5 && rem <= 8) k = 1;
-    else if (slots >= 2 && rem >= 10 && rem <= 16) k = 2;
-    else if (slots >= 3 && rem >= 15 && rem <= 24) k = 3;
-    else continue;
-    FftShape sh{};
-    sh.npass = n5 + k;
-    for (int i = 0; i < n5; ++i) sh.logr[i] = 5;
-    for (int i = 0; i < k; ++i) sh.logr[n5 + i] = rem / k + (i < rem % k ? 1 : 0);
-    sh.tc = (1 << n5) - 1;
-    if (!valid_fft_shape(sh, logF)) continue;
-    *out = sh;
-    return true;
+  bool found = false;
+  int best_bits = -1, best_np = 9;
+  for (int np = 2; np <= 4; ++np) {
+    int r[4] = {5, 5, 5, 5};
+    for (;;) {
+      int sum = 0, tcb = 0;
+      for (int i = 0; i < np; ++i) {
+        sum += r[i];
+        if (r[i] <= 6) tcb += r[i];
+      }
+      if (sum == logF && (tcb > best_bits || (tcb == best_bits && np < best_np))) {
+        FftShape sh{};
+        sh.npass = np;
+        // tensor-core passes first
+        int k = 0;
+        for (int i = 0; i < np; ++i)
+          if (r[i] <= 6) sh.logr[k++] = r[i];
+        const int ntc = k;
+        for (int i = 0; i < np; ++i)
+          if (r[i] > 6) sh.logr[k++] = r[i];
+        sh.tc = (1 << ntc) - 1;
+        if (ntc > 0 && valid_fft_shape(sh, logF)) {
+          *out = sh;
+          best_bits = tcb;
+          best_np = np;
+          found = true;
+        }
+      }
+      int i = 0;  // next tuple in [5, 8]^np
+      while (i < np && r[i] == 8) r[i++] = 5;
+      if (i == np) break;
+      ++r[i];
+    }
   }
-  return false;
+  return found;
 }
 
 int plan_shape(DevicePlan* d, const std::string& gpu, bool tune, int prec, int logF, int64_t ncols, void* A, void* B,

@@ -656,8 +656,8 @@ bool valid_fft_shape(const FftShape& sh, int logF) {
   int sum = 0;
   for (int i = 0; i < sh.npass; ++i) {
     if (sh.logr[i] < 5 || sh.logr[i] > 8) return false;
-    // a tensor-core pass has radix 32 and tiles of 128 sequences within a column
-    if (((sh.tc >> i) & 1) && (sh.logr[i] != 5 || logF < 12)) return false;
+    // a tensor-core pass has radix 32 or 64 and tiles of 4096 points within a column
+    if (((sh.tc >> i) & 1) && ((sh.logr[i] != 5 && sh.logr[i] != 6) || logF < 12)) return false;
     sum += sh.logr[i];
   }
   return sum == logF;
@@ -696,7 +696,7 @@ int run_fft(C* a, C* b, int logF, int ncols, bool inverse, const C* tw, int logF
     const C* h = i == 0 ? hmul : nullptr;
     if ((sh.tc >> i) & 1) {
       if constexpr (std::is_same<C, double2>::value)
-        launch_pass_tc(inverse, src, dst, logF, logS, ncols, tc->twq + ((size_t)1 << logF), h, nseg,
+        launch_pass_tc(inverse, lr, src, dst, logF, logS, ncols, tc->twq + ((size_t)1 << logF), h, nseg,
                        (!inverse && i == 0) ? g0 : none, inverse ? tc->inv : tc->fwd, tc->err, st);
     } else if (inverse) {
       launch_pass_r<true, C>(lr, src, dst, logF, logS, ncols, tw, logFmax, h, nseg, none, st);

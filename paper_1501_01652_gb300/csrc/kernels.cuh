@@ -143,7 +143,7 @@ struct FftShape {
   int one_launch;  // 1: the whole transform in one launch (2^6 .. 2^12 points)
   int npass;       // otherwise passes of radix 2^logr[i], first to last
   int logr[4];
-  int tc;          // bit i: pass i (radix 32, FP64 transforms of 2^12 or more points) runs on the tensor cores
+  int tc;          // bit i: pass i (radix 32 or 64, FP64 transforms of 2^12 or more points) runs on the tensor cores
 };
 
 // Tables of the tensor-core passes (tcfft.cu): the digit planes of the 32-point DFT matrix,
@@ -166,12 +166,12 @@ struct FftGen {
 // into out (tc_dft_digits_bytes() bytes), host side.
 void tc_dft_digits(int inverse, void* out);
 size_t tc_dft_digits_bytes();
-// One radix-32 Stockham pass of 2^logF-point FP64 transforms (logF >= 12) over ncols columns on
-// the tensor cores: the mapping of k_fft_pass_reg<5>, with hmul or gen on its loads as there
+// One Stockham pass of radix 2^logR (5 or 6) of 2^logF-point FP64 transforms (logF >= 12) over ncols
+// columns on the tensor cores: the mapping of k_fft_pass_reg<logR>, with hmul or gen on its loads as there
 // (first passes only); twq is the Q62 twiddle table of this length (W_F^t at twq[t]).
-void launch_pass_tc(bool inverse, const double2* src, double2* dst, int logF, int logS, int ncols, const longlong2* twq,
-                    const double2* hmul, int64_t nseg, const FftGen& gen, const void* bdig, unsigned* err,
-                    cudaStream_t st);
+void launch_pass_tc(bool inverse, int logR, const double2* src, double2* dst, int logF, int logS, int ncols,
+                    const longlong2* twq, const double2* hmul, int64_t nseg, const FftGen& gen, const void* bdig,
+                    unsigned* err, cudaStream_t st);
 // twq[t] = round(tw[t] 2^62) (both parts), t < n.
 void launch_twiddles_q62(const double2* tw, longlong2* twq, int64_t n, cudaStream_t st);
 

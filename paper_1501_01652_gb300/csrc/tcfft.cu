@@ -144,16 +144,16 @@ __device__ __forceinline__ GenSrc gen_source(const FftGen& g, int64_t col) {
   return r;
 }
 
-// Loads of one tile's inputs for thread (sequence g, quarter qd: elements e = 8 qd .. 8 qd + 7)
-// into v, with the first pass's column generation or spectrum product.
+// Loads of one tile's inputs for a thread (its sequence's elements e = e0 + j es, j < 8) into v,
+// with the first pass's column generation or spectrum product.
 __device__ __forceinline__ void load_inputs(double2 (&v)[8], const double2* __restrict__ src,
                                             const double2* __restrict__ hmul, int64_t nseg, const FftGen& gen,
-                                            int logF, int logS, int64_t col, uint32_t ibase, int qd) {
+                                            int logF, int logS, int64_t col, uint32_t ibase, int e0, int es) {
   if (gen.coef) {
     const GenSrc gs = gen_source(gen, col);
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      const int64_t t = (int64_t)ibase + ((int64_t)(8 * qd + j) << logS);
+      const int64_t t = (int64_t)ibase + ((int64_t)(e0 + j * es) << logS);
       if (t < gs.lim) {
         const double c = __ldg(gs.c + t);
         const double2 w = __ldg(gs.v + t);
@@ -168,17 +168,21 @@ __device__ __forceinline__ void load_inputs(double2 (&v)[8], const double2* __re
     const double2* hc = hmul + (seg << logF);
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      const uint32_t t = ibase + ((uint32_t)(8 * qd + j) << logS);
+      const uint32_t t = ibase + ((uint32_t)(e0 + j * es) << logS);
       v[j] = cmul(x[t], __ldg(&hc[t]));
     }
   } else {
     const double2* x = src + (col << logF);
 #pragma unroll
-    for (int j = 0; j < 8; ++j) v[j] = x[ibase + ((uint32_t)(8 * qd + j) << logS)];
+    for (int j = 0; j < 8; ++j) v[j] = x[ibase + ((uint32_t)(e0 + j * es) << logS)];
   }
 }
 
-template <bool INV>
+// R64: a radix-64 pass. Each 64-point DFT is two 32-point DFTs, of the even and of the odd
+// elements (rows j and 64 + j of the tile, both scaled by the sequence's 2^E), on the tensor cores,
+// and one radix-2 step in 64-bit integers: y_r = Z0_r + W_64^r Z1_r, y_{r+32} = Z0_r - W_64^r Z1_r,
+// r < 32 (the odd rows' Z1 times the Q62 twiddle, exchanged through shared memory).
+template <bool INV, bool R64>
 __global__ void __launch_bounds__(kThreads, 1)
     k_fft_pass_tc(const double2* __restrict__ src, double2* __restrict__ dst, int logF, int logS, int64_t ntiles,
                   const longlong2* __restrict__ twq, const double2* __restrict__ hmul, int64_t nseg, FftGen gen,
@@ -220,14 +224,19 @@ __global__ void __launch_bounds__(kThreads, 1)
                  : "memory");
   }
 
-  const int lgs = logF - 5;                 // log2 of the sequences per column
-  const int tpc_log = lgs - 7;              // log2 of the tiles per column
+  constexpr int LR = R64 ? 6 : 5;            // log2 of the radix
+  constexpr int LT = R64 ? 6 : 7;            // log2 of the sequences per tile
+  const int lgs = logF - LR;                 // log2 of the sequences per column
+  const int tpc_log = lgs - LT;              // log2 of the tiles per column
   const uint32_t smask = (1u << logS) - 1u;
+  const int jrow = R64 ? (i & 63) : i;       // the tile's sequence of this row
+  const int par = R64 ? (i >> 6) : 0;        // R64: even (0) or odd (1) elements
+  const int e0 = R64 ? 16 * qd + par : 8 * qd, es = R64 ? 2 : 1;  // this thread's elements e0 + j es
   auto seq_of = [&](int64_t tile, int64_t& col, uint32_t& g, uint32_t& p, uint32_t& ibase) {
     col = tile >> tpc_log;
-    g = (uint32_t)((tile & ((int64_t(1) << tpc_log) - 1)) << 7) + (uint32_t)i;
+    g = (uint32_t)((tile & ((int64_t(1) << tpc_log) - 1)) << LT) + (uint32_t)jrow;
     p = g >> logS;
-    ibase = (g & smask) + ((p << 5) << logS);  // element e at ibase + (e << logS)
+    ibase = (g & smask) + ((p << LR) << logS);  // element e at ibase + (e << logS)
   };
   double2 v[8];
   int64_t tile = blockIdx.x;
@@ -235,7 +244,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     int64_t col;
     uint32_t g, p, ib;
     seq_of(tile, col, g, p, ib);
-    load_inputs(v, src, hmul, nseg, gen, logF, logS, col, ib, qd);
+    load_inputs(v, src, hmul, nseg, gen, logF, logS, col, ib, e0, es);
   }
   // every thread waits; the CTA agrees on the outcome, so all of it leaves the loop together
   if (__syncthreads_or(!bar_wait(bar_b, 0, t0) ? 1 : 0)) s_fail = 1;
@@ -252,7 +261,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int j = 0; j < 8; ++j) m = max(m, max(exp_field(v[j].x), exp_field(v[j].y)));
     emx[qd * kRows + i] = m;
     __syncthreads();
-    const int E = max(max(emx[i], emx[kRows + i]), max(emx[2 * kRows + i], emx[3 * kRows + i])) - 1022;
+    int mx = max(max(emx[i], emx[kRows + i]), max(emx[2 * kRows + i], emx[3 * kRows + i]));
+    if (R64) {  // both rows of the sequence
+      const int o = i ^ 64;
+      mx = max(mx, max(max(emx[o], emx[kRows + o]), max(emx[2 * kRows + o], emx[3 * kRows + o])));
+    }
+    const int E = mx - 1022;
     // 2. X = v 2^(54 - E) in integers, times the pass twiddles W_F^{p s e} (Q62) with the product
     //    rounded back to units of X
     long long xr[8], xi[8];
@@ -265,7 +279,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t ps = p << logS;
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
-        const longlong2 w = __ldg(&twq[ps * (uint32_t)(8 * qd + j)]);
+        const longlong2 w = __ldg(&twq[ps * (uint32_t)(e0 + j * es)]);
         const long long wi = INV ? -w.y : w.y;
         // three products (Gauss): re = a c - b d, im = (a + b)(c + d) - a c - b d, with a, b the
         // parts of X shifted left by 7 (at most 2^61 each, their sum at most 2^62) and c, d the
@@ -348,7 +362,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       int64_t ncol;
       uint32_t ng, np, nib;
       seq_of(next, ncol, ng, np, nib);
-      load_inputs(v, src, hmul, nseg, gen, logF, logS, ncol, nib, qd);
+      load_inputs(v, src, hmul, nseg, gen, logF, logS, ncol, nib, e0, es);
     }
     if (__syncthreads_or(!bar_wait(bar_m, phase, t0) ? 1 : 0)) {
       s_fail = 1;
@@ -364,13 +378,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     const bool wide_range = __any_sync(0xffffffffu, E - 55 < -900 || E - 55 > 900);
     const double scale2 = wide_range ? ldexp(1.0, E - 55) : 1.0;
     double2* y = dst + (col << logF) + g;
+    // R64: the exchange of Z0 and W_64^r Z1 (int64 pairs) at [r][row] of the digit area, which
+    // the finished products no longer read
+    longlong2* xch = reinterpret_cast<longlong2*>(sm + kSmA);
 #pragma unroll 1
     for (int c8 = 0; c8 < 2; ++c8) {
       uint32_t d[kDiag][8];
 #pragma unroll
       for (int s = 0; s < kDiag; ++s) tmem_ld8(lane_addr + (uint32_t)(s * kKr + 16 * qd + 8 * c8), d[s]);
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      double o[8];
       long long Ys[8];
 #pragma unroll
       for (int n = 0; n < 8; ++n) {
@@ -388,6 +404,27 @@ __global__ void __launch_bounds__(kThreads, 1)
         Y += (t + 4096) >> 13;
         Ys[n] = Y;
       }
+      if (R64) {
+        // |Z| <= 2^60.5 in units of Y (a sum of 32 inputs of modulus at most sqrt(2) 2^E): the odd
+        // rows rotate by W_64^r in three products of (Z shifted by 1) with the Q62 twiddle
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int r = 8 * qd + 4 * c8 + u;
+          long long zr = Ys[2 * u], zi = Ys[2 * u + 1];
+          if (par) {
+            const longlong2 w = __ldg(&twq[(uint32_t)r << (logF - 6)]);  // W_64^r = W_F^{r F / 64}
+            const long long wi = INV ? -w.y : w.y;
+            const long long ar = zr << 1, ai = zi << 1;
+            const long long ac = __mul64hi(ar, w.x), bd = __mul64hi(ai, wi);
+            const long long im = __mul64hi(ar + ai, w.x + wi) - ac - bd;
+            zr = (ac - bd) << 1;
+            zi = im << 1;
+          }
+          xch[r * kRows + i] = make_longlong2(zr, zi);
+        }
+        continue;
+      }
+      double o[8];
       if (!wide_range) {
 #pragma unroll
         for (int n = 0; n < 8; ++n) {
@@ -402,6 +439,27 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int u = 0; u < 4; ++u) {
         const int r = 8 * qd + 4 * c8 + u;  // output r: reals 2r, 2r + 1
         y[(int64_t)r << lgs] = make_double2(o[2 * u], o[2 * u + 1]);
+      }
+    }
+    if (R64) {
+      // the radix-2 step: thread (row i, quarter qd) takes outputs r and r + 32 of its sequence for
+      // r = 8 qd + 4 (i >> 6) .. + 3
+      __syncthreads();
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int r = 8 * qd + 4 * par + u;
+        const longlong2 z0 = xch[r * kRows + jrow], z1 = xch[r * kRows + 64 + jrow];
+        const long long Ya[4] = {z0.x + z1.x, z0.y + z1.y, z0.x - z1.x, z0.y - z1.y};
+        double o[4];
+#pragma unroll
+        for (int n = 0; n < 4; ++n) {
+          const double yd = __ll2double_rn(Ya[n]);
+          o[n] = wide_range ? yd * scale2
+                            : (Ya[n] ? __longlong_as_double(__double_as_longlong(yd) + ((long long)(E - 55) << 52))
+                                     : 0.0);
+        }
+        y[(int64_t)r << lgs] = make_double2(o[0], o[1]);
+        y[(int64_t)(r + 32) << lgs] = make_double2(o[2], o[3]);
       }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -465,26 +523,41 @@ void launch_twiddles_q62(const double2* tw, longlong2* twq, int64_t n, cudaStrea
   k_twiddles_q62<<<(unsigned)std::min<int64_t>((n + 255) / 256, 152 * 16), 256, 0, st>>>(tw, twq, n);
 }
 
-void launch_pass_tc(bool inverse, const double2* src, double2* dst, int logF, int logS, int ncols, const longlong2* twq,
-                    const double2* hmul, int64_t nseg, const FftGen& gen, const void* bdig, unsigned* err,
-                    cudaStream_t st) {
-  const int64_t ntiles = ((int64_t)ncols << logF) >> 12;  // 128 sequences of 32 points
-  static bool configured[2] = {false, false};
-  if (!configured[inverse]) {
-    if (inverse) cudaFuncSetAttribute(k_fft_pass_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmTotal);
-    else cudaFuncSetAttribute(k_fft_pass_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmTotal);
-    configured[inverse] = true;
+void launch_pass_tc(bool inverse, int logR, const double2* src, double2* dst, int logF, int logS, int ncols,
+                    const longlong2* twq, const double2* hmul, int64_t nseg, const FftGen& gen, const void* bdig,
+                    unsigned* err, cudaStream_t st) {
+  const int64_t ntiles = ((int64_t)ncols << logF) >> (logR == 6 ? 12 : 12);  // 4096 points per tile
+  static bool configured[4] = {false, false, false, false};
+  const int k = (inverse ? 1 : 0) + (logR == 6 ? 2 : 0);
+  if (!configured[k]) {
+    if (k == 0) cudaFuncSetAttribute(k_fft_pass_tc<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmTotal);
+    if (k == 1) cudaFuncSetAttribute(k_fft_pass_tc<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmTotal);
+    if (k == 2) cudaFuncSetAttribute(k_fft_pass_tc<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmTotal);
+    if (k == 3) cudaFuncSetAttribute(k_fft_pass_tc<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmTotal);
+    configured[k] = true;
   }
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const unsigned grid = (unsigned)std::min<int64_t>(ntiles, sms);
-  if (inverse)
-    k_fft_pass_tc<true><<<grid, kThreads, kSmTotal, st>>>(src, dst, logF, logS, ntiles, twq, hmul, nseg, gen, bdig,
-                                                         err);
-  else
-    k_fft_pass_tc<false><<<grid, kThreads, kSmTotal, st>>>(src, dst, logF, logS, ntiles, twq, hmul, nseg, gen, bdig,
-                                                          err);
+  switch (k) {
+    case 0:
+      k_fft_pass_tc<false, false><<<grid, kThreads, kSmTotal, st>>>(src, dst, logF, logS, ntiles, twq, hmul, nseg, gen,
+                                                                    bdig, err);
+      break;
+    case 1:
+      k_fft_pass_tc<true, false><<<grid, kThreads, kSmTotal, st>>>(src, dst, logF, logS, ntiles, twq, hmul, nseg, gen,
+                                                                   bdig, err);
+      break;
+    case 2:
+      k_fft_pass_tc<false, true><<<grid, kThreads, kSmTotal, st>>>(src, dst, logF, logS, ntiles, twq, hmul, nseg, gen,
+                                                                   bdig, err);
+      break;
+    default:
+      k_fft_pass_tc<true, true><<<grid, kThreads, kSmTotal, st>>>(src, dst, logF, logS, ntiles, twq, hmul, nseg, gen,
+                                                                  bdig, err);
+      break;
+  }
 }
 
 }  // namespace hk

@@ -475,11 +475,13 @@ def test_autotuned_shapes_are_recorded_and_exact():
 
 
 # ---------------------------------------------------------------------------------------------
-# Radix-32 FFT passes on the tensor cores (split-digit products in FP64 accuracy)
+# Radix-32 and radix-64 FFT passes on the tensor cores (split-digit products in FP64 accuracy)
 # ---------------------------------------------------------------------------------------------
 @pytest.mark.parametrize("logF,ncols,radices,tc", [
-    (12, 4, [5, 7], 0b01), (12, 4, [7, 5], 0b10), (15, 8, [5, 5, 5], 0b111), (17, 4, [5, 6, 6], 0b001),
-    (20, 8, [5, 5, 5, 5], 0b1111), (21, 16, [5, 5, 5, 6], 0b0111), (22, 2, [5, 5, 5, 7], 0b0111),
+    (12, 4, [5, 7], 0b01), (12, 4, [7, 5], 0b10), (12, 4, [6, 6], 0b11), (13, 4, [6, 7], 0b01),
+    (15, 8, [5, 5, 5], 0b111), (17, 4, [5, 6, 6], 0b111), (18, 8, [6, 6, 6], 0b101),
+    (20, 8, [5, 5, 5, 5], 0b1111), (21, 16, [5, 5, 5, 6], 0b1111), (21, 4, [6, 5, 5, 5], 0b1110),
+    (22, 2, [5, 5, 5, 7], 0b0111), (22, 2, [5, 5, 6, 6], 0b1111),
 ])
 @pytest.mark.parametrize("inverse", [False, True])
 def test_tensor_core_fft_passes(logF, ncols, radices, tc, inverse):
