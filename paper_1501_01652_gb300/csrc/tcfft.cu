@@ -17,7 +17,7 @@
 //    2^-53 of 2^E per output, the rounding of an FP64 product;
 //  * the diagonals are combined in 64-bit integers, Y = sum_s D_s 2^(43 - 8s) = y 2^(55-E)
 //    (|y| < 2^(E+6), so |Y| < 2^61), the two smallest diagonals rounded to the nearest unit,
-//    and converted to double once.
+//    and converted to double once (int64 to double, the scale added to the exponent field).
 // The pass twiddles W_F^{p s e} multiply the integers X (Q62 twiddles, 64-bit high products,
 // rounded back to units of X; a rotation keeps |X| below 2^54.5, inside the digits' range), so the
 // FP64 pipe (the scarce one on this part) sees only the two int64-to-double conversions of each
@@ -392,17 +392,21 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int n = 0; n < 8; ++n) {
         // diagonals 0-3 hold at most 1, 2, 3, 4 x 2^20 in size: adding 1.5 2^23 puts the integer in
         // the low mantissa bits exactly (|x| <= 2^22); the larger ones convert on the F2I path
-        long long Y = 0;
+        int D[kDiag];
 #pragma unroll
-        for (int s = 0; s < 4; ++s)
-          Y += (long long)(__float_as_int(__uint_as_float(d[s][n]) + 12582912.0f) - 0x4B400000) << (43 - 8 * s);
+        for (int s = 0; s < 4; ++s) D[s] = __float_as_int(__uint_as_float(d[s][n]) + 12582912.0f) - 0x4B400000;
 #pragma unroll
-        for (int s = 4; s < 6; ++s) Y += (long long)__float2int_rn(__uint_as_float(d[s][n])) << (43 - 8 * s);
-        // D_6 2^-5 + D_7 2^-13, exact as an integer over 2^13 and rounded to the nearest unit
-        const long long t = ((long long)__float2int_rn(__uint_as_float(d[6][n])) << 8) +
-                            (long long)__float2int_rn(__uint_as_float(d[7][n]));
-        Y += (t + 4096) >> 13;
-        Ys[n] = Y;
+        for (int s = 4; s < kDiag; ++s) D[s] = __float2int_rn(__uint_as_float(d[s][n]));
+        // D_6 2^-5 + D_7 2^-13, exact as an integer over 2^13 and rounded to the nearest unit; then
+        // D_5..D_2 times 2^3, 2^11, 2^19, 2^27 as 32-bit multiply-adds into the 64-bit sum, and
+        // D_1 2^35, D_0 2^43 added to its high word: all modulo 2^64, exact since |Y| < 2^61
+        long long Y = ((long long)D[6] * 256 + D[7] + 4096) >> 13;
+        Y += (long long)D[5] * 8;
+        Y += (long long)D[4] * 2048;
+        Y += (long long)D[3] * 524288;
+        Y += (long long)D[2] * 134217728;
+        const unsigned hi = (unsigned)((unsigned long long)Y >> 32) + ((unsigned)D[1] << 3) + ((unsigned)D[0] << 11);
+        Ys[n] = (long long)(((unsigned long long)hi << 32) | ((unsigned long long)Y & 0xFFFFFFFFULL));
       }
       if (R64) {
         // |Z| <= 2^60.5 in units of Y (a sum of 32 inputs of modulus at most sqrt(2) 2^E): the odd
