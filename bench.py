@@ -35,11 +35,13 @@ from hankel_inputs import coefficients, sample_rows, seed_for  # noqa: E402
 FP64_PEAK_GFLOPS = 152 * 4 * 2.07  # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz = 1258 GFLOP/s
 HBM_FALLBACK_GBS = 6800.0          # used only when MEASURED_PEAKS.json is absent
 FP64_MEASURED_GFLOPS = 1004.0      # DFMA microbenchmark on this part (2 x 502 G instructions/s)
-# DRAM bytes per algorithmic byte of an FP64 FFT pass launch, from an ncu capture of two
-# radix-128 inverse passes of 2^24 points (k_fft_pass_reg<7, 1, double2>, 8192 CTAs; the first
-# with the chirp-spectrum product folded into its loads): 310.7 + 226.0 MB and 270.2 + 217.5 MB
-# of DRAM reads + writes against 536.9 MB algorithmic each.
-FFT_TRAFFIC_RATIO = (310.663 + 225.980 + 270.203 + 217.533) / (2 * 536.871)
+# DRAM bytes per algorithmic byte of an FFT pass launch of FP64 transforms, from an ncu capture of
+# one radix-32 pass on the tensor cores over 8 x 2^20 points (k_fft_pass_tc<0, 0>): 136.8 + 85.1 MB
+# of DRAM reads + writes against 268.4 MB algorithmic (part of the writes still in L2 at the end).
+FFT_TRAFFIC_RATIO = (136.813 + 85.120) / 268.435
+# Executed fp16 MMA flops per complex point of a tensor-core radix-32 pass: 34 digit pairs, 4 K
+# steps of 128 x 64 x 16 per tile of 4096 points (plus one 128 x 64 x 16 clear).
+TC_MMA_FLOPS_PER_POINT = (2 * 128 * 16 * 64 * (34 * 4 + 1)) / 4096.0
 # The double-float transforms are bound by the FP32 pipe: 152 SMs x 128 lanes x 2.07 GHz =
 # 40.3 T instructions/s. Their radix-2 butterfly (two double-float dot products of 16 FP32
 # instructions each, four sums of 8) takes 64 FP32 instructions for the 10 flops of the
@@ -406,6 +408,7 @@ def run_ours(args):
     want_err = world == 1 and not args.no_cpu_baseline and not args.quick
     ce = torch.from_numpy(err_c).to(dev)
     f_err = [p.exec(ce).cpu().numpy()[0] for p in plans] if want_err else []
+    tc_pass = tensor_pass_roofline(hk, plans, args.steps)
     for p in plans:
         p.destroy()
 
@@ -471,6 +474,7 @@ def run_ours(args):
         "stage_steps_ms": sum(ev_step_ms) / len(ev_step_ms),
         "term_precision": term_split,
         "roofline": roofline,
+        "tensor_core_pass": tc_pass,
         "fft_autotune": autotune,
         "e2e": {"value": served_e2e, "unit": "coeffs/s", "h2d_bytes_per_step": coeffs_per_step * 8,
                 "d2h_bytes_per_step": coeffs_per_step * 8,
@@ -504,6 +508,54 @@ def run_ours(args):
     print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def tensor_pass_roofline(hk, plans, steps):
+    """The longest transform the plans run with tensor-core passes, timed alone (CUDA events, outside
+    the timed region) in its tuned split and in the built-in FP64 one; the executed fp16 MMA rate of
+    its radix-32 passes against the measured bf16 peak (the fp16 rate)."""
+    best = None
+    for p in plans:
+        for sh in p.fft_shapes():
+            if any(sh["tensor_passes"]) and (best is None or (sh["log2_len"], sh["col_bucket"]) >
+                                              (best["log2_len"], best["col_bucket"])):
+                best = sh
+    if best is None:
+        return None
+    logF, rad = best["log2_len"], best["radices"]
+    mask = sum(1 << i for i, t in enumerate(best["tensor_passes"]) if t)
+    ncols = max(1, min(1 << best["col_bucket"], (1 << 25) >> logF))
+    err, ms = hk.debug_fft_compare(logF, ncols, rad, mask)
+    # the same length on the FP64 pipe in the library's built-in split (the fewest passes of radix
+    # up to 2^8, as equal as possible)
+    npass = (logF + 7) // 8
+    while npass > 1 and logF // npass < 5:
+        npass -= 1
+    builtin = [logF // npass + (1 if i < logF % npass else 0) for i in range(npass)]
+    try:
+        _, ms64 = hk.debug_fft_compare(logF, ncols, builtin, 0)
+    except RuntimeError:
+        ms64 = None
+    points = ncols * (1 << logF)
+    ntc = sum(1 for t in best["tensor_passes"] if t)
+    peak = bf16_peak()
+    mma = TC_MMA_FLOPS_PER_POINT * points * ntc / (ms / 1000.0) / 1e12
+    return {"log2_len": logF, "ncols": ncols, "radices": rad, "tensor_passes": best["tensor_passes"],
+            "ms": ms, "ms_fp64_pipe": ms64, "fp64_pipe_radices": builtin,
+            "speedup_over_fp64_pipe": (ms64 / ms) if ms64 else None,
+            "max_rel_diff_vs_fp64_pipe": err,
+            "fp64_equiv_gflops": 5.0 * points * logF / (ms / 1000.0) / 1e9,
+            "mma_tflops": mma, "bound": "tensor", "peak": peak, "unit": "TFLOP/s", "frac": mma / peak,
+            "note": "executed fp16 digit-product MMA flops (radix-32 count per pass) over the whole transform's "
+                    "time; the passes are issue-bound on the integer pipe (profiles/k_fft_pass_tc_*)"}
+
+
+def bf16_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["bf16_tflops"])
+    except (OSError, KeyError, ValueError):
+        return 1900.0
 
 
 def term_counts(plans):
@@ -540,10 +592,13 @@ def fft_roofline(stats, steps):
             e = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
                  "frac": ach / FP64_PEAK_GFLOPS,
                  "traffic": FFT_TRAFFIC_RATIO * by / nl if nl else None,
-                 "traffic_unit": "DRAM bytes per launch (ncu ratio x algorithmic bytes)",
+                 "traffic_unit": "DRAM bytes per launch (ncu ratio of the tensor-core pass x algorithmic bytes)",
                  "frac_of_measured_fp64": ach / FP64_MEASURED_GFLOPS,
-                 "kernel": "k_fft_pass_reg / k_fft_small<double2> (FP64 transforms, forward + inverse)",
-                 "peak_source": "nominal FP64 from unit counts and clock (152 SM x 4 flop/clk x 2.07 GHz)"}
+                 "kernel": "FP64-accuracy transforms: k_fft_pass_tc (radix-32/64 passes on the tensor cores) and "
+                           "k_fft_pass_reg / k_fft_small<double2> (FP64 pipe), forward + inverse",
+                 "peak_source": "nominal FP64 from unit counts and clock (152 SM x 4 flop/clk x 2.07 GHz): the "
+                                "pipe these transforms would run on without the tensor cores; a frac_of_measured_fp64 "
+                                "above 1 is the tensor-core passes beating that roofline"}
         elif k2 == "fft_df64":
             e = {"bound": "alu", "achieved": ach, "peak": DF64_PEAK_GFLOPS, "unit": "GFLOP/s",
                  "frac": ach / DF64_PEAK_GFLOPS, "traffic": None,
