@@ -72,10 +72,10 @@ def parse_args():
     ap.add_argument("--mode", default="dht", choices=["dht", "mix"], help="mix: the serving-mix workload")
     ap.add_argument("--quick", action="store_true", help="batched form only (no plain form, serving runs or CPU leg)")
     ap.add_argument("--no-mixed", action="store_true", help="skip the opt-in mixed-precision batched form")
-    ap.add_argument("--mix-requests", type=int, default=150)
-    ap.add_argument("--mix-rate", type=float, default=100.0, help="Poisson arrivals per second")
+    ap.add_argument("--mix-requests", type=int, default=1000, help="requests per arrival rate")
+    ap.add_argument("--mix-rates", default="100,1000,10000", help="Poisson arrivals per second, one run each")
     ap.add_argument("--mix-nmin", type=int, default=10)
-    ap.add_argument("--mix-nmax", type=int, default=16)
+    ap.add_argument("--mix-nmax", type=int, default=20)
     ap.add_argument("--mix-vmax", type=int, default=64)
     ap.add_argument("--clocks-csv", default=None,
                     help="keep the nvidia-smi samples of the timed region in this file (default: a temporary file)")
@@ -629,28 +629,46 @@ MIX_EPS = [1e-15, 1e-8, 1e-4]
 
 def mix_requests(args):
     """Seeded serving mix: task uniform over MIX_TASKS, N = 2^k with k uniform in
-    [mix_nmin, mix_nmax] (log-uniform N), eps uniform over MIX_EPS, 1..mix_vmax vectors."""
+    [mix_nmin, mix_nmax] (log-uniform N), eps uniform over MIX_EPS, 1..mix_vmax vectors. A request's
+    coefficients are the first vectors of a seeded uniform[-1, 1] pool of its N (one pool of mix_vmax
+    vectors per N keeps the host memory of a thousand requests bounded)."""
     rng = np.random.default_rng(seed_for(5, 0))
+    pools = {}
     reqs = []
     for i in range(args.mix_requests):
         task, nu = MIX_TASKS[rng.integers(len(MIX_TASKS))]
         N = 1 << int(rng.integers(args.mix_nmin, args.mix_nmax + 1))
         eps = MIX_EPS[rng.integers(len(MIX_EPS))]
         nv = int(rng.integers(1, args.mix_vmax + 1))
-        reqs.append((task, nu, N, eps, coefficients("uniform", N, nv, seed_for(5, 1 + i))))
+        if N not in pools:
+            pools[N] = coefficients("uniform", N, args.mix_vmax, seed_for(5, 1 + len(pools)))
+        reqs.append((task, nu, N, eps, pools[N][:nv]))
     return reqs
 
 
-def run_mix_stream(hk, server_kw, reqs, rate, seed):
-    srv = hk.Server(**server_kw)
+def warm_plans(srv, reqs):
+    """Build every plan key of the stream once (one one-vector request each), outside the timing."""
     seen = set()
-    for task, nu, N, eps, c in reqs:  # warm the plan cache: one small request per plan key
+    for task, nu, N, eps, c in reqs:
         if (task, nu, N, eps) not in seen:
             seen.add((task, nu, N, eps))
             t, _ = srv.submit(task, nu, N, eps, c[:1])
             srv.wait(t)
+    return len(seen)
+
+
+def run_mix_stream(srv, reqs, rate, seed):
+    """Submit reqs with Poisson arrivals at `rate` per second; every request's latency is its
+    submission-to-completion time. Returns throughput over the makespan and p50/p99 latency."""
     rng = np.random.default_rng(seed)
     gaps = rng.exponential(1.0 / rate, size=len(reqs))
+    # output arrays: one pool per N (requests in flight at once may share one; only the timing is read)
+    outs = {}
+    vmax = max(c.shape[0] for *_, c in reqs)
+    for *_, c in reqs:
+        if c.shape[1] not in outs:
+            outs[c.shape[1]] = np.empty((vmax, c.shape[1]))
+    before = srv.stats()
     t0 = time.perf_counter()
     due = t0
     tickets = []
@@ -658,39 +676,59 @@ def run_mix_stream(hk, server_kw, reqs, rate, seed):
         due += gap
         while time.perf_counter() < due:
             time.sleep(min(0.0005, max(0.0, due - time.perf_counter())))
-        tickets.append(srv.submit(task, nu, N, eps, c)[0])
+        tickets.append(srv.submit(task, nu, N, eps, c, outs[N][:c.shape[0]])[0])
     lat = [srv.wait(t) for t in tickets]
     makespan = time.perf_counter() - t0
     st = srv.stats()
-    srv.close()
     coeffs = sum(c.size for *_, c in reqs)
-    return {"coeffs_per_s": coeffs / makespan, "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99),
-            "makespan_s": makespan, "batches": st["batches"], "plans": st["plans_built"],
-            "graphs": st["graphs_captured"]}
+    return {"rate_per_s": rate, "requests": len(reqs), "coeffs_per_s": coeffs / makespan, "p50_ms": pct(lat, 50),
+            "p99_ms": pct(lat, 99), "max_ms": max(lat), "makespan_s": makespan,
+            "batches": st["batches"] - before["batches"], "contexts_added": st["contexts_added"],
+            "plans_built": st["plans_built"], "plans_evicted": st["plans_evicted"],
+            "graphs": st["graphs_captured"], "device_bytes": st["device_bytes"]}
 
 
 def run_mix(args):
-    """Serving mix through the request loop: served (batched, 4 streams, graphs, FP32 stages
-    where eps >= 1e-5) against plain (one request at a time, FP64), same arrival stream."""
+    """Serving mix through the request loop: served (packed batches on 4 streams, up to two batches
+    of one plan in flight, CUDA graphs, AUTO precision: FP64 below eps = 1e-5, FP32 stages above)
+    against plain (one request at a time, every stage FP64), the same arrival streams, at each rate
+    of --mix-rates."""
     import torch
 
     import paper_1501_01652_gb300 as hk
 
     torch.cuda.set_device(0)
     reqs = mix_requests(args)
-    served = run_mix_stream(hk, dict(streams=4, max_batch=64, use_graphs=True, precision="auto"), reqs,
-                            args.mix_rate, 3)
-    plain = run_mix_stream(hk, dict(streams=1, max_batch=64, use_graphs=False, precision="fp64", pack=False), reqs,
-                           args.mix_rate, 3)
-    line = {"metric": "serving mix coeffs/s and p50/p99 ms, served vs plain FP64", "value": served["coeffs_per_s"],
-            "unit": "coeffs/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
-            "config": {"workload": "serving_mix", "requests": len(reqs), "rate_per_s": args.mix_rate,
+    rates = [float(r) for r in args.mix_rates.split(",")]
+    forms = {"served": dict(streams=4, max_batch=64, use_graphs=True, precision="auto", contexts_per_plan=2),
+             "plain_fp64": dict(streams=1, max_batch=64, use_graphs=False, precision="fp64", pack=False,
+                                contexts_per_plan=1)}
+    out = {}
+    for name, kw in forms.items():
+        srv = hk.Server(memory_cap=120 << 30, **kw)
+        t0 = time.perf_counter()
+        keys = warm_plans(srv, reqs)
+        warm_s = time.perf_counter() - t0
+        out[name] = {"plan_keys": keys, "plan_warmup_s": warm_s,
+                     "per_rate": [run_mix_stream(srv, reqs, rate, 3 + i) for i, rate in enumerate(rates)]}
+        srv.close()
+    per_rate = []
+    for i, rate in enumerate(rates):
+        sv, pl = out["served"]["per_rate"][i], out["plain_fp64"]["per_rate"][i]
+        per_rate.append({"rate_per_s": rate, "served_coeffs_per_s": sv["coeffs_per_s"],
+                         "plain_coeffs_per_s": pl["coeffs_per_s"],
+                         "served_over_plain": sv["coeffs_per_s"] / pl["coeffs_per_s"],
+                         "served_p50_ms": sv["p50_ms"], "served_p99_ms": sv["p99_ms"],
+                         "plain_p50_ms": pl["p50_ms"], "plain_p99_ms": pl["p99_ms"],
+                         "p99_plain_over_served": pl["p99_ms"] / sv["p99_ms"]})
+    line = {"metric": "serving mix coeffs/s and p50/p99 ms, served vs plain FP64",
+            "value": per_rate[len(per_rate) // 2]["served_coeffs_per_s"], "unit": "coeffs/s", "n_gpus": 1,
+            "higher_is_better": True, "data": "synthetic",
+            "config": {"workload": "serving_mix", "requests_per_rate": len(reqs), "rates_per_s": rates,
                        "N": "2^%d..2^%d log-uniform" % (args.mix_nmin, args.mix_nmax),
                        "vectors_per_request": "1..%d" % args.mix_vmax, "eps": MIX_EPS,
-                       "tasks": ["%s-%d" % t for t in MIX_TASKS]},
-            "served": served, "plain_fp64": plain,
-            "served_over_plain": served["coeffs_per_s"] / plain["coeffs_per_s"],
-            "p99_ratio_plain_over_served": plain["p99_ms"] / served["p99_ms"]}
+                       "tasks": ["%s-%d" % t for t in MIX_TASKS], "memory_cap_gib": 120},
+            "per_rate": per_rate, "detail": out}
     print(json.dumps(line))
 
 
