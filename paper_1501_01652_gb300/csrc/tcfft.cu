@@ -22,11 +22,12 @@
 // rounded back to units of X; a rotation keeps |X| below 2^54.5, inside the digits' range), so the
 // FP64 pipe (the scarce one on this part) sees only the two int64-to-double conversions of each
 // output and the first pass's column generation or spectrum product (FP64 products on its loads,
-// as in the FP64 pass). One CTA per SM (persistent; 168 KB of shared
-// memory for the digits, all 512 TMEM columns for the 8 diagonal accumulators): per tile of 128
-// sequences it splits the inputs (512 threads: sequence i, quarter qd of its elements), one
-// thread issues the 45 MMAs, every thread sends out the loads of the CTA's next tile while
-// they run, and after their commit reads back 8 of its sequence's outputs. Waits on mbarriers are bounded: a wait that runs out sets the plan's error word and
+// as in the FP64 pass). One CTA per SM (persistent; 168 KB of shared memory for the digits, all
+// 512 TMEM columns for the 8 diagonal accumulators): per tile of 128 sequences 512 threads
+// (sequence i, quarter qd of its elements) write the digits, one thread issues the 45 MMAs, and
+// while they run every thread loads the CTA's next tile and brings it to fixed point; after the
+// MMAs' commit the threads write the next tile's digits and read back 8 of their sequence's
+// outputs. Waits on mbarriers are bounded: a wait that runs out sets the plan's error word and
 // the kernel stops, frees its TMEM and returns.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -48,16 +49,17 @@ constexpr int kRows = 128;              // sequences per tile (MMA M)
 constexpr int kKr = 2 * kR;             // reals per sequence (MMA K = N = 64)
 constexpr int kDig = 7;                 // digits per operand
 constexpr int kDiag = 8;                // diagonals kept (s = a + b <= 7)
-constexpr int kThreads = 512;   // sequence i = thread % 128, quarter thread / 128
+constexpr int kWorkers = 512;   // sequence i = thread % 128, quarter thread / 128
+constexpr int kThreads = kWorkers + 32;  // and one warp that issues the products
 constexpr uint32_t kAPlane = kRows * kKr * 2;  // 16 KB per digit plane of the sequences
 constexpr uint32_t kBPlane = kKr * kKr * 2;    // 8 KB per digit plane of the DFT matrix
 constexpr uint32_t kSmA = 0;
 constexpr uint32_t kSmB = kSmA + kDig * kAPlane;           // 112 KB
-constexpr uint32_t kSmZero = kSmB + kDig * kBPlane;        // 168 KB: a zero plane of the sequences' layout
-constexpr uint32_t kSmBar = kSmZero + kAPlane;             // 184 KB
+constexpr uint32_t kSmBar = kSmB + kDig * kBPlane;         // 168 KB
 constexpr uint32_t kSmSlot = kSmBar + 16;
 constexpr uint32_t kSmExp = kSmBar + 32;                   // [4][128] exponents
-constexpr uint32_t kSmTotal = kSmExp + 4 * kRows * 4;
+constexpr uint32_t kSmW = kSmExp + 4 * kRows * 4;          // R64: W_64^r, r < 32 (Q62)
+constexpr uint32_t kSmTotal = kSmW + 32 * 16;
 constexpr uint32_t kTmemCols = 512;                        // kDiag x 64 fp32 columns
 // The digits of X are the base-256 digits of X + kOff, less 128 (kOff has every digit 128).
 constexpr unsigned long long kOff = 0x0080808080808080ULL;
@@ -96,10 +98,19 @@ __device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity, long lon
   }
 }
 
+// Barrier of the 512 worker threads (the issuing warp does not take part).
+__device__ __forceinline__ void worker_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kWorkers) : "memory"); }
+
 __device__ __forceinline__ void mma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
       "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&r)[4]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(taddr));
 }
 
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
@@ -144,63 +155,187 @@ __device__ __forceinline__ GenSrc gen_source(const FftGen& g, int64_t col) {
   return r;
 }
 
-// Loads of one tile's inputs for a thread (its sequence's elements e = e0 + j es, j < 8) into v,
-// with the first pass's column generation or spectrum product.
-__device__ __forceinline__ void load_inputs(double2 (&v)[8], const double2* __restrict__ src,
-                                            const double2* __restrict__ hmul, int64_t nseg, const FftGen& gen,
-                                            int logF, int logS, int64_t col, uint32_t ibase, int e0, int es) {
+// A thread's inputs of one tile (its sequence's elements e = e0 + j es, j < 8) in two steps, so that
+// the loads can go out a tile ahead: prefetch_inputs sends out the loads that are streamed once
+// (the column values, or the coefficients of a generated column) into v, and finish_inputs applies
+// the first pass's spectrum product or column generation with the tables these share with other
+// columns (mostly in L2).
+__device__ __forceinline__ void prefetch_inputs(double2 (&v)[8], const double2* __restrict__ src,
+                                                const double2* __restrict__ hmul, int64_t nseg, const FftGen& gen,
+                                                int logF, int logS, int64_t col, uint32_t ibase, int e0, int es) {
   if (gen.coef) {
     const GenSrc gs = gen_source(gen, col);
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       const int64_t t = (int64_t)ibase + ((int64_t)(e0 + j * es) << logS);
-      if (t < gs.lim) {
-        const double c = __ldg(gs.c + t);
-        const double2 w = __ldg(gs.v + t);
-        v[j] = make_double2(c * w.x, c * w.y);
-      } else {
-        v[j] = make_double2(0.0, 0.0);
-      }
-    }
-  } else if (hmul) {
-    const int64_t scol = col / nseg, seg = col - scol * nseg;
-    const double2* x = src + (scol << logF);
-    const double2* hc = hmul + (seg << logF);
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const uint32_t t = ibase + ((uint32_t)(e0 + j * es) << logS);
-      v[j] = cmul(x[t], __ldg(&hc[t]));
+      v[j].x = t < gs.lim ? __ldg(gs.c + t) : 0.0;
     }
   } else {
-    const double2* x = src + (col << logF);
+    const double2* x = src + ((hmul ? col / nseg : col) << logF);
 #pragma unroll
     for (int j = 0; j < 8; ++j) v[j] = x[ibase + ((uint32_t)(e0 + j * es) << logS)];
   }
 }
 
+__device__ __forceinline__ void finish_inputs(double2 (&v)[8], const double2* __restrict__ hmul, int64_t nseg,
+                                              const FftGen& gen, int logF, int logS, int64_t col, uint32_t ibase,
+                                              int e0, int es) {
+  if (gen.coef) {
+    const GenSrc gs = gen_source(gen, col);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int64_t t = (int64_t)ibase + ((int64_t)(e0 + j * es) << logS);
+      const double c = v[j].x;  // 0 beyond the column's points
+      const double2 w = t < gs.lim ? __ldg(gs.v + t) : make_double2(0.0, 0.0);
+      v[j] = make_double2(c * w.x, c * w.y);
+    }
+  } else if (hmul) {
+    const double2* hc = hmul + ((col % nseg) << logF);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = cmul(v[j], __ldg(&hc[ibase + ((uint32_t)(e0 + j * es) << logS)]));
+  }
+}
+
+// Scale and fixed point of one tile's inputs (steps 1 and 2 of a tile): the sequence's scale
+// 2^E (largest exponent over its four quarters, and for R64 over both of its rows, before the
+// twiddles), X = v 2^(54 - E) in integers, and X times the pass twiddles W_F^{p s e} (Q62) with
+// the product rounded back to units of X. All worker threads call it (one worker barrier).
+template <bool INV, bool R64>
+__device__ __forceinline__ int tile_fixed(const double2 (&v)[8], long long (&xr)[8], long long (&xi)[8],
+                                          int* emx, int i, int qd, uint32_t p, int logS,
+                                          const longlong2* __restrict__ twq, int e0, int es) {
+  int m = 1;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) m = max(m, max(exp_field(v[j].x), exp_field(v[j].y)));
+  emx[qd * kRows + i] = m;
+  worker_sync();
+  int mx = max(max(emx[i], emx[kRows + i]), max(emx[2 * kRows + i], emx[3 * kRows + i]));
+  if (R64) {  // both rows of the sequence
+    const int o = i ^ 1;
+    mx = max(mx, max(max(emx[o], emx[kRows + o]), max(emx[2 * kRows + o], emx[3 * kRows + o])));
+  }
+  const int E = mx - 1022;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    xr[j] = to_fixed(v[j].x, E);
+    xi[j] = to_fixed(v[j].y, E);
+  }
+  if (p != 0) {
+    const uint32_t ps = p << logS;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const longlong2 w = __ldg(&twq[ps * (uint32_t)(e0 + j * es)]);
+      const long long wi = INV ? -w.y : w.y;
+      // three products (Gauss): re = a c - b d, im = (a + b)(c + d) - a c - b d, with a, b the
+      // parts of X shifted left by 7 (at most 2^61 each, their sum at most 2^62) and c, d the
+      // twiddle's (|c + d| <= 2^62.5): no product or sum overflows
+      const long long ar = xr[j] << 7, ai = xi[j] << 7;
+      const long long ac = __mul64hi(ar, w.x), bd = __mul64hi(ai, wi);
+      const long long re = (ac - bd) << 1;  // (X w) 2^6, within 4 units
+      const long long im = (__mul64hi(ar + ai, w.x + wi) - ac - bd) << 1;
+      xr[j] = (re + 32) >> 6;
+      xi[j] = (im + 32) >> 6;
+    }
+  }
+  return E;
+}
+
+// Step 3: the digits. Plane a holds digit a (weight 256^(6 - a)) of every real; this thread writes
+// K columns 16 qd .. 16 qd + 15 of row i (2 core-matrix rows of 16 bytes per plane). The digits of
+// X are the bytes of X + kOff less 128: one byte permutation takes byte b of the real and
+// imaginary parts into the low bytes of the two fp16 halves, whose bits 0x6400 + u are 1024 + u,
+// and one packed subtraction of 1152 leaves u - 128.
+__device__ __forceinline__ void store_digits(const long long (&xr)[8], const long long (&xi)[8], unsigned char* sm,
+                                             int i, int qd) {
+#pragma unroll
+  for (int c2 = 0; c2 < 2; ++c2) {
+    uint32_t rlo[4], rhi[4], ilo[4], ihi[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const unsigned long long yr = (unsigned long long)xr[4 * c2 + u] + kOff;
+      const unsigned long long yi = (unsigned long long)xi[4 * c2 + u] + kOff;
+      rlo[u] = (uint32_t)yr;
+      rhi[u] = (uint32_t)(yr >> 32);
+      ilo[u] = (uint32_t)yi;
+      ihi[u] = (uint32_t)(yi >> 32);
+    }
+    const uint32_t off = core_off((uint32_t)i, (uint32_t)(16 * qd + 8 * c2));
+    const __half2 bias = __half2half2(__ushort_as_half(0x6480));
+#pragma unroll
+    for (int a = 0; a < kDig; ++a) {
+      const int b = kDig - 1 - a;  // byte of X + kOff
+      const uint32_t sel = (uint32_t)(b & 3) | ((uint32_t)(4 + (b & 3)) << 8);
+      uint32_t wd[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const uint32_t pr = b >= 4 ? __byte_perm(rhi[u], ihi[u], sel) : __byte_perm(rlo[u], ilo[u], sel);
+        const uint32_t bits = (pr & 0x00ff00ffu) | 0x64006400u;
+        const __half2 d = __hsub2(*reinterpret_cast<const __half2*>(&bits), bias);
+        wd[u] = *reinterpret_cast<const uint32_t*>(&d);
+      }
+      *reinterpret_cast<uint4*>(sm + kSmA + a * kAPlane + off) = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+    }
+  }
+}
+
+// Step 4, issued by one thread: the products, K steps of 16 reals (256 bytes). One MMA multiplies
+// digit a of the sequences by several consecutive digit planes b of the DFT matrix at once (N = 64
+// per plane, the planes lie one after another): its output for plane b lands 64 b columns after
+// its start, so starting at diagonal a puts every product on its diagonal a + b. Planes
+// b <= min(6, 7 - a) are used, as two MMAs (b < 4 and b >= 4). In the first K step the MMAs of
+// digit 0 overwrite diagonals 0-6 and plane 6 of digit 1 overwrites diagonal 7 (its own MMA), so
+// every other product accumulates.
+__device__ __forceinline__ void issue_products(uint32_t sbase, uint32_t tbase, uint32_t bar_m) {
+  asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll 1
+  for (int ks = 0; ks < kKr / 16; ++ks)
+#pragma unroll
+    for (int a = 0; a < kDig; ++a) {
+      const uint64_t ad = mat_desc(sbase + kSmA + a * kAPlane + ks * 256);
+      const int nb1 = min(4, kDiag - a), nb2 = max(0, min(kDig - 1, kDiag - 1 - a) - 3);
+      const uint32_t acc = (ks > 0 || a > 0) ? 1u : 0u;
+      mma_f16(tbase + (uint32_t)(a * kKr), ad, mat_desc(sbase + kSmB + ks * 256), idesc_n(kKr * nb1), acc);
+      if (ks == 0 && a == 1) {
+        mma_f16(tbase + 5u * kKr, ad, mat_desc(sbase + kSmB + 4 * kBPlane), idesc_n(2 * kKr), 1u);
+        mma_f16(tbase + 7u * kKr, ad, mat_desc(sbase + kSmB + 6 * kBPlane), idesc_n(kKr), 0u);
+      } else if (nb2 > 0) {
+        mma_f16(tbase + (uint32_t)((a + 4) * kKr), ad, mat_desc(sbase + kSmB + 4 * kBPlane + ks * 256),
+                idesc_n(kKr * nb2), acc);
+      }
+    }
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar_m)
+               : "memory");
+}
+
 // R64: a radix-64 pass. Each 64-point DFT is two 32-point DFTs, of the even and of the odd
-// elements (rows j and 64 + j of the tile, both scaled by the sequence's 2^E), on the tensor cores,
-// and one radix-2 step in 64-bit integers: y_r = Z0_r + W_64^r Z1_r, y_{r+32} = Z0_r - W_64^r Z1_r,
-// r < 32 (the odd rows' Z1 times the Q62 twiddle, exchanged through shared memory).
+// elements (rows 2j and 2j + 1 of the tile, both scaled by the sequence's 2^E), on the tensor
+// cores, and one radix-2 step in 64-bit integers: y_r = Z0_r + W_64^r Z1_r,
+// y_{r+32} = Z0_r - W_64^r Z1_r, r < 32. The two rows of a sequence are neighbouring lanes of one
+// warp: of the two outputs r of a quarter of the read-back, the even lane takes the first and the
+// odd lane the second, each receiving the other row's Z by one lane exchange.
+//
+// Per CTA the tiles form a pipeline. One warp only issues the products (the issue of 45 MMAs
+// holds its thread for about as long as they run). While the products of tile t run, the 512
+// worker threads bring tile t + 1 (loaded during tile t - 1) to fixed point and send out the
+// loads of tile t + 2; once the products are done they write tile t + 1's digits over tile t's
+// (which the products no longer read) and read tile t's sums out of TMEM.
 template <bool INV, bool R64>
 __global__ void __launch_bounds__(kThreads, 1)
     k_fft_pass_tc(const double2* __restrict__ src, double2* __restrict__ dst, int logF, int logS, int64_t ntiles,
                   const longlong2* __restrict__ twq, const double2* __restrict__ hmul, int64_t nseg, FftGen gen,
                   const void* __restrict__ bdig, unsigned* err) {
   extern __shared__ __align__(1024) unsigned char sm[];
-  const int tid = threadIdx.x, i = tid & (kRows - 1), qd = tid >> 7, warp = tid >> 5;
+  const int tid = threadIdx.x, i = tid & (kRows - 1), qd = (tid >> 7) & 3, warp = tid >> 5;
+  const bool worker = tid < kWorkers, issuer = tid == kWorkers;
   const uint32_t sbase = smem_addr(sm);
   const uint32_t bar_b = sbase + kSmBar, bar_m = sbase + kSmBar + 8;
   uint32_t* slot = reinterpret_cast<uint32_t*>(sm + kSmSlot);
   int* emx = reinterpret_cast<int*>(sm + kSmExp);
-  __shared__ int s_fail;
+  longlong2* tw64 = reinterpret_cast<longlong2*>(sm + kSmW);
   const long long t0 = clock64();
 
-  for (int z = tid; z < (int)(kAPlane / 16); z += kThreads)
-    reinterpret_cast<uint4*>(sm + kSmZero)[z] = make_uint4(0u, 0u, 0u, 0u);
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  if (R64 && tid < 32) tw64[tid] = __ldg(&twq[(uint32_t)tid << (logF - 6)]);  // W_64^r = W_F^{r F / 64}
   if (tid == 0) {
-    s_fail = 0;
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar_b), "r"(1));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar_m), "r"(1));
     asm volatile("fence.mbarrier_init.release.cluster;");
@@ -215,7 +350,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tbase = *slot;
   // the DFT matrix digits: one bulk copy into shared memory
-  if (tid == 0) {
+  if (issuer) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_b), "r"(kDig * kBPlane)
                  : "memory");
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -229,8 +364,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int lgs = logF - LR;                 // log2 of the sequences per column
   const int tpc_log = lgs - LT;              // log2 of the tiles per column
   const uint32_t smask = (1u << logS) - 1u;
-  const int jrow = R64 ? (i & 63) : i;       // the tile's sequence of this row
-  const int par = R64 ? (i >> 6) : 0;        // R64: even (0) or odd (1) elements
+  const int jrow = R64 ? (i >> 1) : i;       // the tile's sequence of this row
+  const int par = R64 ? (i & 1) : 0;         // R64: even (0) or odd (1) elements
   const int e0 = R64 ? 16 * qd + par : 8 * qd, es = R64 ? 2 : 1;  // this thread's elements e0 + j es
   auto seq_of = [&](int64_t tile, int64_t& col, uint32_t& g, uint32_t& p, uint32_t& ibase) {
     col = tile >> tpc_log;
@@ -239,239 +374,149 @@ __global__ void __launch_bounds__(kThreads, 1)
     ibase = (g & smask) + ((p << LR) << logS);  // element e at ibase + (e << logS)
   };
   double2 v[8];
-  int64_t tile = blockIdx.x;
-  if (tile < ntiles) {
+  long long xr[8], xi[8];
+  int E = 0;
+  int64_t tile = blockIdx.x;  // the grid has at most ntiles CTAs
+  if (worker) {
     int64_t col;
     uint32_t g, p, ib;
     seq_of(tile, col, g, p, ib);
-    load_inputs(v, src, hmul, nseg, gen, logF, logS, col, ib, e0, es);
+    prefetch_inputs(v, src, hmul, nseg, gen, logF, logS, col, ib, e0, es);
+    finish_inputs(v, hmul, nseg, gen, logF, logS, col, ib, e0, es);
+    E = tile_fixed<INV, R64>(v, xr, xi, emx, i, qd, p, logS, twq, e0, es);
+    const int64_t n1 = tile + gridDim.x;
+    if (n1 < ntiles) {
+      seq_of(n1, col, g, p, ib);
+      prefetch_inputs(v, src, hmul, nseg, gen, logF, logS, col, ib, e0, es);
+    }
   }
-  // every thread waits; the CTA agrees on the outcome, so all of it leaves the loop together
-  if (__syncthreads_or(!bar_wait(bar_b, 0, t0) ? 1 : 0)) s_fail = 1;
-  __syncthreads();
+  const bool b_ok = bar_wait(bar_b, 0, t0);
+  if (worker) store_digits(xr, xi, sm, i, qd);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  // the CTA agrees on every failure, so all of it leaves the loop together
+  bool stop = __syncthreads_or(b_ok ? 0 : 1) != 0;
 
   uint32_t phase = 0;
-  for (; tile < ntiles && !s_fail; tile += gridDim.x) {
-    int64_t col;
-    uint32_t g, p, ibase;
-    seq_of(tile, col, g, p, ibase);
-    // 1. the sequence's scale 2^E (largest exponent over its four quarters, before the twiddles)
-    int m = 1;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) m = max(m, max(exp_field(v[j].x), exp_field(v[j].y)));
-    emx[qd * kRows + i] = m;
-    __syncthreads();
-    int mx = max(max(emx[i], emx[kRows + i]), max(emx[2 * kRows + i], emx[3 * kRows + i]));
-    if (R64) {  // both rows of the sequence
-      const int o = i ^ 64;
-      mx = max(mx, max(max(emx[o], emx[kRows + o]), max(emx[2 * kRows + o], emx[3 * kRows + o])));
-    }
-    const int E = mx - 1022;
-    // 2. X = v 2^(54 - E) in integers, times the pass twiddles W_F^{p s e} (Q62) with the product
-    //    rounded back to units of X
-    long long xr[8], xi[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      xr[j] = to_fixed(v[j].x, E);
-      xi[j] = to_fixed(v[j].y, E);
-    }
-    if (p != 0) {
-      const uint32_t ps = p << logS;
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const longlong2 w = __ldg(&twq[ps * (uint32_t)(e0 + j * es)]);
-        const long long wi = INV ? -w.y : w.y;
-        // three products (Gauss): re = a c - b d, im = (a + b)(c + d) - a c - b d, with a, b the
-        // parts of X shifted left by 7 (at most 2^61 each, their sum at most 2^62) and c, d the
-        // twiddle's (|c + d| <= 2^62.5): no product or sum overflows
-        const long long ar = xr[j] << 7, ai = xi[j] << 7;
-        const long long ac = __mul64hi(ar, w.x), bd = __mul64hi(ai, wi);
-        const long long re = (ac - bd) << 1;  // (X w) 2^6, within 4 units
-        const long long im = (__mul64hi(ar + ai, w.x + wi) - ac - bd) << 1;
-        xr[j] = (re + 32) >> 6;
-        xi[j] = (im + 32) >> 6;
-      }
-    }
-    // 3. digits: plane a holds digit a (weight 256^(6 - a)) of every real; this thread writes
-    //    K columns 16 qd .. 16 qd + 15 of row i (2 core-matrix rows of 16 bytes per plane). The
-    //    digits of X are the bytes of X + kOff less 128: one byte permutation takes byte b of the
-    //    real and imaginary parts into the low bytes of the two fp16 halves, whose bits 0x6400 + u
-    //    are 1024 + u, and one packed subtraction of 1152 leaves u - 128.
-#pragma unroll
-    for (int c2 = 0; c2 < 2; ++c2) {
-      uint32_t rlo[4], rhi[4], ilo[4], ihi[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const unsigned long long yr = (unsigned long long)xr[4 * c2 + u] + kOff;
-        const unsigned long long yi = (unsigned long long)xi[4 * c2 + u] + kOff;
-        rlo[u] = (uint32_t)yr;
-        rhi[u] = (uint32_t)(yr >> 32);
-        ilo[u] = (uint32_t)yi;
-        ihi[u] = (uint32_t)(yi >> 32);
-      }
-      const uint32_t off = core_off((uint32_t)i, (uint32_t)(16 * qd + 8 * c2));
-      const __half2 bias = __half2half2(__ushort_as_half(0x6480));
-#pragma unroll
-      for (int a = 0; a < kDig; ++a) {
-        const int b = kDig - 1 - a;      // byte of X + kOff
-        const uint32_t sel = (uint32_t)(b & 3) | ((uint32_t)(4 + (b & 3)) << 8);
-        uint32_t wd[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const uint32_t pr = b >= 4 ? __byte_perm(rhi[u], ihi[u], sel)
-                                     : __byte_perm(rlo[u], ilo[u], sel);
-          const uint32_t bits = (pr & 0x00ff00ffu) | 0x64006400u;
-          const __half2 d = __hsub2(*reinterpret_cast<const __half2*>(&bits), bias);
-          wd[u] = *reinterpret_cast<const uint32_t*>(&d);
-        }
-        *reinterpret_cast<uint4*>(sm + kSmA + a * kAPlane + off) = make_uint4(wd[0], wd[1], wd[2], wd[3]);
-      }
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
-    // 4. one thread issues the products, K steps of 16 reals (256 bytes). One MMA multiplies digit a
-    //    of the sequences by several consecutive digit planes b of the DFT matrix at once (N = 64
-    //    per plane, the planes lie one after another): its output for plane b lands 64 b columns
-    //    after its start, so starting at diagonal a puts every product on its diagonal a + b.
-    //    Planes b <= min(6, 7 - a) are used, as two MMAs (b < 4 and b >= 4); the first K step's
-    //    MMAs of digit 0 overwrite diagonals 0-6 and a product with a zero A clears diagonal 7,
-    //    so everything after accumulates.
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;");
-      const uint64_t zd = mat_desc(sbase + kSmZero);
-      mma_f16(tbase + 7 * kKr, zd, mat_desc(sbase + kSmB), idesc_n(kKr), 0u);
-#pragma unroll 1
-      for (int ks = 0; ks < kKr / 16; ++ks)
-#pragma unroll
-        for (int a = 0; a < kDig; ++a) {
-          const uint64_t ad = mat_desc(sbase + kSmA + a * kAPlane + ks * 256);
-          const int nb1 = min(4, kDiag - a), nb2 = max(0, min(kDig - 1, kDiag - 1 - a) - 3);
-          const uint32_t acc = (ks > 0 || a > 0) ? 1u : 0u;
-          mma_f16(tbase + (uint32_t)(a * kKr), ad, mat_desc(sbase + kSmB + ks * 256), idesc_n(kKr * nb1), acc);
-          if (nb2 > 0)
-            mma_f16(tbase + (uint32_t)((a + 4) * kKr), ad, mat_desc(sbase + kSmB + 4 * kBPlane + ks * 256),
-                    idesc_n(kKr * nb2), acc);
-        }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar_m)
-                   : "memory");
-    }
-    // 5. the next tile's loads go out while the products run
+  for (; tile < ntiles && !stop; tile += gridDim.x) {
     const int64_t next = tile + gridDim.x;
-    if (next < ntiles) {
-      int64_t ncol;
-      uint32_t ng, np, nib;
-      seq_of(next, ncol, ng, np, nib);
-      load_inputs(v, src, hmul, nseg, gen, logF, logS, ncol, nib, e0, es);
-    }
-    if (__syncthreads_or(!bar_wait(bar_m, phase, t0) ? 1 : 0)) {
-      s_fail = 1;
-      break;
-    }
-    phase ^= 1u;
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    // 6. read back: lane i (warp quarter warp & 3), columns 16 qd .. 16 qd + 15 of every diagonal;
-    //    y = Y 2^(E - 55), applied to the exponent field of the converted Y
-    const uint32_t lane_addr = tbase + ((uint32_t)(32 * (warp & 3)) << 16);
-    // 2^(E - 55) goes into the exponent field of the converted Y while the result stays a normal
-    // number (every realistic input); a warp with a sequence outside that range multiplies instead
-    const bool wide_range = __any_sync(0xffffffffu, E - 55 < -900 || E - 55 > 900);
-    const double scale2 = wide_range ? ldexp(1.0, E - 55) : 1.0;
-    double2* y = dst + (col << logF) + g;
-    // R64: the exchange of Z0 and W_64^r Z1 (int64 pairs) at [r][row] of the digit area, which
-    // the finished products no longer read
-    longlong2* xch = reinterpret_cast<longlong2*>(sm + kSmA);
+    bool fail = false;
+    if (issuer) issue_products(sbase, tbase, bar_m);
+    if (worker) {
+      const int Et = E;
+      if (next < ntiles) {  // the same for every worker
+        int64_t ncol;
+        uint32_t ng, np, nib;
+        seq_of(next, ncol, ng, np, nib);
+        finish_inputs(v, hmul, nseg, gen, logF, logS, ncol, nib, e0, es);
+        E = tile_fixed<INV, R64>(v, xr, xi, emx, i, qd, np, logS, twq, e0, es);
+        const int64_t next2 = next + gridDim.x;
+        if (next2 < ntiles) {
+          seq_of(next2, ncol, ng, np, nib);
+          prefetch_inputs(v, src, hmul, nseg, gen, logF, logS, ncol, nib, e0, es);
+        }
+      }
+      fail = !bar_wait(bar_m, phase, t0);
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      // the products no longer read the digit planes: the next tile's digits go in
+      if (next < ntiles) store_digits(xr, xi, sm, i, qd);
+
+      int64_t col;
+      uint32_t g, p, ibase;
+      seq_of(tile, col, g, p, ibase);
+      // read back: lane i (warp quarter warp & 3), columns 16 qd .. 16 qd + 15 of every diagonal, a
+      // quarter at a time; y = Y 2^(Et - 55), applied to the exponent field of the converted Y
+      const uint32_t lane_addr = tbase + ((uint32_t)(32 * (warp & 3)) << 16);
+      // 2^(Et - 55) goes into the exponent field of the converted Y while the result stays a
+      // normal number (every realistic input); a warp with a sequence outside that range multiplies
+      const bool wide_range = __any_sync(0xffffffffu, Et - 55 < -900 || Et - 55 > 900);
+      const double scale2 = wide_range ? ldexp(1.0, Et - 55) : 1.0;
+      double2* y = dst + (col << logF) + g;
 #pragma unroll 1
-    for (int c8 = 0; c8 < 2; ++c8) {
-      uint32_t d[kDiag][8];
+      for (int c4 = 0; c4 < 4; ++c4) {
+        uint32_t d[kDiag][4];
 #pragma unroll
-      for (int s = 0; s < kDiag; ++s) tmem_ld8(lane_addr + (uint32_t)(s * kKr + 16 * qd + 8 * c8), d[s]);
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      long long Ys[8];
-#pragma unroll
-      for (int n = 0; n < 8; ++n) {
-        // diagonals 0-3 hold at most 1, 2, 3, 4 x 2^20 in size: adding 1.5 2^23 puts the integer in
-        // the low mantissa bits exactly (|x| <= 2^22); the larger ones convert on the F2I path
-        int D[kDiag];
-#pragma unroll
-        for (int s = 0; s < 4; ++s) D[s] = __float_as_int(__uint_as_float(d[s][n]) + 12582912.0f) - 0x4B400000;
-#pragma unroll
-        for (int s = 4; s < kDiag; ++s) D[s] = __float2int_rn(__uint_as_float(d[s][n]));
-        // D_6 2^-5 + D_7 2^-13, exact as an integer over 2^13 and rounded to the nearest unit; then
-        // D_5..D_2 times 2^3, 2^11, 2^19, 2^27 as 32-bit multiply-adds into the 64-bit sum, and
-        // D_1 2^35, D_0 2^43 added to its high word: all modulo 2^64, exact since |Y| < 2^61
-        long long Y = ((long long)D[6] * 256 + D[7] + 4096) >> 13;
-        Y += (long long)D[5] * 8;
-        Y += (long long)D[4] * 2048;
-        Y += (long long)D[3] * 524288;
-        Y += (long long)D[2] * 134217728;
-        const unsigned hi = (unsigned)((unsigned long long)Y >> 32) + ((unsigned)D[1] << 3) + ((unsigned)D[0] << 11);
-        Ys[n] = (long long)(((unsigned long long)hi << 32) | ((unsigned long long)Y & 0xFFFFFFFFULL));
-      }
-      if (R64) {
-        // |Z| <= 2^60.5 in units of Y (a sum of 32 inputs of modulus at most sqrt(2) 2^E): the odd
-        // rows rotate by W_64^r in three products of (Z shifted by 1) with the Q62 twiddle
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int r = 8 * qd + 4 * c8 + u;
-          long long zr = Ys[2 * u], zi = Ys[2 * u + 1];
-          if (par) {
-            const longlong2 w = __ldg(&twq[(uint32_t)r << (logF - 6)]);  // W_64^r = W_F^{r F / 64}
-            const long long wi = INV ? -w.y : w.y;
-            const long long ar = zr << 1, ai = zi << 1;
-            const long long ac = __mul64hi(ar, w.x), bd = __mul64hi(ai, wi);
-            const long long im = __mul64hi(ar + ai, w.x + wi) - ac - bd;
-            zr = (ac - bd) << 1;
-            zi = im << 1;
-          }
-          xch[r * kRows + i] = make_longlong2(zr, zi);
-        }
-        continue;
-      }
-      double o[8];
-      if (!wide_range) {
-#pragma unroll
-        for (int n = 0; n < 8; ++n) {
-          const double yd = __ll2double_rn(Ys[n]);  // one rounding; Y = 0 stays 0
-          o[n] = Ys[n] ? __longlong_as_double(__double_as_longlong(yd) + ((long long)(E - 55) << 52)) : 0.0;
-        }
-      } else {
-#pragma unroll
-        for (int n = 0; n < 8; ++n) o[n] = __ll2double_rn(Ys[n]) * scale2;
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int r = 8 * qd + 4 * c8 + u;  // output r: reals 2r, 2r + 1
-        y[(int64_t)r << lgs] = make_double2(o[2 * u], o[2 * u + 1]);
-      }
-    }
-    if (R64) {
-      // the radix-2 step: thread (row i, quarter qd) takes outputs r and r + 32 of its sequence for
-      // r = 8 qd + 4 (i >> 6) .. + 3
-      __syncthreads();
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int r = 8 * qd + 4 * par + u;
-        const longlong2 z0 = xch[r * kRows + jrow], z1 = xch[r * kRows + 64 + jrow];
-        const long long Ya[4] = {z0.x + z1.x, z0.y + z1.y, z0.x - z1.x, z0.y - z1.y};
-        double o[4];
+        for (int s = 0; s < kDiag; ++s) tmem_ld4(lane_addr + (uint32_t)(s * kKr + 16 * qd + 4 * c4), d[s]);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        long long Ys[4];
 #pragma unroll
         for (int n = 0; n < 4; ++n) {
-          const double yd = __ll2double_rn(Ya[n]);
-          o[n] = wide_range ? yd * scale2
-                            : (Ya[n] ? __longlong_as_double(__double_as_longlong(yd) + ((long long)(E - 55) << 52))
-                                     : 0.0);
+          // diagonals 0-3 hold at most 1, 2, 3, 4 x 2^20 in size: adding 1.5 2^23 puts the integer
+          // in the low mantissa bits exactly (|x| <= 2^22); the larger ones convert on the F2I path
+          int D[kDiag];
+#pragma unroll
+          for (int s = 0; s < 4; ++s) D[s] = __float_as_int(__uint_as_float(d[s][n]) + 12582912.0f) - 0x4B400000;
+#pragma unroll
+          for (int s = 4; s < kDiag; ++s) D[s] = __float2int_rn(__uint_as_float(d[s][n]));
+          // D_6 2^-5 + D_7 2^-13, exact as an integer over 2^13 and rounded to the nearest unit; then
+          // D_5..D_2 times 2^3, 2^11, 2^19, 2^27 as 32-bit multiply-adds into the 64-bit sum, and
+          // D_1 2^35, D_0 2^43 added to its high word: all modulo 2^64, exact since |Y| < 2^61
+          long long Y = ((long long)D[6] * 256 + D[7] + 4096) >> 13;
+          Y += (long long)D[5] * 8;
+          Y += (long long)D[4] * 2048;
+          Y += (long long)D[3] * 524288;
+          Y += (long long)D[2] * 134217728;
+          const unsigned hi =
+              (unsigned)((unsigned long long)Y >> 32) + ((unsigned)D[1] << 3) + ((unsigned)D[0] << 11);
+          Ys[n] = (long long)(((unsigned long long)hi << 32) | ((unsigned long long)Y & 0xFFFFFFFFULL));
         }
-        y[(int64_t)r << lgs] = make_double2(o[0], o[1]);
-        y[(int64_t)(r + 32) << lgs] = make_double2(o[2], o[3]);
+        if (R64) {
+          // the lane pair's outputs r0 = 8 qd + 2 c4 (even lane) and r0 + 1 (odd lane): each lane sends
+          // the other's Z and receives its own sequence's other row
+          const long long sr = par ? Ys[0] : Ys[2], si = par ? Ys[1] : Ys[3];
+          const long long rr = __shfl_xor_sync(0xffffffffu, sr, 1), ri = __shfl_xor_sync(0xffffffffu, si, 1);
+          const int r = 8 * qd + 2 * c4 + par;
+          const long long z0r = par ? rr : Ys[0], z0i = par ? ri : Ys[1];
+          const long long z1r = par ? Ys[2] : rr, z1i = par ? Ys[3] : ri;
+          // |Z| <= 2^60.5 in units of Y (a sum of 32 inputs of modulus at most sqrt(2) 2^E): Z1 rotates
+          // by W_64^r in three products of (Z1 shifted by 1) with the Q62 twiddle
+          const longlong2 w = tw64[r];
+          const long long wi = INV ? -w.y : w.y;
+          const long long ar = z1r << 1, ai = z1i << 1;
+          const long long ac = __mul64hi(ar, w.x), bd = __mul64hi(ai, wi);
+          const long long tr = (ac - bd) << 1, ti = (__mul64hi(ar + ai, w.x + wi) - ac - bd) << 1;
+          const long long Ya[4] = {z0r + tr, z0i + ti, z0r - tr, z0i - ti};
+          double o[4];
+#pragma unroll
+          for (int n = 0; n < 4; ++n) {
+            const double yd = __ll2double_rn(Ya[n]);
+            o[n] = wide_range ? yd * scale2
+                              : (Ya[n] ? __longlong_as_double(__double_as_longlong(yd) + ((long long)(Et - 55) << 52))
+                                       : 0.0);
+          }
+          y[(int64_t)r << lgs] = make_double2(o[0], o[1]);
+          y[(int64_t)(r + 32) << lgs] = make_double2(o[2], o[3]);
+          continue;
+        }
+        double o[4];
+        if (!wide_range) {
+#pragma unroll
+          for (int n = 0; n < 4; ++n) {
+            const double yd = __ll2double_rn(Ys[n]);  // one rounding; Y = 0 stays 0
+            o[n] = Ys[n] ? __longlong_as_double(__double_as_longlong(yd) + ((long long)(Et - 55) << 52)) : 0.0;
+          }
+        } else {
+#pragma unroll
+          for (int n = 0; n < 4; ++n) o[n] = __ll2double_rn(Ys[n]) * scale2;
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int r = 8 * qd + 2 * c4 + u;  // output r: reals 2r, 2r + 1
+          y[(int64_t)r << lgs] = make_double2(o[2 * u], o[2 * u + 1]);
+        }
       }
+      // the next tile's digits to the tensor cores' view
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
+    // TMEM free for the next products
     asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
+    stop = __syncthreads_or(fail ? 1 : 0) != 0;
+    if (stop) break;
+    phase ^= 1u;
   }
   // teardown: a failed wait may leave a copy or the products in flight; wait for them (bounded)
   // before the TMEM is freed
-  if (s_fail) {
+  if (stop) {
     if (tid == 0) atomicOr(err, 1u);
     const long long t1 = clock64();
     bar_wait(bar_b, 0, t1);
@@ -530,7 +575,8 @@ void launch_twiddles_q62(const double2* tw, longlong2* twq, int64_t n, cudaStrea
 void launch_pass_tc(bool inverse, int logR, const double2* src, double2* dst, int logF, int logS, int ncols,
                     const longlong2* twq, const double2* hmul, int64_t nseg, const FftGen& gen, const void* bdig,
                     unsigned* err, cudaStream_t st) {
-  const int64_t ntiles = ((int64_t)ncols << logF) >> (logR == 6 ? 12 : 12);  // 4096 points per tile
+  const int64_t ntiles = ((int64_t)ncols << logF) >> 12;  // 4096 points per tile
+  if (ntiles <= 0) return;
   static bool configured[4] = {false, false, false, false};
   const int k = (inverse ? 1 : 0) + (logR == 6 ? 2 : 0);
   if (!configured[k]) {
