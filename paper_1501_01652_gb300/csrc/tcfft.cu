@@ -35,6 +35,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <atomic>
 #include <vector>
 
 #include "cplx.cuh"
@@ -58,8 +59,8 @@ constexpr uint32_t kSmB = kSmA + kDig * kAPlane;           // 112 KB
 constexpr uint32_t kSmBar = kSmB + kDig * kBPlane;         // 168 KB
 constexpr uint32_t kSmSlot = kSmBar + 16;
 constexpr uint32_t kSmExp = kSmBar + 32;                   // [4][128] exponents
-constexpr uint32_t kSmW = kSmExp + 4 * kRows * 4;          // R64: W_64^r, r < 32 (Q62)
-constexpr uint32_t kSmTotal = kSmW + 32 * 16;
+constexpr uint32_t kSmW = kSmExp + 4 * kRows * 4;          // R64: [2][32] rotations W_64^r (Q62)
+constexpr uint32_t kSmTotal = kSmW + 64 * 16;
 constexpr uint32_t kTmemCols = 512;                        // kDiag x 64 fp32 columns
 // The digits of X are the base-256 digits of X + kOff, less 128 (kOff has every digit 128).
 constexpr unsigned long long kOff = 0x0080808080808080ULL;
@@ -107,15 +108,13 @@ __device__ __forceinline__ void mma_f16(uint32_t d, uint64_t a, uint64_t b, uint
       "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
-__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&r)[4]) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(taddr));
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, uint32_t (&r)[2]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(taddr));
 }
 
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, uint32_t (&r)[4]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
                : "r"(taddr));
 }
 
@@ -128,6 +127,13 @@ __device__ __forceinline__ long long to_fixed(double v, int E) {
   const int t = min(1022 + E - max(ef, 1), 63);
   const long long X = (long long)((M2 + ((1ULL << t) >> 1)) >> t);
   return (long long)b < 0 ? -X : X;
+}
+
+// Y 2^sc as a double (one rounding; Y = 0 stays 0) for a normal result: the FP64 pipe's conversion
+// and an add to the exponent field.
+__device__ __forceinline__ double ll2double_fp(long long Y, int sc) {
+  const double yd = __ll2double_rn(Y);
+  return Y ? __longlong_as_double(__double_as_longlong(yd) + ((long long)sc << 52)) : 0.0;
 }
 
 // Exponent field of v (0 for zeros and subnormals).
@@ -155,6 +161,25 @@ __device__ __forceinline__ GenSrc gen_source(const FftGen& g, int64_t col) {
   return r;
 }
 
+// The rows of a tile. A pass's sequences are g = p s + q of each column c (stride s = 2^logS,
+// p < P = F / (R s), q < s): element e of sequence (c, g) is x[c F + q + s (R p + e)], output r goes
+// to y[c F + g + (F / R) r]. A tile holds NS = 4096 / R sequences, in one of two tilings:
+//  * by columns (kByColumn): NS consecutive sequences of one column, so p varies along the tile
+//    when s < NS, and the pass twiddles W_F^{p s e} multiply the inputs;
+//  * by twiddle group: NS sequences with one p, the (c, q) pairs u = c s + q in blocks of NS
+//    (from NS / s columns when s < NS), tile t = (u-block) P + p. The pass twiddles then depend on
+//    e alone and fold into the tile's DFT matrix; a row past the last column loads zeros and
+//    stores nothing. The first pass of a transform (s = F / R, p = 0) has no twiddles.
+enum PassMode { kNoTwiddle = 0, kByColumn = 1, kByGroup = 2 };
+
+struct TileRow {
+  int64_t c;       // column
+  uint32_t g;      // sequence within the column
+  uint32_t ibase;  // element e at ibase + (e << logS) of the column
+  uint32_t p;      // twiddle group
+  bool valid;
+};
+
 // A thread's inputs of one tile (its sequence's elements e = e0 + j es, j < 8) in two steps, so that
 // the loads can go out a tile ahead: prefetch_inputs sends out the loads that are streamed once
 // (the column values, or the coefficients of a generated column) into v, and finish_inputs applies
@@ -162,45 +187,50 @@ __device__ __forceinline__ GenSrc gen_source(const FftGen& g, int64_t col) {
 // columns (mostly in L2).
 __device__ __forceinline__ void prefetch_inputs(double2 (&v)[8], const double2* __restrict__ src,
                                                 const double2* __restrict__ hmul, int64_t nseg, const FftGen& gen,
-                                                int logF, int logS, int64_t col, uint32_t ibase, int e0, int es) {
-  if (gen.coef) {
-    const GenSrc gs = gen_source(gen, col);
+                                                int logF, int logS, const TileRow& w, int e0, int es) {
+  if (!w.valid) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = make_double2(0.0, 0.0);
+  } else if (gen.coef) {
+    const GenSrc gs = gen_source(gen, w.c);
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      const int64_t t = (int64_t)ibase + ((int64_t)(e0 + j * es) << logS);
+      const int64_t t = (int64_t)w.ibase + ((int64_t)(e0 + j * es) << logS);
       v[j].x = t < gs.lim ? __ldg(gs.c + t) : 0.0;
     }
   } else {
-    const double2* x = src + ((hmul ? col / nseg : col) << logF);
+    const double2* x = src + ((hmul ? w.c / nseg : w.c) << logF);
 #pragma unroll
-    for (int j = 0; j < 8; ++j) v[j] = x[ibase + ((uint32_t)(e0 + j * es) << logS)];
+    for (int j = 0; j < 8; ++j) v[j] = x[w.ibase + ((uint32_t)(e0 + j * es) << logS)];
   }
 }
 
 __device__ __forceinline__ void finish_inputs(double2 (&v)[8], const double2* __restrict__ hmul, int64_t nseg,
-                                              const FftGen& gen, int logF, int logS, int64_t col, uint32_t ibase,
-                                              int e0, int es) {
+                                              const FftGen& gen, int logF, int logS, const TileRow& w, int e0,
+                                              int es) {
+  if (!w.valid) return;
   if (gen.coef) {
-    const GenSrc gs = gen_source(gen, col);
+    const GenSrc gs = gen_source(gen, w.c);
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      const int64_t t = (int64_t)ibase + ((int64_t)(e0 + j * es) << logS);
+      const int64_t t = (int64_t)w.ibase + ((int64_t)(e0 + j * es) << logS);
       const double c = v[j].x;  // 0 beyond the column's points
-      const double2 w = t < gs.lim ? __ldg(gs.v + t) : make_double2(0.0, 0.0);
-      v[j] = make_double2(c * w.x, c * w.y);
+      const double2 tw = t < gs.lim ? __ldg(gs.v + t) : make_double2(0.0, 0.0);
+      v[j] = make_double2(c * tw.x, c * tw.y);
     }
   } else if (hmul) {
-    const double2* hc = hmul + ((col % nseg) << logF);
+    const double2* hc = hmul + ((w.c % nseg) << logF);
 #pragma unroll
-    for (int j = 0; j < 8; ++j) v[j] = cmul(v[j], __ldg(&hc[ibase + ((uint32_t)(e0 + j * es) << logS)]));
+    for (int j = 0; j < 8; ++j) v[j] = cmul(v[j], __ldg(&hc[w.ibase + ((uint32_t)(e0 + j * es) << logS)]));
   }
 }
 
 // Scale and fixed point of one tile's inputs (steps 1 and 2 of a tile): the sequence's scale
 // 2^E (largest exponent over its four quarters, and for R64 over both of its rows, before the
-// twiddles), X = v 2^(54 - E) in integers, and X times the pass twiddles W_F^{p s e} (Q62) with
-// the product rounded back to units of X. All worker threads call it (one worker barrier).
-template <bool INV, bool R64>
+// twiddles), X = v 2^(54 - E) in integers, and, when the twiddles multiply the inputs (TWD), X
+// times W_F^{p s e} (Q62) with the product rounded back to units of X. All worker threads call it
+// (one worker barrier).
+template <bool INV, bool R64, bool TWD>
 __device__ __forceinline__ int tile_fixed(const double2 (&v)[8], long long (&xr)[8], long long (&xi)[8],
                                           int* emx, int i, int qd, uint32_t p, int logS,
                                           const longlong2* __restrict__ twq, int e0, int es) {
@@ -220,7 +250,7 @@ __device__ __forceinline__ int tile_fixed(const double2 (&v)[8], long long (&xr)
     xr[j] = to_fixed(v[j].x, E);
     xi[j] = to_fixed(v[j].y, E);
   }
-  if (p != 0) {
+  if (TWD && p != 0) {
     const uint32_t ps = p << logS;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
@@ -240,42 +270,76 @@ __device__ __forceinline__ int tile_fixed(const double2 (&v)[8], long long (&xr)
   return E;
 }
 
-// Step 3: the digits. Plane a holds digit a (weight 256^(6 - a)) of every real; this thread writes
-// K columns 16 qd .. 16 qd + 15 of row i (2 core-matrix rows of 16 bytes per plane). The digits of
-// X are the bytes of X + kOff less 128: one byte permutation takes byte b of the real and
-// imaginary parts into the low bytes of the two fp16 halves, whose bits 0x6400 + u are 1024 + u,
-// and one packed subtraction of 1152 leaves u - 128.
+// Digits of four pairs (re[u], im[u]) of 54-bit integers, as 8 consecutive fp16 K elements
+// (re, im, re, im, ...) of one core-matrix row in every digit plane (base + a pstride + off). Plane
+// a holds digit a (weight 256^(6 - a)). The digits of X are the bytes of X + kOff less 128: one
+// byte permutation takes byte b of the two parts into the low bytes of the two fp16 halves, whose
+// bits 0x6400 + u are 1024 + u, and one packed subtraction of 1152 leaves u - 128.
+__device__ __forceinline__ void put_digits(const long long* re, const long long* im, unsigned char* base,
+                                           uint32_t off, uint32_t pstride) {
+  uint32_t rlo[4], rhi[4], ilo[4], ihi[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const unsigned long long yr = (unsigned long long)re[u] + kOff;
+    const unsigned long long yi = (unsigned long long)im[u] + kOff;
+    rlo[u] = (uint32_t)yr;
+    rhi[u] = (uint32_t)(yr >> 32);
+    ilo[u] = (uint32_t)yi;
+    ihi[u] = (uint32_t)(yi >> 32);
+  }
+  const __half2 bias = __half2half2(__ushort_as_half(0x6480));
+#pragma unroll
+  for (int a = 0; a < kDig; ++a) {
+    const int b = kDig - 1 - a;  // byte of X + kOff
+    const uint32_t sel = (uint32_t)(b & 3) | ((uint32_t)(4 + (b & 3)) << 8);
+    uint32_t wd[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const uint32_t pr = b >= 4 ? __byte_perm(rhi[u], ihi[u], sel) : __byte_perm(rlo[u], ilo[u], sel);
+      const uint32_t bits = (pr & 0x00ff00ffu) | 0x64006400u;
+      const __half2 d = __hsub2(*reinterpret_cast<const __half2*>(&bits), bias);
+      wd[u] = *reinterpret_cast<const uint32_t*>(&d);
+    }
+    *reinterpret_cast<uint4*>(base + a * pstride + off) = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+  }
+}
+
+// Step 3: the sequences' digits; this thread writes K columns 16 qd .. 16 qd + 15 of row i (2
+// core-matrix rows of 16 bytes per plane).
 __device__ __forceinline__ void store_digits(const long long (&xr)[8], const long long (&xi)[8], unsigned char* sm,
                                              int i, int qd) {
 #pragma unroll
-  for (int c2 = 0; c2 < 2; ++c2) {
-    uint32_t rlo[4], rhi[4], ilo[4], ihi[4];
+  for (int c2 = 0; c2 < 2; ++c2)
+    put_digits(xr + 4 * c2, xi + 4 * c2, sm + kSmA, core_off((uint32_t)i, (uint32_t)(16 * qd + 8 * c2)), kAPlane);
+}
+
+// By twiddle group: the tile's DFT matrix, the real 64 x 64 form of sum_m W_32^{r m} W_F^{sigma p s m}
+// (sigma = 1; for R64 the even elements' 32-point DFT, sigma = 2), from the Q62 table: entry
+// (r, m) is W_F^{m (r F / 32 + sigma p s)}. Thread tid takes N row n = tid >> 3 (output r = n >> 1,
+// real or imaginary part) and K columns 8 (tid & 7) .. + 7 (inputs m = 4 (tid & 7) .. + 3).
+template <bool R64>
+__device__ __forceinline__ void load_group_twiddles(longlong2 (&w)[4], const longlong2* __restrict__ twq, int logF,
+                                                    int logS, uint32_t p, int tid) {
+  const uint32_t r = (uint32_t)(tid >> 4), kg = (uint32_t)(tid & 7);
+  const uint32_t mask = (1u << logF) - 1u;
+  const uint32_t step = (r << (logF - 5)) + ((p << logS) << (R64 ? 1 : 0));
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const unsigned long long yr = (unsigned long long)xr[4 * c2 + u] + kOff;
-      const unsigned long long yi = (unsigned long long)xi[4 * c2 + u] + kOff;
-      rlo[u] = (uint32_t)yr;
-      rhi[u] = (uint32_t)(yr >> 32);
-      ilo[u] = (uint32_t)yi;
-      ihi[u] = (uint32_t)(yi >> 32);
-    }
-    const uint32_t off = core_off((uint32_t)i, (uint32_t)(16 * qd + 8 * c2));
-    const __half2 bias = __half2half2(__ushort_as_half(0x6480));
+  for (int j = 0; j < 4; ++j) w[j] = __ldg(&twq[((4 * kg + (uint32_t)j) * step) & mask]);
+}
+
+// The entries' digits (units 2^-54): real output row (co = 0) takes (wr, -wi) for the (real,
+// imaginary) input parts, the imaginary row (wi, wr); the inverse conjugates.
+template <bool INV>
+__device__ __forceinline__ void store_group_digits(const longlong2 (&w)[4], unsigned char* sm, int tid) {
+  const int n = tid >> 3, kg = tid & 7, co = n & 1;
+  long long re[4], im[4];
 #pragma unroll
-    for (int a = 0; a < kDig; ++a) {
-      const int b = kDig - 1 - a;  // byte of X + kOff
-      const uint32_t sel = (uint32_t)(b & 3) | ((uint32_t)(4 + (b & 3)) << 8);
-      uint32_t wd[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const uint32_t pr = b >= 4 ? __byte_perm(rhi[u], ihi[u], sel) : __byte_perm(rlo[u], ilo[u], sel);
-        const uint32_t bits = (pr & 0x00ff00ffu) | 0x64006400u;
-        const __half2 d = __hsub2(*reinterpret_cast<const __half2*>(&bits), bias);
-        wd[u] = *reinterpret_cast<const uint32_t*>(&d);
-      }
-      *reinterpret_cast<uint4*>(sm + kSmA + a * kAPlane + off) = make_uint4(wd[0], wd[1], wd[2], wd[3]);
-    }
+  for (int j = 0; j < 4; ++j) {
+    const long long wr = w[j].x, wi = INV ? -w[j].y : w[j].y;
+    re[j] = ((co ? wi : wr) + 128) >> 8;
+    im[j] = ((co ? wr : -wi) + 128) >> 8;
   }
+  put_digits(re, im, sm + kSmB, core_off((uint32_t)n, (uint32_t)(8 * kg)), kBPlane);
 }
 
 // Step 4, issued by one thread: the products, K steps of 16 reals (256 bytes). One MMA multiplies
@@ -312,18 +376,20 @@ __device__ __forceinline__ void issue_products(uint32_t sbase, uint32_t tbase, u
 // cores, and one radix-2 step in 64-bit integers: y_r = Z0_r + W_64^r Z1_r,
 // y_{r+32} = Z0_r - W_64^r Z1_r, r < 32. The two rows of a sequence are neighbouring lanes of one
 // warp: of the two outputs r of a quarter of the read-back, the even lane takes the first and the
-// odd lane the second, each receiving the other row's Z by one lane exchange.
+// odd lane the second, each receiving the other row's Z by one lane exchange. By twiddle group,
+// the odd elements' extra factor W_F^{p s} joins the rotation: W_F^{r F / 64 + p s}.
 //
 // Per CTA the tiles form a pipeline. One warp only issues the products (the issue of 45 MMAs
 // holds its thread for about as long as they run). While the products of tile t run, the 512
-// worker threads bring tile t + 1 (loaded during tile t - 1) to fixed point and send out the
-// loads of tile t + 2; once the products are done they write tile t + 1's digits over tile t's
-// (which the products no longer read) and read tile t's sums out of TMEM.
-template <bool INV, bool R64>
+// worker threads bring tile t + 1 (loaded during tile t - 1) to fixed point; once the products
+// are done they write tile t + 1's digits (and, by twiddle group, its DFT matrix) over tile t's
+// (which the products no longer read), send out the loads of tile t + 2 and read tile t's sums
+// out of TMEM.
+template <bool INV, bool R64, int MODE>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_fft_pass_tc(const double2* __restrict__ src, double2* __restrict__ dst, int logF, int logS, int64_t ntiles,
-                  const longlong2* __restrict__ twq, const double2* __restrict__ hmul, int64_t nseg, FftGen gen,
-                  const void* __restrict__ bdig, unsigned* err) {
+    k_fft_pass_tc(const double2* __restrict__ src, double2* __restrict__ dst, int logF, int logS, int64_t ncols,
+                  int64_t ntiles, const longlong2* __restrict__ twq, const double2* __restrict__ hmul, int64_t nseg,
+                  FftGen gen, const void* __restrict__ bdig, unsigned* err) {
   extern __shared__ __align__(1024) unsigned char sm[];
   const int tid = threadIdx.x, i = tid & (kRows - 1), qd = (tid >> 7) & 3, warp = tid >> 5;
   const bool worker = tid < kWorkers, issuer = tid == kWorkers;
@@ -331,10 +397,69 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t bar_b = sbase + kSmBar, bar_m = sbase + kSmBar + 8;
   uint32_t* slot = reinterpret_cast<uint32_t*>(sm + kSmSlot);
   int* emx = reinterpret_cast<int*>(sm + kSmExp);
-  longlong2* tw64 = reinterpret_cast<longlong2*>(sm + kSmW);
+  longlong2* tw64 = reinterpret_cast<longlong2*>(sm + kSmW);  // [2][32]: by twiddle group, two p
   const long long t0 = clock64();
 
-  if (R64 && tid < 32) tw64[tid] = __ldg(&twq[(uint32_t)tid << (logF - 6)]);  // W_64^r = W_F^{r F / 64}
+  constexpr int LR = R64 ? 6 : 5;            // log2 of the radix
+  constexpr int LT = R64 ? 6 : 7;            // log2 of the sequences per tile
+  const int lgs = logF - LR;                 // log2 of the sequences per column
+  const uint32_t smask = (1u << logS) - 1u;
+  const int jrow = R64 ? (i >> 1) : i;       // the tile's sequence of this row
+  const int par = R64 ? (i & 1) : 0;         // R64: even (0) or odd (1) elements
+  const int e0 = R64 ? 16 * qd + par : 8 * qd, es = R64 ? 2 : 1;  // this thread's elements e0 + j es
+  const int logP = lgs - logS;               // log2 of the twiddle groups
+  const int tpc_log = lgs - LT;              // by columns: log2 of the tiles per column
+  const int64_t nu = ncols << logS;          // by twiddle group: the (c, q) pairs per group
+  // CTA b takes tiles b, b + grid, ... (the CTAs stream through neighbouring tiles together), except
+  // by twiddle group: there it takes the contiguous range [b ntiles / grid, (b + 1) ntiles / grid)
+  // in p-major order, t = p ublocks + ub, so that its tiles mostly share p and its DFT matrix is
+  // rebuilt only when p changes; Pos walks it without divisions.
+  struct Pos {
+    uint32_t t, ub, p;  // tiles number below 2^31 (4096 points of 16 bytes each)
+  };
+  const uint32_t ublocks = (uint32_t)((nu + (int64_t(1) << LT) - 1) >> LT);
+  auto advance = [&](Pos x) {
+    if (MODE == kByGroup) {
+      ++x.t;
+      if (++x.ub == ublocks) {
+        x.ub = 0;
+        ++x.p;
+      }
+    } else {
+      x.t += gridDim.x;
+    }
+    return x;
+  };
+  auto row_of = [&](const Pos& x) {
+    TileRow w;
+    if (MODE == kByColumn) {
+      w.c = (int64_t)(x.t >> tpc_log);
+      w.g = ((x.t & ((1u << tpc_log) - 1u)) << LT) + (uint32_t)jrow;
+      w.p = w.g >> logS;
+      w.ibase = (w.g & smask) + ((w.p << LR) << logS);
+      w.valid = true;
+    } else {
+      w.p = MODE == kByGroup ? x.p : 0u;
+      const int64_t u = ((int64_t)(MODE == kByGroup ? x.ub : x.t) << LT) + jrow;
+      w.valid = u < nu;
+      const uint32_t q = (uint32_t)u & smask;
+      w.c = w.valid ? (u >> logS) : 0;
+      w.g = (w.p << logS) + q;
+      w.ibase = q + (w.p << (logS + LR));
+    }
+    return w;
+  };
+  const uint32_t t_end =
+      MODE == kByGroup ? (uint32_t)(ntiles * (int64_t)(blockIdx.x + 1) / gridDim.x) : (uint32_t)ntiles;
+  Pos cur;
+  cur.t = MODE == kByGroup ? (uint32_t)(ntiles * (int64_t)blockIdx.x / gridDim.x) : blockIdx.x;
+  cur.p = MODE == kByGroup ? cur.t / ublocks : 0u;
+  cur.ub = cur.t - cur.p * ublocks;
+
+  if (R64 && tid < 32) {
+    // W_64^r = W_F^{r F / 64}; by twiddle group the first tile's W_F^{r F / 64 + p s}
+    tw64[tid] = __ldg(&twq[((uint32_t)tid << (logF - 6)) + (cur.p << logS)]);
+  }
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar_b), "r"(1));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar_m), "r"(1));
@@ -349,8 +474,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tbase = *slot;
-  // the DFT matrix digits: one bulk copy into shared memory
-  if (issuer) {
+  // the DFT matrix digits (without twiddles): one bulk copy into shared memory
+  if (issuer && MODE != kByGroup) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_b), "r"(kDig * kBPlane)
                  : "memory");
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -359,38 +484,23 @@ __global__ void __launch_bounds__(kThreads, 1)
                  : "memory");
   }
 
-  constexpr int LR = R64 ? 6 : 5;            // log2 of the radix
-  constexpr int LT = R64 ? 6 : 7;            // log2 of the sequences per tile
-  const int lgs = logF - LR;                 // log2 of the sequences per column
-  const int tpc_log = lgs - LT;              // log2 of the tiles per column
-  const uint32_t smask = (1u << logS) - 1u;
-  const int jrow = R64 ? (i >> 1) : i;       // the tile's sequence of this row
-  const int par = R64 ? (i & 1) : 0;         // R64: even (0) or odd (1) elements
-  const int e0 = R64 ? 16 * qd + par : 8 * qd, es = R64 ? 2 : 1;  // this thread's elements e0 + j es
-  auto seq_of = [&](int64_t tile, int64_t& col, uint32_t& g, uint32_t& p, uint32_t& ibase) {
-    col = tile >> tpc_log;
-    g = (uint32_t)((tile & ((int64_t(1) << tpc_log) - 1)) << LT) + (uint32_t)jrow;
-    p = g >> logS;
-    ibase = (g & smask) + ((p << LR) << logS);  // element e at ibase + (e << logS)
-  };
   double2 v[8];
   long long xr[8], xi[8];
   int E = 0;
-  int64_t tile = blockIdx.x;  // the grid has at most ntiles CTAs
-  if (worker) {
-    int64_t col;
-    uint32_t g, p, ib;
-    seq_of(tile, col, g, p, ib);
-    prefetch_inputs(v, src, hmul, nseg, gen, logF, logS, col, ib, e0, es);
-    finish_inputs(v, hmul, nseg, gen, logF, logS, col, ib, e0, es);
-    E = tile_fixed<INV, R64>(v, xr, xi, emx, i, qd, p, logS, twq, e0, es);
-    const int64_t n1 = tile + gridDim.x;
-    if (n1 < ntiles) {
-      seq_of(n1, col, g, p, ib);
-      prefetch_inputs(v, src, hmul, nseg, gen, logF, logS, col, ib, e0, es);
+  if (worker) {  // the grid has at most ntiles CTAs: every CTA has a tile
+    const TileRow w0 = row_of(cur);
+    prefetch_inputs(v, src, hmul, nseg, gen, logF, logS, w0, e0, es);
+    finish_inputs(v, hmul, nseg, gen, logF, logS, w0, e0, es);
+    E = tile_fixed<INV, R64, MODE == kByColumn>(v, xr, xi, emx, i, qd, w0.p, logS, twq, e0, es);
+    if (MODE == kByGroup) {
+      longlong2 gw[4];
+      load_group_twiddles<R64>(gw, twq, logF, logS, w0.p, tid);
+      store_group_digits<INV>(gw, sm, tid);
     }
+    const Pos n1 = advance(cur);
+    if (n1.t < t_end) prefetch_inputs(v, src, hmul, nseg, gen, logF, logS, row_of(n1), e0, es);
   }
-  const bool b_ok = bar_wait(bar_b, 0, t0);
+  const bool b_ok = MODE == kByGroup ? true : bar_wait(bar_b, 0, t0);
   if (worker) store_digits(xr, xi, sm, i, qd);
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -398,79 +508,106 @@ __global__ void __launch_bounds__(kThreads, 1)
   bool stop = __syncthreads_or(b_ok ? 0 : 1) != 0;
 
   uint32_t phase = 0;
-  for (; tile < ntiles && !stop; tile += gridDim.x) {
-    const int64_t next = tile + gridDim.x;
+  int bsel = 0;  // R64 by twiddle group: the rotation table of the current tile's p
+  for (; cur.t < t_end && !stop; cur = advance(cur)) {
+    const Pos nx = advance(cur);
+    const bool has_next = nx.t < t_end;  // the same for the whole CTA
+    const bool newp = MODE == kByGroup && has_next && nx.p != cur.p;
     bool fail = false;
     if (issuer) issue_products(sbase, tbase, bar_m);
     if (worker) {
       const int Et = E;
-      if (next < ntiles) {  // the same for every worker
-        int64_t ncol;
-        uint32_t ng, np, nib;
-        seq_of(next, ncol, ng, np, nib);
-        finish_inputs(v, hmul, nseg, gen, logF, logS, ncol, nib, e0, es);
-        E = tile_fixed<INV, R64>(v, xr, xi, emx, i, qd, np, logS, twq, e0, es);
-        const int64_t next2 = next + gridDim.x;
-        if (next2 < ntiles) {
-          seq_of(next2, ncol, ng, np, nib);
-          prefetch_inputs(v, src, hmul, nseg, gen, logF, logS, ncol, nib, e0, es);
-        }
+      if (has_next) {
+        const TileRow wn = row_of(nx);
+        finish_inputs(v, hmul, nseg, gen, logF, logS, wn, e0, es);
+        E = tile_fixed<INV, R64, MODE == kByColumn>(v, xr, xi, emx, i, qd, wn.p, logS, twq, e0, es);
+        if (R64 && newp && tid < 32)
+          tw64[32 * (bsel ^ 1) + tid] = __ldg(&twq[((uint32_t)tid << (logF - 6)) + (nx.p << logS)]);
       }
       fail = !bar_wait(bar_m, phase, t0);
       asm volatile("tcgen05.fence::after_thread_sync;");
-      // the products no longer read the digit planes: the next tile's digits go in
-      if (next < ntiles) store_digits(xr, xi, sm, i, qd);
+      // the products no longer read the digit planes: the next tile's digits (and on a new p its
+      // DFT matrix) go in, and the loads of the tile after it go out (they land while this tile is
+      // read back)
+      if (has_next) {
+        store_digits(xr, xi, sm, i, qd);
+        if (newp) {
+          longlong2 gw[4];
+          load_group_twiddles<R64>(gw, twq, logF, logS, nx.p, tid);
+          store_group_digits<INV>(gw, sm, tid);
+        }
+        const Pos n2 = advance(nx);
+        if (n2.t < t_end) prefetch_inputs(v, src, hmul, nseg, gen, logF, logS, row_of(n2), e0, es);
+      }
 
-      int64_t col;
-      uint32_t g, p, ibase;
-      seq_of(tile, col, g, p, ibase);
-      // read back: lane i (warp quarter warp & 3), columns 16 qd .. 16 qd + 15 of every diagonal, a
-      // quarter at a time; y = Y 2^(Et - 55), applied to the exponent field of the converted Y
+      const TileRow wt = row_of(cur);
+      // read back: lane i (warp quarter warp & 3), columns 16 qd .. 16 qd + 15 of every diagonal, NR
+      // at a time (radix 64: the two outputs of a lane pair); y = Y 2^(Et - 55), applied to the
+      // exponent field of the converted Y
       const uint32_t lane_addr = tbase + ((uint32_t)(32 * (warp & 3)) << 16);
       // 2^(Et - 55) goes into the exponent field of the converted Y while the result stays a
       // normal number (every realistic input); a warp with a sequence outside that range multiplies
       const bool wide_range = __any_sync(0xffffffffu, Et - 55 < -900 || Et - 55 > 900);
       const double scale2 = wide_range ? ldexp(1.0, Et - 55) : 1.0;
-      double2* y = dst + (col << logF) + g;
+      double2* y = dst + (wt.c << logF) + wt.g;
+      const longlong2* rot = tw64 + 32 * bsel;
+      constexpr int NR = R64 ? 4 : 2;
 #pragma unroll 1
-      for (int c4 = 0; c4 < 4; ++c4) {
-        uint32_t d[kDiag][4];
+      for (int c4 = 0; c4 < 16 / NR; ++c4) {
+        // diagonals 4-7 first, then 0-3 (radix 64 holds four reals' digits in half the registers)
+        long long Ys[NR];
+        {
+          uint32_t d[4][NR];
 #pragma unroll
-        for (int s = 0; s < kDiag; ++s) tmem_ld4(lane_addr + (uint32_t)(s * kKr + 16 * qd + 4 * c4), d[s]);
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        long long Ys[4];
+          for (int s = 0; s < 4; ++s) tmem_ld(lane_addr + (uint32_t)((s + 4) * kKr + 16 * qd + NR * c4), d[s]);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-        for (int n = 0; n < 4; ++n) {
-          // diagonals 0-3 hold at most 1, 2, 3, 4 x 2^20 in size: adding 1.5 2^23 puts the integer
-          // in the low mantissa bits exactly (|x| <= 2^22); the larger ones convert on the F2I path
-          int D[kDiag];
+          for (int n = 0; n < NR; ++n) {
+            // diagonals 4-7 convert on the F2I path; D_6 2^-5 + D_7 2^-13 is exact as an integer over
+            // 2^13 and rounded to the nearest unit; D_5 and D_4 weigh 2^3 and 2^11
+            int D[4];
 #pragma unroll
-          for (int s = 0; s < 4; ++s) D[s] = __float_as_int(__uint_as_float(d[s][n]) + 12582912.0f) - 0x4B400000;
+            for (int s = 0; s < 4; ++s) D[s] = __float2int_rn(__uint_as_float(d[s][n]));
+            long long Y = ((long long)D[2] * 256 + D[3] + 4096) >> 13;
+            Y += (long long)D[1] * 8;
+            Y += (long long)D[0] * 2048;
+            Ys[n] = Y;
+          }
+        }
+        {
+          uint32_t d[4][NR];
 #pragma unroll
-          for (int s = 4; s < kDiag; ++s) D[s] = __float2int_rn(__uint_as_float(d[s][n]));
-          // D_6 2^-5 + D_7 2^-13, exact as an integer over 2^13 and rounded to the nearest unit; then
-          // D_5..D_2 times 2^3, 2^11, 2^19, 2^27 as 32-bit multiply-adds into the 64-bit sum, and
-          // D_1 2^35, D_0 2^43 added to its high word: all modulo 2^64, exact since |Y| < 2^61
-          long long Y = ((long long)D[6] * 256 + D[7] + 4096) >> 13;
-          Y += (long long)D[5] * 8;
-          Y += (long long)D[4] * 2048;
-          Y += (long long)D[3] * 524288;
-          Y += (long long)D[2] * 134217728;
-          const unsigned hi =
-              (unsigned)((unsigned long long)Y >> 32) + ((unsigned)D[1] << 3) + ((unsigned)D[0] << 11);
-          Ys[n] = (long long)(((unsigned long long)hi << 32) | ((unsigned long long)Y & 0xFFFFFFFFULL));
+          for (int s = 0; s < 4; ++s) tmem_ld(lane_addr + (uint32_t)(s * kKr + 16 * qd + NR * c4), d[s]);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int n = 0; n < NR; ++n) {
+            // diagonals 0-3 hold at most 1, 2, 3, 4 x 2^20 in size: adding 1.5 2^23 puts the integer
+            // in the low mantissa bits exactly (|x| <= 2^22). D_3 and D_2 weigh 2^19 and 2^27 (32-bit
+            // multiply-adds into the 64-bit sum), D_1 2^35 and D_0 2^43 are added to its high word:
+            // all modulo 2^64, exact since |Y| < 2^61
+            int D[4];
+#pragma unroll
+            for (int s = 0; s < 4; ++s) D[s] = __float_as_int(__uint_as_float(d[s][n]) + 12582912.0f) - 0x4B400000;
+            long long Y = Ys[n];
+            Y += (long long)D[3] * 524288;
+            Y += (long long)D[2] * 134217728;
+            const unsigned hi =
+                (unsigned)((unsigned long long)Y >> 32) + ((unsigned)D[1] << 3) + ((unsigned)D[0] << 11);
+            Ys[n] = (long long)(((unsigned long long)hi << 32) | ((unsigned long long)Y & 0xFFFFFFFFULL));
+          }
         }
         if (R64) {
           // the lane pair's outputs r0 = 8 qd + 2 c4 (even lane) and r0 + 1 (odd lane): each lane sends
           // the other's Z and receives its own sequence's other row
-          const long long sr = par ? Ys[0] : Ys[2], si = par ? Ys[1] : Ys[3];
+          const long long sr = par ? Ys[0] : Ys[NR - 2], si = par ? Ys[1] : Ys[NR - 1];
           const long long rr = __shfl_xor_sync(0xffffffffu, sr, 1), ri = __shfl_xor_sync(0xffffffffu, si, 1);
           const int r = 8 * qd + 2 * c4 + par;
           const long long z0r = par ? rr : Ys[0], z0i = par ? ri : Ys[1];
-          const long long z1r = par ? Ys[2] : rr, z1i = par ? Ys[3] : ri;
+          const long long z1r = par ? Ys[NR - 2] : rr, z1i = par ? Ys[NR - 1] : ri;
           // |Z| <= 2^60.5 in units of Y (a sum of 32 inputs of modulus at most sqrt(2) 2^E): Z1 rotates
-          // by W_64^r in three products of (Z1 shifted by 1) with the Q62 twiddle
-          const longlong2 w = tw64[r];
+          // by W_64^r (by twiddle group W_F^{r F / 64 + p s}) in three products of (Z1 shifted by 1)
+          // with the Q62 twiddle
+          const longlong2 w = rot[r];
           const long long wi = INV ? -w.y : w.y;
           const long long ar = z1r << 1, ai = z1i << 1;
           const long long ac = __mul64hi(ar, w.x), bd = __mul64hi(ai, wi);
@@ -478,31 +615,25 @@ __global__ void __launch_bounds__(kThreads, 1)
           const long long Ya[4] = {z0r + tr, z0i + ti, z0r - tr, z0i - ti};
           double o[4];
 #pragma unroll
-          for (int n = 0; n < 4; ++n) {
-            const double yd = __ll2double_rn(Ya[n]);
-            o[n] = wide_range ? yd * scale2
-                              : (Ya[n] ? __longlong_as_double(__double_as_longlong(yd) + ((long long)(Et - 55) << 52))
-                                       : 0.0);
+          for (int n = 0; n < 4; ++n) o[n] = wide_range ? __ll2double_rn(Ya[n]) * scale2 : ll2double_fp(Ya[n], Et - 55);
+          if (wt.valid) {
+            y[(int64_t)r << lgs] = make_double2(o[0], o[1]);
+            y[(int64_t)(r + 32) << lgs] = make_double2(o[2], o[3]);
           }
-          y[(int64_t)r << lgs] = make_double2(o[0], o[1]);
-          y[(int64_t)(r + 32) << lgs] = make_double2(o[2], o[3]);
           continue;
         }
-        double o[4];
+        double o[NR];
         if (!wide_range) {
 #pragma unroll
-          for (int n = 0; n < 4; ++n) {
-            const double yd = __ll2double_rn(Ys[n]);  // one rounding; Y = 0 stays 0
-            o[n] = Ys[n] ? __longlong_as_double(__double_as_longlong(yd) + ((long long)(Et - 55) << 52)) : 0.0;
-          }
+          for (int n = 0; n < NR; ++n) o[n] = ll2double_fp(Ys[n], Et - 55);
         } else {
 #pragma unroll
-          for (int n = 0; n < 4; ++n) o[n] = __ll2double_rn(Ys[n]) * scale2;
+          for (int n = 0; n < NR; ++n) o[n] = __ll2double_rn(Ys[n]) * scale2;
         }
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const int r = 8 * qd + 2 * c4 + u;  // output r: reals 2r, 2r + 1
-          y[(int64_t)r << lgs] = make_double2(o[2 * u], o[2 * u + 1]);
+        for (int u = 0; u < NR / 2; ++u) {
+          const int r = 8 * qd + (NR / 2) * c4 + u;  // output r: reals 2r, 2r + 1
+          if (wt.valid) y[(int64_t)r << lgs] = make_double2(o[2 * u], o[2 * u + 1]);
         }
       }
       // the next tile's digits to the tensor cores' view
@@ -513,13 +644,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     stop = __syncthreads_or(fail ? 1 : 0) != 0;
     if (stop) break;
     phase ^= 1u;
+    if (newp) bsel ^= 1;
   }
   // teardown: a failed wait may leave a copy or the products in flight; wait for them (bounded)
   // before the TMEM is freed
   if (stop) {
     if (tid == 0) atomicOr(err, 1u);
     const long long t1 = clock64();
-    bar_wait(bar_b, 0, t1);
+    if (MODE != kByGroup) bar_wait(bar_b, 0, t1);
     bar_wait(bar_m, phase, t1);
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -575,39 +707,39 @@ void launch_twiddles_q62(const double2* tw, longlong2* twq, int64_t n, cudaStrea
 void launch_pass_tc(bool inverse, int logR, const double2* src, double2* dst, int logF, int logS, int ncols,
                     const longlong2* twq, const double2* hmul, int64_t nseg, const FftGen& gen, const void* bdig,
                     unsigned* err, cudaStream_t st) {
-  const int64_t ntiles = ((int64_t)ncols << logF) >> 12;  // 4096 points per tile
-  if (ntiles <= 0) return;
-  static bool configured[4] = {false, false, false, false};
-  const int k = (inverse ? 1 : 0) + (logR == 6 ? 2 : 0);
-  if (!configured[k]) {
-    if (k == 0) cudaFuncSetAttribute(k_fft_pass_tc<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmTotal);
-    if (k == 1) cudaFuncSetAttribute(k_fft_pass_tc<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmTotal);
-    if (k == 2) cudaFuncSetAttribute(k_fft_pass_tc<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmTotal);
-    if (k == 3) cudaFuncSetAttribute(k_fft_pass_tc<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmTotal);
-    configured[k] = true;
-  }
+  if (ncols <= 0) return;
+  using Kern = void (*)(const double2*, double2*, int, int, int64_t, int64_t, const longlong2*, const double2*,
+                        int64_t, FftGen, const void*, unsigned*);
+  static const Kern kern[12] = {
+      k_fft_pass_tc<false, false, kNoTwiddle>, k_fft_pass_tc<true, false, kNoTwiddle>,
+      k_fft_pass_tc<false, true, kNoTwiddle>,  k_fft_pass_tc<true, true, kNoTwiddle>,
+      k_fft_pass_tc<false, false, kByColumn>,  k_fft_pass_tc<true, false, kByColumn>,
+      k_fft_pass_tc<false, true, kByColumn>,   k_fft_pass_tc<true, true, kByColumn>,
+      k_fft_pass_tc<false, false, kByGroup>,   k_fft_pass_tc<true, false, kByGroup>,
+      k_fft_pass_tc<false, true, kByGroup>,    k_fft_pass_tc<true, true, kByGroup>};
+  // the tiling: the first pass of a transform (stride F / R) has no twiddles; the others go by
+  // twiddle group when its tiles are at least 7/8 full and a row's outputs come in runs of at
+  // least 32 bytes (s >= 2; at s = 1 the rows of a group tile write 16 bytes to each of 64 or 128
+  // columns), else by columns
+  const int LT = logR == 6 ? 6 : 7;
+  const int logP = logF - logR - logS;
+  const int64_t nu = (int64_t)ncols << logS, ublocks = (nu + (int64_t(1) << LT) - 1) >> LT;
+  int mode = kNoTwiddle;
+  if (logP > 0) mode = logS >= 1 && (ublocks << LT) - nu <= (ublocks << LT) / 8 ? kByGroup : kByColumn;
+  const int64_t ntiles = mode == kByColumn ? (((int64_t)ncols << logF) >> 12) : (ublocks << logP);  // (below 2^31: a tile is 4096 points of 16 bytes, far more than any device holds)
+  const int k = (inverse ? 1 : 0) + (logR == 6 ? 2 : 0) + 4 * mode;
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const unsigned grid = (unsigned)std::min<int64_t>(ntiles, sms);
-  switch (k) {
-    case 0:
-      k_fft_pass_tc<false, false><<<grid, kThreads, kSmTotal, st>>>(src, dst, logF, logS, ntiles, twq, hmul, nseg, gen,
-                                                                    bdig, err);
-      break;
-    case 1:
-      k_fft_pass_tc<true, false><<<grid, kThreads, kSmTotal, st>>>(src, dst, logF, logS, ntiles, twq, hmul, nseg, gen,
-                                                                   bdig, err);
-      break;
-    case 2:
-      k_fft_pass_tc<false, true><<<grid, kThreads, kSmTotal, st>>>(src, dst, logF, logS, ntiles, twq, hmul, nseg, gen,
-                                                                   bdig, err);
-      break;
-    default:
-      k_fft_pass_tc<true, true><<<grid, kThreads, kSmTotal, st>>>(src, dst, logF, logS, ntiles, twq, hmul, nseg, gen,
-                                                                  bdig, err);
-      break;
+  // the shared-memory opt-in, once per device and kernel
+  static std::atomic<unsigned> configured[64];
+  const unsigned bit = 1u << k;
+  if (dev >= 64 || !(configured[dev].load(std::memory_order_relaxed) & bit)) {
+    cudaFuncSetAttribute(kern[k], cudaFuncAttributeMaxDynamicSharedMemorySize, kSmTotal);
+    if (dev < 64) configured[dev].fetch_or(bit, std::memory_order_relaxed);
   }
+  const unsigned grid = (unsigned)std::min<int64_t>(ntiles, sms);
+  kern[k]<<<grid, kThreads, kSmTotal, st>>>(src, dst, logF, logS, ncols, ntiles, twq, hmul, nseg, gen, bdig, err);
 }
 
 }  // namespace hk
