@@ -36,12 +36,12 @@ FP64_PEAK_GFLOPS = 152 * 4 * 2.07  # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GH
 HBM_FALLBACK_GBS = 6800.0          # used only when MEASURED_PEAKS.json is absent
 FP64_MEASURED_GFLOPS = 1004.0      # DFMA microbenchmark on this part (2 x 502 G instructions/s)
 # DRAM bytes per algorithmic byte of an FFT pass launch of FP64 transforms, from an ncu capture of
-# one radix-32 pass on the tensor cores over 8 x 2^20 points (k_fft_pass_tc<0, 0>): 136.8 + 85.1 MB
-# of DRAM reads + writes against 268.4 MB algorithmic (part of the writes still in L2 at the end).
-FFT_TRAFFIC_RATIO = (136.813 + 85.120) / 268.435
-# Executed fp16 MMA flops per complex point of a tensor-core radix-32 pass: 34 digit pairs, 4 K
-# steps of 128 x 64 x 16 per tile of 4096 points (plus one 128 x 64 x 16 clear).
-TC_MMA_FLOPS_PER_POINT = (2 * 128 * 16 * 64 * (34 * 4 + 1)) / 4096.0
+# three passes on the tensor cores over 16 x 2^21 points (two radix-32 passes by twiddle group, one
+# stride-1 radix-64 pass): 3328.8 MB of DRAM reads + writes against 3 x 1073.7 MB algorithmic.
+FFT_TRAFFIC_RATIO = (537.629 + 494.579 + 563.824 + 496.177 + 731.730 + 504.892) / (3 * 1073.742)
+# Executed fp16 MMA flops per complex point of a tensor-core radix-32 pass: 34 digit-plane products
+# of 128 x 64 x 16 in each of 4 K steps per tile of 4096 points.
+TC_MMA_FLOPS_PER_POINT = (2 * 128 * 16 * 64 * 34 * 4) / 4096.0
 # The double-float transforms are bound by the FP32 pipe: 152 SMs x 128 lanes x 2.07 GHz =
 # 40.3 T instructions/s. Their radix-2 butterfly (two double-float dot products of 16 FP32
 # instructions each, four sums of 8) takes 64 FP32 instructions for the 10 flops of the
