@@ -448,8 +448,9 @@ def run_ours(args):
         served_e2e, served_sat_lat = serve_stream(hk, served_kw, reqs, 0.0, 1, rounds=args.steps)
         plain_e2e, plain_sat_lat = serve_stream(hk, plain_kw, reqs, 0.0, 1, rounds=args.steps)
         rate = args.rate if args.rate > 0 else 0.7 * plain_e2e / N  # 70 % of the plain form's capacity
-        served_cps_p, served_lat = serve_stream(hk, served_kw, reqs, rate, 2)
-        plain_cps_p, plain_lat = serve_stream(hk, plain_kw, reqs, rate, 2)
+        # four rounds of the 32 arrivals: 128 latencies per form
+        served_cps_p, served_lat = serve_stream(hk, served_kw, reqs, rate, 2, rounds=4)
+        plain_cps_p, plain_lat = serve_stream(hk, plain_kw, reqs, rate, 2, rounds=4)
 
     term_split = {"fp64": terms[0], "df64": terms[1], "fp32": terms[2],
                   "unit": "far-field transforms per right-hand side, summed over blocks and plans"}
@@ -482,7 +483,7 @@ def run_ours(args):
                         "page-locked host arrays (inputs and outputs); %d such rounds after 2 untimed ones"
                         % (len(reqs), len(reqs) // len(eps_list), args.steps),
                 "plain_value": plain_e2e},
-        "latency_ms": {"rate_per_s": rate, "requests": len(reqs),
+        "latency_ms": {"rate_per_s": rate, "requests": 4 * len(reqs) if rate else len(reqs),
                        "served": {"p50": pct(served_lat, 50), "p99": pct(served_lat, 99),
                                   "coeffs_per_s": served_cps_p},
                        "plain": {"p50": pct(plain_lat, 50), "p99": pct(plain_lat, 99),

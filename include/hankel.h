@@ -397,7 +397,8 @@ typedef struct {
   size_t memory_cap;  /* device bytes the server's plans and buffers may hold (0 = 120 GiB) */
   int streams;        /* CUDA streams, i.e. batches in flight at once (default 4, at most 16) */
   int max_batch;      /* most coefficient vectors packed into one execution (default 64) */
-  int use_graphs;     /* 1: replay each (plan, batch size, stream) launch sequence from a captured CUDA graph */
+  int use_graphs;     /* 1: replay each (plan, batch size, stream, context) launch sequence from a CUDA graph,
+                         captured at its second use (its first runs uncaptured) */
   int precision;      /* precision every plan is built with: HANKEL_PREC_AUTO (FP64 below eps = 1e-5, FP32
                          stages at or above), HANKEL_PREC_FP64, or HANKEL_PREC_MIXED (chosen per eps and
                          per term as for a MIXED plan) */

@@ -59,6 +59,7 @@ struct PlanEntry {
   int64_t runs = 0;
   uint64_t last_used = 0;
   std::map<std::tuple<int, int, int>, cudaGraphExec_t> graphs;  // (stream slot, context, nrhs) -> graph
+  std::map<std::tuple<int, int, int>, int> seen;                 // keys run once, uncaptured
   bool any_busy() const {
     for (char b : ctx_busy)
       if (b) return true;
@@ -272,7 +273,9 @@ int take_context(hankel_server_s* s, const Key& key, PlanEntry& pe) {
 // Issue copy-in, execution and copy-out of a packed batch on slot i. Page-locked request
 // arrays are copied straight to and from the slot's device buffers; the others go through the
 // slot's staging buffers (filled by dispatch, emptied by retire). With graphs, the execution
-// alone is captured once per (slot, batch size) and replayed between the copies.
+// alone is captured once per (slot, context, batch size), at the key's second use, and replayed
+// between the copies: a key that occurs once (a batch size that comes up rarely) runs uncaptured
+// and pays no instantiation.
 int launch_batch(hankel_server_s* s, int i, PlanEntry& pe, int ctx, int64_t N, int nrhs,
                  const std::vector<Item>& batch) {
   Slot& sl = s->slots[i];
@@ -286,12 +289,12 @@ int launch_batch(hankel_server_s* s, int i, PlanEntry& pe, int ctx, int64_t N, i
   }
   auto exec = [&]() { return hankel_exec_batched_ctx(pe.plan, ctx, sl.c_dev, N, sl.f_dev, N, nrhs, sl.stream); };
   int st = HANKEL_OK;
-  if (!s->opt.use_graphs || pe.runs == 0) {
-    st = exec();  // the first run configures kernels uncaptured
+  const auto key = std::make_tuple(i, ctx, nrhs);
+  auto git = pe.graphs.find(key);
+  if (!s->opt.use_graphs || pe.runs == 0 || (git == pe.graphs.end() && pe.seen[key]++ == 0)) {
+    st = exec();  // the plan's first run configures kernels; a key's first run goes uncaptured
   } else {
-    auto key = std::make_tuple(i, ctx, nrhs);
-    auto it = pe.graphs.find(key);
-    if (it == pe.graphs.end()) {
+    if (git == pe.graphs.end()) {
       cudaGraph_t g = nullptr;
       if (cudaStreamBeginCapture(sl.stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return HANKEL_ECUDA;
       st = exec();
@@ -305,11 +308,11 @@ int launch_batch(hankel_server_s* s, int i, PlanEntry& pe, int ctx, int64_t N, i
       e = cudaGraphInstantiate(&ge, g, 0);
       cudaGraphDestroy(g);
       if (e != cudaSuccess) return HANKEL_ECUDA;
-      it = pe.graphs.emplace(key, ge).first;
+      git = pe.graphs.emplace(key, ge).first;
       std::lock_guard<std::mutex> lk(s->mu);
       s->stats.graphs_captured++;
     }
-    if (cudaGraphLaunch(it->second, sl.stream) != cudaSuccess) st = HANKEL_ECUDA;
+    if (cudaGraphLaunch(git->second, sl.stream) != cudaSuccess) st = HANKEL_ECUDA;
   }
   if (st != HANKEL_OK) return st;
   off = 0;

@@ -43,8 +43,6 @@ def test_mixed_stream_matches_alone(graphs):
     st = srv.stats()
     assert st["completed"] == len(reqs) and st["failed"] == 0
     assert st["batches"] < len(reqs)  # requests of one plan were packed together
-    if graphs:
-        assert st["graphs_captured"] > 0
     for (task, nu, N, eps, c), (_, f) in zip(reqs, tickets):
         ref = _alone(task, nu, N, eps, c)
         bound = 10 * eps * np.abs(c).sum(axis=1, keepdims=True)
@@ -53,15 +51,18 @@ def test_mixed_stream_matches_alone(graphs):
 
 
 def test_repeat_submissions_with_graphs_are_stable():
+    # the plan's first run and a (slot, context, batch size)'s first run go uncaptured; the key's
+    # second run is captured and later ones replay: every result is the same
     c = coefficients("normal", 4096, 2, 77)
-    srv = hk.Server(streams=2, max_batch=2, use_graphs=True)
+    srv = hk.Server(streams=1, max_batch=2, use_graphs=True)
     outs = []
-    for _ in range(4):
+    for _ in range(5):
         t, f = srv.submit("dht", 0, 4096, 1e-8, c)
         srv.wait(t)
         outs.append(f.copy())
     for f in outs[1:]:
         assert np.array_equal(f, outs[0])
+    assert srv.stats()["graphs_captured"] == 1
     srv.close()
 
 
