@@ -122,7 +122,8 @@ enum hankel_status {
 /* Options for hankel_plan_ex(). Fill with hankel_options_default() first. */
 typedef struct {
   int task;               /* enum hankel_task */
-  int nu;                 /* order of J; >= 0; must be 0 for HANKEL_DHT */
+  int nu;                 /* order of J; >= 0; must be 0 for HANKEL_DHT (Section 6 builds the order-0
+                             DHT on the nodes j_{0,n}; other orders are refused with EINVAL) */
   int64_t N;              /* number of coefficients and of outputs; 2 <= N <= 2^24 */
   double eps;             /* working accuracy, 1e-16 <= eps < 1 */
   int grid;               /* enum hankel_grid (tasks 0 and 1 only) */
