@@ -465,21 +465,30 @@ void build_nodes(HostPlan& hp) {
 // few). Pick the length with the fewest estimated FP64 operations per column:
 // about 3.6 per point and radix-2 stage of each FFT plus 4 per point and segment
 // for the spectrum products.
-constexpr double kStageOps = 3.6, kMacOps = 4.0;
+// In an FP64 plan, transforms of 2^12 points or more run their passes on the tensor cores, at about
+// 0.56 of the FP64 pipe's time per point (the autotuned splits against the built-in ones at 2^12,
+// 2^18 and 2^21 points); their stages are costed at that fraction.
+constexpr double kStageOps = 3.6, kMacOps = 4.0, kTensorStageFrac = 0.56;
 
-double full_column_cost(const Block& b) { return 2.0 * b.F * b.logF * kStageOps + kMacOps * b.F; }
+double stage_ops(const HostPlan& hp, int logF) {
+  return (!hp.fp32 && !hp.df64 && logF >= 12) ? kStageOps * kTensorStageFrac : kStageOps;
+}
 
-void choose_segments(Block& b) {
+double full_column_cost(const HostPlan& hp, const Block& b) {
+  return 2.0 * b.F * b.logF * stage_ops(hp, b.logF) + kMacOps * b.F;
+}
+
+void choose_segments(const HostPlan& hp, Block& b) {
   const int64_t thin = std::min(b.R, b.C), wide = std::max(b.R, b.C);
-  const double kStage = kStageOps, kMac = kMacOps;
-  double best = full_column_cost(b);
+  const double kMac = kMacOps;
+  double best = full_column_cost(hp, b);
   const int lfull = b.logF;  // b.logF changes when a shorter length wins
   for (int lf = 6; lf < lfull; ++lf) {
     const int64_t Fs = int64_t(1) << lf;
     if (Fs < 2 * thin) continue;
     const int64_t S = Fs - thin + 1;
     const int64_t nseg = (wide + S - 1) / S;
-    const double cost = (double)(nseg + 1) * Fs * lf * kStage + kMac * (double)nseg * Fs;
+    const double cost = (double)(nseg + 1) * Fs * lf * stage_ops(hp, lf) + kMac * (double)nseg * Fs;
     if (cost < best) {
       best = cost;
       b.mode = (b.R <= b.C) ? kBlockRowSeg : kBlockColSeg;
@@ -492,9 +501,9 @@ void choose_segments(Block& b) {
 }
 
 // Estimated FP64 operations per stacked column of a block (the model of choose_segments).
-double column_cost(const Block& b) {
-  if (b.mode == kBlockFull) return full_column_cost(b);
-  return (double)(b.nseg + 1) * b.F * b.logF * kStageOps + kMacOps * (double)b.nseg * b.F;
+double column_cost(const HostPlan& hp, const Block& b) {
+  if (b.mode == kBlockFull) return full_column_cost(hp, b);
+  return (double)(b.nseg + 1) * b.F * b.logF * stage_ops(hp, b.logF) + kMacOps * (double)b.nseg * b.F;
 }
 
 // A far block on rows k0..k1 and columns n0..n1 with its transform length and segmenting.
@@ -510,7 +519,7 @@ Block make_block(const HostPlan& hp, int64_t k0, int64_t k1, int64_t n0, int64_t
   b.mode = kBlockFull;
   b.S = b.C;
   b.nseg = 1;
-  if (!(hp.opt.flags & HANKEL_FLAG_NO_SEGMENT)) choose_segments(b);
+  if (!(hp.opt.flags & HANKEL_FLAG_NO_SEGMENT)) choose_segments(hp, b);
   return b;
 }
 
@@ -951,7 +960,7 @@ constexpr int64_t kMinSide = 64;
 double block_work(const HostPlan& hp, const Block& b) {
   const bool lowrank = !(hp.opt.flags & (HANKEL_FLAG_NO_LOWRANK | HANKEL_FLAG_ALL_COLUMNS));
   const int terms = lowrank ? estimate_rank(hp, b) : (int)b.lcols.size();
-  return (double)terms * column_cost(b) + kBlockLaunchOps / hp.opt.max_nrhs;
+  return (double)terms * column_cost(hp, b) + kBlockLaunchOps / hp.opt.max_nrhs;
 }
 
 void refine(const HostPlan& hp, const NodeRanges& nr, Block b, double budget, int depth, std::vector<Block>& out) {
