@@ -332,13 +332,13 @@ std::vector<FftShape> shape_candidates(int logF, int ncols, int prec, bool tc) {
         return;
     if (out.size() < 40 && valid_fft_shape(sh, logF)) out.push_back(sh);
   };
-  // FP64 transforms of 2^12 points and more: also the variant with every radix-32 pass on the
-  // tensor cores
+  // FP64 transforms: also the variant with every radix-32 and radix-64 pass on the tensor cores
+  // (below 2^12 points, the first pass only)
   auto add = [&](FftShape sh) {
     add1(sh);
-    if (tc && prec == kTermFP64 && !sh.one_launch && logF >= 12) {
+    if (tc && prec == kTermFP64 && !sh.one_launch) {
       int m = 0;
-      for (int i = 0; i < sh.npass; ++i)
+      for (int i = 0; i < sh.npass && (logF >= 12 || i == 0); ++i)
         if (sh.logr[i] == 5 || sh.logr[i] == 6) m |= 1 << i;
       if (m) {
         sh.tc = m;

@@ -656,8 +656,9 @@ bool valid_fft_shape(const FftShape& sh, int logF) {
   int sum = 0;
   for (int i = 0; i < sh.npass; ++i) {
     if (sh.logr[i] < 5 || sh.logr[i] > 8) return false;
-    // a tensor-core pass has radix 32 or 64 and tiles of 4096 points within a column
-    if (((sh.tc >> i) & 1) && ((sh.logr[i] != 5 && sh.logr[i] != 6) || logF < 12)) return false;
+    // a tensor-core pass has radix 32 or 64; below 4096 points only the first pass (no twiddles,
+    // its tiles span columns) runs there
+    if (((sh.tc >> i) & 1) && ((sh.logr[i] != 5 && sh.logr[i] != 6) || (logF < 12 && i > 0))) return false;
     sum += sh.logr[i];
   }
   return sum == logF;

@@ -482,6 +482,10 @@ def test_autotuned_shapes_are_recorded_and_exact():
     (15, 8, [5, 5, 5], 0b111), (17, 4, [5, 6, 6], 0b111), (18, 8, [6, 6, 6], 0b101),
     (20, 8, [5, 5, 5, 5], 0b1111), (21, 16, [5, 5, 5, 6], 0b1111), (21, 4, [6, 5, 5, 5], 0b1110),
     (22, 2, [5, 5, 5, 7], 0b0111), (22, 2, [5, 5, 6, 6], 0b1111),
+    # a first pass on the tensor cores below 4096 points (tiles spanning columns, the last one ragged)
+    (10, 3, [5, 5], 0b01), (10, 16, [5, 5], 0b01), (11, 5, [6, 5], 0b01), (11, 8, [5, 6], 0b01),
+    # a pass tiled by twiddle group whose last tile is ragged (15 columns x 64 sequences)
+    (16, 15, [5, 5, 6], 0b111),
 ])
 @pytest.mark.parametrize("inverse", [False, True])
 def test_tensor_core_fft_passes(logF, ncols, radices, tc, inverse):
