@@ -465,13 +465,24 @@ void build_nodes(HostPlan& hp) {
 // few). Pick the length with the fewest estimated FP64 operations per column:
 // about 3.6 per point and radix-2 stage of each FFT plus 4 per point and segment
 // for the spectrum products.
-// In an FP64 plan, transforms of 2^12 points or more run their passes on the tensor cores, at about
+// In an FP64 plan, the radix-32 and radix-64 passes of a transform run on the tensor cores, at about
 // 0.56 of the FP64 pipe's time per point (the autotuned splits against the built-in ones at 2^12,
-// 2^18 and 2^21 points); their stages are costed at that fraction.
+// 2^18 and 2^21 points). A length's stages are costed by the share of its bits those radices can
+// take in a split of 2-4 passes of radix 2^5..2^8 (below 2^12 points, the first pass only):
+// 2^13 and 2^14 keep a radix-128 or radix-256 pass on the FP64 pipe, 2^19 one of radix 128.
 constexpr double kStageOps = 3.6, kMacOps = 4.0, kTensorStageFrac = 0.56;
 
+int tensor_bits(int logF) {
+  if (logF < 10) return 0;
+  if (logF < 12) return logF == 10 ? 5 : 6;
+  if (logF == 13 || logF == 14) return 6;
+  if (logF == 19) return 12;
+  return logF;
+}
+
 double stage_ops(const HostPlan& hp, int logF) {
-  return (!hp.fp32 && !hp.df64 && logF >= 12) ? kStageOps * kTensorStageFrac : kStageOps;
+  if (hp.fp32 || hp.df64) return kStageOps;
+  return kStageOps * (1.0 - (1.0 - kTensorStageFrac) * tensor_bits(logF) / (double)logF);
 }
 
 double full_column_cost(const HostPlan& hp, const Block& b) {
