@@ -439,7 +439,10 @@ def run_ours(args):
     for i in range(nreq):
         e = eps_list[i % len(eps_list)]
         reqs.append((e, pinned_like(coefficients("normal", N, 1, seed_for(4, 200 + i))[0])))
-    served_kw = dict(streams=4, max_batch=B, use_graphs=True, precision="auto")
+    # batches of at most 2 vectors (spread-out arrivals) run on plans built for 2; one batch of a plan
+    # at a time (the requests of this stream all share two plans: a second context would run a
+    # plan's batches side by side, each slower, where in turn and packed they finish sooner)
+    served_kw = dict(streams=4, max_batch=B, use_graphs=True, precision="auto", small_batch=2, contexts_per_plan=1)
     plain_kw = dict(streams=1, max_batch=1, use_graphs=False, precision="fp64", pack=False)
     if args.quick:
         served_e2e = plain_e2e = served_cps_p = plain_cps_p = rate = None

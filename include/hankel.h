@@ -410,6 +410,9 @@ typedef struct {
   int contexts_per_plan; /* batches of one plan in flight at once, each on an execution context of its own
                             (hankel_plan_add_context; made when needed and the memory cap allows; default
                             2, 1..8) */
+  int small_batch;       /* 1..max_batch - 1: a batch of at most this many vectors runs on a second plan of
+                            its (task, nu, N, eps), built for that many (a plan built for max_batch runs one
+                            vector about 15 % slower); 0 (default): one plan per (task, nu, N, eps) */
 } hankel_server_options;
 
 /* Statistics since the server was created. */

@@ -299,7 +299,7 @@ class Server:
     """
 
     def __init__(self, streams=4, max_batch=64, use_graphs=False, precision="auto", memory_cap=0, pack=True,
-                 batch_window_us=None, contexts_per_plan=None):
+                 batch_window_us=None, contexts_per_plan=None, small_batch=None):
         self._lib = _lib.load()
         o = _lib.ServerOptions()
         _lib.check(self._lib.hankel_server_options_default(ctypes.byref(o)), "hankel_server_options_default")
@@ -310,6 +310,8 @@ class Server:
             o.batch_window_us = int(batch_window_us)
         if contexts_per_plan is not None:
             o.contexts_per_plan = int(contexts_per_plan)
+        if small_batch is not None:
+            o.small_batch = int(small_batch)
         if memory_cap:
             o.memory_cap = int(memory_cap)
         self._h = ctypes.c_void_p()

@@ -80,7 +80,8 @@ class StageStat(ctypes.Structure):
 class ServerOptions(ctypes.Structure):
     _fields_ = [("memory_cap", ctypes.c_size_t), ("streams", ctypes.c_int), ("max_batch", ctypes.c_int),
                 ("use_graphs", ctypes.c_int), ("precision", ctypes.c_int), ("pack_requests", ctypes.c_int),
-                ("batch_window_us", ctypes.c_int), ("contexts_per_plan", ctypes.c_int)]
+                ("batch_window_us", ctypes.c_int), ("contexts_per_plan", ctypes.c_int),
+                ("small_batch", ctypes.c_int)]
 
 
 class ServerStats(ctypes.Structure):

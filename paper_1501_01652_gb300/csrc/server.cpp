@@ -34,7 +34,10 @@ bool alloc_fault();  // api.cpp: hankel_debug_fail_allocs
 namespace {
 
 typedef std::chrono::steady_clock Clock;
-typedef std::tuple<int, int, int64_t, double> Key;  // task, nu, N, eps
+typedef std::tuple<int, int, int64_t, double> Key;        // task, nu, N, eps
+typedef std::tuple<int, int, int64_t, double, int> PKey;  // Key and the plan class (0: small batches)
+
+PKey plan_key(const Key& k, int cls) { return PKey(std::get<0>(k), std::get<1>(k), std::get<2>(k), std::get<3>(k), cls); }
 
 constexpr size_t kDefaultCap = size_t(120) << 30;
 constexpr size_t kPlanWorkspace = size_t(1) << 30;
@@ -92,7 +95,7 @@ struct Slot {
   size_t pin_cap = 0;  // doubles in each staging buffer (allocated only for pageable requests)
   bool busy = false;
   std::vector<Item> items;
-  Key key;
+  PKey key;
   int ctx = 0;  // the plan's execution context the batch runs on
   int64_t N = 0;
 };
@@ -111,13 +114,17 @@ struct hankel_server_s {
   bool stop = false;
   hankel_server_stats stats{};
   // dispatcher-owned
-  std::map<Key, PlanEntry> plans;
+  std::map<PKey, PlanEntry> plans;
   std::vector<Slot> slots;
   uint64_t tick = 0;
   size_t plan_bytes = 0, slot_bytes = 0;
 };
 
 namespace {
+
+// The class of plan a batch of nrhs vectors runs on: 0 (built for small_batch vectors) when it
+// has at most that many and the option is on, else 1 (built for max_batch).
+int plan_class(const hankel_server_s* s, int nrhs) { return s->opt.small_batch > 0 && nrhs <= s->opt.small_batch ? 0 : 1; }
 
 void drop_slot_graphs(hankel_server_s* s, int slot) {
   for (auto& kv : s->plans) {
@@ -191,12 +198,12 @@ void destroy_plan(hankel_server_s* s, PlanEntry& pe) {
 }
 
 // Cached plan for key, built on a miss; idle plans are evicted (LRU) while over the cap.
-int get_plan(hankel_server_s* s, const Key& key, PlanEntry** out) {
+int get_plan(hankel_server_s* s, const PKey& key, PlanEntry** out) {
   auto it = s->plans.find(key);
   if (it == s->plans.end()) {
     hankel_options o;
     hankel_options_default(&o, std::get<0>(key), std::get<1>(key), std::get<2>(key), std::get<3>(key));
-    o.max_nrhs = s->opt.max_batch;
+    o.max_nrhs = std::get<4>(key) == 0 ? s->opt.small_batch : s->opt.max_batch;
     o.precision = s->opt.precision;
     o.workspace_limit = kPlanWorkspace;
     hankel_plan_t p = nullptr;
@@ -235,7 +242,7 @@ int get_plan(hankel_server_s* s, const Key& key, PlanEntry** out) {
 // An idle execution context of pe: an existing one, or a new one while the plan has fewer than
 // contexts_per_plan and the device memory cap allows it (idle plans are evicted to make room).
 // Returns -1 when every context is busy and no other can be made now.
-int take_context(hankel_server_s* s, const Key& key, PlanEntry& pe) {
+int take_context(hankel_server_s* s, const PKey& key, PlanEntry& pe) {
   int k = pe.idle_ctx();
   if (k >= 0) return k;
   if ((int)pe.ctx_busy.size() >= std::min(s->opt.contexts_per_plan, pe.ctx_limit)) return -1;
@@ -379,23 +386,23 @@ bool dispatch(hankel_server_s* s, int i) {
   {
     std::lock_guard<std::mutex> lk(s->mu);
     // a plan is busy when every context it has or may still get carries a batch
-    auto busy = [&](const Key& k) {
+    auto busy = [&](const PKey& k) {
       auto it = s->plans.find(k);
       return it != s->plans.end() && it->second.idle_ctx() < 0 &&
              (int)it->second.ctx_busy.size() >= std::min(s->opt.contexts_per_plan, it->second.ctx_limit);
     };
     // the oldest queued request whose plan is idle and whose batch is ready: full, packing off,
     // no request of the plan arrived within the batch window (a burst of submissions stays one
-    // batch), or its oldest request has waited ten windows
+    // batch), or its oldest request has waited ten windows. The plan is the one of the class the
+    // batch would take (its vectors so far; the batch formed below settles it)
     const Clock::time_point now = Clock::now();
     const auto window = std::chrono::microseconds(std::max(0, s->opt.batch_window_us));
     std::vector<Key> seen;
     auto q = s->queue.begin();
     for (; q != s->queue.end(); ++q) {
       const Request& r0 = s->reqs[*q];
-      if (busy(r0.key) || std::find(seen.begin(), seen.end(), r0.key) != seen.end()) continue;
+      if (std::find(seen.begin(), seen.end(), r0.key) != seen.end()) continue;
       seen.push_back(r0.key);
-      if (!s->opt.pack_requests) break;
       int queued = 0;
       Clock::time_point newest = r0.t_submit;
       for (int64_t t : s->queue)
@@ -403,6 +410,9 @@ bool dispatch(hankel_server_s* s, int i) {
           queued += s->reqs[t].nrhs;
           newest = std::max(newest, s->reqs[t].t_submit);
         }
+      if (!s->opt.pack_requests) queued = r0.nrhs;
+      if (busy(plan_key(r0.key, plan_class(s, std::min(queued, s->opt.max_batch))))) continue;
+      if (!s->opt.pack_requests) break;
       if (queued >= s->opt.max_batch || now - newest >= window || now - r0.t_submit >= 10 * window) break;
     }
     if (q == s->queue.end()) return false;
@@ -418,14 +428,15 @@ bool dispatch(hankel_server_s* s, int i) {
       }
     }
   }
+  const PKey pkey = plan_key(key, plan_class(s, nrhs));
   PlanEntry* pe = nullptr;
-  int st = get_plan(s, key, &pe);
+  int st = get_plan(s, pkey, &pe);
   const int64_t N = std::get<2>(key);
   bool staging = false;
   for (const Item& it : batch) staging = staging || !it.c_pinned || !it.f_pinned;
   int ctx = -1;
   if (st == HANKEL_OK) {
-    ctx = take_context(s, key, *pe);
+    ctx = take_context(s, pkey, *pe);
     if (ctx < 0) {
       // no context can be had now (memory): put the batch back at the front of the queue; it
       // is dispatched once a batch of this plan retires
@@ -457,7 +468,7 @@ bool dispatch(hankel_server_s* s, int i) {
   pe->runs++;
   sl.busy = true;
   sl.items = batch;
-  sl.key = key;
+  sl.key = pkey;
   sl.ctx = ctx;
   sl.N = N;
   std::lock_guard<std::mutex> lk(s->mu);
@@ -502,6 +513,7 @@ int hankel_server_options_default(hankel_server_options* o) {
   o->pack_requests = 1;
   o->batch_window_us = 200;
   o->contexts_per_plan = 2;
+  o->small_batch = 0;
   return HANKEL_OK;
 }
 
@@ -514,6 +526,7 @@ int hankel_server_create(hankel_server_t* out, const hankel_server_options* o) {
   if (opt.memory_cap == 0) opt.memory_cap = kDefaultCap;
   if (opt.streams < 1 || opt.streams > 16 || opt.max_batch < 1 || opt.batch_window_us < 0) return HANKEL_EINVAL;
   if (opt.contexts_per_plan < 1 || opt.contexts_per_plan > 8) return HANKEL_EINVAL;
+  if (opt.small_batch < 0 || opt.small_batch >= opt.max_batch) opt.small_batch = 0;  // one plan per key
   if (opt.precision != HANKEL_PREC_AUTO && opt.precision != HANKEL_PREC_FP64 && opt.precision != HANKEL_PREC_MIXED)
     return HANKEL_EINVAL;
   hankel_server_s* s = new hankel_server_s();

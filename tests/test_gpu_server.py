@@ -266,3 +266,23 @@ def test_cancel_queued_requests():
     st = srv.stats()
     assert st["cancelled"] == sum(cancelled) and st["completed"] == 10 - sum(cancelled)
     srv.close()
+
+
+def test_small_batches_run_on_their_own_plan():
+    # with small_batch = 2, a lone request runs on a plan built for 2 vectors and a burst of 8
+    # on the plan built for max_batch: two plans for one (task, nu, N, eps), results within the bar
+    N, eps = 6000, 1e-15
+    cs = [coefficients("normal", N, 1, 4400 + i) for i in range(9)]
+    srv = hk.Server(streams=2, max_batch=8, use_graphs=True, small_batch=2, batch_window_us=5000)
+    t, f0 = srv.submit("dht", 0, N, eps, cs[0])
+    srv.wait(t)
+    burst = [srv.submit("dht", 0, N, eps, c) for c in cs[1:]]
+    for tk, _ in burst:
+        srv.wait(tk)
+    st = srv.stats()
+    assert st["plans_built"] == 2 and st["failed"] == 0
+    bound = lambda c: 10 * eps * np.abs(c).sum()
+    assert np.abs(f0 - _alone("dht", 0, N, eps, cs[0])).max() <= bound(cs[0])
+    for c, (_, f) in zip(cs[1:], burst):
+        assert np.abs(f - _alone("dht", 0, N, eps, c)).max() <= bound(c)
+    srv.close()
