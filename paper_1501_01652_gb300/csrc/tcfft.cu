@@ -149,10 +149,11 @@ struct GenSrc {
   int64_t lim;
 };
 __device__ __forceinline__ GenSrc gen_source(const FftGen& g, int64_t col) {
-  const int64_t cc = col / g.nsegc;
-  const int64_t sg = col - cc * g.nsegc;
-  const int64_t gi = g.c0 + cc;
-  const int64_t rhs = gi / g.ncols, li = gi - rhs * g.ncols;
+  // column and group indices are below 2^31: 32-bit divisions (a 64-bit one is a long sequence)
+  const uint32_t cc = (uint32_t)col / (uint32_t)g.nsegc;
+  const int64_t sg = col - (int64_t)cc * g.nsegc;
+  const uint32_t gi = (uint32_t)g.c0 + cc;
+  const uint32_t rhs = gi / (uint32_t)g.ncols, li = gi - rhs * (uint32_t)g.ncols;
   const int64_t nlo = sg * g.S;
   GenSrc r;
   r.c = reinterpret_cast<const double*>(g.coef) + rhs * g.ldc + g.n0 - 1 + nlo;
@@ -199,7 +200,7 @@ __device__ __forceinline__ void prefetch_inputs(double2 (&v)[8], const double2* 
       v[j].x = t < gs.lim ? __ldg(gs.c + t) : 0.0;
     }
   } else {
-    const double2* x = src + ((hmul ? w.c / nseg : w.c) << logF);
+    const double2* x = src + ((hmul ? (int64_t)((uint32_t)w.c / (uint32_t)nseg) : w.c) << logF);
 #pragma unroll
     for (int j = 0; j < 8; ++j) v[j] = x[w.ibase + ((uint32_t)(e0 + j * es) << logS)];
   }
@@ -219,7 +220,7 @@ __device__ __forceinline__ void finish_inputs(double2 (&v)[8], const double2* __
       v[j] = make_double2(c * tw.x, c * tw.y);
     }
   } else if (hmul) {
-    const double2* hc = hmul + ((w.c % nseg) << logF);
+    const double2* hc = hmul + ((int64_t)((uint32_t)w.c % (uint32_t)nseg) << logF);
 #pragma unroll
     for (int j = 0; j < 8; ++j) v[j] = cmul(v[j], __ldg(&hc[w.ibase + ((uint32_t)(e0 + j * es) << logS)]));
   }
@@ -407,7 +408,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int jrow = R64 ? (i >> 1) : i;       // the tile's sequence of this row
   const int par = R64 ? (i & 1) : 0;         // R64: even (0) or odd (1) elements
   const int e0 = R64 ? 16 * qd + par : 8 * qd, es = R64 ? 2 : 1;  // this thread's elements e0 + j es
-  const int logP = lgs - logS;               // log2 of the twiddle groups
   const int tpc_log = lgs - LT;              // by columns: log2 of the tiles per column
   const int64_t nu = ncols << logS;          // by twiddle group: the (c, q) pairs per group
   // CTA b takes tiles b, b + grid, ... (the CTAs stream through neighbouring tiles together), except
