@@ -14,8 +14,10 @@ typedef std::complex<double> cplx;
 // Largest number of Taylor powers u2 of the column perturbation b_n carried
 // by one stacked column (2T+K-2 of Section 5.1 at eps = 1e-16 is 10).
 constexpr int kMaxU = 16;
-// Near-field Bessel table: intervals of width 1 with Taylor polynomials of this degree.
-constexpr int kJTabLog = 4;                 // near-field J table: 2^kJTabLog Taylor intervals
+// Near-field Bessel table: 64 Taylor intervals per unit of z, so that degree 6 (eps = 1e-15) or 4
+// (1e-8) suffices; 128 would leave the double-float lookup, whose interval offset is formed in
+// float, short of its accuracy at z near 100.
+constexpr int kJTabLog = 6;                 // near-field J table: 2^kJTabLog Taylor intervals
 constexpr int kJTabSub = 1 << kJTabLog;     // per unit of z
 constexpr int kJTabDegMax = 10;  // largest Taylor degree of the near-field J table
 
