@@ -72,6 +72,8 @@ def parse_args():
     ap.add_argument("--mode", default="dht", choices=["dht", "mix"], help="mix: the serving-mix workload")
     ap.add_argument("--quick", action="store_true", help="batched form only (no plain form, serving runs or CPU leg)")
     ap.add_argument("--no-mixed", action="store_true", help="skip the opt-in mixed-precision batched form")
+    ap.add_argument("--fp32-eps", type=float, default=1e-4,
+                    help="tolerance of the FP32-stage batched form reported beside the value (0: skip)")
     ap.add_argument("--mix-requests", type=int, default=1000, help="requests per arrival rate")
     ap.add_argument("--mix-rates", default="100,1000,10000", help="Poisson arrivals per second, one run each")
     ap.add_argument("--mix-nmin", type=int, default=10)
@@ -431,6 +433,25 @@ def run_ours(args):
                  "form": "precision='mixed': narrower than FP64 below eps = 1e-5 by explicit opt-in"}
         for p in mplans:
             p.destroy()
+
+    # the default policy's FP32-stage class (eps >= 1e-5): one batched plan, its transforms against
+    # the measured HBM copy rate; reported beside the FP64 value, never as it
+    fp32 = None
+    if args.fp32_eps > 0:
+        p32 = [hk.Plan("dht", 0, N, args.fp32_eps, max_nrhs=B)]
+        f32 = [fs[0]]
+        s_step, _, _ = timed_steps(p32, cB, f32, stream, args.steps, args.warmup, flush, False)
+        _, _, s_stats = timed_steps(p32, cB, f32, stream, args.steps, 0, flush, True)
+        s_err = p32[0].exec(ce).cpu().numpy()[0] if want_err else None
+        s_roof = fft_roofline(s_stats, args.steps)
+        fp32 = {"eps": args.fp32_eps, "dtype": dtype_of([p32[0].info["precision"]], term_counts(p32)),
+                "ms_per_step": sum(s_step) / len(s_step),
+                "coeffs_per_s": N * B * len(s_step) / (sum(s_step) / 1000.0),
+                "stage_ms_per_step": {k: round(sum(st[k]["ms"] for st in s_stats) / args.steps, 3)
+                                      for k in s_stats[0]},
+                "roofline": s_roof,
+                "form": "default policy at eps >= 1e-5: FP32 stages, %d vectors per execution" % B}
+        p32[0].destroy()
     del fs
 
     # request streams through the library's server: end to end with host arrays
@@ -474,6 +495,7 @@ def run_ours(args):
                        "form": "one vector per execution, every stage FP64"},
         "served_over_plain": value / plain_cps if plain_cps else None,
         "mixed_precision": mixed,
+        "fp32_stages": fp32,
         "stage_ms_per_step": stage_ms,
         "stage_steps_ms": sum(ev_step_ms) / len(ev_step_ms),
         "term_precision": term_split,
@@ -506,6 +528,9 @@ def run_ours(args):
         rows = base_rows(N, args.cpu_rows, seed_for(4, 99))
         line["error_vs_oracle"] = {str(e): float(np.max(np.abs(f[rows] - ref)) / (e * l1))
                                    for e, f in zip(eps_list, f_err)}
+        if fp32 is not None and s_err is not None:
+            fp32["error_vs_oracle"] = {str(args.fp32_eps): float(np.max(np.abs(s_err[rows] - ref)) /
+                                                                 (args.fp32_eps * l1))}
         if mixed:
             mixed["error_vs_oracle"] = {str(e): float(np.max(np.abs(f[rows] - ref)) / (e * l1))
                                         for e, f in zip(eps_list, m_err)}
@@ -614,7 +639,8 @@ def fft_roofline(stats, steps):
             e = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": (gbs or 0.0) / peak,
                  "traffic": None, "peak_source": src,
                  "kernel": "k_fft_pass_reg / k_fft_small<float2> (FP32 transforms, forward + inverse)",
-                 "bytes_model": "each pass reads and writes every point once (16 B per complex float)",
+                 "bytes_model": "each pass reads and writes every point once (8 B read + 8 B written per "
+                                "complex float point)",
                  "gflops_5FlogF": ach}
         e.update(common)
         return e
