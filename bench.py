@@ -401,6 +401,7 @@ def run_ours(args):
                         "at plan creation on the plan's workspace (ms of one launch sequence)"}
     stage_ms = {k: round(sum(st[k]["ms"] for st in stats) / args.steps, 3) for k in stats[0]}
     roofline = fft_roofline(stats, args.steps)
+    hbm_stages = stage_hbm(stats, args.steps)
     precs = [p.info["precision"] for p in plans]
     terms = term_counts(plans)
     dtype = dtype_of(precs, terms)
@@ -500,6 +501,7 @@ def run_ours(args):
         "stage_steps_ms": sum(ev_step_ms) / len(ev_step_ms),
         "term_precision": term_split,
         "roofline": roofline,
+        "hbm_stages": hbm_stages,
         "tensor_core_pass": tc_pass,
         "fft_autotune": autotune,
         "e2e": {"value": served_e2e, "unit": "coeffs/s", "h2d_bytes_per_step": coeffs_per_step * 8,
@@ -601,6 +603,22 @@ def dtype_of(precs, terms):
     kinds = ["f64" if (1 in precs or terms[0]) else None, "df64" if (3 in precs or terms[1]) else None,
              "f32" if (2 in precs or terms[2]) else None]
     return "+".join(k for k in kinds if k)
+
+
+def stage_hbm(stats, steps):
+    """The streaming stages besides the transforms, against the measured HBM copy rate: the segment
+    sums (`k_seg_mac`) and the row sums (`k_out`, and `k_add_lanes` when the lanes run)."""
+    peak, src = hbm_peak()
+    out = {"peak": peak, "unit": "GB/s", "peak_source": src,
+           "bytes_model": "every operand read once and every result written once"}
+    for k, kern in (("pointwise", "k_seg_mac"), ("out", "k_out")):
+        ms = sum(st[k]["ms"] for st in stats)
+        by = sum(st[k]["bytes"] for st in stats)
+        gbs = by / (ms / 1000.0) / 1e9 if ms > 0 else None
+        out[k] = {"kernel": kern, "ms_per_step": ms / steps, "gbytes_per_step": by / steps / 1e9,
+                  "launches": sum(st[k]["launches"] for st in stats) // steps, "achieved": gbs,
+                  "frac": (gbs / peak) if gbs else None}
+    return out
 
 
 def fft_roofline(stats, steps):

@@ -364,7 +364,9 @@ typedef struct {
   double ms;         /* summed kernel time from CUDA events on the execution stream (0 when timing is off) */
   double flops;      /* algorithmic floating-point operations (FFT: 5 F log2 F per column transform) */
   double entries;    /* near field: matrix entries evaluated (times right-hand sides) */
-  double bytes;      /* algorithmic DRAM bytes (FFT: each pass reads and writes every point once, 32 B) */
+  double bytes;      /* algorithmic DRAM bytes: FFT, each pass reads and writes every point once (32 B
+                        per FP64 point); segment sums and row sums, every operand read once and every
+                        result written once (0 for the other stages) */
   int64_t launches;  /* kernel launches */
 } hankel_stage_stat;
 

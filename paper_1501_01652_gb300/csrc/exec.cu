@@ -1043,7 +1043,9 @@ int run_block(DevicePlan* d, const DevicePlan::ExecCtx* x, const DevBlock& db, c
         StageScope sc(d, HANKEL_STAGE_POINTWISE, st, record);
         launch_seg_mac<C>(res, H, other, b.F, b.nseg, nc, st);
         HK_LAUNCHED();
-        sc.done(1, 8.0 * (double)b.F * (double)b.nseg * nc, 0.0);
+        // every segment spectrum and chirp spectrum read once, every sum written once
+        sc.done(1, 8.0 * (double)b.F * (double)b.nseg * nc, 0.0,
+                (double)sizeof(C) * (double)b.F * ((double)b.nseg * (nc + 1) + nc));
       }
       StageScope sc(d, fst, st, record);
       int np = 0;
@@ -1070,7 +1072,11 @@ int run_block(DevicePlan* d, const DevicePlan::ExecCtx* x, const DevBlock& db, c
                  nc, c0, tg.nl, f, ldf, tg.Ut, std::is_same<C, double2>::value ? nullptr : x->cexp};
       launch_out<C>(oa, st);
       HK_LAUNCHED();
-      sc.done(1, 0.0, 0.0);
+      // the block's rows of every transform and of every distinct row weight read once, and the
+      // chunk's right-hand sides of f read and written once
+      const int64_t nr = (c0 + nc - 1) / tg.nl - c0 / tg.nl + 1;
+      sc.done(1, 0.0, 0.0,
+              (double)b.R * ((double)sizeof(C) * (nc + std::min<int64_t>(nc, tg.nl)) + 16.0 * (double)nr));
     }
   }
   return HANKEL_OK;
@@ -1192,7 +1198,7 @@ int run_all(DevicePlan* d, DevicePlan::ExecCtx* x, const HostPlan& hp, const dou
     const double* acc[2] = {x->lanes[1].acc, d->nlanes > 2 ? x->lanes[2].acc : nullptr};
     launch_add_lanes(f, ldf, acc, d->nlanes - 1, d->hpN, nrhs, st);
     HK_LAUNCHED();
-    sc.done(1, 0.0, 0.0);
+    sc.done(1, 0.0, 0.0, 8.0 * (double)(d->nlanes + 1) * (double)d->hpN * nrhs);
   }
   return HANKEL_OK;
 }

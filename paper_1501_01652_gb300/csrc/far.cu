@@ -47,6 +47,8 @@ __global__ void __launch_bounds__(256) k_out(OutArgs a) {
   for (int64_t rhs = r_first + blockIdx.y; rhs <= r_last; rhs += gridDim.y) {
     const int64_t lo = max(a.c0, rhs * a.ncols), hi = min(a.c0 + a.nc, (rhs + 1) * a.ncols);
     R ar = 0;
+    // unrolled so that several iterations' loads are in flight; the sum keeps its order
+#pragma unroll 4
     for (int64_t g = lo; g < hi; ++g) {
       const int64_t li = g - rhs * a.ncols;
       const C w = ldgc(&Ut[li * a.R]);
@@ -57,35 +59,44 @@ __global__ void __launch_bounds__(256) k_out(OutArgs a) {
   }
 }
 
-// Overlap-add of column segments: out[cc][t] = sum_s in[cc*nseg + s][t] H[s][t]. A CTA covers
-// kMacPts consecutive points of one column; its kMacLanes thread rows split the segments
-// (s = lane, lane + kMacLanes, ...) and the partial sums are added in a fixed order.
-constexpr int kMacPts = 32, kMacLanes = 8;
+// Overlap-add of column segments: out[cc][t] = sum_s in[cc*nseg + s][t] H[s][t]. A CTA of
+// kMacThreads threads covers P = kMacThreads / L consecutive points of one column; its L thread
+// rows split the segments (s = lane, lane + L, ...) and the L partial sums are added in a fixed
+// order. L (1, 2, 4 or 8) depends on the block alone (its segment count and F), so a column's
+// result does not depend on how many columns run together.
+constexpr int kMacThreads = 256, kMacLogThreads = 8;
 
 template <class C>
-__global__ void __launch_bounds__(kMacPts* kMacLanes) k_seg_mac(const C* __restrict__ in, const C* __restrict__ H,
-                                                                 C* __restrict__ out, int64_t F, int64_t nseg) {
+__global__ void __launch_bounds__(kMacThreads) k_seg_mac(const C* __restrict__ in, const C* __restrict__ H,
+                                                          C* __restrict__ out, int64_t F, int64_t nseg, int logL) {
   typedef typename RealOf<C>::type R;
-  __shared__ R sr[kMacLanes][kMacPts], si[kMacLanes][kMacPts];
-  const int pt = threadIdx.x % kMacPts, lane = threadIdx.x / kMacPts;
-  const int64_t tiles = F / kMacPts;
+  __shared__ R sr[kMacThreads], si[kMacThreads];
+  const int logP = kMacLogThreads - logL;
+  const int pt = threadIdx.x & ((1 << logP) - 1), lane = threadIdx.x >> logP;
+  const int64_t tiles = F >> logP;
   const int64_t cc = blockIdx.x / tiles;
-  const int64_t t = (blockIdx.x - cc * tiles) * kMacPts + pt;
+  const int64_t t = ((blockIdx.x - cc * tiles) << logP) + pt;
   const C* x = in + cc * nseg * F + t;
   R ar = 0, ai = 0;
-  for (int64_t s = lane; s < nseg; s += kMacLanes) {
+  // unrolled so that several iterations' loads are in flight; the sums keep their order
+#pragma unroll 4
+  for (int64_t s = lane; s < nseg; s += (1 << logL)) {
     const C v = x[s * F];
     const C h = ldgc(&H[s * F + t]);
     ar = fmar(v.x, h.x, fmar(-v.y, h.y, ar));
     ai = fmar(v.x, h.y, fmar(v.y, h.x, ai));
   }
-  sr[lane][pt] = ar;
-  si[lane][pt] = ai;
+  if (logL == 0) {  // the same for the whole CTA
+    out[cc * F + t] = mkc(ar, ai);
+    return;
+  }
+  sr[threadIdx.x] = ar;
+  si[threadIdx.x] = ai;
   __syncthreads();
   if (lane == 0) {
-    for (int j = 1; j < kMacLanes; ++j) {
-      ar += sr[j][pt];
-      ai += si[j][pt];
+    for (int j = 1; j < (1 << logL); ++j) {
+      ar += sr[(j << logP) + pt];
+      ai += si[(j << logP) + pt];
     }
     out[cc * F + t] = mkc(ar, ai);
   }
@@ -267,9 +278,14 @@ void launch_diag_scale(const double* x, int64_t ldx, const double* v, double sca
 
 template <class C>
 void launch_seg_mac(const C* in, const C* H, C* out, int64_t F, int64_t nseg, int nc, cudaStream_t st) {
-  // F >= 64 is a multiple of kMacPts
-  const int64_t blocks = (F / kMacPts) * nc;
-  k_seg_mac<C><<<(unsigned)blocks, kMacPts * kMacLanes, 0, st>>>(in, H, out, F, nseg);
+  // thread rows per point: one while a thread's segment loop is short, up to eight for long ones;
+  // a CTA's points (kMacThreads / L) stay within one column (F >= 64, a power of two)
+  int logF = 0;
+  while ((int64_t(1) << logF) < F) ++logF;
+  int logL = nseg >= 128 ? 3 : nseg >= 64 ? 2 : nseg >= 32 ? 1 : 0;
+  logL = std::max(logL, kMacLogThreads - logF);
+  const int64_t blocks = (F >> (kMacLogThreads - logL)) * nc;
+  k_seg_mac<C><<<(unsigned)blocks, kMacThreads, 0, st>>>(in, H, out, F, nseg, logL);
 }
 
 void launch_add_lanes(double* f, int64_t ldf, const double* const* acc, int nacc, int64_t N, int nrhs,
