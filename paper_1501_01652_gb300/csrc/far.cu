@@ -44,16 +44,20 @@ __global__ void __launch_bounds__(256) k_out(OutArgs a) {
   const C* Y = reinterpret_cast<const C*>(a.Y) + sg * a.F + (kp - sg * a.Sr) + a.off;
   const C* Ut = reinterpret_cast<const C*>(a.Ut) + kp;
   const int64_t r_first = a.c0 / a.ncols, r_last = (a.c0 + a.nc - 1) / a.ncols;
+  const int64_t ystride = a.nsegr * a.F;
   for (int64_t rhs = r_first + blockIdx.y; rhs <= r_last; rhs += gridDim.y) {
     const int64_t lo = max(a.c0, rhs * a.ncols), hi = min(a.c0 + a.nc, (rhs + 1) * a.ncols);
     R ar = 0;
+    const C* wp = Ut + (lo - rhs * a.ncols) * a.R;
+    const C* yp = Y + (lo - a.c0) * ystride;
     // unrolled so that several iterations' loads are in flight; the sum keeps its order
 #pragma unroll 4
-    for (int64_t g = lo; g < hi; ++g) {
-      const int64_t li = g - rhs * a.ncols;
-      const C w = ldgc(&Ut[li * a.R]);
-      const C y = Y[(g - a.c0) * a.nsegr * a.F];
+    for (int g = (int)(hi - lo); g > 0; --g) {
+      const C w = ldgc(wp);
+      const C y = *yp;
       ar = fmar(w.x, y.x, fmar(-w.y, y.y, ar));
+      wp += a.R;
+      yp += ystride;
     }
     a.f[rhs * a.ldf + i] += a.cexp ? ldexp((double)ar, a.cexp[rhs]) : (double)ar;
   }
@@ -76,15 +80,19 @@ __global__ void __launch_bounds__(kMacThreads) k_seg_mac(const C* __restrict__ i
   const int64_t tiles = F >> logP;
   const int64_t cc = blockIdx.x / tiles;
   const int64_t t = ((blockIdx.x - cc * tiles) << logP) + pt;
-  const C* x = in + cc * nseg * F + t;
+  const C* x = in + cc * nseg * F + lane * F + t;
+  const C* hp = H + lane * F + t;
+  const int64_t step = F << logL;
   R ar = 0, ai = 0;
   // unrolled so that several iterations' loads are in flight; the sums keep their order
 #pragma unroll 4
-  for (int64_t s = lane; s < nseg; s += (1 << logL)) {
-    const C v = x[s * F];
-    const C h = ldgc(&H[s * F + t]);
+  for (int s = (int)((nseg - lane + (1 << logL) - 1) >> logL); s > 0; --s) {
+    const C v = *x;
+    const C h = ldgc(hp);
     ar = fmar(v.x, h.x, fmar(-v.y, h.y, ar));
     ai = fmar(v.x, h.y, fmar(v.y, h.x, ai));
+    x += step;
+    hp += step;
   }
   if (logL == 0) {  // the same for the whole CTA
     out[cc * F + t] = mkc(ar, ai);
