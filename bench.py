@@ -606,18 +606,25 @@ def dtype_of(precs, terms):
 
 
 def stage_hbm(stats, steps):
-    """The streaming stages besides the transforms, against the measured HBM copy rate: the segment
-    sums (`k_seg_mac`) and the row sums (`k_out`, and `k_add_lanes` when the lanes run)."""
+    """The segment sums (`k_seg_mac`) and row sums (`k_out`) against both of their bounds: the
+    measured HBM copy rate for their algorithmic bytes, and the FP64 pipe for their complex
+    multiply-adds (4 DFMA per point and segment, 2 per column and row), which binds on this part."""
     peak, src = hbm_peak()
     out = {"peak": peak, "unit": "GB/s", "peak_source": src,
-           "bytes_model": "every operand read once and every result written once"}
+           "bytes_model": "every operand read once and every result written once",
+           "flops_model": "segment sums 8 flop per point and segment, row sums 4 flop per column and row",
+           "fp64_peak_gflops": FP64_PEAK_GFLOPS, "fp64_measured_gflops": FP64_MEASURED_GFLOPS}
     for k, kern in (("pointwise", "k_seg_mac"), ("out", "k_out")):
         ms = sum(st[k]["ms"] for st in stats)
         by = sum(st[k]["bytes"] for st in stats)
+        fl = sum(st[k]["flops"] for st in stats)
         gbs = by / (ms / 1000.0) / 1e9 if ms > 0 else None
+        gfl = fl / (ms / 1000.0) / 1e9 if ms > 0 else None
         out[k] = {"kernel": kern, "ms_per_step": ms / steps, "gbytes_per_step": by / steps / 1e9,
                   "launches": sum(st[k]["launches"] for st in stats) // steps, "achieved": gbs,
-                  "frac": (gbs / peak) if gbs else None}
+                  "frac": (gbs / peak) if gbs else None, "gflops": gfl,
+                  "frac_of_fp64_peak": (gfl / FP64_PEAK_GFLOPS) if gfl else None,
+                  "frac_of_measured_fp64": (gfl / FP64_MEASURED_GFLOPS) if gfl else None}
     return out
 
 

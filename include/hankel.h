@@ -362,7 +362,8 @@ enum hankel_stage {
 /* Accumulated statistics of one stage since timing was (re)enabled. */
 typedef struct {
   double ms;         /* summed kernel time from CUDA events on the execution stream (0 when timing is off) */
-  double flops;      /* algorithmic floating-point operations (FFT: 5 F log2 F per column transform) */
+  double flops;      /* algorithmic floating-point operations (FFT: 5 F log2 F per column transform;
+                        segment sums: 8 per point and segment; row sums: 4 per column and row) */
   double entries;    /* near field: matrix entries evaluated (times right-hand sides) */
   double bytes;      /* algorithmic DRAM bytes: FFT, each pass reads and writes every point once (32 B
                         per FP64 point); segment sums and row sums, every operand read once and every

@@ -1075,7 +1075,7 @@ int run_block(DevicePlan* d, const DevicePlan::ExecCtx* x, const DevBlock& db, c
       // the block's rows of every transform and of every distinct row weight read once, and the
       // chunk's right-hand sides of f read and written once
       const int64_t nr = (c0 + nc - 1) / tg.nl - c0 / tg.nl + 1;
-      sc.done(1, 0.0, 0.0,
+      sc.done(1, 4.0 * (double)b.R * nc, 0.0,
               (double)b.R * ((double)sizeof(C) * (nc + std::min<int64_t>(nc, tg.nl)) + 16.0 * (double)nr));
     }
   }
